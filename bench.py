@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the partial-assembly hot path on GB300; prints ONE JSON line (rank 0).
+
+Workload (one "step"): the 64^3-hex, p = 3 (Q = 5) Poisson problem on the +-0.1h perturbed unit
+cube (7,189,057 dofs): Jacobi-preconditioned CG to a relative residual of 1e-8 from a zero guess,
+through the C ABI (fe_pcg): diagonal assembly, boundary conditions, one fused PA diffusion apply
+per iteration, FP64 vector updates and inner products, and the final true-residual apply.
+Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the timed region.
+
+  value        GDOF/s = ndofs * (PCG applies) / time, summed over ranks: the apply throughput
+               the solver sustains end to end on the device (every PCG kernel inside the time);
+  ms_per_step  time of one PCG solve to 1e-8 (the metric's time-to-solution part);
+  e2e          the same, through host buffers: pinned b -> device, fe_pcg, x -> pinned host;
+  roofline     of the dominant kernel (the fused apply), timed alone with CUDA events;
+  cpu_baseline the CPU oracle (element-matrix apply) on a bounded sample of the same mesh.
+
+--impl reference times the CPU oracle alone (the reference of this build) on the same metric.
+Multi-GPU (torchrun): every rank solves its own copy of the problem (independent problems, weak
+scaling, no collective on the data path); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ELEM, ORDER, RTOL = 64, 3, 1e-8
+MAXIT = 20000
+METRIC = "GDOF/s of FP64 PA diffusion apply (frac of HBM roofline); PCG time-to-1e-8 residual"
+UNIT = "GDOF/s"
+FP64_DFMA_PER_CLK_PER_SM = 2           # measured on GB300 (FP64 peak)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic(ndofs, ne, p, q, diffusion=True):
+    """Minimum bytes and FP64 flops of one apply: x read once, y written once, the dof map and
+    the quadrature data read once; flops of the sum-factorised contractions and the pointwise D."""
+    D = p + 1
+    qd = (6 if diffusion else 1) * q ** 3 * 8
+    nbytes = 16 * ndofs + ne * (4 * D ** 3 + qd)
+    if diffusion:
+        f = 2 * (4 * q * D ** 3 + 6 * q * q * D * D + 6 * q ** 3 * D) + 15 * q ** 3
+    else:
+        f = 4 * (q * D ** 3 + q * q * D * D + q ** 3 * D) + q ** 3
+    return nbytes, ne * f
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region (200 ms period)."""
+
+    REASONS = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.result = None
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.REASONS[1:], f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if sm:
+            self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                           "samples": len(sm), "reasons": sorted(reasons)}
+        return False
+
+
+def cpu_oracle_sample(budget_s=12.0):
+    """The oracle's element-matrix apply (as it stands) on an 8^3-element corner block of the
+    workload mesh, repeated for ~budget_s; GDOF/s scaled by the workload's dofs per element."""
+    import numpy as np
+    from oracle import operator as oop
+    from paper_2603_09038_gb300.inputs import perturbed_vertices, uniform_vector
+    full = perturbed_vertices(N_ELEM, N_ELEM, N_ELEM)
+    s = 8
+    idx = np.arange((N_ELEM + 1) ** 3).reshape(N_ELEM + 1, N_ELEM + 1, N_ELEM + 1)
+    sub = full[idx[: s + 1, : s + 1, : s + 1].reshape(-1)]
+    prob = oop.Problem(s, s, s, ORDER, sub)
+    x = uniform_vector(prob.ndofs, seed=0)
+    dofs_per_elem = (N_ELEM * ORDER + 1) ** 3 / N_ELEM ** 3
+    reps, t0, c0 = 0, time.perf_counter(), os.times()
+    while True:
+        oop.apply(prob, x, oop.DIFFUSION)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    c1 = os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    gdofs = reps * prob.ne * dofs_per_elem / el / 1e9
+    return {"value": gdofs, "unit": UNIT, "cores": max(1, int(round(cpu / el))),
+            "kind": "oracle",
+            "sample": "oracle element-matrix diffusion apply on an 8^3-element block of the "
+                      "64^3 p=3 mesh, %d applies in %.1f s; rate scaled by the workload's "
+                      "%.2f dofs per element" % (reps, el, dofs_per_elem),
+            "seconds": el, "applies": reps}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step, results = [], None
+    budget = max(2.0, min(12.0, 60.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(budget)
+        if i >= args.warmup:
+            per_step.append(r)
+    tot_t = sum(r["seconds"] for r in per_step)
+    value = sum(r["value"] * r["seconds"] for r in per_step) / tot_t
+    last = per_step[-1]
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * tot_t / len(per_step), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "poisson_64cubed_p3_jacobi_pcg", "elements": N_ELEM ** 3,
+                      "order": ORDER, "q1d": ORDER + 2, "ndofs": (N_ELEM * ORDER + 1) ** 3,
+                      "parallelism": "cpu"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
+                            "kind": "oracle", "sample": last["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    fe.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, p = args.n, args.p
+    V = perturbed_vertices(n, n, n)
+    mesh = fe.fe_mesh_setup(n, n, n, p, V)
+    pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+    ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
+    q = p + 2
+    stream = torch.cuda.current_stream()
+    fe.fe_pa_set_variant(pa, args.variant)
+    b = torch.empty(ndofs, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    fe.fe_load_vector_sine(pa, b)
+    torch.cuda.synchronize()
+
+    def solve():
+        st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+        if st != fe.FE_OK:
+            raise RuntimeError("fe_pcg failed: %d %s" % (st, fe.fe_last_error()))
+        return stats
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K PCG solves, device time by CUDA events on the launching stream
+    smi_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local_rank
+    applies, iters, launches = 0, [], 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(smi_index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = solve()
+            applies += s["iters"] + 1
+            iters.append(s["iters"])
+            launches += s["launches"]
+            last_stats = s
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    t = e0.elapsed_time(e1) / 1000.0
+    if dist is not None:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * ndofs * applies / t / 1e9
+
+    # ---- end to end through host buffers: pinned b -> device, solve, x -> pinned host
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty(ndofs, dtype=torch.float64).pin_memory()
+    e2e_applies = 0
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.copy_(b_host, non_blocking=True)
+        s = solve()
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_applies += s["iters"] + 1
+    te = time.perf_counter() - t0
+    barrier()
+    if dist is not None:
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": world * ndofs * e2e_applies / te / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * ndofs, "d2h_bytes_per_step": 8 * ndofs,
+           "ms_per_step": 1000.0 * te / args.steps}
+
+    # ---- the dominant kernel alone: fused diffusion apply, CUDA events on its stream
+    def time_apply(variant, reps):
+        fe.fe_pa_set_variant(pa, variant)
+        xa = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
+        ya = torch.empty_like(xa)
+        for _ in range(3):
+            fe.fe_apply(pa, fe.FE_DIFFUSION, variant, xa, ya, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, z in ev:
+            a.record(stream)
+            fe.fe_apply(pa, fe.FE_DIFFUSION, variant, xa, ya, stream)
+            z.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(z) for a, z in ev)
+        return ms
+
+    nbytes, flops = algorithmic(ndofs, ne, p, q, True)
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = 152 * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
+    kernels = {}
+    for variant in ("f64", "f32x2"):
+        ms = time_apply(variant, 20)
+        kernels[variant] = {
+            "ms": ms, "gdofs": ndofs / (ms * 1e-3) / 1e9,
+            "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+            "fp64_tflops_equiv": flops / (ms * 1e-3) / 1e12,
+        }
+    fe.fe_pa_set_variant(pa, args.variant)
+    k = kernels[args.variant]
+    if args.variant == "f64":
+        roof = {"bound": "alu", "achieved": k["fp64_tflops_equiv"], "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": k["fp64_tflops_equiv"] / fp64_peak,
+                "traffic": None, "kernel": "k_pa_apply<D=4,Q=5,diffusion,f64>",
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (DFMA rate "
+                               "measured on GB300)" % sm_max,
+                "hbm": {"achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                        "frac": k["hbm_frac"], "peak_source": peak_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": k["hbm_frac"], "traffic": None,
+                "kernel": "k_pa_apply<D=4,Q=5,diffusion,f32x2>", "peak_source": peak_src}
+    roof["bytes_per_launch"] = nbytes
+    roof["flops_per_launch"] = flops
+    roof["launch_ms"] = k["ms"]
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.variant == "f64" else "f32x2",
+           "data": "synthetic",
+           "config": {"workload": "poisson_64cubed_p3_jacobi_pcg", "elements": ne, "order": p,
+                      "q1d": q, "ndofs": ndofs, "rtol": args.rtol, "preconditioner": "jacobi",
+                      "variant": args.variant, "pcg_iters": iters[-1] if iters else None,
+                      "applies_per_step": applies / max(1, args.steps),
+                      "l2_flush": "inputs larger than L2 (1.57 GB quadrature data per apply)",
+                      "parallelism": "independent problem per GPU"},
+           "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
+           "pcg_time_to_1e-8_s": t / args.steps,
+           "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
+    if clk.result:
+        out["clocks"] = clk.result
+    fe.fe_pa_destroy(pa)
+    fe.fe_mesh_destroy(mesh)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_oracle_sample(args.cpu_seconds)
+            out["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=["f64", "f32x2"], default="f64")
+    ap.add_argument("--n", type=int, default=N_ELEM)
+    ap.add_argument("--p", type=int, default=ORDER)
+    ap.add_argument("--rtol", type=float, default=RTOL)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

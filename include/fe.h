@@ -1,0 +1,145 @@
+/*
+ * fe.h -- C ABI of libfe: GB300-native partial-assembly (PA) finite element operators.
+ *
+ * The library applies the high-order H1 diffusion and mass operators on hexahedral meshes in the
+ * matrix-free partial-assembly form  y = P^T G^T B^T D B G P x  (paper Section II-B, Eq. (1)):
+ *   G   element restriction (gather of element dofs through a dof map; G^T is scatter-add),
+ *   B   tensor-product basis, applied by sum factorisation as 1D contractions (Eq. (2)),
+ *   D   the block-diagonal operator at quadrature points, precomputed once ("partial assembly"),
+ *   P   the parallel restriction, the identity on one GPU.
+ * Each apply is one fused CUDA kernel: gather, forward contractions, D, transposed
+ * contractions and atomic scatter-add (the fusion of Section III-G).
+ *
+ * Conventions (every entry point):
+ *  - Returns FE_OK (0) or a negative fe_status; nothing aborts, traps or asserts on the device.
+ *    fe_last_error() gives a message for the calling thread's last non-OK status.
+ *  - "dev_" pointers are caller-owned device memory (e.g. torch.empty(..., device='cuda')
+ *    .data_ptr()); "host_" pointers are caller-owned host memory.  Vectors are FP64, length
+ *    ndofs, contiguous.  Input and output vectors must not alias.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default stream).  Applies are
+ *    asynchronous and stream-ordered; setup calls and fe_pcg synchronise the stream.
+ *  - Handles (fe_mesh, fe_pa) are opaque, library-owned, freed by their *_destroy function, and
+ *    not safe for concurrent use from several host threads.
+ *
+ * Numbering (the paper is silent; standard lexicographic choices): elements e = ex + nx*(ey +
+ * ny*ez); element-local dofs a = i + D*(j + D*k), D = order+1 (x fastest); global dofs on the
+ * (nx*p+1)(ny*p+1)(nz*p+1) GLL lattice, x fastest; vertices on the (nx+1)(ny+1)(nz+1) lattice.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_mesh fe_mesh;
+typedef struct fe_pa fe_pa;
+
+typedef enum {
+  FE_OK = 0,
+  FE_ERR_ARG = -1,           /* invalid argument (null pointer, bad size, inverted element, ...) */
+  FE_ERR_CUDA = -2,          /* a CUDA runtime call failed; see fe_last_error()                  */
+  FE_ERR_OOM = -3,           /* device allocation failed                                         */
+  FE_ERR_UNSUPPORTED = -4,   /* order / quadrature / variant combination not built               */
+  FE_ERR_NOT_CONVERGED = -5, /* fe_pcg hit maxit before reaching rtol                            */
+  FE_ERR_BREAKDOWN = -6,     /* fe_pcg found p.Ap <= 0 (operator not SPD on the free dofs)        */
+  FE_ERR_NAN = -7            /* fe_pcg met a NaN or Inf                                          */
+} fe_status;
+
+typedef enum { FE_DIFFUSION = 1, FE_MASS = 2 } fe_op;
+
+typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1 } fe_pc;
+
+/* Arithmetic of the apply kernels.  All variants take and return FP64 vectors.
+ *  FE_VARIANT_F64     FP64 FMA on the FP64 pipe (IEEE double throughout).
+ *  FE_VARIANT_F32X2   FP64-accurate float-float ("double-FP32") arithmetic on the FP32 pipe:
+ *                     each value is an unevaluated sum hi + lo of two floats (about 47 bits of
+ *                     significand), products and sums by error-free transformations (Dekker's
+ *                     product with FMA, Knuth's TwoSum).  Inputs must lie within the float
+ *                     exponent range (|v| < 3e38; values below ~1e-22 lose relative accuracy).
+ *  FE_VARIANT_F64_DMMA FP64 with the 1D contractions on the FP64 tensor-core instruction
+ *                     mma.sync.m8n8k4.f64 (the paper's DMMA, Section III-B).               */
+typedef enum { FE_VARIANT_F64 = 0, FE_VARIANT_F32X2 = 1, FE_VARIANT_F64_DMMA = 2 } fe_variant;
+
+typedef struct {
+  int iters;             /* iterations performed                                              */
+  double rel_resid;      /* recursive ||r||_2 / ||b||_2 at exit                               */
+  double true_rel_resid; /* ||b - A x||_2 / ||b||_2 recomputed at exit (FP64 variant apply)  */
+  double seconds;        /* host wall time of the call, including the diagonal assembly       */
+  int launches;          /* kernels of this library launched by the call (no-op ones included) */
+} fe_pcg_stats;
+
+/* Builds the mesh topology on the device: the element dof map (int32 [ne][D^3], the G of
+ * Eq. (1)), the boundary-dof mask and the 1D GLL nodes.  host_vertices: FP64
+ * [(nx+1)(ny+1)(nz+1)][3], x fastest, copied.  order 1..8.  Synchronous. */
+int fe_mesh_setup(int nx, int ny, int nz, int order, const double* host_vertices, fe_mesh** out);
+
+/* Sizes of a mesh: global dofs (incl. boundary), elements, order. */
+int fe_mesh_sizes(const fe_mesh* mesh, int64_t* ndofs, int64_t* nelems, int* order);
+
+/* Copies the boundary-dof mask (uint8 [ndofs], 1 on the cube's boundary lattice) to dev_mask. */
+int fe_mesh_boundary_mask(const fe_mesh* mesh, uint8_t* dev_mask, void* stream);
+
+/* Copies the element dof map (int32 [ne][D^3]) to dev_map. */
+int fe_mesh_dof_map(const fe_mesh* mesh, int32_t* dev_map, void* stream);
+
+/* Partial assembly (Section II-B: "precompute and store the block-diagonal D at quadrature
+ * points").  Computes per element and Gauss point the trilinear Jacobian J, det J and
+ * adj(J), and stores
+ *   diffusion  D_q = w_q c_e adj(J) adj(J)^T / det J   (6 symmetric entries)
+ *   mass       M_q = w_q c_e det J
+ * q1d: Gauss points per axis, 0 => order+2 (the only value built).  dev_coeff: FP64 [ne]
+ * piecewise-constant coefficient, or NULL for 1.  ops: FE_DIFFUSION | FE_MASS (bitwise or).
+ * Fails with FE_ERR_ARG if an element has det J <= 0 at a Gauss point.  Synchronous. */
+int fe_pa_setup(const fe_mesh* mesh, int q1d, const double* dev_coeff, int ops, void* stream,
+                fe_pa** out);
+
+/* Selects the arithmetic of subsequent applies, diagonal-free; stream-ordered.  Switching to or
+ * from FE_VARIANT_F32X2 re-encodes the stored quadrature data in place. */
+int fe_pa_set_variant(fe_pa* pa, int variant, void* stream);
+int fe_pa_get_variant(const fe_pa* pa, int* variant);
+
+/* y = A x on the full L-vector (no boundary conditions), with the handle's variant.
+ * Overwrites y (it is zeroed, then accumulated by atomic scatter-add).  Asynchronous. */
+int fe_apply_diffusion(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream);
+int fe_apply_mass(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream);
+/* Same for op = FE_DIFFUSION or FE_MASS with an explicit variant. */
+int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* dev_y,
+             void* stream);
+
+/* diag(A) (no boundary conditions) by a sum-factorised diagonal kernel in FP64 (with
+ * FE_VARIANT_F32X2 data, each stored pair is widened to FP64 first).  Asynchronous. */
+int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream);
+
+/* Load vector of the manufactured problem -div grad u = f, u = sin(pi x) sin(pi y) sin(pi z):
+ * b_a = sum_e sum_q w_q det J f(x_q) phi_a(x_q), f = 3 pi^2 u, with the operator's Gauss rule.
+ * Asynchronous. */
+int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
+
+/* Jacobi (or un-) preconditioned CG for A_bc x = b with homogeneous Dirichlet conditions on the
+ * mesh boundary: A_bc = (1-m) A (1-m) + m (m = boundary mask).  b's boundary entries are
+ * ignored; x is overwritten (zero initial guess; x = 0 on the boundary).  Stops when the
+ * recursive residual satisfies ||r||_2 <= rtol ||b||_2 or after maxit iterations.  FP64 vectors
+ * and deterministic FP64 inner products; applies use the handle's variant.  Work vectors are
+ * allocated on first use and cached in the handle.  Synchronous; fills *stats (may be NULL).
+ * Returns FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN or FE_ERR_NAN (x holds the last
+ * iterate in every case). */
+int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
+           fe_pcg_stats* stats, void* stream);
+
+void fe_pa_destroy(fe_pa* pa);
+void fe_mesh_destroy(fe_mesh* mesh);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* fe_last_error(void);
+
+/* Library version string. */
+const char* fe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

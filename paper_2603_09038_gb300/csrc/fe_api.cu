@@ -1,0 +1,601 @@
+// C ABI of libfe: mesh topology (G), partial assembly (D at quadrature points), apply dispatch,
+// diagonal and load-vector kernels.  See include/fe.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "fe_internal.h"
+
+// ------------------------------------------------------------------------------- errors
+namespace fe {
+
+static thread_local std::string g_last_error;
+
+int set_error(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_error(cudaError_t err, const char* what) {
+  if (err == cudaSuccess) return FE_OK;
+  const int status = (err == cudaErrorMemoryAllocation) ? FE_ERR_OOM : FE_ERR_CUDA;
+  return set_error(status, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+}  // namespace fe
+
+using namespace fe;
+
+#define FE_CHECK_CUDA(call, what)                   \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_error(e_, what); \
+  } while (0)
+
+// ------------------------------------------------------------------------------- kernels
+namespace {
+
+struct Rule {
+  double pts[kMaxQ];
+  double wts[kMaxQ];
+};
+
+struct Tables {
+  double B[kMaxQ * kMaxD];
+  double G[kMaxQ * kMaxD];
+};
+
+// Element dof map: map[e][a] for a = i + D*(j + D*k) -> lexicographic GLL lattice index.
+__global__ void k_dof_map(int32_t* __restrict__ map, int nx, int ny, int p, int64_t Nx,
+                          int64_t Ny, int64_t ne) {
+  const int D = p + 1, D3 = D * D * D;
+  const int64_t n = ne * D3;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / D3;
+    const int a = (int)(t - e * D3);
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    const int i = a % D, j = (a / D) % D, k = a / (D * D);
+    map[t] = (int32_t)((ex * p + i) + Nx * ((ey * p + j) + Ny * (ez * p + k)));
+  }
+}
+
+__global__ void k_boundary_mask(uint8_t* __restrict__ mask, int64_t Nx, int64_t Ny, int64_t Nz) {
+  const int64_t n = Nx * Ny * Nz;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = g % Nx, iy = (g / Nx) % Ny, iz = g / (Nx * Ny);
+    mask[g] = (ix == 0 || iy == 0 || iz == 0 || ix == Nx - 1 || iy == Ny - 1 || iz == Nz - 1);
+  }
+}
+
+// Trilinear map of element e at reference point (s, t, u): physical point X and Jacobian
+// J[i][r] = d x_i / d xi_r, from the 8 corners (corner a + 2b + 4c at lattice offset (a, b, c)).
+__device__ void trilinear(const double* __restrict__ V, int nx, int ny, int64_t e, double s,
+                          double t, double u, double X[3], double J[3][3]) {
+  const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+  for (int i = 0; i < 3; ++i) {
+    X[i] = 0.0;
+    J[i][0] = J[i][1] = J[i][2] = 0.0;
+  }
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int64_t v = (ex + a) + (int64_t)(nx + 1) * ((ey + b) + (int64_t)(ny + 1) * (ez + c));
+        const double fa = a ? s : 1.0 - s, fb = b ? t : 1.0 - t, fc = c ? u : 1.0 - u;
+        const double da = a ? 1.0 : -1.0, db = b ? 1.0 : -1.0, dc = c ? 1.0 : -1.0;
+        const double N = fa * fb * fc;
+        const double dN0 = da * fb * fc, dN1 = fa * db * fc, dN2 = fa * fb * dc;
+        for (int i = 0; i < 3; ++i) {
+          const double xv = V[3 * v + i];
+          X[i] += N * xv;
+          J[i][0] += dN0 * xv;
+          J[i][1] += dN1 * xv;
+          J[i][2] += dN2 * xv;
+        }
+      }
+}
+
+// Partial assembly: one thread per (element, Gauss point).
+//   diffusion  D = w c adj(J) adj(J)^T / det J  stored [e][qz][comp][qy][qx]
+//   mass       M = w c det J                    stored [e][qz][qy][qx]
+__global__ void k_qdata(const double* __restrict__ V, int nx, int ny, int64_t ne, int Q,
+                        const Rule rule, const double* __restrict__ coeff,
+                        double* __restrict__ qdd, double* __restrict__ qdm, int* __restrict__ bad) {
+  const int Q2 = Q * Q, Q3 = Q2 * Q;
+  const int64_t n = ne * Q3;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / Q3;
+    const int q = (int)(t - e * Q3);
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / Q2;
+    double X[3], J[3][3];
+    trilinear(V, nx, ny, e, rule.pts[qx], rule.pts[qy], rule.pts[qz], X, J);
+    // adjugate (transpose of the cofactor matrix): adj(J) = det(J) J^{-1}
+    double A[3][3];
+    A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+    if (!(det > 0.0)) atomicExch(bad, 1);
+    const double c = coeff ? coeff[e] : 1.0;
+    const double w = rule.wts[qx] * rule.wts[qy] * rule.wts[qz] * c;
+    if (qdm) qdm[e * Q3 + q] = w * det;
+    if (qdd) {
+      const double s = w / det;
+      // (adj adj^T)[r][s] = sum_k A[r][k] A[s][k]
+      const int rr[6] = {0, 0, 0, 1, 1, 2}, ss[6] = {0, 1, 2, 1, 2, 2};
+      double* out = qdd + e * (int64_t)(6 * Q3) + (int64_t)qz * 6 * Q2 + qy * Q + qx;
+      for (int m = 0; m < 6; ++m) {
+        const int r = rr[m], sc = ss[m];
+        out[m * Q2] = s * (A[r][0] * A[sc][0] + A[r][1] * A[sc][1] + A[r][2] * A[sc][2]);
+      }
+    }
+  }
+}
+
+// Block-level sum-factorised transpose contraction for one element (runtime D, Q):
+// acc[k][j][i] += sum_{qz,qy,qx} Tz[qz][k] Ty[qy][j] Tx[qx][i] F[qz][qy][qx].
+__device__ void contract_transpose(const double* F, const double* Tx, const double* Ty,
+                                   const double* Tz, double* T1, double* T2, double* acc, int D,
+                                   int Q) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < Q * Q * D; t += nt) {
+    const int i = t % D, qy = (t / D) % Q, qz = t / (D * Q);
+    double s = 0.0;
+    for (int qx = 0; qx < Q; ++qx) s = fma(Tx[qx * D + i], F[(qz * Q + qy) * Q + qx], s);
+    T1[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < Q * D * D; t += nt) {
+    const int i = t % D, j = (t / D) % D, qz = t / (D * D);
+    double s = 0.0;
+    for (int qy = 0; qy < Q; ++qy) s = fma(Ty[qy * D + j], T1[(qz * Q + qy) * D + i], s);
+    T2[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < D * D * D; t += nt) {
+    const int i = t % D, j = (t / D) % D, k = t / (D * D);
+    double s = 0.0;
+    for (int qz = 0; qz < Q; ++qz) s = fma(Tz[qz * D + k], T2[(qz * D + j) * D + i], s);
+    acc[t] += s;
+  }
+  __syncthreads();
+}
+
+constexpr int kEltThreads = 64;
+
+struct EltSmem {
+  double F[kMaxQ * kMaxQ * kMaxQ];
+  double T1[kMaxQ * kMaxQ * kMaxD];
+  double T2[kMaxQ * kMaxD * kMaxD];
+  double acc[kMaxD * kMaxD * kMaxD];
+  double tx[kMaxQ * kMaxD], ty[kMaxQ * kMaxD], tz[kMaxQ * kMaxD];
+};
+
+// diag(A): per element sum over the symmetric pairs (r, s) of D^{rs} contracted with the
+// products of the 1D factors of grad phi_r and grad phi_s (B or G per axis), one block per
+// element; mass uses M with B*B on every axis.
+__global__ void __launch_bounds__(kEltThreads) k_diagonal(const int32_t* __restrict__ map,
+                                                          const double* __restrict__ qd,
+                                                          int64_t ne, int D, int Q, int diff,
+                                                          int pairs, const Tables tab,
+                                                          double* __restrict__ diag) {
+  __shared__ EltSmem sm;
+  const int Q2 = Q * Q, Q3 = Q2 * Q, D3 = D * D * D, QD = Q * D;
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int t = threadIdx.x; t < D3; t += blockDim.x) sm.acc[t] = 0.0;
+    const int npairs = diff ? 6 : 1;
+    const int rr[6] = {0, 0, 0, 1, 1, 2}, ss[6] = {0, 1, 2, 1, 2, 2};
+    for (int m = 0; m < npairs; ++m) {
+      const int r = rr[m], s = ss[m];
+      const double scale = (diff && r != s) ? 2.0 : 1.0;
+      for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+        const int qx = t % Q, qy = (t / Q) % Q, qz = t / Q2;
+        const int64_t idx = diff ? e * 6 * Q3 + (int64_t)qz * 6 * Q2 + m * Q2 + qy * Q + qx
+                                 : e * Q3 + t;
+        double v;
+        if (pairs) {  // float-pair encoded data: widen hi + lo
+          const float2 hl = reinterpret_cast<const float2*>(qd)[idx];
+          v = (double)hl.x + (double)hl.y;
+        } else {
+          v = qd[idx];
+        }
+        sm.F[t] = scale * v;
+      }
+      for (int t = threadIdx.x; t < QD; t += blockDim.x) {
+        double f[3];
+        for (int ax = 0; ax < 3; ++ax) {
+          const double fr = (diff && ax == r) ? tab.G[t] : tab.B[t];
+          const double fs = (diff && ax == s) ? tab.G[t] : tab.B[t];
+          f[ax] = fr * fs;
+        }
+        sm.tx[t] = f[0];
+        sm.ty[t] = f[1];
+        sm.tz[t] = f[2];
+      }
+      __syncthreads();
+      contract_transpose(sm.F, sm.tx, sm.ty, sm.tz, sm.T1, sm.T2, sm.acc, D, Q);
+    }
+    for (int t = threadIdx.x; t < D3; t += blockDim.x) atomicAdd(&diag[map[e * D3 + t]], sm.acc[t]);
+    __syncthreads();
+  }
+}
+
+// Load vector of f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z): F[q] = w_q det J f(x_q), then B^T
+// in all three directions, scatter-added; one block per element.
+__global__ void __launch_bounds__(kEltThreads) k_load_sine(const double* __restrict__ V, int nx,
+                                                           int ny, const int32_t* __restrict__ map,
+                                                           int64_t ne, int D, int Q,
+                                                           const Rule rule, const Tables tab,
+                                                           double* __restrict__ b) {
+  __shared__ EltSmem sm;
+  const int Q2 = Q * Q, Q3 = Q2 * Q, D3 = D * D * D, QD = Q * D;
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int t = threadIdx.x; t < QD; t += blockDim.x) sm.tx[t] = sm.ty[t] = sm.tz[t] = tab.B[t];
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    for (int t = threadIdx.x; t < D3; t += blockDim.x) sm.acc[t] = 0.0;
+    for (int t = threadIdx.x; t < Q3; t += blockDim.x) {
+      const int qx = t % Q, qy = (t / Q) % Q, qz = t / Q2;
+      double X[3], J[3][3];
+      trilinear(V, nx, ny, e, rule.pts[qx], rule.pts[qy], rule.pts[qz], X, J);
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      const double f = 3.0 * pi * pi * sin(pi * X[0]) * sin(pi * X[1]) * sin(pi * X[2]);
+      sm.F[t] = rule.wts[qx] * rule.wts[qy] * rule.wts[qz] * det * f;
+    }
+    __syncthreads();
+    contract_transpose(sm.F, sm.tx, sm.ty, sm.tz, sm.T1, sm.T2, sm.acc, D, Q);
+    for (int t = threadIdx.x; t < D3; t += blockDim.x) atomicAdd(&b[map[e * D3 + t]], sm.acc[t]);
+    __syncthreads();
+  }
+}
+
+unsigned int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 64) g = 152 * 64;
+  if (g < 1) g = 1;
+  return (unsigned int)g;
+}
+
+unsigned int elem_grid(int64_t ne) {
+  int64_t g = ne < 152 * 256 ? ne : 152 * 256;
+  return (unsigned int)(g < 1 ? 1 : g);
+}
+
+Tables make_tables(const Basis1D& b) {
+  Tables t;
+  std::memset(&t, 0, sizeof(t));
+  for (int i = 0; i < b.Q * b.D; ++i) {
+    t.B[i] = b.B[i];
+    t.G[i] = b.G[i];
+  }
+  return t;
+}
+
+Rule make_rule(const Basis1D& b) {
+  Rule r;
+  std::memset(&r, 0, sizeof(r));
+  for (int i = 0; i < b.Q; ++i) {
+    r.pts[i] = b.pts[i];
+    r.wts[i] = b.wts[i];
+  }
+  return r;
+}
+
+// Fills the quadrature data of pa from the mesh geometry and coefficient (FP64 encoding).
+int compute_qdata(fe_pa* pa, const double* coeff, cudaStream_t s, int* d_bad) {
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ne * (int64_t)pa->Q * pa->Q * pa->Q;
+  k_qdata<<<grid_for(n, 256), 256, 0, s>>>(m->d_vertices, m->nx, m->ny, m->ne, pa->Q,
+                                           make_rule(pa->basis), coeff, pa->d_qd_diff,
+                                           pa->d_qd_mass, d_bad);
+  return cuda_error(cudaGetLastError(), "qdata kernel launch");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------- dispatch
+namespace fe {
+
+int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
+                   cudaStream_t s, const int* skip) {
+  if (!pa || !x || !y) return set_error(FE_ERR_ARG, "fe_apply: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_apply: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_apply: operator not set up in fe_pa_setup");
+  const fe_mesh* m = pa->mesh;
+  const bool pairs = (variant == FE_VARIANT_F32X2);
+  if (pairs != (pa->qd_format == FE_VARIANT_F32X2))
+    return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
+                                 "encoding; call fe_pa_set_variant first");
+  if (skip == nullptr) {
+    FE_CHECK_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->ndofs, s), "zero y");
+  }
+  ApplyArgs a;
+  a.map = m->d_map;
+  a.qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
+  a.x = x;
+  a.y = y;
+  a.ne = m->ne;
+  a.p = pa->p;
+  a.Q = pa->Q;
+  a.basis = &pa->basis;
+  a.skip = skip;
+  switch (variant) {
+    case FE_VARIANT_F64:
+      return launch_apply_f64(op, a, s);
+    case FE_VARIANT_F32X2:
+      return launch_apply_f32x2(op, a, s);
+    case FE_VARIANT_F64_DMMA:
+      return launch_apply_dmma(op, a, s);
+    default:
+      return set_error(FE_ERR_ARG, "fe_apply: unknown variant");
+  }
+}
+
+}  // namespace fe
+
+// ------------------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* fe_last_error(void) { return g_last_error.c_str(); }
+
+const char* fe_version(void) { return "libfe 0.1 (sm_103a)"; }
+
+int fe_mesh_setup(int nx, int ny, int nz, int order, const double* host_vertices, fe_mesh** out) {
+  clear_error();
+  if (!out) return set_error(FE_ERR_ARG, "fe_mesh_setup: out is NULL");
+  *out = nullptr;
+  if (!host_vertices) return set_error(FE_ERR_ARG, "fe_mesh_setup: vertices is NULL");
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(FE_ERR_ARG, "fe_mesh_setup: mesh size < 1");
+  if (order < 1 || order > kMaxOrder)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_mesh_setup: order must be 1..8");
+  fe_mesh* m = new fe_mesh();
+  m->nx = nx;
+  m->ny = ny;
+  m->nz = nz;
+  m->p = order;
+  m->D = order + 1;
+  m->ne = (int64_t)nx * ny * nz;
+  m->Nx = (int64_t)nx * order + 1;
+  m->Ny = (int64_t)ny * order + 1;
+  m->Nz = (int64_t)nz * order + 1;
+  m->ndofs = m->Nx * m->Ny * m->Nz;
+  const int64_t D3 = (int64_t)m->D * m->D * m->D;
+  if (m->ndofs > 2147483647LL || m->ne * D3 > ((int64_t)1 << 40)) {
+    delete m;
+    return set_error(FE_ERR_UNSUPPORTED, "fe_mesh_setup: more than 2^31-1 dofs");
+  }
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  cudaGetDevice(&m->device);
+  cudaError_t err;
+  if ((err = cudaMalloc(&m->d_vertices, sizeof(double) * 3 * nv)) != cudaSuccess ||
+      (err = cudaMalloc(&m->d_map, sizeof(int32_t) * m->ne * D3)) != cudaSuccess ||
+      (err = cudaMalloc(&m->d_mask, (size_t)m->ndofs)) != cudaSuccess) {
+    fe_mesh_destroy(m);
+    return cuda_error(err, "fe_mesh_setup: cudaMalloc");
+  }
+  err = cudaMemcpy(m->d_vertices, host_vertices, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) {
+    k_dof_map<<<grid_for(m->ne * D3, 256), 256>>>(m->d_map, nx, ny, order, m->Nx, m->Ny, m->ne);
+    k_boundary_mask<<<grid_for(m->ndofs, 256), 256>>>(m->d_mask, m->Nx, m->Ny, m->Nz);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  if (err != cudaSuccess) {
+    fe_mesh_destroy(m);
+    return cuda_error(err, "fe_mesh_setup");
+  }
+  *out = m;
+  return FE_OK;
+}
+
+int fe_mesh_sizes(const fe_mesh* m, int64_t* ndofs, int64_t* nelems, int* order) {
+  clear_error();
+  if (!m) return set_error(FE_ERR_ARG, "fe_mesh_sizes: mesh is NULL");
+  if (ndofs) *ndofs = m->ndofs;
+  if (nelems) *nelems = m->ne;
+  if (order) *order = m->p;
+  return FE_OK;
+}
+
+int fe_mesh_boundary_mask(const fe_mesh* m, uint8_t* dev_mask, void* stream) {
+  clear_error();
+  if (!m || !dev_mask) return set_error(FE_ERR_ARG, "fe_mesh_boundary_mask: null argument");
+  FE_CHECK_CUDA(cudaMemcpyAsync(dev_mask, m->d_mask, (size_t)m->ndofs, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream),
+                "fe_mesh_boundary_mask");
+  return FE_OK;
+}
+
+int fe_mesh_dof_map(const fe_mesh* m, int32_t* dev_map, void* stream) {
+  clear_error();
+  if (!m || !dev_map) return set_error(FE_ERR_ARG, "fe_mesh_dof_map: null argument");
+  const size_t n = (size_t)m->ne * m->D * m->D * m->D;
+  FE_CHECK_CUDA(cudaMemcpyAsync(dev_map, m->d_map, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream),
+                "fe_mesh_dof_map");
+  return FE_OK;
+}
+
+void fe_mesh_destroy(fe_mesh* m) {
+  if (!m) return;
+  cudaFree(m->d_vertices);
+  cudaFree(m->d_map);
+  cudaFree(m->d_mask);
+  delete m;
+}
+
+int fe_pa_setup(const fe_mesh* m, int q1d, const double* dev_coeff, int ops, void* stream,
+                fe_pa** out) {
+  clear_error();
+  if (!out) return set_error(FE_ERR_ARG, "fe_pa_setup: out is NULL");
+  *out = nullptr;
+  if (!m) return set_error(FE_ERR_ARG, "fe_pa_setup: mesh is NULL");
+  if (ops <= 0 || (ops & ~(FE_DIFFUSION | FE_MASS)))
+    return set_error(FE_ERR_ARG, "fe_pa_setup: ops must be FE_DIFFUSION and/or FE_MASS");
+  const int Q = q1d == 0 ? m->p + 2 : q1d;
+  if (Q != m->p + 2) return set_error(FE_ERR_UNSUPPORTED, "fe_pa_setup: only q1d = order + 2");
+  cudaStream_t s = (cudaStream_t)stream;
+  fe_pa* pa = new fe_pa();
+  pa->mesh = m;
+  pa->p = m->p;
+  pa->D = m->D;
+  pa->Q = Q;
+  pa->ops = ops;
+  if (!make_basis_1d(m->p, Q, &pa->basis)) {
+    delete pa;
+    return set_error(FE_ERR_UNSUPPORTED, "fe_pa_setup: bad order/rule");
+  }
+  const int64_t nq = m->ne * (int64_t)Q * Q * Q;
+  cudaError_t err = cudaSuccess;
+  if (ops & FE_DIFFUSION) err = cudaMalloc(&pa->d_qd_diff, sizeof(double) * 6 * nq);
+  if (err == cudaSuccess && (ops & FE_MASS)) err = cudaMalloc(&pa->d_qd_mass, sizeof(double) * nq);
+  int* d_bad = nullptr;
+  if (err == cudaSuccess) err = cudaMalloc(&d_bad, sizeof(int));
+  if (err != cudaSuccess) {
+    cudaFree(d_bad);
+    fe_pa_destroy(pa);
+    return cuda_error(err, "fe_pa_setup: cudaMalloc");
+  }
+  cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+  int st = compute_qdata(pa, dev_coeff, s, d_bad);
+  int bad = 0;
+  if (st == FE_OK) {
+    err = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) st = cuda_error(err, "fe_pa_setup");
+  }
+  cudaFree(d_bad);
+  if (st != FE_OK) {
+    fe_pa_destroy(pa);
+    return st;
+  }
+  if (bad) {
+    fe_pa_destroy(pa);
+    return set_error(FE_ERR_ARG, "fe_pa_setup: an element has det J <= 0 at a Gauss point");
+  }
+  // keep the coefficient so that the FP64 encoding can be recomputed after a variant switch
+  if (dev_coeff) {
+    double* c = nullptr;
+    err = cudaMalloc(&c, sizeof(double) * m->ne);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(c, dev_coeff, sizeof(double) * m->ne, cudaMemcpyDeviceToDevice, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) {
+      cudaFree(c);
+      fe_pa_destroy(pa);
+      return cuda_error(err, "fe_pa_setup: coefficient copy");
+    }
+    pa->d_coeff = c;
+  }
+  *out = pa;
+  return FE_OK;
+}
+
+int fe_pa_set_variant(fe_pa* pa, int variant, void* stream) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_pa_set_variant: pa is NULL");
+  if (variant != FE_VARIANT_F64 && variant != FE_VARIANT_F32X2 && variant != FE_VARIANT_F64_DMMA)
+    return set_error(FE_ERR_ARG, "fe_pa_set_variant: unknown variant");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool want_pairs = (variant == FE_VARIANT_F32X2);
+  const bool have_pairs = (pa->qd_format == FE_VARIANT_F32X2);
+  if (want_pairs && !have_pairs) {
+    const int64_t nq = pa->mesh->ne * (int64_t)pa->Q * pa->Q * pa->Q;
+    int st = encode_f32x2(pa->d_qd_diff, pa->d_qd_diff ? 6 * nq : 0, true, s);
+    if (st == FE_OK) st = encode_f32x2(pa->d_qd_mass, pa->d_qd_mass ? nq : 0, true, s);
+    if (st != FE_OK) return st;
+    pa->qd_format = FE_VARIANT_F32X2;
+  } else if (!want_pairs && have_pairs) {
+    // recompute the exact FP64 data rather than widen the pairs (which would lose bits)
+    int* d_bad = nullptr;
+    FE_CHECK_CUDA(cudaMalloc(&d_bad, sizeof(int)), "fe_pa_set_variant: cudaMalloc");
+    cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+    int st = compute_qdata(pa, pa->d_coeff, s, d_bad);
+    cudaError_t err = cudaStreamSynchronize(s);
+    cudaFree(d_bad);
+    if (st != FE_OK) return st;
+    if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant");
+    pa->qd_format = FE_VARIANT_F64;
+  }
+  pa->variant = variant;
+  return FE_OK;
+}
+
+int fe_pa_get_variant(const fe_pa* pa, int* variant) {
+  clear_error();
+  if (!pa || !variant) return set_error(FE_ERR_ARG, "fe_pa_get_variant: null argument");
+  *variant = pa->variant;
+  return FE_OK;
+}
+
+int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* dev_y,
+             void* stream) {
+  clear_error();
+  return apply_dispatch(pa, op, variant, dev_x, dev_y, (cudaStream_t)stream);
+}
+
+int fe_apply_diffusion(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_apply_diffusion: pa is NULL");
+  return apply_dispatch(pa, FE_DIFFUSION, pa->variant, dev_x, dev_y, (cudaStream_t)stream);
+}
+
+int fe_apply_mass(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_apply_mass: pa is NULL");
+  return apply_dispatch(pa, FE_MASS, pa->variant, dev_x, dev_y, (cudaStream_t)stream);
+}
+
+int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream) {
+  clear_error();
+  if (!pa || !dev_diag) return set_error(FE_ERR_ARG, "fe_assemble_diagonal: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_assemble_diagonal: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_assemble_diagonal: operator not set up");
+  cudaStream_t s = (cudaStream_t)stream;
+  const fe_mesh* m = pa->mesh;
+  FE_CHECK_CUDA(cudaMemsetAsync(dev_diag, 0, sizeof(double) * m->ndofs, s), "zero diag");
+  const double* qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
+  k_diagonal<<<elem_grid(m->ne), kEltThreads, 0, s>>>(m->d_map, qd, m->ne, pa->D, pa->Q,
+                                                      op == FE_DIFFUSION ? 1 : 0,
+                                                      pa->qd_format == FE_VARIANT_F32X2 ? 1 : 0,
+                                                      make_tables(pa->basis), dev_diag);
+  return cuda_error(cudaGetLastError(), "diagonal kernel launch");
+}
+
+int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream) {
+  clear_error();
+  if (!pa || !dev_b) return set_error(FE_ERR_ARG, "fe_load_vector_sine: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const fe_mesh* m = pa->mesh;
+  FE_CHECK_CUDA(cudaMemsetAsync(dev_b, 0, sizeof(double) * m->ndofs, s), "zero b");
+  k_load_sine<<<elem_grid(m->ne), kEltThreads, 0, s>>>(m->d_vertices, m->nx, m->ny, m->d_map,
+                                                       m->ne, pa->D, pa->Q, make_rule(pa->basis),
+                                                       make_tables(pa->basis), dev_b);
+  return cuda_error(cudaGetLastError(), "load vector kernel launch");
+}
+
+void fe_pa_destroy(fe_pa* pa) {
+  if (!pa) return;
+  cudaFree(pa->d_qd_diff);
+  cudaFree(pa->d_qd_mass);
+  cudaFree(pa->d_coeff);
+  cudaFree(pa->d_work);
+  cudaFree(pa->d_red);
+  cudaFree(pa->d_flags);
+  delete pa;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations of libfe (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/fe.h"
+
+namespace fe {
+
+constexpr int kMaxOrder = 8;
+constexpr int kMaxD = kMaxOrder + 1;
+constexpr int kMaxQ = kMaxOrder + 2;
+
+// Records msg as the calling thread's last error and returns status.
+int set_error(int status, const std::string& msg);
+int cuda_error(cudaError_t err, const char* what);
+void clear_error();
+
+// 1D tables for order p with a q-point Gauss rule on [0, 1] (host, FP64):
+// nodes[d] GLL nodes, pts[q]/wts[q] Gauss-Legendre rule, B[q*D+d] = l_d(x_q), G[q*D+d] = l_d'(x_q).
+struct Basis1D {
+  int p = 0, D = 0, Q = 0;
+  double nodes[kMaxD];
+  double pts[kMaxQ];
+  double wts[kMaxQ];
+  double B[kMaxQ * kMaxD];
+  double G[kMaxQ * kMaxD];
+};
+// Returns false if p or q is out of range.
+bool make_basis_1d(int p, int q, Basis1D* out);
+
+}  // namespace fe
+
+struct fe_mesh {
+  int nx = 0, ny = 0, nz = 0, p = 0, D = 0;
+  int64_t ne = 0, ndofs = 0;
+  int64_t Nx = 0, Ny = 0, Nz = 0;  // GLL lattice points per axis
+  int device = 0;
+  double* d_vertices = nullptr;    // [(nx+1)(ny+1)(nz+1)][3]
+  int32_t* d_map = nullptr;        // [ne][D^3]
+  uint8_t* d_mask = nullptr;       // [ndofs]
+};
+
+struct fe_pa {
+  const fe_mesh* mesh = nullptr;   // not owned; must outlive the fe_pa
+  int p = 0, D = 0, Q = 0, ops = 0;
+  int variant = FE_VARIANT_F64;
+  int qd_format = FE_VARIANT_F64;  // encoding of the stored quadrature data
+  fe::Basis1D basis;
+  double* d_qd_diff = nullptr;     // [ne][Q][6][Q][Q] (qz, component, qy, qx)
+  double* d_qd_mass = nullptr;     // [ne][Q][Q][Q]
+  double* d_coeff = nullptr;       // [ne] copy of the coefficient (nullptr => 1)
+  // PCG workspace (allocated on first fe_pcg, freed by fe_pa_destroy)
+  double* d_work = nullptr;        // 5 vectors of ndofs
+  double* d_red = nullptr;         // reduction partials + scalars
+  int* d_flags = nullptr;
+  int64_t work_ndofs = 0;
+};
+
+namespace fe {
+
+// Arguments of one apply launch.
+struct ApplyArgs {
+  const int32_t* map;
+  const double* qd;      // FP64 or float-pair encoded, per variant
+  const double* x;
+  double* y;
+  int64_t ne;
+  int p, Q;
+  const Basis1D* basis;
+  const int* skip;       // optional device flag; nonzero => the launch does nothing
+};
+
+// Launchers (one translation unit per variant); return FE_OK or an error status.
+int launch_apply_f64(int op, const ApplyArgs& a, cudaStream_t s);
+int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s);
+int launch_apply_dmma(int op, const ApplyArgs& a, cudaStream_t s);
+
+// Re-encodes n FP64 values in place as float pairs (hi, lo) or back.
+int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);
+
+// y = A x (y zeroed first).  skip: optional device flag, nonzero => no-op (also skips zeroing).
+int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
+                   cudaStream_t s, const int* skip = nullptr);
+
+}  // namespace fe

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libfe (C ABI in include/fe.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no arithmetic of its
+own.  Device buffers are passed as torch CUDA tensors (or raw integer device addresses);
+streams default to torch's current stream.  A non-OK status raises ``FEError`` carrying the
+library's message, except where a status is part of the result (``fe_pcg``).
+If ``libfe.so`` has not been built, ``load()`` raises: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfe.so")
+
+FE_OK = 0
+FE_ERR_ARG = -1
+FE_ERR_CUDA = -2
+FE_ERR_OOM = -3
+FE_ERR_UNSUPPORTED = -4
+FE_ERR_NOT_CONVERGED = -5
+FE_ERR_BREAKDOWN = -6
+FE_ERR_NAN = -7
+
+FE_DIFFUSION = 1
+FE_MASS = 2
+FE_PC_NONE = 0
+FE_PC_JACOBI = 1
+FE_VARIANT_F64 = 0
+FE_VARIANT_F32X2 = 1
+FE_VARIANT_F64_DMMA = 2
+
+VARIANTS = {"f64": FE_VARIANT_F64, "f32x2": FE_VARIANT_F32X2, "dmma": FE_VARIANT_F64_DMMA}
+
+
+class FEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libfe status %d: %s" % (status, msg))
+        self.status = status
+
+
+class fe_pcg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double),
+                ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("launches", ctypes.c_int)]
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "fe_mesh_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                     ctypes.POINTER(_VP)]),
+    "fe_mesh_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    "fe_mesh_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
+    "fe_mesh_dof_map": (ctypes.c_int, [_VP, _VP, _VP]),
+    "fe_pa_setup": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "fe_pa_set_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "fe_pa_get_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "fe_apply_diffusion": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_apply_mass": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_apply": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_assemble_diagonal": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "fe_load_vector_sine": (ctypes.c_int, [_VP, _VP, _VP]),
+    "fe_pcg": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
+                              ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_pa_destroy": (None, [_VP]),
+    "fe_mesh_destroy": (None, [_VP]),
+    "fe_last_error": (ctypes.c_char_p, []),
+    "fe_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path=LIB_PATH):
+    """Loads libfe.so (once) and declares the C signatures; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libfe.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != FE_OK:
+        raise FEError(status, _lib.fe_last_error().decode())
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return _VP(t)
+    return _VP(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _VP(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _VP(stream)
+    return _VP(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- entry points (same names)
+
+def fe_mesh_setup(nx, ny, nz, order, vertices):
+    """vertices: host float64 array [(nx+1)(ny+1)(nz+1), 3]; returns the mesh handle."""
+    lib = load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    out = _VP()
+    _check(lib.fe_mesh_setup(int(nx), int(ny), int(nz), int(order),
+                             v.ctypes.data_as(_VP), ctypes.byref(out)))
+    return out.value
+
+
+def fe_mesh_sizes(mesh):
+    lib = load()
+    nd, ne, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(lib.fe_mesh_sizes(_VP(mesh), ctypes.byref(nd), ctypes.byref(ne), ctypes.byref(p)))
+    return nd.value, ne.value, p.value
+
+
+def fe_mesh_boundary_mask(mesh, dev_mask, stream=None):
+    _check(load().fe_mesh_boundary_mask(_VP(mesh), _ptr(dev_mask), _stream(stream)))
+
+
+def fe_mesh_dof_map(mesh, dev_map, stream=None):
+    _check(load().fe_mesh_dof_map(_VP(mesh), _ptr(dev_map), _stream(stream)))
+
+
+def fe_pa_setup(mesh, q1d=0, dev_coeff=None, ops=FE_DIFFUSION | FE_MASS, stream=None):
+    lib = load()
+    out = _VP()
+    _check(lib.fe_pa_setup(_VP(mesh), int(q1d), _ptr(dev_coeff), int(ops), _stream(stream),
+                           ctypes.byref(out)))
+    return out.value
+
+
+def fe_pa_set_variant(pa, variant, stream=None):
+    v = VARIANTS.get(variant, variant)
+    _check(load().fe_pa_set_variant(_VP(pa), int(v), _stream(stream)))
+
+
+def fe_pa_get_variant(pa):
+    v = ctypes.c_int()
+    _check(load().fe_pa_get_variant(_VP(pa), ctypes.byref(v)))
+    return v.value
+
+
+def fe_apply_diffusion(pa, dev_x, dev_y, stream=None):
+    _check(load().fe_apply_diffusion(_VP(pa), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_apply_mass(pa, dev_x, dev_y, stream=None):
+    _check(load().fe_apply_mass(_VP(pa), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_apply(pa, op, variant, dev_x, dev_y, stream=None):
+    v = VARIANTS.get(variant, variant)
+    _check(load().fe_apply(_VP(pa), int(op), int(v), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_assemble_diagonal(pa, op, dev_diag, stream=None):
+    _check(load().fe_assemble_diagonal(_VP(pa), int(op), _ptr(dev_diag), _stream(stream)))
+
+
+def fe_load_vector_sine(pa, dev_b, stream=None):
+    _check(load().fe_load_vector_sine(_VP(pa), _ptr(dev_b), _stream(stream)))
+
+
+def fe_pcg(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
+    """Returns (status, stats dict); the status is not raised (non-convergence is a result)."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_pcg(_VP(pa), int(op), int(pc), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                        int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, {"iters": st.iters, "rel_resid": st.rel_resid,
+                    "true_rel_resid": st.true_rel_resid, "seconds": st.seconds,
+                    "launches": st.launches}
+
+
+def fe_pa_destroy(pa):
+    if pa:
+        load().fe_pa_destroy(_VP(pa))
+
+
+def fe_mesh_destroy(mesh):
+    if mesh:
+        load().fe_mesh_destroy(_VP(mesh))
+
+
+def fe_last_error():
+    return load().fe_last_error().decode()
+
+
+def fe_version():
+    return load().fe_version().decode()

@@ -1,0 +1,185 @@
+"""GPU parity of the fused PA apply (through the C ABI) against the CPU oracle.
+
+Small meshes: every output element compared with the oracle's element-matrix apply, for every
+order 1..8, both operators and every arithmetic variant, on meshes whose element count spans
+several thread blocks and leaves a ragged last block.  Full-size meshes (the ~50 M dof order
+sweep and the 64^3 p=3 Poisson mesh, in the launch configuration the benchmark times): sampled
+outputs, each computed one by one by the oracle, plus invariants that hold at any size.
+Bound: relative max-norm error <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_problem, rel_err, torch_cuda, TOL
+from oracle import operator as oop
+from oracle.element import DIFFUSION, MASS
+from paper_2603_09038_gb300.inputs import uniform_vector, ORDER_SWEEP_N
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["f64", "f32x2"]
+OPS = [(1, DIFFUSION), (2, MASS)]      # (FE_DIFFUSION / FE_MASS code, oracle kind)
+
+
+def _apply(fe, pa, op, variant, xh):
+    torch = torch_cuda()
+    x = torch.from_numpy(xh).cuda()
+    y = torch.full_like(x, float("nan"))
+    fe.fe_apply(pa, op, variant, x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_config1_parity_ten_applies(variant):
+    """4^3 hexes, p=2, Q=4, +-0.1h perturbation, c=1, x ~ U[-1,1] with seeds 0..9."""
+    n, p = 4, 2
+    with gpu_problem(n, n, n, p) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        prob = oop.Problem(n, n, n, p, V)
+        for op, kind in OPS:
+            for seed in range(10):
+                xh = uniform_vector(prob.ndofs, seed)
+                assert rel_err(_apply(fe, pa, op, variant, xh), oop.apply(prob, xh, kind)) <= TOL
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("p", range(1, 9))
+def test_all_orders_ragged_blocks(variant, p):
+    dims = (5, 4, 7) if p <= 3 else (3, 2, 5)
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        xh = uniform_vector(prob.ndofs, seed=p)
+        for op, kind in OPS:
+            assert rel_err(_apply(fe, pa, op, variant, xh), oop.apply(prob, xh, kind)) <= TOL
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_element_and_switching_back(variant):
+    with gpu_problem(1, 1, 1, 4, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(1, 1, 1, 4, V, coeff=c)
+        xh = uniform_vector(prob.ndofs, seed=3)
+        fe.fe_pa_set_variant(pa, variant)
+        for op, kind in OPS:
+            assert rel_err(_apply(fe, pa, op, variant, xh), oop.apply(prob, xh, kind)) <= TOL
+        fe.fe_pa_set_variant(pa, "f64")      # back to exact FP64 data
+        for op, kind in OPS:
+            assert rel_err(_apply(fe, pa, op, "f64", xh), oop.apply(prob, xh, kind)) <= 1e-14
+
+
+def _sampled_rows(ndofs, rng, k=64):
+    rows = rng.choice(ndofs, size=k, replace=False)
+    return np.unique(np.concatenate([rows, [0, ndofs - 1, ndofs // 2]]))
+
+
+def _full_size_check(n, p, variants, sigma=1.0):
+    torch = torch_cuda()
+    with gpu_problem(n, n, n, p, sigma=sigma) as (fe, mesh, pa, V, c):
+        ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
+        prob = oop.Problem(n, n, n, p, V, coeff=c)
+        rng = np.random.default_rng(p)
+        rows = _sampled_rows(ndofs, rng)
+        xh = uniform_vector(ndofs, seed=p)
+        x = torch.from_numpy(xh).cuda()
+        y = torch.empty_like(x)
+        ones = torch.ones_like(x)
+        for variant in variants:
+            fe.fe_pa_set_variant(pa, variant)
+            for op, kind in OPS:
+                fe.fe_apply(pa, op, variant, x, y)
+                torch.cuda.synchronize()
+                ys = y[torch.from_numpy(rows).cuda()].cpu().numpy()
+                scale = float(y.abs().max())
+                ref = oop.apply_rows(prob, xh, kind, rows)
+                assert np.abs(ys - ref).max() <= TOL * scale, (variant, kind)
+                # invariants at full size: A 1 = 0; 1^T M 1 = sum_e c_e vol_e (unit cube if c=1)
+                fe.fe_apply(pa, op, variant, ones, y)
+                torch.cuda.synchronize()
+                if kind == DIFFUSION:
+                    assert float(y.abs().max()) <= TOL * scale
+                else:
+                    total = float(y.sum())
+                    if c is None:
+                        assert abs(total - 1.0) <= 1e-11
+                    else:
+                        assert c.min() <= total <= c.max()
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_order_sweep_full_size_sampled(p):
+    """The ~50 M dof order-sweep meshes with a log-normal (sigma = 1) coefficient."""
+    _full_size_check(ORDER_SWEEP_N[p], p, VARIANTS)
+
+
+def test_poisson_mesh_full_size_sampled():
+    """64^3 hexes, p = 3 (7.19 M dofs), c = 1: the benchmark's workload."""
+    _full_size_check(64, 3, VARIANTS, sigma=None)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
+def test_diagonal_matches_oracle(p):
+    torch = torch_cuda()
+    dims = (3, 2, 4)
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        d = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        for op, kind in OPS:
+            fe.fe_assemble_diagonal(pa, op, d)
+            torch.cuda.synchronize()
+            assert rel_err(d.cpu().numpy(), oop.diagonal(prob, kind)) <= TOL
+
+
+@pytest.mark.parametrize("p", [1, 3, 6])
+def test_load_vector_matches_oracle(p):
+    from oracle.solve import load_vector
+    torch = torch_cuda()
+    dims = (3, 4, 2)
+    with gpu_problem(*dims, p) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        torch.cuda.synchronize()
+        assert rel_err(b.cpu().numpy(), load_vector(prob)) <= TOL
+
+
+def test_dof_map_and_mask_match_oracle():
+    from oracle.mesh import dof_map, boundary_mask
+    torch = torch_cuda()
+    dims, p = (3, 4, 2), 3
+    with gpu_problem(*dims, p) as (fe, mesh, pa, V, c):
+        ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
+        m = torch.empty((ne, (p + 1) ** 3), dtype=torch.int32, device="cuda")
+        fe.fe_mesh_dof_map(mesh, m)
+        mask = torch.empty(ndofs, dtype=torch.uint8, device="cuda")
+        fe.fe_mesh_boundary_mask(mesh, mask)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(m.cpu().numpy(), dof_map(*dims, p))
+        np.testing.assert_array_equal(mask.cpu().numpy(), boundary_mask(*dims, p))
+
+
+def test_errors_are_status_codes():
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    torch = torch_cuda()
+    fe = __import__("gpu_util").lib()
+    V = perturbed_vertices(1, 1, 1, amp=0.0)
+    V[[0, 1]] = V[[1, 0]]                       # inverted element
+    mesh = fe.fe_mesh_setup(1, 1, 1, 2, V)
+    try:
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+        assert ei.value.status == fe.FE_ERR_ARG and "det J" in str(ei.value)
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_pa_setup(mesh, 3, None, fe.FE_DIFFUSION)
+        assert ei.value.status == fe.FE_ERR_UNSUPPORTED
+    finally:
+        fe.fe_mesh_destroy(mesh)
+    with gpu_problem(2, 2, 2, 2, ops=1) as (fe, mesh, pa, V, c):
+        x = torch.zeros(5 ** 3, dtype=torch.float64, device="cuda")
+        y = torch.zeros_like(x)
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_apply(pa, fe.FE_MASS, "f64", x, y)       # mass was not set up
+        assert ei.value.status == fe.FE_ERR_ARG
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_apply(pa, fe.FE_DIFFUSION, "f32x2", x, y)  # data still FP64-encoded
+        assert ei.value.status == fe.FE_ERR_ARG

@@ -1,0 +1,88 @@
+"""GPU Jacobi-PCG (fe_pcg through the C ABI) against the oracle's CG, the manufactured
+O(h^{p+1}) convergence on the 64^3 p = 3 Poisson problem, and the failure paths (made on the
+host: NaN in b, an indefinite operator, maxit)."""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_problem, torch_cuda
+from oracle import operator as oop
+from oracle.element import DIFFUSION
+from oracle.mesh import boundary_mask
+from oracle.solve import pcg as oracle_pcg, load_vector, l2_error
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_solve(prob, b, rtol):
+    m = boundary_mask(prob.nx, prob.ny, prob.nz, prob.p).astype(np.float64)
+    keep = 1.0 - m
+    A = oop.assemble(prob, DIFFUSION)
+    d = oop.diagonal(prob, DIFFUSION) * keep + m
+    return oracle_pcg(lambda v: keep * (A @ (keep * v)) + m * v, b * keep, d, rtol=rtol)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32x2"])
+@pytest.mark.parametrize("dims,p", [((4, 4, 4), 2), ((6, 5, 4), 3), ((3, 3, 3), 6)])
+def test_pcg_matches_oracle_cg(variant, dims, p):
+    torch = torch_cuda()
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        rtol = 1e-10
+        fe.fe_pa_set_variant(pa, variant)
+        st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, rtol, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert stats["rel_resid"] <= rtol and stats["true_rel_resid"] <= 10 * rtol
+        xr, it, hist = _oracle_solve(prob, load_vector(prob), rtol)
+        assert abs(stats["iters"] - it) <= 1, (stats["iters"], it)
+        xg = x.cpu().numpy()
+        assert np.abs(xg - xr).max() <= 1e-8 * np.abs(xr).max()
+        assert np.all(xg[boundary_mask(*dims, p) == 1] == 0.0)
+
+
+def test_pcg_failure_paths():
+    torch = torch_cuda()
+    with gpu_problem(3, 3, 3, 2) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, 1e-12, 1)
+        assert st == fe.FE_ERR_NOT_CONVERGED and stats["iters"] == 1
+        b2 = b.clone()
+        b2[n // 2] = float("nan")                 # an interior dof
+        st, _ = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b2, x, 1e-10, 100)
+        assert st == fe.FE_ERR_NAN
+        zero = torch.zeros_like(b)
+        st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, zero, x, 1e-10, 100)
+        assert st == fe.FE_OK and stats["iters"] == 0 and float(x.abs().max()) == 0.0
+    neg = -np.ones(27)                             # negative coefficient: -K is not SPD
+    with gpu_problem(3, 3, 3, 2, coeff=neg) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        st, _ = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_NONE, b, x, 1e-10, 100)
+        assert st == fe.FE_ERR_BREAKDOWN
+        st, _ = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, 1e-10, 100)
+        assert st == fe.FE_ERR_BREAKDOWN
+
+
+def test_poisson_64_cubed_p3_convergence():
+    """64^3 hexes p=3 (7.19 M dofs): Jacobi-PCG to 1e-10; the L2 error against the exact sine
+    falls like h^{p+1} from 16^3 to 32^3 to 64^3 (rate 4 +- 0.2)."""
+    torch = torch_cuda()
+    errs = []
+    for n in (16, 32, 64):
+        with gpu_problem(n, n, n, 3) as (fe, mesh, pa, V, c):
+            nd, _, _ = fe.fe_mesh_sizes(mesh)
+            b = torch.empty(nd, dtype=torch.float64, device="cuda")
+            fe.fe_load_vector_sine(pa, b)
+            x = torch.empty_like(b)
+            st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, 1e-10, 20000)
+            assert st == fe.FE_OK and stats["true_rel_resid"] <= 1e-9
+            errs.append(l2_error(oop.Problem(n, n, n, 3, V), x.cpu().numpy()))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 4.0) < 0.2), (errs, rates)
