@@ -59,6 +59,22 @@ def algorithmic(ndofs, ne, p, q, diffusion=True):
     return nbytes, ne * f
 
 
+def max_over_ranks(t, dist=None, device="cpu"):
+    """Slowest rank's time: every rank gets max_r t_r (identity on one process)."""
+    if dist is None:
+        return float(t)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_gdofs(world, ndofs, applies, seconds):
+    """Whole-job throughput: every rank solves its own problem (weak scaling), so the units are
+    world * ndofs * applies, over the slowest rank's time."""
+    return world * ndofs * applies / seconds / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region (200 ms period)."""
 
@@ -227,12 +243,8 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    t = e0.elapsed_time(e1) / 1000.0
-    if dist is not None:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * ndofs * applies / t / 1e9
+    t = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev)
+    value = job_gdofs(world, ndofs, applies, t)
 
     # ---- end to end through host buffers: pinned b -> device, solve, x -> pinned host
     b_host = b.cpu().pin_memory()
@@ -249,11 +261,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_applies += s["iters"] + 1
     te = time.perf_counter() - t0
     barrier()
-    if dist is not None:
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": world * ndofs * e2e_applies / te / 1e9, "unit": UNIT,
+    te = max_over_ranks(te, dist, dev)
+    e2e = {"value": job_gdofs(world, ndofs, e2e_applies, te), "unit": UNIT,
            "h2d_bytes_per_step": 8 * ndofs, "d2h_bytes_per_step": 8 * ndofs,
            "ms_per_step": 1000.0 * te / args.steps}
 
@@ -332,6 +341,58 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_sweep(args, local_rank):
+    """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1): device time of one
+    apply (median of 10 after 3 warm-ups, CUDA events) per operator and variant, one JSON line
+    each.  Not the contract line: the per-order roofline table."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices, lognormal_coefficient, ORDER_SWEEP_N
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    fe.load()
+    peaks, _ = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak = 152 * FP64_DFMA_PER_CLK_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    stream = torch.cuda.current_stream()
+    orders = [int(v) for v in args.orders.split(",")]
+    for p in orders:
+        n = ORDER_SWEEP_N[p]
+        V = perturbed_vertices(n, n, n)
+        c = torch.from_numpy(lognormal_coefficient(n ** 3, 1.0)).to(dev)
+        mesh = fe.fe_mesh_setup(n, n, n, p, V)
+        pa = fe.fe_pa_setup(mesh, 0, c, fe.FE_DIFFUSION | fe.FE_MASS)
+        ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
+        x = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
+        y = torch.empty_like(x)
+        for variant in args.variants.split(","):
+            fe.fe_pa_set_variant(pa, variant)
+            for op, name in ((fe.FE_DIFFUSION, "diffusion"), (fe.FE_MASS, "mass")):
+                for _ in range(3):
+                    fe.fe_apply(pa, op, variant, x, y, stream)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(10)]
+                torch.cuda.synchronize()
+                for a, z in ev:
+                    a.record(stream)
+                    fe.fe_apply(pa, op, variant, x, y, stream)
+                    z.record(stream)
+                torch.cuda.synchronize()
+                ms = statistics.median(a.elapsed_time(z) for a, z in ev)
+                nbytes, flops = algorithmic(ndofs, ne, p, p + 2, op == fe.FE_DIFFUSION)
+                print(json.dumps({
+                    "sweep": True, "p": p, "n": n, "ndofs": ndofs, "op": name, "variant": variant,
+                    "ms": round(ms, 4), "gdofs": ndofs / ms / 1e6,
+                    "hbm_gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm_peak,
+                    "fp64_tflops_equiv": flops / ms / 1e9, "fp64_frac": flops / ms * 1e3 / fp64_peak}))
+                sys.stdout.flush()
+        fe.fe_pa_destroy(pa)
+        fe.fe_mesh_destroy(mesh)
+        del x, y, c
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,6 +405,9 @@ def main():
     ap.add_argument("--rtol", type=float, default=RTOL)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")
+    ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--variants", default="f64,f32x2")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -352,6 +416,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist
