@@ -130,6 +130,26 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
 
+/* fe_pcg without any device allocation (the paper has no counterpart: this is a service for
+ * callers that cannot allocate).  Some applications give all device memory to their own pool
+ * allocator up front, and some latency-critical loops cannot afford the blocking and device
+ * synchronisation that cudaMalloc/cudaFree can cause; neither can call a routine that allocates.
+ * This entry point solves the same system as fe_pcg, with the same kernels, arguments, stats and
+ * status codes, but takes every work vector, reduction partial and flag from one fixed device
+ * array compiled into the library: at most 262,144 dofs (FE_PCG_NOALLOC_MAX_DOFS), about 10.5 MB
+ * of device memory that every GPU which loads the library keeps until the process exits.  Larger
+ * meshes are rejected with FE_ERR_ARG and a message.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine (the fe_pa must already exist: fe_pa_setup does allocate).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current and caches it; make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents (the call clears what
+ *    must start at zero).  Calls whose GPU work overlaps -- on two streams, or from two host
+ *    threads -- race on it and give wrong results: serialise them.
+ * Synchronous, like fe_pcg. */
+#define FE_PCG_NOALLOC_MAX_DOFS 262144
+int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x,
+                   double rtol, int maxit, fe_pcg_stats* stats, void* stream);
+
 void fe_pa_destroy(fe_pa* pa);
 void fe_mesh_destroy(fe_mesh* mesh);
 

@@ -16,6 +16,8 @@
 
 #include <chrono>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "fe_internal.h"
 
@@ -349,5 +351,164 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
       return set_error(FE_ERR_NAN, "fe_pcg: NaN or Inf in the iteration");
     default:
       return set_error(FE_ERR_NOT_CONVERGED, "fe_pcg: maxit reached before rtol");
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// fe_pcg_noalloc: the same Jacobi-PCG for callers that must not allocate device memory.
+//
+// Some callers cannot let a library call cudaMalloc: applications that hand (nearly) all of
+// the GPU's memory to their own pool allocator up front, so that a driver allocation would fail
+// or fragment the pool, and latency-critical loops that cannot afford the blocking and device
+// synchronisation that cudaMalloc and cudaFree can cause.  This entry point therefore takes its
+// work vectors, reduction partials and flags from one fixed device array that is part of the
+// library image (kNoAllocMaxDofs dofs; about 10.5 MB, held on every GPU that loads the
+// library until the process exits) instead of allocating them.
+namespace {
+
+constexpr int64_t kNoAllocMaxDofs = (int64_t)1 << 18;  // 262,144 dofs, e.g. 64^3 GLL points
+constexpr int64_t kNoAllocDoubles =
+    5 * kNoAllocMaxDofs + 2 * kReduceBlocks + kScalars + 2;  // + 4 ints of flags
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {nullptr};
+
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return cuda_error(err, "fe_pcg_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(FE_ERR_UNSUPPORTED, "fe_pcg_noalloc: device index >= 64");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess) return cuda_error(err, "fe_pcg_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return FE_OK;
+}
+
+}  // namespace
+
+extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b,
+                              double* dev_x, double rtol, int maxit, fe_pcg_stats* stats,
+                              void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0};
+  int launches = 0;
+  if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: operator not set up");
+  if (pc != FE_PC_NONE && pc != FE_PC_JACOBI)
+    return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad preconditioner");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad rtol or maxit");
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  if (n > kNoAllocMaxDofs)
+    return set_error(FE_ERR_ARG, "fe_pcg_noalloc: the mesh has " + std::to_string(n) +
+                                     " dofs, more than the fixed scratch holds (" +
+                                     std::to_string(kNoAllocMaxDofs) + "); use fe_pcg");
+  double* base = nullptr;
+  int st = noalloc_scratch(&base);
+  if (st != FE_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* r = base;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* d = q + n;
+  double* part0 = base + 5 * kNoAllocMaxDofs;
+  double* part1 = part0 + kReduceBlocks;
+  double* sc = part1 + kReduceBlocks;
+  int* flags = reinterpret_cast<int*>(sc + kScalars);
+  const uint8_t* mask = m->d_mask;
+  cudaError_t err;
+
+#define NOALLOC_LAUNCH_CHECK(what)                              \
+  do {                                                          \
+    cudaError_t e_ = cudaGetLastError();                        \
+    if (e_ != cudaSuccess) return cuda_error(e_, what);         \
+  } while (0)
+
+  // the array keeps the previous call's contents: the flags must start at zero; every vector
+  // and partial is written before it is read (d by the diagonal assembly, q by k_zero)
+  if ((err = cudaMemsetAsync(flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_noalloc: flags");
+  const double* dj = nullptr;
+  if (pc == FE_PC_JACOBI) {
+    st = fe_assemble_diagonal(pa, op, d, stream);
+    if (st != FE_OK) return st;
+    k_fix_diag<<<kReduceBlocks, kReduceThreads, 0, s>>>(d, mask, n, flags);
+    NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: diag fix launch");
+    launches += 2;
+    dj = d;
+  }
+  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, mask, dj, dev_x, r, z, p, n, part0, part1);
+  k_finish_init<<<1, 1, 0, s>>>(part0, part1, sc, flags);
+  NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: init launch");
+  launches += 2;
+  int hflags[4] = {0, 0, 0, 0};
+  if (pc == FE_PC_JACOBI) {
+    if ((err = cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg_noalloc: init");
+    if (hflags[2]) return set_error(FE_ERR_BREAKDOWN, "fe_pcg_noalloc: non-positive diagonal entry");
+  }
+  int queued = 0;
+  for (;;) {
+    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
+      k_zero<<<kReduceBlocks, kReduceThreads, 0, s>>>(q, n, flags);
+      st = apply_dispatch(pa, op, pa->variant, p, q, s, flags);
+      if (st != FE_OK) return st;
+      k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, q, n, part0, flags);
+      k_finish_pq<<<1, 1, 0, s>>>(part0, sc, flags);
+      k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, r, z, p, q, dj, mask, n, sc, part0,
+                                                          part1, flags);
+      k_finish_update<<<1, 1, 0, s>>>(part0, part1, sc, flags, rtol, maxit);
+      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, z, n, sc, flags);
+      NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: iteration launch");
+      launches += 7;
+    }
+    if ((err = cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg_noalloc: iteration");
+    if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
+  }
+  st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
+  if (st != FE_OK) return st;
+  k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, mask, n, part0);
+  k_finish_resid<<<1, 1, 0, s>>>(part0, sc);
+  NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: residual launch");
+  launches += 3;
+  double hsc[kScalars];
+  if ((err = cudaMemcpyAsync(hsc, sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_noalloc: stats");
+#undef NOALLOC_LAUNCH_CHECK
+  if (stats) {
+    stats->iters = hflags[F_ITERS];
+    stats->rel_resid = hsc[S_REL];
+    stats->true_rel_resid = hsc[S_BB] > 0.0 ? hsc[S_TRUE] : 0.0;
+    stats->seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = launches;
+  }
+  switch (hflags[F_STATE]) {
+    case ST_CONV:
+      return FE_OK;
+    case ST_BREAK:
+      return set_error(FE_ERR_BREAKDOWN, "fe_pcg_noalloc: p.Ap <= 0 (operator not SPD on the free dofs)");
+    case ST_NAN:
+      return set_error(FE_ERR_NAN, "fe_pcg_noalloc: NaN or Inf in the iteration");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, "fe_pcg_noalloc: maxit reached before rtol");
   }
 }

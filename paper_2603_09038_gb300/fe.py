@@ -66,6 +66,8 @@ _SIGS = {
     "fe_load_vector_sine": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pcg": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                               ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_pcg_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -184,6 +186,23 @@ def fe_pcg(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
     st = fe_pcg_stats()
     status = lib.fe_pcg(_VP(pa), int(op), int(pc), _ptr(dev_b), _ptr(dev_x), float(rtol),
                         int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, {"iters": st.iters, "rel_resid": st.rel_resid,
+                    "true_rel_resid": st.true_rel_resid, "seconds": st.seconds,
+                    "launches": st.launches}
+
+
+FE_PCG_NOALLOC_MAX_DOFS = 262144
+
+
+def fe_pcg_noalloc(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
+    """fe_pcg that allocates no device memory (fixed in-library scratch, at most
+    FE_PCG_NOALLOC_MAX_DOFS dofs); same return value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_pcg_noalloc(_VP(pa), int(op), int(pc), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                                int(maxit), ctypes.byref(st), _stream(stream))
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, {"iters": st.iters, "rel_resid": st.rel_resid,
