@@ -266,6 +266,33 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": 8 * ndofs, "d2h_bytes_per_step": 8 * ndofs,
            "ms_per_step": 1000.0 * te / args.steps}
 
+    # ---- mixed-precision iterative refinement to the same FP64-accurate 1e-8 residual: FP32
+    #      inner Jacobi-PCG, outer residual with the FP64-accurate operator of this variant
+    def solve_ir():
+        st, stats = fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT,
+                                 args.inner_rtol, stream)
+        if st != fe.FE_OK:
+            raise RuntimeError("fe_pcg_ir failed: %d %s" % (st, fe.fe_last_error()))
+        return stats
+    for _ in range(2):
+        solve_ir()
+    ir_stats = []
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ir_stats.append(solve_ir())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ir = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev) / args.steps
+    pcg_ir = {"time_to_1e-8_s": t_ir, "speedup_vs_pcg": (t / args.steps) / t_ir,
+              "inner_iters": ir_stats[-1]["iters"], "outer_iters": ir_stats[-1]["outer_iters"],
+              "inner_rtol": args.inner_rtol or 1e-2,
+              "true_rel_resid": ir_stats[-1]["true_rel_resid"],
+              "outer_operator": "f32x2" if args.variant == "f32x2" else "f64",
+              "inner_operator": "f32"}
+    launches_ir = sum(s_["launches"] for s_ in ir_stats)
+
     # ---- the dominant kernel alone: fused diffusion apply, CUDA events on its stream
     def time_apply(variant, reps):
         fe.fe_pa_set_variant(pa, variant)
@@ -290,27 +317,36 @@ def run_ours(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp64_peak = 152 * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12      # TFLOP/s
     kernels = {}
-    for variant in ("f64", "f32x2"):
+    nbytes32 = 16 * ndofs + ne * (4 * (p + 1) ** 3 + 4 * 6 * q ** 3)   # FP32 quadrature data
+    for variant in ("f64", "f32x2", "dmma", "f32"):
         ms = time_apply(variant, 20)
+        nb = nbytes32 if variant == "f32" else nbytes
         kernels[variant] = {
             "ms": ms, "gdofs": ndofs / (ms * 1e-3) / 1e9,
-            "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+            "hbm_gbs": nb / (ms * 1e-3) / 1e9, "hbm_frac": nb / (ms * 1e-3) / 1e9 / hbm_peak,
             "fp64_tflops_equiv": flops / (ms * 1e-3) / 1e12,
         }
     fe.fe_pa_set_variant(pa, args.variant)
     k = kernels[args.variant]
-    if args.variant == "f64":
+    hbm_obj = {"achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["hbm_frac"],
+               "peak_source": peak_src}
+    if args.variant in ("f64", "dmma"):
         roof = {"bound": "alu", "achieved": k["fp64_tflops_equiv"], "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": k["fp64_tflops_equiv"] / fp64_peak,
-                "traffic": None, "kernel": "k_pa_apply<D=4,Q=5,diffusion,f64>",
+                "traffic": None, "kernel": "k_pa_apply<D=4,Q=5,diffusion,%s>" % args.variant,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (DFMA rate "
-                               "measured on GB300)" % sm_max,
-                "hbm": {"achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                        "frac": k["hbm_frac"], "peak_source": peak_src}}
+                               "measured on GB300)" % sm_max, "hbm": hbm_obj}
     else:
-        roof = {"bound": "hbm", "achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": k["hbm_frac"], "traffic": None,
-                "kernel": "k_pa_apply<D=4,Q=5,diffusion,f32x2>", "peak_source": peak_src}
+        # float-float: FP32 issue rate (152 SMs x 128 lanes x clock) / 6 instructions per
+        # anchored FP64-equivalent multiply-add x 2 flops
+        ff_peak = 152 * 128 * sm_max * 1e6 / 6 * 2 / 1e12
+        roof = {"bound": "alu", "achieved": k["fp64_tflops_equiv"], "peak": ff_peak,
+                "unit": "TFLOP/s", "frac": k["fp64_tflops_equiv"] / ff_peak, "traffic": None,
+                "kernel": "k_pa_apply<D=4,Q=5,diffusion,%s>" % args.variant,
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz / 6 instructions per "
+                               "anchored float-float multiply-add x 2 flop (FP64-equivalent)"
+                               % sm_max, "hbm": hbm_obj}
+    roof["fp64_fma_probe_tflops"] = fe.fe_probe_throughput("fp64_fma")
     roof["bytes_per_launch"] = nbytes
     roof["flops_per_launch"] = flops
     roof["launch_ms"] = k["ms"]
@@ -327,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2_flush": "inputs larger than L2 (1.57 GB quadrature data per apply)",
                       "parallelism": "independent problem per GPU"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
-           "pcg_time_to_1e-8_s": t / args.steps,
+           "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir,
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result
@@ -393,21 +429,40 @@ def run_sweep(args, local_rank):
     return 0
 
 
+def run_peaks(local_rank):
+    """Throughput probes (libfe fe_probe_throughput) behind the FP64 roofline: one JSON line."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    out = {"peaks": True}
+    for unit in ("fp64_fma", "fp64_dmma", "fp32_fma", "f32x2_mac"):
+        out[unit + "_tflops"] = fe.fe_probe_throughput(unit)
+    props = torch.cuda.get_device_properties(local_rank)
+    out["sms"] = props.multi_processor_count
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", choices=["f64", "f32x2"], default="f64")
+    ap.add_argument("--variant", choices=["f64", "f32x2", "dmma"], default="f32x2",
+                    help="arithmetic of the FP64-accurate apply (f32x2: float-float on the FP32 "
+                         "pipe, <= 1e-12 relative like f64)")
     ap.add_argument("--n", type=int, default=N_ELEM)
     ap.add_argument("--p", type=int, default=ORDER)
     ap.add_argument("--rtol", type=float, default=RTOL)
+    ap.add_argument("--inner-rtol", type=float, default=0.0, help="fe_pcg_ir inner tolerance")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
-    ap.add_argument("--variants", default="f64,f32x2")
+    ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32 throughput probes")
+    ap.add_argument("--variants", default="f64,f32x2,dmma")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -418,6 +473,8 @@ def main():
         return run_reference(args, rank, world)
     if args.sweep:
         return run_sweep(args, local_rank)
+    if args.peaks:
+        return run_peaks(local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

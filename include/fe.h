@@ -61,8 +61,16 @@ typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1 } fe_pc;
  *                     product with FMA, Knuth's TwoSum).  Inputs must lie within the float
  *                     exponent range (|v| < 3e38; values below ~1e-22 lose relative accuracy).
  *  FE_VARIANT_F64_DMMA FP64 with the 1D contractions on the FP64 tensor-core instruction
- *                     mma.sync.m8n8k4.f64 (the paper's DMMA, Section III-B).               */
-typedef enum { FE_VARIANT_F64 = 0, FE_VARIANT_F32X2 = 1, FE_VARIANT_F64_DMMA = 2 } fe_variant;
+ *                     mma.sync.m8n8k4.f64 (the paper's DMMA, Section III-B).
+ *  FE_VARIANT_F32     plain FP32 arithmetic on an FP32 copy of the quadrature data (made on
+ *                     first use): NOT FP64-accurate (relative error ~1e-6); it is the inner
+ *                     operator of fe_pcg_ir's mixed-precision iterative refinement.          */
+typedef enum {
+  FE_VARIANT_F64 = 0,
+  FE_VARIANT_F32X2 = 1,
+  FE_VARIANT_F64_DMMA = 2,
+  FE_VARIANT_F32 = 3
+} fe_variant;
 
 typedef struct {
   int iters;             /* iterations performed                                              */
@@ -70,6 +78,7 @@ typedef struct {
   double true_rel_resid; /* ||b - A x||_2 / ||b||_2 recomputed at exit (FP64 variant apply)  */
   double seconds;        /* host wall time of the call, including the diagonal assembly       */
   int launches;          /* kernels of this library launched by the call (no-op ones included) */
+  int outer_iters;       /* refinement steps (fe_pcg_ir); 1 for fe_pcg                        */
 } fe_pcg_stats;
 
 /* Builds the mesh topology on the device: the element dof map (int32 [ne][D^3], the G of
@@ -130,6 +139,21 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
 
+/* Mixed-precision iterative refinement around an FP32 inner PCG (SURVEY "next" item; the paper
+ * itself stays in FP64 throughout).  Outer loop, in FP64 vectors:
+ *   r = (1-m)(b - A x)   with the handle's FP64-accurate operator (FE_VARIANT_F64, or
+ *                        FE_VARIANT_F32X2 when the data is pair-encoded);
+ *   solve A_bc d = r     by PCG (pc) with the FE_VARIANT_F32 operator to inner_rtol * ||r||
+ *                        (0 => 1e-2, the fastest setting measured on the 64^3 p=3 problem);
+ *   x += d,
+ * from x = 0 until ||r||_2 <= rtol ||b||_2 (checked with the FP64-accurate residual, so the
+ * result meets the same residual criterion as fe_pcg).  maxit bounds the total inner iterations.
+ * The FP32 copy of the quadrature data is made on first use.  stats: iters = inner iterations,
+ * outer_iters = refinement steps, rel_resid = true_rel_resid = final FP64-accurate residual.
+ * Returns FE_ERR_NOT_CONVERGED also when a refinement step fails to reduce the residual. */
+int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
+              double inner_rtol, fe_pcg_stats* stats, void* stream);
+
 /* fe_pcg without any device allocation (the paper has no counterpart: this is a service for
  * callers that cannot allocate).  Some applications give all device memory to their own pool
  * allocator up front, and some latency-critical loops cannot afford the blocking and device
@@ -149,6 +173,15 @@ int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double
 #define FE_PCG_NOALLOC_MAX_DOFS 262144
 int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x,
                    double rtol, int maxit, fe_pcg_stats* stats, void* stream);
+
+/* Measurement utility behind the roofline denominators (not part of the operator): runs
+ * independent multiply-add chains on every SM of the current device and returns the sustained
+ * rate in *tflops (multiply-add = 2 flops; one m8n8k4 DMMA = 512 flops).  Units:
+ * FE_PROBE_FP64_FMA, FE_PROBE_FP64_DMMA, FE_PROBE_FP32_FMA, FE_PROBE_F32X2_MAC (the anchored
+ * float-float step of the apply, counted as one FP64-equivalent multiply-add).  Synchronous;
+ * allocates 64 bytes of scratch. */
+enum { FE_PROBE_FP64_FMA = 0, FE_PROBE_FP64_DMMA = 1, FE_PROBE_FP32_FMA = 2, FE_PROBE_F32X2_MAC = 3 };
+int fe_probe_throughput(int unit, double* tflops);
 
 void fe_pa_destroy(fe_pa* pa);
 void fe_mesh_destroy(fe_mesh* mesh);

@@ -315,16 +315,25 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_apply: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_apply: operator not set up in fe_pa_setup");
   const fe_mesh* m = pa->mesh;
-  const bool pairs = (variant == FE_VARIANT_F32X2);
-  if (pairs != (pa->qd_format == FE_VARIANT_F32X2))
-    return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
-                                 "encoding; call fe_pa_set_variant first");
+  if (variant == FE_VARIANT_F32) {
+    if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr)
+      return set_error(FE_ERR_ARG, "fe_apply: no FP32 quadrature data; call "
+                                   "fe_pa_set_variant(FE_VARIANT_F32) first");
+  } else {
+    const bool pairs = (variant == FE_VARIANT_F32X2);
+    if (pairs != (pa->qd_format == FE_VARIANT_F32X2))
+      return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
+                                   "encoding; call fe_pa_set_variant first");
+  }
   if (skip == nullptr) {
     FE_CHECK_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->ndofs, s), "zero y");
   }
   ApplyArgs a;
   a.map = m->d_map;
-  a.qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
+  if (variant == FE_VARIANT_F32)
+    a.qd = reinterpret_cast<const double*>(op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32);
+  else
+    a.qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
   a.x = x;
   a.y = y;
   a.ne = m->ne;
@@ -339,6 +348,8 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
       return launch_apply_f32x2(op, a, s);
     case FE_VARIANT_F64_DMMA:
       return launch_apply_dmma(op, a, s);
+    case FE_VARIANT_F32:
+      return launch_apply_f32(op, a, s);
     default:
       return set_error(FE_ERR_ARG, "fe_apply: unknown variant");
   }
@@ -507,9 +518,30 @@ int fe_pa_setup(const fe_mesh* m, int q1d, const double* dev_coeff, int ops, voi
 int fe_pa_set_variant(fe_pa* pa, int variant, void* stream) {
   clear_error();
   if (!pa) return set_error(FE_ERR_ARG, "fe_pa_set_variant: pa is NULL");
-  if (variant != FE_VARIANT_F64 && variant != FE_VARIANT_F32X2 && variant != FE_VARIANT_F64_DMMA)
+  if (variant != FE_VARIANT_F64 && variant != FE_VARIANT_F32X2 && variant != FE_VARIANT_F64_DMMA &&
+      variant != FE_VARIANT_F32)
     return set_error(FE_ERR_ARG, "fe_pa_set_variant: unknown variant");
   cudaStream_t s = (cudaStream_t)stream;
+  if (variant == FE_VARIANT_F32) {
+    // FP32 copy of the quadrature data next to the FP64 (or pair) data, made once
+    const int64_t nq = pa->mesh->ne * (int64_t)pa->Q * pa->Q * pa->Q;
+    const bool pairs = (pa->qd_format == FE_VARIANT_F32X2);
+    cudaError_t err = cudaSuccess;
+    if (pa->d_qd_diff && !pa->d_qd_diff32) {
+      err = cudaMalloc(&pa->d_qd_diff32, sizeof(float) * 6 * nq);
+      if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
+      const int st = make_qd_f32(pa->d_qd_diff, pa->d_qd_diff32, 6 * nq, pairs, s);
+      if (st != FE_OK) return st;
+    }
+    if (pa->d_qd_mass && !pa->d_qd_mass32) {
+      err = cudaMalloc(&pa->d_qd_mass32, sizeof(float) * nq);
+      if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
+      const int st = make_qd_f32(pa->d_qd_mass, pa->d_qd_mass32, nq, pairs, s);
+      if (st != FE_OK) return st;
+    }
+    pa->variant = variant;
+    return FE_OK;
+  }
   const bool want_pairs = (variant == FE_VARIANT_F32X2);
   const bool have_pairs = (pa->qd_format == FE_VARIANT_F32X2);
   if (want_pairs && !have_pairs) {
@@ -592,6 +624,8 @@ void fe_pa_destroy(fe_pa* pa) {
   cudaFree(pa->d_qd_diff);
   cudaFree(pa->d_qd_mass);
   cudaFree(pa->d_coeff);
+  cudaFree(pa->d_qd_diff32);
+  cudaFree(pa->d_qd_mass32);
   cudaFree(pa->d_work);
   cudaFree(pa->d_red);
   cudaFree(pa->d_flags);

@@ -4,7 +4,7 @@
 namespace fe {
 
 int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s) {
-  return dispatch_order<256, ArF32x2>(op, a, s);
+  return dispatch_order<ArF32x2>(op, a, s);
 }
 
 // In-place re-encoding of FP64 quadrature data as (hi, lo) float pairs and back.  The pair is

@@ -4,7 +4,7 @@
 namespace fe {
 
 int launch_apply_f64(int op, const ApplyArgs& a, cudaStream_t s) {
-  return dispatch_order<128, ArF64>(op, a, s);
+  return dispatch_order<ArF64>(op, a, s);
 }
 
 }  // namespace fe

@@ -42,9 +42,9 @@ struct ApplyLayout {
 };
 
 // DIFF: diffusion (qdata [e][qz][6][qy][qx]: xx, xy, xz, yy, yz, zz) or mass ([e][qz][qy][qx]).
-template <int D, int Q, int NE, int NT, bool DIFF, class Ar>
-__global__ void __launch_bounds__(NT) k_pa_apply(const int32_t* __restrict__ map,
-                                                 const double* __restrict__ qd,
+template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
+                                                 const typename Ar::QdT* __restrict__ qd,
                                                  const double* __restrict__ x,
                                                  double* __restrict__ y, int64_t ne,
                                                  const int* __restrict__ skip,
@@ -83,20 +83,29 @@ __global__ void __launch_bounds__(NT) k_pa_apply(const int32_t* __restrict__ map
     const int j = l / D, k = l - j * D;
     const T* in = bufA + el * SZ_A + l;
     T v[D];
+    float m = 0.0f;
 #pragma unroll
-    for (int i = 0; i < D; ++i) v[i] = in[i * S_DD];
+    for (int i = 0; i < D; ++i) {
+      v[i] = in[i * S_DD];
+      m = Ar::amax(m, v[i]);
+    }
+    const auto sb = Ar::sigB(tab, m, false);
     T* outb = bufB + el * SZ_B + j * S_QD + k * Q;
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
-      T ab = Ar::zero();
+      auto ab = Ar::begin(sb);
 #pragma unroll
-      for (int i = 0; i < D; ++i) Ar::madB(ab, tab, qx, i, v[i]);
-      outb[qx] = Ar::norm(ab);
-      if constexpr (DIFF) {
-        T ag = Ar::zero();
+      for (int i = 0; i < D; ++i) Ar::amadB(ab, tab, qx, i, v[i]);
+      outb[qx] = Ar::end(ab, sb);
+    }
+    if constexpr (DIFF) {
+      const auto sg = Ar::sigG(tab, m, false);
 #pragma unroll
-        for (int i = 0; i < D; ++i) Ar::madG(ag, tab, qx, i, v[i]);
-        outb[D * S_QD + qx] = Ar::norm(ag);
+      for (int qx = 0; qx < Q; ++qx) {
+        auto ag = Ar::begin(sg);
+#pragma unroll
+        for (int i = 0; i < D; ++i) Ar::amadG(ag, tab, qx, i, v[i]);
+        outb[D * S_QD + qx] = Ar::end(ag, sg);
       }
     }
   }
@@ -109,107 +118,169 @@ __global__ void __launch_bounds__(NT) k_pa_apply(const int32_t* __restrict__ map
     const int k = l / Q, qx = l - k * Q;
     const T* in = bufB + el * SZ_B + l;
     T vb[D];
+    float mb = 0.0f;
 #pragma unroll
-    for (int j = 0; j < D; ++j) vb[j] = in[j * S_QD];
+    for (int j = 0; j < D; ++j) {
+      vb[j] = in[j * S_QD];
+      mb = Ar::amax(mb, vb[j]);
+    }
     T* out = bufA + el * SZ_A + k * S_QQ + qx;
+    const auto s_bb = Ar::sigB(tab, mb, false);
     if constexpr (DIFF) {
       T vg[D];
+      float mg = 0.0f;
 #pragma unroll
-      for (int j = 0; j < D; ++j) vg[j] = in[D * S_QD + j * S_QD];
+      for (int j = 0; j < D; ++j) {
+        vg[j] = in[D * S_QD + j * S_QD];
+        mg = Ar::amax(mg, vg[j]);
+      }
+      const auto s_bg = Ar::sigB(tab, mg, false), s_gb = Ar::sigG(tab, mb, false);
 #pragma unroll
       for (int qy = 0; qy < Q; ++qy) {
-        T a0 = Ar::zero(), a1 = Ar::zero(), a2 = Ar::zero();
+        auto a0 = Ar::begin(s_bg), a1 = Ar::begin(s_gb), a2 = Ar::begin(s_bb);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-          Ar::madB(a0, tab, qy, j, vg[j]);
-          Ar::madG(a1, tab, qy, j, vb[j]);
-          Ar::madB(a2, tab, qy, j, vb[j]);
+          Ar::amadB(a0, tab, qy, j, vg[j]);
+          Ar::amadG(a1, tab, qy, j, vb[j]);
+          Ar::amadB(a2, tab, qy, j, vb[j]);
         }
-        out[qy * Q] = Ar::norm(a0);
-        out[D * S_QQ + qy * Q] = Ar::norm(a1);
-        out[2 * D * S_QQ + qy * Q] = Ar::norm(a2);
+        out[qy * Q] = Ar::end(a0, s_bg);
+        out[D * S_QQ + qy * Q] = Ar::end(a1, s_gb);
+        out[2 * D * S_QQ + qy * Q] = Ar::end(a2, s_bb);
       }
     } else {
 #pragma unroll
       for (int qy = 0; qy < Q; ++qy) {
-        T a0 = Ar::zero();
+        auto a0 = Ar::begin(s_bb);
 #pragma unroll
-        for (int j = 0; j < D; ++j) Ar::madB(a0, tab, qy, j, vb[j]);
-        out[qy * Q] = Ar::norm(a0);
+        for (int j = 0; j < D; ++j) Ar::amadB(a0, tab, qy, j, vb[j]);
+        out[qy * Q] = Ar::end(a0, s_bb);
       }
     }
   }
   __syncthreads();
 
   // ---- z phase: contract k -> qz, apply D, contract qz -> k.  line (qy, qx)
-  //      out S4c[qy][k*Q + qx]
+  //      out S4c[qy][k*Q + qx].  The forward contraction is anchored (bound from the inputs),
+  //      the pointwise product too (exact bound per point); the transposed contraction, whose
+  //      inputs appear only inside the qz loop, is anchored in a second pass over the column
+  //      for Q <= 6 and compensated otherwise.
   for (int t = tid; t < nel * Q2; t += NT) {
     const int el = t / Q2, l = t - el * Q2;
     const int qy = l / Q, qx = l - qy * Q;
     const T* in = bufA + el * SZ_A + l;
-    const double* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
+    const typename Ar::QdT* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
     T* out = bufB + el * SZ_B + qy * S_QD + qx;
     if constexpr (DIFF) {
-      T u0[D], u1[D], u2[D], w0[D], w1[D], w2[D];
+      // bounds of the three input columns (one pass over shared memory)
+      float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        u0[k] = in[k * S_QQ];
-        u1[k] = in[D * S_QQ + k * S_QQ];
-        u2[k] = in[2 * D * S_QQ + k * S_QQ];
-        w0[k] = w1[k] = w2[k] = Ar::zero();
+        m0 = Ar::amax(m0, in[k * S_QQ]);
+        m1 = Ar::amax(m1, in[D * S_QQ + k * S_QQ]);
+        m2 = Ar::amax(m2, in[2 * D * S_QQ + k * S_QQ]);
       }
+      const auto s0 = Ar::sigB(tab, m0, false), s1 = Ar::sigB(tab, m1, false);
+      const auto s2 = Ar::sigG(tab, m2, false);
+      // Inputs are re-read from shared memory at every qz when REREAD (the empty asm with a
+      // memory clobber keeps the compiler from caching them in registers): only the 3D
+      // accumulators stay live, which keeps high orders at two or more blocks per SM.
+      // ZTWO (float-float, Q <= 6): keep the column's v values and finish with an anchored
+      // transposed contraction; otherwise accumulate w with compensated steps inside the loop
+      constexpr bool ZTWO = Ar::kAnchored && Q <= 6;
+      constexpr int NW_ = ZTWO ? 1 : D;
+      constexpr int NV_ = ZTWO ? Q : 1;
+      T w0[NW_], w1[NW_], w2[NW_];
+      T vs0[NV_], vs1[NV_], vs2[NV_];
+      float vm0 = 0.0f, vm1 = 0.0f, vm2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NW_; ++k) w0[k] = w1[k] = w2[k] = Ar::zero();
+      // quadrature data of the next qz is loaded one iteration ahead (register double buffer)
+      T nd[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + c * Q2);
 #pragma unroll
       for (int qz = 0; qz < Q; ++qz) {
-        T g0 = Ar::zero(), g1 = Ar::zero(), g2 = Ar::zero();
+        if constexpr (REREAD) asm volatile("" ::: "memory");
+        T cd[6];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          Ar::madB(g0, tab, qz, k, u0[k]);
-          Ar::madB(g1, tab, qz, k, u1[k]);
-          Ar::madG(g2, tab, qz, k, u2[k]);
+        for (int c = 0; c < 6; ++c) cd[c] = nd[c];
+        if (qz + 1 < Q) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + ((qz + 1) * 6 + c) * Q2);
         }
-        g0 = Ar::norm(g0);
-        g1 = Ar::norm(g1);
-        g2 = Ar::norm(g2);
-        const double* qq = qe + qz * 6 * Q2;
-        const T dxx = Ar::load_qd(qq), dxy = Ar::load_qd(qq + Q2), dxz = Ar::load_qd(qq + 2 * Q2);
-        const T dyy = Ar::load_qd(qq + 3 * Q2), dyz = Ar::load_qd(qq + 4 * Q2);
-        const T dzz = Ar::load_qd(qq + 5 * Q2);
-        T v0 = Ar::mul(dxx, g0), v1 = Ar::mul(dxy, g0), v2 = Ar::mul(dxz, g0);
-        Ar::mad(v0, dxy, g1);
-        Ar::mad(v0, dxz, g2);
-        Ar::mad(v1, dyy, g1);
-        Ar::mad(v1, dyz, g2);
-        Ar::mad(v2, dyz, g1);
-        Ar::mad(v2, dzz, g2);
-        v0 = Ar::norm(v0);
-        v1 = Ar::norm(v1);
-        v2 = Ar::norm(v2);
+        auto a0 = Ar::begin(s0), a1 = Ar::begin(s1), a2 = Ar::begin(s2);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          Ar::madB(w0[k], tab, qz, k, v0);
-          Ar::madB(w1[k], tab, qz, k, v1);
-          Ar::madG(w2[k], tab, qz, k, v2);
+          Ar::amadB(a0, tab, qz, k, in[k * S_QQ]);
+          Ar::amadB(a1, tab, qz, k, in[D * S_QQ + k * S_QQ]);
+          Ar::amadG(a2, tab, qz, k, in[2 * D * S_QQ + k * S_QQ]);
+        }
+        const T g0 = Ar::end(a0, s0), g1 = Ar::end(a1, s1), g2 = Ar::end(a2, s2);
+        // v = D g, D symmetric: (xx, xy, xz, yy, yz, zz)
+        const T v0 = Ar::dot3(cd[0], g0, cd[1], g1, cd[2], g2);
+        const T v1 = Ar::dot3(cd[1], g0, cd[3], g1, cd[4], g2);
+        const T v2 = Ar::dot3(cd[2], g0, cd[4], g1, cd[5], g2);
+        if constexpr (ZTWO) {
+          vs0[qz] = v0;
+          vs1[qz] = v1;
+          vs2[qz] = v2;
+          vm0 = Ar::amax(vm0, v0);
+          vm1 = Ar::amax(vm1, v1);
+          vm2 = Ar::amax(vm2, v2);
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            Ar::madB(w0[k], tab, qz, k, v0);
+            Ar::madB(w1[k], tab, qz, k, v1);
+            Ar::madG(w2[k], tab, qz, k, v2);
+          }
         }
       }
+      if constexpr (ZTWO) {
+        // second pass over the column: the transposed z contraction, anchored now that the
+        // bounds max_qz |v_c| are known
+        const auto t0 = Ar::sigB(tab, vm0, true), t1 = Ar::sigB(tab, vm1, true);
+        const auto t2 = Ar::sigG(tab, vm2, true);
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        out[k * Q] = Ar::norm(w0[k]);
-        out[Q * S_QD + k * Q] = Ar::norm(w1[k]);
-        out[2 * Q * S_QD + k * Q] = Ar::norm(w2[k]);
+        for (int k = 0; k < D; ++k) {
+          auto r0 = Ar::begin(t0), r1 = Ar::begin(t1), r2 = Ar::begin(t2);
+#pragma unroll
+          for (int qz = 0; qz < Q; ++qz) {
+            Ar::amadB(r0, tab, qz, k, vs0[qz]);
+            Ar::amadB(r1, tab, qz, k, vs1[qz]);
+            Ar::amadG(r2, tab, qz, k, vs2[qz]);
+          }
+          out[k * Q] = Ar::end(r0, t0);
+          out[Q * S_QD + k * Q] = Ar::end(r1, t1);
+          out[2 * Q * S_QD + k * Q] = Ar::end(r2, t2);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          out[k * Q] = Ar::norm(w0[k]);
+          out[Q * S_QD + k * Q] = Ar::norm(w1[k]);
+          out[2 * Q * S_QD + k * Q] = Ar::norm(w2[k]);
+        }
       }
     } else {
-      T u[D], w[D];
+      float m = 0.0f;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        u[k] = in[k * S_QQ];
-        w[k] = Ar::zero();
-      }
+      for (int k = 0; k < D; ++k) m = Ar::amax(m, in[k * S_QQ]);
+      const auto s = Ar::sigB(tab, m, false);
+      T w[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) w[k] = Ar::zero();
+      T nd = Ar::load_qd(qe);
 #pragma unroll
       for (int qz = 0; qz < Q; ++qz) {
-        T g = Ar::zero();
+        if constexpr (REREAD) asm volatile("" ::: "memory");
+        const T cd = nd;
+        if (qz + 1 < Q) nd = Ar::load_qd(qe + (qz + 1) * Q2);
+        auto a = Ar::begin(s);
 #pragma unroll
-        for (int k = 0; k < D; ++k) Ar::madB(g, tab, qz, k, u[k]);
-        const T v = Ar::norm(Ar::mul(Ar::load_qd(qe + qz * Q2), Ar::norm(g)));
+        for (int k = 0; k < D; ++k) Ar::amadB(a, tab, qz, k, in[k * S_QQ]);
+        const T v = Ar::norm(Ar::mul(cd, Ar::end(a, s)));
 #pragma unroll
         for (int k = 0; k < D; ++k) Ar::madB(w[k], tab, qz, k, v);
       }
@@ -221,42 +292,58 @@ __global__ void __launch_bounds__(NT) k_pa_apply(const int32_t* __restrict__ map
 
   // ---- y^T phase: contract qy -> j.  line (k, qx); out S5c[qx][j*D + k]
   //      diffusion: c0 (-> G_x^T) = B_y^T s0, c1 (-> B_x^T) = G_y^T s1 + B_y^T s2
+  //      (outer-product form over qy with anchored accumulators; bounds from a first pass)
   for (int t = tid; t < nel * QD; t += NT) {
     const int el = t / QD, l = t - el * QD;
     const int k = l / Q, qx = l - k * Q;
     const T* in = bufB + el * SZ_B + l;
     T* out = bufA + el * SZ_A + qx * S_DD + k;
     if constexpr (DIFF) {
-      T s0[Q], s1[Q], s2[Q];
+      float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
 #pragma unroll
       for (int qy = 0; qy < Q; ++qy) {
-        s0[qy] = in[qy * S_QD];
-        s1[qy] = in[Q * S_QD + qy * S_QD];
-        s2[qy] = in[2 * Q * S_QD + qy * S_QD];
+        m0 = Ar::amax(m0, in[qy * S_QD]);
+        m1 = Ar::amax(m1, in[Q * S_QD + qy * S_QD]);
+        m2 = Ar::amax(m2, in[2 * Q * S_QD + qy * S_QD]);
+      }
+      const auto sg = Ar::sigB(tab, m0, true), sb = Ar::sigGB(tab, m1, m2, true);
+      typename Ar::Acc rg[D], rb[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        rg[j] = Ar::begin(sg);
+        rb[j] = Ar::begin(sb);
+      }
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) {
+        const T a0 = in[qy * S_QD], a1 = in[Q * S_QD + qy * S_QD], a2 = in[2 * Q * S_QD + qy * S_QD];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          Ar::amadB(rg[j], tab, qy, j, a0);
+          Ar::amadG(rb[j], tab, qy, j, a1);
+          Ar::amadB(rb[j], tab, qy, j, a2);
+        }
       }
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        T rg = Ar::zero(), rb = Ar::zero();
-#pragma unroll
-        for (int qy = 0; qy < Q; ++qy) {
-          Ar::madB(rg, tab, qy, j, s0[qy]);
-          Ar::madG(rb, tab, qy, j, s1[qy]);
-          Ar::madB(rb, tab, qy, j, s2[qy]);
-        }
-        out[j * D] = Ar::norm(rg);
-        out[Q * S_DD + j * D] = Ar::norm(rb);
+        out[j * D] = Ar::end(rg[j], sg);
+        out[Q * S_DD + j * D] = Ar::end(rb[j], sb);
       }
     } else {
-      T s0[Q];
+      float m0 = 0.0f;
 #pragma unroll
-      for (int qy = 0; qy < Q; ++qy) s0[qy] = in[qy * S_QD];
+      for (int qy = 0; qy < Q; ++qy) m0 = Ar::amax(m0, in[qy * S_QD]);
+      const auto s0 = Ar::sigB(tab, m0, true);
+      typename Ar::Acc r[D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        T r = Ar::zero();
+      for (int j = 0; j < D; ++j) r[j] = Ar::begin(s0);
 #pragma unroll
-        for (int qy = 0; qy < Q; ++qy) Ar::madB(r, tab, qy, j, s0[qy]);
-        out[j * D] = Ar::norm(r);
+      for (int qy = 0; qy < Q; ++qy) {
+        const T a0 = in[qy * S_QD];
+#pragma unroll
+        for (int j = 0; j < D; ++j) Ar::amadB(r[j], tab, qy, j, a0);
       }
+#pragma unroll
+      for (int j = 0; j < D; ++j) out[j * D] = Ar::end(r[j], s0);
     }
   }
   __syncthreads();
@@ -266,27 +353,34 @@ __global__ void __launch_bounds__(NT) k_pa_apply(const int32_t* __restrict__ map
     const int el = t / D2, l = t - el * D2;
     const int j = l / D, k = l - j * D;
     const T* in = bufA + el * SZ_A + l;
-    T sg[Q], sb[Q];
+    float mg = 0.0f, mb = 0.0f;
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) {
-      sg[qx] = in[qx * S_DD];
-      if constexpr (DIFF) sb[qx] = in[Q * S_DD + qx * S_DD];
+      mg = Ar::amax(mg, in[qx * S_DD]);
+      if constexpr (DIFF) mb = Ar::amax(mb, in[Q * S_DD + qx * S_DD]);
+    }
+    const auto s = DIFF ? Ar::sigGB(tab, mg, mb, true) : Ar::sigB(tab, mg, true);
+    typename Ar::Acc r[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) r[i] = Ar::begin(s);
+#pragma unroll
+    for (int qx = 0; qx < Q; ++qx) {
+      const T ag = in[qx * S_DD];
+      if constexpr (DIFF) {
+        const T ab = in[Q * S_DD + qx * S_DD];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          Ar::amadG(r[i], tab, qx, i, ag);
+          Ar::amadB(r[i], tab, qx, i, ab);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) Ar::amadB(r[i], tab, qx, i, ag);
+      }
     }
     T* out = bufB + el * SZ_B + j * D + k * D2;
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      T r = Ar::zero();
-#pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        if constexpr (DIFF) {
-          Ar::madG(r, tab, qx, i, sg[qx]);
-          Ar::madB(r, tab, qx, i, sb[qx]);
-        } else {
-          Ar::madB(r, tab, qx, i, sg[qx]);
-        }
-      }
-      out[i] = r;
-    }
+    for (int i = 0; i < D; ++i) out[i] = Ar::end(r[i], s);
   }
   __syncthreads();
 

@@ -1,6 +1,8 @@
 // Launch helpers shared by the per-variant translation units of the fused apply.
 #pragma once
 
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "fe_apply_kernel.cuh"
@@ -8,12 +10,67 @@
 
 namespace fe {
 
-// Elements per block: as many as fit in ~96 KB of shared memory (two blocks per SM), a power
-// of two, at most 64.
-template <int D, int Q, bool DIFF, class T>
+// Launch shape per arithmetic variant: threads per block, shared-memory budget per block (the
+// elements per block follow from it) and the smallest D from which the z phase re-reads its
+// inputs from shared memory instead of holding them in registers.  The defaults come from
+// sweeps on GB300; the macros exist for tuning builds.
+#ifndef FE_F64_NT
+#define FE_F64_NT 128
+#endif
+#ifndef FE_F64_SMEM
+#define FE_F64_SMEM (96 * 1024)
+#endif
+#ifndef FE_F64_REREAD_D
+#define FE_F64_REREAD_D 5
+#endif
+#ifndef FE_F64_MINB
+#define FE_F64_MINB 1
+#endif
+#ifndef FE_F32X2_MINB
+#define FE_F32X2_MINB 2
+#endif
+#ifndef FE_F32X2_NT
+#define FE_F32X2_NT 256
+#endif
+#ifndef FE_F32X2_SMEM
+#define FE_F32X2_SMEM (96 * 1024)
+#endif
+#ifndef FE_F32X2_REREAD_D
+#define FE_F32X2_REREAD_D 2
+#endif
+
+template <class Ar>
+struct ApplyTuning;
+template <>
+struct ApplyTuning<ArF64> {
+  static constexpr int NT = FE_F64_NT, SMEM = FE_F64_SMEM, REREAD_D = FE_F64_REREAD_D,
+                       MINB = FE_F64_MINB;
+};
+#ifndef FE_F32_NT
+#define FE_F32_NT 256
+#endif
+#ifndef FE_F32_SMEM
+#define FE_F32_SMEM (48 * 1024)
+#endif
+#ifndef FE_F32_MINB
+#define FE_F32_MINB 2
+#endif
+template <>
+struct ApplyTuning<ArF32> {
+  static constexpr int NT = FE_F32_NT, SMEM = FE_F32_SMEM, REREAD_D = 2, MINB = FE_F32_MINB;
+};
+template <>
+struct ApplyTuning<ArF32x2> {
+  static constexpr int NT = FE_F32X2_NT, SMEM = FE_F32X2_SMEM, REREAD_D = FE_F32X2_REREAD_D,
+                       MINB = FE_F32X2_MINB;
+};
+
+// Elements per block: as many as fit in the variant's shared-memory budget, a power of two,
+// at most 64.
+template <int D, int Q, bool DIFF, class T, int SMEM>
 constexpr int elems_per_block() {
   constexpr int bytes = ApplyLayout<D, Q, DIFF>::PER_ELEM * (int)sizeof(T);
-  int ne = (96 * 1024) / bytes;
+  int ne = SMEM / bytes;
   int p2 = 1;
   while (p2 * 2 <= ne && p2 < 64) p2 *= 2;
   return p2;
@@ -28,6 +85,14 @@ inline void fill_tab(const Basis1D& b, TabF64<D, Q>* t) {
 }
 
 template <int D, int Q>
+inline void fill_tab(const Basis1D& b, TabF32<D, Q>* t) {
+  for (int i = 0; i < Q * D; ++i) {
+    t->B[i] = (float)b.B[i];
+    t->G[i] = (float)b.G[i];
+  }
+}
+
+template <int D, int Q>
 inline void fill_tab(const Basis1D& b, TabF32x2<D, Q>* t) {
   for (int i = 0; i < Q * D; ++i) {
     const float bh = (float)b.B[i], gh = (float)b.G[i];
@@ -36,14 +101,42 @@ inline void fill_tab(const Basis1D& b, TabF32x2<D, Q>* t) {
     t->Gh[i] = gh;
     t->Gl[i] = (float)(b.G[i] - (double)gh);
   }
+  // largest absolute row (forward use) and column (transposed use) sums of the high words,
+  // rounded up, for the anchors of the float-float dot products
+  double rB = 0, rG = 0, cB = 0, cG = 0;
+  for (int q = 0; q < Q; ++q) {
+    double sb = 0, sg = 0;
+    for (int d = 0; d < D; ++d) {
+      sb += std::fabs((double)t->Bh[q * D + d]);
+      sg += std::fabs((double)t->Gh[q * D + d]);
+    }
+    rB = std::max(rB, sb);
+    rG = std::max(rG, sg);
+  }
+  for (int d = 0; d < D; ++d) {
+    double sb = 0, sg = 0;
+    for (int q = 0; q < Q; ++q) {
+      sb += std::fabs((double)t->Bh[q * D + d]);
+      sg += std::fabs((double)t->Gh[q * D + d]);
+    }
+    cB = std::max(cB, sb);
+    cG = std::max(cG, sg);
+  }
+  const double up = 1.0 + 1e-6;
+  t->rB = (float)(rB * up);
+  t->rG = (float)(rG * up);
+  t->cB = (float)(cB * up);
+  t->cG = (float)(cG * up);
 }
 
-template <int D, int Q, int NT, bool DIFF, class Ar>
+template <int D, int Q, bool DIFF, class Ar>
 int run_apply(const ApplyArgs& a, cudaStream_t s) {
   using T = typename Ar::T;
-  constexpr int NE = elems_per_block<D, Q, DIFF, T>();
+  using Tune = ApplyTuning<Ar>;
+  constexpr int NT = Tune::NT;
+  constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM>();
   const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF>::PER_ELEM * sizeof(T);
-  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar>;
+  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -54,19 +147,20 @@ int run_apply(const ApplyArgs& a, cudaStream_t s) {
   fill_tab<D, Q>(*a.basis, &tab);
   const int64_t nblk = (a.ne + NE - 1) / NE;
   if (nblk == 0) return FE_OK;
-  kern<<<(unsigned int)nblk, NT, smem, s>>>(a.map, a.qd, a.x, a.y, a.ne, a.skip, tab);
+  kern<<<(unsigned int)nblk, NT, smem, s>>>(
+      a.map, reinterpret_cast<const typename Ar::QdT*>(a.qd), a.x, a.y, a.ne, a.skip, tab);
   return cuda_error(cudaGetLastError(), "apply kernel launch");
 }
 
 // Dispatch on the order for the default rule Q = p + 2.
-template <int NT, class Ar>
+template <class Ar>
 int dispatch_order(int op, const ApplyArgs& a, cudaStream_t s) {
   const bool diff = (op == FE_DIFFUSION);
   if (a.Q != a.p + 2) return set_error(FE_ERR_UNSUPPORTED, "only q1d = order + 2 is built");
 #define FE_CASE(P)                                                                  \
   case P:                                                                           \
-    return diff ? run_apply<P + 1, P + 2, NT, true, Ar>(a, s)                       \
-                : run_apply<P + 1, P + 2, NT, false, Ar>(a, s);
+    return diff ? run_apply<P + 1, P + 2, true, Ar>(a, s)                           \
+                : run_apply<P + 1, P + 2, false, Ar>(a, s);
   switch (a.p) {
     FE_CASE(1)
     FE_CASE(2)

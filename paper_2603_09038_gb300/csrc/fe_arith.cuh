@@ -3,20 +3,33 @@
 //  ArF64    IEEE FP64 on the FP64 pipe: every multiply-add is one DFMA.
 //  ArF32x2  FP64-accurate float-float arithmetic on the FP32 pipe (GB300's FP64 pipe delivers
 //           ~1.2 TFLOP/s against ~75 TFLOP/s FP32).  A value is the unevaluated sum h + l of two
-//           floats.  Products use Dekker's error-free product (via FMA: p = fl(a*b),
-//           e = fma(a, b, -p) is exact); sums use Knuth's TwoSum (s = fl(a+b),
-//           err = (a - (s - bb)) + (b - bb), bb = s - a, exact).  Accumulators carry their
-//           rounding errors in the low word and are renormalised once per output.  The
-//           relative error of a length-n dot product is O(n * 2^-47) of sum |a_i b_i|, i.e. FP64
-//           class.  Intrinsics with explicit rounding (__fmul_rn, __fadd_rn, ...) keep the
-//           compiler from contracting the error-free steps into FMAs.
+//           floats (|l| <= ulp(h)).  Two accumulation schemes:
+//
+//   * anchored dot products (amad*, dot3), used wherever a bound B >= sum_i |a_i x_i| of the sum
+//     is known before it starts (a 1D contraction: max_i |x_i| times the 1D table's largest
+//     absolute row or column sum; a row of the pointwise D: the exact sum of |a_i| |x_i|).  The high accumulator starts at the anchor
+//     sigma = 2^ceil(log2(4 B)), so it stays within [3 sigma/4, 5 sigma/4]; then per term
+//         t = fma(ah, xh, A);  z = t - A;  r = fma(ah, xh, -z);  L += r;  L += ah xl + al xh
+//     z is exact (Sterbenz: t / A lies in [1/2, 2]), so A - sigma is exactly the sum of the
+//     parts of the products above ulp(A), and r, the rest of each product, is rounded once to
+//     float -- an error below 2^-24 ulp(A), i.e. 2^-47 sigma.  Six FP32 instructions per term.
+//   * compensated dot products (mad*), for sums whose bound is not known in advance (the
+//     transposed z contraction at Q > 6, whose inputs are produced on the fly; the mass
+//     pointwise product): Dekker's exact product by FMA plus Knuth's TwoSum, twelve
+//     instructions per term.
+//
+//  The primitives (fe_f2.h) are __host__ __device__ with explicit rounding, so the same
+//  error-free steps also run in the CPU unit test of that header.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fe_f2.h"
+
 namespace fe {
 
+// ---------------------------------------------------------------------------- tables
 // 1D basis tables passed by value in the kernel parameter space (constant bank), so that
 // fully unrolled contractions read them as immediate constant operands.
 template <int D, int Q>
@@ -25,25 +38,35 @@ struct TabF64 {
   double G[Q * D];
 };
 
+// Float-float tables; rB/rG = max_q sum_d |.| (forward contractions), cB/cG = max_d sum_q |.|
+// (transposed contractions), each rounded up.
 template <int D, int Q>
 struct TabF32x2 {
   float Bh[Q * D], Bl[Q * D];
   float Gh[Q * D], Gl[Q * D];
+  float rB, rG, cB, cG;
 };
 
-struct f2 {
-  float h, l;
+template <int D, int Q>
+struct TabF32 {
+  float B[Q * D];
+  float G[Q * D];
 };
 
-// ---------------------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------- policies
 struct ArF64 {
+  static constexpr bool kAnchored = false;
+  using QdT = double;
   using T = double;
+  using Acc = double;
+  using Sig = float;  // unused
   template <int D, int Q>
   using Tab = TabF64<D, Q>;
 
   static __device__ __forceinline__ T zero() { return 0.0; }
   static __device__ __forceinline__ T from_f64(double v) { return v; }
   static __device__ __forceinline__ T load_qd(const double* p) { return __ldcs(p); }
+  // compensated / plain accumulation
   template <int D, int Q>
   static __device__ __forceinline__ void madB(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
     acc = fma(t.B[q * D + d], x, acc);
@@ -55,58 +78,39 @@ struct ArF64 {
   static __device__ __forceinline__ void mad(T& acc, T a, T x) { acc = fma(a, x, acc); }
   static __device__ __forceinline__ T mul(T a, T x) { return a * x; }
   static __device__ __forceinline__ T norm(T a) { return a; }
+  // anchored accumulation degenerates to plain FMA in FP64
+  static __device__ __forceinline__ float amax(float m, T) { return m; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigB(const Tab<D, Q>&, float, bool) { return 0.f; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigG(const Tab<D, Q>&, float, bool) { return 0.f; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigGB(const Tab<D, Q>&, float, float, bool) {
+    return 0.f;
+  }
+  static __device__ __forceinline__ Acc begin(Sig) { return 0.0; }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadB(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fma(t.B[q * D + d], x, acc);
+  }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadG(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fma(t.G[q * D + d], x, acc);
+  }
+  static __device__ __forceinline__ T end(Acc a, Sig) { return a; }
+  // a0 x0 + a1 x1 + a2 x2 (one row of the pointwise D)
+  static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
+    return fma(a2, x2, fma(a1, x1, a0 * x0));
+  }
   static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, v); }
 };
 
-// ---------------------------------------------------------------------------------------------
-// float-float helpers
-
-// acc += a * x with a = (ah, al) and x = (x.h, x.l); acc stays unnormalised (h, l).
-static __device__ __forceinline__ void f2_mad(f2& acc, float ah, float al, f2 x) {
-  const float p = __fmul_rn(ah, x.h);
-  float e = __fmaf_rn(ah, x.h, -p);          // exact low part of ah * x.h
-  e = __fmaf_rn(ah, x.l, e);
-  e = __fmaf_rn(al, x.h, e);
-  const float s = __fadd_rn(acc.h, p);       // TwoSum(acc.h, p)
-  const float bb = __fsub_rn(s, acc.h);
-  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  acc.h = s;
-  acc.l = __fadd_rn(acc.l, __fadd_rn(e, err));
-}
-
-// Normalised (h, l) with h = fl(h + l) (TwoSum, valid for any ordering of magnitudes).
-static __device__ __forceinline__ f2 f2_norm(f2 a) {
-  const float s = __fadd_rn(a.h, a.l);
-  const float bb = __fsub_rn(s, a.h);
-  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(a.l, bb));
-  return f2{s, err};
-}
-
-// Splits an FP64 value into floats without touching the FP64 pipe: h = v truncated to 24
-// significant bits (exact), l = the next 23 bits of the remainder (exact), by integer
-// manipulation of the IEEE encodings.  Valid for 2^-80 < |v| < 2^127; smaller magnitudes fall
-// back to a plain conversion (their relative accuracy is irrelevant for O(1) data), larger
-// ones overflow to +-inf.
-static __device__ __forceinline__ f2 f2_from_f64(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
-  const unsigned int sign = hw & 0x80000000u;
-  const int ex = (int)((hw >> 20) & 0x7FFu);  // biased double exponent
-  const int fexp = ex - 896;                  // biased float exponent (1023 - 127)
-  if (fexp <= 0 || fexp >= 255 || ex < 943) return f2{__double2float_rn(v), 0.0f};
-  const unsigned int mant = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  const float h = __uint_as_float(sign | ((unsigned int)fexp << 23) | mant);
-  // remaining 29 significand bits: keep the top 23, an exact integer r < 2^23, scaled by
-  // 2^(ex - 1075 + 6) (float exponent field ex - 942 >= 1 for ex >= 943)
-  const unsigned int rem = (lw & 0x1FFFFFFFu) >> 6;
-  const float r = __fsub_rn(__uint_as_float(0x4B000000u | rem), 8388608.0f);
-  const float l = __fmul_rn(r, __uint_as_float((unsigned int)(ex - 942) << 23));
-  return f2{h, __uint_as_float(__float_as_uint(l) | sign)};
-}
-
-// ---------------------------------------------------------------------------------------------
 struct ArF32x2 {
+  static constexpr bool kAnchored = true;
+  using QdT = double;  // 8-byte (hi, lo) float pairs
   using T = f2;
+  using Acc = Anch;
+  using Sig = float;
   template <int D, int Q>
   using Tab = TabF32x2<D, Q>;
 
@@ -132,9 +136,96 @@ struct ArF32x2 {
     return r;
   }
   static __device__ __forceinline__ T norm(T a) { return f2_norm(a); }
+  static __device__ __forceinline__ float amax(float m, T x) { return fmaxf(m, fabsf(x.h)); }
+  // anchors: forward (row sums) or transposed (column sums) use of the table
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigB(const Tab<D, Q>& t, float m, bool transposed) {
+    return anchor_of(f_mul(transposed ? t.cB : t.rB, m));
+  }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigG(const Tab<D, Q>& t, float m, bool transposed) {
+    return anchor_of(f_mul(transposed ? t.cG : t.rG, m));
+  }
+  // bound of G.a + B.b with max |a| = mg, max |b| = mb
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigGB(const Tab<D, Q>& t, float mg, float mb,
+                                             bool transposed) {
+    return anchor_of(f_fma(transposed ? t.cG : t.rG, mg, f_mul(transposed ? t.cB : t.rB, mb)));
+  }
+  static __device__ __forceinline__ Acc begin(Sig s) { return anch_begin(s); }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadB(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    anch_mad(acc, t.Bh[q * D + d], t.Bl[q * D + d], x);
+  }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadG(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    anch_mad(acc, t.Gh[q * D + d], t.Gl[q * D + d], x);
+  }
+  static __device__ __forceinline__ T end(Acc a, Sig s) { return anch_end(a, s); }
+  // a0 x0 + a1 x1 + a2 x2, anchored with the exact bound sum |a_i.h x_i.h| of this point
+  static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
+    const float b = f_fma(fabsf(a2.h), fabsf(x2.h),
+                          f_fma(fabsf(a1.h), fabsf(x1.h), f_mul(fabsf(a0.h), fabsf(x0.h))));
+    const float sg = anchor_of(b);
+    Anch acc = anch_begin(sg);
+    anch_mad(acc, a0.h, a0.l, x0);
+    anch_mad(acc, a1.h, a1.l, x1);
+    anch_mad(acc, a2.h, a2.l, x2);
+    return anch_end(acc, sg);
+  }
   static __device__ __forceinline__ void scatter(double* y, T v) {
     atomicAdd(y, (double)v.h + (double)v.l);
   }
+};
+
+// Plain FP32 (the inner solves of mixed-precision iterative refinement): FP32 quadrature data
+// (half the bytes), FP32 FMAs; FP64 vectors in and out, converted by integer manipulation.
+struct ArF32 {
+  static constexpr bool kAnchored = false;
+  using QdT = float;
+  using T = float;
+  using Acc = float;
+  using Sig = float;
+  template <int D, int Q>
+  using Tab = TabF32<D, Q>;
+
+  static __device__ __forceinline__ T zero() { return 0.0f; }
+  static __device__ __forceinline__ T from_f64(double v) { return f2_from_f64(v).h; }
+  static __device__ __forceinline__ T load_qd(const float* p) { return __ldcs(p); }
+  template <int D, int Q>
+  static __device__ __forceinline__ void madB(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fmaf(t.B[q * D + d], x, acc);
+  }
+  template <int D, int Q>
+  static __device__ __forceinline__ void madG(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fmaf(t.G[q * D + d], x, acc);
+  }
+  static __device__ __forceinline__ void mad(T& acc, T a, T x) { acc = fmaf(a, x, acc); }
+  static __device__ __forceinline__ T mul(T a, T x) { return a * x; }
+  static __device__ __forceinline__ T norm(T a) { return a; }
+  static __device__ __forceinline__ float amax(float m, T) { return m; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigB(const Tab<D, Q>&, float, bool) { return 0.f; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigG(const Tab<D, Q>&, float, bool) { return 0.f; }
+  template <int D, int Q>
+  static __device__ __forceinline__ Sig sigGB(const Tab<D, Q>&, float, float, bool) {
+    return 0.f;
+  }
+  static __device__ __forceinline__ Acc begin(Sig) { return 0.0f; }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadB(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fmaf(t.B[q * D + d], x, acc);
+  }
+  template <int D, int Q>
+  static __device__ __forceinline__ void amadG(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+    acc = fmaf(t.G[q * D + d], x, acc);
+  }
+  static __device__ __forceinline__ T end(Acc a, Sig) { return a; }
+  static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
+    return fmaf(a2, x2, fmaf(a1, x1, a0 * x0));
+  }
+  static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, f64_from_f32(v)); }
 };
 
 }  // namespace fe

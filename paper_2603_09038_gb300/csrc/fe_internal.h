@@ -53,6 +53,8 @@ struct fe_pa {
   double* d_qd_diff = nullptr;     // [ne][Q][6][Q][Q] (qz, component, qy, qx)
   double* d_qd_mass = nullptr;     // [ne][Q][Q][Q]
   double* d_coeff = nullptr;       // [ne] copy of the coefficient (nullptr => 1)
+  float* d_qd_diff32 = nullptr;    // FP32 copy for FE_VARIANT_F32 (made on first use)
+  float* d_qd_mass32 = nullptr;
   // PCG workspace (allocated on first fe_pcg, freed by fe_pa_destroy)
   double* d_work = nullptr;        // 5 vectors of ndofs
   double* d_red = nullptr;         // reduction partials + scalars
@@ -78,6 +80,8 @@ struct ApplyArgs {
 int launch_apply_f64(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_dmma(int op, const ApplyArgs& a, cudaStream_t s);
+int launch_apply_f32(int op, const ApplyArgs& a, cudaStream_t s);
+int make_qd_f32(const double* src, float* dst, int64_t n, bool pairs, cudaStream_t s);
 
 // Re-encodes n FP64 values in place as float pairs (hi, lo) or back.
 int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);

@@ -6,9 +6,9 @@
 // the boundary entries of b ignored, every iterate, residual and search direction stays zero on
 // the boundary, so A_bc p reduces to (1-m) A p.
 //
-// GB300 layout of one iteration (no host round trip): zero q | fused apply q = A p | p.q
-// partials | control (alpha) | x, r, z update + r.z, r.r partials | control (beta, stop test) |
-// p update.  Scalars and the stop flag live in device memory; every kernel returns at once when
+// GB300 layout of one iteration (no host round trip): fused apply q = A p | p.q partials |
+// control (alpha) | x, r, z update + r.z, r.r partials | control (beta, stop test) | p update
+// (which also zeroes q for the next atomic scatter).  Scalars and the stop flag live in device memory; every kernel returns at once when
 // the flag is set, so the host queues iterations in batches and reads the flag once per batch.
 // Inner products are deterministic: a fixed grid of kReduceBlocks blocks, fixed in-block trees,
 // and the partials summed in block order by a single thread.
@@ -60,10 +60,28 @@ __device__ __forceinline__ void block_sum2(double a, double b, double* part0, do
   }
 }
 
+// Deterministic sum of the kReduceBlocks partials by one block of kReduceBlocks threads (fixed
+// shuffle tree, then the warp sums in order); every thread returns the total.
+constexpr int kFinishThreads = kReduceBlocks;
+
 __device__ __forceinline__ double ordered_sum(const double* part) {
-  double s = 0.0;
-  for (int i = 0; i < kReduceBlocks; ++i) s += part[i];
-  return s;
+  __shared__ double ws[kFinishThreads / 32];
+  __shared__ double total;
+  double v = part[threadIdx.x];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = ws[threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) total = w;
+  }
+  __syncthreads();
+  const double t = total;
+  __syncthreads();
+  return t;
 }
 
 __global__ void __launch_bounds__(kReduceThreads) k_init(const double* __restrict__ b,
@@ -72,7 +90,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_init(const double* __restric
                                                          double* __restrict__ x,
                                                          double* __restrict__ r,
                                                          double* __restrict__ z,
-                                                         double* __restrict__ p, int64_t n,
+                                                         double* __restrict__ p,
+                                                         double* __restrict__ q, int64_t n,
                                                          double* part0, double* part1) {
   double s_rz = 0.0, s_bb = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -83,14 +102,18 @@ __global__ void __launch_bounds__(kReduceThreads) k_init(const double* __restric
     r[i] = bi;
     z[i] = zi;
     p[i] = zi;
+    q[i] = 0.0;
     s_rz = fma(bi, zi, s_rz);
     s_bb = fma(bi, bi, s_bb);
   }
   block_sum2(s_rz, s_bb, part0, part1);
 }
 
-__global__ void k_finish_init(const double* part0, const double* part1, double* sc, int* flags) {
+__global__ void __launch_bounds__(kFinishThreads) k_finish_init(const double* part0,
+                                                              const double* part1, double* sc,
+                                                              int* flags) {
   const double rz = ordered_sum(part0), bb = ordered_sum(part1);
+  if (threadIdx.x != 0) return;
   sc[S_RZ] = rz;
   sc[S_BB] = bb;
   sc[S_REL] = 0.0;
@@ -104,14 +127,6 @@ __global__ void k_finish_init(const double* part0, const double* part1, double* 
   if (flags[F_STATE] == ST_RUN) sc[S_REL] = 1.0;
 }
 
-__global__ void __launch_bounds__(kReduceThreads) k_zero(double* __restrict__ v, int64_t n,
-                                                         const int* flags) {
-  if (flags[F_STATE] != ST_RUN) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = 0.0;
-}
-
 __global__ void __launch_bounds__(kReduceThreads) k_dot(const double* __restrict__ a,
                                                         const double* __restrict__ b, int64_t n,
                                                         double* part0, const int* flags) {
@@ -123,9 +138,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_dot(const double* __restrict
   block_sum2(s, 0.0, part0, nullptr);
 }
 
-__global__ void k_finish_pq(const double* part0, double* sc, int* flags) {
+__global__ void __launch_bounds__(kFinishThreads) k_finish_pq(const double* part0, double* sc,
+                                                            int* flags) {
   if (flags[F_STATE] != ST_RUN) return;
   const double pq = ordered_sum(part0);
+  if (threadIdx.x != 0) return;
   sc[S_PQ] = pq;
   if (!isfinite(pq))
     flags[F_STATE] = ST_NAN;
@@ -163,10 +180,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
   block_sum2(s_rz, s_rr, part0, part1);
 }
 
-__global__ void k_finish_update(const double* part0, const double* part1, double* sc,
-                                int* flags, double rtol, int maxit) {
+__global__ void __launch_bounds__(kFinishThreads) k_finish_update(const double* part0,
+                                                                const double* part1, double* sc,
+                                                                int* flags, double rtol,
+                                                                int maxit) {
   if (flags[F_STATE] != ST_RUN) return;
   const double rz = ordered_sum(part0), rr = ordered_sum(part1);
+  if (threadIdx.x != 0) return;
   const int it = flags[F_ITERS] + 1;
   flags[F_ITERS] = it;
   const double rel = sqrt(rr / sc[S_BB]);
@@ -185,15 +205,18 @@ __global__ void k_finish_update(const double* part0, const double* part1, double
   if (it >= maxit) flags[F_STATE] = ST_MAXIT;
 }
 
+// p = z + beta p, and q = 0 for the next apply's atomic scatter-add.
 __global__ void __launch_bounds__(kReduceThreads) k_pupdate(double* __restrict__ p,
                                                             const double* __restrict__ z,
-                                                            int64_t n, const double* sc,
-                                                            const int* flags) {
+                                                            double* __restrict__ q, int64_t n,
+                                                            const double* sc, const int* flags) {
   if (flags[F_STATE] != ST_RUN) return;
   const double beta = sc[S_BETA];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     p[i] = fma(beta, p[i], z[i]);
+    q[i] = 0.0;
+  }
 }
 
 // Jacobi: boundary entries of the diagonal set to 1 (they are never used); any non-positive
@@ -210,22 +233,203 @@ __global__ void __launch_bounds__(kReduceThreads) k_fix_diag(double* __restrict_
   }
 }
 
-// ||(1-m)(b - q)||^2 partials for the true residual.
+// ||(1-m)(b - q)||^2 partials for the true residual; the residual itself is stored in rout
+// when given.
 __global__ void __launch_bounds__(kReduceThreads) k_resid(const double* __restrict__ b,
                                                           const double* __restrict__ q,
                                                           const uint8_t* __restrict__ mask,
-                                                          int64_t n, double* part0) {
-  double s = 0.0;
+                                                          double* __restrict__ rout, int64_t n,
+                                                          double* part0, double* part1) {
+  double s = 0.0, sb = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = mask[i] ? 0.0 : b[i] - q[i];
+    const bool bnd = mask[i] != 0;
+    const double bi = bnd ? 0.0 : b[i];
+    const double ri = bnd ? 0.0 : bi - q[i];
+    if (rout) rout[i] = ri;
     s = fma(ri, ri, s);
+    sb = fma(bi, bi, sb);
   }
-  block_sum2(s, 0.0, part0, nullptr);
+  block_sum2(s, sb, part0, part1);
 }
 
-__global__ void k_finish_resid(const double* part0, double* sc) {
-  sc[S_TRUE] = sqrt(ordered_sum(part0) / sc[S_BB]);
+// ||(1-m)(b - A x)|| / ||(1-m) b|| into sc[S_TRUE] (0 when b vanishes), ||(1-m) b||^2 into sc[S_BB].
+__global__ void __launch_bounds__(kFinishThreads) k_finish_resid(const double* part0,
+                                                               const double* part1, double* sc) {
+  const double rr = ordered_sum(part0), bb = ordered_sum(part1);
+  if (threadIdx.x == 0) {
+    sc[S_BB] = bb;
+    sc[S_TRUE] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+struct PcgWork {
+  double *r, *z, *p, *q, *d;
+  double *part0, *part1, *sc;
+  int* flags;
+};
+
+struct PcgResult {
+  int state = ST_RUN, iters = 0, launches = 0;
+  double rel = 0.0, bb = 0.0;
+};
+
+// Carves the work vectors (nvec of ndofs) and the reduction area out of the handle's cached
+// workspace, (re)allocating it when the mesh size or the vector count grows.
+int pcg_workspace(fe_pa* pa, int nvec, PcgWork* w, double** extra) {
+  const int64_t n = pa->mesh->ndofs;
+  if (pa->work_ndofs != n * nvec) {
+    cudaFree(pa->d_work);
+    cudaFree(pa->d_red);
+    cudaFree(pa->d_flags);
+    pa->d_work = pa->d_red = nullptr;
+    pa->d_flags = nullptr;
+    pa->work_ndofs = 0;
+    cudaError_t err;
+    if ((err = cudaMalloc(&pa->d_work, sizeof(double) * nvec * n)) != cudaSuccess ||
+        (err = cudaMalloc(&pa->d_red, sizeof(double) * (2 * kReduceBlocks + kScalars))) !=
+            cudaSuccess ||
+        (err = cudaMalloc(&pa->d_flags, sizeof(int) * 4)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg: workspace cudaMalloc");
+    pa->work_ndofs = n * nvec;
+  }
+  w->r = pa->d_work;
+  w->z = w->r + n;
+  w->p = w->z + n;
+  w->q = w->p + n;
+  w->d = w->q + n;
+  if (extra) *extra = w->d + n;
+  w->part0 = pa->d_red;
+  w->part1 = w->part0 + kReduceBlocks;
+  w->sc = w->part1 + kReduceBlocks;
+  w->flags = pa->d_flags;
+  return FE_OK;
+}
+
+// Jacobi diagonal into w.d (boundary entries 1); FE_ERR_BREAKDOWN on a non-positive entry.
+int pcg_jacobi(const fe_pa* pa, int op, const PcgWork& w, cudaStream_t s, int* launches) {
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(w.flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg: flags");
+  int st = fe_assemble_diagonal(pa, op, w.d, s);
+  if (st != FE_OK) return st;
+  k_fix_diag<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.d, pa->mesh->d_mask, pa->mesh->ndofs, w.flags);
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg: diag fix launch");
+  *launches += 2;
+  int hflags[4];
+  if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg: diagonal");
+  if (hflags[2]) return set_error(FE_ERR_BREAKDOWN, "fe_pcg: non-positive diagonal entry");
+  return FE_OK;
+}
+
+// The CG iteration proper: solves A_bc x = b from x = 0 with the given apply variant and the
+// Jacobi diagonal dj (or none); synchronous; res gets the state, iterations and launches.
+int pcg_run(const fe_pa* pa, int op, int variant, const double* b, double* x, const double* dj,
+            double rtol, int maxit, const PcgWork& w, cudaStream_t s, PcgResult* res) {
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  const uint8_t* mask = m->d_mask;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(w.flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg: flags");
+  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(b, mask, dj, x, w.r, w.z, w.p, w.q, n, w.part0,
+                                                  w.part1);
+  k_finish_init<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags);
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg: init launch");
+  res->launches += 2;
+  int hflags[4] = {0, 0, 0, 0};
+  int queued = 0;
+  for (;;) {
+    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
+      int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags);
+      if (st != FE_OK) return st;
+      k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.q, n, w.part0, w.flags);
+      k_finish_pq<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
+      k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, w.r, w.z, w.p, w.q, dj, mask, n, w.sc,
+                                                          w.part0, w.part1, w.flags);
+      k_finish_update<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
+      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.z, w.q, n, w.sc, w.flags);
+      if ((err = cudaGetLastError()) != cudaSuccess)
+        return cuda_error(err, "fe_pcg: iteration launch");
+      res->launches += 6;
+    }
+    if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg: iteration");
+    if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
+  }
+  double hsc[kScalars];
+  if ((err = cudaMemcpyAsync(hsc, w.sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg: stats");
+  res->state = hflags[F_STATE];
+  res->iters = hflags[F_ITERS];
+  res->rel = hsc[S_REL];
+  res->bb = hsc[S_BB];
+  return FE_OK;
+}
+
+// ||(1-m)(b - A x)|| / ||b|| with the given variant (q is overwritten); also stores the
+// residual in rout when given.
+int pcg_true_residual(const fe_pa* pa, int op, int variant, const double* b, const double* x,
+                      double* rout, const PcgWork& w, cudaStream_t s, int* launches,
+                      double* rel) {
+  const int64_t n = pa->mesh->ndofs;
+  int st = apply_dispatch(pa, op, variant, x, w.q, s);
+  if (st != FE_OK) return st;
+  k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(b, w.q, pa->mesh->d_mask, rout, n, w.part0,
+                                                   w.part1);
+  k_finish_resid<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc);
+  cudaError_t err;
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg: residual launch");
+  *launches += 3;
+  double hsc[kScalars];
+  if ((err = cudaMemcpyAsync(hsc, w.sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg: residual");
+  *rel = hsc[S_TRUE];
+  return FE_OK;
+}
+
+int pcg_status(int state, const char* who) {
+  switch (state) {
+    case ST_CONV:
+      return FE_OK;
+    case ST_BREAK:
+      return set_error(FE_ERR_BREAKDOWN, std::string(who) + ": p.Ap <= 0 (operator not SPD on the free dofs)");
+    case ST_NAN:
+      return set_error(FE_ERR_NAN, std::string(who) + ": NaN or Inf in the iteration");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, std::string(who) + ": maxit reached before rtol");
+  }
+}
+
+int pcg_check_args(const fe_pa* pa, int op, int pc, const double* b, const double* x, double rtol,
+                   int maxit, const char* who) {
+  if (!pa || !b || !x) return set_error(FE_ERR_ARG, std::string(who) + ": null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, std::string(who) + ": bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, std::string(who) + ": operator not set up");
+  if (pc != FE_PC_NONE && pc != FE_PC_JACOBI)
+    return set_error(FE_ERR_ARG, std::string(who) + ": bad preconditioner");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, std::string(who) + ": bad rtol or maxit");
+  return FE_OK;
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_axpy(double* __restrict__ x,
+                                                         const double* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
 }
 
 }  // namespace
@@ -234,124 +438,107 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
                       int maxit, fe_pcg_stats* stats, void* stream) {
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
-  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0};
-  int launches = 0;
-  if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_pcg: null argument");
-  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pcg: bad op");
-  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pcg: operator not set up");
-  if (pc != FE_PC_NONE && pc != FE_PC_JACOBI) return set_error(FE_ERR_ARG, "fe_pcg: bad preconditioner");
-  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_pcg: bad rtol or maxit");
-  cudaStream_t s = (cudaStream_t)stream;
-  const fe_mesh* m = pa->mesh;
-  const int64_t n = m->ndofs;
-  cudaError_t err;
-  if (pa->work_ndofs != n) {
-    cudaFree(pa->d_work);
-    cudaFree(pa->d_red);
-    cudaFree(pa->d_flags);
-    pa->d_work = pa->d_red = nullptr;
-    pa->d_flags = nullptr;
-    pa->work_ndofs = 0;
-    if ((err = cudaMalloc(&pa->d_work, sizeof(double) * 5 * n)) != cudaSuccess ||
-        (err = cudaMalloc(&pa->d_red, sizeof(double) * (2 * kReduceBlocks + kScalars))) !=
-            cudaSuccess ||
-        (err = cudaMalloc(&pa->d_flags, sizeof(int) * 4)) != cudaSuccess)
-      return cuda_error(err, "fe_pcg: workspace cudaMalloc");
-    pa->work_ndofs = n;
-  }
-  double* r = pa->d_work;
-  double* z = r + n;
-  double* p = z + n;
-  double* q = p + n;
-  double* d = q + n;
-  double* part0 = pa->d_red;
-  double* part1 = part0 + kReduceBlocks;
-  double* sc = part1 + kReduceBlocks;
-  int* flags = pa->d_flags;
-  const uint8_t* mask = m->d_mask;
-
-#define PCG_LAUNCH_CHECK(what)                                  \
-  do {                                                          \
-    cudaError_t e_ = cudaGetLastError();                        \
-    if (e_ != cudaSuccess) return cuda_error(e_, what);         \
-  } while (0)
-
-
-  if ((err = cudaMemsetAsync(flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
-    return cuda_error(err, "fe_pcg: flags");
-  const double* dj = nullptr;
-  if (pc == FE_PC_JACOBI) {
-    int st = fe_assemble_diagonal(pa, op, d, stream);
-    if (st != FE_OK) return st;
-    k_fix_diag<<<kReduceBlocks, kReduceThreads, 0, s>>>(d, mask, n, flags);
-    PCG_LAUNCH_CHECK("fe_pcg: diag fix launch");
-    launches += 2;
-    dj = d;
-  }
-  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, mask, dj, dev_x, r, z, p, n, part0, part1);
-  k_finish_init<<<1, 1, 0, s>>>(part0, part1, sc, flags);
-  PCG_LAUNCH_CHECK("fe_pcg: init launch");
-  launches += 2;
-  int hflags[4] = {0, 0, 0, 0};
-  if (pc == FE_PC_JACOBI) {
-    if ((err = cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (err = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_error(err, "fe_pcg: init");
-    if (hflags[2]) return set_error(FE_ERR_BREAKDOWN, "fe_pcg: non-positive diagonal entry");
-  }
-  int queued = 0;
-  for (;;) {
-    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
-      k_zero<<<kReduceBlocks, kReduceThreads, 0, s>>>(q, n, flags);
-      int st = apply_dispatch(pa, op, pa->variant, p, q, s, flags);
-      if (st != FE_OK) return st;
-      k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, q, n, part0, flags);
-      k_finish_pq<<<1, 1, 0, s>>>(part0, sc, flags);
-      k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, r, z, p, q, dj, mask, n, sc, part0,
-                                                          part1, flags);
-      k_finish_update<<<1, 1, 0, s>>>(part0, part1, sc, flags, rtol, maxit);
-      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, z, n, sc, flags);
-      PCG_LAUNCH_CHECK("fe_pcg: iteration launch");
-      launches += 7;
-    }
-    if ((err = cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (err = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_error(err, "fe_pcg: iteration");
-    if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
-  }
-  // true residual ||(1-m)(b - A x)|| / ||b|| with the same apply
-  int st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  int st = pcg_check_args(pa, op, pc, dev_b, dev_x, rtol, maxit, "fe_pcg");
   if (st != FE_OK) return st;
-  k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, mask, n, part0);
-  k_finish_resid<<<1, 1, 0, s>>>(part0, sc);
-  PCG_LAUNCH_CHECK("fe_pcg: residual launch");
-  launches += 3;
-  double hsc[kScalars];
-  if ((err = cudaMemcpyAsync(hsc, sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess ||
-      (err = cudaStreamSynchronize(s)) != cudaSuccess)
-    return cuda_error(err, "fe_pcg: stats");
-#undef PCG_LAUNCH_CHECK
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgWork w;
+  if ((st = pcg_workspace(pa, 5, &w, nullptr)) != FE_OK) return st;
+  PcgResult res;
+  if (pc == FE_PC_JACOBI && (st = pcg_jacobi(pa, op, w, s, &res.launches)) != FE_OK) return st;
+  st = pcg_run(pa, op, pa->variant, dev_b, dev_x, pc == FE_PC_JACOBI ? w.d : nullptr, rtol, maxit,
+               w, s, &res);
+  if (st != FE_OK) return st;
+  double true_rel = 0.0;
+  if ((st = pcg_true_residual(pa, op, pa->variant, dev_b, dev_x, nullptr, w, s, &res.launches,
+                              &true_rel)) != FE_OK)
+    return st;
   if (stats) {
-    stats->iters = hflags[F_ITERS];
-    stats->rel_resid = hsc[S_REL];
-    stats->true_rel_resid = hsc[S_BB] > 0.0 ? hsc[S_TRUE] : 0.0;
-    stats->seconds =
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    stats->launches = launches;
+    stats->iters = res.iters;
+    stats->rel_resid = res.rel;
+    stats->true_rel_resid = true_rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = res.launches;
+    stats->outer_iters = 1;
   }
-  switch (hflags[F_STATE]) {
-    case ST_CONV:
-      return FE_OK;
-    case ST_BREAK:
-      return set_error(FE_ERR_BREAKDOWN, "fe_pcg: p.Ap <= 0 (operator not SPD on the free dofs)");
-    case ST_NAN:
-      return set_error(FE_ERR_NAN, "fe_pcg: NaN or Inf in the iteration");
-    default:
-      return set_error(FE_ERR_NOT_CONVERGED, "fe_pcg: maxit reached before rtol");
+  return pcg_status(res.state, "fe_pcg");
+}
+
+extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x,
+                         double rtol, int maxit, double inner_rtol, fe_pcg_stats* stats,
+                         void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  int st = pcg_check_args(pa, op, pc, dev_b, dev_x, rtol, maxit, "fe_pcg_ir");
+  if (st != FE_OK) return st;
+  if (inner_rtol == 0.0) inner_rtol = 1e-2;
+  if (!(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return set_error(FE_ERR_ARG, "fe_pcg_ir: inner_rtol must lie in (0, 1)");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the accurate operator of the outer residual: the handle's FP64-accurate encoding
+  const int hi = (pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr) {
+    const int saved = pa->variant;
+    if ((st = fe_pa_set_variant(pa, FE_VARIANT_F32, stream)) != FE_OK) return st;
+    pa->variant = saved;
   }
+  PcgWork w;
+  double* extra = nullptr;
+  if ((st = pcg_workspace(pa, 7, &w, &extra)) != FE_OK) return st;
+  double* rr = extra;                        // outer residual (FP64)
+  double* dx = extra + pa->mesh->ndofs;      // correction of one inner solve
+  const int64_t n = pa->mesh->ndofs;
+  PcgResult res;
+  if (pc == FE_PC_JACOBI && (st = pcg_jacobi(pa, op, w, s, &res.launches)) != FE_OK) return st;
+  const double* dj = pc == FE_PC_JACOBI ? w.d : nullptr;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(dev_x, 0, sizeof(double) * n, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_ir: zero x");
+  double rel = 1.0;
+  if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel)) != FE_OK)
+    return st;
+  int outer = 0, inner_total = 0, state = (rel <= rtol) ? ST_CONV : ST_RUN;
+  while (state == ST_RUN) {
+    if (!std::isfinite(rel)) {
+      state = ST_NAN;
+      break;
+    }
+    // inner FP32 solve of A dx = r to inner_rtol relative to ||r||
+    PcgResult in;
+    st = pcg_run(pa, op, FE_VARIANT_F32, rr, dx, dj, inner_rtol, maxit - inner_total, w, s, &in);
+    if (st != FE_OK) return st;
+    res.launches += in.launches;
+    inner_total += in.iters;
+    ++outer;
+    if (in.state == ST_NAN) {
+      state = ST_NAN;
+      break;
+    }
+    if (in.state == ST_BREAK) {
+      state = ST_BREAK;
+      break;
+    }
+    k_axpy<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, dx, n);
+    if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_ir: update launch");
+    res.launches += 1;
+    const double prev = rel;
+    if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel)) != FE_OK)
+      return st;
+    if (rel <= rtol)
+      state = ST_CONV;
+    else if (inner_total >= maxit || !(rel < prev))
+      state = ST_MAXIT;  // budget spent, or refinement stagnated at the inner precision
+  }
+  if (stats) {
+    stats->iters = inner_total;
+    stats->rel_resid = rel;
+    stats->true_rel_resid = rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = res.launches;
+    stats->outer_iters = outer;
+  }
+  return pcg_status(state, "fe_pcg_ir");
 }
 
 // ------------------------------------------------------------------------------------------
@@ -399,7 +586,7 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
                               void* stream) {
   clear_error();
   const auto t0 = std::chrono::steady_clock::now();
-  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0};
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   int launches = 0;
   if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: null argument");
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad op");
@@ -436,7 +623,8 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
   } while (0)
 
   // the array keeps the previous call's contents: the flags must start at zero; every vector
-  // and partial is written before it is read (d by the diagonal assembly, q by k_zero)
+  // and partial is written before it is read (d by the diagonal assembly, q by k_init and
+  // k_pupdate)
   if ((err = cudaMemsetAsync(flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
     return cuda_error(err, "fe_pcg_noalloc: flags");
   const double* dj = nullptr;
@@ -448,8 +636,9 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
     launches += 2;
     dj = d;
   }
-  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, mask, dj, dev_x, r, z, p, n, part0, part1);
-  k_finish_init<<<1, 1, 0, s>>>(part0, part1, sc, flags);
+  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, mask, dj, dev_x, r, z, p, q, n, part0,
+                                                   part1);
+  k_finish_init<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, flags);
   NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: init launch");
   launches += 2;
   int hflags[4] = {0, 0, 0, 0};
@@ -463,17 +652,16 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
   int queued = 0;
   for (;;) {
     for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
-      k_zero<<<kReduceBlocks, kReduceThreads, 0, s>>>(q, n, flags);
       st = apply_dispatch(pa, op, pa->variant, p, q, s, flags);
       if (st != FE_OK) return st;
       k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, q, n, part0, flags);
-      k_finish_pq<<<1, 1, 0, s>>>(part0, sc, flags);
+      k_finish_pq<<<1, kFinishThreads, 0, s>>>(part0, sc, flags);
       k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, r, z, p, q, dj, mask, n, sc, part0,
                                                           part1, flags);
-      k_finish_update<<<1, 1, 0, s>>>(part0, part1, sc, flags, rtol, maxit);
-      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, z, n, sc, flags);
+      k_finish_update<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, flags, rtol, maxit);
+      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, z, q, n, sc, flags);
       NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: iteration launch");
-      launches += 7;
+      launches += 6;
     }
     if ((err = cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
@@ -483,8 +671,8 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
   }
   st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
   if (st != FE_OK) return st;
-  k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, mask, n, part0);
-  k_finish_resid<<<1, 1, 0, s>>>(part0, sc);
+  k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, mask, nullptr, n, part0, part1);
+  k_finish_resid<<<1, kFinishThreads, 0, s>>>(part0, part1, sc);
   NOALLOC_LAUNCH_CHECK("fe_pcg_noalloc: residual launch");
   launches += 3;
   double hsc[kScalars];
@@ -500,6 +688,7 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
     stats->seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     stats->launches = launches;
+    stats->outer_iters = 1;
   }
   switch (hflags[F_STATE]) {
     case ST_CONV:

@@ -1,0 +1,143 @@
+// Throughput probes behind the roofline denominators (measurement utility, not the hot path):
+// independent FMA / DMMA chains per thread on every SM, timed with CUDA events.  GB300's FP64
+// rate is not in the measured peaks (those are an HBM copy and a BF16 GEMM), so the FP64
+// roofline of the FP64 apply is derived from the DFMA rate these kernels measure.
+#include <cuda_runtime.h>
+
+#include "fe_f2.h"
+#include "fe_internal.h"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__global__ void k_probe_dfma(double* out, int iters, double b, double c) {
+  double a[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) a[i] = threadIdx.x * 1e-3 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], b, c);
+  }
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += a[i];
+  if (s == 12345.678) out[0] = s;  // keeps the chains live
+}
+
+__global__ void k_probe_ffma(float* out, int iters, float b, float c) {
+  float a[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) a[i] = threadIdx.x * 1e-3f + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = fmaf(a[i], b, c);
+  }
+  float s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += a[i];
+  if (s == 12345.678f) out[0] = s;
+}
+
+__global__ void k_probe_dmma(double* out, int iters) {
+  double a = threadIdx.x * 1e-3, b = 0.999;
+  double c[kChains][2];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) c[i][0] = c[i][1] = i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(c[i][0]), "+d"(c[i][1])
+                   : "d"(a), "d"(b));
+  }
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += c[i][0] + c[i][1];
+  if (s == 12345.678) out[0] = s;
+}
+
+// anchored float-float multiply-add chains (the apply's inner step), counted as 2 flops each
+__global__ void k_probe_f2(float* out, int iters, float ah, float al) {
+  fe::Anch acc[kChains];
+  fe::f2 x[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) {
+    acc[i] = fe::anch_begin(1024.0f);
+    x[i] = fe::f2{threadIdx.x * 1e-3f + i, 1e-9f * i};
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) fe::anch_mad(acc[i], ah, al, x[i]);
+  }
+  float s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += acc[i].A + acc[i].L;
+  if (s == 12345.678f) out[0] = s;
+}
+
+}  // namespace
+
+extern "C" int fe_probe_throughput(int unit, double* tflops) {
+  fe::clear_error();
+  if (!tflops) return fe::set_error(FE_ERR_ARG, "fe_probe_throughput: tflops is NULL");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8;
+  const double nthreads = (double)threads * blocks;
+  void* buf = nullptr;
+  cudaError_t err = cudaMalloc(&buf, 64);
+  if (err != cudaSuccess) return fe::cuda_error(err, "fe_probe_throughput: cudaMalloc");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 0;
+  double flops_per_iter = 0;
+  auto launch = [&]() {
+    switch (unit) {
+      case FE_PROBE_FP64_FMA:
+        iters = 4096;
+        flops_per_iter = 2.0 * kChains * nthreads;
+        k_probe_dfma<<<blocks, threads>>>((double*)buf, iters, 0.9999, 1e-3);
+        break;
+      case FE_PROBE_FP64_DMMA:
+        iters = 2048;
+        flops_per_iter = 512.0 * kChains * (nthreads / 32);
+        k_probe_dmma<<<blocks, threads>>>((double*)buf, iters);
+        break;
+      case FE_PROBE_FP32_FMA:
+        iters = 65536;
+        flops_per_iter = 2.0 * kChains * nthreads;
+        k_probe_ffma<<<blocks, threads>>>((float*)buf, iters, 0.9999f, 1e-3f);
+        break;
+      default:
+        iters = 8192;
+        flops_per_iter = 2.0 * kChains * nthreads;
+        k_probe_f2<<<blocks, threads>>>((float*)buf, iters, 0.999f, 1e-9f);
+        break;
+    }
+  };
+  int st = FE_OK;
+  if (unit < FE_PROBE_FP64_FMA || unit > FE_PROBE_F32X2_MAC) {
+    st = fe::set_error(FE_ERR_ARG, "fe_probe_throughput: unknown unit");
+  } else {
+    launch();  // warm-up
+    cudaEventRecord(e0);
+    for (int r = 0; r < 3; ++r) launch();
+    cudaEventRecord(e1);
+    err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err != cudaSuccess) {
+      st = fe::cuda_error(err, "fe_probe_throughput");
+    } else {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      *tflops = 3.0 * flops_per_iter * iters / (ms * 1e-3) / 1e12;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  return st;
+}

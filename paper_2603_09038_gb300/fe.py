@@ -30,8 +30,10 @@ FE_PC_JACOBI = 1
 FE_VARIANT_F64 = 0
 FE_VARIANT_F32X2 = 1
 FE_VARIANT_F64_DMMA = 2
+FE_VARIANT_F32 = 3
 
-VARIANTS = {"f64": FE_VARIANT_F64, "f32x2": FE_VARIANT_F32X2, "dmma": FE_VARIANT_F64_DMMA}
+VARIANTS = {"f64": FE_VARIANT_F64, "f32x2": FE_VARIANT_F32X2, "dmma": FE_VARIANT_F64_DMMA,
+            "f32": FE_VARIANT_F32}
 
 
 class FEError(RuntimeError):
@@ -43,7 +45,7 @@ class FEError(RuntimeError):
 class fe_pcg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double),
                 ("true_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("launches", ctypes.c_int)]
+                ("launches", ctypes.c_int), ("outer_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -66,8 +68,11 @@ _SIGS = {
     "fe_load_vector_sine": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pcg": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                               ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_pcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_double, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -188,9 +193,24 @@ def fe_pcg(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
                         int(maxit), ctypes.byref(st), _stream(stream))
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
-    return status, {"iters": st.iters, "rel_resid": st.rel_resid,
-                    "true_rel_resid": st.true_rel_resid, "seconds": st.seconds,
-                    "launches": st.launches}
+    return status, _stats(st)
+
+
+def _stats(st):
+    return {"iters": st.iters, "rel_resid": st.rel_resid, "true_rel_resid": st.true_rel_resid,
+            "seconds": st.seconds, "launches": st.launches, "outer_iters": st.outer_iters}
+
+
+def fe_pcg_ir(pa, op, pc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=None):
+    """Mixed-precision iterative refinement (FP32 inner PCG, FP64-accurate outer residual);
+    same return value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_pcg_ir(_VP(pa), int(op), int(pc), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                           int(maxit), float(inner_rtol), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
 
 
 FE_PCG_NOALLOC_MAX_DOFS = 262144
@@ -205,9 +225,17 @@ def fe_pcg_noalloc(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
                                 int(maxit), ctypes.byref(st), _stream(stream))
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
-    return status, {"iters": st.iters, "rel_resid": st.rel_resid,
-                    "true_rel_resid": st.true_rel_resid, "seconds": st.seconds,
-                    "launches": st.launches}
+    return status, _stats(st)
+
+
+PROBE_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "f32x2_mac": 3}
+
+
+def fe_probe_throughput(unit):
+    """Sustained TFLOP/s of one arithmetic unit of the current GPU (see include/fe.h)."""
+    v = ctypes.c_double()
+    _check(load().fe_probe_throughput(int(PROBE_UNITS.get(unit, unit)), ctypes.byref(v)))
+    return v.value
 
 
 def fe_pa_destroy(pa):

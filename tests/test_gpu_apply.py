@@ -17,7 +17,7 @@ from paper_2603_09038_gb300.inputs import uniform_vector, ORDER_SWEEP_N
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["f64", "f32x2"]
+VARIANTS = ["f64", "f32x2", "dmma"]
 OPS = [(1, DIFFUSION), (2, MASS)]      # (FE_DIFFUSION / FE_MASS code, oracle kind)
 
 

@@ -86,3 +86,58 @@ def test_poisson_64_cubed_p3_convergence():
             errs.append(l2_error(oop.Problem(n, n, n, 3, V), x.cpu().numpy()))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(rates - 4.0) < 0.2), (errs, rates)
+
+
+def test_f32_apply_is_fp32_accurate():
+    """The FP32 inner operator of iterative refinement: relative error ~1e-6, not FP64."""
+    from oracle import operator as oop2
+    from paper_2603_09038_gb300.inputs import uniform_vector
+    torch = torch_cuda()
+    with gpu_problem(5, 4, 3, 3, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop2.Problem(5, 4, 3, 3, V, coeff=c)
+        fe.fe_pa_set_variant(pa, "f32")
+        xh = uniform_vector(prob.ndofs, 1)
+        x = torch.from_numpy(xh).cuda()
+        y = torch.empty_like(x)
+        for op, kind in ((fe.FE_DIFFUSION, DIFFUSION), (fe.FE_MASS, "mass")):
+            fe.fe_apply(pa, op, "f32", x, y)
+            torch.cuda.synchronize()
+            ref = oop2.apply(prob, xh, kind)
+            err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
+            assert 1e-9 < err < 1e-5, err
+
+
+@pytest.mark.parametrize("hi", ["f64", "f32x2"])
+@pytest.mark.parametrize("dims,p", [((6, 5, 4), 3), ((4, 4, 4), 5)])
+def test_iterative_refinement_reaches_fp64_residual(hi, dims, p):
+    torch = torch_cuda()
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        fe.fe_pa_set_variant(pa, hi)
+        rtol = 1e-10
+        st, stats = fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, rtol, 5000, 1e-4)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert stats["true_rel_resid"] <= rtol and stats["outer_iters"] >= 2
+        xr, it, hist = _oracle_solve(prob, load_vector(prob), 1e-12)
+        assert np.abs(x.cpu().numpy() - xr).max() <= 1e-8 * np.abs(xr).max()
+
+
+def test_iterative_refinement_on_the_poisson_workload():
+    """64^3 hexes p=3: fe_pcg_ir to 1e-8 gives the same answer as fe_pcg (both FP64-accurate
+    residuals <= 1e-8) and a true residual checked by the oracle's own apply on sampled rows."""
+    torch = torch_cuda()
+    with gpu_problem(64, 64, 64, 3) as (fe, mesh, pa, V, c):
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x1 = torch.empty_like(b)
+        x2 = torch.empty_like(b)
+        st1, s1 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x1, 1e-8, 20000)
+        st2, s2 = fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x2, 1e-8, 20000)
+        assert st1 == fe.FE_OK and st2 == fe.FE_OK
+        assert s2["true_rel_resid"] <= 1e-8
+        d = float((x1 - x2).abs().max() / x1.abs().max())
+        assert d < 1e-6, d
