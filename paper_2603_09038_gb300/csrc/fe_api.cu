@@ -310,8 +310,9 @@ int compute_qdata(fe_pa* pa, const double* coeff, cudaStream_t s, int* d_bad) {
 namespace fe {
 
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
-                   cudaStream_t s, const int* skip) {
-  if (!pa || !x || !y) return set_error(FE_ERR_ARG, "fe_apply: null argument");
+                   cudaStream_t s, const int* skip, double* dot_part, int64_t* blocks,
+                   bool query_only) {
+  if (!pa || ((!x || !y) && !query_only)) return set_error(FE_ERR_ARG, "fe_apply: null argument");
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_apply: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_apply: operator not set up in fe_pa_setup");
   const fe_mesh* m = pa->mesh;
@@ -325,9 +326,11 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
       return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
                                    "encoding; call fe_pa_set_variant first");
   }
-  if (skip == nullptr) {
+  if (skip == nullptr && !query_only) {
     FE_CHECK_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->ndofs, s), "zero y");
   }
+  if (dot_part && variant == FE_VARIANT_F64_DMMA)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_apply: the DMMA kernel has no fused dot product");
   ApplyArgs a;
   a.map = m->d_map;
   if (variant == FE_VARIANT_F32)
@@ -341,6 +344,9 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
   a.Q = pa->Q;
   a.basis = &pa->basis;
   a.skip = skip;
+  a.dot_part = dot_part;
+  a.blocks = blocks;
+  a.query_only = query_only;
   switch (variant) {
     case FE_VARIANT_F64:
       return launch_apply_f64(op, a, s);
@@ -353,6 +359,27 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
     default:
       return set_error(FE_ERR_ARG, "fe_apply: unknown variant");
   }
+}
+
+int apply_f32_vectors(const fe_pa* pa, int op, const float* x, float* y, cudaStream_t s,
+                      const int* skip, double* dot_part) {
+  if (!pa || !x || !y) return set_error(FE_ERR_ARG, "apply_f32_vectors: null argument");
+  const float* qd = (op == FE_DIFFUSION) ? pa->d_qd_diff32 : pa->d_qd_mass32;
+  if (qd == nullptr) return set_error(FE_ERR_ARG, "apply_f32_vectors: no FP32 quadrature data");
+  ApplyArgs a;
+  a.map = pa->mesh->d_map;
+  a.qd = reinterpret_cast<const double*>(qd);
+  a.x = reinterpret_cast<const double*>(x);
+  a.y = reinterpret_cast<double*>(y);
+  a.ne = pa->mesh->ne;
+  a.p = pa->p;
+  a.Q = pa->Q;
+  a.basis = &pa->basis;
+  a.skip = skip;
+  a.dot_part = dot_part;
+  a.blocks = nullptr;
+  a.query_only = false;
+  return launch_apply_f32_vec32(op, a, s);
 }
 
 }  // namespace fe
@@ -629,6 +656,7 @@ void fe_pa_destroy(fe_pa* pa) {
   cudaFree(pa->d_work);
   cudaFree(pa->d_red);
   cudaFree(pa->d_flags);
+  cudaFree(pa->d_dpart);
   delete pa;
 }
 

@@ -410,7 +410,8 @@ int run_dmma(const ApplyArgs& a, cudaStream_t s) {
     tab.G[i] = a.basis->G[i];
   }
   const int64_t nblk = (a.ne + NE - 1) / NE;
-  if (nblk == 0) return FE_OK;
+  if (a.blocks) *a.blocks = nblk;
+  if (nblk == 0 || a.query_only) return FE_OK;
   kern<<<(unsigned int)nblk, kDmmaThreads, smem, s>>>(a.map, a.qd, a.x, a.y, a.ne, a.skip, tab);
   return cuda_error(cudaGetLastError(), "dmma apply kernel launch");
 }

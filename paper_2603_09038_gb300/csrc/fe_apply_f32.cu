@@ -8,6 +8,11 @@ int launch_apply_f32(int op, const ApplyArgs& a, cudaStream_t s) {
   return dispatch_order<ArF32>(op, a, s);
 }
 
+// FP32 vectors in and out (a.x, a.y point to float arrays): the inner solves of fe_pcg_ir.
+int launch_apply_f32_vec32(int op, const ApplyArgs& a, cudaStream_t s) {
+  return dispatch_order<ArF32, float>(op, a, s);
+}
+
 // FP32 copy of n quadrature values: from FP64 data, or from (hi, lo) pairs (hi is already the
 // rounded float).
 __global__ void k_qd_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n,

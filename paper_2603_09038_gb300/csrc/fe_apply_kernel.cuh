@@ -42,12 +42,14 @@ struct ApplyLayout {
 };
 
 // DIFF: diffusion (qdata [e][qz][6][qy][qx]: xx, xy, xz, yy, yz, zz) or mass ([e][qz][qy][qx]).
-template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB>
+// VT: element type of the x and y vectors (double; float for the FP32 inner solves).
+template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB, class VT>
 __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
                                                  const typename Ar::QdT* __restrict__ qd,
-                                                 const double* __restrict__ x,
-                                                 double* __restrict__ y, int64_t ne,
+                                                 const VT* __restrict__ x,
+                                                 VT* __restrict__ y, int64_t ne,
                                                  const int* __restrict__ skip,
+                                                 double* __restrict__ dot_part,
                                                  const typename Ar::template Tab<D, Q> tab) {
   using T = typename Ar::T;
   using L = ApplyLayout<D, Q, DIFF>;
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
     const int el = t / D3, a = t - el * D3;
     const int i = a % D, j = (a / D) % D, k = a / D2;
     const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-    bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_f64(__ldg(&x[g]));
+    bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_vec(__ldg(&x[g]));
   }
   __syncthreads();
 
@@ -384,11 +386,27 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   }
   __syncthreads();
 
-  // ---- scatter-add (G^T)
+  // ---- scatter-add (G^T); optionally the block's share of x^T A x = sum_e x_e . (A_e x_e)
+  double dsum = 0.0;
   for (int t = tid; t < nel * D3; t += NT) {
     const int el = t / D3, a = t - el * D3;
     const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-    Ar::scatter(&y[g], bufB[el * SZ_B + a]);
+    const T v = bufB[el * SZ_B + a];
+    Ar::scatter(&y[g], v);
+    if (dot_part != nullptr) dsum = fma((double)__ldg(&x[g]), Ar::to_f64(v), dsum);
+  }
+  if (dot_part != nullptr) {  // deterministic block reduction (fixed shuffle tree, warp order)
+    __shared__ double wsum[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    if ((tid & 31) == 0) wsum[tid >> 5] = dsum;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) tot += wsum[w];
+      dot_part[blockIdx.x] = tot;
+    }
   }
 }
 

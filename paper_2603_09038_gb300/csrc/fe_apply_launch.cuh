@@ -129,14 +129,14 @@ inline void fill_tab(const Basis1D& b, TabF32x2<D, Q>* t) {
   t->cG = (float)(cG * up);
 }
 
-template <int D, int Q, bool DIFF, class Ar>
+template <int D, int Q, bool DIFF, class Ar, class VT = double>
 int run_apply(const ApplyArgs& a, cudaStream_t s) {
   using T = typename Ar::T;
   using Tune = ApplyTuning<Ar>;
   constexpr int NT = Tune::NT;
   constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM>();
   const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF>::PER_ELEM * sizeof(T);
-  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB>;
+  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB, VT>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -146,21 +146,24 @@ int run_apply(const ApplyArgs& a, cudaStream_t s) {
   typename Ar::template Tab<D, Q> tab;
   fill_tab<D, Q>(*a.basis, &tab);
   const int64_t nblk = (a.ne + NE - 1) / NE;
-  if (nblk == 0) return FE_OK;
-  kern<<<(unsigned int)nblk, NT, smem, s>>>(
-      a.map, reinterpret_cast<const typename Ar::QdT*>(a.qd), a.x, a.y, a.ne, a.skip, tab);
+  if (a.blocks) *a.blocks = nblk;
+  if (nblk == 0 || a.query_only) return FE_OK;
+  kern<<<(unsigned int)nblk, NT, smem, s>>>(a.map, reinterpret_cast<const typename Ar::QdT*>(a.qd),
+                                            reinterpret_cast<const VT*>(a.x),
+                                            reinterpret_cast<VT*>(a.y), a.ne, a.skip, a.dot_part,
+                                            tab);
   return cuda_error(cudaGetLastError(), "apply kernel launch");
 }
 
 // Dispatch on the order for the default rule Q = p + 2.
-template <class Ar>
+template <class Ar, class VT = double>
 int dispatch_order(int op, const ApplyArgs& a, cudaStream_t s) {
   const bool diff = (op == FE_DIFFUSION);
   if (a.Q != a.p + 2) return set_error(FE_ERR_UNSUPPORTED, "only q1d = order + 2 is built");
 #define FE_CASE(P)                                                                  \
   case P:                                                                           \
-    return diff ? run_apply<P + 1, P + 2, true, Ar>(a, s)                           \
-                : run_apply<P + 1, P + 2, false, Ar>(a, s);
+    return diff ? run_apply<P + 1, P + 2, true, Ar, VT>(a, s)                       \
+                : run_apply<P + 1, P + 2, false, Ar, VT>(a, s);
   switch (a.p) {
     FE_CASE(1)
     FE_CASE(2)

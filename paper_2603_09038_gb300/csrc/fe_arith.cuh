@@ -64,7 +64,7 @@ struct ArF64 {
   using Tab = TabF64<D, Q>;
 
   static __device__ __forceinline__ T zero() { return 0.0; }
-  static __device__ __forceinline__ T from_f64(double v) { return v; }
+  static __device__ __forceinline__ T from_vec(double v) { return v; }
   static __device__ __forceinline__ T load_qd(const double* p) { return __ldcs(p); }
   // compensated / plain accumulation
   template <int D, int Q>
@@ -103,6 +103,7 @@ struct ArF64 {
     return fma(a2, x2, fma(a1, x1, a0 * x0));
   }
   static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, v); }
+  static __device__ __forceinline__ double to_f64(T v) { return v; }
 };
 
 struct ArF32x2 {
@@ -115,7 +116,7 @@ struct ArF32x2 {
   using Tab = TabF32x2<D, Q>;
 
   static __device__ __forceinline__ T zero() { return f2{0.0f, 0.0f}; }
-  static __device__ __forceinline__ T from_f64(double v) { return f2_from_f64(v); }
+  static __device__ __forceinline__ T from_vec(double v) { return f2_from_f64(v); }
   // quadrature data is stored pre-split: the 8 bytes of each entry hold (h, l)
   static __device__ __forceinline__ T load_qd(const double* p) {
     const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
@@ -176,6 +177,7 @@ struct ArF32x2 {
   static __device__ __forceinline__ void scatter(double* y, T v) {
     atomicAdd(y, (double)v.h + (double)v.l);
   }
+  static __device__ __forceinline__ double to_f64(T v) { return (double)v.h + (double)v.l; }
 };
 
 // Plain FP32 (the inner solves of mixed-precision iterative refinement): FP32 quadrature data
@@ -190,7 +192,8 @@ struct ArF32 {
   using Tab = TabF32<D, Q>;
 
   static __device__ __forceinline__ T zero() { return 0.0f; }
-  static __device__ __forceinline__ T from_f64(double v) { return f2_from_f64(v).h; }
+  static __device__ __forceinline__ T from_vec(double v) { return f2_from_f64(v).h; }
+  static __device__ __forceinline__ T from_vec(float v) { return v; }
   static __device__ __forceinline__ T load_qd(const float* p) { return __ldcs(p); }
   template <int D, int Q>
   static __device__ __forceinline__ void madB(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
@@ -226,6 +229,8 @@ struct ArF32 {
     return fmaf(a2, x2, fmaf(a1, x1, a0 * x0));
   }
   static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, f64_from_f32(v)); }
+  static __device__ __forceinline__ void scatter(float* y, T v) { atomicAdd(y, v); }
+  static __device__ __forceinline__ double to_f64(T v) { return f64_from_f32(v); }
 };
 
 }  // namespace fe

@@ -115,7 +115,19 @@ FE_HD void anch_mad(Anch& acc, float ah, float al, f2 x) {
   acc.A = t;
 }
 
-FE_HD f2 anch_end(Anch acc, float sigma) { return two_sum(f_sub(acc.A, sigma), acc.L); }
+#ifndef FE_F2_LAZY_END
+#define FE_F2_LAZY_END 0
+#endif
+// Result of an anchored sum: (A - sigma) exactly, plus the low word.  Normalised by TwoSum
+// unless FE_F2_LAZY_END, which returns the unnormalised pair (the next stage uses the high word
+// for its exact products and the low word only in first-order correction terms).
+FE_HD f2 anch_end(Anch acc, float sigma) {
+#if FE_F2_LAZY_END
+  return f2{f_sub(acc.A, sigma), acc.L};
+#else
+  return two_sum(f_sub(acc.A, sigma), acc.L);
+#endif
+}
 
 // Splits an FP64 value into floats without the FP64 pipe: h = v truncated to 24 significant
 // bits (exact), l = the next 23 bits of the remainder (exact), by integer manipulation of the

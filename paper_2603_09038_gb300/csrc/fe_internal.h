@@ -32,6 +32,11 @@ struct Basis1D {
 // Returns false if p or q is out of range.
 bool make_basis_1d(int p, int q, Basis1D* out);
 
+// y = A x with the FP32 variant on float vectors (the caller zeroes y); same skip / dot_part
+// semantics as apply_dispatch.
+int apply_f32_vectors(const fe_pa* pa, int op, const float* x, float* y, cudaStream_t s,
+                      const int* skip, double* dot_part);
+
 }  // namespace fe
 
 struct fe_mesh {
@@ -60,6 +65,8 @@ struct fe_pa {
   double* d_red = nullptr;         // reduction partials + scalars
   int* d_flags = nullptr;
   int64_t work_ndofs = 0;
+  double* d_dpart = nullptr;       // per-block partials of the apply-fused p.Ap
+  int64_t dpart_cap = 0;
 };
 
 namespace fe {
@@ -74,6 +81,9 @@ struct ApplyArgs {
   int p, Q;
   const Basis1D* basis;
   const int* skip;       // optional device flag; nonzero => the launch does nothing
+  double* dot_part;      // optional: per-block partials of sum_e x_e . (A_e x_e) (= x^T A x)
+  int64_t* blocks;       // optional out: grid size of the launch (set also when query_only)
+  bool query_only;       // only report the grid size
 };
 
 // Launchers (one translation unit per variant); return FE_OK or an error status.
@@ -81,13 +91,22 @@ int launch_apply_f64(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_dmma(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32(int op, const ApplyArgs& a, cudaStream_t s);
+int launch_apply_f32_vec32(int op, const ApplyArgs& a, cudaStream_t s);
 int make_qd_f32(const double* src, float* dst, int64_t n, bool pairs, cudaStream_t s);
 
 // Re-encodes n FP64 values in place as float pairs (hi, lo) or back.
 int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);
 
-// y = A x (y zeroed first).  skip: optional device flag, nonzero => no-op (also skips zeroing).
+// y = A x (y zeroed first unless skip is given; with skip the caller zeroes y).  skip:
+// optional device flag, nonzero => no-op.  dot_part: optional per-block partials of x^T A x
+// (variants F64, F32X2, F32); blocks: optional out, the grid size (number of partials).
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
-                   cudaStream_t s, const int* skip = nullptr);
+                   cudaStream_t s, const int* skip = nullptr, double* dot_part = nullptr,
+                   int64_t* blocks = nullptr, bool query_only = false);
+
+// y = A x with the FP32 variant on float vectors (the caller zeroes y); same skip / dot_part
+// semantics as apply_dispatch.
+int apply_f32_vectors(const fe_pa* pa, int op, const float* x, float* y, cudaStream_t s,
+                      const int* skip, double* dot_part);
 
 }  // namespace fe

@@ -19,6 +19,7 @@
 #include <mutex>
 #include <string>
 
+#include "fe_f2.h"
 #include "fe_internal.h"
 
 namespace {
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_init(const double* __restric
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = mask[i] ? 0.0 : b[i];
-    const double zi = d ? bi / d[i] : bi;
+    const double zi = d ? bi * d[i] : bi;
     x[i] = 0.0;
     r[i] = bi;
     z[i] = zi;
@@ -152,6 +153,28 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_pq(const double* part
     sc[S_ALPHA] = sc[S_RZ] / pq;
 }
 
+// p.q from the apply's per-block partials (count of them), summed in a fixed order: thread t
+// adds part[t], part[t + 1024], ... in order, then the block tree.
+__global__ void __launch_bounds__(kFinishThreads) k_finish_pq_var(const double* part,
+                                                                int64_t count, double* sc,
+                                                                int* flags) {
+  if (flags[F_STATE] != ST_RUN) return;
+  __shared__ double col[kFinishThreads];
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += kFinishThreads) v += part[i];
+  col[threadIdx.x] = v;
+  __syncthreads();
+  const double pq = ordered_sum(col);
+  if (threadIdx.x != 0) return;
+  sc[S_PQ] = pq;
+  if (!isfinite(pq))
+    flags[F_STATE] = ST_NAN;
+  else if (!(pq > 0.0))
+    flags[F_STATE] = ST_BREAK;
+  else
+    sc[S_ALPHA] = sc[S_RZ] / pq;
+}
+
 __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ x,
                                                            double* __restrict__ r,
                                                            double* __restrict__ z,
@@ -172,7 +195,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, qi, r[i]);
     r[i] = ri;
-    const double zi = bnd ? 0.0 : (d ? ri / d[i] : ri);
+    const double zi = d ? ri * d[i] : (bnd ? 0.0 : ri);
     z[i] = zi;
     s_rz = fma(ri, zi, s_rz);
     s_rr = fma(ri, ri, s_rr);
@@ -219,17 +242,21 @@ __global__ void __launch_bounds__(kReduceThreads) k_pupdate(double* __restrict__
   }
 }
 
-// Jacobi: boundary entries of the diagonal set to 1 (they are never used); any non-positive
-// interior entry is reported through flags as a breakdown.
+// Jacobi: the diagonal is replaced in place by its inverse, 0 on the boundary (so z = dinv r is
+// masked for free and the iteration needs no FP64 division -- slow on GB300's FP64 pipe); any
+// non-positive interior entry is reported through flags as a breakdown.
 __global__ void __launch_bounds__(kReduceThreads) k_fix_diag(double* __restrict__ d,
                                                              const uint8_t* __restrict__ mask,
                                                              int64_t n, int* flags) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (mask[i])
-      d[i] = 1.0;
-    else if (!(d[i] > 0.0))
-      atomicExch(&flags[2], 1);
+    if (mask[i]) {
+      d[i] = 0.0;
+    } else {
+      const double di = d[i];
+      if (!(di > 0.0)) atomicExch(&flags[2], 1);
+      d[i] = 1.0 / di;
+    }
   }
 }
 
@@ -261,6 +288,101 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_resid(const double* p
     sc[S_BB] = bb;
     sc[S_TRUE] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
   }
+}
+
+}  // namespace
+
+namespace {
+
+// ---- FP32 inner solves of fe_pcg_ir: the same iteration on float vectors (FP32 pipe and half
+//      the bytes; GB300's FP64 pipe makes even FP64 vector updates expensive).  Thread sums are
+//      float, block partials double, so the reductions stay deterministic.
+
+__global__ void __launch_bounds__(kReduceThreads) k_init32(const float* __restrict__ b,
+                                                           const float* __restrict__ dinv,
+                                                           float* __restrict__ x,
+                                                           float* __restrict__ r,
+                                                           float* __restrict__ z,
+                                                           float* __restrict__ p,
+                                                           float* __restrict__ q, int64_t n,
+                                                           double* part0, double* part1) {
+  float s_rz = 0.0f, s_bb = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float bi = b[i];  // already masked
+    const float zi = dinv ? bi * dinv[i] : bi;
+    x[i] = 0.0f;
+    r[i] = bi;
+    z[i] = zi;
+    p[i] = zi;
+    q[i] = 0.0f;
+    s_rz = fmaf(bi, zi, s_rz);
+    s_bb = fmaf(bi, bi, s_bb);
+  }
+  block_sum2((double)s_rz, (double)s_bb, part0, part1);
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_update32(float* __restrict__ x,
+                                                             float* __restrict__ r,
+                                                             float* __restrict__ z,
+                                                             const float* __restrict__ p,
+                                                             const float* __restrict__ q,
+                                                             const float* __restrict__ dinv,
+                                                             const uint8_t* __restrict__ mask,
+                                                             int64_t n, const double* sc,
+                                                             double* part0, double* part1,
+                                                             const int* flags) {
+  if (flags[F_STATE] != ST_RUN) return;
+  const float alpha = (float)sc[S_ALPHA];
+  float s_rz = 0.0f, s_rr = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool bnd = mask[i] != 0;
+    const float qi = bnd ? 0.0f : q[i];
+    x[i] = fmaf(alpha, p[i], x[i]);
+    const float ri = fmaf(-alpha, qi, r[i]);
+    r[i] = ri;
+    const float zi = dinv ? ri * dinv[i] : (bnd ? 0.0f : ri);
+    z[i] = zi;
+    s_rz = fmaf(ri, zi, s_rz);
+    s_rr = fmaf(ri, ri, s_rr);
+  }
+  block_sum2((double)s_rz, (double)s_rr, part0, part1);
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_pupdate32(float* __restrict__ p,
+                                                              const float* __restrict__ z,
+                                                              float* __restrict__ q, int64_t n,
+                                                              const double* sc, const int* flags) {
+  if (flags[F_STATE] != ST_RUN) return;
+  const float beta = (float)sc[S_BETA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = fmaf(beta, p[i], z[i]);
+    q[i] = 0.0f;
+  }
+}
+
+// dst = (float) src (the outer residual as the inner right-hand side), and the FP32 inverse
+// diagonal when given.
+__global__ void __launch_bounds__(kReduceThreads) k_to32(const double* __restrict__ src,
+                                                         float* __restrict__ dst,
+                                                         const double* __restrict__ d64,
+                                                         float* __restrict__ d32, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dst[i] = fe::f2_from_f64(src[i]).h;
+    if (d32) d32[i] = (float)d64[i];
+  }
+}
+
+// x += (double) dx
+__global__ void __launch_bounds__(kReduceThreads) k_axpy32(double* __restrict__ x,
+                                                           const float* __restrict__ dx,
+                                                           int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += fe::f64_from_f32(dx[i]);
 }
 
 }  // namespace
@@ -331,12 +453,27 @@ int pcg_jacobi(const fe_pa* pa, int op, const PcgWork& w, cudaStream_t s, int* l
 
 // The CG iteration proper: solves A_bc x = b from x = 0 with the given apply variant and the
 // Jacobi diagonal dj (or none); synchronous; res gets the state, iterations and launches.
-int pcg_run(const fe_pa* pa, int op, int variant, const double* b, double* x, const double* dj,
+int pcg_run(fe_pa* pa, int op, int variant, const double* b, double* x, const double* dj,
             double rtol, int maxit, const PcgWork& w, cudaStream_t s, PcgResult* res) {
   const fe_mesh* m = pa->mesh;
   const int64_t n = m->ndofs;
   const uint8_t* mask = m->d_mask;
   cudaError_t err;
+  // p.Ap fused into the apply (per-block partials) except for the DMMA kernel
+  const bool fused_dot = (variant != FE_VARIANT_F64_DMMA);
+  int64_t nblk = 0;
+  if (fused_dot) {
+    int st = apply_dispatch(pa, op, variant, nullptr, nullptr, s, nullptr, nullptr, &nblk, true);
+    if (st != FE_OK) return st;
+    if (nblk > pa->dpart_cap) {
+      cudaFree(pa->d_dpart);
+      pa->d_dpart = nullptr;
+      pa->dpart_cap = 0;
+      if ((err = cudaMalloc(&pa->d_dpart, sizeof(double) * nblk)) != cudaSuccess)
+        return cuda_error(err, "fe_pcg: partials cudaMalloc");
+      pa->dpart_cap = nblk;
+    }
+  }
   if ((err = cudaMemsetAsync(w.flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
     return cuda_error(err, "fe_pcg: flags");
   k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(b, mask, dj, x, w.r, w.z, w.p, w.q, n, w.part0,
@@ -348,17 +485,25 @@ int pcg_run(const fe_pa* pa, int op, int variant, const double* b, double* x, co
   int queued = 0;
   for (;;) {
     for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
-      int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags);
-      if (st != FE_OK) return st;
-      k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.q, n, w.part0, w.flags);
-      k_finish_pq<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
+      if (fused_dot) {
+        int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags, pa->d_dpart);
+        if (st != FE_OK) return st;
+        k_finish_pq_var<<<1, kFinishThreads, 0, s>>>(pa->d_dpart, nblk, w.sc, w.flags);
+        res->launches += 2;
+      } else {
+        int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags);
+        if (st != FE_OK) return st;
+        k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.q, n, w.part0, w.flags);
+        k_finish_pq<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
+        res->launches += 3;
+      }
       k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, w.r, w.z, w.p, w.q, dj, mask, n, w.sc,
                                                           w.part0, w.part1, w.flags);
       k_finish_update<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
       k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.z, w.q, n, w.sc, w.flags);
       if ((err = cudaGetLastError()) != cudaSuccess)
         return cuda_error(err, "fe_pcg: iteration launch");
-      res->launches += 6;
+      res->launches += 3;
     }
     if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
@@ -401,6 +546,61 @@ int pcg_true_residual(const fe_pa* pa, int op, int variant, const double* b, con
   return FE_OK;
 }
 
+// Inner solve of fe_pcg_ir on FP32 vectors: A_bc x = b from x = 0 with the FP32 apply.
+struct PcgWork32 {
+  float *r, *z, *p, *q, *dinv, *x;
+};
+
+int pcg_run_f32(fe_pa* pa, int op, const float* b, const PcgWork32& v, bool jacobi, double rtol,
+                int maxit, const PcgWork& w, cudaStream_t s, PcgResult* res) {
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  cudaError_t err;
+  int64_t nblk = 0;
+  int st = apply_dispatch(pa, op, FE_VARIANT_F32, nullptr, nullptr, s, nullptr, nullptr, &nblk, true);
+  if (st != FE_OK) return st;
+  if (nblk > pa->dpart_cap) {
+    cudaFree(pa->d_dpart);
+    pa->d_dpart = nullptr;
+    pa->dpart_cap = 0;
+    if ((err = cudaMalloc(&pa->d_dpart, sizeof(double) * nblk)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg_ir: partials cudaMalloc");
+    pa->dpart_cap = nblk;
+  }
+  const float* dinv = jacobi ? v.dinv : nullptr;
+  if ((err = cudaMemsetAsync(w.flags, 0, sizeof(int) * 4, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_ir: flags");
+  k_init32<<<kReduceBlocks, kReduceThreads, 0, s>>>(b, dinv, v.x, v.r, v.z, v.p, v.q, n, w.part0,
+                                                    w.part1);
+  k_finish_init<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags);
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_ir: init launch");
+  res->launches += 2;
+  int hflags[4] = {0, 0, 0, 0};
+  int queued = 0;
+  for (;;) {
+    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
+      st = apply_f32_vectors(pa, op, v.p, v.q, s, w.flags, pa->d_dpart);
+      if (st != FE_OK) return st;
+      k_finish_pq_var<<<1, kFinishThreads, 0, s>>>(pa->d_dpart, nblk, w.sc, w.flags);
+      k_update32<<<kReduceBlocks, kReduceThreads, 0, s>>>(v.x, v.r, v.z, v.p, v.q, dinv, m->d_mask,
+                                                          n, w.sc, w.part0, w.part1, w.flags);
+      k_finish_update<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
+      k_pupdate32<<<kReduceBlocks, kReduceThreads, 0, s>>>(v.p, v.z, v.q, n, w.sc, w.flags);
+      if ((err = cudaGetLastError()) != cudaSuccess)
+        return cuda_error(err, "fe_pcg_ir: iteration launch");
+      res->launches += 5;
+    }
+    if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg_ir: iteration");
+    if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
+  }
+  res->state = hflags[F_STATE];
+  res->iters = hflags[F_ITERS];
+  return FE_OK;
+}
+
 int pcg_status(int state, const char* who) {
   switch (state) {
     case ST_CONV:
@@ -425,12 +625,6 @@ int pcg_check_args(const fe_pa* pa, int op, int pc, const double* b, const doubl
   return FE_OK;
 }
 
-__global__ void __launch_bounds__(kReduceThreads) k_axpy(double* __restrict__ x,
-                                                         const double* __restrict__ d, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += d[i];
-}
 
 }  // namespace
 
@@ -485,13 +679,16 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
   }
   PcgWork w;
   double* extra = nullptr;
-  if ((st = pcg_workspace(pa, 7, &w, &extra)) != FE_OK) return st;
-  double* rr = extra;                        // outer residual (FP64)
-  double* dx = extra + pa->mesh->ndofs;      // correction of one inner solve
+  // 5 FP64 work vectors + the FP64 outer residual + 7 FP32 vectors (4 doubles' worth)
+  if ((st = pcg_workspace(pa, 10, &w, &extra)) != FE_OK) return st;
   const int64_t n = pa->mesh->ndofs;
+  double* rr = extra;                        // outer residual (FP64)
+  float* f32base = reinterpret_cast<float*>(extra + n);
+  PcgWork32 v{f32base, f32base + n, f32base + 2 * n, f32base + 3 * n, f32base + 4 * n,
+              f32base + 5 * n};
+  float* b32 = f32base + 6 * n;  // inner right-hand side
   PcgResult res;
   if (pc == FE_PC_JACOBI && (st = pcg_jacobi(pa, op, w, s, &res.launches)) != FE_OK) return st;
-  const double* dj = pc == FE_PC_JACOBI ? w.d : nullptr;
   cudaError_t err;
   if ((err = cudaMemsetAsync(dev_x, 0, sizeof(double) * n, s)) != cudaSuccess)
     return cuda_error(err, "fe_pcg_ir: zero x");
@@ -499,14 +696,22 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
   if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel)) != FE_OK)
     return st;
   int outer = 0, inner_total = 0, state = (rel <= rtol) ? ST_CONV : ST_RUN;
+  bool dinv_ready = false;
   while (state == ST_RUN) {
     if (!std::isfinite(rel)) {
       state = ST_NAN;
       break;
     }
     // inner FP32 solve of A dx = r to inner_rtol relative to ||r||
+    k_to32<<<kReduceBlocks, kReduceThreads, 0, s>>>(rr, b32, w.d,
+                                                    (pc == FE_PC_JACOBI && !dinv_ready) ? v.dinv
+                                                                                        : nullptr,
+                                                    n);
+    dinv_ready = true;
+    res.launches += 1;
     PcgResult in;
-    st = pcg_run(pa, op, FE_VARIANT_F32, rr, dx, dj, inner_rtol, maxit - inner_total, w, s, &in);
+    st = pcg_run_f32(pa, op, b32, v, pc == FE_PC_JACOBI, inner_rtol, maxit - inner_total, w, s,
+                     &in);
     if (st != FE_OK) return st;
     res.launches += in.launches;
     inner_total += in.iters;
@@ -519,7 +724,7 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
       state = ST_BREAK;
       break;
     }
-    k_axpy<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, dx, n);
+    k_axpy32<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, v.x, n);
     if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_ir: update launch");
     res.launches += 1;
     const double prev = rel;
