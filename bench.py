@@ -35,6 +35,11 @@ MAXIT = 20000
 METRIC = "GDOF/s of FP64 PA diffusion apply (frac of HBM roofline); PCG time-to-1e-8 residual"
 UNIT = "GDOF/s"
 FP64_DFMA_PER_CLK_PER_SM = 2           # measured on GB300 (FP64 peak)
+# DRAM bytes (read + write) of one apply launch from an ncu capture of the same kernel on the
+# 32^3 p=3 mesh, with that launch's algorithmic bytes: scaled to the benchmark's launch by the
+# algorithmic bytes (traffic grows with the elements).  Only for kernels unchanged since.
+NCU_TRAFFIC = {("f32x2", 3): (219.799808e6 + 4.077312e6, 219599376,
+                              "profiles/k_pa_apply_f32x2_p3_poisson32.md")}
 
 
 def measured_peaks():
@@ -346,6 +351,11 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz / 6 instructions per "
                                "anchored float-float multiply-add x 2 flop (FP64-equivalent)"
                                % sm_max, "hbm": hbm_obj}
+    key = (args.variant, p)
+    if key in NCU_TRAFFIC:
+        meas, algo, src = NCU_TRAFFIC[key]
+        roof["traffic"] = meas * nbytes / algo
+        roof["traffic_source"] = "ncu dram bytes of the 32^3 launch scaled by algorithmic bytes (%s)" % src
     roof["fp64_fma_probe_tflops"] = fe.fe_probe_throughput("fp64_fma")
     roof["bytes_per_launch"] = nbytes
     roof["flops_per_launch"] = flops
@@ -429,6 +439,47 @@ def run_sweep(args, local_rank):
     return 0
 
 
+def run_batched(args, local_rank):
+    """Batched apply on the 64^3 p=3 mesh: per-right-hand-side GDOF/s of one launch over nrhs
+    right-hand sides against single applies, per variant (one JSON line each)."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    fe.load()
+    n, p = args.n, args.p
+    mesh = fe.fe_mesh_setup(n, n, n, p, perturbed_vertices(n, n, n))
+    pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+    nd, ne, _ = fe.fe_mesh_sizes(mesh)
+    stream = torch.cuda.current_stream()
+    nr = args.batched
+    X = torch.rand(nr, nd, dtype=torch.float64, device=dev) * 2 - 1
+    Y = torch.empty_like(X)
+    for variant in ("f32x2", "f32", "f64"):
+        fe.fe_pa_set_variant(pa, variant)
+        res = {}
+        for k in (1, nr):
+            for _ in range(2):
+                fe.fe_apply_batched(pa, fe.FE_DIFFUSION, variant, k, X, nd, Y, nd, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(5)]
+            torch.cuda.synchronize()
+            for a, z in ev:
+                a.record(stream)
+                fe.fe_apply_batched(pa, fe.FE_DIFFUSION, variant, k, X, nd, Y, nd, stream)
+                z.record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(z) for a, z in ev)
+            res[k] = k * nd / ms / 1e6
+        print(json.dumps({"batched": True, "workload": "poisson_%dcubed_p%d" % (n, p),
+                          "variant": variant, "nrhs": nr, "gdofs_single": res[1],
+                          "gdofs_per_rhs_batched": res[nr], "speedup": res[nr] / res[1]}))
+    fe.fe_pa_destroy(pa)
+    fe.fe_mesh_destroy(mesh)
+    return 0
+
+
 def run_peaks(local_rank):
     """Throughput probes (libfe fe_probe_throughput) behind the FP64 roofline: one JSON line."""
     import torch
@@ -462,6 +513,7 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32 throughput probes")
+    ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -475,6 +527,8 @@ def main():
         return run_sweep(args, local_rank)
     if args.peaks:
         return run_peaks(local_rank)
+    if args.batched:
+        return run_batched(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

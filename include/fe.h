@@ -119,6 +119,14 @@ int fe_apply_mass(const fe_pa* pa, const double* dev_x, double* dev_y, void* str
 int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* dev_y,
              void* stream);
 
+/* Batched apply (SURVEY "next" item: many right-hand sides per launch): y_r = A x_r for
+ * r < nrhs, x_r = dev_x + r*ldx, y_r = dev_y + r*ldy (leading dimensions in elements, >= ndofs).
+ * One launch; every thread block applies all right-hand sides to its elements one after the
+ * other, so after the first one its dof map and quadrature data are read from L2 instead of
+ * HBM.  Variants F64, F32X2 and F32 (not DMMA).  y is zeroed first.  Asynchronous. */
+int fe_apply_batched(const fe_pa* pa, int op, int variant, int nrhs, const double* dev_x,
+                     int64_t ldx, double* dev_y, int64_t ldy, void* stream);
+
 /* diag(A) (no boundary conditions) by a sum-factorised diagonal kernel in FP64 (with
  * FE_VARIANT_F32X2 data, each stored pair is widened to FP64 first).  Asynchronous. */
 int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream);

@@ -311,7 +311,7 @@ namespace fe {
 
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
                    cudaStream_t s, const int* skip, double* dot_part, int64_t* blocks,
-                   bool query_only) {
+                   bool query_only, int nrhs, int64_t ldx, int64_t ldy) {
   if (!pa || ((!x || !y) && !query_only)) return set_error(FE_ERR_ARG, "fe_apply: null argument");
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_apply: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_apply: operator not set up in fe_pa_setup");
@@ -326,8 +326,18 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
       return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
                                    "encoding; call fe_pa_set_variant first");
   }
+  if (nrhs < 1 || (nrhs > 1 && (ldx < m->ndofs || ldy < m->ndofs)))
+    return set_error(FE_ERR_ARG, "fe_apply: nrhs >= 1 and ldx, ldy >= ndofs required");
+  if (nrhs > 1 && (dot_part || variant == FE_VARIANT_F64_DMMA))
+    return set_error(FE_ERR_UNSUPPORTED, "fe_apply: batched apply has no fused dot / DMMA kernel");
   if (skip == nullptr && !query_only) {
-    FE_CHECK_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->ndofs, s), "zero y");
+    if (nrhs == 1 || ldy == m->ndofs) {
+      FE_CHECK_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * m->ndofs * nrhs, s), "zero y");
+    } else {
+      FE_CHECK_CUDA(cudaMemset2DAsync(y, sizeof(double) * ldy, 0, sizeof(double) * m->ndofs,
+                                      nrhs, s),
+                    "zero y");
+    }
   }
   if (dot_part && variant == FE_VARIANT_F64_DMMA)
     return set_error(FE_ERR_UNSUPPORTED, "fe_apply: the DMMA kernel has no fused dot product");
@@ -347,6 +357,9 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
   a.dot_part = dot_part;
   a.blocks = blocks;
   a.query_only = query_only;
+  a.nrhs = nrhs;
+  a.ldx = ldx;
+  a.ldy = ldy;
   switch (variant) {
     case FE_VARIANT_F64:
       return launch_apply_f64(op, a, s);
@@ -604,6 +617,13 @@ int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* 
              void* stream) {
   clear_error();
   return apply_dispatch(pa, op, variant, dev_x, dev_y, (cudaStream_t)stream);
+}
+
+int fe_apply_batched(const fe_pa* pa, int op, int variant, int nrhs, const double* dev_x,
+                     int64_t ldx, double* dev_y, int64_t ldy, void* stream) {
+  clear_error();
+  return apply_dispatch(pa, op, variant, dev_x, dev_y, (cudaStream_t)stream, nullptr, nullptr,
+                        nullptr, false, nrhs, ldx, ldy);
 }
 
 int fe_apply_diffusion(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream) {

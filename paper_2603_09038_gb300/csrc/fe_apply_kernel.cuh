@@ -43,13 +43,16 @@ struct ApplyLayout {
 
 // DIFF: diffusion (qdata [e][qz][6][qy][qx]: xx, xy, xz, yy, yz, zz) or mass ([e][qz][qy][qx]).
 // VT: element type of the x and y vectors (double; float for the FP32 inner solves).
-template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB, class VT>
+// MULTI: several right-hand sides per launch (nrhs); when false the launch handles exactly one.
+template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB, class VT,
+          bool MULTI>
 __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
                                                  const typename Ar::QdT* __restrict__ qd,
-                                                 const VT* __restrict__ x,
-                                                 VT* __restrict__ y, int64_t ne,
+                                                 const VT* __restrict__ x0,
+                                                 VT* __restrict__ y0, int64_t ne,
                                                  const int* __restrict__ skip,
-                                                 double* __restrict__ dot_part,
+                                                 double* __restrict__ dot_part, int nrhs,
+                                                 int64_t ldx, int64_t ldy,
                                                  const typename Ar::template Tab<D, Q> tab) {
   using T = typename Ar::T;
   using L = ApplyLayout<D, Q, DIFF>;
@@ -69,6 +72,15 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   const int64_t e0 = (int64_t)blockIdx.x * NE;
   const int nel = (int)((ne - e0) < NE ? (ne - e0) : NE);
   const int tid = threadIdx.x;
+  auto dacc = Ar::dot_zero();
+
+  // Several right-hand sides (x0 + r ldx -> y0 + r ldy) are applied one after the other by the
+  // same block: after the first, the block's dof map and quadrature data come from L2.
+  const int nr = MULTI ? nrhs : 1;
+  for (int rhs = 0; rhs < nr; ++rhs) {
+  const VT* __restrict__ x = x0 + rhs * ldx;
+  VT* __restrict__ y = y0 + rhs * ldy;
+  if (rhs > 0) __syncthreads();  // the previous scatter has read its last bufB value
 
   // ---- gather (G): E0[i][j*D + k] = x[map[e][i + D j + D^2 k]]
   for (int t = tid; t < nel * D3; t += NT) {
@@ -387,15 +399,16 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   __syncthreads();
 
   // ---- scatter-add (G^T); optionally the block's share of x^T A x = sum_e x_e . (A_e x_e)
-  double dsum = 0.0;
   for (int t = tid; t < nel * D3; t += NT) {
     const int el = t / D3, a = t - el * D3;
     const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
     const T v = bufB[el * SZ_B + a];
     Ar::scatter(&y[g], v);
-    if (dot_part != nullptr) dsum = fma((double)__ldg(&x[g]), Ar::to_f64(v), dsum);
+    if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), v);
   }
-  if (dot_part != nullptr) {  // deterministic block reduction (fixed shuffle tree, warp order)
+  }  // right-hand sides
+  if (dot_part != nullptr) {  // (single right-hand side only)  // deterministic block reduction (fixed shuffle tree, warp order)
+    double dsum = Ar::dot_value(dacc);
     __shared__ double wsum[NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);

@@ -41,10 +41,13 @@ namespace fe {
 
 template <class Ar>
 struct ApplyTuning;
+// SPLIT: a separate single-right-hand-side instantiation (the batch loop cost the
+// memory-latency-bound FP32 kernel ~20 %; the ALU-bound variants do not notice it).
 template <>
 struct ApplyTuning<ArF64> {
   static constexpr int NT = FE_F64_NT, SMEM = FE_F64_SMEM, REREAD_D = FE_F64_REREAD_D,
                        MINB = FE_F64_MINB;
+  static constexpr bool SPLIT = false;
 };
 #ifndef FE_F32_NT
 #define FE_F32_NT 256
@@ -58,11 +61,13 @@ struct ApplyTuning<ArF64> {
 template <>
 struct ApplyTuning<ArF32> {
   static constexpr int NT = FE_F32_NT, SMEM = FE_F32_SMEM, REREAD_D = 2, MINB = FE_F32_MINB;
+  static constexpr bool SPLIT = true;
 };
-template <>
-struct ApplyTuning<ArF32x2> {
+template <bool A, bool L>
+struct ApplyTuning<ArF32x2T<A, L>> {
   static constexpr int NT = FE_F32X2_NT, SMEM = FE_F32X2_SMEM, REREAD_D = FE_F32X2_REREAD_D,
                        MINB = FE_F32X2_MINB;
+  static constexpr bool SPLIT = false;
 };
 
 // Elements per block: as many as fit in the variant's shared-memory budget, a power of two,
@@ -129,14 +134,14 @@ inline void fill_tab(const Basis1D& b, TabF32x2<D, Q>* t) {
   t->cG = (float)(cG * up);
 }
 
-template <int D, int Q, bool DIFF, class Ar, class VT = double>
-int run_apply(const ApplyArgs& a, cudaStream_t s) {
+template <int D, int Q, bool DIFF, class Ar, class VT, bool MULTI>
+int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   using T = typename Ar::T;
   using Tune = ApplyTuning<Ar>;
   constexpr int NT = Tune::NT;
   constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM>();
   const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF>::PER_ELEM * sizeof(T);
-  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB, VT>;
+  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB, VT, MULTI>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -151,19 +156,33 @@ int run_apply(const ApplyArgs& a, cudaStream_t s) {
   kern<<<(unsigned int)nblk, NT, smem, s>>>(a.map, reinterpret_cast<const typename Ar::QdT*>(a.qd),
                                             reinterpret_cast<const VT*>(a.x),
                                             reinterpret_cast<VT*>(a.y), a.ne, a.skip, a.dot_part,
-                                            tab);
+                                            a.nrhs, a.ldx, a.ldy, tab);
   return cuda_error(cudaGetLastError(), "apply kernel launch");
 }
 
-// Dispatch on the order for the default rule Q = p + 2.
+template <int D, int Q, bool DIFF, class Ar, class VT = double>
+int run_apply(const ApplyArgs& a, cudaStream_t s) {
+  if constexpr (ApplyTuning<Ar>::SPLIT) {
+    if (a.nrhs == 1) return launch_kernel<D, Q, DIFF, Ar, VT, false>(a, s);
+  }
+  return launch_kernel<D, Q, DIFF, Ar, VT, true>(a, s);
+}
+
+// Dispatch on the order for the default rule Q = p + 2 (Ar may depend on the order through
+// ArForOrder).
+template <class Ar, int P>
+struct ArForOrder {
+  using type = Ar;
+};
+
 template <class Ar, class VT = double>
 int dispatch_order(int op, const ApplyArgs& a, cudaStream_t s) {
   const bool diff = (op == FE_DIFFUSION);
   if (a.Q != a.p + 2) return set_error(FE_ERR_UNSUPPORTED, "only q1d = order + 2 is built");
 #define FE_CASE(P)                                                                  \
   case P:                                                                           \
-    return diff ? run_apply<P + 1, P + 2, true, Ar, VT>(a, s)                       \
-                : run_apply<P + 1, P + 2, false, Ar, VT>(a, s);
+    return diff ? run_apply<P + 1, P + 2, true, typename ArForOrder<Ar, P>::type, VT>(a, s) \
+                : run_apply<P + 1, P + 2, false, typename ArForOrder<Ar, P>::type, VT>(a, s);
   switch (a.p) {
     FE_CASE(1)
     FE_CASE(2)

@@ -7,12 +7,14 @@
 //
 //   * anchored dot products (amad*, dot3), used wherever a bound B >= sum_i |a_i x_i| of the sum
 //     is known before it starts (a 1D contraction: max_i |x_i| times the 1D table's largest
-//     absolute row or column sum; a row of the pointwise D: the exact sum of |a_i| |x_i|).  The high accumulator starts at the anchor
-//     sigma = 2^ceil(log2(4 B)), so it stays within [3 sigma/4, 5 sigma/4]; then per term
+//     absolute row or column sum; a row of the pointwise D: the exact sum of |a_i| |x_i|).  The
+//     high accumulator starts at the anchor sigma = 2^ceil(log2(2 (1 + 2^-9) B)), so it stays
+//     within [sigma/2, 3 sigma/2]; then per term
 //         t = fma(ah, xh, A);  z = t - A;  r = fma(ah, xh, -z);  L += r;  L += ah xl + al xh
-//     z is exact (Sterbenz: t / A lies in [1/2, 2]), so A - sigma is exactly the sum of the
-//     parts of the products above ulp(A), and r, the rest of each product, is rounded once to
-//     float -- an error below 2^-24 ulp(A), i.e. 2^-47 sigma.  Six FP32 instructions per term.
+//     z is exact (t and A are multiples of 2^-24 sigma and differ by less than 2^23 of them), so
+//     A - sigma is exactly the sum of the parts of the products above that grid, and r, the rest
+//     of each product, is rounded once to float -- an error below 2^-48 sigma.  Six FP32
+//     instructions per term; the error of the sum is a small multiple of 2^-48 sigma.
 //   * compensated dot products (mad*), for sums whose bound is not known in advance (the
 //     transposed z contraction at Q > 6, whose inputs are produced on the fly; the mass
 //     pointwise product): Dekker's exact product by FMA plus Knuth's TwoSum, twelve
@@ -103,11 +105,18 @@ struct ArF64 {
     return fma(a2, x2, fma(a1, x1, a0 * x0));
   }
   static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, v); }
-  static __device__ __forceinline__ double to_f64(T v) { return v; }
+  // accumulation of the fused x . (A x): FP64
+  using DotAcc = double;
+  static __device__ __forceinline__ DotAcc dot_zero() { return 0.0; }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) { a = fma(x, v, a); }
+  static __device__ __forceinline__ double dot_value(DotAcc a) { return a; }
 };
 
-struct ArF32x2 {
-  static constexpr bool kAnchored = true;
+// ANCHORED: anchored dot products (else every sum is compensated); LAZY: anchored results are
+// left unnormalised.  The launcher picks the combination per order from the measured error.
+template <bool ANCHORED, bool LAZY>
+struct ArF32x2T {
+  static constexpr bool kAnchored = ANCHORED;
   using QdT = double;  // 8-byte (hi, lo) float pairs
   using T = f2;
   using Acc = Anch;
@@ -153,18 +162,40 @@ struct ArF32x2 {
                                              bool transposed) {
     return anchor_of(f_fma(transposed ? t.cG : t.rG, mg, f_mul(transposed ? t.cB : t.rB, mb)));
   }
-  static __device__ __forceinline__ Acc begin(Sig s) { return anch_begin(s); }
+  static __device__ __forceinline__ Acc begin(Sig s) {
+    return ANCHORED ? anch_begin(s) : Anch{0.0f, 0.0f};
+  }
   template <int D, int Q>
   static __device__ __forceinline__ void amadB(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
-    anch_mad(acc, t.Bh[q * D + d], t.Bl[q * D + d], x);
+    amad(acc, t.Bh[q * D + d], t.Bl[q * D + d], x);
   }
   template <int D, int Q>
   static __device__ __forceinline__ void amadG(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
-    anch_mad(acc, t.Gh[q * D + d], t.Gl[q * D + d], x);
+    amad(acc, t.Gh[q * D + d], t.Gl[q * D + d], x);
   }
-  static __device__ __forceinline__ T end(Acc a, Sig s) { return anch_end(a, s); }
+  static __device__ __forceinline__ void amad(Acc& acc, float ah, float al, T x) {
+    if constexpr (ANCHORED) {
+      anch_mad(acc, ah, al, x);
+    } else {  // compensated, the Anch pair used as (h, l)
+      f2 c{acc.A, acc.L};
+      f2_mad(c, ah, al, x);
+      acc = Anch{c.h, c.l};
+    }
+  }
+  static __device__ __forceinline__ T end(Acc a, Sig s) {
+    if constexpr (!ANCHORED) return f2_norm(f2{a.A, a.L});
+    if constexpr (LAZY) return anch_end_lazy(a, s);
+    return anch_end(a, s);
+  }
   // a0 x0 + a1 x1 + a2 x2, anchored with the exact bound sum |a_i.h x_i.h| of this point
   static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
+    if constexpr (!ANCHORED) {
+      f2 c{0.0f, 0.0f};
+      f2_mad(c, a0.h, a0.l, x0);
+      f2_mad(c, a1.h, a1.l, x1);
+      f2_mad(c, a2.h, a2.l, x2);
+      return f2_norm(c);
+    }
     const float b = f_fma(fabsf(a2.h), fabsf(x2.h),
                           f_fma(fabsf(a1.h), fabsf(x1.h), f_mul(fabsf(a0.h), fabsf(x0.h))));
     const float sg = anchor_of(b);
@@ -172,13 +203,23 @@ struct ArF32x2 {
     anch_mad(acc, a0.h, a0.l, x0);
     anch_mad(acc, a1.h, a1.l, x1);
     anch_mad(acc, a2.h, a2.l, x2);
-    return anch_end(acc, sg);
+    return end(acc, sg);
   }
   static __device__ __forceinline__ void scatter(double* y, T v) {
     atomicAdd(y, (double)v.h + (double)v.l);
   }
-  static __device__ __forceinline__ double to_f64(T v) { return (double)v.h + (double)v.l; }
+  // accumulation of the fused x . (A x): compensated float-float on the FP32 pipe (FP64-class
+  // accuracy without FP64 instructions per term), widened once per thread
+  using DotAcc = f2;
+  static __device__ __forceinline__ DotAcc dot_zero() { return f2{0.0f, 0.0f}; }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) {
+    const f2 xf = f2_from_f64(x);
+    f2_mad(a, xf.h, xf.l, v);
+  }
+  static __device__ __forceinline__ double dot_value(DotAcc a) { return (double)a.h + (double)a.l; }
 };
+
+using ArF32x2 = ArF32x2T<true, false>;
 
 // Plain FP32 (the inner solves of mixed-precision iterative refinement): FP32 quadrature data
 // (half the bytes), FP32 FMAs; FP64 vectors in and out, converted by integer manipulation.
@@ -230,7 +271,14 @@ struct ArF32 {
   }
   static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, f64_from_f32(v)); }
   static __device__ __forceinline__ void scatter(float* y, T v) { atomicAdd(y, v); }
-  static __device__ __forceinline__ double to_f64(T v) { return f64_from_f32(v); }
+  // accumulation of the fused x . (A x): FP32 (the inner solves need no more)
+  using DotAcc = float;
+  static __device__ __forceinline__ DotAcc dot_zero() { return 0.0f; }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) {
+    a = fmaf(f2_from_f64(x).h, v, a);
+  }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, float x, T v) { a = fmaf(x, v, a); }
+  static __device__ __forceinline__ double dot_value(DotAcc a) { return f64_from_f32(a); }
 };
 
 }  // namespace fe

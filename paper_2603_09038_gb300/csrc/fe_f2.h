@@ -91,10 +91,12 @@ FE_HD void f2_mad(f2& acc, float ah, float al, f2 x) {
 
 FE_HD f2 f2_norm(f2 a) { return two_sum(a.h, a.l); }
 
-// Smallest power of two >= 4 b (b >= 0 finite; 0 for b = 0): the anchor of a dot product whose
-// terms satisfy sum |a_i x_i| <= b.
+// Anchor of a dot product whose terms satisfy sum |a_i x_i| <= b: the smallest power of two
+// sigma >= 2 (1 + 2^-9) b (0 for b = 0).  Every partial sum A = sigma + sum z_i then stays in
+// [sigma/2, 3 sigma/2], where floats are multiples of 2^-24 sigma, and each step t - A is below
+// 2^23 of those units: exact.
 FE_HD float anchor_of(float b) {
-  const uint32_t u = f_bits(f_mul(4.0f, b));
+  const uint32_t u = f_bits(f_mul(2.00390625f, b));
   return f_from_bits((u + 0x007FFFFFu) & 0x7F800000u);
 }
 
@@ -115,19 +117,13 @@ FE_HD void anch_mad(Anch& acc, float ah, float al, f2 x) {
   acc.A = t;
 }
 
-#ifndef FE_F2_LAZY_END
-#define FE_F2_LAZY_END 0
-#endif
-// Result of an anchored sum: (A - sigma) exactly, plus the low word.  Normalised by TwoSum
-// unless FE_F2_LAZY_END, which returns the unnormalised pair (the next stage uses the high word
-// for its exact products and the low word only in first-order correction terms).
-FE_HD f2 anch_end(Anch acc, float sigma) {
-#if FE_F2_LAZY_END
-  return f2{f_sub(acc.A, sigma), acc.L};
-#else
-  return two_sum(f_sub(acc.A, sigma), acc.L);
-#endif
-}
+// Result of an anchored sum: (A - sigma) exactly, plus the low word, normalised by TwoSum.
+FE_HD f2 anch_end(Anch acc, float sigma) { return two_sum(f_sub(acc.A, sigma), acc.L); }
+
+// The same without normalisation: the next stage uses the high word for its exact products
+// and the low word only in first-order correction terms, so an unnormalised pair costs
+// accuracy only through slightly larger bounds (used where the error budget allows).
+FE_HD f2 anch_end_lazy(Anch acc, float sigma) { return f2{f_sub(acc.A, sigma), acc.L}; }
 
 // Splits an FP64 value into floats without the FP64 pipe: h = v truncated to 24 significant
 // bits (exact), l = the next 23 bits of the remainder (exact), by integer manipulation of the

@@ -84,6 +84,8 @@ struct ApplyArgs {
   double* dot_part;      // optional: per-block partials of sum_e x_e . (A_e x_e) (= x^T A x)
   int64_t* blocks;       // optional out: grid size of the launch (set also when query_only)
   bool query_only;       // only report the grid size
+  int nrhs = 1;          // right-hand sides x + r ldx -> y + r ldy, r < nrhs
+  int64_t ldx = 0, ldy = 0;
 };
 
 // Launchers (one translation unit per variant); return FE_OK or an error status.
@@ -102,7 +104,8 @@ int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);
 // (variants F64, F32X2, F32); blocks: optional out, the grid size (number of partials).
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
                    cudaStream_t s, const int* skip = nullptr, double* dot_part = nullptr,
-                   int64_t* blocks = nullptr, bool query_only = false);
+                   int64_t* blocks = nullptr, bool query_only = false, int nrhs = 1,
+                   int64_t ldx = 0, int64_t ldy = 0);
 
 // y = A x with the FP32 variant on float vectors (the caller zeroes y); same skip / dot_part
 // semantics as apply_dispatch.

@@ -175,6 +175,13 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_pq_var(const double* 
     sc[S_ALPHA] = sc[S_RZ] / pq;
 }
 
+// Per-dof inner-product terms accumulated in compensated float-float on the FP32 pipe (FP64-class
+// accuracy; GB300's FP64 pipe would make two DFMAs per dof the bottleneck of this pass).
+__device__ __forceinline__ void f2_acc_prod(fe::f2& acc, double a, double b) {
+  const fe::f2 af = fe::f2_from_f64(a), bf = fe::f2_from_f64(b);
+  fe::f2_mad(acc, af.h, af.l, bf);
+}
+
 __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ x,
                                                            double* __restrict__ r,
                                                            double* __restrict__ z,
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
                                                            const int* flags) {
   if (flags[F_STATE] != ST_RUN) return;
   const double alpha = sc[S_ALPHA];
-  double s_rz = 0.0, s_rr = 0.0;
+  fe::f2 s_rz{0.0f, 0.0f}, s_rr{0.0f, 0.0f};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool bnd = mask[i] != 0;
@@ -197,10 +204,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
     r[i] = ri;
     const double zi = d ? ri * d[i] : (bnd ? 0.0 : ri);
     z[i] = zi;
-    s_rz = fma(ri, zi, s_rz);
-    s_rr = fma(ri, ri, s_rr);
+    f2_acc_prod(s_rz, ri, zi);
+    f2_acc_prod(s_rr, ri, ri);
   }
-  block_sum2(s_rz, s_rr, part0, part1);
+  block_sum2((double)s_rz.h + (double)s_rz.l, (double)s_rr.h + (double)s_rr.l, part0, part1);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish_update(const double* part0,

@@ -64,6 +64,8 @@ _SIGS = {
     "fe_apply_diffusion": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_apply_mass": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_apply": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_apply_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                        ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
     "fe_assemble_diagonal": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "fe_load_vector_sine": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pcg": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
@@ -175,6 +177,13 @@ def fe_apply_mass(pa, dev_x, dev_y, stream=None):
 def fe_apply(pa, op, variant, dev_x, dev_y, stream=None):
     v = VARIANTS.get(variant, variant)
     _check(load().fe_apply(_VP(pa), int(op), int(v), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_apply_batched(pa, op, variant, nrhs, dev_x, ldx, dev_y, ldy, stream=None):
+    """nrhs applies in one launch; x, y hold the right-hand sides at strides ldx, ldy."""
+    v = VARIANTS.get(variant, variant)
+    _check(load().fe_apply_batched(_VP(pa), int(op), int(v), int(nrhs), _ptr(dev_x), int(ldx),
+                                   _ptr(dev_y), int(ldy), _stream(stream)))
 
 
 def fe_assemble_diagonal(pa, op, dev_diag, stream=None):

@@ -74,25 +74,33 @@ def _sampled_rows(ndofs, rng, k=64):
 
 
 def _full_size_check(n, p, variants, sigma=1.0):
+    """FP64: sampled outputs against the oracle (computed one by one); every other variant: every
+    output against the FP64 result, plus the same sampled outputs against the oracle."""
     torch = torch_cuda()
     with gpu_problem(n, n, n, p, sigma=sigma) as (fe, mesh, pa, V, c):
         ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
         prob = oop.Problem(n, n, n, p, V, coeff=c)
         rng = np.random.default_rng(p)
         rows = _sampled_rows(ndofs, rng)
+        trows = torch.from_numpy(rows).cuda()
         xh = uniform_vector(ndofs, seed=p)
         x = torch.from_numpy(xh).cuda()
         y = torch.empty_like(x)
         ones = torch.ones_like(x)
-        for variant in variants:
+        yref = {}
+        for variant in ["f64"] + [v for v in variants if v != "f64"]:
             fe.fe_pa_set_variant(pa, variant)
             for op, kind in OPS:
                 fe.fe_apply(pa, op, variant, x, y)
                 torch.cuda.synchronize()
-                ys = y[torch.from_numpy(rows).cuda()].cpu().numpy()
                 scale = float(y.abs().max())
                 ref = oop.apply_rows(prob, xh, kind, rows)
-                assert np.abs(ys - ref).max() <= TOL * scale, (variant, kind)
+                assert np.abs(y[trows].cpu().numpy() - ref).max() <= TOL * scale, (variant, kind)
+                if variant == "f64":
+                    yref[kind] = y.clone()
+                else:
+                    full = float((y - yref[kind]).abs().max()) / float(yref[kind].abs().max())
+                    assert full <= TOL, (variant, kind, full)
                 # invariants at full size: A 1 = 0; 1^T M 1 = sum_e c_e vol_e (unit cube if c=1)
                 fe.fe_apply(pa, op, variant, ones, y)
                 torch.cuda.synchronize()
@@ -183,3 +191,29 @@ def test_errors_are_status_codes():
         with pytest.raises(fe.FEError) as ei:
             fe.fe_apply(pa, fe.FE_DIFFUSION, "f32x2", x, y)  # data still FP64-encoded
         assert ei.value.status == fe.FE_ERR_ARG
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32x2", "f32"])
+def test_batched_apply_matches_single_applies(variant):
+    """fe_apply_batched over 5 right-hand sides (padded leading dimension) equals 5 single
+    applies (same kernel arithmetic; only the atomic order may differ)."""
+    torch = torch_cuda()
+    dims, p = (5, 4, 3), 3
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        fe.fe_pa_set_variant(pa, variant)
+        nr, ld = 5, nd + 7
+        X = torch.rand(nr, ld, dtype=torch.float64, device="cuda") * 2 - 1
+        Y = torch.full((nr, ld), 7.0, dtype=torch.float64, device="cuda")
+        for op in (fe.FE_DIFFUSION, fe.FE_MASS):
+            fe.fe_apply_batched(pa, op, variant, nr, X, ld, Y, ld)
+            y1 = torch.empty(nd, dtype=torch.float64, device="cuda")
+            for r in range(nr):
+                fe.fe_apply(pa, op, variant, X[r, :nd].contiguous(), y1)
+                torch.cuda.synchronize()
+                ref = y1.cpu().numpy()
+                got = Y[r, :nd].cpu().numpy()
+                tol = 1e-6 if variant == "f32" else TOL
+                assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+        with pytest.raises(fe.FEError):
+            fe.fe_apply_batched(pa, fe.FE_DIFFUSION, variant, 2, X, nd - 1, Y, ld)
