@@ -34,7 +34,7 @@ N_ELEM, ORDER, RTOL = 64, 3, 1e-8
 MAXIT = 20000
 METRIC = "GDOF/s of FP64 PA diffusion apply (frac of HBM roofline); PCG time-to-1e-8 residual"
 UNIT = "GDOF/s"
-FP64_DFMA_PER_CLK_PER_SM = 2           # measured on GB300 (FP64 peak)
+FP64_DFMA_PER_CLK_PER_SM = 2           # measured on GB300 by fe_probe_throughput
 # DRAM bytes (read + write) of one apply launch from an ncu capture of the same kernel on the
 # 32^3 p=3 mesh, with that launch's algorithmic bytes: scaled to the benchmark's launch by the
 # algorithmic bytes (traffic grows with the elements).  Only for kernels unchanged since.

@@ -95,8 +95,8 @@ int fe_mesh_boundary_mask(const fe_mesh* mesh, uint8_t* dev_mask, void* stream);
 /* Copies the element dof map (int32 [ne][D^3]) to dev_map. */
 int fe_mesh_dof_map(const fe_mesh* mesh, int32_t* dev_map, void* stream);
 
-/* Partial assembly (Section II-B: "precompute and store the block-diagonal D at quadrature
- * points").  Computes per element and Gauss point the trilinear Jacobian J, det J and
+/* Partial assembly (Section II-B: the block-diagonal D at the quadrature points is evaluated once
+ * and kept).  Computes per element and Gauss point the trilinear Jacobian J, det J and
  * adj(J), and stores
  *   diffusion  D_q = w_q c_e adj(J) adj(J)^T / det J   (6 symmetric entries)
  *   mass       M_q = w_q c_e det J
@@ -119,7 +119,7 @@ int fe_apply_mass(const fe_pa* pa, const double* dev_x, double* dev_y, void* str
 int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* dev_y,
              void* stream);
 
-/* Batched apply (SURVEY "next" item: many right-hand sides per launch): y_r = A x_r for
+/* Batched apply (an extension beyond the paper: many right-hand sides per launch): y_r = A x_r for
  * r < nrhs, x_r = dev_x + r*ldx, y_r = dev_y + r*ldy (leading dimensions in elements, >= ndofs).
  * One launch; every thread block applies all right-hand sides to its elements one after the
  * other, so after the first one its dof map and quadrature data are read from L2 instead of
@@ -147,7 +147,7 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
 
-/* Mixed-precision iterative refinement around an FP32 inner PCG (SURVEY "next" item; the paper
+/* Mixed-precision iterative refinement around an FP32 inner PCG (an extension; the paper
  * itself stays in FP64 throughout).  Outer loop, in FP64 vectors:
  *   r = (1-m)(b - A x)   with the handle's FP64-accurate operator (FE_VARIANT_F64, or
  *                        FE_VARIANT_F32X2 when the data is pair-encoded);
@@ -190,6 +190,70 @@ int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double*
  * allocates 64 bytes of scratch. */
 enum { FE_PROBE_FP64_FMA = 0, FE_PROBE_FP64_DMMA = 1, FE_PROBE_FP32_FMA = 2, FE_PROBE_F32X2_MAC = 3 };
 int fe_probe_throughput(int unit, double* tflops);
+
+/* ---- Learned element-patch preconditioner and flexible CG (an extension; the paper has no
+ * learned component and solves with Jacobi-PCG only).
+ *
+ * The preconditioner is an additive patch map  z = M(r) = sum_e R_e^T W_e S_e s_e f(x_e / s_e)  with
+ *   W_e = diag(1 / number of elements sharing the dof)^(1/2) on element e, 0 on the boundary,
+ *   S = diag(A)^(-1/2), x_e = S_e W_e R_e r, s_e = ||x_e||_2, and
+ *   f(x) = relu(relu(x W1) W2) W3 + x W0, a bias-free three-layer perceptron D^3 -> width ->
+ *   width -> D^3 (D = order + 1) plus a linear skip term, with BF16 weights and activations and
+ *   FP32 accumulation on the tensor cores.  With f(x) = S_e^{-1} A_ee^{-1} S_e^{-1} x exactly, M
+ *   is the symmetrically weighted additive Schwarz method on element patches.  M is nonlinear
+ *   (though positively homogeneous), so it is used inside flexible CG.
+ * Training pairs come from the operator itself: for interior elements three apart in each
+ * direction, the block A_ee of the assembled matrix on the element's dofs is probed with D^3
+ * applies and factored by FP64 Cholesky; f is trained with Adam, to the relative squared error,
+ * on pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v scaled by 1/||x||, for v i.i.d. normal, A_ee u for
+ * normal u, or W_e r for residuals r of a short Jacobi-FCG run.
+ * Built for orders 1..4 (the FP64 Cholesky of A_ee runs in one block's shared memory).
+ * Handles are library-owned, refer to (do not own) their fe_pa, and are not thread-safe. */
+typedef struct fe_lpc fe_lpc;
+
+/* Creates the preconditioner for operator op of pa: He-normal weights W1..W3 (seeded), W0 = 0,
+ * the diagonal scalings and the partition-of-unity weights.  width 8..4096.  Synchronous. */
+int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out);
+
+/* Number of FP32 master weights: 2 * D^3 * width + width^2 + D^6 (W1 [D^3][width],
+ * W2 [width][width], W3 [width][D^3], W0 [D^3][D^3], row-major, packed in that order). */
+int fe_lpc_nparams(const fe_lpc* lpc, int64_t* nparams);
+
+/* Runs `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on batches of `batch`
+ * pairs drawn from the training set, which is generated on the first call with `reps` pairs per
+ * sampled element (0 => 16).  *final_loss (may be NULL) = the relative squared error of the last
+ * batch before its step.  Returns FE_ERR_ARG if the mesh has fewer than 3 elements per axis,
+ * FE_ERR_UNSUPPORTED for orders above 4, FE_ERR_BREAKDOWN if a sampled block is not positive
+ * definite.  Synchronous. */
+int fe_lpc_train(fe_lpc* lpc, int steps, int batch, double lr, int reps, double* final_loss,
+                 void* stream);
+
+/* Copies the FP32 master weights (fe_lpc_nparams floats) to host_w (set = 0) or from host_w
+ * (set != 0; the BF16 copy is refreshed).  Synchronous. */
+int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);
+
+/* Test hook of the training kernels: for `batch` host rows X (FP32 [batch][D^3], rounded to
+ * BF16) and targets T (FP32 [batch][D^3]), runs the forward pass and back-propagation with the
+ * current weights and returns the outputs Y (FP32, may be NULL), the gradient of the loss
+ * sum ||Y - T||^2 / sum ||T||^2 with respect to the packed weights (FP32, may be NULL) and the
+ * loss.  Does not update the weights.  Synchronous. */
+int fe_lpc_loss_grad(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
+                     float* host_y, float* host_grad, double* loss);
+
+/* z = M(r) for FP64 device vectors of length ndofs (z overwritten; z = 0 on the boundary).
+ * Asynchronous. */
+int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
+
+/* Flexible CG (FCG with one stored direction: beta = -(z.q)/(p.q), alpha = (p.r)/(p.q)) for the
+ * same system, arguments and stopping rule as fe_pcg, preconditioned by lpc, or by Jacobi when
+ * lpc is NULL.  If the learned preconditioner produces a non-descent direction (z.r <= 0) or the
+ * residual stops improving (no 1% gain in 100 iterations) the iteration restarts from the
+ * current iterate with Jacobi.  Applies use pa's variant; vectors and inner products are FP64.
+ * stats: outer_iters = 1 + number of such restarts.  Synchronous. */
+int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
+           int maxit, fe_pcg_stats* stats, void* stream);
+
+void fe_lpc_destroy(fe_lpc* lpc);
 
 void fe_pa_destroy(fe_pa* pa);
 void fe_mesh_destroy(fe_mesh* mesh);

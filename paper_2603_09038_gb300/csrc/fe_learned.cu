@@ -1,0 +1,1155 @@
+// Learned element-patch preconditioner and flexible CG (an extension; the paper has no learned
+// component).
+//
+// Preconditioner:  z = sum_e R_e^T W_e S_e s_e f(x_e / s_e),  x_e = S_e W_e R_e r,  s_e = ||x_e||_2,
+// with W_e = diag(1/multiplicity)^(1/2) on the element's dofs (0 on the Dirichlet boundary),
+// S = diag(A)^(-1/2), and f(x) = relu(relu(x W1) W2) W3 + x W0: a bias-free three-layer MLP
+// D^3 -> width -> width -> D^3 with ReLU plus a linear skip term, BF16 weights and activations,
+// FP32 accumulation on the tensor cores.  With f(x) = S_e^{-1} A_ee^{-1} S_e^{-1} x exactly this is
+// the symmetrically weighted additive Schwarz method on element patches, which needs about half
+// the iterations of Jacobi on these problems (the one-sided weighting R^T W^2 A_ee^{-1} R does
+// not beat Jacobi).  The symmetric diagonal scaling makes the map nearly the same on every
+// element even across coefficient jumps, so one network serves the whole mesh.
+//
+// Training pairs come from the FP64-accurate operator itself: for interior elements three apart
+// in every direction (so that their neighbourhoods do not overlap), the block A_ee of the
+// assembled matrix on the element's dofs is probed with D^3 applies of the global operator,
+// factored (batched FP64 Cholesky) and used to produce pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v
+// for v i.i.d. normal, v = A_ee u, and v = W_e r for residual snapshots r of Jacobi-FCG runs,
+// both scaled by 1/||x||.
+// Training minimises the relative squared error with Adam, all on the GPU with the kernels
+// below.  The flexible CG (Notay's FCG(1)) tolerates the nonlinear preconditioner and falls back
+// to Jacobi-PCG on its residual when it stagnates; convergence is judged on the FP64 residual.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "fe_internal.h"
+#include "fe_mlp.cuh"
+
+using namespace fe;
+
+namespace fe {
+int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s);
+}
+
+struct fe_lpc {
+  fe_pa* pa = nullptr;  // not owned
+  int op = FE_DIFFUSION;
+  int din = 0, width = 0;
+  int64_t nparam = 0;
+  float* w32 = nullptr;         // packed FP32 master weights W1 | W2 | W3
+  __nv_bfloat16* wb = nullptr;  // BF16 copy used by the GEMMs
+  float *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+  int adam_t = 0;
+  double* wsq = nullptr;        // (1/multiplicity)^(1/2) per dof, 0 on the boundary
+  double* dinv = nullptr;       // inverse diagonal, 0 on the boundary (Jacobi)
+  double* dis = nullptr;        // diagonal^(-1/2), 0 on the boundary
+  double* fsc = nullptr;        // wsq * dis: the input/output scaling F = W S of the apply
+  __nv_bfloat16* wimg = nullptr;  // shared-memory weight image of the fused apply
+  bool wimg_ok = false;
+  int fused_grid = 0;           // persistent grid of the fused apply (0: unfused GEMM path)
+  // training samples
+  int64_t nsamp = 0;
+  __nv_bfloat16* Xs = nullptr;  // [nsamp][din]
+  float* Ts = nullptr;          // [nsamp][din]
+  uint64_t seed = 0;
+  // forward/backward workspace for up to cap rows
+  int64_t cap = 0;
+  __nv_bfloat16 *Xb = nullptr, *H1b = nullptr, *H2b = nullptr, *dYb = nullptr, *dA1b = nullptr,
+                *dA2b = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *Tb = nullptr, *scale = nullptr;
+  double* red = nullptr;        // loss reductions
+};
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kLpcMaxOrder = 4;          // FP64 Cholesky of A_ee in one block's shared memory
+constexpr int64_t kProbeDoubles = 1 << 26;  // bound on the probed blocks (2 x 512 MB)
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // splitmix64 finaliser
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double normal01(uint64_t key) {  // Box-Muller on two hashed uniforms
+  const uint64_t a = mix64(key), b = mix64(key ^ 0xD1B54A32D192ED03ull);
+  const double u1 = ((a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+__global__ void k_init_weights(float* w, int din, int width, uint64_t seed) {
+  const int64_t n1 = (int64_t)din * width, n2 = (int64_t)width * width, n3 = n1;
+  const int64_t n = n1 + n2 + n3 + (int64_t)din * din;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int fan_in = i < n1 ? din : width;
+    w[i] = i < n1 + n2 + n3
+               ? (float)(normal01(seed * 0x100000001ull + (uint64_t)i) * sqrt(2.0 / fan_in))
+               : 0.0f;  // skip term starts at zero
+  }
+}
+
+__global__ void k_normal_vec(double* __restrict__ v, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = normal01(seed + 0x9E3779B97F4A7C15ull * (uint64_t)i);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16(a[i]);
+}
+
+// multiplicity of every dof (elements sharing it), then wsq = mult^(-1/2) off the boundary
+__global__ void k_count(const int32_t* __restrict__ map, int64_t n, double* __restrict__ c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&c[map[i]], 1.0);
+}
+
+__global__ void k_wsq(double* __restrict__ c, const uint8_t* __restrict__ mask, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c[i] = mask[i] ? 0.0 : 1.0 / sqrt(c[i]);
+}
+
+__global__ void k_invert_diag(double* __restrict__ d, const uint8_t* __restrict__ mask, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (mask[i] || !(d[i] > 0.0)) ? 0.0 : 1.0 / d[i];
+}
+
+// b = sqrt(a) and c = w * b
+__global__ void k_sqrt_vec(const double* __restrict__ a, double* __restrict__ b,
+                           const double* __restrict__ w, double* __restrict__ c, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = sqrt(a[i]);
+    b[i] = bi;
+    c[i] = w[i] * bi;
+  }
+}
+
+// ---- probing of A_ee for the sample elements
+__global__ void k_probe_set(double* __restrict__ v, const int32_t* __restrict__ map,
+                            const int32_t* __restrict__ elems, int ns, int din, int a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ns) v[map[(int64_t)elems[s] * din + a]] = 1.0;
+}
+
+__global__ void k_probe_get(const double* __restrict__ w, const int32_t* __restrict__ map,
+                            const int32_t* __restrict__ elems, int ns, int din, int a,
+                            double* __restrict__ Aee) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)ns * din) return;
+  const int s = (int)(i / din), b = (int)(i % din);
+  Aee[((int64_t)s * din + b) * din + a] = w[map[(int64_t)elems[s] * din + b]];
+}
+
+// Batched Cholesky A = L L^T in place (lower triangle), one block per matrix; FP64.
+__global__ void k_cholesky(double* __restrict__ Aee, int din, int* __restrict__ fail) {
+  extern __shared__ double sm[];
+  double* A = Aee + (int64_t)blockIdx.x * din * din;
+  for (int i = threadIdx.x; i < din * din; i += blockDim.x) sm[i] = A[i];
+  __syncthreads();
+  for (int k = 0; k < din; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = sm[k * din + k];
+      if (!(d > 0.0)) atomicExch(fail, 1);
+      sm[k * din + k] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double lkk = sm[k * din + k];
+    for (int i = k + 1 + threadIdx.x; i < din; i += blockDim.x) sm[i * din + k] /= lkk;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (din - k - 1) * (din - k - 1); idx += blockDim.x) {
+      const int i = k + 1 + idx / (din - k - 1), j = k + 1 + idx % (din - k - 1);
+      if (j <= i) sm[i * din + j] -= sm[i * din + k] * sm[j * din + k];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < din * din; i += blockDim.x) A[i] = sm[i];
+}
+
+// Samples: per sample element s and replica q, v is (q mod 3) i.i.d. normal, A_ee u for normal u
+// (then A_ee^{-1} v = u), or W_e r for a residual snapshot r of a Jacobi-FCG run; u = A_ee^{-1} v
+// by the Cholesky factors; x = S v and t = u / S, both stored scaled by 1/||x||.
+__global__ void k_samples(const double* __restrict__ Lfac, const double* __restrict__ Afull,
+                          const double* __restrict__ snaps, int nsnap,
+                          const int32_t* __restrict__ map, const int32_t* __restrict__ elems,
+                          const double* __restrict__ dis, const double* __restrict__ wsq,
+                          int ns, int din, int reps,
+                          uint64_t seed, __nv_bfloat16* __restrict__ Xs, float* __restrict__ Ts) {
+  extern __shared__ double sh[];
+  double* r = sh;
+  double* t = sh + din;
+  double* u = sh + 2 * din;
+  const int s = blockIdx.x;
+  const double* L = Lfac + (int64_t)s * din * din;
+  const double* A = Afull + (int64_t)s * din * din;
+  for (int q = 0; q < reps; ++q) {
+    const int64_t row = (int64_t)s * reps + q;
+    const int kind = q % 3;
+    const bool applied = kind == 1;
+    const double* snap = snaps + ((int64_t)((q / 3) % nsnap) * ns + s) * din;
+    for (int i = threadIdx.x; i < din; i += blockDim.x)
+      u[i] = kind == 2 ? snap[i] * wsq[map[(int64_t)elems[s] * din + i]]
+                       : normal01(seed ^ ((uint64_t)row * 1315423911ull + (uint64_t)i * 2654435761ull));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (applied) {
+        for (int i = 0; i < din; ++i) {
+          double acc = 0.0;
+          for (int j = 0; j < din; ++j) acc += A[(int64_t)i * din + j] * u[j];
+          r[i] = acc;
+          t[i] = u[i];
+        }
+      } else {
+        for (int i = 0; i < din; ++i) r[i] = u[i];
+        for (int i = 0; i < din; ++i) {  // L y = r
+          double acc = r[i];
+          for (int j = 0; j < i; ++j) acc -= L[(int64_t)i * din + j] * t[j];
+          t[i] = acc / L[(int64_t)i * din + i];
+        }
+        for (int i = din - 1; i >= 0; --i) {  // L^T t = y
+          double acc = t[i];
+          for (int j = i + 1; j < din; ++j) acc -= L[(int64_t)j * din + i] * t[j];
+          t[i] = acc / L[(int64_t)i * din + i];
+        }
+      }
+      double nx = 0.0;
+      for (int i = 0; i < din; ++i) {
+        const double si = dis[map[(int64_t)elems[s] * din + i]];  // > 0 on interior elements
+        const double xi = si * r[i];
+        u[i] = xi;
+        t[i] /= si;
+        nx += xi * xi;
+      }
+      nx = sqrt(nx);
+      const double inv = nx > 0.0 ? 1.0 / nx : 0.0;
+      for (int i = 0; i < din; ++i) {
+        Xs[row * din + i] = __float2bfloat16((float)(u[i] * inv));
+        Ts[row * din + i] = (float)(t[i] * inv);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// batch rows gathered from the sample set by a hashed index per (step, row)
+__global__ void k_batch(const __nv_bfloat16* __restrict__ Xs, const float* __restrict__ Ts,
+                        int64_t nsamp, int din, int batch, uint64_t key,
+                        __nv_bfloat16* __restrict__ Xb, float* __restrict__ Tb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)batch * din) return;
+  const int b = (int)(i / din), c = (int)(i % din);
+  const int64_t src = (int64_t)(mix64(key + (uint64_t)b) % (uint64_t)nsamp);
+  Xb[i] = Xs[src * din + c];
+  Tb[i] = Ts[src * din + c];
+}
+
+// sum (y - t)^2 and sum t^2 (atomics into red[0], red[1])
+__global__ void k_loss_terms(const float* __restrict__ Y, const float* __restrict__ T, int64_t n,
+                             double* __restrict__ red) {
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)Y[i] - (double)T[i];
+    a += d * d;
+    b += (double)T[i] * (double)T[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&red[0], a);
+    atomicAdd(&red[1], b);
+  }
+}
+
+__global__ void k_dY(const float* __restrict__ Y, const float* __restrict__ T, int64_t n,
+                     const double* __restrict__ red, __nv_bfloat16* __restrict__ dY) {
+  const float sc = (float)(2.0 / red[1]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dY[i] = __float2bfloat16(sc * (Y[i] - T[i]));
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2, __nv_bfloat16* __restrict__ wb) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16(wi);
+  }
+}
+
+// preconditioner input rows: x_e = F r on the element (F = W S), scaled to unit norm
+__global__ void k_lpc_gather(const double* __restrict__ r, const int32_t* __restrict__ map,
+                             const double* __restrict__ fsc,
+                             int64_t e0, int64_t nrows, int din, __nv_bfloat16* __restrict__ X,
+                             float* __restrict__ scale) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= nrows) return;
+  const int32_t* m = map + (e0 + row) * din;
+  double ss = 0.0;
+  for (int a = lane; a < din; a += 32) {
+    const double xi = fsc[m[a]] * r[m[a]];
+    ss += xi * xi;
+  }
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const double s = sqrt(ss);
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  for (int a = lane; a < din; a += 32)
+    X[row * din + a] = __float2bfloat16((float)(fsc[m[a]] * r[m[a]] * inv));
+  if (lane == 0) scale[row] = (float)s;
+}
+
+__global__ void k_lpc_scatter(const float* __restrict__ Y, const float* __restrict__ scale,
+                              const int32_t* __restrict__ map, const double* __restrict__ fsc,
+                              int64_t e0, int64_t nrows, int din, double* __restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * din) return;
+  const int64_t row = i / din;
+  const int32_t g = map[(e0 + row) * din + (i % din)];
+  const double w = fsc[g];
+  if (w != 0.0) atomicAdd(&z[g], w * (double)scale[row] * (double)Y[i]);
+}
+
+unsigned int grid1(int64_t n) {
+  int64_t g = (n + kT - 1) / kT;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned int)(g < 1 ? 1 : g);
+}
+
+int ensure_workspace(fe_lpc* L, int64_t rows) {
+  if (rows <= L->cap) return FE_OK;
+  cudaFree(L->Xb); cudaFree(L->H1b); cudaFree(L->H2b); cudaFree(L->dYb); cudaFree(L->dA1b);
+  cudaFree(L->dA2b); cudaFree(L->Z1); cudaFree(L->Z2); cudaFree(L->Y); cudaFree(L->Tb);
+  cudaFree(L->scale);
+  L->cap = 0;
+  const int64_t w = L->width, d = L->din;
+  cudaError_t err;
+  if ((err = cudaMalloc(&L->Xb, 2 * rows * d)) != cudaSuccess ||
+      (err = cudaMalloc(&L->H1b, 2 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->H2b, 2 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->dYb, 2 * rows * d)) != cudaSuccess ||
+      (err = cudaMalloc(&L->dA1b, 2 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->dA2b, 2 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->Z1, 4 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->Z2, 4 * rows * w)) != cudaSuccess ||
+      (err = cudaMalloc(&L->Y, 4 * rows * d)) != cudaSuccess ||
+      (err = cudaMalloc(&L->Tb, 4 * rows * d)) != cudaSuccess ||
+      (err = cudaMalloc(&L->scale, 4 * rows)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc: workspace cudaMalloc");
+  L->cap = rows;
+  return FE_OK;
+}
+
+// Y = f(X) for `rows` rows already in L->Xb; the pre-activations Z1, Z2 are kept for the
+// backward pass only when keep is set.
+int mlp_forward(fe_lpc* L, int64_t rows, cudaStream_t s, bool keep = true) {
+  const int d = L->din, w = L->width;
+  const __nv_bfloat16* W1 = L->wb;
+  const __nv_bfloat16* W2 = W1 + (int64_t)d * w;
+  const __nv_bfloat16* W3 = W2 + (int64_t)w * w;
+  const __nv_bfloat16* W0 = W3 + (int64_t)w * d;
+  cudaError_t err;
+  if ((err = mlp::gemm<false, false, mlp::EPI_RELU_BF16>((int)rows, w, d, L->Xb, d, W1, w, keep ? L->Z1 : nullptr, w,
+                                                         L->H1b, w, s)) != cudaSuccess ||
+      (err = mlp::gemm<false, false, mlp::EPI_RELU_BF16>((int)rows, w, w, L->H1b, w, W2, w, keep ? L->Z2 : nullptr, w,
+                                                         L->H2b, w, s)) != cudaSuccess ||
+      (err = mlp::gemm<false, false, mlp::EPI_STORE>((int)rows, d, w, L->H2b, w, W3, d, L->Y, d,
+                                                     nullptr, 0, s)) != cudaSuccess ||
+      (err = mlp::gemm<false, false, mlp::EPI_ACCUM>((int)rows, d, d, L->Xb, d, W0, d, L->Y, d,
+                                                     nullptr, 0, s)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc: forward launch");
+  return FE_OK;
+}
+
+// loss and gradient (into L->grad) of the batch in L->Xb / L->Tb
+int mlp_loss_grad(fe_lpc* L, int64_t rows, cudaStream_t s, double* loss_out) {
+  int st = mlp_forward(L, rows, s);
+  if (st != FE_OK) return st;
+  const int d = L->din, w = L->width;
+  const __nv_bfloat16* W2 = L->wb + (int64_t)d * w;
+  const __nv_bfloat16* W3 = W2 + (int64_t)w * w;
+  float* g1 = L->grad;
+  float* g2 = g1 + (int64_t)d * w;
+  float* g3 = g2 + (int64_t)w * w;
+  float* g0 = g3 + (int64_t)w * d;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(L->red, 0, 2 * sizeof(double), s)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc: reduction");
+  k_loss_terms<<<grid1(rows * d), kT, 0, s>>>(L->Y, L->Tb, rows * d, L->red);
+  k_dY<<<grid1(rows * d), kT, 0, s>>>(L->Y, L->Tb, rows * d, L->red, L->dYb);
+  if ((err = cudaGetLastError()) != cudaSuccess ||
+      (err = mlp::gemm<true, false, mlp::EPI_STORE>(w, d, (int)rows, L->H2b, w, L->dYb, d, g3, d,
+                                                    nullptr, 0, s)) != cudaSuccess ||
+      (err = mlp::gemm<false, true, mlp::EPI_RELU_MASK_BF16>((int)rows, w, d, L->dYb, d, W3, d,
+                                                             L->Z2, w, L->dA2b, w, s)) != cudaSuccess ||
+      (err = mlp::gemm<true, false, mlp::EPI_STORE>(w, w, (int)rows, L->H1b, w, L->dA2b, w, g2, w,
+                                                    nullptr, 0, s)) != cudaSuccess ||
+      (err = mlp::gemm<false, true, mlp::EPI_RELU_MASK_BF16>((int)rows, w, w, L->dA2b, w, W2, w,
+                                                             L->Z1, w, L->dA1b, w, s)) != cudaSuccess ||
+      (err = mlp::gemm<true, false, mlp::EPI_STORE>(d, w, (int)rows, L->Xb, d, L->dA1b, w, g1, w,
+                                                    nullptr, 0, s)) != cudaSuccess ||
+      (err = mlp::gemm<true, false, mlp::EPI_STORE>(d, d, (int)rows, L->Xb, d, L->dYb, d, g0, d,
+                                                    nullptr, 0, s)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc: backward launch");
+  if (loss_out) {
+    double h[2];
+    if ((err = cudaMemcpyAsync(h, L->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_lpc: loss");
+    *loss_out = h[1] > 0.0 ? h[0] / h[1] : 0.0;
+  }
+  return FE_OK;
+}
+
+// ---- flexible CG
+constexpr int kRB = 1024;  // reduction blocks (of kT threads); partials reduced by one block
+
+enum { S_PQ = 0, S_PR, S_RR, S_ZQ, S_ZR, S_BB, S_ALPHA, S_BETA, S_TRUE, S_N };
+
+__device__ __forceinline__ void block_partial2(double a, double b, double* pa, double* pb) {
+  __shared__ double sa[kT / 32], sb[kT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x / 32;
+  if ((threadIdx.x & 31) == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int i = 0; i < kT / 32; ++i) {
+      ta += sa[i];
+      tb += sb[i];
+    }
+    pa[blockIdx.x] = ta;
+    pb[blockIdx.x] = tb;
+  }
+}
+
+// fixed-order sum of kRB partials by one block of kRB threads
+__device__ __forceinline__ double finish_sum(const double* part) {
+  __shared__ double sh[kRB];
+  sh[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int h = kRB / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+// r = (1-m) b, x = 0; partial ||r||^2
+__global__ void __launch_bounds__(kT) k_fcg_init(const double* __restrict__ b,
+                                                 const uint8_t* __restrict__ mask,
+                                                 double* __restrict__ x, double* __restrict__ r,
+                                                 int64_t n, double* part0, double* part1) {
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = mask[i] ? 0.0 : b[i];
+    r[i] = ri;
+    x[i] = 0.0;
+    a = fma(ri, ri, a);
+  }
+  block_partial2(a, 0.0, part0, part1);
+}
+
+// q masked on the boundary; partials p.q and p.r
+__global__ void __launch_bounds__(kT) k_fcg_pq(const double* __restrict__ p, double* __restrict__ q,
+                                               const double* __restrict__ r,
+                                               const uint8_t* __restrict__ mask, int64_t n,
+                                               double* part0, double* part1) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double qi = q[i];
+    if (mask[i]) {
+      qi = 0.0;
+      q[i] = 0.0;
+    }
+    a = fma(p[i], qi, a);
+    c = fma(p[i], r[i], c);
+  }
+  block_partial2(a, c, part0, part1);
+}
+
+// x += alpha p, r -= alpha q; partial ||r||^2
+__global__ void __launch_bounds__(kT) k_fcg_xr(double* __restrict__ x, double* __restrict__ r,
+                                               const double* __restrict__ p,
+                                               const double* __restrict__ q, int64_t n,
+                                               const double* sc, double* part0, double* part1) {
+  const double alpha = sc[S_ALPHA];
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    a = fma(ri, ri, a);
+  }
+  block_partial2(a, 0.0, part0, part1);
+}
+
+// partials z.q and z.r
+__global__ void __launch_bounds__(kT) k_fcg_zq(const double* __restrict__ z,
+                                               const double* __restrict__ q,
+                                               const double* __restrict__ r, int64_t n,
+                                               double* part0, double* part1) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a = fma(z[i], q[i], a);
+    c = fma(z[i], r[i], c);
+  }
+  block_partial2(a, c, part0, part1);
+}
+
+// which: 0 init (bb, rr), 1 after p.q (alpha), 2 after the update (rr), 3 after z.q (beta)
+__global__ void __launch_bounds__(kRB) k_fcg_finish(const double* part0, const double* part1,
+                                                    double* sc, int which) {
+  const double a = finish_sum(part0), b = finish_sum(part1);
+  if (threadIdx.x != 0) return;
+  if (which == 0) {
+    sc[S_BB] = a;
+    sc[S_RR] = a;
+  } else if (which == 1) {
+    sc[S_PQ] = a;
+    sc[S_PR] = b;
+    sc[S_ALPHA] = a != 0.0 ? b / a : 0.0;
+  } else if (which == 2) {
+    sc[S_RR] = a;
+  } else if (which == 3) {
+    sc[S_ZQ] = a;
+    sc[S_ZR] = b;
+    sc[S_BETA] = sc[S_PQ] != 0.0 ? -a / sc[S_PQ] : 0.0;
+  } else {
+    sc[S_TRUE] = a;
+    sc[S_BB] = b;
+  }
+}
+
+// z = dinv r (Jacobi; dinv is 0 on the boundary)
+__global__ void __launch_bounds__(kT) k_fcg_jacobi(const double* __restrict__ dinv,
+                                                   const double* __restrict__ r,
+                                                   double* __restrict__ z, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = dinv[i] * r[i];
+}
+
+// p = z + beta p (beta from sc, or 0 for a restart)
+__global__ void __launch_bounds__(kT) k_fcg_p(double* __restrict__ p, const double* __restrict__ z,
+                                              int64_t n, const double* sc, int restart) {
+  const double beta = restart ? 0.0 : sc[S_BETA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+// partials ||(1-m)(b - q)||^2 and ||(1-m) b||^2
+__global__ void __launch_bounds__(kT) k_fcg_resid(const double* __restrict__ b,
+                                                  const double* __restrict__ q,
+                                                  const uint8_t* __restrict__ mask, int64_t n,
+                                                  double* part0, double* part1) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask[i]) continue;
+    const double d = b[i] - q[i];
+    a = fma(d, d, a);
+    c = fma(b[i], b[i], c);
+  }
+  block_partial2(a, c, part0, part1);
+}
+
+// r restricted to the sample elements -> out[s][a]
+__global__ void k_snap(const double* __restrict__ r, const int32_t* __restrict__ map,
+                       const int32_t* __restrict__ elems, int ns, int din,
+                       double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)ns * din) return;
+  out[i] = r[map[(int64_t)elems[i / din] * din + (i % din)]];
+}
+
+struct Snapshots {  // residual snapshots at the listed iterations (training data)
+  const int32_t* elems = nullptr;
+  int ns = 0, din = 0;
+  std::vector<int> at;  // iterations, ascending
+  double* out = nullptr;  // [at.size()][ns][din]
+};
+
+struct FcgResult {
+  int iters = 0, launches = 0, restarts = 0, status = FE_OK;
+  double rel = 0.0, true_rel = 0.0;
+};
+
+// FCG from x = 0; lpc == nullptr => Jacobi throughout.  Synchronous.
+int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b, double* x,
+            double rtol, int maxit, Snapshots* snap, cudaStream_t s, FcgResult* res) {
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  const uint8_t* mask = m->d_mask;
+  double *vec = nullptr, *red = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&vec, sizeof(double) * 4 * n)) != cudaSuccess ||
+      (err = cudaMalloc(&red, sizeof(double) * (2 * kRB + S_N))) != cudaSuccess) {
+    cudaFree(vec);
+    return cuda_error(err, "fe_fcg: workspace cudaMalloc");
+  }
+  double *r = vec, *z = vec + n, *p = vec + 2 * n, *q = vec + 3 * n;
+  double *part0 = red, *part1 = red + kRB, *sc = red + 2 * kRB;
+  int st = FE_OK;
+  bool learned = lpc != nullptr;
+  size_t next_snap = 0;
+  auto precond = [&]() -> int {
+    res->launches += learned ? 5 : 1;
+    if (learned) return fe::lpc_apply(lpc, r, z, s);
+    k_fcg_jacobi<<<kRB, kT, 0, s>>>(dinv, r, z, n);
+    return FE_OK;
+  };
+  auto take_snap = [&](int it) {
+    if (!snap) return;
+    while (next_snap < snap->at.size() && snap->at[next_snap] == it) {
+      k_snap<<<(unsigned int)(((int64_t)snap->ns * snap->din + kT - 1) / kT), kT, 0, s>>>(
+          r, m->d_map, snap->elems, snap->ns, snap->din,
+          snap->out + (int64_t)next_snap * snap->ns * snap->din);
+      ++next_snap;
+    }
+  };
+  double hsc[S_N];
+  auto read_sc = [&]() -> int {
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(e, "fe_fcg: iteration");
+    return FE_OK;
+  };
+  cudaMemsetAsync(sc, 0, sizeof(double) * S_N, s);
+  k_fcg_init<<<kRB, kT, 0, s>>>(b, mask, x, r, n, part0, part1);
+  k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 0);
+  res->launches += 2;
+  take_snap(0);
+  if ((st = precond()) == FE_OK) {
+    k_fcg_zq<<<kRB, kT, 0, s>>>(z, r, r, n, part0, part1);  // z.r (twice)
+    k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 3);
+    res->launches += 2;
+    st = read_sc();
+  }
+  if (st == FE_OK && learned && hsc[S_BB] > 0.0 && !(hsc[S_ZR] > 0.0)) {
+    learned = false;  // not a descent direction: Jacobi from the start
+    ++res->restarts;
+    st = precond();
+  }
+  if (st == FE_OK) {
+    k_fcg_p<<<kRB, kT, 0, s>>>(p, z, n, sc, 1);
+    ++res->launches;
+  }
+  const double bb = hsc[S_BB];
+  double rel = 1.0, best = 1.0;
+  int last_gain = 0;
+  res->status = FE_ERR_NOT_CONVERGED;
+  if (st == FE_OK && !(bb > 0.0)) {
+    res->status = isfinite(bb) ? FE_OK : FE_ERR_NAN;
+    rel = 0.0;
+  }
+  for (int it = 1; st == FE_OK && res->status == FE_ERR_NOT_CONVERGED && it <= maxit; ++it) {
+    if ((st = apply_dispatch(pa, op, pa->variant, p, q, s)) != FE_OK) break;
+    k_fcg_pq<<<kRB, kT, 0, s>>>(p, q, r, mask, n, part0, part1);
+    k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 1);
+    k_fcg_xr<<<kRB, kT, 0, s>>>(x, r, p, q, n, sc, part0, part1);
+    k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 2);
+    res->launches += 5;
+    take_snap(it);
+    if ((st = precond()) != FE_OK) break;
+    k_fcg_zq<<<kRB, kT, 0, s>>>(z, q, r, n, part0, part1);
+    k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 3);
+    res->launches += 2;
+    if ((st = read_sc()) != FE_OK) break;
+    res->iters = it;
+    rel = sqrt(hsc[S_RR] / bb);
+    if (!isfinite(rel) || !isfinite(hsc[S_PQ])) {
+      res->status = FE_ERR_NAN;
+      break;
+    }
+    if (!(hsc[S_PQ] > 0.0)) {
+      res->status = FE_ERR_BREAKDOWN;
+      break;
+    }
+    if (rel <= rtol) {
+      res->status = FE_OK;
+      break;
+    }
+    if (rel < 0.99 * best) {
+      best = rel;
+      last_gain = it;
+    } else if (rel < best) {
+      best = rel;
+    }
+    bool restart = false;
+    if (learned && (!(hsc[S_ZR] > 0.0) || it - last_gain >= 100)) {
+      learned = false;  // fall back to Jacobi from the current iterate
+      restart = true;
+      ++res->restarts;
+      last_gain = it;
+      if ((st = precond()) != FE_OK) break;
+    }
+    k_fcg_p<<<kRB, kT, 0, s>>>(p, z, n, sc, restart ? 1 : 0);
+    ++res->launches;
+  }
+  res->rel = rel;
+  if (st == FE_OK) {  // true residual with the handle's operator
+    if ((st = apply_dispatch(pa, op, pa->variant, x, q, s)) == FE_OK) {
+      k_fcg_resid<<<kRB, kT, 0, s>>>(b, q, mask, n, part0, part1);
+      k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
+      res->launches += 3;
+      if ((st = read_sc()) == FE_OK)
+        res->true_rel = hsc[S_BB] > 0.0 ? sqrt(hsc[S_TRUE] / hsc[S_BB]) : 0.0;
+    }
+  }
+  cudaFree(vec);
+  cudaFree(red);
+  return st;
+}
+
+// Training data (first call of fe_lpc_train): probing, Cholesky, residual snapshots, samples.
+int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
+  fe_mesh* m = const_cast<fe_mesh*>(L->pa->mesh);
+  const int din = L->din;
+  std::vector<int32_t> el;
+  for (int ez = 1; ez + 1 < m->nz; ez += 3)
+    for (int ey = 1; ey + 1 < m->ny; ey += 3)
+      for (int ex = 1; ex + 1 < m->nx; ex += 3)
+        el.push_back((int32_t)(ex + (int64_t)m->nx * (ey + (int64_t)m->ny * ez)));
+  if (el.empty())
+    return set_error(FE_ERR_ARG, "fe_lpc_train: mesh too small (needs >= 3 elements per axis)");
+  const int64_t cap = kProbeDoubles / ((int64_t)din * din);
+  if ((int64_t)el.size() > cap) {  // keep an evenly strided subset
+    std::vector<int32_t> sub;
+    for (int64_t i = 0; i < cap; ++i) sub.push_back(el[(size_t)(i * (int64_t)el.size() / cap)]);
+    el.swap(sub);
+  }
+  const int ns = (int)el.size();
+  const int hi = (L->pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  int32_t* d_el = nullptr;
+  double *v = nullptr, *w = nullptr, *Aee = nullptr, *Afull = nullptr, *snapbuf = nullptr;
+  int* d_fail = nullptr;
+  Snapshots snap;
+  snap.at = {0, 1, 2, 4, 8, 16, 32, 64};
+  const int nsnap = 2 * (int)snap.at.size();  // two right-hand sides
+  cudaError_t err;
+  const size_t mat = (size_t)ns * din * din;
+  if ((err = cudaMalloc(&d_el, sizeof(int32_t) * ns)) != cudaSuccess ||
+      (err = cudaMalloc(&v, sizeof(double) * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&w, sizeof(double) * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&Aee, sizeof(double) * mat)) != cudaSuccess ||
+      (err = cudaMalloc(&Afull, sizeof(double) * mat)) != cudaSuccess ||
+      (err = cudaMalloc(&snapbuf, sizeof(double) * nsnap * ns * din)) != cudaSuccess ||
+      (err = cudaMalloc(&d_fail, sizeof(int))) != cudaSuccess) {
+    cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(Afull); cudaFree(snapbuf);
+    cudaFree(d_fail);
+    return cuda_error(err, "fe_lpc_train: sample cudaMalloc");
+  }
+  int st = FE_OK;
+  cudaMemcpyAsync(d_el, el.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, s);
+  // snapshots a short run never reaches stay zero (zero rows add nothing to loss or gradient)
+  cudaMemsetAsync(snapbuf, 0, sizeof(double) * nsnap * ns * din, s);
+  cudaMemsetAsync(d_fail, 0, sizeof(int), s);
+  for (int a = 0; a < din && st == FE_OK; ++a) {
+    cudaMemsetAsync(v, 0, sizeof(double) * m->ndofs, s);
+    k_probe_set<<<(ns + kT - 1) / kT, kT, 0, s>>>(v, m->d_map, d_el, ns, din, a);
+    st = apply_dispatch(L->pa, L->op, hi, v, w, s);
+    if (st != FE_OK) break;
+    k_probe_get<<<(unsigned int)(((int64_t)ns * din + kT - 1) / kT), kT, 0, s>>>(w, m->d_map, d_el,
+                                                                                  ns, din, a, Aee);
+  }
+  // residual snapshots of Jacobi-FCG on the sine load and on a random right-hand side
+  snap.elems = d_el;
+  snap.ns = ns;
+  snap.din = din;
+  for (int rhs = 0; rhs < 2 && st == FE_OK; ++rhs) {
+    if (rhs == 0)
+      st = fe_load_vector_sine(L->pa, v, s);
+    else
+      k_normal_vec<<<grid1(m->ndofs), kT, 0, s>>>(v, m->ndofs, L->seed ^ 0x5DEECE66Dull);
+    if (st != FE_OK) break;
+    snap.out = snapbuf + (int64_t)rhs * snap.at.size() * ns * din;
+    FcgResult fr;
+    st = fcg_run(L->pa, L->op, nullptr, L->dinv, v, w, 0.0, snap.at.back(), &snap, s, &fr);
+  }
+  if (st == FE_OK) {
+    cudaMemcpyAsync(Afull, Aee, sizeof(double) * mat, cudaMemcpyDeviceToDevice, s);
+    const size_t shm = sizeof(double) * din * din;
+    cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_cholesky<<<ns, 128, shm, s>>>(Aee, din, d_fail);
+    L->nsamp = (int64_t)ns * reps;
+    if ((err = cudaMalloc(&L->Xs, sizeof(__nv_bfloat16) * L->nsamp * din)) != cudaSuccess ||
+        (err = cudaMalloc(&L->Ts, sizeof(float) * L->nsamp * din)) != cudaSuccess)
+      st = cuda_error(err, "fe_lpc_train: sample cudaMalloc");
+  }
+  if (st == FE_OK) {
+    k_samples<<<ns, 64, sizeof(double) * 3 * din, s>>>(Aee, Afull, snapbuf, nsnap, m->d_map, d_el,
+                                                       L->dis, L->wsq, ns, din, reps, L->seed,
+                                                       L->Xs, L->Ts);
+    int fail = 0;
+    if ((err = cudaGetLastError()) != cudaSuccess ||
+        (err = cudaMemcpyAsync(&fail, d_fail, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      st = cuda_error(err, "fe_lpc_train: samples");
+    else if (fail)
+      st = set_error(FE_ERR_BREAKDOWN, "fe_lpc_train: an element block is not positive definite");
+  }
+  if (st != FE_OK) L->nsamp = 0;
+  cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(Afull); cudaFree(snapbuf);
+  cudaFree(d_fail);
+  return st;
+}
+
+}  // namespace
+
+namespace {
+
+constexpr size_t kMaxSmem = 232448;  // 227 KB per block (opt-in)
+
+template <int DP, int W>
+cudaError_t fused_launch(const fe_lpc* L, const double* r, double* z, int grid, cudaStream_t s) {
+  if constexpr (mlp::FusedLayout<DP, W>::SMEM <= kMaxSmem) {
+    const fe_mesh* m = L->pa->mesh;
+    mlp::k_lpc_fused<DP, W><<<grid, 256, mlp::FusedLayout<DP, W>::SMEM, s>>>(
+        reinterpret_cast<const uint4*>(L->wimg), r, m->d_map, L->fsc, m->ne, L->din, z);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+// Blocks per SM of the fused kernel for (DP, W), 0 if it is not built or does not fit.
+template <int DP, int W>
+int fused_occupancy() {
+  if constexpr (mlp::FusedLayout<DP, W>::SMEM <= kMaxSmem) {
+    const int smem = (int)mlp::FusedLayout<DP, W>::SMEM;
+    if (cudaFuncSetAttribute(mlp::k_lpc_fused<DP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+      return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp::k_lpc_fused<DP, W>, 256, smem) !=
+        cudaSuccess)
+      return 0;
+    return occ;
+  }
+  return 0;
+}
+
+// The built (DP, W) pairs of the fused kernel.
+#define FE_FUSED_CASES(X) \
+  X(16, 64) X(16, 128) X(16, 256) X(32, 64) X(32, 128) X(32, 256) X(64, 64) X(64, 128) \
+  X(64, 256) X(128, 64) X(128, 128)
+
+int fused_occ(int DP, int W) {
+#define FE_OCC_CASE(dp, w) \
+  if (DP == dp && W == w) return fused_occupancy<dp, w>();
+  FE_FUSED_CASES(FE_OCC_CASE)
+#undef FE_OCC_CASE
+  return 0;
+}
+
+cudaError_t fused_run(const fe_lpc* L, const double* r, double* z, cudaStream_t s) {
+  const int DP = mlp::fused_dp(L->din), W = L->width;
+#define FE_RUN_CASE(dp, w) \
+  if (DP == dp && W == w) return fused_launch<dp, w>(L, r, z, L->fused_grid, s);
+  FE_FUSED_CASES(FE_RUN_CASE)
+#undef FE_RUN_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+// Chooses the fused kernel when one is built for (D^3, width) and fits in shared memory.
+void fused_setup(fe_lpc* L) {
+  L->fused_grid = 0;
+  const int DP = mlp::fused_dp(L->din);
+  const int occ = fused_occ(DP, L->width);
+  if (occ <= 0) return;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return;
+  int64_t off[5];
+  mlp::fused_offsets(DP, L->width, off);
+  if (cudaMalloc(&L->wimg, sizeof(__nv_bfloat16) * off[4]) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int64_t tiles = (L->pa->mesh->ne + 15) / 16;
+  const int64_t want = (tiles + 7) / 8;
+  const int64_t cap = (int64_t)sms * occ;
+  L->fused_grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+}  // namespace
+
+namespace fe {
+// z = M(r): the learned additive patch preconditioner (z overwritten).
+int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
+  const fe_mesh* m = L->pa->mesh;
+  const int din = L->din;
+  if (L->fused_grid > 0) {
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+      return cuda_error(err, "fe_lpc_apply: zero z");
+    const int DP = mlp::fused_dp(din);
+    if (!L->wimg_ok) {
+      int64_t off[5];
+      mlp::fused_offsets(DP, L->width, off);
+      mlp::k_pack_wimg<<<grid1(off[4]), kT, 0, s>>>(L->w32, din, L->width, DP, L->wimg);
+      L->wimg_ok = true;
+    }
+    return cuda_error(fused_run(L, r, z, s), "fe_lpc_apply: fused launch");
+  }
+  const int64_t chunk = m->ne < (1 << 18) ? m->ne : (1 << 18);  // rows per pass
+  int st = ensure_workspace(L, chunk);
+  if (st != FE_OK) return st;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_apply: zero z");
+  for (int64_t e0 = 0; e0 < m->ne; e0 += chunk) {
+    const int64_t rows = (m->ne - e0) < chunk ? (m->ne - e0) : chunk;
+    k_lpc_gather<<<(unsigned int)((rows + 7) / 8), 256, 0, s>>>(r, m->d_map, L->fsc, e0, rows, din,
+                                                               L->Xb, L->scale);
+    if ((st = mlp_forward(L, rows, s, false)) != FE_OK) return st;
+    k_lpc_scatter<<<(unsigned int)((rows * din + kT - 1) / kT), kT, 0, s>>>(L->Y, L->scale, m->d_map,
+                                                                           L->fsc, e0, rows, din, z);
+  }
+  return cuda_error(cudaGetLastError(), "fe_lpc_apply launch");
+}
+}  // namespace fe
+
+extern "C" {
+
+int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
+  clear_error();
+  if (!out) return set_error(FE_ERR_ARG, "fe_lpc_create: out is NULL");
+  *out = nullptr;
+  if (!pa) return set_error(FE_ERR_ARG, "fe_lpc_create: pa is NULL");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_lpc_create: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_lpc_create: operator not set up");
+  if (width < 8 || width > 4096) return set_error(FE_ERR_ARG, "fe_lpc_create: width out of range");
+  if (pa->p > kLpcMaxOrder)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_create: orders above 4 are not built");
+  fe_lpc* L = new fe_lpc();
+  L->pa = pa;
+  L->op = op;
+  L->din = pa->D * pa->D * pa->D;
+  L->width = width;
+  L->seed = seed;
+  L->nparam = 2LL * L->din * width + (int64_t)width * width + (int64_t)L->din * L->din;
+  const fe_mesh* m = pa->mesh;
+  cudaStream_t s = 0;
+  cudaError_t err;
+  if ((err = cudaMalloc(&L->w32, 4 * L->nparam)) != cudaSuccess ||
+      (err = cudaMalloc(&L->wb, 2 * L->nparam)) != cudaSuccess ||
+      (err = cudaMalloc(&L->adam_m, 4 * L->nparam)) != cudaSuccess ||
+      (err = cudaMalloc(&L->adam_v, 4 * L->nparam)) != cudaSuccess ||
+      (err = cudaMalloc(&L->grad, 4 * L->nparam)) != cudaSuccess ||
+      (err = cudaMalloc(&L->wsq, 8 * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&L->dinv, 8 * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&L->dis, 8 * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&L->fsc, 8 * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&L->red, 16)) != cudaSuccess) {
+    fe_lpc_destroy(L);
+    return cuda_error(err, "fe_lpc_create: cudaMalloc");
+  }
+  cudaMemsetAsync(L->adam_m, 0, 4 * L->nparam, s);
+  cudaMemsetAsync(L->adam_v, 0, 4 * L->nparam, s);
+  k_init_weights<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->din, width, seed);
+  k_to_bf16<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->wb, L->nparam);
+  cudaMemsetAsync(L->wsq, 0, 8 * m->ndofs, s);
+  k_count<<<grid1(m->ne * L->din), kT, 0, s>>>(m->d_map, m->ne * L->din, L->wsq);
+  k_wsq<<<grid1(m->ndofs), kT, 0, s>>>(L->wsq, m->d_mask, m->ndofs);
+  int st = fe_assemble_diagonal(pa, op, L->dinv, s);
+  if (st == FE_OK) {
+    k_invert_diag<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, m->d_mask, m->ndofs);
+    k_sqrt_vec<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, L->dis, L->wsq, L->fsc, m->ndofs);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) st = cuda_error(err, "fe_lpc_create");
+  }
+  if (st != FE_OK) {
+    fe_lpc_destroy(L);
+    return st;
+  }
+  fused_setup(L);
+  *out = L;
+  return FE_OK;
+}
+
+int fe_lpc_train(fe_lpc* L, int steps, int batch, double lr, int reps, double* final_loss,
+                 void* stream) {
+  clear_error();
+  if (!L) return set_error(FE_ERR_ARG, "fe_lpc_train: NULL handle");
+  if (steps < 0 || batch < 1 || batch > (1 << 20) || !(lr > 0.0))
+    return set_error(FE_ERR_ARG, "fe_lpc_train: bad steps, batch (1..2^20) or lr");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  if (L->nsamp == 0 && (st = make_samples(L, reps > 0 ? reps : 16, s)) != FE_OK) return st;
+  if ((st = ensure_workspace(L, batch)) != FE_OK) return st;
+  const float b1 = 0.9f, b2 = 0.999f;
+  double loss = 0.0;
+  for (int it = 0; it < steps; ++it) {
+    const uint64_t key = L->seed * 0x9E3779B97F4A7C15ull + (uint64_t)(L->adam_t + 1) * 0x632BE59BD9B4E019ull;
+    k_batch<<<(unsigned int)(((int64_t)batch * L->din + kT - 1) / kT), kT, 0, s>>>(
+        L->Xs, L->Ts, L->nsamp, L->din, batch, key, L->Xb, L->Tb);
+    if ((st = mlp_loss_grad(L, batch, s, (it + 1 == steps) ? &loss : nullptr)) != FE_OK) return st;
+    ++L->adam_t;
+    const float c1 = 1.0f - powf(b1, (float)L->adam_t), c2 = 1.0f - powf(b2, (float)L->adam_t);
+    L->wimg_ok = false;
+    k_adam<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->grad, L->adam_m, L->adam_v, L->nparam,
+                                           (float)lr, b1, b2, 1e-8f, c1, c2, L->wb);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_error(err, "fe_lpc_train: step launch");
+  }
+  if (final_loss) *final_loss = loss;
+  return cuda_error(cudaStreamSynchronize(s), "fe_lpc_train");
+}
+
+int fe_lpc_weights(fe_lpc* L, float* host_w, int set) {
+  clear_error();
+  if (!L || !host_w) return set_error(FE_ERR_ARG, "fe_lpc_weights: null argument");
+  cudaError_t err;
+  if (set) {
+    if ((err = cudaMemcpy(L->w32, host_w, 4 * L->nparam, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_error(err, "fe_lpc_weights");
+    k_to_bf16<<<grid1(L->nparam), kT>>>(L->w32, L->wb, L->nparam);
+    L->wimg_ok = false;
+    return cuda_error(cudaDeviceSynchronize(), "fe_lpc_weights");
+  }
+  return cuda_error(cudaMemcpy(host_w, L->w32, 4 * L->nparam, cudaMemcpyDeviceToHost),
+                    "fe_lpc_weights");
+}
+
+int fe_lpc_loss_grad(fe_lpc* L, int batch, const float* host_x, const float* host_t,
+                     float* host_y, float* host_grad, double* loss) {
+  clear_error();
+  if (!L || !host_x || !host_t || batch < 1 || batch > (1 << 20))
+    return set_error(FE_ERR_ARG, "fe_lpc_loss_grad: bad arguments");
+  int st = ensure_workspace(L, batch);
+  if (st != FE_OK) return st;
+  const int64_t n = (int64_t)batch * L->din;
+  std::vector<__nv_bfloat16> xb(n);
+  for (int64_t i = 0; i < n; ++i) xb[i] = __float2bfloat16(host_x[i]);
+  cudaError_t err;
+  if ((err = cudaMemcpy(L->Xb, xb.data(), 2 * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(L->Tb, host_t, 4 * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_loss_grad: copy");
+  double l = 0.0;
+  if ((st = mlp_loss_grad(L, batch, 0, &l)) != FE_OK) return st;
+  if (host_y && (err = cudaMemcpy(host_y, L->Y, 4 * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_loss_grad: y");
+  if (host_grad &&
+      (err = cudaMemcpy(host_grad, L->grad, 4 * L->nparam, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_loss_grad: grad");
+  if (loss) *loss = l;
+  return FE_OK;
+}
+
+int fe_lpc_apply(fe_lpc* L, const double* dev_r, double* dev_z, void* stream) {
+  clear_error();
+  if (!L || !dev_r || !dev_z) return set_error(FE_ERR_ARG, "fe_lpc_apply: null argument");
+  return lpc_apply(L, dev_r, dev_z, (cudaStream_t)stream);
+}
+
+int fe_lpc_nparams(const fe_lpc* L, int64_t* n) {
+  clear_error();
+  if (!L || !n) return set_error(FE_ERR_ARG, "fe_lpc_nparams: null argument");
+  *n = L->nparam;
+  return FE_OK;
+}
+
+int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
+           int maxit, fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_fcg: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_fcg: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_fcg: operator not set up");
+  if (lpc && (lpc->pa != pa || lpc->op != op))
+    return set_error(FE_ERR_ARG, "fe_fcg: preconditioner built for another operator");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_fcg: bad rtol or maxit");
+  cudaStream_t s = (cudaStream_t)stream;
+  const fe_mesh* m = pa->mesh;
+  double* dinv = lpc ? lpc->dinv : nullptr;
+  double* own = nullptr;
+  int st = FE_OK;
+  FcgResult res;
+  if (!dinv) {
+    cudaError_t err = cudaMalloc(&own, sizeof(double) * m->ndofs);
+    if (err != cudaSuccess) return cuda_error(err, "fe_fcg: cudaMalloc");
+    dinv = own;
+    if ((st = fe_assemble_diagonal(pa, op, dinv, s)) == FE_OK) {
+      k_invert_diag<<<grid1(m->ndofs), kT, 0, s>>>(dinv, m->d_mask, m->ndofs);
+      res.launches += 2;
+    }
+  }
+  if (st == FE_OK) st = fcg_run(pa, op, lpc, dinv, dev_b, dev_x, rtol, maxit, nullptr, s, &res);
+  cudaFree(own);
+  if (st != FE_OK) return st;
+  if (stats) {
+    stats->iters = res.iters;
+    stats->rel_resid = res.rel;
+    stats->true_rel_resid = res.true_rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = res.launches;
+    stats->outer_iters = 1 + res.restarts;
+  }
+  switch (res.status) {
+    case FE_OK:
+      return FE_OK;
+    case FE_ERR_BREAKDOWN:
+      return set_error(FE_ERR_BREAKDOWN, "fe_fcg: p.Ap <= 0 (operator not SPD on the free dofs)");
+    case FE_ERR_NAN:
+      return set_error(FE_ERR_NAN, "fe_fcg: NaN or Inf in the iteration");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, "fe_fcg: maxit reached before rtol");
+  }
+}
+
+void fe_lpc_destroy(fe_lpc* L) {
+  if (!L) return;
+  cudaFree(L->w32); cudaFree(L->wb); cudaFree(L->adam_m); cudaFree(L->adam_v); cudaFree(L->grad);
+  cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->wimg); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
+  cudaFree(L->Xb); cudaFree(L->H1b); cudaFree(L->H2b); cudaFree(L->dYb); cudaFree(L->dA1b);
+  cudaFree(L->dA2b); cudaFree(L->Z1); cudaFree(L->Z2); cudaFree(L->Y); cudaFree(L->Tb);
+  cudaFree(L->scale);
+  delete L;
+}
+
+}  // extern "C"

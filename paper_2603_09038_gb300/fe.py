@@ -75,6 +75,18 @@ _SIGS = {
     "fe_pcg_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "fe_lpc_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.POINTER(_VP)]),
+    "fe_lpc_nparams": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "fe_lpc_train": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), _VP]),
+    "fe_lpc_weights": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                              ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_lpc_destroy": (None, [_VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -245,6 +257,85 @@ def fe_probe_throughput(unit):
     v = ctypes.c_double()
     _check(load().fe_probe_throughput(int(PROBE_UNITS.get(unit, unit)), ctypes.byref(v)))
     return v.value
+
+
+# ---------------------------------------------------- learned patch preconditioner and FCG
+
+def fe_lpc_create(pa, op, width=256, seed=0):
+    """Learned element-patch preconditioner for operator op of pa (see include/fe.h)."""
+    out = _VP()
+    _check(load().fe_lpc_create(_VP(pa), int(op), int(width), int(seed), ctypes.byref(out)))
+    return out.value
+
+
+def fe_lpc_nparams(lpc):
+    n = ctypes.c_int64()
+    _check(load().fe_lpc_nparams(_VP(lpc), ctypes.byref(n)))
+    return n.value
+
+
+def fe_lpc_train(lpc, steps, batch, lr, reps=0, stream=None):
+    """Adam steps on the patch training set (made on the first call); returns the last loss."""
+    loss = ctypes.c_double()
+    _check(load().fe_lpc_train(_VP(lpc), int(steps), int(batch), float(lr), int(reps),
+                               ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def _f32_host(a, n):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d floats, got %d" % (n, a.size))
+    return a
+
+
+def fe_lpc_weights(lpc, host_w=None):
+    """Returns the packed FP32 master weights (numpy), or sets them from host_w."""
+    import numpy as np
+    n = fe_lpc_nparams(lpc)
+    if host_w is None:
+        w = np.empty(n, dtype=np.float32)
+        _check(load().fe_lpc_weights(_VP(lpc), _VP(w.ctypes.data), 0))
+        return w
+    w = _f32_host(host_w, n)
+    _check(load().fe_lpc_weights(_VP(lpc), _VP(w.ctypes.data), 1))
+    return w
+
+
+def fe_lpc_loss_grad(lpc, X, T):
+    """(loss, Y, grad) of the BF16 tensor-core forward/backward pass on host rows X, T."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    if X.shape != T.shape or X.ndim != 2:
+        raise ValueError("X and T must be [batch, D^3] arrays of the same shape")
+    Y = np.empty_like(X)
+    g = np.empty(fe_lpc_nparams(lpc), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load().fe_lpc_loss_grad(_VP(lpc), X.shape[0], _VP(X.ctypes.data), _VP(T.ctypes.data),
+                                   _VP(Y.ctypes.data), _VP(g.ctypes.data), ctypes.byref(loss)))
+    return loss.value, Y, g
+
+
+def fe_lpc_apply(lpc, dev_r, dev_z, stream=None):
+    return _check(load().fe_lpc_apply(_VP(lpc), _ptr(dev_r), _ptr(dev_z), _stream(stream)))
+
+
+def fe_fcg(pa, op, lpc, dev_b, dev_x, rtol, maxit, stream=None):
+    """Flexible CG preconditioned by lpc (None => Jacobi); same return value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_fcg(_VP(pa), int(op), _VP(lpc) if lpc else None, _ptr(dev_b), _ptr(dev_x),
+                        float(rtol), int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
+
+
+def fe_lpc_destroy(lpc):
+    if lpc:
+        load().fe_lpc_destroy(_VP(lpc))
 
 
 def fe_pa_destroy(pa):

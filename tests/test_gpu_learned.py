@@ -1,0 +1,216 @@
+"""GPU learned patch preconditioner and flexible CG through the C ABI.
+
+* The BF16 tensor-core forward and backward passes (fe_lpc_loss_grad) against the FP64 oracle
+  (oracle/mlp.py, itself pinned by finite differences) on ragged shapes; the tolerance covers
+  the BF16 rounding of the activations and of the back-propagated signals (unit roundoff 2^-8 per
+  rounding, a few roundings deep, relative Frobenius error <= 3e-2) and is far below the O(1)
+  error of a transposed or dropped term.
+* The patch apply z = sum_e R_e^T W_e S_e s_e f(x_e / s_e), x_e = S_e W_e R_e r, S = diag(A)^(-1/2),
+  against the same sum written out in numpy with the oracle's MLP and the oracle's diagonal, on
+  the fused inference kernel and on the unfused GEMM path (a width whose weights exceed shared
+  memory).
+* Flexible CG: with Jacobi it equals PCG (iterations, solution vs the oracle's dense solve); with
+  zero weights it falls back to Jacobi; trained, it reaches the same FP64 residual as Jacobi-PCG
+  in fewer iterations.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_problem, torch_cuda
+from oracle import mlp as omlp
+from oracle import operator as oop
+from oracle.element import DIFFUSION
+from oracle.mesh import boundary_mask
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_round(a):
+    """Round-to-nearest-even of float32 values to bfloat16, returned as float64 (input prep)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unpack(w, din, width):
+    n1, n2 = din * width, width * width
+    n3 = n1 + n2 + width * din
+    return (w[:n1].reshape(din, width), w[n1:n1 + n2].reshape(width, width),
+            w[n1 + n2:n3].reshape(width, din), w[n3:].reshape(din, din))
+
+
+def rel_fro(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("p,width,batch", [(2, 40, 200), (3, 64, 130), (1, 16, 77)])
+def test_loss_grad_matches_oracle(p, width, batch):
+    with gpu_problem(2, 2, 2, p) as (fe, mesh, pa, V, c):
+        din = (p + 1) ** 3
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 7)
+        try:
+            assert fe.fe_lpc_nparams(lpc) == 2 * din * width + width * width + din * din
+            rng = np.random.default_rng(11 + p)
+            W = omlp.init_weights(din, width, 5 + p)[:3] + (0.2 * rng.standard_normal((din, din)),)
+            fe.fe_lpc_weights(lpc, np.concatenate([w.reshape(-1) for w in W]))
+            got = fe.fe_lpc_weights(lpc)
+            assert np.array_equal(got, np.concatenate([w.reshape(-1) for w in W]).astype(np.float32))
+            X = rng.standard_normal((batch, din)).astype(np.float32)
+            T = rng.standard_normal((batch, din)).astype(np.float32)
+            loss, Y, g = fe.fe_lpc_loss_grad(lpc, X, T)
+            Wb = tuple(bf16_round(w) for w in unpack(got, din, width))
+            Yr, _ = omlp.forward(Wb, bf16_round(X))
+            Lr, G = omlp.grad(Wb, bf16_round(X), T)
+            assert rel_fro(Y, Yr) <= 3e-2
+            assert abs(loss - Lr) <= 3e-2 * Lr
+            for gg, gr in zip(unpack(g.astype(np.float64), din, width), G):
+                assert rel_fro(gg, gr) <= 3e-2
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+@pytest.mark.parametrize("dims,p,width", [((4, 3, 3), 2, 32), ((5, 3, 2), 3, 256),
+                                          ((3, 3, 4), 1, 64), ((2, 3, 3), 4, 512)])
+def test_patch_apply_matches_numpy_sum(dims, p, width):
+    torch = torch_cuda()
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        n, ne, _ = fe.fe_mesh_sizes(mesh)
+        din = (p + 1) ** 3
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 3)
+        try:
+            w = fe.fe_lpc_weights(lpc)
+            w[-din * din:] = 0.1 * np.random.default_rng(8).standard_normal(din * din)
+            fe.fe_lpc_weights(lpc, w)
+            r = torch.from_numpy(np.random.default_rng(4).standard_normal(n)).cuda()
+            z = torch.empty_like(r)
+            fe.fe_lpc_apply(lpc, r, z)
+            z2 = torch.empty_like(r)
+            fe.fe_lpc_apply(lpc, 2.0 * r, z2)
+            torch.cuda.synchronize()
+            zg, z2g = z.cpu().numpy(), z2.cpu().numpy()
+            # the same map written out with the oracle's diagonal and MLP
+            mask = boundary_mask(*dims, p)
+            dis = np.where(mask == 1, 0.0, 1.0 / np.sqrt(oop.diagonal(prob, DIFFUSION)))
+            dmap = torch.empty(ne * din, dtype=torch.int32, device="cuda")
+            fe.fe_mesh_dof_map(mesh, dmap)
+            dmap = dmap.cpu().numpy().reshape(ne, din).astype(np.int64)
+            mult = np.bincount(dmap.reshape(-1), minlength=n).astype(np.float64)
+            wsq = np.where(mask == 1, 0.0, 1.0 / np.sqrt(mult))
+            Wb = tuple(bf16_round(x) for x in unpack(w, din, width))
+            rh = r.cpu().numpy()
+            xe = dis[dmap] * wsq[dmap] * rh[dmap]
+            s = np.linalg.norm(xe, axis=1)
+            Y, _ = omlp.forward(Wb, bf16_round(xe / s[:, None]))
+            zr = np.zeros(n)
+            np.add.at(zr, dmap.reshape(-1), (wsq[dmap] * dis[dmap] * s[:, None] * Y).reshape(-1))
+            assert rel_fro(zg, zr) <= 3e-2
+            assert np.all(zg[mask == 1] == 0.0)
+            # positively homogeneous: M(2r) = 2 M(r) up to the order of the atomic adds
+            assert np.abs(z2g - 2.0 * zg).max() <= 1e-12 * np.abs(zg).max()
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def _dense_solve(prob, b):
+    m = boundary_mask(prob.nx, prob.ny, prob.nz, prob.p).astype(np.float64)
+    keep = 1.0 - m
+    A = oop.assemble(prob, DIFFUSION).toarray()
+    Abc = keep[:, None] * A * keep[None, :] + np.diag(m)
+    return np.linalg.solve(Abc, b * keep)
+
+
+def test_fcg_jacobi_equals_pcg_and_oracle():
+    torch = torch_cuda()
+    dims, p = (5, 4, 4), 3
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x1, x2 = torch.empty_like(b), torch.empty_like(b)
+        st, s1 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x1, 1e-10, 5000)
+        assert st == fe.FE_OK
+        st, s2 = fe.fe_fcg(pa, fe.FE_DIFFUSION, None, b, x2, 1e-10, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert abs(s1["iters"] - s2["iters"]) <= 2, (s1["iters"], s2["iters"])
+        assert s2["rel_resid"] <= 1e-10 and s2["true_rel_resid"] <= 1e-9
+        assert s2["outer_iters"] == 1
+        xr = _dense_solve(prob, b.cpu().numpy())
+        xg = x2.cpu().numpy()
+        assert np.abs(xg - xr).max() <= 1e-8 * np.abs(xr).max()
+
+
+def test_fcg_zero_network_falls_back_to_jacobi():
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 2) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 16, 1)
+        try:
+            fe.fe_lpc_weights(lpc, np.zeros(fe.fe_lpc_nparams(lpc), dtype=np.float32))
+            st, s = fe.fe_fcg(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-10, 2000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert s["outer_iters"] == 2 and s["true_rel_resid"] <= 1e-9
+            st, sj = fe.fe_fcg(pa, fe.FE_DIFFUSION, None, b, x, 1e-10, 2000)
+            assert abs(s["iters"] - sj["iters"]) <= 2
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_lpc_argument_errors():
+    torch = torch_cuda()
+    with gpu_problem(2, 2, 2, 5) as (fe, mesh, pa, V, c):
+        with pytest.raises(fe.FEError) as e:
+            fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 64, 0)
+        assert e.value.status == fe.FE_ERR_UNSUPPORTED
+    with gpu_problem(2, 2, 2, 2, ops=1) as (fe, mesh, pa, V, c):
+        with pytest.raises(fe.FEError):
+            fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 4, 0)
+        with pytest.raises(fe.FEError):
+            fe.fe_lpc_create(pa, fe.FE_MASS, 32, 0)      # operator not set up
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 32, 0)
+        try:
+            with pytest.raises(fe.FEError) as e:           # fewer than 3 elements per axis
+                fe.fe_lpc_train(lpc, 1, 64, 1e-3)
+            assert e.value.status == fe.FE_ERR_ARG
+            with gpu_problem(3, 3, 3, 2) as (fe2, mesh2, pa2, V2, c2):
+                n, _, _ = fe.fe_mesh_sizes(mesh2)
+                b = torch.ones(n, dtype=torch.float64, device="cuda")
+                x = torch.empty_like(b)
+                with pytest.raises(fe.FEError):            # built for another handle
+                    fe.fe_fcg(pa2, fe.FE_DIFFUSION, lpc, b, x, 1e-8, 10)
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_trained_fcg_beats_jacobi_iterations(p):
+    """The gain test: trained on the operator's own patch solves, FCG reaches the same FP64
+    residual as Jacobi-PCG in fewer iterations, and the two solutions agree."""
+    torch = torch_cuda()
+    n = 12
+    with gpu_problem(n, n, n, p, sigma=2.0, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, "f32x2")
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        xj, xl = torch.empty_like(b), torch.empty_like(b)
+        st, sj = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xj, 1e-8, 20000)
+        assert st == fe.FE_OK
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 128, 2)
+        try:
+            l0 = fe.fe_lpc_train(lpc, 1, 512, 1e-3)
+            l1 = fe.fe_lpc_train(lpc, 600, 512, 1e-3)
+            assert l1 < 0.5 * l0, (l0, l1)
+            st, sl = fe.fe_fcg(pa, fe.FE_DIFFUSION, lpc, b, xl, 1e-8, 20000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert sl["true_rel_resid"] <= 1e-7
+            assert sl["outer_iters"] == 1, sl             # no fallback needed
+            assert sl["iters"] < sj["iters"], (sl, sj)
+            d = (xl - xj).abs().max().item() / xj.abs().max().item()
+            assert d <= 1e-6
+        finally:
+            fe.fe_lpc_destroy(lpc)
