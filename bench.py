@@ -12,7 +12,11 @@ Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the t
   ms_per_step  time of one PCG solve to 1e-8 (the metric's time-to-solution part);
   e2e          the same, through host buffers: pinned b -> device, fe_pcg, x -> pinned host;
   roofline     of the dominant kernel (the fused apply), timed alone with CUDA events;
-  cpu_baseline the CPU oracle (element-matrix apply) on a bounded sample of the same mesh.
+  cpu_baseline the CPU oracle (element-matrix apply) on a bounded sample of the same mesh;
+  pcg_ir       mixed-precision iterative refinement (FP32 inner PCG) to the same residual;
+  learned_fcg  the learned element-patch preconditioner (trained on the GPU from the operator's
+               own patch solves) inside flexible CG, to the same FP64 residual, against the
+               Jacobi-PCG time above, with its fused BF16 tensor-core kernel timed alone.
 
 --impl reference times the CPU oracle alone (the reference of this build) on the same metric.
 Multi-GPU (torchrun): every rank solves its own copy of the problem (independent problems, weak
@@ -298,6 +302,68 @@ def run_ours(args, rank, world, local_rank):
               "inner_operator": "f32"}
     launches_ir = sum(s_["launches"] for s_ in ir_stats)
 
+    # ---- learned patch preconditioner inside flexible CG, to the same FP64 1e-8 residual:
+    #      training (data generation from the operator + Adam) timed once on the host clock,
+    #      the solve timed like the PCG above, the fused preconditioner kernel alone
+    learned = None
+    if args.lpc_width > 0:
+        t0 = time.perf_counter()
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, args.lpc_width, 1)
+        loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+
+        def solve_fcg(pc):
+            st, stats = fe.fe_fcg(pa, fe.FE_DIFFUSION, pc, b, x, args.rtol, MAXIT, stream)
+            if st != fe.FE_OK:
+                raise RuntimeError("fe_fcg failed: %d %s" % (st, fe.fe_last_error()))
+            return stats
+
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out_ = [fn() for _ in range(reps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev) / reps, out_[-1]
+
+        t_fcg, s_fcg = timed(lambda: solve_fcg(lpc), args.steps)
+        t_fj, s_fj = timed(lambda: solve_fcg(None), args.steps)
+        r_ = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
+        z_ = torch.empty_like(r_)
+        for _ in range(3):
+            fe.fe_lpc_apply(lpc, r_, z_, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(20)]
+        torch.cuda.synchronize()
+        for a_, z2 in ev:
+            a_.record(stream)
+            fe.fe_lpc_apply(lpc, r_, z_, stream)
+            z2.record(stream)
+        torch.cuda.synchronize()
+        ms_lpc = statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
+        din, w = (p + 1) ** 3, args.lpc_width
+        lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
+        mma_peak = fe.fe_probe_throughput("bf16_mma")
+        bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
+        learned = {
+            "time_to_1e-8_s": t_fcg, "speedup_vs_jacobi_pcg": (t / args.steps) / t_fcg,
+            "fcg_iters": s_fcg["iters"], "jacobi_pcg_iters": iters[-1] if iters else None,
+            "fallbacks_to_jacobi": s_fcg["outer_iters"] - 1,
+            "true_rel_resid": s_fcg["true_rel_resid"],
+            "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
+            "train_s": t_train, "train_steps": args.lpc_steps, "train_batch": 1024,
+            "final_batch_loss": loss, "width": w, "patch": "element, %d dofs" % din,
+            "network": "relu(relu(x W1) W2) W3 + x W0, BF16 weights/activations, FP32 accumulate",
+            "precond_apply_ms": ms_lpc, "precond_tflops": lpc_flops / (ms_lpc * 1e-3) / 1e12,
+            "precond_flops_per_launch": lpc_flops,
+            "mma_sync_bf16_probe_tflops": mma_peak,
+            "frac_of_mma_sync_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / mma_peak,
+            "frac_of_bf16_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / bf16_peak,
+            "kernel": "k_lpc_fused<DP=%d,W=%d>" % ((din + 15) // 16 * 16, w)}
+        fe.fe_lpc_destroy(lpc)
+
     # ---- the dominant kernel alone: fused diffusion apply, CUDA events on its stream
     def time_apply(variant, reps):
         fe.fe_pa_set_variant(pa, variant)
@@ -373,7 +439,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2_flush": "inputs larger than L2 (1.57 GB quadrature data per apply)",
                       "parallelism": "independent problem per GPU"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
-           "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir,
+           "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir, "learned_fcg": learned,
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result
@@ -508,6 +574,9 @@ def main():
     ap.add_argument("--p", type=int, default=ORDER)
     ap.add_argument("--rtol", type=float, default=RTOL)
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="fe_pcg_ir inner tolerance")
+    ap.add_argument("--lpc-width", type=int, default=128,
+                    help="width of the learned preconditioner's MLP (0: skip that comparison)")
+    ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")

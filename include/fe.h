@@ -184,11 +184,18 @@ int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double*
 
 /* Measurement utility behind the roofline denominators (not part of the operator): runs
  * independent multiply-add chains on every SM of the current device and returns the sustained
- * rate in *tflops (multiply-add = 2 flops; one m8n8k4 DMMA = 512 flops).  Units:
- * FE_PROBE_FP64_FMA, FE_PROBE_FP64_DMMA, FE_PROBE_FP32_FMA, FE_PROBE_F32X2_MAC (the anchored
- * float-float step of the apply, counted as one FP64-equivalent multiply-add).  Synchronous;
- * allocates 64 bytes of scratch. */
-enum { FE_PROBE_FP64_FMA = 0, FE_PROBE_FP64_DMMA = 1, FE_PROBE_FP32_FMA = 2, FE_PROBE_F32X2_MAC = 3 };
+ * rate in *tflops (multiply-add = 2 flops; one m8n8k4 DMMA = 512 flops; one m16n8k16 MMA = 4096
+ * flops).  Units: FE_PROBE_FP64_FMA, FE_PROBE_FP64_DMMA, FE_PROBE_FP32_FMA, FE_PROBE_F32X2_MAC
+ * (the anchored float-float step of the apply, counted as one FP64-equivalent multiply-add),
+ * FE_PROBE_BF16_MMA (mma.sync m16n8k16 BF16 with FP32 accumulation, the instruction of the
+ * learned preconditioner's kernels).  Synchronous; allocates 64 bytes of scratch. */
+enum {
+  FE_PROBE_FP64_FMA = 0,
+  FE_PROBE_FP64_DMMA = 1,
+  FE_PROBE_FP32_FMA = 2,
+  FE_PROBE_F32X2_MAC = 3,
+  FE_PROBE_BF16_MMA = 4
+};
 int fe_probe_throughput(int unit, double* tflops);
 
 /* ---- Learned element-patch preconditioner and flexible CG (an extension; the paper has no
@@ -202,10 +209,11 @@ int fe_probe_throughput(int unit, double* tflops);
  *   FP32 accumulation on the tensor cores.  With f(x) = S_e^{-1} A_ee^{-1} S_e^{-1} x exactly, M
  *   is the symmetrically weighted additive Schwarz method on element patches.  M is nonlinear
  *   (though positively homogeneous), so it is used inside flexible CG.
- * Training pairs come from the operator itself: for interior elements three apart in each
- * direction, the block A_ee of the assembled matrix on the element's dofs is probed with D^3
- * applies and factored by FP64 Cholesky; f is trained with Adam, to the relative squared error,
- * on pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v scaled by 1/||x||, for v i.i.d. normal, A_ee u for
+ * Training pairs come from the operator itself: for interior elements (in up to 27 classes of
+ * elements three apart in each direction, at most 2^28 / D^6 elements), the block A_ee of the
+ * assembled matrix on the element's dofs is probed with D^3 applies per class and factored by
+ * FP64 Cholesky; f is trained with Adam, to the relative squared error,
+ * on pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v scaled by 1/||t||, for v i.i.d. normal, A_ee u for
  * normal u, or W_e r for residuals r of a short Jacobi-FCG run.
  * Built for orders 1..4 (the FP64 Cholesky of A_ee runs in one block's shared memory).
  * Handles are library-owned, refer to (do not own) their fe_pa, and are not thread-safe. */
@@ -247,8 +255,8 @@ int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
 /* Flexible CG (FCG with one stored direction: beta = -(z.q)/(p.q), alpha = (p.r)/(p.q)) for the
  * same system, arguments and stopping rule as fe_pcg, preconditioned by lpc, or by Jacobi when
  * lpc is NULL.  If the learned preconditioner produces a non-descent direction (z.r <= 0) or the
- * residual stops improving (no 1% gain in 100 iterations) the iteration restarts from the
- * current iterate with Jacobi.  Applies use pa's variant; vectors and inner products are FP64.
+ * residual stops improving (no 1% gain in 500 iterations, or a 1e4-fold rise) the iteration
+ * restarts from the current iterate with Jacobi.  Applies use pa's variant; vectors and inner products are FP64.
  * stats: outer_iters = 1 + number of such restarts.  Synchronous. */
 int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
            int maxit, fe_pcg_stats* stats, void* stream);

@@ -11,12 +11,13 @@
 // not beat Jacobi).  The symmetric diagonal scaling makes the map nearly the same on every
 // element even across coefficient jumps, so one network serves the whole mesh.
 //
-// Training pairs come from the FP64-accurate operator itself: for interior elements three apart
-// in every direction (so that their neighbourhoods do not overlap), the block A_ee of the
-// assembled matrix on the element's dofs is probed with D^3 applies of the global operator,
+// Training pairs come from the FP64-accurate operator itself: for interior elements, taken in
+// classes of elements three apart in every direction (within a class no two neighbourhoods
+// overlap), the block A_ee of the assembled matrix on the element's dofs is probed with D^3
+// applies of the global operator per class,
 // factored (batched FP64 Cholesky) and used to produce pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v
 // for v i.i.d. normal, v = A_ee u, and v = W_e r for residual snapshots r of Jacobi-FCG runs,
-// both scaled by 1/||x||.
+// both scaled by 1/||t||.
 // Training minimises the relative squared error with Adam, all on the GPU with the kernels
 // below.  The flexible CG (Notay's FCG(1)) tolerates the nonlinear preconditioner and falls back
 // to Jacobi-PCG on its residual when it stagnates; convergence is judged on the FP64 residual.
@@ -70,7 +71,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kLpcMaxOrder = 4;          // FP64 Cholesky of A_ee in one block's shared memory
-constexpr int64_t kProbeDoubles = 1 << 26;  // bound on the probed blocks (2 x 512 MB)
+constexpr int64_t kProbeDoubles = 1 << 28;  // bound on the probed blocks (2 GB)
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // splitmix64 finaliser
   z += 0x9E3779B97F4A7C15ull;
@@ -183,9 +184,9 @@ __global__ void k_cholesky(double* __restrict__ Aee, int din, int* __restrict__ 
 
 // Samples: per sample element s and replica q, v is (q mod 3) i.i.d. normal, A_ee u for normal u
 // (then A_ee^{-1} v = u), or W_e r for a residual snapshot r of a Jacobi-FCG run; u = A_ee^{-1} v
-// by the Cholesky factors; x = S v and t = u / S, both stored scaled by 1/||x||.
-__global__ void k_samples(const double* __restrict__ Lfac, const double* __restrict__ Afull,
-                          const double* __restrict__ snaps, int nsnap,
+// by the Cholesky factors; x = S v and t = u / S, both stored scaled by 1/||t||.
+__global__ void k_samples(const double* __restrict__ Lfac, const double* __restrict__ snaps,
+                          int nsnap,
                           const int32_t* __restrict__ map, const int32_t* __restrict__ elems,
                           const double* __restrict__ dis, const double* __restrict__ wsq,
                           int ns, int din, int reps,
@@ -196,7 +197,6 @@ __global__ void k_samples(const double* __restrict__ Lfac, const double* __restr
   double* u = sh + 2 * din;
   const int s = blockIdx.x;
   const double* L = Lfac + (int64_t)s * din * din;
-  const double* A = Afull + (int64_t)s * din * din;
   for (int q = 0; q < reps; ++q) {
     const int64_t row = (int64_t)s * reps + q;
     const int kind = q % 3;
@@ -207,13 +207,18 @@ __global__ void k_samples(const double* __restrict__ Lfac, const double* __restr
                        : normal01(seed ^ ((uint64_t)row * 1315423911ull + (uint64_t)i * 2654435761ull));
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (applied) {
+      if (applied) {  // r = A_ee u = L (L^T u)
         for (int i = 0; i < din; ++i) {
           double acc = 0.0;
-          for (int j = 0; j < din; ++j) acc += A[(int64_t)i * din + j] * u[j];
-          r[i] = acc;
-          t[i] = u[i];
+          for (int j = i; j < din; ++j) acc += L[(int64_t)j * din + i] * u[j];
+          t[i] = acc;
         }
+        for (int i = din - 1; i >= 0; --i) {
+          double acc = 0.0;
+          for (int j = 0; j <= i; ++j) acc += L[(int64_t)i * din + j] * t[j];
+          r[i] = acc;
+        }
+        for (int i = 0; i < din; ++i) t[i] = u[i];
       } else {
         for (int i = 0; i < din; ++i) r[i] = u[i];
         for (int i = 0; i < din; ++i) {  // L y = r
@@ -227,16 +232,19 @@ __global__ void k_samples(const double* __restrict__ Lfac, const double* __restr
           t[i] = acc / L[(int64_t)i * din + i];
         }
       }
-      double nx = 0.0;
+      double nt = 0.0;
       for (int i = 0; i < din; ++i) {
         const double si = dis[map[(int64_t)elems[s] * din + i]];  // > 0 on interior elements
-        const double xi = si * r[i];
-        u[i] = xi;
+        u[i] = si * r[i];
         t[i] /= si;
-        nx += xi * xi;
+        nt += t[i] * t[i];
       }
-      nx = sqrt(nx);
-      const double inv = nx > 0.0 ? 1.0 / nx : 0.0;
+      // Pairs are scaled to ||t|| = 1, so that the batch loss is the mean relative error per
+      // sample: with 1/||x|| the smooth modes (large t for a small x) would dominate it and the
+      // high-frequency response, where a poor preconditioner hurts most, would go unfitted.  The
+      // network is positively homogeneous, so the scale of a pair changes only its weight.
+      nt = sqrt(nt);
+      const double inv = nt > 0.0 ? 1.0 / nt : 0.0;
       for (int i = 0; i < din; ++i) {
         Xs[row * din + i] = __float2bfloat16((float)(u[i] * inv));
         Ts[row * din + i] = (float)(t[i] * inv);
@@ -429,6 +437,7 @@ int mlp_loss_grad(fe_lpc* L, int64_t rows, cudaStream_t s, double* loss_out) {
 
 // ---- flexible CG
 constexpr int kRB = 1024;  // reduction blocks (of kT threads); partials reduced by one block
+constexpr int kStall = 500;  // learned preconditioner: iterations without a 1% gain before Jacobi
 
 enum { S_PQ = 0, S_PR, S_RR, S_ZQ, S_ZR, S_BB, S_ALPHA, S_BETA, S_TRUE, S_N };
 
@@ -718,7 +727,7 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
       best = rel;
     }
     bool restart = false;
-    if (learned && (!(hsc[S_ZR] > 0.0) || it - last_gain >= 100)) {
+    if (learned && (!(hsc[S_ZR] > 0.0) || it - last_gain >= kStall || rel > 1e4 * best)) {
       learned = false;  // fall back to Jacobi from the current iterate
       restart = true;
       ++res->restarts;
@@ -747,23 +756,37 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
 int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
   fe_mesh* m = const_cast<fe_mesh*>(L->pa->mesh);
   const int din = L->din;
+  // Interior elements in 27 classes by (ex, ey, ez) mod 3: elements of one class are three apart,
+  // so their blocks share no dof and no element and one class is probed with D^3 applies.
+  // Classes are taken in turn until the block storage bound is reached.
+  const int64_t cap = kProbeDoubles / ((int64_t)din * din);
   std::vector<int32_t> el;
-  for (int ez = 1; ez + 1 < m->nz; ez += 3)
-    for (int ey = 1; ey + 1 < m->ny; ey += 3)
-      for (int ex = 1; ex + 1 < m->nx; ex += 3)
-        el.push_back((int32_t)(ex + (int64_t)m->nx * (ey + (int64_t)m->ny * ez)));
+  std::vector<int> cls_start{0};
+  for (int oz = 1; oz <= 3; ++oz)
+    for (int oy = 1; oy <= 3; ++oy)
+      for (int ox = 1; ox <= 3; ++ox) {
+        std::vector<int32_t> c;
+        for (int ez = oz; ez + 1 < m->nz; ez += 3)
+          for (int ey = oy; ey + 1 < m->ny; ey += 3)
+            for (int ex = ox; ex + 1 < m->nx; ex += 3)
+              c.push_back((int32_t)(ex + (int64_t)m->nx * (ey + (int64_t)m->ny * ez)));
+        if (c.empty()) continue;
+        const int64_t room = cap - (int64_t)el.size();
+        if (room <= 0) break;
+        if ((int64_t)c.size() > room) {  // an evenly strided subset of the class
+          std::vector<int32_t> sub;
+          for (int64_t i = 0; i < room; ++i) sub.push_back(c[(size_t)(i * (int64_t)c.size() / room)]);
+          c.swap(sub);
+        }
+        el.insert(el.end(), c.begin(), c.end());
+        cls_start.push_back((int)el.size());
+      }
   if (el.empty())
     return set_error(FE_ERR_ARG, "fe_lpc_train: mesh too small (needs >= 3 elements per axis)");
-  const int64_t cap = kProbeDoubles / ((int64_t)din * din);
-  if ((int64_t)el.size() > cap) {  // keep an evenly strided subset
-    std::vector<int32_t> sub;
-    for (int64_t i = 0; i < cap; ++i) sub.push_back(el[(size_t)(i * (int64_t)el.size() / cap)]);
-    el.swap(sub);
-  }
   const int ns = (int)el.size();
   const int hi = (L->pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
   int32_t* d_el = nullptr;
-  double *v = nullptr, *w = nullptr, *Aee = nullptr, *Afull = nullptr, *snapbuf = nullptr;
+  double *v = nullptr, *w = nullptr, *Aee = nullptr, *snapbuf = nullptr;
   int* d_fail = nullptr;
   Snapshots snap;
   snap.at = {0, 1, 2, 4, 8, 16, 32, 64};
@@ -774,11 +797,9 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
       (err = cudaMalloc(&v, sizeof(double) * m->ndofs)) != cudaSuccess ||
       (err = cudaMalloc(&w, sizeof(double) * m->ndofs)) != cudaSuccess ||
       (err = cudaMalloc(&Aee, sizeof(double) * mat)) != cudaSuccess ||
-      (err = cudaMalloc(&Afull, sizeof(double) * mat)) != cudaSuccess ||
       (err = cudaMalloc(&snapbuf, sizeof(double) * nsnap * ns * din)) != cudaSuccess ||
       (err = cudaMalloc(&d_fail, sizeof(int))) != cudaSuccess) {
-    cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(Afull); cudaFree(snapbuf);
-    cudaFree(d_fail);
+    cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(snapbuf); cudaFree(d_fail);
     return cuda_error(err, "fe_lpc_train: sample cudaMalloc");
   }
   int st = FE_OK;
@@ -786,13 +807,16 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
   // snapshots a short run never reaches stay zero (zero rows add nothing to loss or gradient)
   cudaMemsetAsync(snapbuf, 0, sizeof(double) * nsnap * ns * din, s);
   cudaMemsetAsync(d_fail, 0, sizeof(int), s);
-  for (int a = 0; a < din && st == FE_OK; ++a) {
-    cudaMemsetAsync(v, 0, sizeof(double) * m->ndofs, s);
-    k_probe_set<<<(ns + kT - 1) / kT, kT, 0, s>>>(v, m->d_map, d_el, ns, din, a);
-    st = apply_dispatch(L->pa, L->op, hi, v, w, s);
-    if (st != FE_OK) break;
-    k_probe_get<<<(unsigned int)(((int64_t)ns * din + kT - 1) / kT), kT, 0, s>>>(w, m->d_map, d_el,
-                                                                                  ns, din, a, Aee);
+  for (size_t c = 0; c + 1 < cls_start.size() && st == FE_OK; ++c) {
+    const int c0 = cls_start[c], nc = cls_start[c + 1] - cls_start[c];
+    for (int a = 0; a < din && st == FE_OK; ++a) {
+      cudaMemsetAsync(v, 0, sizeof(double) * m->ndofs, s);
+      k_probe_set<<<(nc + kT - 1) / kT, kT, 0, s>>>(v, m->d_map, d_el + c0, nc, din, a);
+      st = apply_dispatch(L->pa, L->op, hi, v, w, s);
+      if (st != FE_OK) break;
+      k_probe_get<<<(unsigned int)(((int64_t)nc * din + kT - 1) / kT), kT, 0, s>>>(
+          w, m->d_map, d_el + c0, nc, din, a, Aee + (int64_t)c0 * din * din);
+    }
   }
   // residual snapshots of Jacobi-FCG on the sine load and on a random right-hand side
   snap.elems = d_el;
@@ -809,7 +833,6 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
     st = fcg_run(L->pa, L->op, nullptr, L->dinv, v, w, 0.0, snap.at.back(), &snap, s, &fr);
   }
   if (st == FE_OK) {
-    cudaMemcpyAsync(Afull, Aee, sizeof(double) * mat, cudaMemcpyDeviceToDevice, s);
     const size_t shm = sizeof(double) * din * din;
     cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     k_cholesky<<<ns, 128, shm, s>>>(Aee, din, d_fail);
@@ -819,7 +842,7 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
       st = cuda_error(err, "fe_lpc_train: sample cudaMalloc");
   }
   if (st == FE_OK) {
-    k_samples<<<ns, 64, sizeof(double) * 3 * din, s>>>(Aee, Afull, snapbuf, nsnap, m->d_map, d_el,
+    k_samples<<<ns, 64, sizeof(double) * 3 * din, s>>>(Aee, snapbuf, nsnap, m->d_map, d_el,
                                                        L->dis, L->wsq, ns, din, reps, L->seed,
                                                        L->Xs, L->Ts);
     int fail = 0;
@@ -831,8 +854,7 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
       st = set_error(FE_ERR_BREAKDOWN, "fe_lpc_train: an element block is not positive definite");
   }
   if (st != FE_OK) L->nsamp = 0;
-  cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(Afull); cudaFree(snapbuf);
-  cudaFree(d_fail);
+  cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(snapbuf); cudaFree(d_fail);
   return st;
 }
 

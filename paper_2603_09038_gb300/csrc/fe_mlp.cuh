@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fe_f2.h"
+
 namespace fe {
 namespace mlp {
 
@@ -214,14 +216,17 @@ __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
   return pack2(__float2bfloat16(lo > 0.0f ? lo : 0.0f), __float2bfloat16(hi > 0.0f ? hi : 0.0f));
 }
 
+// Widths up to 128 with D^3 <= 64 are register-capped for two resident blocks per SM (16 warps
+// to hide the gather's memory latency); larger tiles need the full register file of one block.
 template <int DP, int W>
-__global__ void __launch_bounds__(256, 1) k_lpc_fused(
+__global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fused(
     const uint4* __restrict__ wimg, const double* __restrict__ r, const int32_t* __restrict__ map,
     const double* __restrict__ fsc, int64_t ne, int din, double* __restrict__ z) {
   using Lay = FusedLayout<DP, W>;
   static_assert(W % 64 == 0 && DP % 16 == 0, "fused MLP tile sizes");
   constexpr int DPW = DP / 2, WW = W / 2;   // 32-bit words per image row
   constexpr int WPL = (DPW + 31) / 32;      // staging words per lane in the gather
+  constexpr int GR = 8 / WPL;               // rows gathered per step (loads in flight)
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* sw = reinterpret_cast<uint32_t*>(smem);
   {
@@ -239,12 +244,14 @@ __global__ void __launch_bounds__(256, 1) k_lpc_fused(
   const int64_t ntiles = (ne + 15) / 16;
   for (int64_t tile = (int64_t)blockIdx.x * Lay::WARPS + warp; tile < ntiles;
        tile += (int64_t)gridDim.x * Lay::WARPS) {
-    // ---- gather: x = F r on the element, normalised, to BF16 (4 rows at a time for ILP)
+    // ---- gather: x = F r on the element, normalised, to BF16 (GR rows at a time for ILP).  The
+    // FP64 inputs are narrowed to floats by integer manipulation and the scaling is done in
+    // FP32: GB300's FP64 pipe (2 DFMA per clock per SM) would otherwise bound the kernel.
 #pragma unroll 1
-    for (int i0 = 0; i0 < 16; i0 += 4) {
-      double xv[4][WPL][2];
+    for (int i0 = 0; i0 < 16; i0 += GR) {
+      float xv[GR][WPL][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < GR; ++i) {
         const int64_t e = tile * 16 + i0 + i;
 #pragma unroll
         for (int w = 0; w < WPL; ++w) {
@@ -252,34 +259,43 @@ __global__ void __launch_bounds__(256, 1) k_lpc_fused(
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int k = 2 * kw + h;
-            double v = 0.0;
+            float v = 0.0f;
             if (kw < DPW && k < din && e < ne) {
               const int32_t idx = map[e * din + k];
-              v = fsc[idx] * r[idx];
+              v = f2_from_f64(fsc[idx]).h * f2_from_f64(r[idx]).h;
             }
             xv[i][w][h] = v;
           }
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        double ss = 0.0;
+      for (int i = 0; i < GR; ++i) {
+        // ||x|| from the largest magnitude m: sum (x/m)^2 cannot overflow or underflow
+        float mx = 0.0f;
 #pragma unroll
-        for (int w = 0; w < WPL; ++w) ss += xv[i][w][0] * xv[i][w][0] + xv[i][w][1] * xv[i][w][1];
+        for (int w = 0; w < WPL; ++w) mx = fmaxf(mx, fmaxf(fabsf(xv[i][w][0]), fabsf(xv[i][w][1])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float im = mx > 0.0f ? 1.0f / mx : 0.0f;
+        float ss = 0.0f;
+#pragma unroll
+        for (int w = 0; w < WPL; ++w) {
+          const float a0 = xv[i][w][0] * im, a1 = xv[i][w][1] * im;
+          ss = fmaf(a0, a0, fmaf(a1, a1, ss));
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        const double s = sqrt(ss);
-        const double inv = s > 0.0 ? 1.0 / s : 0.0;
+        const float sn = sqrtf(ss);               // ||x|| / m, in [1, 8 sqrt(2)]
+        const float inv = mx > 0.0f ? im / sn : 0.0f;
         const int row = i0 + i;
 #pragma unroll
         for (int w = 0; w < WPL; ++w) {
           const int kw = lane + 32 * w;
           if (kw < DPW)
-            xs[row * DPW + swz(row, kw, DPW)] =
-                pack2(__float2bfloat16((float)(xv[i][w][0] * inv)),
-                      __float2bfloat16((float)(xv[i][w][1] * inv)));
+            xs[row * DPW + swz(row, kw, DPW)] = pack2(__float2bfloat16(xv[i][w][0] * inv),
+                                                      __float2bfloat16(xv[i][w][1] * inv));
         }
-        if (lane == 0) ssc[row] = (float)s;
+        if (lane == 0) ssc[row] = mx * sn;
       }
     }
     __syncwarp();
@@ -376,8 +392,8 @@ __global__ void __launch_bounds__(256, 1) k_lpc_fused(
         const int64_t e = tile * 16 + row;
         if (col < din && e < ne) {
           const int32_t idx = map[e * din + col];
-          const double f = fsc[idx];
-          if (f != 0.0) atomicAdd(&z[idx], f * (double)(c >= 2 ? s_hi : s_lo) * (double)y[j][c]);
+          const float f = f2_from_f64(fsc[idx]).h;
+          if (f != 0.0f) atomicAdd(&z[idx], f64_from_f32(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
         }
       }
     }

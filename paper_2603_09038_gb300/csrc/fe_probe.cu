@@ -57,6 +57,27 @@ __global__ void k_probe_dmma(double* out, int iters) {
   if (s == 12345.678) out[0] = s;
 }
 
+// BF16 m16n8k16 tensor-core MMA chains with FP32 accumulation (the instruction of the learned
+// preconditioner's kernels), 4096 flops each per warp
+__global__ void k_probe_hmma(float* out, int iters, uint32_t av, uint32_t bv) {
+  float c[kChains][4];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) c[i][0] = c[i][1] = c[i][2] = c[i][3] = (float)i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i)
+      asm volatile(
+          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+          "{%8,%9}, {%0,%1,%2,%3};"
+          : "+f"(c[i][0]), "+f"(c[i][1]), "+f"(c[i][2]), "+f"(c[i][3])
+          : "r"(av), "r"(av), "r"(av), "r"(av), "r"(bv), "r"(bv));
+  }
+  float s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s += c[i][0] + c[i][1] + c[i][2] + c[i][3];
+  if (s == 12345.678f) out[0] = s;
+}
+
 // anchored float-float multiply-add chains (the apply's inner step), counted as 2 flops each
 __global__ void k_probe_f2(float* out, int iters, float ah, float al) {
   fe::Anch acc[kChains];
@@ -111,6 +132,11 @@ extern "C" int fe_probe_throughput(int unit, double* tflops) {
         flops_per_iter = 2.0 * kChains * nthreads;
         k_probe_ffma<<<blocks, threads>>>((float*)buf, iters, 0.9999f, 1e-3f);
         break;
+      case FE_PROBE_BF16_MMA:
+        iters = 4096;
+        flops_per_iter = 4096.0 * kChains * (nthreads / 32);
+        k_probe_hmma<<<blocks, threads>>>((float*)buf, iters, 0x3F803F80u, 0x3F7F3F7Fu);
+        break;
       default:
         iters = 8192;
         flops_per_iter = 2.0 * kChains * nthreads;
@@ -119,7 +145,7 @@ extern "C" int fe_probe_throughput(int unit, double* tflops) {
     }
   };
   int st = FE_OK;
-  if (unit < FE_PROBE_FP64_FMA || unit > FE_PROBE_F32X2_MAC) {
+  if (unit < FE_PROBE_FP64_FMA || unit > FE_PROBE_BF16_MMA) {
     st = fe::set_error(FE_ERR_ARG, "fe_probe_throughput: unknown unit");
   } else {
     launch();  // warm-up

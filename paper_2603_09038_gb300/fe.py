@@ -249,7 +249,7 @@ def fe_pcg_noalloc(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
     return status, _stats(st)
 
 
-PROBE_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "f32x2_mac": 3}
+PROBE_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "f32x2_mac": 3, "bf16_mma": 4}
 
 
 def fe_probe_throughput(unit):
