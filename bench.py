@@ -215,6 +215,7 @@ def run_ours(args, rank, world, local_rank):
     V = perturbed_vertices(n, n, n)
     mesh = fe.fe_mesh_setup(n, n, n, p, V)
     pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+    fe_mesh_of[pa] = mesh
     ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
     q = p + 2
     stream = torch.cuda.current_stream()
@@ -302,67 +303,11 @@ def run_ours(args, rank, world, local_rank):
               "inner_operator": "f32"}
     launches_ir = sum(s_["launches"] for s_ in ir_stats)
 
-    # ---- learned patch preconditioner inside flexible CG, to the same FP64 1e-8 residual:
-    #      training (data generation from the operator + Adam) timed once on the host clock,
-    #      the solve timed like the PCG above, the fused preconditioner kernel alone
+    # ---- learned patch preconditioner inside flexible CG, to the same FP64 1e-8 residual
     learned = None
     if args.lpc_width > 0:
-        t0 = time.perf_counter()
-        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, args.lpc_width, 1)
-        loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t0
-
-        def solve_fcg(pc):
-            st, stats = fe.fe_fcg(pa, fe.FE_DIFFUSION, pc, b, x, args.rtol, MAXIT, stream)
-            if st != fe.FE_OK:
-                raise RuntimeError("fe_fcg failed: %d %s" % (st, fe.fe_last_error()))
-            return stats
-
-        def timed(fn, reps):
-            fn()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            out_ = [fn() for _ in range(reps)]
-            e1.record(stream)
-            torch.cuda.synchronize()
-            return max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev) / reps, out_[-1]
-
-        t_fcg, s_fcg = timed(lambda: solve_fcg(lpc), args.steps)
-        t_fj, s_fj = timed(lambda: solve_fcg(None), args.steps)
-        r_ = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
-        z_ = torch.empty_like(r_)
-        for _ in range(3):
-            fe.fe_lpc_apply(lpc, r_, z_, stream)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(20)]
-        torch.cuda.synchronize()
-        for a_, z2 in ev:
-            a_.record(stream)
-            fe.fe_lpc_apply(lpc, r_, z_, stream)
-            z2.record(stream)
-        torch.cuda.synchronize()
-        ms_lpc = statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
-        din, w = (p + 1) ** 3, args.lpc_width
-        lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
-        mma_peak = fe.fe_probe_throughput("bf16_mma")
-        bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
-        learned = {
-            "time_to_1e-8_s": t_fcg, "speedup_vs_jacobi_pcg": (t / args.steps) / t_fcg,
-            "fcg_iters": s_fcg["iters"], "jacobi_pcg_iters": iters[-1] if iters else None,
-            "fallbacks_to_jacobi": s_fcg["outer_iters"] - 1,
-            "true_rel_resid": s_fcg["true_rel_resid"],
-            "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
-            "train_s": t_train, "train_steps": args.lpc_steps, "train_batch": 1024,
-            "final_batch_loss": loss, "width": w, "patch": "element, %d dofs" % din,
-            "network": "relu(relu(x W1) W2) W3 + x W0, BF16 weights/activations, FP32 accumulate",
-            "precond_apply_ms": ms_lpc, "precond_tflops": lpc_flops / (ms_lpc * 1e-3) / 1e12,
-            "precond_flops_per_launch": lpc_flops,
-            "mma_sync_bf16_probe_tflops": mma_peak,
-            "frac_of_mma_sync_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / mma_peak,
-            "frac_of_bf16_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / bf16_peak,
-            "kernel": "k_lpc_fused<DP=%d,W=%d>" % ((din + 15) // 16 * 16, w)}
-        fe.fe_lpc_destroy(lpc)
+        learned = learned_fcg(fe, pa, b, x, args, stream, dist, dev, t / args.steps,
+                              iters[-1] if iters else None)
 
     # ---- the dominant kernel alone: fused diffusion apply, CUDA events on its stream
     def time_apply(variant, reps):
@@ -450,6 +395,115 @@ def run_ours(args, rank, world, local_rank):
             cb = cpu_oracle_sample(args.cpu_seconds)
             out["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
         print(json.dumps(out))
+    return 0
+
+
+def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters):
+    """The learned element-patch preconditioner inside flexible CG to the same FP64 residual as
+    Jacobi-PCG (time t_pcg, pcg_iters iterations): training (data generation from the operator's
+    own patch solves + Adam) timed once on the host clock, the solve timed with CUDA events like
+    the PCG, and the fused BF16 tensor-core preconditioner kernel alone (median of 20)."""
+    import torch
+    ndofs, ne, p = fe.fe_mesh_sizes(fe_mesh_of[pa])
+    t0 = time.perf_counter()
+    lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, args.lpc_width, 1)
+    loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve_fcg(pc):
+        st, stats = fe.fe_fcg(pa, fe.FE_DIFFUSION, pc, b, x, args.rtol, MAXIT, stream)
+        if st != fe.FE_OK:
+            raise RuntimeError("fe_fcg failed: %d %s" % (st, fe.fe_last_error()))
+        return stats
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out_ = [fn() for _ in range(reps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev) / reps, out_[-1]
+
+    t_fcg, s_fcg = timed(lambda: solve_fcg(lpc), max(1, args.steps))
+    t_fj, s_fj = timed(lambda: solve_fcg(None), max(1, args.steps))
+    r_ = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
+    z_ = torch.empty_like(r_)
+    for _ in range(3):
+        fe.fe_lpc_apply(lpc, r_, z_, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(20)]
+    torch.cuda.synchronize()
+    for a_, z2 in ev:
+        a_.record(stream)
+        fe.fe_lpc_apply(lpc, r_, z_, stream)
+        z2.record(stream)
+    torch.cuda.synchronize()
+    ms_lpc = statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
+    din, w = (p + 1) ** 3, args.lpc_width
+    lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
+    mma_peak = fe.fe_probe_throughput("bf16_mma")
+    bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
+    fe.fe_lpc_destroy(lpc)
+    return {
+        "time_to_1e-8_s": t_fcg, "speedup_vs_jacobi_pcg": t_pcg / t_fcg if t_pcg else None,
+        "jacobi_pcg_time_s": t_pcg,
+        "fcg_iters": s_fcg["iters"], "jacobi_pcg_iters": pcg_iters,
+        "fallbacks_to_jacobi": s_fcg["outer_iters"] - 1,
+        "true_rel_resid": s_fcg["true_rel_resid"],
+        "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
+        "train_s": t_train, "train_steps": args.lpc_steps, "train_batch": 1024,
+        "final_batch_loss": loss, "width": w, "patch": "element, %d dofs" % din,
+        "network": "relu(relu(x W1) W2) W3 + x W0, BF16 weights/activations, FP32 accumulate",
+        "precond_apply_ms": ms_lpc, "precond_tflops": lpc_flops / (ms_lpc * 1e-3) / 1e12,
+        "precond_flops_per_launch": lpc_flops,
+        "mma_sync_bf16_probe_tflops": mma_peak,
+        "frac_of_mma_sync_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / mma_peak,
+        "frac_of_bf16_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / bf16_peak,
+        "kernel": "k_lpc_fused<DP=%d,W=%d>" % ((din + 15) // 16 * 16, w)}
+
+
+fe_mesh_of = {}   # fe_pa handle -> its fe_mesh handle (for sizes)
+
+
+def run_learned(args, local_rank):
+    """--learned: only the learned-preconditioner comparison on an --n^3, order --p mesh with a
+    log-normal coefficient of --sigma (0: Poisson), as one JSON line."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices, lognormal_coefficient
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    fe.load()
+    n, p = args.n, args.p
+    mesh = fe.fe_mesh_setup(n, n, n, p, perturbed_vertices(n, n, n))
+    c = torch.from_numpy(lognormal_coefficient(n ** 3, args.sigma)).to(dev) if args.sigma else None
+    pa = fe.fe_pa_setup(mesh, 0, c, fe.FE_DIFFUSION)
+    fe_mesh_of[pa] = mesh
+    fe.fe_pa_set_variant(pa, args.variant)
+    ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
+    stream = torch.cuda.current_stream()
+    b = torch.empty(ndofs, dtype=torch.float64, device=dev)
+    x = torch.empty_like(b)
+    fe.fe_load_vector_sine(pa, b)
+    st, s0 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, args.steps)):
+        st, s0 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pcg = e0.elapsed_time(e1) / 1000.0 / max(1, args.steps)
+    out = {"learned": True, "workload": "diffusion_%dcubed_p%d_sigma%g" % (n, p, args.sigma),
+           "ndofs": ndofs, "variant": args.variant, "rtol": args.rtol}
+    out.update(learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"]))
+    fe.fe_pa_destroy(pa)
+    fe.fe_mesh_destroy(mesh)
+    print(json.dumps(out))
     return 0
 
 
@@ -553,7 +607,7 @@ def run_peaks(local_rank):
     torch.cuda.set_device(local_rank)
     fe.load()
     out = {"peaks": True}
-    for unit in ("fp64_fma", "fp64_dmma", "fp32_fma", "f32x2_mac"):
+    for unit in ("fp64_fma", "fp64_dmma", "fp32_fma", "f32x2_mac", "bf16_mma"):
         out[unit + "_tflops"] = fe.fe_probe_throughput(unit)
     props = torch.cuda.get_device_properties(local_rank)
     out["sms"] = props.multi_processor_count
@@ -577,11 +631,15 @@ def main():
     ap.add_argument("--lpc-width", type=int, default=128,
                     help="width of the learned preconditioner's MLP (0: skip that comparison)")
     ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
+    ap.add_argument("--learned", action="store_true",
+                    help="only the learned-preconditioner comparison (with --n, --p, --sigma)")
+    ap.add_argument("--sigma", type=float, default=0.0,
+                    help="--learned: log-normal coefficient sigma (0: Poisson)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
-    ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32 throughput probes")
+    ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32/BF16-mma.sync throughput probes")
     ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")
     args = ap.parse_args()
@@ -598,6 +656,8 @@ def main():
         return run_peaks(local_rank)
     if args.batched:
         return run_batched(args, local_rank)
+    if args.learned:
+        return run_learned(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -14,7 +14,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fe_f2.h"
 
 namespace fe {
 namespace mlp {
@@ -245,8 +244,10 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
   for (int64_t tile = (int64_t)blockIdx.x * Lay::WARPS + warp; tile < ntiles;
        tile += (int64_t)gridDim.x * Lay::WARPS) {
     // ---- gather: x = F r on the element, normalised, to BF16 (GR rows at a time for ILP).  The
-    // FP64 inputs are narrowed to floats by integer manipulation and the scaling is done in
-    // FP32: GB300's FP64 pipe (2 DFMA per clock per SM) would otherwise bound the kernel.
+    // FP64 inputs are narrowed to floats (one conversion each) and the scaling is done in FP32:
+    // with FP64 arithmetic here GB300's FP64 pipe (2 DFMA per clock per SM) bound the kernel
+    // (81 % busy); narrowing by integer manipulation instead of the conversion instruction was
+    // measured slower (more instructions in a latency-bound kernel).
 #pragma unroll 1
     for (int i0 = 0; i0 < 16; i0 += GR) {
       float xv[GR][WPL][2];
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
             float v = 0.0f;
             if (kw < DPW && k < din && e < ne) {
               const int32_t idx = map[e * din + k];
-              v = f2_from_f64(fsc[idx]).h * f2_from_f64(r[idx]).h;
+              v = (float)fsc[idx] * (float)r[idx];
             }
             xv[i][w][h] = v;
           }
@@ -392,8 +393,8 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
         const int64_t e = tile * 16 + row;
         if (col < din && e < ne) {
           const int32_t idx = map[e * din + col];
-          const float f = f2_from_f64(fsc[idx]).h;
-          if (f != 0.0f) atomicAdd(&z[idx], f64_from_f32(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
+          const float f = (float)fsc[idx];
+          if (f != 0.0f) atomicAdd(&z[idx], (double)(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
         }
       }
     }
