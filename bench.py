@@ -14,6 +14,7 @@ Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the t
   roofline     of the dominant kernel (the fused apply), timed alone with CUDA events;
   cpu_baseline the CPU oracle (element-matrix apply) on a bounded sample of the same mesh;
   pcg_ir       mixed-precision iterative refinement (FP32 inner PCG) to the same residual;
+  pcg_chebyshev  Chebyshev-polynomial preconditioned CG (degree 4) to the same residual;
   learned_fcg  the learned element-patch preconditioner (trained on the GPU from the operator's
                own patch solves) inside flexible CG, to the same FP64 residual, against the
                Jacobi-PCG time above, with its fused BF16 tensor-core kernel timed alone.
@@ -303,6 +304,26 @@ def run_ours(args, rank, world, local_rank):
               "inner_operator": "f32"}
     launches_ir = sum(s_["launches"] for s_ in ir_stats)
 
+    # ---- Chebyshev-polynomial preconditioned CG (degree 4, [1.1 lmax/30, 1.1 lmax], lmax by
+    #      20 power steps on the first solve, cached) to the same 1e-8 residual
+    def solve_cheb():
+        st, stats = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, b, x, args.rtol, MAXIT, stream)
+        if st != fe.FE_OK:
+            raise RuntimeError("fe_pcg (Chebyshev) failed: %d %s" % (st, fe.fe_last_error()))
+        return stats
+    for _ in range(2):
+        solve_cheb()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cheb_stats = [solve_cheb() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ch = max_over_ranks(e0.elapsed_time(e1) / 1000.0, dist, dev) / max(1, args.steps)
+    pcg_cheb = {"time_to_1e-8_s": t_ch, "speedup_vs_jacobi_pcg": (t / args.steps) / t_ch,
+                "iters": cheb_stats[-1]["iters"] if cheb_stats else None, "degree": 4,
+                "applies_per_iter": 4, "lmax_estimate": fe.fe_estimate_lmax(pa, fe.FE_DIFFUSION, 20),
+                "true_rel_resid": cheb_stats[-1]["true_rel_resid"] if cheb_stats else None}
+
     # ---- learned patch preconditioner inside flexible CG, to the same FP64 1e-8 residual
     learned = None
     if args.lpc_width > 0:
@@ -384,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
                       "l2_flush": "inputs larger than L2 (1.57 GB quadrature data per apply)",
                       "parallelism": "independent problem per GPU"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
-           "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir, "learned_fcg": learned,
+           "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir, "pcg_chebyshev": pcg_cheb,
+           "learned_fcg": learned,
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result

@@ -51,7 +51,7 @@ typedef enum {
 
 typedef enum { FE_DIFFUSION = 1, FE_MASS = 2 } fe_op;
 
-typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1 } fe_pc;
+typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1, FE_PC_CHEBYSHEV = 2 } fe_pc;
 
 /* Arithmetic of the apply kernels.  All variants take and return FP64 vectors.
  *  FE_VARIANT_F64     FP64 FMA on the FP64 pipe (IEEE double throughout).
@@ -136,7 +136,7 @@ int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream
  * Asynchronous. */
 int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 
-/* Jacobi (or un-) preconditioned CG for A_bc x = b with homogeneous Dirichlet conditions on the
+/* Jacobi- (or un-, or Chebyshev-) preconditioned CG for A_bc x = b with homogeneous Dirichlet conditions on the
  * mesh boundary: A_bc = (1-m) A (1-m) + m (m = boundary mask).  b's boundary entries are
  * ignored; x is overwritten (zero initial guess; x = 0 on the boundary).  Stops when the
  * recursive residual satisfies ||r||_2 <= rtol ||b||_2 or after maxit iterations.  FP64 vectors
@@ -146,6 +146,28 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
  * iterate in every case). */
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
+
+/* PCG with a Chebyshev polynomial preconditioner (an extension; the paper uses no solver here):
+ * z = q(D^-1 A_bc) D^-1 r from `degree` steps of the Chebyshev semi-iteration for
+ * D^-1 A_bc z = D^-1 r, started at z = 0, on the interval [hi / lmin_ratio, hi], so that
+ * 1 - lam q(lam) = T_degree((theta - lam) / delta) / T_degree(theta / delta) (theta, delta the
+ * interval's centre and half-width, T the Chebyshev polynomial).  q is positive on (0, hi], so
+ * the preconditioner is linear and SPD when hi bounds the spectrum of D^-1 A_bc.  Each iteration
+ * costs `degree` applies (one for CG, degree - 1 for the polynomial).
+ *   degree      1..32, 0 => 4 (degree 1 is Jacobi scaled by 1/theta);
+ *   lmax        hi; 0 => 1.1 x fe_estimate_lmax with 20 power steps, computed on the first such
+ *               call for this handle and operator and cached in the handle;
+ *   lmin_ratio  hi / lo > 1; 0 => 30.
+ * Everything else (system, stopping rule, stats, status codes) as fe_pcg; fe_pcg with
+ * pc = FE_PC_CHEBYSHEV calls this with the defaults.  Work vectors: 7 of ndofs, cached. */
+int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, double lmin_ratio,
+                     const double* dev_b, double* dev_x, double rtol, int maxit,
+                     fe_pcg_stats* stats, void* stream);
+
+/* Largest-eigenvalue estimate of D^-1 A_bc (D = diag(A), boundary rows and columns removed):
+ * `iters` power steps (0..1000) from a fixed pseudo-random start, then the generalised Rayleigh
+ * quotient (v.Av)/(v.Dv) of the last iterate, a lower bound of lambda_max.  Synchronous. */
+int fe_estimate_lmax(fe_pa* pa, int op, int iters, double* lmax, void* stream);
 
 /* Mixed-precision iterative refinement around an FP32 inner PCG (an extension; the paper
  * itself stays in FP64 throughout).  Outer loop, in FP64 vectors:

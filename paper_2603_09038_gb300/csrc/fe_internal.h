@@ -67,6 +67,7 @@ struct fe_pa {
   int64_t work_ndofs = 0;
   double* d_dpart = nullptr;       // per-block partials of the apply-fused p.Ap
   int64_t dpart_cap = 0;
+  double cheb_lmax[2] = {0.0, 0.0};  // cached lambda_max estimates of D^-1 A (diffusion, mass)
 };
 
 namespace fe {

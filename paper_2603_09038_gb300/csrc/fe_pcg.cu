@@ -18,6 +18,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "fe_f2.h"
 #include "fe_internal.h"
@@ -285,6 +286,146 @@ __global__ void __launch_bounds__(kReduceThreads) k_resid(const double* __restri
     sb = fma(bi, bi, sb);
   }
   block_sum2(s, sb, part0, part1);
+}
+
+// ---- Chebyshev polynomial preconditioner z = q(D^-1 A_bc) D^-1 r: k steps of the Chebyshev
+// semi-iteration for D^-1 A z = D^-1 r from z = 0 on an interval [lo, hi] that contains the
+// spectrum, so that 1 - lam q(lam) = T_k((theta - lam)/delta) / T_k(theta/delta) (theta, delta
+// the interval's centre and half-width): positive q on (0, hi], a linear SPD preconditioner.
+// Three-term recurrence in the directions d_j with host-computed coefficients; k - 1 applies.
+
+// first step: d = dinv r / theta, z = d; the r.z partials when it is also the last step
+__global__ void __launch_bounds__(kReduceThreads) k_cheb_first(const double* __restrict__ r,
+                                                               const double* __restrict__ dinv,
+                                                               double* __restrict__ dv,
+                                                               double* __restrict__ z, int64_t n,
+                                                               double inv_theta, double* part0,
+                                                               const int* flags, int with_dot) {
+  if (flags[F_STATE] != ST_RUN) return;
+  fe::f2 acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    const double di = dinv[i] * ri * inv_theta;
+    dv[i] = di;
+    z[i] = di;
+    if (with_dot) f2_acc_prod(acc, ri, di);
+  }
+  if (with_dot) block_sum2((double)acc.h + (double)acc.l, 0.0, part0, nullptr);
+}
+
+// step j: d = c1 d + c2 dinv (r - A z), z += d, and q2 (= A z, scatter target) zeroed for the
+// next step's apply; the r.z partials on the last step
+__global__ void __launch_bounds__(kReduceThreads) k_cheb_step(const double* __restrict__ r,
+                                                              double* __restrict__ q2,
+                                                              const double* __restrict__ dinv,
+                                                              double* __restrict__ dv,
+                                                              double* __restrict__ z, int64_t n,
+                                                              double c1, double c2, double* part0,
+                                                              const int* flags, int with_dot) {
+  if (flags[F_STATE] != ST_RUN) return;
+  fe::f2 acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    const double di = fma(c1, dv[i], c2 * dinv[i] * (ri - q2[i]));
+    dv[i] = di;
+    const double zi = z[i] + di;
+    z[i] = zi;
+    q2[i] = 0.0;
+    if (with_dot) f2_acc_prod(acc, ri, zi);
+  }
+  if (with_dot) block_sum2((double)acc.h + (double)acc.l, 0.0, part0, nullptr);
+}
+
+// x += alpha p, r -= alpha (1-m) q; the r.r partials (into part1)
+__global__ void __launch_bounds__(kReduceThreads) k_update_xr(double* __restrict__ x,
+                                                              double* __restrict__ r,
+                                                              const double* __restrict__ p,
+                                                              const double* __restrict__ q,
+                                                              const uint8_t* __restrict__ mask,
+                                                              int64_t n, const double* sc,
+                                                              double* part1, const int* flags) {
+  if (flags[F_STATE] != ST_RUN) return;
+  const double alpha = sc[S_ALPHA];
+  fe::f2 acc{0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double qi = mask[i] ? 0.0 : q[i];
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, qi, r[i]);
+    r[i] = ri;
+    f2_acc_prod(acc, ri, ri);
+  }
+  block_sum2((double)acc.h + (double)acc.l, 0.0, part1, nullptr);
+}
+
+// initial r.z of the Chebyshev-preconditioned start; beta = 0 so that k_pupdate sets p = z
+__global__ void __launch_bounds__(kFinishThreads) k_finish_rz(const double* part0, double* sc,
+                                                            int* flags) {
+  if (flags[F_STATE] != ST_RUN) return;
+  const double rz = ordered_sum(part0);
+  if (threadIdx.x != 0) return;
+  sc[S_RZ] = rz;
+  sc[S_BETA] = 0.0;
+  if (!isfinite(rz))
+    flags[F_STATE] = ST_NAN;
+  else if (!(rz > 0.0))
+    flags[F_STATE] = ST_BREAK;
+}
+
+// power iteration for the largest eigenvalue of D^-1 A_bc: start vector (interior dofs, hashed
+// signs and magnitudes in [0.5, 1)), v = dinv w, and the generalised Rayleigh quotient
+// (v.Av) / (v.Dv) partials
+__global__ void __launch_bounds__(kReduceThreads) k_power_init(double* __restrict__ v,
+                                                               const uint8_t* __restrict__ mask,
+                                                               int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    const double u = 0.5 + 0.5 * (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    v[i] = mask[i] ? 0.0 : ((h & 1) ? u : -u);
+  }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_power_scale(double* __restrict__ w,
+                                                                const double* __restrict__ dinv,
+                                                                double* __restrict__ v,
+                                                                int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    v[i] = dinv[i] * w[i];
+    w[i] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_power_rq(const double* __restrict__ v,
+                                                             const double* __restrict__ w,
+                                                             const double* __restrict__ dinv,
+                                                             int64_t n, double* part0,
+                                                             double* part1) {
+  double num = 0.0, den = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = dinv[i];
+    if (di > 0.0) {
+      num = fma(v[i], w[i], num);
+      den = fma(v[i], v[i] / di, den);
+    }
+  }
+  block_sum2(num, den, part0, part1);
+}
+
+__global__ void __launch_bounds__(kFinishThreads) k_finish2(const double* part0,
+                                                          const double* part1, double* sc) {
+  const double a = ordered_sum(part0), b = ordered_sum(part1);
+  if (threadIdx.x == 0) {
+    sc[S_TRUE] = a;
+    sc[S_BB] = b;
+  }
 }
 
 // ||(1-m)(b - A x)|| / ||(1-m) b|| into sc[S_TRUE] (0 when b vanishes), ||(1-m) b||^2 into sc[S_BB].
@@ -608,6 +749,142 @@ int pcg_run_f32(fe_pa* pa, int op, const float* b, const PcgWork32& v, bool jaco
   return FE_OK;
 }
 
+// Largest eigenvalue estimate of D^-1 A_bc: `iters` power steps from a fixed pseudo-random
+// start, then the generalised Rayleigh quotient (v.Av)/(v.Dv) of the last iterate (a lower
+// bound that converges from below).  dinv: inverse diagonal, 0 on the boundary.  v, w: work.
+int cheb_lmax(const fe_pa* pa, int op, int variant, const double* dinv, double* v, double* w,
+              const PcgWork& ws, cudaStream_t s, int iters, int* launches, double* out) {
+  const int64_t n = pa->mesh->ndofs;
+  cudaError_t err;
+  k_power_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(v, pa->mesh->d_mask, n);
+  ++*launches;
+  for (int it = 0; it < iters; ++it) {
+    int st = apply_dispatch(pa, op, variant, v, w, s);
+    if (st != FE_OK) return st;
+    k_power_scale<<<kReduceBlocks, kReduceThreads, 0, s>>>(w, dinv, v, n);
+    *launches += 2;
+  }
+  int st = apply_dispatch(pa, op, variant, v, w, s);
+  if (st != FE_OK) return st;
+  k_power_rq<<<kReduceBlocks, kReduceThreads, 0, s>>>(v, w, dinv, n, ws.part0, ws.part1);
+  k_finish2<<<1, kFinishThreads, 0, s>>>(ws.part0, ws.part1, ws.sc);
+  *launches += 3;
+  double hsc[kScalars];
+  if ((err = cudaGetLastError()) != cudaSuccess ||
+      (err = cudaMemcpyAsync(hsc, ws.sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_chebyshev: eigenvalue estimate");
+  const double lam = hsc[S_BB] > 0.0 ? hsc[S_TRUE] / hsc[S_BB] : 0.0;
+  if (!(lam > 0.0) || !std::isfinite(lam))
+    return set_error(FE_ERR_BREAKDOWN, "fe_pcg_chebyshev: no positive eigenvalue estimate");
+  *out = lam;
+  return FE_OK;
+}
+
+// PCG with the Chebyshev preconditioner of `degree` steps on [lo, hi]; same conventions as
+// pcg_run (x = 0 start, device-resident state, batches of kBatch iterations between flag
+// reads).  dv, q2: two extra work vectors.
+int pcg_run_cheb(fe_pa* pa, int op, int variant, const double* b, double* x, const double* dinv,
+                 int degree, double lo, double hi, double rtol, int maxit, const PcgWork& w,
+                 double* dv, double* q2, cudaStream_t s, PcgResult* res) {
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  const uint8_t* mask = m->d_mask;
+  cudaError_t err;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  std::vector<double> c1(degree, 0.0), c2(degree, 0.0);
+  double rho = delta / theta;
+  for (int j = 1; j < degree; ++j) {
+    const double rn = 1.0 / (2.0 * theta / delta - rho);
+    c1[j] = rn * rho;
+    c2[j] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  const bool fused_dot = (variant != FE_VARIANT_F64_DMMA);
+  int64_t nblk = 0;
+  if (fused_dot) {
+    int st = apply_dispatch(pa, op, variant, nullptr, nullptr, s, nullptr, nullptr, &nblk, true);
+    if (st != FE_OK) return st;
+    if (nblk > pa->dpart_cap) {
+      cudaFree(pa->d_dpart);
+      pa->d_dpart = nullptr;
+      pa->dpart_cap = 0;
+      if ((err = cudaMalloc(&pa->d_dpart, sizeof(double) * nblk)) != cudaSuccess)
+        return cuda_error(err, "fe_pcg_chebyshev: partials cudaMalloc");
+      pa->dpart_cap = nblk;
+    }
+  }
+  // z = q(D^-1 A) D^-1 r into w.z, the r.z partials into w.part0 (skipped once stopped)
+  auto precondition = [&]() -> int {
+    k_cheb_first<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.r, dinv, dv, w.z, n, 1.0 / theta,
+                                                          w.part0, w.flags, degree == 1);
+    ++res->launches;
+    for (int j = 1; j < degree; ++j) {
+      int st = apply_dispatch(pa, op, variant, w.z, q2, s, w.flags);
+      if (st != FE_OK) return st;
+      k_cheb_step<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.r, q2, dinv, dv, w.z, n, c1[j], c2[j],
+                                                           w.part0, w.flags, j == degree - 1);
+      res->launches += 2;
+    }
+    return FE_OK;
+  };
+  if ((err = cudaMemsetAsync(w.flags, 0, sizeof(int) * 4, s)) != cudaSuccess ||
+      (err = cudaMemsetAsync(q2, 0, sizeof(double) * n, s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_chebyshev: init");
+  k_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(b, mask, dinv, x, w.r, w.z, w.p, w.q, n, w.part0,
+                                                  w.part1);
+  k_finish_init<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags);
+  res->launches += 2;
+  int st = precondition();
+  if (st != FE_OK) return st;
+  k_finish_rz<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
+  k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.z, w.q, n, w.sc, w.flags);
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_chebyshev: start");
+  res->launches += 2;
+  int hflags[4] = {0, 0, 0, 0};
+  int queued = 0;
+  for (;;) {
+    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
+      if (fused_dot) {
+        if ((st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags, pa->d_dpart)) != FE_OK)
+          return st;
+        k_finish_pq_var<<<1, kFinishThreads, 0, s>>>(pa->d_dpart, nblk, w.sc, w.flags);
+        res->launches += 2;
+      } else {
+        if ((st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags)) != FE_OK) return st;
+        k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.q, n, w.part0, w.flags);
+        k_finish_pq<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
+        res->launches += 3;
+      }
+      k_update_xr<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, w.r, w.p, w.q, mask, n, w.sc,
+                                                           w.part1, w.flags);
+      ++res->launches;
+      if ((st = precondition()) != FE_OK) return st;
+      k_finish_update<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
+      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.z, w.q, n, w.sc, w.flags);
+      if ((err = cudaGetLastError()) != cudaSuccess)
+        return cuda_error(err, "fe_pcg_chebyshev: iteration launch");
+      res->launches += 2;
+    }
+    if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (err = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(err, "fe_pcg_chebyshev: iteration");
+    if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
+  }
+  double hsc[kScalars];
+  if ((err = cudaMemcpyAsync(hsc, w.sc, sizeof(double) * kScalars, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_chebyshev: stats");
+  res->state = hflags[F_STATE];
+  res->iters = hflags[F_ITERS];
+  res->rel = hsc[S_REL];
+  res->bb = hsc[S_BB];
+  return FE_OK;
+}
+
 int pcg_status(int state, const char* who) {
   switch (state) {
     case ST_CONV:
@@ -638,6 +915,8 @@ int pcg_check_args(const fe_pa* pa, int op, int pc, const double* b, const doubl
 extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol,
                       int maxit, fe_pcg_stats* stats, void* stream) {
   clear_error();
+  if (pc == FE_PC_CHEBYSHEV)
+    return fe_pcg_chebyshev(pa, op, 0, 0.0, 0.0, dev_b, dev_x, rtol, maxit, stats, stream);
   const auto t0 = std::chrono::steady_clock::now();
   if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   int st = pcg_check_args(pa, op, pc, dev_b, dev_x, rtol, maxit, "fe_pcg");
@@ -912,4 +1191,76 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
     default:
       return set_error(FE_ERR_NOT_CONVERGED, "fe_pcg_noalloc: maxit reached before rtol");
   }
+}
+
+namespace {
+constexpr int kChebDegree = 4;       // default steps of the Chebyshev preconditioner
+constexpr double kChebRatio = 30.0;  // default hi / lo of its interval
+constexpr double kChebSafety = 1.1;  // hi = kChebSafety x the power-iteration estimate
+constexpr int kPowerIters = 20;
+}  // namespace
+
+extern "C" int fe_estimate_lmax(fe_pa* pa, int op, int iters, double* lmax, void* stream) {
+  clear_error();
+  if (!pa || !lmax) return set_error(FE_ERR_ARG, "fe_estimate_lmax: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_estimate_lmax: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_estimate_lmax: operator not set up");
+  if (iters < 0 || iters > 1000) return set_error(FE_ERR_ARG, "fe_estimate_lmax: iters in 0..1000");
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgWork w;
+  double* extra = nullptr;
+  int st;
+  if ((st = pcg_workspace(pa, 7, &w, &extra)) != FE_OK) return st;
+  int launches = 0;
+  if ((st = pcg_jacobi(pa, op, w, s, &launches)) != FE_OK) return st;
+  const int64_t n = pa->mesh->ndofs;
+  return cheb_lmax(pa, op, pa->variant, w.d, extra, extra + n, w, s, iters, &launches, lmax);
+}
+
+extern "C" int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, double lmin_ratio,
+                                const double* dev_b, double* dev_x, double rtol, int maxit,
+                                fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  int st = pcg_check_args(pa, op, FE_PC_JACOBI, dev_b, dev_x, rtol, maxit, "fe_pcg_chebyshev");
+  if (st != FE_OK) return st;
+  if (degree == 0) degree = kChebDegree;
+  if (lmin_ratio == 0.0) lmin_ratio = kChebRatio;
+  if (degree < 1 || degree > 32)
+    return set_error(FE_ERR_ARG, "fe_pcg_chebyshev: degree must lie in 1..32");
+  if (!(lmin_ratio > 1.0) || !(lmax >= 0.0) || !std::isfinite(lmax))
+    return set_error(FE_ERR_ARG, "fe_pcg_chebyshev: need lmin_ratio > 1 and lmax >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgWork w;
+  double* extra = nullptr;
+  if ((st = pcg_workspace(pa, 7, &w, &extra)) != FE_OK) return st;
+  const int64_t n = pa->mesh->ndofs;
+  PcgResult res;
+  if ((st = pcg_jacobi(pa, op, w, s, &res.launches)) != FE_OK) return st;
+  double hi = lmax;
+  if (hi == 0.0) {
+    double& cached = pa->cheb_lmax[op == FE_DIFFUSION ? 0 : 1];
+    if (cached <= 0.0 &&
+        (st = cheb_lmax(pa, op, pa->variant, w.d, extra, extra + n, w, s, kPowerIters,
+                        &res.launches, &cached)) != FE_OK)
+      return st;
+    hi = kChebSafety * cached;
+  }
+  if ((st = pcg_run_cheb(pa, op, pa->variant, dev_b, dev_x, w.d, degree, hi / lmin_ratio, hi, rtol,
+                         maxit, w, extra, extra + n, s, &res)) != FE_OK)
+    return st;
+  double true_rel = 0.0;
+  if ((st = pcg_true_residual(pa, op, pa->variant, dev_b, dev_x, nullptr, w, s, &res.launches,
+                              &true_rel)) != FE_OK)
+    return st;
+  if (stats) {
+    stats->iters = res.iters;
+    stats->rel_resid = res.rel;
+    stats->true_rel_resid = true_rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = res.launches;
+    stats->outer_iters = 1;
+  }
+  return pcg_status(res.state, "fe_pcg_chebyshev");
 }

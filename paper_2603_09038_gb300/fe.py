@@ -27,6 +27,7 @@ FE_DIFFUSION = 1
 FE_MASS = 2
 FE_PC_NONE = 0
 FE_PC_JACOBI = 1
+FE_PC_CHEBYSHEV = 2
 FE_VARIANT_F64 = 0
 FE_VARIANT_F32X2 = 1
 FE_VARIANT_F64_DMMA = 2
@@ -75,6 +76,11 @@ _SIGS = {
     "fe_pcg_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_probe_throughput": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "fe_pcg_chebyshev": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_estimate_lmax": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double), _VP]),
     "fe_lpc_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                      ctypes.POINTER(_VP)]),
     "fe_lpc_nparams": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
@@ -232,6 +238,25 @@ def fe_pcg_ir(pa, op, pc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=None
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_pcg_chebyshev(pa, op, dev_b, dev_x, rtol, maxit, degree=0, lmax=0.0, lmin_ratio=0.0,
+                     stream=None):
+    """Chebyshev-polynomial-preconditioned CG (see include/fe.h); same return value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_pcg_chebyshev(_VP(pa), int(op), int(degree), float(lmax), float(lmin_ratio),
+                                  _ptr(dev_b), _ptr(dev_x), float(rtol), int(maxit),
+                                  ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
+
+
+def fe_estimate_lmax(pa, op, iters=20, stream=None):
+    v = ctypes.c_double()
+    _check(load().fe_estimate_lmax(_VP(pa), int(op), int(iters), ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 FE_PCG_NOALLOC_MAX_DOFS = 262144

@@ -141,3 +141,79 @@ def test_iterative_refinement_on_the_poisson_workload():
         assert s2["true_rel_resid"] <= 1e-8
         d = float((x1 - x2).abs().max() / x1.abs().max())
         assert d < 1e-6, d
+
+
+def _bc_system(prob):
+    m = boundary_mask(prob.nx, prob.ny, prob.nz, prob.p).astype(np.float64)
+    keep = 1.0 - m
+    A = oop.assemble(prob, DIFFUSION).toarray()
+    Abc = keep[:, None] * A * keep[None, :] + np.diag(m)
+    return A, Abc, keep
+
+
+def test_chebyshev_pcg_matches_oracle_and_estimate_bounds():
+    """fe_pcg_chebyshev with the oracle's exact lambda_max: the same iteration count as the
+    oracle's Chebyshev-PCG (same polynomial), the dense solution; fe_estimate_lmax is a lower
+    bound within 15 % of the exact value after 20 power steps."""
+    from oracle.solve import pcg_prec, chebyshev
+    torch = torch_cuda()
+    dims, p = (5, 4, 4), 3
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        A, Abc, keep = _bc_system(prob)
+        dg = np.diag(Abc)
+        s = np.sqrt(dg)
+        lmax = float(np.linalg.eigvalsh(Abc / s[:, None] / s[None, :]).max())
+        est = fe.fe_estimate_lmax(pa, fe.FE_DIFFUSION, 20)
+        assert 0.85 * lmax <= est <= lmax * (1 + 1e-10), (est, lmax)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        for variant in ("f64", "f32x2"):
+            fe.fe_pa_set_variant(pa, variant)
+            st, stats = fe.fe_pcg_chebyshev(pa, fe.FE_DIFFUSION, b, x, 1e-10, 2000, degree=4,
+                                            lmax=lmax, lmin_ratio=30.0)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert stats["rel_resid"] <= 1e-10 and stats["true_rel_resid"] <= 1e-9
+            bh = b.cpu().numpy() * keep
+            Aop = lambda v: keep * (A @ (keep * v))
+            xo, ito, _ = pcg_prec(Aop, bh, lambda r: chebyshev(Aop, keep / dg, r, 4, lmax / 30, lmax),
+                                  rtol=1e-10)
+            assert abs(stats["iters"] - ito) <= 1, (stats["iters"], ito)
+            xr = np.linalg.solve(Abc, bh)
+            assert np.abs(x.cpu().numpy() - xr).max() <= 1e-8 * np.abs(xr).max()
+
+
+def test_pcg_chebyshev_default_beats_jacobi_iterations():
+    torch = torch_cuda()
+    n, p = 12, 3
+    with gpu_problem(n, n, n, p, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, "f32x2")
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        xj, xc = torch.empty_like(b), torch.empty_like(b)
+        st, sj = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xj, 1e-8, 5000)
+        assert st == fe.FE_OK
+        st, sc = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, b, xc, 1e-8, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert sc["true_rel_resid"] <= 1e-7
+        assert 2 * sc["iters"] < sj["iters"], (sc, sj)
+        d = (xc - xj).abs().max().item() / xj.abs().max().item()
+        assert d <= 1e-6
+
+
+def test_chebyshev_argument_errors():
+    torch = torch_cuda()
+    with gpu_problem(3, 3, 3, 2) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.ones(n, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        for kw in ({"degree": 33}, {"degree": -1}, {"lmin_ratio": 1.0}, {"lmax": -1.0}):
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_pcg_chebyshev(pa, fe.FE_DIFFUSION, b, x, 1e-8, 10, **kw)
+            assert e.value.status == fe.FE_ERR_ARG
+        with pytest.raises(fe.FEError):
+            fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, b, x, 1e-8, 10)
+        with pytest.raises(fe.FEError):
+            fe.fe_estimate_lmax(pa, fe.FE_DIFFUSION, -1)
