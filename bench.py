@@ -529,6 +529,47 @@ def run_learned(args, local_rank):
     return 0
 
 
+def run_graphs(args, local_rank):
+    """--graphs: Jacobi-PCG time to 1e-8 with the iteration batches replayed as CUDA graphs vs
+    launched kernel by kernel, Poisson, p = --p, on meshes from 8^3 to --n^3 (one JSON line each)."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for n in [m for m in (8, 16, 32, 64) if m <= args.n]:
+        mesh = fe.fe_mesh_setup(n, n, n, args.p, perturbed_vertices(n, n, n))
+        pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+        fe.fe_pa_set_variant(pa, args.variant)
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        fe.fe_load_vector_sine(pa, b)
+        out = {"graphs": True, "workload": "poisson_%dcubed_p%d" % (n, args.p), "ndofs": nd,
+               "variant": args.variant}
+        for mode in (1, 0):
+            fe.fe_pcg_set_graphs(pa, mode)
+            for _ in range(2):
+                fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+            torch.cuda.synchronize()
+            reps = max(3, args.steps)
+            e0.record(stream)
+            for _ in range(reps):
+                st, s_ = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            key = "graph" if mode else "eager"
+            out[key + "_ms"] = e0.elapsed_time(e1) / reps
+            out[key + "_iters"] = s_["iters"]
+        out["speedup"] = out["eager_ms"] / out["graph_ms"]
+        print(json.dumps(out), flush=True)
+        fe.fe_pa_destroy(pa)
+        fe.fe_mesh_destroy(mesh)
+    return 0
+
+
 def run_sweep(args, local_rank):
     """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1): device time of one
     apply (median of 10 after 3 warm-ups, CUDA events) per operator and variant, one JSON line
@@ -655,6 +696,8 @@ def main():
     ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
     ap.add_argument("--learned", action="store_true",
                     help="only the learned-preconditioner comparison (with --n, --p, --sigma)")
+    ap.add_argument("--graphs", action="store_true",
+                    help="PCG with and without CUDA-graph replay on 8^3 .. --n^3 meshes")
     ap.add_argument("--sigma", type=float, default=0.0,
                     help="--learned: log-normal coefficient sigma (0: Poisson)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -680,6 +723,8 @@ def main():
         return run_batched(args, local_rank)
     if args.learned:
         return run_learned(args, local_rank)
+    if args.graphs:
+        return run_graphs(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

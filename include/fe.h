@@ -169,6 +169,14 @@ int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, double lmin_rat
  * quotient (v.Av)/(v.Dv) of the last iterate, a lower bound of lambda_max.  Synchronous. */
 int fe_estimate_lmax(fe_pa* pa, int op, int iters, double* lmax, void* stream);
 
+/* fe_pcg (Jacobi / none) enqueues its iterations in batches of 8 between two reads of the
+ * device-resident stop flag.  By default the first batch is launched kernel by kernel and the
+ * next ones are one captured CUDA graph of 8 iterations replayed with a single launch each
+ * (captured on a private stream, so any caller stream works; if the capture fails, the kernels
+ * are launched one by one).  enable = 0 turns the graphs off for this handle (same kernels and
+ * results, more launch overhead on small meshes). */
+int fe_pcg_set_graphs(fe_pa* pa, int enable);
+
 /* Mixed-precision iterative refinement around an FP32 inner PCG (an extension; the paper
  * itself stays in FP64 throughout).  Outer loop, in FP64 vectors:
  *   r = (1-m)(b - A x)   with the handle's FP64-accurate operator (FE_VARIANT_F64, or

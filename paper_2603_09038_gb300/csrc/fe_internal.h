@@ -68,6 +68,7 @@ struct fe_pa {
   double* d_dpart = nullptr;       // per-block partials of the apply-fused p.Ap
   int64_t dpart_cap = 0;
   double cheb_lmax[2] = {0.0, 0.0};  // cached lambda_max estimates of D^-1 A (diffusion, mass)
+  bool pcg_graphs = true;          // fe_pcg replays its iteration batches as CUDA graphs
 };
 
 namespace fe {

@@ -543,6 +543,43 @@ struct PcgWork {
   int* flags;
 };
 
+// One batch of PCG iterations captured as a CUDA graph (on a private stream: the caller's may be
+// the legacy stream, which cannot be captured) and replayed on the caller's stream with one
+// launch.  The captured kernels read every scalar from device memory, so the same graph serves
+// all batches of a solve.  A capture that fails leaves `failed` set and the caller enqueues
+// kernels one by one instead (same kernels, same results).
+struct GraphBatch {
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+  bool failed = false;
+  template <typename Fn>
+  void capture(Fn&& enqueue) {
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    failed = true;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int st = enqueue(cs);
+      const cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (st == FE_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&exec, g, 0) == cudaSuccess)
+        failed = false;
+      else
+        exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();  // a failed capture is not an error of the solve
+    clear_error();
+  }
+  ~GraphBatch() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 struct PcgResult {
   int state = ST_RUN, iters = 0, launches = 0;
   double rel = 0.0, bb = 0.0;
@@ -629,30 +666,51 @@ int pcg_run(fe_pa* pa, int op, int variant, const double* b, double* x, const do
   k_finish_init<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags);
   if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg: init launch");
   res->launches += 2;
+  // `count` iterations on stream q; returns the kernels enqueued through *nk
+  auto enqueue = [&](cudaStream_t q, int count, int* nk) -> int {
+    for (int j = 0; j < count; ++j) {
+      if (fused_dot) {
+        int st = apply_dispatch(pa, op, variant, w.p, w.q, q, w.flags, pa->d_dpart);
+        if (st != FE_OK) return st;
+        k_finish_pq_var<<<1, kFinishThreads, 0, q>>>(pa->d_dpart, nblk, w.sc, w.flags);
+        *nk += 2;
+      } else {
+        int st = apply_dispatch(pa, op, variant, w.p, w.q, q, w.flags);
+        if (st != FE_OK) return st;
+        k_dot<<<kReduceBlocks, kReduceThreads, 0, q>>>(w.p, w.q, n, w.part0, w.flags);
+        k_finish_pq<<<1, kFinishThreads, 0, q>>>(w.part0, w.sc, w.flags);
+        *nk += 3;
+      }
+      k_update<<<kReduceBlocks, kReduceThreads, 0, q>>>(x, w.r, w.z, w.p, w.q, dj, mask, n, w.sc,
+                                                          w.part0, w.part1, w.flags);
+      k_finish_update<<<1, kFinishThreads, 0, q>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
+      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, q>>>(w.p, w.z, w.q, n, w.sc, w.flags);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_error(e, "fe_pcg: iteration launch");
+      *nk += 3;
+    }
+    return FE_OK;
+  };
   int hflags[4] = {0, 0, 0, 0};
   int queued = 0;
+  GraphBatch graph;
   for (;;) {
-    for (int j = 0; j < kBatch && queued < maxit; ++j, ++queued) {
-      if (fused_dot) {
-        int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags, pa->d_dpart);
-        if (st != FE_OK) return st;
-        k_finish_pq_var<<<1, kFinishThreads, 0, s>>>(pa->d_dpart, nblk, w.sc, w.flags);
-        res->launches += 2;
-      } else {
-        int st = apply_dispatch(pa, op, variant, w.p, w.q, s, w.flags);
-        if (st != FE_OK) return st;
-        k_dot<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.q, n, w.part0, w.flags);
-        k_finish_pq<<<1, kFinishThreads, 0, s>>>(w.part0, w.sc, w.flags);
-        res->launches += 3;
-      }
-      k_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, w.r, w.z, w.p, w.q, dj, mask, n, w.sc,
-                                                          w.part0, w.part1, w.flags);
-      k_finish_update<<<1, kFinishThreads, 0, s>>>(w.part0, w.part1, w.sc, w.flags, rtol, maxit);
-      k_pupdate<<<kReduceBlocks, kReduceThreads, 0, s>>>(w.p, w.z, w.q, n, w.sc, w.flags);
-      if ((err = cudaGetLastError()) != cudaSuccess)
-        return cuda_error(err, "fe_pcg: iteration launch");
-      res->launches += 3;
+    const int count = maxit - queued < kBatch ? maxit - queued : kBatch;
+    if (queued > 0 && count == kBatch && pa->pcg_graphs && !graph.failed && !graph.exec) {
+      // the first batch ran eagerly (first-use kernel attributes are set); capture the next
+      int nk = 0;
+      graph.capture([&](cudaStream_t q) { return enqueue(q, kBatch, &nk); });
+      graph.kernels = nk;
     }
+    if (graph.exec && count == kBatch) {
+      if ((err = cudaGraphLaunch(graph.exec, s)) != cudaSuccess)
+        return cuda_error(err, "fe_pcg: graph launch");
+      res->launches += graph.kernels;
+    } else {
+      int st = enqueue(s, count, &res->launches);
+      if (st != FE_OK) return st;
+    }
+    queued += count;
     if ((err = cudaMemcpyAsync(hflags, w.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
         (err = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1263,4 +1321,11 @@ extern "C" int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, doub
     stats->outer_iters = 1;
   }
   return pcg_status(res.state, "fe_pcg_chebyshev");
+}
+
+extern "C" int fe_pcg_set_graphs(fe_pa* pa, int enable) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_pcg_set_graphs: pa is NULL");
+  pa->pcg_graphs = enable != 0;
+  return FE_OK;
 }

@@ -79,6 +79,7 @@ _SIGS = {
     "fe_pcg_chebyshev": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_double, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_pcg_set_graphs": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fe_estimate_lmax": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_double), _VP]),
     "fe_lpc_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -251,6 +252,10 @@ def fe_pcg_chebyshev(pa, op, dev_b, dev_x, rtol, maxit, degree=0, lmax=0.0, lmin
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_pcg_set_graphs(pa, enable):
+    _check(load().fe_pcg_set_graphs(_VP(pa), int(bool(enable))))
 
 
 def fe_estimate_lmax(pa, op, iters=20, stream=None):

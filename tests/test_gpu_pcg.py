@@ -217,3 +217,29 @@ def test_chebyshev_argument_errors():
             fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, b, x, 1e-8, 10)
         with pytest.raises(fe.FEError):
             fe.fe_estimate_lmax(pa, fe.FE_DIFFUSION, -1)
+
+
+@pytest.mark.parametrize("variant,maxit", [("f32x2", 5000), ("f64", 5000), ("dmma", 5000), ("f32x2", 21)])
+def test_pcg_graph_replay_matches_eager(variant, maxit):
+    """Iteration batches replayed as CUDA graphs give the same solve as kernel-by-kernel launches
+    (atomics may change the last bits, so iterations within 1 and solutions within 1e-10), and
+    stop at maxit exactly when it is not a multiple of the batch."""
+    torch = torch_cuda()
+    with gpu_problem(8, 8, 8, 3, sigma=1.0, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        xg, xe = torch.empty_like(b), torch.empty_like(b)
+        fe.fe_pcg_set_graphs(pa, 1)
+        st_g, sg = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xg, 1e-10, maxit)
+        fe.fe_pcg_set_graphs(pa, 0)
+        st_e, se = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xe, 1e-10, maxit)
+        assert st_g == st_e
+        if maxit == 21:
+            assert st_g == fe.FE_ERR_NOT_CONVERGED and sg["iters"] == se["iters"] == 21
+        else:
+            assert st_g == fe.FE_OK and abs(sg["iters"] - se["iters"]) <= 1
+        assert sg["launches"] == se["launches"] or maxit != 21
+        d = (xg - xe).abs().max().item() / xe.abs().max().item()
+        assert d <= 1e-10 if maxit != 21 else d <= 1e-12
