@@ -570,6 +570,59 @@ def run_graphs(args, local_rank):
     return 0
 
 
+def run_batched_pcg(args, local_rank):
+    """--batched-pcg N: N right-hand sides solved by fe_pcg_batched (one batched apply per
+    iteration) against N single fe_pcg solves, on the --n^3, order --p Poisson mesh."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    n, p, nr = args.n, args.p, args.batched_pcg
+    mesh = fe.fe_mesh_setup(n, n, n, p, perturbed_vertices(n, n, n))
+    pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+    fe.fe_pa_set_variant(pa, args.variant)
+    nd, _, _ = fe.fe_mesh_sizes(mesh)
+    stream = torch.cuda.current_stream()
+    sine = torch.empty(nd, dtype=torch.float64, device="cuda")
+    fe.fe_load_vector_sine(pa, sine)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    B = torch.stack([sine * (1.0 + 0.1 * j) + 0.01 * torch.rand(nd, dtype=torch.float64,
+                                                                  device="cuda", generator=g)
+                     for j in range(nr)]).reshape(-1).contiguous()
+    X = torch.empty_like(B)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, nr, B, nd, X, nd, args.rtol, MAXIT, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st, stats = fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, nr, B, nd, X, nd, args.rtol,
+                                  MAXIT, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) / 1000.0
+    x1 = torch.empty(nd, dtype=torch.float64, device="cuda")
+    fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, B[:nd], x1, args.rtol, MAXIT, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    iters1 = []
+    for j in range(nr):
+        st1, s1 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, B[j * nd:(j + 1) * nd], x1,
+                            args.rtol, MAXIT, stream)
+        iters1.append(s1["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_s = e0.elapsed_time(e1) / 1000.0
+    print(json.dumps({"batched_pcg": True, "workload": "poisson_%dcubed_p%d" % (n, p), "nrhs": nr,
+                      "ndofs": nd, "variant": args.variant, "status": st,
+                      "batched_s": t_b, "single_solves_s": t_s, "speedup": t_s / t_b,
+                      "gdofs_per_rhs_iter_batched": nd * sum(x["iters"] for x in stats) / t_b / 1e9,
+                      "iters_batched": [x["iters"] for x in stats], "iters_single": iters1,
+                      "max_true_rel_resid": max(x["true_rel_resid"] for x in stats)}))
+    fe.fe_pa_destroy(pa)
+    fe.fe_mesh_destroy(mesh)
+    return 0
+
+
 def run_sweep(args, local_rank):
     """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1): device time of one
     apply (median of 10 after 3 warm-ups, CUDA events) per operator and variant, one JSON line
@@ -696,6 +749,8 @@ def main():
     ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
     ap.add_argument("--learned", action="store_true",
                     help="only the learned-preconditioner comparison (with --n, --p, --sigma)")
+    ap.add_argument("--batched-pcg", type=int, default=0,
+                    help="this many right-hand sides by fe_pcg_batched vs single solves")
     ap.add_argument("--graphs", action="store_true",
                     help="PCG with and without CUDA-graph replay on 8^3 .. --n^3 meshes")
     ap.add_argument("--sigma", type=float, default=0.0,
@@ -725,6 +780,8 @@ def main():
         return run_learned(args, local_rank)
     if args.graphs:
         return run_graphs(args, local_rank)
+    if args.batched_pcg:
+        return run_batched_pcg(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

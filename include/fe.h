@@ -192,6 +192,20 @@ int fe_pcg_set_graphs(fe_pa* pa, int enable);
 int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
               double inner_rtol, fe_pcg_stats* stats, void* stream);
 
+/* Batched Jacobi- (or un-) preconditioned CG: nrhs independent systems A_bc x_j = b_j with the
+ * same operator (the batched-RHS extension; the paper solves one system), b_j = dev_b + j*ldb,
+ * x_j = dev_x + j*ldx (leading dimensions in elements, >= ndofs; 1 <= nrhs <= 1024).  The systems
+ * advance in lockstep so that each iteration applies the operator to all search directions in
+ * one batched launch (FE_VARIANT_F64, F32X2, F32; the DMMA variant applies them one by one);
+ * each keeps its own scalars and stops on its own residual, and the call returns when all have
+ * stopped.  Same system, stopping rule and iteration batches (with CUDA-graph replay) as
+ * fe_pcg.  stats: NULL or an array of nrhs (iters, residuals per system; seconds and launches of
+ * the whole call).  Allocates its work vectors (4 nrhs + 1 of ndofs) per call.  Returns FE_OK
+ * when every system converged, else the first failing system's status (see stats). */
+int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double* dev_b, int64_t ldb,
+                   double* dev_x, int64_t ldx, double rtol, int maxit, fe_pcg_stats* stats,
+                   void* stream);
+
 /* fe_pcg without any device allocation (the paper has no counterpart: this is a service for
  * callers that cannot allocate).  Some applications give all device memory to their own pool
  * allocator up front, and some latency-critical loops cannot afford the blocking and device

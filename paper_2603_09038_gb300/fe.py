@@ -80,6 +80,9 @@ _SIGS = {
                                         ctypes.c_double, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_set_graphs": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_pcg_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                      ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_estimate_lmax": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_double), _VP]),
     "fe_lpc_create": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -252,6 +255,18 @@ def fe_pcg_chebyshev(pa, op, dev_b, dev_x, rtol, maxit, degree=0, lmax=0.0, lmin
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_pcg_batched(pa, op, pc, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stream=None):
+    """nrhs systems in lockstep with one batched apply per iteration; returns (status, [stats])."""
+    lib = load()
+    st = (fe_pcg_stats * int(nrhs))()
+    status = lib.fe_pcg_batched(_VP(pa), int(op), int(pc), int(nrhs), _ptr(dev_b), int(ldb),
+                                _ptr(dev_x), int(ldx), float(rtol), int(maxit), st,
+                                _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, [_stats(x) for x in st]
 
 
 def fe_pcg_set_graphs(pa, enable):

@@ -243,3 +243,65 @@ def test_pcg_graph_replay_matches_eager(variant, maxit):
         assert sg["launches"] == se["launches"] or maxit != 21
         d = (xg - xe).abs().max().item() / xe.abs().max().item()
         assert d <= 1e-10 if maxit != 21 else d <= 1e-12
+
+
+@pytest.mark.parametrize("variant", ["f32x2", "f64", "dmma"])
+def test_pcg_batched_matches_single_solves(variant):
+    """fe_pcg_batched on 5 right-hand sides (padded leading dimensions, one zero system) gives each
+    system the solve fe_pcg gives it alone: iterations within 1, solutions within 1e-9."""
+    torch = torch_cuda()
+    dims, p = (6, 5, 4), 3
+    with gpu_problem(*dims, p, sigma=1.0, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        nr, ld = 5, n + 7
+        rng = np.random.default_rng(3)
+        Bh = np.zeros((nr, ld))
+        sine = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, sine)
+        Bh[0, :n] = sine.cpu().numpy()
+        Bh[1, :n] = rng.standard_normal(n)
+        Bh[2, :n] = 0.0                       # converges at once
+        Bh[3, :n] = 3.0 * sine.cpu().numpy() + rng.uniform(-1, 1, n)
+        Bh[4, :n] = rng.uniform(0, 1, n)
+        B = torch.from_numpy(Bh.reshape(-1)).cuda()
+        X = torch.full((nr * ld,), 7.0, dtype=torch.float64, device="cuda")
+        st, stats = fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, nr, B, ld, X, ld,
+                                      1e-10, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert stats[2]["iters"] == 0
+        Xh = X.cpu().numpy().reshape(nr, ld)
+        assert np.all(Xh[2, :n] == 0.0)
+        assert np.all(Xh[:, n:] == 7.0)       # padding untouched
+        x1 = torch.empty(n, dtype=torch.float64, device="cuda")
+        for j in (0, 1, 3, 4):
+            b1 = torch.from_numpy(np.ascontiguousarray(Bh[j, :n])).cuda()
+            st1, s1 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b1, x1, 1e-10, 5000)
+            assert st1 == fe.FE_OK
+            assert abs(stats[j]["iters"] - s1["iters"]) <= 1, (j, stats[j], s1)
+            assert stats[j]["rel_resid"] <= 1e-10 and stats[j]["true_rel_resid"] <= 1e-9
+            ref = x1.cpu().numpy()
+            assert np.abs(Xh[j, :n] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_pcg_batched_failure_is_per_system():
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 2, ops=1) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        sine = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, sine)
+        B = torch.stack([sine, sine.clone(), sine.clone()]).reshape(-1).contiguous()
+        B[n + n // 2] = float("nan")          # an interior dof of system 1
+        X = torch.empty_like(B)
+        st, stats = fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, 3, B, n, X, n, 1e-10, 500)
+        assert st == fe.FE_ERR_NAN
+        assert stats[0]["rel_resid"] <= 1e-10 and stats[2]["rel_resid"] <= 1e-10
+        assert stats[0]["iters"] == stats[2]["iters"] > 0
+        st, stats = fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, 1, sine, n, X, n, 1e-12, 3)
+        assert st == fe.FE_ERR_NOT_CONVERGED and stats[0]["iters"] == 3
+        for args in ((0, n, n), (2, n - 1, n), (2, n, n - 1)):
+            with pytest.raises(fe.FEError):
+                fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, args[0], B, args[1], X,
+                                  args[2], 1e-8, 10)
+        with pytest.raises(fe.FEError):
+            fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, 1, sine, n, X, n, 1e-8, 10)
