@@ -363,6 +363,10 @@ def run_ours(args, rank, world, local_rank):
             "hbm_gbs": nb / (ms * 1e-3) / 1e9, "hbm_frac": nb / (ms * 1e-3) / 1e9 / hbm_peak,
             "fp64_tflops_equiv": flops / (ms * 1e-3) / 1e12,
         }
+    autotune = None
+    if world == 1:
+        best, ms_at = fe.fe_pa_autotune(pa, fe.FE_DIFFUSION, 1, 10, stream)
+        autotune = {"chosen": best, "ms": ms_at, "nrhs": 1}
     fe.fe_pa_set_variant(pa, args.variant)
     k = kernels[args.variant]
     hbm_obj = {"achieved": k["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["hbm_frac"],
@@ -406,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
                       "parallelism": "independent problem per GPU"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
            "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir, "pcg_chebyshev": pcg_cheb,
-           "learned_fcg": learned,
+           "learned_fcg": learned, "autotune": autotune,
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result

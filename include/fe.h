@@ -111,6 +111,16 @@ int fe_pa_setup(const fe_mesh* mesh, int q1d, const double* dev_coeff, int ops, 
 int fe_pa_set_variant(fe_pa* pa, int variant, void* stream);
 int fe_pa_get_variant(const fe_pa* pa, int* variant);
 
+/* Autotuner of the arithmetic (an extension): times one apply of op (nrhs right-hand sides in
+ * one batched launch, 1..64) with each FP64-accurate variant -- FE_VARIANT_F32X2, FE_VARIANT_F64
+ * and, for nrhs = 1, FE_VARIANT_F64_DMMA -- as the mean of `reps` launches after one
+ * warm-up (CUDA events on `stream`), selects the fastest with fe_pa_set_variant, and returns it
+ * in *best_variant; ms (NULL or double[4], indexed by fe_variant) gets the times, -1 where not
+ * timed.  FE_VARIANT_F32 is not a candidate (not FP64-accurate).  Allocates 2 nrhs vectors of
+ * scratch.  Synchronous. */
+int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, double* ms,
+                   void* stream);
+
 /* y = A x on the full L-vector (no boundary conditions), with the handle's variant.
  * Overwrites y (it is zeroed, then accumulated by atomic scatter-add).  Asynchronous. */
 int fe_apply_diffusion(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream);

@@ -398,6 +398,13 @@ int apply_f32_vectors(const fe_pa* pa, int op, const float* x, float* y, cudaStr
 }  // namespace fe
 
 // ------------------------------------------------------------------------------- C ABI
+// x_i = sin(0.001 i) + 1.5: a smooth, nonzero input for timing runs
+__global__ void k_load_sine_like(double* __restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = sin(0.001 * (double)(i % 100000)) + 1.5;
+}
+
 extern "C" {
 
 const char* fe_last_error(void) { return g_last_error.c_str(); }
@@ -611,6 +618,64 @@ int fe_pa_get_variant(const fe_pa* pa, int* variant) {
   if (!pa || !variant) return set_error(FE_ERR_ARG, "fe_pa_get_variant: null argument");
   *variant = pa->variant;
   return FE_OK;
+}
+
+int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, double* ms,
+                   void* stream) {
+  clear_error();
+  if (!pa || !best_variant) return set_error(FE_ERR_ARG, "fe_pa_autotune: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pa_autotune: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pa_autotune: operator not set up");
+  if (nrhs < 1 || nrhs > 64 || reps < 1 || reps > 1000)
+    return set_error(FE_ERR_ARG, "fe_pa_autotune: need 1 <= nrhs <= 64 and 1 <= reps <= 1000");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = pa->mesh->ndofs;
+  double *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&x, sizeof(double) * n * nrhs)) != cudaSuccess ||
+      (err = cudaMalloc(&y, sizeof(double) * n * nrhs)) != cudaSuccess ||
+      (err = cudaEventCreate(&e0)) != cudaSuccess || (err = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaFree(x);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    return cuda_error(err, "fe_pa_autotune: setup");
+  }
+  // any input gives the same work; a smooth, nonzero one keeps the arithmetic representative
+  k_load_sine_like<<<256, 256, 0, s>>>(x, n * nrhs);
+  const int cand[3] = {FE_VARIANT_F32X2, FE_VARIANT_F64, FE_VARIANT_F64_DMMA};
+  double t[4] = {-1.0, -1.0, -1.0, -1.0};
+  int best = -1, st = FE_OK;
+  for (int c = 0; c < 3 && st == FE_OK; ++c) {
+    const int v = cand[c];
+    if (v == FE_VARIANT_F64_DMMA && nrhs > 1) continue;  // no batched DMMA kernel
+    if ((st = fe_pa_set_variant(pa, v, stream)) != FE_OK) break;
+    for (int r = 0; r <= reps && st == FE_OK; ++r) {  // the first launch is a warm-up
+      if (r == 1) cudaEventRecord(e0, s);
+      st = apply_dispatch(pa, op, v, x, y, s, nullptr, nullptr, nullptr, false, nrhs, n, n);
+    }
+    if (st != FE_OK) break;
+    cudaEventRecord(e1, s);
+    if ((err = cudaEventSynchronize(e1)) != cudaSuccess) {
+      st = cuda_error(err, "fe_pa_autotune: timing");
+      break;
+    }
+    float msf = 0.0f;
+    cudaEventElapsedTime(&msf, e0, e1);
+    t[v] = msf / reps;
+    if (best < 0 || t[v] < t[best]) best = v;
+  }
+  if (st == FE_OK) st = fe_pa_set_variant(pa, best, stream);
+  if (st == FE_OK) {
+    *best_variant = best;
+    if (ms)
+      for (int v = 0; v < 4; ++v) ms[v] = t[v];
+  }
+  cudaFree(x);
+  cudaFree(y);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* dev_y,

@@ -80,6 +80,8 @@ _SIGS = {
                                         ctypes.c_double, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_set_graphs": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_pa_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     "fe_pcg_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
                                       ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
@@ -267,6 +269,17 @@ def fe_pcg_batched(pa, op, pc, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stream
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, [_stats(x) for x in st]
+
+
+def fe_pa_autotune(pa, op, nrhs=1, reps=5, stream=None):
+    """Selects the fastest FP64-accurate variant; returns (variant name, {name: ms})."""
+    import numpy as np
+    best = ctypes.c_int()
+    ms = np.zeros(4)
+    _check(load().fe_pa_autotune(_VP(pa), int(op), int(nrhs), int(reps), ctypes.byref(best),
+                                 _VP(ms.ctypes.data), _stream(stream)))
+    names = {v: k for k, v in VARIANTS.items()}
+    return names[best.value], {names[i]: float(ms[i]) for i in range(4) if ms[i] >= 0}
 
 
 def fe_pcg_set_graphs(pa, enable):

@@ -217,3 +217,25 @@ def test_batched_apply_matches_single_applies(variant):
                 assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
         with pytest.raises(fe.FEError):
             fe.fe_apply_batched(pa, fe.FE_DIFFUSION, variant, 2, X, nd - 1, Y, ld)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_autotune_selects_fastest_accurate_variant(nrhs):
+    torch = torch_cuda()
+    with gpu_problem(12, 12, 12, 3, sigma=1.0) as (fe, mesh, pa, V, c):
+        best, ms = fe.fe_pa_autotune(pa, fe.FE_DIFFUSION, nrhs, 3)
+        assert best in ("f64", "f32x2", "dmma")
+        assert "f32" not in ms and ("dmma" in ms) == (nrhs == 1)
+        assert ms[best] == min(ms.values())
+        assert fe.fe_pa_get_variant(pa) == fe.VARIANTS[best]
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        x = torch.rand(n, dtype=torch.float64, device="cuda") * 2 - 1
+        y, y64 = torch.empty_like(x), torch.empty_like(x)
+        fe.fe_apply_diffusion(pa, x, y)
+        fe.fe_pa_set_variant(pa, "f64")
+        fe.fe_apply(pa, fe.FE_DIFFUSION, "f64", x, y64)
+        torch.cuda.synchronize()
+        assert (y - y64).abs().max().item() <= TOL * y64.abs().max().item()
+        for bad in ((0, 3), (65, 3), (1, 0)):
+            with pytest.raises(fe.FEError):
+                fe.fe_pa_autotune(pa, fe.FE_DIFFUSION, *bad)
