@@ -17,7 +17,8 @@ Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the t
   pcg_chebyshev  Chebyshev-polynomial preconditioned CG (degree 4) to the same residual;
   learned_fcg  the learned element-patch preconditioner (trained on the GPU from the operator's
                own patch solves) inside flexible CG, to the same FP64 residual, against the
-               Jacobi-PCG time above, with its fused BF16 tensor-core kernel timed alone.
+               Jacobi-PCG time above, with its fused BF16 tensor-core kernel timed alone;
+               learned_fcg_linear the same with the linear patch map (width 0).
 
 --impl reference times the CPU oracle alone (the reference of this build) on the same metric.
 Multi-GPU (torchrun): every rank solves its own copy of the problem (independent problems, weak
@@ -325,10 +326,12 @@ def run_ours(args, rank, world, local_rank):
                 "true_rel_resid": cheb_stats[-1]["true_rel_resid"] if cheb_stats else None}
 
     # ---- learned patch preconditioner inside flexible CG, to the same FP64 1e-8 residual
-    learned = None
+    learned = learned_linear = None
     if args.lpc_width > 0:
         learned = learned_fcg(fe, pa, b, x, args, stream, dist, dev, t / args.steps,
                               iters[-1] if iters else None)
+        learned_linear = learned_fcg(fe, pa, b, x, args, stream, dist, dev, t / args.steps,
+                                     iters[-1] if iters else None, width=0)
 
     # ---- the dominant kernel alone: fused diffusion apply, CUDA events on its stream
     def time_apply(variant, reps):
@@ -410,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
                       "parallelism": "independent problem per GPU"},
            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "apply_kernel": kernels,
            "pcg_time_to_1e-8_s": t / args.steps, "pcg_ir": pcg_ir, "pcg_chebyshev": pcg_cheb,
-           "learned_fcg": learned, "autotune": autotune,
+           "learned_fcg": learned, "learned_fcg_linear": learned_linear, "autotune": autotune,
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result
@@ -424,7 +427,7 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters):
+def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=None):
     """The learned element-patch preconditioner inside flexible CG to the same FP64 residual as
     Jacobi-PCG (time t_pcg, pcg_iters iterations): training (data generation from the operator's
     own patch solves + Adam) timed once on the host clock, the solve timed with CUDA events like
@@ -432,7 +435,8 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters):
     import torch
     ndofs, ne, p = fe.fe_mesh_sizes(fe_mesh_of[pa])
     t0 = time.perf_counter()
-    lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, args.lpc_width, 1)
+    width = args.lpc_width if width is None else width
+    lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 1)
     loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -468,7 +472,7 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters):
         z2.record(stream)
     torch.cuda.synchronize()
     ms_lpc = statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
-    din, w = (p + 1) ** 3, args.lpc_width
+    din, w = (p + 1) ** 3, width
     lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
     mma_peak = fe.fe_probe_throughput("bf16_mma")
     bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
@@ -482,7 +486,8 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters):
         "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
         "train_s": t_train, "train_steps": args.lpc_steps, "train_batch": 1024,
         "final_batch_loss": loss, "width": w, "patch": "element, %d dofs" % din,
-        "network": "relu(relu(x W1) W2) W3 + x W0, BF16 weights/activations, FP32 accumulate",
+        "network": ("relu(relu(x W1) W2) W3 + x W0" if w else "x W0 (linear patch map)") +
+                   ", BF16 weights/activations, FP32 accumulate",
         "precond_apply_ms": ms_lpc, "precond_tflops": lpc_flops / (ms_lpc * 1e-3) / 1e12,
         "precond_flops_per_launch": lpc_flops,
         "mma_sync_bf16_probe_tflops": mma_peak,
@@ -527,6 +532,7 @@ def run_learned(args, local_rank):
     out = {"learned": True, "workload": "diffusion_%dcubed_p%d_sigma%g" % (n, p, args.sigma),
            "ndofs": ndofs, "variant": args.variant, "rtol": args.rtol}
     out.update(learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"]))
+    out["linear"] = learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"], width=0)
     fe.fe_pa_destroy(pa)
     fe.fe_mesh_destroy(mesh)
     print(json.dumps(out))

@@ -274,7 +274,9 @@ int fe_probe_throughput(int unit, double* tflops);
 typedef struct fe_lpc fe_lpc;
 
 /* Creates the preconditioner for operator op of pa: He-normal weights W1..W3 (seeded), W0 = 0,
- * the diagonal scalings and the partition-of-unity weights.  width 8..4096.  Synchronous. */
+ * the diagonal scalings and the partition-of-unity weights.  width 8..4096, or 0 for the linear
+ * patch map f(x) = x W0 (no hidden layers; measured to need fewer FCG iterations than the MLP on
+ * these operators, the MLP's nonlinear error acting like preconditioner noise).  Synchronous. */
 int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out);
 
 /* Number of FP32 master weights: 2 * D^3 * width + width^2 + D^6 (W1 [D^3][width],

@@ -7,7 +7,7 @@ and is trained on pairs (x, t) by the relative squared error
     L = sum_b ||y_b - t_b||^2 / sum_b ||t_b||^2.
 The paper has no learned component; this is the textbook MLP and its backpropagation written
 out, pinned by finite differences in tests/test_oracle_mlp.py.  W is (W1, W2, W3, W0); a
-3-tuple means W0 = 0.
+3-tuple means W0 = 0; width 0 (empty W1, W2, W3) is the linear patch map y = x W0.
 """
 import numpy as np
 
@@ -60,9 +60,11 @@ def grad(W, X, T):
 
 
 def init_weights(din, width, seed):
-    """He-normal initialisation (std sqrt(2 / fan_in)) of W1, W2, W3, seeded; W0 = 0."""
+    """He-normal initialisation (std sqrt(2 / fan_in)) of W1, W2, W3, seeded; W0 = 0.  Width 0
+    (no hidden layers: the linear map y = x W0) gives empty W1, W2, W3."""
     rng = np.random.default_rng(seed)
+    sw = np.sqrt(2.0 / width) if width else 0.0
     return (rng.standard_normal((din, width)) * np.sqrt(2.0 / din),
-            rng.standard_normal((width, width)) * np.sqrt(2.0 / width),
-            rng.standard_normal((width, din)) * np.sqrt(2.0 / width),
+            rng.standard_normal((width, width)) * sw,
+            rng.standard_normal((width, din)) * sw,
             np.zeros((din, din)))

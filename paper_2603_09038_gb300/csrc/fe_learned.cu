@@ -5,7 +5,7 @@
 // with W_e = diag(1/multiplicity)^(1/2) on the element's dofs (0 on the Dirichlet boundary),
 // S = diag(A)^(-1/2), and f(x) = relu(relu(x W1) W2) W3 + x W0: a bias-free three-layer MLP
 // D^3 -> width -> width -> D^3 with ReLU plus a linear skip term, BF16 weights and activations,
-// FP32 accumulation on the tensor cores.  With f(x) = S_e^{-1} A_ee^{-1} S_e^{-1} x exactly this is
+// FP32 accumulation on the tensor cores; width 0 keeps only the linear map x W0.  With f(x) = S_e^{-1} A_ee^{-1} S_e^{-1} x exactly this is
 // the symmetrically weighted additive Schwarz method on element patches, which needs about half
 // the iterations of Jacobi on these problems (the one-sided weighting R^T W^2 A_ee^{-1} R does
 // not beat Jacobi).  The symmetric diagonal scaling makes the map nearly the same on every
@@ -355,7 +355,8 @@ int ensure_workspace(fe_lpc* L, int64_t rows) {
   cudaFree(L->dA2b); cudaFree(L->Z1); cudaFree(L->Z2); cudaFree(L->Y); cudaFree(L->Tb);
   cudaFree(L->scale);
   L->cap = 0;
-  const int64_t w = L->width, d = L->din;
+  // hidden-layer buffers get at least 16 bytes so that width 0 (no hidden layers) allocates too
+  const int64_t w = L->width > 0 ? L->width : 1, d = L->din;
   cudaError_t err;
   if ((err = cudaMalloc(&L->Xb, 2 * rows * d)) != cudaSuccess ||
       (err = cudaMalloc(&L->H1b, 2 * rows * w)) != cudaSuccess ||
@@ -377,6 +378,11 @@ int ensure_workspace(fe_lpc* L, int64_t rows) {
 // backward pass only when keep is set.
 int mlp_forward(fe_lpc* L, int64_t rows, cudaStream_t s, bool keep = true) {
   const int d = L->din, w = L->width;
+  if (w == 0) {  // the linear patch map: Y = X W0
+    const cudaError_t e = mlp::gemm<false, false, mlp::EPI_STORE>((int)rows, d, d, L->Xb, d, L->wb,
+                                                                   d, L->Y, d, nullptr, 0, s);
+    return cuda_error(e, "fe_lpc: forward launch");
+  }
   const __nv_bfloat16* W1 = L->wb;
   const __nv_bfloat16* W2 = W1 + (int64_t)d * w;
   const __nv_bfloat16* W3 = W2 + (int64_t)w * w;
@@ -410,7 +416,12 @@ int mlp_loss_grad(fe_lpc* L, int64_t rows, cudaStream_t s, double* loss_out) {
     return cuda_error(err, "fe_lpc: reduction");
   k_loss_terms<<<grid1(rows * d), kT, 0, s>>>(L->Y, L->Tb, rows * d, L->red);
   k_dY<<<grid1(rows * d), kT, 0, s>>>(L->Y, L->Tb, rows * d, L->red, L->dYb);
-  if ((err = cudaGetLastError()) != cudaSuccess ||
+  if (w == 0) {  // linear map: dW0 = X^T dY
+    if ((err = cudaGetLastError()) != cudaSuccess ||
+        (err = mlp::gemm<true, false, mlp::EPI_STORE>(d, d, (int)rows, L->Xb, d, L->dYb, d, g0, d,
+                                                      nullptr, 0, s)) != cudaSuccess)
+      return cuda_error(err, "fe_lpc: backward launch");
+  } else if ((err = cudaGetLastError()) != cudaSuccess ||
       (err = mlp::gemm<true, false, mlp::EPI_STORE>(w, d, (int)rows, L->H2b, w, L->dYb, d, g3, d,
                                                     nullptr, 0, s)) != cudaSuccess ||
       (err = mlp::gemm<false, true, mlp::EPI_RELU_MASK_BF16>((int)rows, w, d, L->dYb, d, W3, d,
@@ -894,8 +905,8 @@ int fused_occupancy() {
 
 // The built (DP, W) pairs of the fused kernel.
 #define FE_FUSED_CASES(X) \
-  X(16, 64) X(16, 128) X(16, 256) X(32, 64) X(32, 128) X(32, 256) X(64, 64) X(64, 128) \
-  X(64, 256) X(128, 64) X(128, 128)
+  X(16, 0) X(16, 64) X(16, 128) X(16, 256) X(32, 0) X(32, 64) X(32, 128) X(32, 256) X(64, 0) \
+  X(64, 64) X(64, 128) X(64, 256) X(128, 0) X(128, 64) X(128, 128)
 
 int fused_occ(int DP, int W) {
 #define FE_OCC_CASE(dp, w) \
@@ -983,7 +994,8 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   if (!pa) return set_error(FE_ERR_ARG, "fe_lpc_create: pa is NULL");
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_lpc_create: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_lpc_create: operator not set up");
-  if (width < 8 || width > 4096) return set_error(FE_ERR_ARG, "fe_lpc_create: width out of range");
+  if ((width != 0 && width < 8) || width > 4096)
+    return set_error(FE_ERR_ARG, "fe_lpc_create: width must be 0 (linear) or 8..4096");
   if (pa->p > kLpcMaxOrder)
     return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_create: orders above 4 are not built");
   fe_lpc* L = new fe_lpc();

@@ -156,7 +156,8 @@ inline cudaError_t gemm(int M, int N, int K, const __nv_bfloat16* A, int lda,
 // A layout), so no activation leaves the registers.  The weights live in shared memory for the
 // whole (persistent) kernel as BF16 images [n][k] (k contiguous, 32-bit words XOR-swizzled by
 // n mod 8 so that the 8 x 4 fragment loads of a warp hit 32 distinct banks), made once per weight
-// update by k_pack_wimg.  DP = D^3 rounded up to a multiple of 16, W = width (a multiple of 64).
+// update by k_pack_wimg.  DP = D^3 rounded up to a multiple of 16, W = width (a multiple of 64,
+// or 0 for the linear patch map f(x) = x W0).
 
 __host__ __device__ constexpr int fused_dp(int din) { return (din + 15) / 16 * 16; }
 
@@ -216,14 +217,15 @@ __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
 }
 
 // Widths up to 128 with D^3 <= 64 are register-capped for two resident blocks per SM (16 warps
-// to hide the gather's memory latency); larger tiles need the full register file of one block.
+// to hide the gather's memory latency); larger tiles need the full register file of one block;
+// the linear map (W = 0) runs three blocks per SM (two for D^3 > 64).
 template <int DP, int W>
-__global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fused(
+__global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 && DP <= 64 ? 2 : 1))) k_lpc_fused(
     const uint4* __restrict__ wimg, const double* __restrict__ r, const int32_t* __restrict__ map,
     const double* __restrict__ fsc, int64_t ne, int din, double* __restrict__ z) {
   using Lay = FusedLayout<DP, W>;
   static_assert(W % 64 == 0 && DP % 16 == 0, "fused MLP tile sizes");
-  constexpr int DPW = DP / 2, WW = W / 2;   // 32-bit words per image row
+  constexpr int DPW = DP / 2, WW = W > 0 ? W / 2 : 1;  // 32-bit words per image row
   constexpr int WPL = (DPW + 31) / 32;      // staging words per lane in the gather
   constexpr int GR = 8 / WPL;               // rows gathered per step (loads in flight)
   extern __shared__ __align__(16) unsigned char smem[];
@@ -300,6 +302,10 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
       }
     }
     __syncwarp();
+    float y[DP / 8][4];
+#pragma unroll
+    for (int j = 0; j < DP / 8; ++j) y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.0f;
+    if constexpr (W > 0) {  // width 0: the linear patch map x W0 alone
     // ---- layer 1: h1 = relu(x W1), 64 output columns at a time
     uint32_t h1[W / 16][4];
 #pragma unroll
@@ -354,10 +360,7 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
         h2[c * 4 + jj][3] = pack_relu(acc[2 * jj + 1][2], acc[2 * jj + 1][3]);
       }
     }
-    // ---- layer 3 and the skip term: y = h2 W3 + x W0
-    float y[DP / 8][4];
-#pragma unroll
-    for (int j = 0; j < DP / 8; ++j) y[j][0] = y[j][1] = y[j][2] = y[j][3] = 0.0f;
+    // ---- layer 3: y = h2 W3
 #pragma unroll
     for (int kk = 0; kk < W / 16; ++kk) {
 #pragma unroll
@@ -368,6 +371,8 @@ __global__ void __launch_bounds__(256, (W <= 128 && DP <= 64 ? 2 : 1)) k_lpc_fus
         mma16816(y[j], h2[kk], b);
       }
     }
+    }  // W > 0
+    // ---- the skip term: y += x W0
 #pragma unroll
     for (int kk = 0; kk < DP / 16; ++kk) {
       const uint32_t a[4] = {xs[g * DPW + swz(g, kk * 8 + t, DPW)],

@@ -44,7 +44,7 @@ def rel_fro(a, b):
     return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("p,width,batch", [(2, 40, 200), (3, 64, 130), (1, 16, 77)])
+@pytest.mark.parametrize("p,width,batch", [(2, 40, 200), (3, 64, 130), (1, 16, 77), (2, 0, 90)])
 def test_loss_grad_matches_oracle(p, width, batch):
     with gpu_problem(2, 2, 2, p) as (fe, mesh, pa, V, c):
         din = (p + 1) ** 3
@@ -65,13 +65,15 @@ def test_loss_grad_matches_oracle(p, width, batch):
             assert rel_fro(Y, Yr) <= 3e-2
             assert abs(loss - Lr) <= 3e-2 * Lr
             for gg, gr in zip(unpack(g.astype(np.float64), din, width), G):
-                assert rel_fro(gg, gr) <= 3e-2
+                if gr.size:
+                    assert rel_fro(gg, gr) <= 3e-2
         finally:
             fe.fe_lpc_destroy(lpc)
 
 
 @pytest.mark.parametrize("dims,p,width", [((4, 3, 3), 2, 32), ((5, 3, 2), 3, 256),
-                                          ((3, 3, 4), 1, 64), ((2, 3, 3), 4, 512)])
+                                          ((3, 3, 4), 1, 64), ((2, 3, 3), 4, 512),
+                                          ((4, 4, 3), 3, 0), ((3, 2, 3), 4, 0)])
 def test_patch_apply_matches_numpy_sum(dims, p, width):
     torch = torch_cuda()
     with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
@@ -186,8 +188,10 @@ def test_lpc_argument_errors():
             fe.fe_lpc_destroy(lpc)
 
 
-@pytest.mark.parametrize("n,p,sigma", [(16, 2, None), (16, 3, None), (16, 3, 1.0)])
-def test_trained_fcg_beats_jacobi_iterations(n, p, sigma):
+@pytest.mark.parametrize("n,p,sigma,width", [(16, 2, None, 128), (16, 3, None, 128),
+                                             (16, 3, 1.0, 128), (16, 3, None, 0),
+                                             (16, 3, 1.0, 0), (16, 2, 1.0, 0)])
+def test_trained_fcg_beats_jacobi_iterations(n, p, sigma, width):
     """The gain test: trained on the operator's own patch solves, FCG reaches the same FP64
     residual as Jacobi-PCG in fewer iterations, and the two solutions agree (Poisson, and a
     log-normal coefficient with sigma = 1)."""
@@ -200,7 +204,7 @@ def test_trained_fcg_beats_jacobi_iterations(n, p, sigma):
         xj, xl = torch.empty_like(b), torch.empty_like(b)
         st, sj = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xj, 1e-8, 20000)
         assert st == fe.FE_OK
-        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 128, 2)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 2)
         try:
             l0 = fe.fe_lpc_train(lpc, 1, 1024, 1e-3)
             l1 = fe.fe_lpc_train(lpc, 2000, 1024, 1e-3)

@@ -56,3 +56,13 @@ def test_positive_homogeneity():
     Y1, _ = mlp.forward(W, X)
     Y3, _ = mlp.forward(W, 3.0 * X)
     np.testing.assert_allclose(Y3, 3.0 * Y1, rtol=1e-14, atol=1e-14)
+
+
+def test_width_zero_is_the_linear_map():
+    rng = np.random.default_rng(9)
+    W = list(mlp.init_weights(5, 0, seed=2))
+    assert W[0].shape == (5, 0) and W[1].shape == (0, 0) and W[2].shape == (0, 5)
+    W[3] = rng.standard_normal((5, 5))
+    X = rng.standard_normal((6, 5))
+    Y, _ = mlp.forward(W, X)
+    np.testing.assert_array_equal(Y, X @ W[3])
