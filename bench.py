@@ -44,7 +44,7 @@ FP64_DFMA_PER_CLK_PER_SM = 2           # measured on GB300 by fe_probe_throughpu
 # DRAM bytes (read + write) of one apply launch from an ncu capture of the same kernel on the
 # 32^3 p=3 mesh, with that launch's algorithmic bytes: scaled to the benchmark's launch by the
 # algorithmic bytes (traffic grows with the elements).  Only for kernels unchanged since.
-NCU_TRAFFIC = {("f32x2", 3): (219.799808e6 + 4.077312e6, 219599376,
+NCU_TRAFFIC = {("f32x2", 3): (219.772672e6 + 4.230912e6, 219599376,
                               "profiles/k_pa_apply_f32x2_p3_poisson32.md")}
 
 
@@ -405,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if args.variant == "f64" else "f32x2",
            "data": "synthetic",
-           "config": {"workload": "poisson_64cubed_p3_jacobi_pcg", "elements": ne, "order": p,
+           "config": {"workload": "poisson_%dcubed_p%d_jacobi_pcg" % (n, p), "elements": ne,
+                      "order": p,
                       "q1d": q, "ndofs": ndofs, "rtol": args.rtol, "preconditioner": "jacobi",
                       "variant": args.variant, "pcg_iters": iters[-1] if iters else None,
                       "applies_per_step": applies / max(1, args.steps),

@@ -14,30 +14,52 @@
 // are dealt out flat to the NT threads, so that warps stay full whatever D and Q are.  A thread
 // keeps its line in registers, contracts it against the 1D tables (kernel parameters, read as
 // constant-bank operands) and writes the results where the next phase's lines are contiguous.
-// Shared-memory arrays are stored "summed index slowest" with every slab padded to an odd
-// number of 8-byte words, so both unit-stride and slab-stride accesses are free of bank
-// conflicts (the concern of Sections III-C/D, solved by layout rather than fragment maps).
+// Shared-memory arrays are stored "summed index slowest" with padded slabs and per-element
+// strides chosen (by a model of every phase's warp accesses, fe_smem_layout.h) to keep bank
+// conflicts low -- the concern of Sections III-C/D, solved by layout rather than fragment maps.
 // The z-direction phase fuses the forward z contraction, the pointwise D and the transposed z
 // contraction in registers, one (qx, qy) column per thread.
 #pragma once
 
 #include "fe_arith.cuh"
+#include "fe_smem_layout.h"
 
 namespace fe {
 
 __host__ __device__ constexpr int odd_pad(int n) { return (n % 2 == 0) ? n + 1 : n; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <int D, int Q, bool DIFF>
+// Field f (0 S_DD, 1 S_QD, 2 S_QQ, 3 SZ_A, 4 SZ_B) of the generated bank-conflict-minimising
+// layout for (D, Q, operator, element bytes, z re-read), or 0 when the table has none.
+__host__ __device__ constexpr int tuned_layout(int D, int Q, bool diff, int es, bool rr, int f) {
+  for (const SmemLayoutEntry& e : kSmemLayouts) {
+    if (e.D == D && e.Q == Q && e.diff == (diff ? 1 : 0) && e.es == es && e.rr == (rr ? 1 : 0)) {
+      return f == 0 ? e.s_dd : f == 1 ? e.s_qd : f == 2 ? e.s_qq : f == 3 ? e.sz_a : e.sz_b;
+    }
+  }
+  return 0;
+}
+
+// Shared-memory strides (in elements of ES bytes): the slabs are padded to an odd number of
+// elements by default; ES != 0 selects the generated layout for that element size and z re-read
+// mode when there is one (fe_smem_layout.h, from smem_layout.py's model of the warp accesses).
+template <int D, int Q, bool DIFF, int ES = 0, bool RR = false>
 struct ApplyLayout {
   static constexpr int D2 = D * D, D3 = D * D * D, Q2 = Q * Q, QD = Q * D;
-  static constexpr int S_DD = odd_pad(D2), S_QD = odd_pad(QD), S_QQ = odd_pad(Q2);
+  static constexpr int TUNED = ES ? tuned_layout(D, Q, DIFF, ES, RR, 3) : 0;
+  static constexpr int S_DD = TUNED ? tuned_layout(D, Q, DIFF, ES, RR, 0) : odd_pad(D2);
+  static constexpr int S_QD = TUNED ? tuned_layout(D, Q, DIFF, ES, RR, 1) : odd_pad(QD);
+  static constexpr int S_QQ = TUNED ? tuned_layout(D, Q, DIFF, ES, RR, 2) : odd_pad(Q2);
   static constexpr int NC_FWD = DIFF ? 2 : 1;  // arrays after the x phase (B x, G x)
   static constexpr int NC_Q = DIFF ? 3 : 1;    // arrays at quadrature points
   // buffer A: E0 [i][line], T2 [c][k][line], S5 [c][qx][line]
-  static constexpr int SZ_A = cmax(D * S_DD, cmax(NC_Q * D * S_QQ, NC_FWD * Q * S_DD));
+  static constexpr int SZ_A_MIN = cmax(D * S_DD, cmax(NC_Q * D * S_QQ, NC_FWD * Q * S_DD));
   // buffer B: T1 [c][j][line], S4 [c][qy][line], Ye [a]
-  static constexpr int SZ_B = cmax(NC_FWD * D * S_QD, cmax(NC_Q * Q * S_QD, D3));
+  static constexpr int SZ_B_MIN = cmax(NC_FWD * D * S_QD, cmax(NC_Q * Q * S_QD, D3));
+  static constexpr int SZ_A = TUNED ? TUNED : SZ_A_MIN;
+  static constexpr int SZ_B = TUNED ? tuned_layout(D, Q, DIFF, ES, RR, 4) : SZ_B_MIN;
+  static_assert(S_DD >= D2 && S_QD >= QD && S_QQ >= Q2 && SZ_A >= SZ_A_MIN && SZ_B >= SZ_B_MIN,
+                "shared-memory layout too small");
   static constexpr int PER_ELEM = SZ_A + SZ_B;
 };
 
@@ -55,7 +77,7 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
                                                  int64_t ldx, int64_t ldy,
                                                  const typename Ar::template Tab<D, Q> tab) {
   using T = typename Ar::T;
-  using L = ApplyLayout<D, Q, DIFF>;
+  using L = ApplyLayout<D, Q, DIFF, (int)sizeof(T), REREAD>;
   constexpr int D2 = L::D2, D3 = L::D3, Q2 = L::Q2, QD = L::QD;
   constexpr int S_DD = L::S_DD, S_QD = L::S_QD, S_QQ = L::S_QQ;
   constexpr int SZ_A = L::SZ_A, SZ_B = L::SZ_B;

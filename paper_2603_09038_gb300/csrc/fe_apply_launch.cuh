@@ -72,9 +72,9 @@ struct ApplyTuning<ArF32x2T<A, L>> {
 
 // Elements per block: as many as fit in the variant's shared-memory budget, a power of two,
 // at most 64.
-template <int D, int Q, bool DIFF, class T, int SMEM>
+template <int D, int Q, bool DIFF, class T, int SMEM, bool RR>
 constexpr int elems_per_block() {
-  constexpr int bytes = ApplyLayout<D, Q, DIFF>::PER_ELEM * (int)sizeof(T);
+  constexpr int bytes = ApplyLayout<D, Q, DIFF, (int)sizeof(T), RR>::PER_ELEM * (int)sizeof(T);
   int ne = SMEM / bytes;
   int p2 = 1;
   while (p2 * 2 <= ne && p2 < 64) p2 *= 2;
@@ -139,8 +139,9 @@ int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   using T = typename Ar::T;
   using Tune = ApplyTuning<Ar>;
   constexpr int NT = Tune::NT;
-  constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM>();
-  const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF>::PER_ELEM * sizeof(T);
+  constexpr bool RR = (D >= Tune::REREAD_D);
+  constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM, RR>();
+  const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF, (int)sizeof(T), RR>::PER_ELEM * sizeof(T);
   auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB, VT, MULTI>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
