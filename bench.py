@@ -477,8 +477,25 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
     lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
     mma_peak = fe.fe_probe_throughput("bf16_mma")
     bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
+    ir = None
+    if width in (0, 64, 128):   # the same preconditioner inside mixed-precision refinement
+        def solve_ir():
+            st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, args.rtol, MAXIT, 0.0, stream)
+            if st != fe.FE_OK:
+                raise RuntimeError("fe_fcg_ir failed: %d %s" % (st, fe.fe_last_error()))
+            return stats
+        try:
+            t_ir, s_ir = timed(solve_ir, max(1, args.steps))
+        except fe.FEError as exc:   # no FP32 kernel for this order and width
+            t_ir, s_ir = None, str(exc)
+    if ir is None and width in (0, 64, 128) and t_ir is not None:
+        ir = {"time_to_1e-8_s": t_ir, "speedup_vs_jacobi_pcg": t_pcg / t_ir if t_pcg else None,
+              "inner_iters": s_ir["iters"], "outer_iters": s_ir["outer_iters"],
+              "true_rel_resid": s_ir["true_rel_resid"], "inner": "FP32 FCG + this network",
+              "outer_operator": "FP64-accurate (handle's variant)"}
     fe.fe_lpc_destroy(lpc)
     return {
+        "mixed_precision_ir": ir,
         "time_to_1e-8_s": t_fcg, "speedup_vs_jacobi_pcg": t_pcg / t_fcg if t_pcg else None,
         "jacobi_pcg_time_s": t_pcg,
         "fcg_iters": s_fcg["iters"], "jacobi_pcg_iters": pcg_iters,

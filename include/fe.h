@@ -317,6 +317,18 @@ int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
 int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
            int maxit, fe_pcg_stats* stats, void* stream);
 
+/* Mixed-precision iterative refinement with the learned preconditioner (the two extensions
+ * combined): outer steps r = (1-m)(b - A x) with the handle's FP64-accurate operator
+ * (FE_VARIANT_F32X2 or FE_VARIANT_F64 per the stored data) in FP64 vectors; inner flexible CG on
+ * FP32 vectors with the FP32 apply (FP32 copy of the quadrature data, made on first use) and lpc
+ * applied to FP32 vectors, to inner_rtol * ||r|| (0 => 1e-2); x += d; until ||r|| <= rtol ||b||,
+ * checked on the FP64-accurate residual.  lpc must have width 0, 64 or 128 (FE_ERR_UNSUPPORTED
+ * otherwise).  stats: iters = inner iterations, outer_iters = refinement steps, rel_resid =
+ * true_rel_resid = the final FP64-accurate residual.  FE_ERR_NOT_CONVERGED also when a
+ * refinement step fails to reduce the residual.  Allocates 2 FP64 and 7 FP32 vectors per call. */
+int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
+              int maxit, double inner_rtol, fe_pcg_stats* stats, void* stream);
+
 void fe_lpc_destroy(fe_lpc* lpc);
 
 void fe_pa_destroy(fe_pa* pa);

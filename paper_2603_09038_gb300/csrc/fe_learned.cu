@@ -27,6 +27,7 @@
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fe_internal.h"
@@ -489,70 +490,77 @@ __device__ __forceinline__ double finish_sum(const double* part) {
   return t;
 }
 
+// The FCG vector kernels take VT = double (the FP64 solver) or float (the inner solve of the
+// mixed-precision refinement); thread-local sums are kept in VT -- float sums keep the float
+// kernels off GB300's narrow FP64 pipe -- and only the block partials are FP64.
+
 // r = (1-m) b, x = 0; partial ||r||^2
-__global__ void __launch_bounds__(kT) k_fcg_init(const double* __restrict__ b,
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_init(const VT* __restrict__ b,
                                                  const uint8_t* __restrict__ mask,
-                                                 double* __restrict__ x, double* __restrict__ r,
+                                                 VT* __restrict__ x, VT* __restrict__ r,
                                                  int64_t n, double* part0, double* part1) {
-  double a = 0.0;
+  VT a = VT(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double ri = mask[i] ? 0.0 : b[i];
+    const VT ri = mask[i] ? VT(0) : b[i];
     r[i] = ri;
-    x[i] = 0.0;
+    x[i] = VT(0);
     a = fma(ri, ri, a);
   }
-  block_partial2(a, 0.0, part0, part1);
+  block_partial2((double)a, 0.0, part0, part1);
 }
 
 // q masked on the boundary; partials p.q and p.r
-__global__ void __launch_bounds__(kT) k_fcg_pq(const double* __restrict__ p, double* __restrict__ q,
-                                               const double* __restrict__ r,
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_pq(const VT* __restrict__ p, VT* __restrict__ q,
+                                               const VT* __restrict__ r,
                                                const uint8_t* __restrict__ mask, int64_t n,
                                                double* part0, double* part1) {
-  double a = 0.0, c = 0.0;
+  VT a = VT(0), c = VT(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double qi = q[i];
+    VT qi = q[i];
     if (mask[i]) {
-      qi = 0.0;
-      q[i] = 0.0;
+      qi = VT(0);
+      q[i] = VT(0);
     }
     a = fma(p[i], qi, a);
     c = fma(p[i], r[i], c);
   }
-  block_partial2(a, c, part0, part1);
+  block_partial2((double)a, (double)c, part0, part1);
 }
 
 // x += alpha p, r -= alpha q; partial ||r||^2
-__global__ void __launch_bounds__(kT) k_fcg_xr(double* __restrict__ x, double* __restrict__ r,
-                                               const double* __restrict__ p,
-                                               const double* __restrict__ q, int64_t n,
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_xr(VT* __restrict__ x, VT* __restrict__ r,
+                                               const VT* __restrict__ p,
+                                               const VT* __restrict__ q, int64_t n,
                                                const double* sc, double* part0, double* part1) {
-  const double alpha = sc[S_ALPHA];
-  double a = 0.0;
+  const VT alpha = (VT)sc[S_ALPHA];
+  VT a = VT(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
+    const VT ri = fma(-alpha, q[i], r[i]);
     r[i] = ri;
     a = fma(ri, ri, a);
   }
-  block_partial2(a, 0.0, part0, part1);
+  block_partial2((double)a, 0.0, part0, part1);
 }
 
 // partials z.q and z.r
-__global__ void __launch_bounds__(kT) k_fcg_zq(const double* __restrict__ z,
-                                               const double* __restrict__ q,
-                                               const double* __restrict__ r, int64_t n,
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_zq(const VT* __restrict__ z, const VT* __restrict__ q,
+                                               const VT* __restrict__ r, int64_t n,
                                                double* part0, double* part1) {
-  double a = 0.0, c = 0.0;
+  VT a = VT(0), c = VT(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     a = fma(z[i], q[i], a);
     c = fma(z[i], r[i], c);
   }
-  block_partial2(a, c, part0, part1);
+  block_partial2((double)a, (double)c, part0, part1);
 }
 
 // which: 0 init (bb, rr), 1 after p.q (alpha), 2 after the update (rr), 3 after z.q (beta)
@@ -580,21 +588,26 @@ __global__ void __launch_bounds__(kRB) k_fcg_finish(const double* part0, const d
 }
 
 // z = dinv r (Jacobi; dinv is 0 on the boundary)
-__global__ void __launch_bounds__(kT) k_fcg_jacobi(const double* __restrict__ dinv,
-                                                   const double* __restrict__ r,
-                                                   double* __restrict__ z, int64_t n) {
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_jacobi(const VT* __restrict__ dinv,
+                                                   const VT* __restrict__ r, VT* __restrict__ z,
+                                                   int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     z[i] = dinv[i] * r[i];
 }
 
-// p = z + beta p (beta from sc, or 0 for a restart)
-__global__ void __launch_bounds__(kT) k_fcg_p(double* __restrict__ p, const double* __restrict__ z,
-                                              int64_t n, const double* sc, int restart) {
-  const double beta = restart ? 0.0 : sc[S_BETA];
+// p = z + beta p (beta from sc, or 0 for a restart); q = 0 for the next float apply
+template <class VT>
+__global__ void __launch_bounds__(kT) k_fcg_p(VT* __restrict__ p, const VT* __restrict__ z,
+                                              VT* __restrict__ q, int64_t n, const double* sc,
+                                              int restart) {
+  const VT beta = restart ? VT(0) : (VT)sc[S_BETA];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     p[i] = fma(beta, p[i], z[i]);
+    if (q) q[i] = VT(0);
+  }
 }
 
 // partials ||(1-m)(b - q)||^2 and ||(1-m) b||^2
@@ -634,37 +647,61 @@ struct FcgResult {
   double rel = 0.0, true_rel = 0.0;
 };
 
-// FCG from x = 0; lpc == nullptr => Jacobi throughout.  Synchronous.
-int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b, double* x,
-            double rtol, int maxit, Snapshots* snap, cudaStream_t s, FcgResult* res) {
+int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s);
+
+// FCG from x = 0; lpc == nullptr => Jacobi throughout.  Synchronous.  VT = double: the handle's
+// variant applies the operator and the true residual is computed at the end; VT = float: the
+// FP32 apply on float vectors (the inner solve of fe_fcg_ir), no true residual.  work: NULL, or
+// 4 n VT values plus reduction space of 2 kRB + S_N doubles (red) supplied by the caller.
+template <class VT>
+int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, double rtol,
+            int maxit, Snapshots* snap, cudaStream_t s, FcgResult* res, VT* work = nullptr,
+            double* red_in = nullptr) {
+  constexpr bool F64 = std::is_same<VT, double>::value;
   const fe_mesh* m = pa->mesh;
   const int64_t n = m->ndofs;
   const uint8_t* mask = m->d_mask;
-  double *vec = nullptr, *red = nullptr;
+  VT* vec = work;
+  double* red = red_in;
   cudaError_t err;
-  if ((err = cudaMalloc(&vec, sizeof(double) * 4 * n)) != cudaSuccess ||
-      (err = cudaMalloc(&red, sizeof(double) * (2 * kRB + S_N))) != cudaSuccess) {
-    cudaFree(vec);
+  if (!vec && (err = cudaMalloc(&vec, sizeof(VT) * 4 * n)) != cudaSuccess)
+    return cuda_error(err, "fe_fcg: workspace cudaMalloc");
+  if (!red && (err = cudaMalloc(&red, sizeof(double) * (2 * kRB + S_N))) != cudaSuccess) {
+    if (!work) cudaFree(vec);
     return cuda_error(err, "fe_fcg: workspace cudaMalloc");
   }
-  double *r = vec, *z = vec + n, *p = vec + 2 * n, *q = vec + 3 * n;
+  VT *r = vec, *z = vec + n, *p = vec + 2 * n, *q = vec + 3 * n;
   double *part0 = red, *part1 = red + kRB, *sc = red + 2 * kRB;
   int st = FE_OK;
   bool learned = lpc != nullptr;
   size_t next_snap = 0;
   auto precond = [&]() -> int {
-    res->launches += learned ? 5 : 1;
-    if (learned) return fe::lpc_apply(lpc, r, z, s);
-    k_fcg_jacobi<<<kRB, kT, 0, s>>>(dinv, r, z, n);
+    res->launches += learned ? 2 : 1;
+    if (learned) {
+      if constexpr (F64)
+        return fe::lpc_apply(lpc, r, z, s);
+      else
+        return lpc_apply32(lpc, r, z, s);
+    }
+    k_fcg_jacobi<VT><<<kRB, kT, 0, s>>>(dinv, r, z, n);
     return FE_OK;
   };
+  auto apply = [&](const VT* in, VT* out) -> int {  // out = A in (out overwritten)
+    if constexpr (F64) {
+      return apply_dispatch(pa, op, pa->variant, in, out, s);
+    } else {
+      return apply_f32_vectors(pa, op, in, out, s, nullptr, nullptr);  // out zeroed by k_fcg_p
+    }
+  };
   auto take_snap = [&](int it) {
-    if (!snap) return;
-    while (next_snap < snap->at.size() && snap->at[next_snap] == it) {
-      k_snap<<<(unsigned int)(((int64_t)snap->ns * snap->din + kT - 1) / kT), kT, 0, s>>>(
-          r, m->d_map, snap->elems, snap->ns, snap->din,
-          snap->out + (int64_t)next_snap * snap->ns * snap->din);
-      ++next_snap;
+    if constexpr (F64) {
+      if (!snap) return;
+      while (next_snap < snap->at.size() && snap->at[next_snap] == it) {
+        k_snap<<<(unsigned int)(((int64_t)snap->ns * snap->din + kT - 1) / kT), kT, 0, s>>>(
+            r, m->d_map, snap->elems, snap->ns, snap->din,
+            snap->out + (int64_t)next_snap * snap->ns * snap->din);
+        ++next_snap;
+      }
     }
   };
   double hsc[S_N];
@@ -677,12 +714,12 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
     return FE_OK;
   };
   cudaMemsetAsync(sc, 0, sizeof(double) * S_N, s);
-  k_fcg_init<<<kRB, kT, 0, s>>>(b, mask, x, r, n, part0, part1);
+  k_fcg_init<VT><<<kRB, kT, 0, s>>>(b, mask, x, r, n, part0, part1);
   k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 0);
   res->launches += 2;
   take_snap(0);
   if ((st = precond()) == FE_OK) {
-    k_fcg_zq<<<kRB, kT, 0, s>>>(z, r, r, n, part0, part1);  // z.r (twice)
+    k_fcg_zq<VT><<<kRB, kT, 0, s>>>(z, r, r, n, part0, part1);  // z.r (twice)
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 3);
     res->launches += 2;
     st = read_sc();
@@ -693,7 +730,7 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
     st = precond();
   }
   if (st == FE_OK) {
-    k_fcg_p<<<kRB, kT, 0, s>>>(p, z, n, sc, 1);
+    k_fcg_p<VT><<<kRB, kT, 0, s>>>(p, z, F64 ? nullptr : q, n, sc, 1);
     ++res->launches;
   }
   const double bb = hsc[S_BB];
@@ -705,15 +742,15 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
     rel = 0.0;
   }
   for (int it = 1; st == FE_OK && res->status == FE_ERR_NOT_CONVERGED && it <= maxit; ++it) {
-    if ((st = apply_dispatch(pa, op, pa->variant, p, q, s)) != FE_OK) break;
-    k_fcg_pq<<<kRB, kT, 0, s>>>(p, q, r, mask, n, part0, part1);
+    if ((st = apply(p, q)) != FE_OK) break;
+    k_fcg_pq<VT><<<kRB, kT, 0, s>>>(p, q, r, mask, n, part0, part1);
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 1);
-    k_fcg_xr<<<kRB, kT, 0, s>>>(x, r, p, q, n, sc, part0, part1);
+    k_fcg_xr<VT><<<kRB, kT, 0, s>>>(x, r, p, q, n, sc, part0, part1);
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 2);
     res->launches += 5;
     take_snap(it);
     if ((st = precond()) != FE_OK) break;
-    k_fcg_zq<<<kRB, kT, 0, s>>>(z, q, r, n, part0, part1);
+    k_fcg_zq<VT><<<kRB, kT, 0, s>>>(z, q, r, n, part0, part1);
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 3);
     res->launches += 2;
     if ((st = read_sc()) != FE_OK) break;
@@ -745,22 +782,55 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const double* dinv, const double* b,
       last_gain = it;
       if ((st = precond()) != FE_OK) break;
     }
-    k_fcg_p<<<kRB, kT, 0, s>>>(p, z, n, sc, restart ? 1 : 0);
+    k_fcg_p<VT><<<kRB, kT, 0, s>>>(p, z, F64 ? nullptr : q, n, sc, restart ? 1 : 0);
     ++res->launches;
   }
   res->rel = rel;
-  if (st == FE_OK) {  // true residual with the handle's operator
-    if ((st = apply_dispatch(pa, op, pa->variant, x, q, s)) == FE_OK) {
-      k_fcg_resid<<<kRB, kT, 0, s>>>(b, q, mask, n, part0, part1);
-      k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
-      res->launches += 3;
-      if ((st = read_sc()) == FE_OK)
-        res->true_rel = hsc[S_BB] > 0.0 ? sqrt(hsc[S_TRUE] / hsc[S_BB]) : 0.0;
+  if constexpr (F64) {
+    if (st == FE_OK) {  // true residual with the handle's operator
+      if ((st = apply_dispatch(pa, op, pa->variant, x, q, s)) == FE_OK) {
+        k_fcg_resid<<<kRB, kT, 0, s>>>(b, q, mask, n, part0, part1);
+        k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
+        res->launches += 3;
+        if ((st = read_sc()) == FE_OK)
+          res->true_rel = hsc[S_BB] > 0.0 ? sqrt(hsc[S_TRUE] / hsc[S_BB]) : 0.0;
+      }
     }
   }
-  cudaFree(vec);
-  cudaFree(red);
+  if (!work) cudaFree(vec);
+  if (!red_in) cudaFree(red);
   return st;
+}
+
+// r = (1-m)(b - q) into rout; partials ||r||^2 and ||(1-m) b||^2 (the outer residual of fe_fcg_ir)
+__global__ void __launch_bounds__(kT) k_ir_resid(const double* __restrict__ b,
+                                                 const double* __restrict__ q,
+                                                 const uint8_t* __restrict__ mask,
+                                                 double* __restrict__ rout, int64_t n,
+                                                 double* part0, double* part1) {
+  double a = 0.0, c = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool bnd = mask[i] != 0;
+    const double bi = bnd ? 0.0 : b[i];
+    const double ri = bnd ? 0.0 : bi - q[i];
+    rout[i] = ri;
+    a = fma(ri, ri, a);
+    c = fma(bi, bi, c);
+  }
+  block_partial2(a, c, part0, part1);
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
 }
 
 // Training data (first call of fe_lpc_train): probing, Cholesky, residual snapshots, samples.
@@ -875,11 +945,11 @@ namespace {
 
 constexpr size_t kMaxSmem = 232448;  // 227 KB per block (opt-in)
 
-template <int DP, int W>
-cudaError_t fused_launch(const fe_lpc* L, const double* r, double* z, int grid, cudaStream_t s) {
+template <int DP, int W, class VT>
+cudaError_t fused_launch(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStream_t s) {
   if constexpr (mlp::FusedLayout<DP, W>::SMEM <= kMaxSmem) {
     const fe_mesh* m = L->pa->mesh;
-    mlp::k_lpc_fused<DP, W><<<grid, 256, mlp::FusedLayout<DP, W>::SMEM, s>>>(
+    mlp::k_lpc_fused<DP, W, VT><<<grid, 256, mlp::FusedLayout<DP, W>::SMEM, s>>>(
         reinterpret_cast<const uint4*>(L->wimg), r, m->d_map, L->fsc, m->ne, L->din, z);
     return cudaGetLastError();
   }
@@ -887,16 +957,16 @@ cudaError_t fused_launch(const fe_lpc* L, const double* r, double* z, int grid, 
 }
 
 // Blocks per SM of the fused kernel for (DP, W), 0 if it is not built or does not fit.
-template <int DP, int W>
+template <int DP, int W, class VT = double>
 int fused_occupancy() {
   if constexpr (mlp::FusedLayout<DP, W>::SMEM <= kMaxSmem) {
     const int smem = (int)mlp::FusedLayout<DP, W>::SMEM;
-    if (cudaFuncSetAttribute(mlp::k_lpc_fused<DP, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(mlp::k_lpc_fused<DP, W, VT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
       return 0;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp::k_lpc_fused<DP, W>, 256, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mlp::k_lpc_fused<DP, W, VT>, 256,
+                                                      smem) != cudaSuccess)
       return 0;
     return occ;
   }
@@ -919,9 +989,36 @@ int fused_occ(int DP, int W) {
 cudaError_t fused_run(const fe_lpc* L, const double* r, double* z, cudaStream_t s) {
   const int DP = mlp::fused_dp(L->din), W = L->width;
 #define FE_RUN_CASE(dp, w) \
-  if (DP == dp && W == w) return fused_launch<dp, w>(L, r, z, L->fused_grid, s);
+  if (DP == dp && W == w) return fused_launch<dp, w, double>(L, r, z, L->fused_grid, s);
   FE_FUSED_CASES(FE_RUN_CASE)
 #undef FE_RUN_CASE
+  return cudaErrorInvalidConfiguration;
+}
+
+// FP32 vectors (the mixed-precision inner solve): the linear map and widths 64, 128.
+#define FE_FUSED_CASES_F32(X) \
+  X(16, 0) X(32, 0) X(64, 0) X(128, 0) X(16, 64) X(32, 64) X(64, 64) X(128, 64) X(16, 128) \
+  X(32, 128) X(64, 128) X(128, 128)
+
+bool fused_f32_built(const fe_lpc* L) {
+  const int DP = mlp::fused_dp(L->din), W = L->width;
+#define FE_HAS_CASE(dp, w) \
+  if (DP == dp && W == w) return true;
+  FE_FUSED_CASES_F32(FE_HAS_CASE)
+#undef FE_HAS_CASE
+  return false;
+}
+
+cudaError_t fused_run_f32(const fe_lpc* L, const float* r, float* z, cudaStream_t s) {
+  const int DP = mlp::fused_dp(L->din), W = L->width;
+#define FE_RUN_CASE32(dp, w)                                                               \
+  if (DP == dp && W == w) {                                                               \
+    static bool attr = fused_occupancy<dp, w, float>() > 0;                               \
+    return attr ? fused_launch<dp, w, float>(L, r, z, L->fused_grid, s)                   \
+                : cudaErrorInvalidConfiguration;                                          \
+  }
+  FE_FUSED_CASES_F32(FE_RUN_CASE32)
+#undef FE_RUN_CASE32
   return cudaErrorInvalidConfiguration;
 }
 
@@ -947,6 +1044,23 @@ void fused_setup(fe_lpc* L) {
   L->fused_grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
 }
 
+}  // namespace
+
+namespace {
+// z = M(r) on FP32 vectors with the fused kernel (z overwritten).
+int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s) {
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(z, 0, sizeof(float) * L->pa->mesh->ndofs, s)) != cudaSuccess)
+    return cuda_error(err, "fe_fcg_ir: zero z");
+  if (!L->wimg_ok) {
+    int64_t off[5];
+    const int DP = mlp::fused_dp(L->din);
+    mlp::fused_offsets(DP, L->width, off);
+    mlp::k_pack_wimg<<<grid1(off[4]), kT, 0, s>>>(L->w32, L->din, L->width, DP, L->wimg);
+    L->wimg_ok = true;
+  }
+  return cuda_error(fused_run_f32(L, r, z, s), "fe_fcg_ir: fused launch");
+}
 }  // namespace
 
 namespace fe {
@@ -986,6 +1100,124 @@ int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
 }  // namespace fe
 
 extern "C" {
+
+int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
+              int maxit, double inner_rtol, fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  if (!pa || !lpc || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_fcg_ir: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_fcg_ir: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_fcg_ir: operator not set up");
+  if (lpc->pa != pa || lpc->op != op)
+    return set_error(FE_ERR_ARG, "fe_fcg_ir: preconditioner built for another operator");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_fcg_ir: bad rtol or maxit");
+  if (inner_rtol == 0.0) inner_rtol = 1e-2;
+  if (!(inner_rtol > 0.0 && inner_rtol < 1.0))
+    return set_error(FE_ERR_ARG, "fe_fcg_ir: inner_rtol must lie in (0, 1)");
+  if (lpc->fused_grid <= 0 || !fused_f32_built(lpc))
+    return set_error(FE_ERR_UNSUPPORTED,
+                     "fe_fcg_ir: no FP32 fused kernel for this order and width (0, 64 or 128)");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr) {
+    const int saved = pa->variant;
+    if ((st = fe_pa_set_variant(pa, FE_VARIANT_F32, stream)) != FE_OK) return st;
+    pa->variant = saved;
+  }
+  const int hi = (pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  const fe_mesh* m = pa->mesh;
+  const int64_t n = m->ndofs;
+  double *dv = nullptr, *red = nullptr;
+  float* fv = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&dv, sizeof(double) * 2 * n)) != cudaSuccess ||
+      (err = cudaMalloc(&red, sizeof(double) * (2 * kRB + S_N))) != cudaSuccess ||
+      (err = cudaMalloc(&fv, sizeof(float) * 7 * n)) != cudaSuccess) {
+    cudaFree(dv);
+    cudaFree(red);
+    return cuda_error(err, "fe_fcg_ir: cudaMalloc");
+  }
+  double *rr = dv, *q = dv + n;
+  float *r32 = fv, *x32 = fv + n, *d32 = fv + 2 * n, *work32 = fv + 3 * n;
+  double *part0 = red, *part1 = red + kRB, *sc = red + 2 * kRB;
+  int launches = 0, outer = 0, inner_total = 0, restarts = 0;
+  double rel = 1.0;
+  auto outer_residual = [&]() -> int {  // rr = (1-m)(b - A x) with the FP64-accurate operator
+    int st2 = apply_dispatch(pa, op, hi, dev_x, q, s);
+    if (st2 != FE_OK) return st2;
+    k_ir_resid<<<kRB, kT, 0, s>>>(dev_b, q, m->d_mask, rr, n, part0, part1);
+    k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
+    launches += 3;
+    double hsc[S_N];
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(e, "fe_fcg_ir: residual");
+    rel = hsc[S_BB] > 0.0 ? sqrt(hsc[S_TRUE] / hsc[S_BB]) : 0.0;
+    return FE_OK;
+  };
+  int state = FE_ERR_NOT_CONVERGED;
+  st = cuda_error(cudaMemsetAsync(dev_x, 0, sizeof(double) * n, s), "fe_fcg_ir: zero x");
+  if (st == FE_OK) {
+    k_to_f32<<<grid1(n), kT, 0, s>>>(lpc->dinv, d32, n);
+    ++launches;
+    st = outer_residual();
+  }
+  if (st == FE_OK && rel <= rtol) state = FE_OK;
+  while (st == FE_OK && state == FE_ERR_NOT_CONVERGED) {
+    if (!std::isfinite(rel)) {
+      state = FE_ERR_NAN;
+      break;
+    }
+    k_to_f32<<<grid1(n), kT, 0, s>>>(rr, r32, n);
+    ++launches;
+    FcgResult in;
+    st = fcg_run<float>(pa, op, lpc, d32, r32, x32, inner_rtol, maxit - inner_total, nullptr, s,
+                        &in, work32, red);
+    if (st != FE_OK) break;
+    launches += in.launches;
+    inner_total += in.iters;
+    restarts += in.restarts;
+    ++outer;
+    if (in.status == FE_ERR_NAN || in.status == FE_ERR_BREAKDOWN) {
+      state = in.status;
+      break;
+    }
+    k_add_f32<<<grid1(n), kT, 0, s>>>(dev_x, x32, n);
+    ++launches;
+    const double prev = rel;
+    if ((st = outer_residual()) != FE_OK) break;
+    if (rel <= rtol)
+      state = FE_OK;
+    else if (inner_total >= maxit || !(rel < prev))
+      state = FE_ERR_NOT_CONVERGED;  // budget spent, or refinement stagnated
+    if (state == FE_ERR_NOT_CONVERGED && (inner_total >= maxit || !(rel < prev))) break;
+  }
+  cudaFree(dv);
+  cudaFree(red);
+  cudaFree(fv);
+  if (st != FE_OK) return st;
+  if (stats) {
+    stats->iters = inner_total;
+    stats->rel_resid = rel;
+    stats->true_rel_resid = rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = launches;
+    stats->outer_iters = outer;
+  }
+  switch (state) {
+    case FE_OK:
+      return FE_OK;
+    case FE_ERR_NAN:
+      return set_error(FE_ERR_NAN, "fe_fcg_ir: NaN or Inf in the iteration");
+    case FE_ERR_BREAKDOWN:
+      return set_error(FE_ERR_BREAKDOWN, "fe_fcg_ir: p.Ap <= 0 in the inner solve");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, "fe_fcg_ir: maxit reached or refinement stagnated");
+  }
+}
 
 int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   clear_error();

@@ -219,10 +219,11 @@ __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
 // Widths up to 128 with D^3 <= 64 are register-capped for two resident blocks per SM (16 warps
 // to hide the gather's memory latency); larger tiles need the full register file of one block;
 // the linear map (W = 0) runs three blocks per SM (two for D^3 > 64).
-template <int DP, int W>
+// VT: element type of the r and z vectors (double; float inside the mixed-precision solver).
+template <int DP, int W, class VT>
 __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 && DP <= 64 ? 2 : 1))) k_lpc_fused(
-    const uint4* __restrict__ wimg, const double* __restrict__ r, const int32_t* __restrict__ map,
-    const double* __restrict__ fsc, int64_t ne, int din, double* __restrict__ z) {
+    const uint4* __restrict__ wimg, const VT* __restrict__ r, const int32_t* __restrict__ map,
+    const double* __restrict__ fsc, int64_t ne, int din, VT* __restrict__ z) {
   using Lay = FusedLayout<DP, W>;
   static_assert(W % 64 == 0 && DP % 16 == 0, "fused MLP tile sizes");
   constexpr int DPW = DP / 2, WW = W > 0 ? W / 2 : 1;  // 32-bit words per image row
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 
         if (col < din && e < ne) {
           const int32_t idx = map[e * din + col];
           const float f = (float)fsc[idx];
-          if (f != 0.0f) atomicAdd(&z[idx], (double)(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
+          if (f != 0.0f) atomicAdd(&z[idx], (VT)(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
         }
       }
     }

@@ -98,6 +98,8 @@ _SIGS = {
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                               ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_fcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_double, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_lpc_destroy": (None, [_VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
@@ -386,6 +388,18 @@ def fe_fcg(pa, op, lpc, dev_b, dev_x, rtol, maxit, stream=None):
     st = fe_pcg_stats()
     status = lib.fe_fcg(_VP(pa), int(op), _VP(lpc) if lpc else None, _ptr(dev_b), _ptr(dev_x),
                         float(rtol), int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
+
+
+def fe_fcg_ir(pa, op, lpc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=None):
+    """Mixed-precision refinement around an FP32 flexible CG preconditioned by lpc; same return
+    value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_fcg_ir(_VP(pa), int(op), _VP(lpc), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                           int(maxit), float(inner_rtol), ctypes.byref(st), _stream(stream))
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)

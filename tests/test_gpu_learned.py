@@ -218,3 +218,47 @@ def test_trained_fcg_beats_jacobi_iterations(n, p, sigma, width):
             assert d <= 1e-6
         finally:
             fe.fe_lpc_destroy(lpc)
+
+
+@pytest.mark.parametrize("width,sigma", [(0, None), (128, None), (0, 1.0)])
+def test_fcg_ir_learned_mixed_precision(width, sigma):
+    """Mixed-precision refinement around the FP32 learned-FCG inner solve reaches the
+    FP64-accurate 1e-8 residual and the Jacobi-PCG solution."""
+    torch = torch_cuda()
+    n, p = 16, 3
+    with gpu_problem(n, n, n, p, sigma=sigma, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, "f32x2")
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        xj, xi = torch.empty_like(b), torch.empty_like(b)
+        st, sj = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xj, 1e-8, 20000)
+        assert st == fe.FE_OK
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 4)
+        try:
+            fe.fe_lpc_train(lpc, 2000, 1024, 1e-3)
+            st, si = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, xi, 1e-8, 20000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert si["true_rel_resid"] <= 1e-8 and si["outer_iters"] >= 2
+            assert fe.fe_pa_get_variant(pa) == fe.VARIANTS["f32x2"]   # handle's variant kept
+            d = (xi - xj).abs().max().item() / xj.abs().max().item()
+            assert d <= 1e-6
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_fcg_ir_rejects_unsupported_width():
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 3, ops=1) as (fe, mesh, pa, V, c):
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.ones(nd, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 256, 4)
+        try:
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-8, 100)
+            assert e.value.status == fe.FE_ERR_UNSUPPORTED
+            with pytest.raises(fe.FEError):
+                fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-8, 100, inner_rtol=1.5)
+        finally:
+            fe.fe_lpc_destroy(lpc)
