@@ -292,6 +292,15 @@ int fe_lpc_nparams(const fe_lpc* lpc, int64_t* nparams);
 int fe_lpc_train(fe_lpc* lpc, int steps, int batch, double lr, int reps, double* final_loss,
                  void* stream);
 
+/* Least-squares fit of the linear term: W0 = argmin sum ||x W0 - t||^2 + ridge mean(diag X^T X)
+ * ||W0||^2 over the whole training set (generated first if needed, `reps` pairs per sampled
+ * element, 0 => 16), by the normal equations -- X^T X and X^T T with the BF16 tensor-core GEMM
+ * (FP32 accumulation), FP64 Cholesky on the host -- in milliseconds instead of Adam steps.  The
+ * other weights are untouched: for width 0 this is the whole preconditioner; for an MLP it is a
+ * starting point for fe_lpc_train.  *fit_loss (may be NULL): the relative squared error of the
+ * fit on the training set.  Synchronous. */
+int fe_lpc_fit_linear(fe_lpc* lpc, double ridge, int reps, double* fit_loss, void* stream);
+
 /* Copies the FP32 master weights (fe_lpc_nparams floats) to host_w (set = 0) or from host_w
  * (set != 0; the BF16 copy is refreshed).  Synchronous. */
 int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);

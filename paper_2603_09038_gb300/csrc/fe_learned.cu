@@ -1306,6 +1306,96 @@ int fe_lpc_train(fe_lpc* L, int steps, int batch, double lr, int reps, double* f
   return cuda_error(cudaStreamSynchronize(s), "fe_lpc_train");
 }
 
+int fe_lpc_fit_linear(fe_lpc* L, double ridge, int reps, double* fit_loss, void* stream) {
+  clear_error();
+  if (!L) return set_error(FE_ERR_ARG, "fe_lpc_fit_linear: NULL handle");
+  if (!(ridge >= 0.0)) return set_error(FE_ERR_ARG, "fe_lpc_fit_linear: ridge must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st;
+  if (L->nsamp == 0 && (st = make_samples(L, reps > 0 ? reps : 16, s)) != FE_OK) return st;
+  const int d = L->din;
+  const int64_t N = L->nsamp;
+  // G = X^T X, H = X^T T over all pairs (BF16 operands, FP32 accumulation), ||T||^2
+  __nv_bfloat16* tb = nullptr;
+  float* gh = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&tb, sizeof(__nv_bfloat16) * N * d)) != cudaSuccess ||
+      (err = cudaMalloc(&gh, sizeof(float) * 2 * d * d)) != cudaSuccess) {
+    cudaFree(tb);
+    return cuda_error(err, "fe_lpc_fit_linear: cudaMalloc");
+  }
+  k_to_bf16<<<grid1(N * d), kT, 0, s>>>(L->Ts, tb, N * d);
+  cudaMemsetAsync(L->red, 0, 2 * sizeof(double), s);
+  k_loss_terms<<<grid1(N * d), kT, 0, s>>>(L->Ts, L->Ts, N * d, L->red);  // red[1] = ||T||^2
+  if ((err = mlp::gemm<true, false, mlp::EPI_STORE>(d, d, (int)N, L->Xs, d, L->Xs, d, gh, d,
+                                                    nullptr, 0, s)) != cudaSuccess ||
+      (err = mlp::gemm<true, false, mlp::EPI_STORE>(d, d, (int)N, L->Xs, d, tb, d, gh + d * d, d,
+                                                    nullptr, 0, s)) != cudaSuccess) {
+    cudaFree(tb);
+    cudaFree(gh);
+    return cuda_error(err, "fe_lpc_fit_linear: GEMM launch");
+  }
+  std::vector<float> hgh(2 * d * d);
+  double red[2];
+  err = cudaMemcpyAsync(hgh.data(), gh, sizeof(float) * 2 * d * d, cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(red, L->red, sizeof(red), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  cudaFree(tb);
+  cudaFree(gh);
+  if (err != cudaSuccess) return cuda_error(err, "fe_lpc_fit_linear: copy");
+  // (G + ridge mean(diag G) I) W0 = H by FP64 Cholesky on the host (d <= 125)
+  std::vector<double> G(d * d), W(d * d);
+  double tr = 0.0;
+  for (int i = 0; i < d; ++i) tr += hgh[i * d + i];
+  const double lam = ridge * tr / d;
+  for (int i = 0; i < d * d; ++i) G[i] = hgh[i];
+  for (int i = 0; i < d; ++i) G[i * d + i] += lam;
+  for (int k = 0; k < d; ++k) {
+    double dk = G[k * d + k];
+    for (int j = 0; j < k; ++j) dk -= G[k * d + j] * G[k * d + j];
+    if (!(dk > 0.0)) return set_error(FE_ERR_BREAKDOWN, "fe_lpc_fit_linear: singular normal equations");
+    G[k * d + k] = sqrt(dk);
+    for (int i = k + 1; i < d; ++i) {
+      double v = G[i * d + k];
+      for (int j = 0; j < k; ++j) v -= G[i * d + j] * G[k * d + j];
+      G[i * d + k] = v / G[k * d + k];
+    }
+  }
+  for (int c = 0; c < d; ++c) {  // column c of W0 from column c of H
+    std::vector<double> y(d);
+    for (int i = 0; i < d; ++i) {
+      double v = hgh[d * d + i * d + c];
+      for (int j = 0; j < i; ++j) v -= G[i * d + j] * y[j];
+      y[i] = v / G[i * d + i];
+    }
+    for (int i = d - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int j = i + 1; j < d; ++j) v -= G[j * d + i] * W[j * d + c];
+      W[i * d + c] = v / G[i * d + i];
+    }
+  }
+  // loss = (||T||^2 - 2 tr(W^T H) + tr(W^T G W)) / ||T||^2 with the unregularised G
+  double cross = 0.0, quad = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int c = 0; c < d; ++c) {
+      cross += W[i * d + c] * hgh[d * d + i * d + c];
+      double gw = 0.0;
+      for (int j = 0; j < d; ++j) gw += (double)hgh[i * d + j] * W[j * d + c];
+      quad += W[i * d + c] * gw;
+    }
+  if (fit_loss) *fit_loss = red[1] > 0.0 ? (red[1] - 2.0 * cross + quad) / red[1] : 0.0;
+  // W0 is the last d x d block of the packed weights
+  std::vector<float> w0(d * d);
+  for (int i = 0; i < d * d; ++i) w0[i] = (float)W[i];
+  const int64_t off = L->nparam - (int64_t)d * d;
+  if ((err = cudaMemcpyAsync(L->w32 + off, w0.data(), sizeof(float) * d * d,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_fit_linear: weights");
+  k_to_bf16<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->wb, L->nparam);
+  L->wimg_ok = false;
+  return cuda_error(cudaStreamSynchronize(s), "fe_lpc_fit_linear");
+}
+
 int fe_lpc_weights(fe_lpc* L, float* host_w, int set) {
   clear_error();
   if (!L || !host_w) return set_error(FE_ERR_ARG, "fe_lpc_weights: null argument");

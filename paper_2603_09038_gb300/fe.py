@@ -93,6 +93,8 @@ _SIGS = {
     "fe_lpc_train": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_double), _VP]),
     "fe_lpc_weights": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "fe_lpc_fit_linear": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), _VP]),
     "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -339,6 +341,14 @@ def fe_lpc_train(lpc, steps, batch, lr, reps=0, stream=None):
     loss = ctypes.c_double()
     _check(load().fe_lpc_train(_VP(lpc), int(steps), int(batch), float(lr), int(reps),
                                ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def fe_lpc_fit_linear(lpc, ridge=1e-6, reps=0, stream=None):
+    """Least-squares fit of the linear term W0 on the training set; returns the fit's loss."""
+    loss = ctypes.c_double()
+    _check(load().fe_lpc_fit_linear(_VP(lpc), float(ridge), int(reps), ctypes.byref(loss),
+                                    _stream(stream)))
     return loss.value
 
 
