@@ -480,18 +480,21 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
     ir = None
     if width in (0, 64, 128):   # the same preconditioner inside mixed-precision refinement
         def solve_ir():
-            st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, args.rtol, MAXIT, 0.0, stream)
+            st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, args.rtol, MAXIT,
+                                     args.inner_rtol, stream)
             if st != fe.FE_OK:
                 raise RuntimeError("fe_fcg_ir failed: %d %s" % (st, fe.fe_last_error()))
             return stats
         try:
             t_ir, s_ir = timed(solve_ir, max(1, args.steps))
-        except fe.FEError as exc:   # no FP32 kernel for this order and width
+        except (fe.FEError, RuntimeError) as exc:  # no FP32 kernel, or the solve failed
             t_ir, s_ir = None, str(exc)
+            ir = {"failed": str(exc).splitlines()[-1]}
     if ir is None and width in (0, 64, 128) and t_ir is not None:
         ir = {"time_to_1e-8_s": t_ir, "speedup_vs_jacobi_pcg": t_pcg / t_ir if t_pcg else None,
               "inner_iters": s_ir["iters"], "outer_iters": s_ir["outer_iters"],
               "true_rel_resid": s_ir["true_rel_resid"], "inner": "FP32 FCG + this network",
+              "inner_rtol": args.inner_rtol or 1e-2,
               "outer_operator": "FP64-accurate (handle's variant)"}
     fe.fe_lpc_destroy(lpc)
     return {
