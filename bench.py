@@ -445,8 +445,9 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
 
     def solve_fcg(pc):
         st, stats = fe.fe_fcg(pa, fe.FE_DIFFUSION, pc, b, x, args.rtol, MAXIT, stream)
-        if st != fe.FE_OK:
+        if st not in (fe.FE_OK, fe.FE_ERR_NOT_CONVERGED):
             raise RuntimeError("fe_fcg failed: %d %s" % (st, fe.fe_last_error()))
+        stats["status"] = st
         return stats
 
     def timed(fn, reps):
@@ -501,7 +502,7 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
         "mixed_precision_ir": ir,
         "time_to_1e-8_s": t_fcg, "speedup_vs_jacobi_pcg": t_pcg / t_fcg if t_pcg else None,
         "jacobi_pcg_time_s": t_pcg,
-        "fcg_iters": s_fcg["iters"], "jacobi_pcg_iters": pcg_iters,
+        "fcg_iters": s_fcg["iters"], "fcg_status": s_fcg["status"], "jacobi_pcg_iters": pcg_iters,
         "fallbacks_to_jacobi": s_fcg["outer_iters"] - 1,
         "true_rel_resid": s_fcg["true_rel_resid"],
         "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
