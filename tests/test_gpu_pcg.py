@@ -305,3 +305,21 @@ def test_pcg_batched_failure_is_per_system():
                                   args[2], 1e-8, 10)
         with pytest.raises(fe.FEError):
             fe.fe_pcg_batched(pa, fe.FE_DIFFUSION, fe.FE_PC_CHEBYSHEV, 1, sine, n, X, n, 1e-8, 10)
+
+
+def test_chebyshev_degree_one_is_scaled_jacobi():
+    """Degree 1 gives z = D^-1 r / theta: a constant multiple of Jacobi, which leaves the CG
+    iterates unchanged, so iterations and solution equal Jacobi-PCG's."""
+    torch = torch_cuda()
+    with gpu_problem(6, 6, 6, 3, sigma=1.0, ops=1) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        xj, xc = torch.empty_like(b), torch.empty_like(b)
+        st, sj = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xj, 1e-10, 5000)
+        st2, sc = fe.fe_pcg_chebyshev(pa, fe.FE_DIFFUSION, b, xc, 1e-10, 5000, degree=1,
+                                      lmax=3.0, lmin_ratio=7.0)
+        assert st == st2 == fe.FE_OK
+        assert abs(sj["iters"] - sc["iters"]) <= 1
+        d = (xc - xj).abs().max().item() / xj.abs().max().item()
+        assert d <= 1e-9
