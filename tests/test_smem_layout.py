@@ -47,3 +47,18 @@ def test_tuned_layout_has_fewer_modelled_wavefronts(pick):
     new = sum(sl.split_cost(D, Q, ne, es, bool(diff), tuple(lay), bool(rr)))
     old = sum(sl.split_cost(D, Q, ne, es, bool(diff), cur, bool(rr)))
     assert new < old
+
+
+def test_bank_model_known_patterns():
+    """Textbook cases of the wavefront model: unit stride is conflict-free (one wavefront for
+    4-byte words, one per half-warp for 8-byte words), stride 2 words is a 2-way conflict,
+    stride 32 words a 32-way conflict, and a broadcast costs one wavefront."""
+    import numpy as np
+    t = np.arange(32)[None, :]
+    assert sl.wavefronts(t, 4) == 1
+    assert sl.wavefronts(2 * t, 4) == 2
+    assert sl.wavefronts(32 * t, 4) == 32
+    assert sl.wavefronts(0 * t, 4) == 1
+    assert sl.wavefronts(t, 8) == 2          # 256 bytes: two half-warps of 128 bytes
+    assert sl.wavefronts(2 * t, 8) == 4      # stride 16 bytes: 2-way within each half-warp
+    assert sl.wavefronts(17 * t, 8) == 2     # odd stride in 8-byte words: conflict-free halves
