@@ -52,6 +52,7 @@ struct fe_lpc {
   double* dinv = nullptr;       // inverse diagonal, 0 on the boundary (Jacobi)
   double* dis = nullptr;        // diagonal^(-1/2), 0 on the boundary
   double* fsc = nullptr;        // wsq * dis: the input/output scaling F = W S of the apply
+  float* fsc32 = nullptr;       // the same in FP32 (read by the fused kernel)
   __nv_bfloat16* wimg = nullptr;  // shared-memory weight image of the fused apply
   bool wimg_ok = false;
   int fused_grid = 0;           // persistent grid of the fused apply (0: unfused GEMM path)
@@ -950,7 +951,7 @@ cudaError_t fused_launch(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStre
   if constexpr (mlp::FusedLayout<DP, W>::SMEM <= kMaxSmem) {
     const fe_mesh* m = L->pa->mesh;
     mlp::k_lpc_fused<DP, W, VT><<<grid, 256, mlp::FusedLayout<DP, W>::SMEM, s>>>(
-        reinterpret_cast<const uint4*>(L->wimg), r, m->d_map, L->fsc, m->ne, L->din, z);
+        reinterpret_cast<const uint4*>(L->wimg), r, m->d_map, L->fsc32, m->ne, L->din, z);
     return cudaGetLastError();
   }
   return cudaErrorInvalidConfiguration;
@@ -1249,6 +1250,7 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
       (err = cudaMalloc(&L->dinv, 8 * m->ndofs)) != cudaSuccess ||
       (err = cudaMalloc(&L->dis, 8 * m->ndofs)) != cudaSuccess ||
       (err = cudaMalloc(&L->fsc, 8 * m->ndofs)) != cudaSuccess ||
+      (err = cudaMalloc(&L->fsc32, 4 * m->ndofs)) != cudaSuccess ||
       (err = cudaMalloc(&L->red, 16)) != cudaSuccess) {
     fe_lpc_destroy(L);
     return cuda_error(err, "fe_lpc_create: cudaMalloc");
@@ -1264,6 +1266,7 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   if (st == FE_OK) {
     k_invert_diag<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, m->d_mask, m->ndofs);
     k_sqrt_vec<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, L->dis, L->wsq, L->fsc, m->ndofs);
+    k_to_f32<<<grid1(m->ndofs), kT, 0, s>>>(L->fsc, L->fsc32, m->ndofs);
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) st = cuda_error(err, "fe_lpc_create");
@@ -1501,7 +1504,7 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
 void fe_lpc_destroy(fe_lpc* L) {
   if (!L) return;
   cudaFree(L->w32); cudaFree(L->wb); cudaFree(L->adam_m); cudaFree(L->adam_v); cudaFree(L->grad);
-  cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->wimg); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
+  cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->fsc32); cudaFree(L->wimg); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
   cudaFree(L->Xb); cudaFree(L->H1b); cudaFree(L->H2b); cudaFree(L->dYb); cudaFree(L->dA1b);
   cudaFree(L->dA2b); cudaFree(L->Z1); cudaFree(L->Z2); cudaFree(L->Y); cudaFree(L->Tb);
   cudaFree(L->scale);

@@ -223,7 +223,7 @@ __device__ __forceinline__ uint32_t pack_relu(float lo, float hi) {
 template <int DP, int W, class VT>
 __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 && DP <= 64 ? 2 : 1))) k_lpc_fused(
     const uint4* __restrict__ wimg, const VT* __restrict__ r, const int32_t* __restrict__ map,
-    const double* __restrict__ fsc, int64_t ne, int din, VT* __restrict__ z) {
+    const float* __restrict__ fsc, int64_t ne, int din, VT* __restrict__ z) {
   using Lay = FusedLayout<DP, W>;
   static_assert(W % 64 == 0 && DP % 16 == 0, "fused MLP tile sizes");
   constexpr int DPW = DP / 2, WW = W > 0 ? W / 2 : 1;  // 32-bit words per image row
@@ -247,10 +247,12 @@ __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 
   for (int64_t tile = (int64_t)blockIdx.x * Lay::WARPS + warp; tile < ntiles;
        tile += (int64_t)gridDim.x * Lay::WARPS) {
     // ---- gather: x = F r on the element, normalised, to BF16 (GR rows at a time for ILP).  The
-    // FP64 inputs are narrowed to floats (one conversion each) and the scaling is done in FP32:
+    // FP64 inputs are narrowed to floats (one conversion each; the scaling F is stored in FP32)
+    // and the scaling is done in FP32:
     // with FP64 arithmetic here GB300's FP64 pipe (2 DFMA per clock per SM) bound the kernel
     // (81 % busy); narrowing by integer manipulation instead of the conversion instruction was
-    // measured slower (more instructions in a latency-bound kernel).
+    // measured slower (more instructions in a latency-bound kernel), for the MLP and for the
+    // linear map alike.
 #pragma unroll 1
     for (int i0 = 0; i0 < 16; i0 += GR) {
       float xv[GR][WPL][2];
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 
             float v = 0.0f;
             if (kw < DPW && k < din && e < ne) {
               const int32_t idx = map[e * din + k];
-              v = (float)fsc[idx] * (float)r[idx];
+              v = fsc[idx] * (float)r[idx];
             }
             xv[i][w][h] = v;
           }
@@ -399,8 +401,9 @@ __global__ void __launch_bounds__(256, (W == 0 ? (DP <= 64 ? 3 : 2) : (W <= 128 
         const int64_t e = tile * 16 + row;
         if (col < din && e < ne) {
           const int32_t idx = map[e * din + col];
-          const float f = (float)fsc[idx];
-          if (f != 0.0f) atomicAdd(&z[idx], (VT)(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
+          const float f = fsc[idx];
+          if (f != 0.0f)
+            atomicAdd(&z[idx], (VT)(f * (c >= 2 ? s_hi : s_lo) * y[j][c]));
         }
       }
     }
