@@ -7,7 +7,9 @@ coefficients that both the CUDA path and the CPU oracle receive as data.
   x fastest, with every vertex not on the cube's boundary moved by h * U[-amp, amp] in each
   coordinate independently (h = 1/n along that axis), so the domain stays the unit cube;
 * ``uniform_vector``: x ~ U[-1, 1];
-* ``lognormal_coefficient``: one value per element, exp(sigma * Z), Z ~ N(0, 1).
+* ``lognormal_coefficient``: one value per element, exp(sigma * Z), Z ~ N(0, 1);
+* ``block_orders``: one polynomial order per element, constant on block^3-element blocks, each
+  block's order drawn uniformly from a set.
 
 Generators are ``numpy.random.default_rng(seed)`` (PCG64), so every input is reproducible.
 """
@@ -44,3 +46,14 @@ def lognormal_coefficient(ne, sigma=1.0, seed=COEFF_SEED):
 
 # Elements per axis of the ~50 M dof order-sweep meshes (n^3 hexes, (n*p+1)^3 dofs).
 ORDER_SWEEP_N = {1: 368, 2: 184, 3: 123, 4: 92, 5: 74, 6: 61, 7: 53, 8: 46}
+
+
+def block_orders(nx, ny, nz, block=8, orders=(2, 4, 6), seed=7):
+    """One polynomial order per element (index ex + nx*(ey + ny*ez)): the mesh is cut into
+    block^3-element blocks (ragged at the far ends) and each block draws its order uniformly from
+    ``orders``."""
+    bx, by, bz = -(-nx // block), -(-ny // block), -(-nz // block)
+    pick = np.random.default_rng(seed).integers(0, len(orders), size=bx * by * bz)
+    o = np.asarray(orders, dtype=np.int32)[pick].reshape(bz, by, bx)
+    ez, ey, ex = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return np.ascontiguousarray(o[ez // block, ey // block, ex // block].reshape(-1))
