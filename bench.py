@@ -748,6 +748,66 @@ def run_batched(args, local_rank):
     return 0
 
 
+def run_mixed_orders(args, local_rank):
+    """Variable-order apply (fe_vspace_apply) on an n^3 mesh cut into 8^3-element blocks whose
+    orders are drawn from {2, 4, 6}: the constraint gather E x, one fused apply per order, the
+    transpose scatter E^T v.  One JSON line per variant: time, true-dof throughput, and the
+    bytes moved (this design's and the minimum: x, y and the quadrature data once)."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import block_orders, perturbed_vertices
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    fe.load()
+    n = args.n
+    orders = block_orders(n, n, n, block=8, orders=(2, 4, 6), seed=7)
+    t0 = time.perf_counter()
+    vs = fe.fe_vspace_setup(n, n, n, orders, perturbed_vertices(n, n, n), ops=fe.FE_DIFFUSION)
+    setup_s = time.perf_counter() - t0
+    ntrue, nlocal, nnz = fe.fe_vspace_sizes(vs)
+    stream = torch.cuda.current_stream()
+    x = torch.rand(ntrue, dtype=torch.float64, device=dev) * 2 - 1
+    y = torch.empty_like(x)
+    e = torch.empty(nlocal, dtype=torch.float64, device=dev)
+    counts = {p: int((orders == p).sum()) for p in (2, 4, 6)}
+    qd = sum(c * (p + 2) ** 3 * 6 * 8 for p, c in counts.items())
+    dmap = sum(c * 4 * (p + 1) ** 3 for p, c in counts.items())
+    csr = 2 * (8 * nnz + 4 * nnz) + 8 * (nlocal + ntrue + 2)
+    design = csr + 2 * 8 * ntrue + 4 * 8 * nlocal + qd + dmap
+    minimum = 2 * 8 * ntrue + qd
+    peaks, src = measured_peaks()
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, z in ev:
+            a.record(stream)
+            fn()
+            z.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(z) for a, z in ev)
+
+    for variant in args.variants.split(","):
+        if variant == "dmma":
+            continue
+        fe.fe_vspace_set_variant(vs, variant)
+        ms = timed(lambda: fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, y, stream))
+        ms_gather = timed(lambda: fe.fe_vspace_prolong(vs, x, e, stream))
+        print(json.dumps({
+            "mixed_orders": True, "workload": "diffusion_%dcubed_blocks8_orders246" % n,
+            "variant": variant, "ntrue": ntrue, "nlocal": nlocal, "nnz_E": nnz,
+            "elements_per_order": counts, "setup_s": setup_s, "apply_ms": ms,
+            "gdofs_true": ntrue / ms / 1e6, "gdofs_local": nlocal / ms / 1e6,
+            "gather_ms": ms_gather, "design_bytes": design, "min_bytes": minimum,
+            "design_gbs": design / ms / 1e6, "frac_of_hbm_design": design / ms / 1e6 / peaks["hbm_gbs"],
+            "frac_of_hbm_min_bytes": minimum / ms / 1e6 / peaks["hbm_gbs"], "peak_source": src}))
+    fe.fe_vspace_destroy(vs)
+    return 0
+
+
 def run_peaks(local_rank):
     """Throughput probes (libfe fe_probe_throughput) behind the FP64 roofline: one JSON line."""
     import torch
@@ -794,6 +854,8 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32/BF16-mma.sync throughput probes")
     ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")
+    ap.add_argument("--mixed-orders", action="store_true",
+                    help="variable-order apply: --n^3 mesh, 8^3 blocks of orders 2, 4, 6")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -814,6 +876,8 @@ def main():
         return run_graphs(args, local_rank)
     if args.batched_pcg:
         return run_batched_pcg(args, local_rank)
+    if args.mixed_orders:
+        return run_mixed_orders(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -340,6 +340,61 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
 
 void fe_lpc_destroy(fe_lpc* lpc);
 
+/* ---- Variable-order spaces (an extension: mixed orders in one mesh) -------------------------
+ * One polynomial order per element on the nx x ny x nz structured mesh.  The global space is the
+ * continuous piecewise-Q_{p_e} space under the minimum rule, and P of Eq. (1) is the constraint
+ * operator that keeps it continuous (Fig. 1's caption: P also carries constraints; the paper
+ * gives no construction, so this is a reading):
+ *  - entity orders: a cell has its element's order, a face / an edge the smallest order among
+ *    the elements containing it; vertices carry one value;
+ *  - true dofs: the values at the interior GLL_q nodes of every entity of order q, numbered
+ *    vertices first (lexicographic on the (nx+1)(ny+1)(nz+1) lattice), then the x-, y- and
+ *    z-directed edges (each family lexicographic on its index box, x fastest; q-1 dofs per edge
+ *    by increasing coordinate), then the x-, y- and z-normal faces likewise ((q-1)^2 dofs each,
+ *    first in-plane axis fastest: x-normal (y, z), y-normal (x, z), z-normal (x, y)), then the
+ *    cells ((p-1)^3 each, x fastest);
+ *  - E = G P: an element node takes the value of the function of the entity whose relative
+ *    interior holds it (edge: degree-q interpolant of its closure nodes; face: Q_q interpolant of
+ *    its closure nodes, whose boundary values come from the bounding edges), evaluated at the
+ *    node's GLL_p position.
+ * The E-vector holds the elements grouped by ascending order, elements ascending within a group,
+ * D^3 nodes per element (a = i + D*(j + D*k)); fe_vspace_layout gives every element's offset.
+ * The action is y = E^T blockdiag(A_e) E x: a CSR gather, the fused apply kernel of each order
+ * (one launch per order present, each order's quadrature data at p+2 Gauss points), and a CSR
+ * scatter.  Vectors are FP64 of length ntrue. */
+typedef struct fe_vspace fe_vspace;
+
+/* host_order: int32 [nx*ny*nz] orders 1..8; host_vertices as for fe_mesh_setup; host_coeff:
+ * FP64 [ne] piecewise-constant coefficient or NULL for 1; ops: FE_DIFFUSION | FE_MASS.  Builds
+ * the numbering and E on the host, uploads E and E^T (CSR: int64 row offsets, int32 columns,
+ * FP64 weights), and the per-order partial assembly.  FE_ERR_ARG on a bad order, size or an
+ * inverted element; FE_ERR_UNSUPPORTED past 2^31-1 true or local dofs.  Synchronous. */
+int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
+                    const double* host_vertices, const double* host_coeff, int ops, void* stream,
+                    fe_vspace** out);
+
+/* Sizes: true dofs, E-vector length (sum of D_e^3), nonzeros of E; any pointer may be NULL. */
+int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_t* nnz);
+
+/* host_first: int64 [ne], the E-vector offset of every element (in element index order). */
+int fe_vspace_layout(const fe_vspace* vs, int64_t* host_first);
+
+/* Copies the true-dof boundary mask (uint8 [ntrue], 1 on the cube's boundary) to dev_mask. */
+int fe_vspace_boundary_mask(const fe_vspace* vs, uint8_t* dev_mask, void* stream);
+
+/* Selects the arithmetic of every order's apply (as fe_pa_set_variant). */
+int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream);
+
+/* dev_e (FP64 [nlocal]) = E dev_x: the element values of a true-dof vector.  Asynchronous. */
+int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream);
+
+/* dev_y = E^T blockdiag(A_e) E dev_x for op (no boundary conditions); uses two library-owned
+ * E-vectors, so calls on one handle must not overlap.  Asynchronous. */
+int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
+                    void* stream);
+
+void fe_vspace_destroy(fe_vspace* vs);
+
 void fe_pa_destroy(fe_pa* pa);
 void fe_mesh_destroy(fe_mesh* mesh);
 

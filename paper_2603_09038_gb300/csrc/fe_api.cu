@@ -103,9 +103,11 @@ __device__ void trilinear(const double* __restrict__ V, int nx, int ny, int64_t 
 // Partial assembly: one thread per (element, Gauss point).
 //   diffusion  D = w c adj(J) adj(J)^T / det J  stored [e][qz][comp][qy][qx]
 //   mass       M = w c det J                    stored [e][qz][qy][qx]
+// ids: optional mesh index of every listed element (an element subset); NULL => e itself.
 __global__ void k_qdata(const double* __restrict__ V, int nx, int ny, int64_t ne, int Q,
                         const Rule rule, const double* __restrict__ coeff,
-                        double* __restrict__ qdd, double* __restrict__ qdm, int* __restrict__ bad) {
+                        const int32_t* __restrict__ ids, double* __restrict__ qdd,
+                        double* __restrict__ qdm, int* __restrict__ bad) {
   const int Q2 = Q * Q, Q3 = Q2 * Q;
   const int64_t n = ne * Q3;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
@@ -114,7 +116,8 @@ __global__ void k_qdata(const double* __restrict__ V, int nx, int ny, int64_t ne
     const int q = (int)(t - e * Q3);
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / Q2;
     double X[3], J[3][3];
-    trilinear(V, nx, ny, e, rule.pts[qx], rule.pts[qy], rule.pts[qz], X, J);
+    trilinear(V, nx, ny, ids ? (int64_t)ids[e] : e, rule.pts[qx], rule.pts[qy], rule.pts[qz],
+              X, J);
     // adjugate (transpose of the cofactor matrix): adj(J) = det(J) J^{-1}
     double A[3][3];
     A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
@@ -299,8 +302,8 @@ int compute_qdata(fe_pa* pa, const double* coeff, cudaStream_t s, int* d_bad) {
   const fe_mesh* m = pa->mesh;
   const int64_t n = m->ne * (int64_t)pa->Q * pa->Q * pa->Q;
   k_qdata<<<grid_for(n, 256), 256, 0, s>>>(m->d_vertices, m->nx, m->ny, m->ne, pa->Q,
-                                           make_rule(pa->basis), coeff, pa->d_qd_diff,
-                                           pa->d_qd_mass, d_bad);
+                                           make_rule(pa->basis), coeff, m->d_elem_ids,
+                                           pa->d_qd_diff, pa->d_qd_mass, d_bad);
   return cuda_error(cudaGetLastError(), "qdata kernel launch");
 }
 
@@ -492,6 +495,7 @@ void fe_mesh_destroy(fe_mesh* m) {
   cudaFree(m->d_vertices);
   cudaFree(m->d_map);
   cudaFree(m->d_mask);
+  cudaFree(m->d_elem_ids);
   delete m;
 }
 

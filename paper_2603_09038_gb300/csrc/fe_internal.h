@@ -47,6 +47,9 @@ struct fe_mesh {
   double* d_vertices = nullptr;    // [(nx+1)(ny+1)(nz+1)][3]
   int32_t* d_map = nullptr;        // [ne][D^3]
   uint8_t* d_mask = nullptr;       // [ndofs]
+  // An element subset of an nx x ny x nz mesh (the order groups of a variable-order space):
+  // mesh index of every element, NULL for the whole structured mesh.
+  int32_t* d_elem_ids = nullptr;
 };
 
 struct fe_pa {

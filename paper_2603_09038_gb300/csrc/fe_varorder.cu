@@ -1,0 +1,599 @@
+// Variable-order spaces: one polynomial order per element, kept continuous by the minimum rule.
+//
+// Eq. (1) reads A = P^T G^T B^T D B G P; with one order P is the identity on one GPU, with
+// several it is the constraint operator (Fig. 1's caption).  The space and its numbering are
+// documented with fe_vspace_setup in fe.h.  Here E = G P is built on the host once, row by row,
+// by evaluating the entity functions at every element node, and kept on the device in CSR form
+// together with its transpose, so that an apply is
+//   u = E x (CSR gather, one thread per E-vector row),
+//   v_g = A_g u_g for every order g present (the fused PA kernel of that order; the group's
+//         element map is the identity into its slice of the E-vector),
+//   y = E^T v (CSR of the transpose, one thread per true dof, fixed order: deterministic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "fe_internal.h"
+
+using namespace fe;
+
+namespace {
+
+constexpr int kRowCap = (kMaxD) * (kMaxD);  // distinct columns of one E row: a face closure
+
+struct Row {
+  int n = 0;
+  int64_t col[kRowCap];
+  double w[kRowCap];
+  void add(int64_t c, double v) {
+    if (v == 0.0) return;
+    for (int t = 0; t < n; ++t)
+      if (col[t] == c) {
+        w[t] += v;
+        return;
+      }
+    col[n] = c;
+    w[n] = v;
+    ++n;
+  }
+};
+
+// l_m(x) of the Lagrange basis on nodes t[0..n-1] (product formula).
+void lagrange_at(const double* t, int n, double x, double* L) {
+  for (int m = 0; m < n; ++m) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != m) v *= (x - t[k]) / (t[m] - t[k]);
+    L[m] = v;
+  }
+}
+
+struct Topo {
+  int n[3] = {0, 0, 0};
+  int64_t ne = 0, nv = 0, ntrue = 0;
+  std::vector<int> ord;                 // [ne]
+  int64_t ebox[3][3], fbox[3][3];       // index boxes (x, y, z extents) of edges / faces per axis
+  std::vector<uint8_t> eq[3], fq[3];    // entity orders
+  std::vector<int64_t> efirst[3], ffirst[3], cfirst;
+  double gll[kMaxOrder + 1][kMaxD];     // GLL nodes on [0, 1] of every order
+
+  int64_t lin(const int64_t* box, const int64_t* i) const {
+    return i[0] + box[0] * (i[1] + box[1] * i[2]);
+  }
+  int64_t vertex(const int64_t* i) const {
+    return i[0] + (int64_t)(n[0] + 1) * (i[1] + (int64_t)(n[1] + 1) * i[2]);
+  }
+  int cell_order(int64_t x, int64_t y, int64_t z) const {
+    if (x < 0 || y < 0 || z < 0 || x >= n[0] || y >= n[1] || z >= n[2]) return 1 << 20;
+    return ord[x + (int64_t)n[0] * (y + (int64_t)n[1] * z)];
+  }
+
+  // Value of the d-directed edge at index idx, at coordinate x in [0, 1] along it, times w.
+  void add_edge(int d, const int64_t* idx, double x, double w, Row& r) const {
+    const int q = eq[d][lin(ebox[d], idx)];
+    double L[kMaxD];
+    lagrange_at(gll[q], q + 1, x, L);
+    for (int m = 0; m <= q; ++m) {
+      const double lw = w * L[m];
+      if (lw == 0.0) continue;
+      if (m == 0) {
+        r.add(vertex(idx), lw);
+      } else if (m == q) {
+        int64_t hi[3] = {idx[0], idx[1], idx[2]};
+        ++hi[d];
+        r.add(vertex(hi), lw);
+      } else {
+        r.add(efirst[d][lin(ebox[d], idx)] + m - 1, lw);
+      }
+    }
+  }
+
+  // Value of the d-normal face at index idx, at in-plane coordinates (xs, xt), times w.
+  void add_face(int d, const int64_t* idx, double xs, double xt, double w, Row& r) const {
+    const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+    const int64_t f = lin(fbox[d], idx);
+    const int q = fq[d][f];
+    double Lu[kMaxD], Lv[kMaxD];
+    lagrange_at(gll[q], q + 1, xs, Lu);
+    lagrange_at(gll[q], q + 1, xt, Lv);
+    for (int b = 0; b <= q; ++b) {
+      for (int a = 0; a <= q; ++a) {
+        const double lw = w * Lu[a] * Lv[b];
+        if (lw == 0.0) continue;
+        const bool ia = a > 0 && a < q, ib = b > 0 && b < q;
+        if (ia && ib) {
+          r.add(ffirst[d][f] + (a - 1) + (int64_t)(q - 1) * (b - 1), lw);
+        } else if (!ia) {  // on the v-directed edge at u = a / q (corners included)
+          int64_t e[3] = {idx[0], idx[1], idx[2]};
+          e[u] += (a == q);
+          add_edge(v, e, gll[q][b], lw, r);
+        } else {           // on the u-directed edge at v = b / q
+          int64_t e[3] = {idx[0], idx[1], idx[2]};
+          e[v] += (b == q);
+          add_edge(u, e, gll[q][a], lw, r);
+        }
+      }
+    }
+  }
+
+  // Row of E for node (i, j, k) of element e.
+  void node_row(int64_t e, int i, int j, int k, Row& r) const {
+    r.n = 0;
+    const int p = ord[e];
+    const int64_t c[3] = {e % n[0], (e / n[0]) % n[1], e / ((int64_t)n[0] * n[1])};
+    const int ijk[3] = {i, j, k};
+    bool fixed[3];
+    int64_t pos[3];
+    int nb = 0;
+    for (int a = 0; a < 3; ++a) {
+      fixed[a] = ijk[a] == 0 || ijk[a] == p;
+      pos[a] = c[a] + (ijk[a] == p);
+      nb += fixed[a];
+    }
+    if (nb == 3) {
+      r.add(vertex(pos), 1.0);
+    } else if (nb == 0) {
+      r.add(cfirst[e] + (i - 1) + (int64_t)(p - 1) * ((j - 1) + (int64_t)(p - 1) * (k - 1)), 1.0);
+    } else if (nb == 2) {
+      const int d = !fixed[0] ? 0 : (!fixed[1] ? 1 : 2);
+      int64_t idx[3] = {pos[0], pos[1], pos[2]};
+      idx[d] = c[d];
+      add_edge(d, idx, gll[p][ijk[d]], 1.0, r);
+    } else {
+      const int d = fixed[0] ? 0 : (fixed[1] ? 1 : 2);
+      const int u = d == 0 ? 1 : 0, v = d == 2 ? 1 : 2;
+      int64_t idx[3] = {c[0], c[1], c[2]};
+      idx[d] = pos[d];
+      add_face(d, idx, gll[p][ijk[u]], gll[p][ijk[v]], 1.0, r);
+    }
+  }
+
+  bool on_boundary_edge(int d, const int64_t* idx) const {
+    for (int a = 0; a < 3; ++a)
+      if (a != d && (idx[a] == 0 || idx[a] == n[a])) return true;
+    return false;
+  }
+};
+
+// Entity orders and the numbering; false if an order is out of range.
+bool build_topology(int nx, int ny, int nz, const int32_t* order, Topo& T) {
+  T.n[0] = nx;
+  T.n[1] = ny;
+  T.n[2] = nz;
+  T.ne = (int64_t)nx * ny * nz;
+  T.ord.assign(order, order + T.ne);
+  for (int p : T.ord)
+    if (p < 1 || p > kMaxOrder) return false;
+  for (int q = 1; q <= kMaxOrder; ++q) {
+    Basis1D b;
+    if (!make_basis_1d(q, q + 2, &b)) return false;
+    for (int m = 0; m <= q; ++m) T.gll[q][m] = b.nodes[m];
+  }
+  T.nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  int64_t off = T.nv;
+  for (int d = 0; d < 3; ++d) {
+    for (int a = 0; a < 3; ++a) T.ebox[d][a] = T.n[a] + (a == d ? 0 : 1);
+    const int64_t cnt = T.ebox[d][0] * T.ebox[d][1] * T.ebox[d][2];
+    T.eq[d].resize(cnt);
+    T.efirst[d].resize(cnt);
+    int64_t i[3];
+    for (i[2] = 0; i[2] < T.ebox[d][2]; ++i[2])
+      for (i[1] = 0; i[1] < T.ebox[d][1]; ++i[1])
+        for (i[0] = 0; i[0] < T.ebox[d][0]; ++i[0]) {
+          int q = 1 << 20;
+          for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) {
+              int64_t c[3] = {i[0], i[1], i[2]};
+              int k = 0;
+              for (int a = 0; a < 3; ++a)
+                if (a != d) c[a] -= (k++ == 0 ? s : t);
+              q = std::min(q, T.cell_order(c[0], c[1], c[2]));
+            }
+          const int64_t l = T.lin(T.ebox[d], i);
+          T.eq[d][l] = (uint8_t)q;
+          T.efirst[d][l] = off;
+          off += q - 1;
+        }
+  }
+  for (int d = 0; d < 3; ++d) {
+    for (int a = 0; a < 3; ++a) T.fbox[d][a] = T.n[a] + (a == d ? 1 : 0);
+    const int64_t cnt = T.fbox[d][0] * T.fbox[d][1] * T.fbox[d][2];
+    T.fq[d].resize(cnt);
+    T.ffirst[d].resize(cnt);
+    int64_t i[3];
+    for (i[2] = 0; i[2] < T.fbox[d][2]; ++i[2])
+      for (i[1] = 0; i[1] < T.fbox[d][1]; ++i[1])
+        for (i[0] = 0; i[0] < T.fbox[d][0]; ++i[0]) {
+          int64_t c[3] = {i[0], i[1], i[2]};
+          const int q0 = T.cell_order(c[0], c[1], c[2]);
+          --c[d];
+          const int q = std::min(q0, T.cell_order(c[0], c[1], c[2]));
+          const int64_t l = T.lin(T.fbox[d], i);
+          T.fq[d][l] = (uint8_t)q;
+          T.ffirst[d][l] = off;
+          off += (int64_t)(q - 1) * (q - 1);
+        }
+  }
+  T.cfirst.resize(T.ne);
+  for (int64_t e = 0; e < T.ne; ++e) {
+    T.cfirst[e] = off;
+    off += (int64_t)(T.ord[e] - 1) * (T.ord[e] - 1) * (T.ord[e] - 1);
+  }
+  T.ntrue = off;
+  return true;
+}
+
+// Runs f(begin, end) over [0, n) on the host's cores.
+template <class F>
+void parallel_for(int64_t n, F f) {
+  const int nt = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  if (n < 4096 || nt == 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    const int64_t b = t * chunk, e = std::min(n, b + chunk);
+    if (b < e) th.emplace_back(f, b, e);
+  }
+  for (auto& x : th) x.join();
+}
+
+__global__ void k_csr_gather(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, int64_t nrows,
+                             const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = ptr[r], e = ptr[r + 1];
+    double s = 0.0;
+    for (int64_t t = b; t < e; ++t) s = fma(val[t], x[col[t]], s);
+    y[r] = s;
+  }
+}
+
+__global__ void k_identity_map(int32_t* __restrict__ map, int64_t n) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    map[t] = (int32_t)t;
+}
+
+unsigned grid_of(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+}
+
+}  // namespace
+
+struct fe_vspace {
+  int nx = 0, ny = 0, nz = 0, ops = 0;
+  int64_t ne = 0, ntrue = 0, nlocal = 0, nnz = 0;
+  std::vector<int64_t> elem_first;      // [ne] E-vector offset per element
+  double* d_vertices = nullptr;
+  int64_t* d_eptr = nullptr;            // E: [nlocal + 1]
+  int32_t* d_ecol = nullptr;            // [nnz] true dof
+  double* d_eval = nullptr;
+  int64_t* d_tptr = nullptr;            // E^T: [ntrue + 1]
+  int32_t* d_tcol = nullptr;            // [nnz] E-vector row
+  double* d_tval = nullptr;
+  uint8_t* d_mask = nullptr;            // [ntrue]
+  double* d_u = nullptr;                // E-vectors [nlocal]
+  double* d_v = nullptr;
+  int ngroups = 0;
+  int group_p[kMaxOrder];
+  int64_t group_off[kMaxOrder];         // first E-vector row of the group
+  fe_mesh* group_mesh[kMaxOrder];
+  fe_pa* group_pa[kMaxOrder];
+};
+
+namespace {
+
+void vspace_free(fe_vspace* vs) {
+  for (int g = 0; g < vs->ngroups; ++g) {
+    fe_pa_destroy(vs->group_pa[g]);
+    if (vs->group_mesh[g]) {
+      vs->group_mesh[g]->d_vertices = nullptr;  // shared, freed below
+      fe_mesh_destroy(vs->group_mesh[g]);
+    }
+  }
+  cudaFree(vs->d_vertices);
+  cudaFree(vs->d_eptr);
+  cudaFree(vs->d_ecol);
+  cudaFree(vs->d_eval);
+  cudaFree(vs->d_tptr);
+  cudaFree(vs->d_tcol);
+  cudaFree(vs->d_tval);
+  cudaFree(vs->d_mask);
+  cudaFree(vs->d_u);
+  cudaFree(vs->d_v);
+  delete vs;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  cudaError_t err = cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size()));
+  if (err != cudaSuccess) return err;
+  return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
+                    const double* host_vertices, const double* host_coeff, int ops, void* stream,
+                    fe_vspace** out) {
+  clear_error();
+  if (!out) return set_error(FE_ERR_ARG, "fe_vspace_setup: out is NULL");
+  *out = nullptr;
+  if (!host_order || !host_vertices) return set_error(FE_ERR_ARG, "fe_vspace_setup: null argument");
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(FE_ERR_ARG, "fe_vspace_setup: mesh size < 1");
+  if (ops <= 0 || (ops & ~(FE_DIFFUSION | FE_MASS)))
+    return set_error(FE_ERR_ARG, "fe_vspace_setup: ops must be FE_DIFFUSION and/or FE_MASS");
+  Topo T;
+  if (!build_topology(nx, ny, nz, host_order, T))
+    return set_error(FE_ERR_ARG, "fe_vspace_setup: orders must be 1..8");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // E-vector layout: groups of ascending order, elements ascending within a group
+  std::vector<int64_t> first(T.ne);
+  int present[kMaxOrder + 1] = {0};
+  for (int p : T.ord) present[p] = 1;
+  int64_t nlocal = 0;
+  std::vector<int64_t> order_elems;  // elements in E-vector order
+  order_elems.reserve(T.ne);
+  for (int p = 1; p <= kMaxOrder; ++p) {
+    if (!present[p]) continue;
+    for (int64_t e = 0; e < T.ne; ++e)
+      if (T.ord[e] == p) {
+        first[e] = nlocal;
+        nlocal += (int64_t)(p + 1) * (p + 1) * (p + 1);
+        order_elems.push_back(e);
+      }
+  }
+  if (T.ntrue > 2147483647LL || nlocal > 2147483647LL)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_setup: more than 2^31-1 true or local dofs");
+
+  // E by rows: count, offsets, fill (two passes over the elements on the host's cores)
+  std::vector<int64_t> rowcnt(nlocal + 1, 0);
+  auto count = [&](int64_t b, int64_t e_end) {
+    Row r;
+    for (int64_t t = b; t < e_end; ++t) {
+      const int64_t e = order_elems[t];
+      const int D = T.ord[e] + 1;
+      for (int a = 0; a < D * D * D; ++a) {
+        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+        rowcnt[first[e] + a + 1] = r.n;
+      }
+    }
+  };
+  parallel_for((int64_t)order_elems.size(), count);
+  for (int64_t r = 0; r < nlocal; ++r) rowcnt[r + 1] += rowcnt[r];
+  const int64_t nnz = rowcnt[nlocal];
+  std::vector<int32_t> ecol(nnz);
+  std::vector<double> evalv(nnz);
+  auto fill = [&](int64_t b, int64_t e_end) {
+    Row r;
+    for (int64_t t = b; t < e_end; ++t) {
+      const int64_t e = order_elems[t];
+      const int D = T.ord[e] + 1;
+      for (int a = 0; a < D * D * D; ++a) {
+        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+        // columns ascending within a row (a fixed summation order): insertion sort
+        for (int z = 1; z < r.n; ++z)
+          for (int y = z; y > 0 && r.col[y - 1] > r.col[y]; --y) {
+            std::swap(r.col[y - 1], r.col[y]);
+            std::swap(r.w[y - 1], r.w[y]);
+          }
+        const int64_t o = rowcnt[first[e] + a];
+        for (int z = 0; z < r.n; ++z) {
+          ecol[o + z] = (int32_t)r.col[z];
+          evalv[o + z] = r.w[z];
+        }
+      }
+    }
+  };
+  parallel_for((int64_t)order_elems.size(), fill);
+
+  // E^T by counting sort on the column (rows ascending within each column)
+  std::vector<int64_t> tptr(T.ntrue + 1, 0);
+  for (int64_t t = 0; t < nnz; ++t) ++tptr[ecol[t] + 1];
+  for (int64_t c = 0; c < T.ntrue; ++c) tptr[c + 1] += tptr[c];
+  std::vector<int32_t> tcol(nnz);
+  std::vector<double> tval(nnz);
+  {
+    std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
+    for (int64_t r = 0; r < nlocal; ++r)
+      for (int64_t t = rowcnt[r]; t < rowcnt[r + 1]; ++t) {
+        const int64_t o = pos[ecol[t]]++;
+        tcol[o] = (int32_t)r;
+        tval[o] = evalv[t];
+      }
+  }
+
+  // boundary mask of the true dofs
+  std::vector<uint8_t> mask(T.ntrue, 0);
+  {
+    int64_t i[3];
+    for (i[2] = 0; i[2] <= nz; ++i[2])
+      for (i[1] = 0; i[1] <= ny; ++i[1])
+        for (i[0] = 0; i[0] <= nx; ++i[0])
+          mask[T.vertex(i)] = i[0] == 0 || i[1] == 0 || i[2] == 0 || i[0] == nx || i[1] == ny ||
+                              i[2] == nz;
+    for (int d = 0; d < 3; ++d) {
+      for (i[2] = 0; i[2] < T.ebox[d][2]; ++i[2])
+        for (i[1] = 0; i[1] < T.ebox[d][1]; ++i[1])
+          for (i[0] = 0; i[0] < T.ebox[d][0]; ++i[0]) {
+            const int64_t l = T.lin(T.ebox[d], i);
+            if (T.on_boundary_edge(d, i))
+              for (int m = 0; m < T.eq[d][l] - 1; ++m) mask[T.efirst[d][l] + m] = 1;
+          }
+      for (i[2] = 0; i[2] < T.fbox[d][2]; ++i[2])
+        for (i[1] = 0; i[1] < T.fbox[d][1]; ++i[1])
+          for (i[0] = 0; i[0] < T.fbox[d][0]; ++i[0]) {
+            const int64_t l = T.lin(T.fbox[d], i);
+            if (i[d] == 0 || i[d] == T.n[d])
+              for (int m = 0; m < (T.fq[d][l] - 1) * (T.fq[d][l] - 1); ++m)
+                mask[T.ffirst[d][l] + m] = 1;
+          }
+    }
+  }
+
+  fe_vspace* vs = new fe_vspace();
+  vs->nx = nx;
+  vs->ny = ny;
+  vs->nz = nz;
+  vs->ops = ops;
+  vs->ne = T.ne;
+  vs->ntrue = T.ntrue;
+  vs->nlocal = nlocal;
+  vs->nnz = nnz;
+  vs->elem_first = first;
+  const int64_t nv = T.nv;
+  cudaError_t err = cudaMalloc(&vs->d_vertices, sizeof(double) * 3 * nv);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(vs->d_vertices, host_vertices, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = upload(&vs->d_eptr, rowcnt);
+  if (err == cudaSuccess) err = upload(&vs->d_ecol, ecol);
+  if (err == cudaSuccess) err = upload(&vs->d_eval, evalv);
+  if (err == cudaSuccess) err = upload(&vs->d_tptr, tptr);
+  if (err == cudaSuccess) err = upload(&vs->d_tcol, tcol);
+  if (err == cudaSuccess) err = upload(&vs->d_tval, tval);
+  if (err == cudaSuccess) err = upload(&vs->d_mask, mask);
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_u, sizeof(double) * std::max<int64_t>(1, nlocal));
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_v, sizeof(double) * std::max<int64_t>(1, nlocal));
+  if (err != cudaSuccess) {
+    vspace_free(vs);
+    return cuda_error(err, "fe_vspace_setup: upload");
+  }
+
+  // one partial assembly per order present, over that order's elements
+  int64_t t0 = 0;
+  for (int p = 1; p <= kMaxOrder; ++p) {
+    if (!present[p]) continue;
+    const int g = vs->ngroups++;
+    vs->group_p[g] = p;
+    vs->group_mesh[g] = nullptr;
+    vs->group_pa[g] = nullptr;
+    std::vector<int32_t> ids;
+    std::vector<double> coeff;
+    while (t0 < (int64_t)order_elems.size() && T.ord[order_elems[t0]] == p) {
+      ids.push_back((int32_t)order_elems[t0]);
+      if (host_coeff) coeff.push_back(host_coeff[order_elems[t0]]);
+      ++t0;
+    }
+    vs->group_off[g] = first[ids[0]];
+    fe_mesh* m = new fe_mesh();
+    vs->group_mesh[g] = m;
+    m->nx = nx;
+    m->ny = ny;
+    m->nz = nz;
+    m->p = p;
+    m->D = p + 1;
+    m->ne = (int64_t)ids.size();
+    m->ndofs = m->ne * m->D * m->D * m->D;
+    cudaGetDevice(&m->device);
+    m->d_vertices = vs->d_vertices;
+    err = upload(&m->d_elem_ids, ids);
+    if (err == cudaSuccess) err = cudaMalloc(&m->d_map, sizeof(int32_t) * m->ndofs);
+    if (err == cudaSuccess) {
+      k_identity_map<<<grid_of(m->ndofs), 256, 0, s>>>(m->d_map, m->ndofs);
+      err = cudaGetLastError();
+    }
+    double* dc = nullptr;
+    if (err == cudaSuccess && host_coeff) err = upload(&dc, coeff);
+    if (err != cudaSuccess) {
+      cudaFree(dc);
+      vspace_free(vs);
+      return cuda_error(err, "fe_vspace_setup: order group");
+    }
+    const int st = fe_pa_setup(m, 0, dc, ops, stream, &vs->group_pa[g]);
+    cudaFree(dc);
+    if (st != FE_OK) {
+      const std::string msg = fe_last_error();
+      vspace_free(vs);
+      return set_error(st, "fe_vspace_setup: " + msg);
+    }
+  }
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) {
+    vspace_free(vs);
+    return cuda_error(err, "fe_vspace_setup");
+  }
+  *out = vs;
+  return FE_OK;
+}
+
+int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_t* nnz) {
+  clear_error();
+  if (!vs) return set_error(FE_ERR_ARG, "fe_vspace_sizes: handle is NULL");
+  if (ntrue) *ntrue = vs->ntrue;
+  if (nlocal) *nlocal = vs->nlocal;
+  if (nnz) *nnz = vs->nnz;
+  return FE_OK;
+}
+
+int fe_vspace_layout(const fe_vspace* vs, int64_t* host_first) {
+  clear_error();
+  if (!vs || !host_first) return set_error(FE_ERR_ARG, "fe_vspace_layout: null argument");
+  std::memcpy(host_first, vs->elem_first.data(), sizeof(int64_t) * vs->ne);
+  return FE_OK;
+}
+
+int fe_vspace_boundary_mask(const fe_vspace* vs, uint8_t* dev_mask, void* stream) {
+  clear_error();
+  if (!vs || !dev_mask) return set_error(FE_ERR_ARG, "fe_vspace_boundary_mask: null argument");
+  cudaError_t err = cudaMemcpyAsync(dev_mask, vs->d_mask, (size_t)vs->ntrue,
+                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_boundary_mask");
+  return FE_OK;
+}
+
+int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream) {
+  clear_error();
+  if (!vs) return set_error(FE_ERR_ARG, "fe_vspace_set_variant: handle is NULL");
+  for (int g = 0; g < vs->ngroups; ++g) {
+    const int st = fe_pa_set_variant(vs->group_pa[g], variant, stream);
+    if (st != FE_OK) return st;
+  }
+  return FE_OK;
+}
+
+int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream) {
+  clear_error();
+  if (!vs || !dev_x || !dev_e) return set_error(FE_ERR_ARG, "fe_vspace_prolong: null argument");
+  k_csr_gather<<<grid_of(vs->nlocal), 256, 0, (cudaStream_t)stream>>>(
+      vs->d_eptr, vs->d_ecol, vs->d_eval, vs->nlocal, dev_x, dev_e);
+  return cuda_error(cudaGetLastError(), "fe_vspace_prolong: launch");
+}
+
+int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
+                    void* stream) {
+  clear_error();
+  if (!vs || !dev_x || !dev_y) return set_error(FE_ERR_ARG, "fe_vspace_apply: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_apply: bad op");
+  if (!(vs->ops & op))
+    return set_error(FE_ERR_ARG, "fe_vspace_apply: operator not set up in fe_vspace_setup");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_csr_gather<<<grid_of(vs->nlocal), 256, 0, s>>>(vs->d_eptr, vs->d_ecol, vs->d_eval,
+                                                   vs->nlocal, dev_x, vs->d_u);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: gather launch");
+  for (int g = 0; g < vs->ngroups; ++g) {
+    const fe_pa* pa = vs->group_pa[g];
+    const int st = apply_dispatch(pa, op, pa->variant, vs->d_u + vs->group_off[g],
+                                  vs->d_v + vs->group_off[g], s);
+    if (st != FE_OK) return st;
+  }
+  k_csr_gather<<<grid_of(vs->ntrue), 256, 0, s>>>(vs->d_tptr, vs->d_tcol, vs->d_tval, vs->ntrue,
+                                                  vs->d_v, dev_y);
+  return cuda_error(cudaGetLastError(), "fe_vspace_apply: scatter launch");
+}
+
+void fe_vspace_destroy(fe_vspace* vs) {
+  if (vs) vspace_free(vs);
+}
+
+}  // extern "C"

@@ -103,6 +103,17 @@ _SIGS = {
     "fe_fcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                  ctypes.c_double, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_lpc_destroy": (None, [_VP]),
+    "fe_vspace_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP,
+                                       ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "fe_vspace_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "fe_vspace_layout": (ctypes.c_int, [_VP, _VP]),
+    "fe_vspace_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
+    "fe_vspace_set_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
+    "fe_vspace_prolong": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_vspace_apply": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_vspace_destroy": (None, [_VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -418,6 +429,56 @@ def fe_fcg_ir(pa, op, lpc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=Non
 def fe_lpc_destroy(lpc):
     if lpc:
         load().fe_lpc_destroy(_VP(lpc))
+
+
+def fe_vspace_setup(nx, ny, nz, orders, vertices, coeff=None, ops=FE_DIFFUSION | FE_MASS,
+                    stream=None):
+    """orders: host int32 [ne]; vertices: host float64 [(nx+1)(ny+1)(nz+1), 3]; coeff: host
+    float64 [ne] or None.  Returns the variable-order space handle."""
+    lib = load()
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    c = None if coeff is None else np.ascontiguousarray(coeff, dtype=np.float64)
+    out = _VP()
+    _check(lib.fe_vspace_setup(int(nx), int(ny), int(nz), o.ctypes.data_as(_VP),
+                               v.ctypes.data_as(_VP), None if c is None else c.ctypes.data_as(_VP),
+                               int(ops), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def fe_vspace_sizes(vs):
+    """(ntrue, nlocal, nnz)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fe_vspace_sizes(_VP(vs), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def fe_vspace_layout(vs, ne):
+    first = np.zeros(int(ne), dtype=np.int64)
+    _check(load().fe_vspace_layout(_VP(vs), first.ctypes.data_as(_VP)))
+    return first
+
+
+def fe_vspace_boundary_mask(vs, dev_mask, stream=None):
+    _check(load().fe_vspace_boundary_mask(_VP(vs), _ptr(dev_mask), _stream(stream)))
+
+
+def fe_vspace_set_variant(vs, variant, stream=None):
+    v = VARIANTS.get(variant, variant)
+    _check(load().fe_vspace_set_variant(_VP(vs), int(v), _stream(stream)))
+
+
+def fe_vspace_prolong(vs, dev_x, dev_e, stream=None):
+    _check(load().fe_vspace_prolong(_VP(vs), _ptr(dev_x), _ptr(dev_e), _stream(stream)))
+
+
+def fe_vspace_apply(vs, op, dev_x, dev_y, stream=None):
+    _check(load().fe_vspace_apply(_VP(vs), int(op), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_vspace_destroy(vs):
+    if vs:
+        load().fe_vspace_destroy(_VP(vs))
 
 
 def fe_pa_destroy(pa):

@@ -1,0 +1,169 @@
+"""GPU parity of the variable-order (minimum-rule) space against the oracle, through the C ABI.
+
+Small meshes: every entry of E x and of y = E^T blockdiag(A_e) E x against the oracle (several
+element blocks per order, ragged block sizes, all orders 1..8 present somewhere).  The benchmark's
+mixed-order workload (64^3 hexes, 8^3-element blocks of orders 2, 4, 6): properties that hold at
+any size (partition of unity, constants in the kernel of the diffusion operator, volume, symmetry).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle.element import DIFFUSION, MASS
+from oracle.varorder import VarSpace
+from paper_2603_09038_gb300.inputs import (block_orders, lognormal_coefficient, perturbed_vertices,
+                                           uniform_vector)
+from tests.gpu_util import TOL, lib, rel_err, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "blocks_2_4_6": ((4, 4, 4), dict(block=2, orders=(2, 4, 6), seed=1), None),
+    "ragged_1to5_sigma1": ((5, 4, 3), dict(block=1, orders=(1, 2, 3, 4, 5), seed=2), 1.0),
+    "orders_6to8": ((2, 2, 1), dict(block=1, orders=(6, 7, 8), seed=3), None),
+    "single_order_3": ((3, 3, 3), dict(block=4, orders=(3,), seed=0), None),
+}
+
+
+def _setup(name):
+    dims, kw, sigma = CASES[name]
+    ne = int(np.prod(dims))
+    orders = block_orders(*dims, **kw)
+    V = perturbed_vertices(*dims, seed=5)
+    c = None if sigma is None else lognormal_coefficient(ne, sigma)
+    return dims, orders, V, c
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(name):
+    """(space, E) of a case, built once per session (the Python construction takes seconds)."""
+    dims, orders, _, _ = _setup(name)
+    S = VarSpace(*dims, orders)
+    return S, S.prolongation()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sizes_layout_and_mask(name):
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        ntrue, nlocal, nnz = fe.fe_vspace_sizes(vs)
+        assert (ntrue, nlocal, nnz) == (S.ntrue, S.nlocal, E.nnz)
+        first = fe.fe_vspace_layout(vs, S.ne)
+        # groups of ascending order, elements ascending within each
+        key = sorted(range(S.ne), key=lambda e: (S.order[e], e))
+        expect = np.zeros(S.ne, dtype=np.int64)
+        off = 0
+        for e in key:
+            expect[e] = off
+            off += int(S.order[e] + 1) ** 3
+        np.testing.assert_array_equal(first, expect)
+        m = torch.zeros(ntrue, dtype=torch.uint8, device="cuda")
+        fe.fe_vspace_boundary_mask(vs, m)
+        np.testing.assert_array_equal(m.cpu().numpy(), S.boundary_mask())
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_prolongation_matches_oracle(name):
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        x = uniform_vector(S.ntrue, seed=21)
+        ref = E @ x
+        dx = torch.from_numpy(x).cuda()
+        de = torch.empty(S.nlocal, dtype=torch.float64, device="cuda")
+        fe.fe_vspace_prolong(vs, dx, de)
+        got = de.cpu().numpy()
+        first = fe.fe_vspace_layout(vs, S.ne)
+        perm = np.concatenate([first[e] + np.arange(int(S.local_size[e])) for e in range(S.ne)])
+        assert rel_err(got[perm], ref) <= 1e-14
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_matches_oracle(name):
+    """Both FP64-accurate variants (FP64 and float-float) against the oracle's E^T A E x."""
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    x = uniform_vector(S.ntrue, seed=22)
+    refs = {kind: S.apply(V, x, kind, coeff=c, E=E) for kind in (DIFFUSION, MASS)}
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.empty(S.ntrue, dtype=torch.float64, device="cuda")
+        for variant in ("f64", "f32x2"):
+            fe.fe_vspace_set_variant(vs, variant)
+            for kind, op in ((DIFFUSION, fe.FE_DIFFUSION), (MASS, fe.FE_MASS)):
+                fe.fe_vspace_apply(vs, op, dx, dy)
+                assert rel_err(dy.cpu().numpy(), refs[kind]) <= TOL, (kind, variant)
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+def test_argument_errors():
+    fe = lib()
+    torch_cuda()
+    V = perturbed_vertices(2, 2, 2)
+    for bad in ([0] + [2] * 7, [9] + [2] * 7):
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_vspace_setup(2, 2, 2, bad, V)
+        assert ei.value.status == fe.FE_ERR_ARG
+    with pytest.raises(fe.FEError):
+        fe.fe_vspace_setup(2, 2, 2, [2] * 8, V, ops=0)
+    vs = fe.fe_vspace_setup(2, 2, 2, [2] * 8, V, ops=fe.FE_MASS)
+    try:
+        import torch
+        x = torch.zeros(fe.fe_vspace_sizes(vs)[0], dtype=torch.float64, device="cuda")
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, torch.empty_like(x))
+        assert ei.value.status == fe.FE_ERR_ARG
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+def test_benchmark_workload_properties():
+    """64^3 hexes, 8^3-element blocks of orders 2, 4, 6, perturbed unit cube (the launch
+    configuration the benchmark times): E 1 = 1 on every node, A 1 = 0 for diffusion,
+    1^T M 1 = volume 1, and x^T A y = y^T A x for both operators."""
+    torch = torch_cuda()
+    fe = lib()
+    n = 64
+    orders = block_orders(n, n, n, block=8, orders=(2, 4, 6), seed=7)
+    V = perturbed_vertices(n, n, n)
+    vs = fe.fe_vspace_setup(n, n, n, orders, V)
+    try:
+        fe.fe_vspace_set_variant(vs, "f32x2")
+        ntrue, nlocal, _ = fe.fe_vspace_sizes(vs)
+        one = torch.ones(ntrue, dtype=torch.float64, device="cuda")
+        e = torch.empty(nlocal, dtype=torch.float64, device="cuda")
+        fe.fe_vspace_prolong(vs, one, e)
+        assert float((e - 1).abs().max()) <= 1e-14
+        y = torch.empty_like(one)
+        fe.fe_vspace_apply(vs, fe.FE_MASS, one, y)
+        assert abs(float(y.sum()) - 1.0) <= 1e-12
+        fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, one, y)
+        x = torch.from_numpy(uniform_vector(ntrue, seed=1)).cuda()
+        ax = torch.empty_like(x)
+        fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, ax)
+        assert float(y.abs().max()) <= 1e-12 * float(ax.abs().max())
+        z = torch.from_numpy(uniform_vector(ntrue, seed=2)).cuda()
+        az = torch.empty_like(z)
+        for op in (fe.FE_DIFFUSION, fe.FE_MASS):
+            fe.fe_vspace_apply(vs, op, x, ax)
+            fe.fe_vspace_apply(vs, op, z, az)
+            a, b = float(torch.dot(z, ax)), float(torch.dot(x, az))
+            assert abs(a - b) <= 1e-12 * float(ax.abs().sum()), op
+    finally:
+        fe.fe_vspace_destroy(vs)
