@@ -37,6 +37,19 @@ from .quadrature import gauss_lobatto, lagrange
 BIG = 1 << 20
 
 
+def _lagrange_at(nodes, x):
+    """Lagrange basis of ``nodes`` at the single point x; a point within 1e-13 of a node is that
+    node (GLL nodes of different orders coincide at 0, 1/2 and 1, and separately computed values
+    of one point may differ in the last bit)."""
+    t = np.asarray(nodes, dtype=np.float64)
+    hit = np.nonzero(np.abs(t - x) <= 1e-13)[0]
+    if hit.size:
+        out = np.zeros(len(t))
+        out[hit[0]] = 1.0
+        return out
+    return lagrange(t, [x])[0][0]
+
+
 class VarSpace:
     """Minimum-rule variable-order H1 space of an nx x ny x nz structured hex mesh; ``order`` holds
     one order (1..8) per element, element index ex + nx*(ey + ny*ez)."""
@@ -133,8 +146,8 @@ class VarSpace:
                     base[v] += (n == q)
                     ed, coord = u, t[m]                 # edge runs along u
                 qe, erows = self._edge_closure(ed, *base)
-                L, _ = lagrange(gauss_lobatto(qe + 1), [coord])
-                rows[m + (q + 1) * n] = _combine(L[0], erows)
+                rows[m + (q + 1) * n] = _combine(_lagrange_at(gauss_lobatto(qe + 1), coord),
+                                                 erows)
         return q, rows
 
     def prolongation(self):
@@ -166,8 +179,7 @@ class VarSpace:
                     if key not in edges:
                         edges[key] = self._edge_closure(*key)
                     qe, erows = edges[key]
-                    L, _ = lagrange(gauss_lobatto(qe + 1), [tp[ijk[d]]])
-                    row = _combine(L[0], erows)
+                    row = _combine(_lagrange_at(gauss_lobatto(qe + 1), tp[ijk[d]]), erows)
                 else:
                     d = fixed.index(True)
                     key = list(cell)
@@ -178,13 +190,14 @@ class VarSpace:
                     qf, frows = faces[key]
                     u, v = [x for x in range(3) if x != d]
                     tq = gauss_lobatto(qf + 1)
-                    Lu, _ = lagrange(tq, [tp[ijk[u]]])
-                    Lv, _ = lagrange(tq, [tp[ijk[v]]])
-                    w = np.outer(Lv[0], Lu[0]).reshape(-1)      # index m + (q+1) n
+                    Lu = _lagrange_at(tq, tp[ijk[u]])
+                    Lv = _lagrange_at(tq, tp[ijk[v]])
+                    w = np.outer(Lv, Lu).reshape(-1)            # index m + (q+1) n
                     row = _combine(w, frows)
                 r = int(self.local_first[e]) + a
                 for c, val in row.items():
-                    if val != 0.0:
+                    # cancelling contributions leave ~1e-17 where the exact weight is 0
+                    if abs(val) > 1e-13:
                         ri.append(r)
                         ci.append(c)
                         data.append(val)

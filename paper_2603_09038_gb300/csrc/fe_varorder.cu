@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -41,8 +42,15 @@ struct Row {
   }
 };
 
-// l_m(x) of the Lagrange basis on nodes t[0..n-1] (product formula).
+// l_m(x) of the Lagrange basis on nodes t[0..n-1] (product formula).  A point within 1e-13 of a
+// node is that node (l_m = delta): GLL nodes of different orders coincide at 0, 1/2 and 1, and
+// their separately computed values may differ in the last bit.
 void lagrange_at(const double* t, int n, double x, double* L) {
+  for (int k = 0; k < n; ++k)
+    if (std::fabs(x - t[k]) <= 1e-13) {
+      for (int m = 0; m < n; ++m) L[m] = m == k ? 1.0 : 0.0;
+      return;
+    }
   for (int m = 0; m < n; ++m) {
     double v = 1.0;
     for (int k = 0; k < n; ++k)
@@ -149,6 +157,15 @@ struct Topo {
       idx[d] = pos[d];
       add_face(d, idx, gll[p][ijk[u]], gll[p][ijk[v]], 1.0, r);
     }
+    // contributions that cancel leave round-off (~1e-17) where the exact weight is 0: drop them
+    int kept = 0;
+    for (int t = 0; t < r.n; ++t)
+      if (std::fabs(r.w[t]) > 1e-13) {
+        r.col[kept] = r.col[t];
+        r.w[kept] = r.w[t];
+        ++kept;
+      }
+    r.n = kept;
   }
 
   bool on_boundary_edge(int d, const int64_t* idx) const {
