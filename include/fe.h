@@ -313,6 +313,12 @@ int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);
 int fe_lpc_loss_grad(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
                      float* host_y, float* host_grad, double* loss);
 
+/* What fe_fcg continues with once it gives up the network: FE_PC_JACOBI (the default: FCG
+ * restarted with Jacobi from the current iterate) or FE_PC_CHEBYSHEV (Chebyshev-PCG on the
+ * residual equation).  fe_fcg_ir's inner solves always fall back to Jacobi.  FE_ERR_ARG
+ * otherwise. */
+int fe_lpc_set_fallback(fe_lpc* lpc, int pc);
+
 /* z = M(r) for FP64 device vectors of length ndofs (z overwritten; z = 0 on the boundary).
  * Asynchronous. */
 int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
@@ -321,8 +327,12 @@ int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
  * same system, arguments and stopping rule as fe_pcg, preconditioned by lpc, or by Jacobi when
  * lpc is NULL.  If the learned preconditioner produces a non-descent direction (z.r <= 0) or the
  * residual stops improving (no 1% gain in 500 iterations, or a 1e4-fold rise) the iteration
- * restarts from the current iterate with Jacobi.  Applies use pa's variant; vectors and inner products are FP64.
- * stats: outer_iters = 1 + number of such restarts.  Synchronous. */
+ * restarts from the current iterate with Jacobi, or -- after fe_lpc_set_fallback(lpc,
+ * FE_PC_CHEBYSHEV) -- hands over to Chebyshev-PCG (fe_pcg_chebyshev with its defaults), which
+ * solves A d = (1-m)(b - A x) to the tolerance that meets rtol for x + d, and x += d.  Applies
+ * use pa's variant; vectors and inner products are FP64.  stats: outer_iters = 1 + number of
+ * such restarts / hand-overs; iters counts both solvers' iterations; with the hand-over also
+ * allocates 3 vectors and fe_pcg_chebyshev's workspace.  Synchronous. */
 int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,
            int maxit, fe_pcg_stats* stats, void* stream);
 

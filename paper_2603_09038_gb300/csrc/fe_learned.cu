@@ -42,6 +42,7 @@ int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s);
 struct fe_lpc {
   fe_pa* pa = nullptr;  // not owned
   int op = FE_DIFFUSION;
+  int fallback = FE_PC_JACOBI;  // what fe_fcg continues with once the network is given up
   int din = 0, width = 0;
   int64_t nparam = 0;
   float* w32 = nullptr;         // packed FP32 master weights W1 | W2 | W3
@@ -646,6 +647,8 @@ struct Snapshots {  // residual snapshots at the listed iterations (training dat
 struct FcgResult {
   int iters = 0, launches = 0, restarts = 0, status = FE_OK;
   double rel = 0.0, true_rel = 0.0;
+  bool stop_at_fallback = false;  // in: end the run where it would fall back to Jacobi
+  bool handed_off = false;        // out: it did (x holds the iterate reached)
 };
 
 int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s);
@@ -728,7 +731,10 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
   if (st == FE_OK && learned && hsc[S_BB] > 0.0 && !(hsc[S_ZR] > 0.0)) {
     learned = false;  // not a descent direction: Jacobi from the start
     ++res->restarts;
-    st = precond();
+    if (res->stop_at_fallback)
+      res->handed_off = true;
+    else
+      st = precond();
   }
   if (st == FE_OK) {
     k_fcg_p<VT><<<kRB, kT, 0, s>>>(p, z, F64 ? nullptr : q, n, sc, 1);
@@ -742,7 +748,8 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
     res->status = isfinite(bb) ? FE_OK : FE_ERR_NAN;
     rel = 0.0;
   }
-  for (int it = 1; st == FE_OK && res->status == FE_ERR_NOT_CONVERGED && it <= maxit; ++it) {
+  for (int it = 1; st == FE_OK && !res->handed_off && res->status == FE_ERR_NOT_CONVERGED &&
+                   it <= maxit; ++it) {
     if ((st = apply(p, q)) != FE_OK) break;
     k_fcg_pq<VT><<<kRB, kT, 0, s>>>(p, q, r, mask, n, part0, part1);
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 1);
@@ -781,6 +788,10 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
       restart = true;
       ++res->restarts;
       last_gain = it;
+      if (res->stop_at_fallback) {
+        res->handed_off = true;
+        break;
+      }
       if ((st = precond()) != FE_OK) break;
     }
     k_fcg_p<VT><<<kRB, kT, 0, s>>>(p, z, F64 ? nullptr : q, n, sc, restart ? 1 : 0);
@@ -820,6 +831,12 @@ __global__ void __launch_bounds__(kT) k_ir_resid(const double* __restrict__ b,
     c = fma(bi, bi, c);
   }
   block_partial2(a, c, part0, part1);
+}
+
+__global__ void k_add_f64(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -1478,11 +1495,62 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
       res.launches += 2;
     }
   }
+  res.stop_at_fallback = lpc && lpc->fallback == FE_PC_CHEBYSHEV;
   if (st == FE_OK) st = fcg_run(pa, op, lpc, dinv, dev_b, dev_x, rtol, maxit, nullptr, s, &res);
   cudaFree(own);
   if (st != FE_OK) return st;
+  int cheb_iters = 0;
+  if (res.handed_off) {
+    // Chebyshev-PCG on the residual equation A d = (1-m)(b - A x) from d = 0, to the tolerance
+    // that makes ||b - A (x + d)|| <= rtol ||b||; then x += d.
+    const int64_t n = m->ndofs;
+    double *buf = nullptr, *red = nullptr;
+    cudaError_t err = cudaMalloc(&buf, sizeof(double) * 3 * n);
+    if (err == cudaSuccess) err = cudaMalloc(&red, sizeof(double) * (2 * kRB + S_N));
+    if (err != cudaSuccess) {
+      cudaFree(buf);
+      return cuda_error(err, "fe_fcg: fallback workspace");
+    }
+    double *q = buf, *r = buf + n, *d = buf + 2 * n;
+    double hsc[S_N];
+    st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
+    if (st == FE_OK) {
+      cudaMemsetAsync(red + 2 * kRB, 0, sizeof(double) * S_N, s);
+      k_ir_resid<<<kRB, kT, 0, s>>>(dev_b, q, m->d_mask, r, n, red, red + kRB);
+      k_fcg_finish<<<1, kRB, 0, s>>>(red, red + kRB, red + 2 * kRB, 4);
+      res.launches += 3;
+      if ((err = cudaGetLastError()) != cudaSuccess ||
+          (err = cudaMemcpyAsync(hsc, red + 2 * kRB, sizeof(hsc), cudaMemcpyDeviceToHost, s)) !=
+              cudaSuccess ||
+          (err = cudaStreamSynchronize(s)) != cudaSuccess)
+        st = cuda_error(err, "fe_fcg: fallback residual");
+    }
+    fe_pcg_stats cs{0, 0.0, 0.0, 0.0, 0, 0};
+    int cst = FE_OK;
+    if (st == FE_OK) {
+      const double rn = sqrt(hsc[S_TRUE]), bn = sqrt(hsc[S_BB]);
+      const double rtol_c = rn > 0.0 ? rtol * bn / rn : 1.0;
+      cst = fe_pcg_chebyshev(pa, op, 0, 0.0, 0.0, r, d, std::min(rtol_c, 1.0),
+                             std::max(1, maxit - res.iters), &cs, stream);
+      if (cst == FE_OK || cst == FE_ERR_NOT_CONVERGED) {
+        k_add_f64<<<grid1(n), kT, 0, s>>>(dev_x, d, n);
+        res.launches += 1 + cs.launches;
+        cheb_iters = cs.iters;
+        res.rel = bn > 0.0 ? cs.rel_resid * rn / bn : 0.0;
+        res.true_rel = bn > 0.0 ? cs.true_rel_resid * rn / bn : 0.0;
+        res.status = cst;
+        err = cudaStreamSynchronize(s);
+        if (err != cudaSuccess) st = cuda_error(err, "fe_fcg: fallback update");
+      } else {
+        st = cst;
+      }
+    }
+    cudaFree(buf);
+    cudaFree(red);
+    if (st != FE_OK) return st;
+  }
   if (stats) {
-    stats->iters = res.iters;
+    stats->iters = res.iters + cheb_iters;
     stats->rel_resid = res.rel;
     stats->true_rel_resid = res.true_rel;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1499,6 +1567,15 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
     default:
       return set_error(FE_ERR_NOT_CONVERGED, "fe_fcg: maxit reached before rtol");
   }
+}
+
+int fe_lpc_set_fallback(fe_lpc* lpc, int pc) {
+  clear_error();
+  if (!lpc) return set_error(FE_ERR_ARG, "fe_lpc_set_fallback: lpc is NULL");
+  if (pc != FE_PC_JACOBI && pc != FE_PC_CHEBYSHEV)
+    return set_error(FE_ERR_ARG, "fe_lpc_set_fallback: pc must be FE_PC_JACOBI or FE_PC_CHEBYSHEV");
+  lpc->fallback = pc;
+  return FE_OK;
 }
 
 void fe_lpc_destroy(fe_lpc* L) {

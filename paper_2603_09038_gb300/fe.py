@@ -98,6 +98,7 @@ _SIGS = {
     "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_lpc_set_fallback": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fe_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                               ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_fcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
@@ -424,6 +425,11 @@ def fe_fcg_ir(pa, op, lpc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=Non
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_lpc_set_fallback(lpc, pc):
+    """pc: FE_PC_JACOBI or FE_PC_CHEBYSHEV -- what fe_fcg continues with once it gives up lpc."""
+    _check(load().fe_lpc_set_fallback(_VP(lpc), int(pc)))
 
 
 def fe_lpc_destroy(lpc):

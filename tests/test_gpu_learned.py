@@ -162,6 +162,55 @@ def test_fcg_zero_network_falls_back_to_jacobi():
             fe.fe_lpc_destroy(lpc)
 
 
+def test_fcg_chebyshev_fallback_hands_over():
+    """With the Chebyshev fallback a zero network (z.r = 0 at once) hands x = 0 over to
+    Chebyshev-PCG on the residual equation, which is then exactly fe_pcg_chebyshev on b: the
+    same iterations and the same solution."""
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 2) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        xc = torch.empty_like(b)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 16, 1)
+        try:
+            fe.fe_lpc_weights(lpc, np.zeros(fe.fe_lpc_nparams(lpc), dtype=np.float32))
+            fe.fe_lpc_set_fallback(lpc, fe.FE_PC_CHEBYSHEV)
+            st, s = fe.fe_fcg(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-10, 2000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert s["outer_iters"] == 2 and s["true_rel_resid"] <= 1e-9
+            st, sc = fe.fe_pcg_chebyshev(pa, fe.FE_DIFFUSION, b, xc, 1e-10, 2000)
+            assert st == fe.FE_OK
+            assert s["iters"] == sc["iters"]
+            assert float((x - xc).abs().max()) <= 1e-13 * float(xc.abs().max())
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_lpc_set_fallback(lpc, 7)
+            assert e.value.status == fe.FE_ERR_ARG
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_fcg_chebyshev_fallback_after_a_stall():
+    """An untrained network of width 64 on a log-normal coefficient: whether or not FCG gives it
+    up (stall or breakdown rule), the solve with the Chebyshev hand-over reaches the tolerance on
+    the true residual."""
+    torch = torch_cuda()
+    with gpu_problem(6, 6, 6, 3, sigma=2.0) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 64, 3)
+        try:
+            fe.fe_lpc_set_fallback(lpc, fe.FE_PC_CHEBYSHEV)
+            st, s = fe.fe_fcg(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-9, 5000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert s["true_rel_resid"] <= 2e-9
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
 def test_lpc_argument_errors():
     torch = torch_cuda()
     with gpu_problem(2, 2, 2, 5) as (fe, mesh, pa, V, c):
