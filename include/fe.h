@@ -403,6 +403,22 @@ int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, v
 int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
                     void* stream);
 
+/* dev_diag (FP64 [ntrue]) = diag(E^T blockdiag(diag A_e) E): every element's own diagonal (the
+ * fe_assemble_diagonal of its order) summed with the squared weights of E.  It is the diagonal
+ * of E^T A E on every true dof that no element reaches through more than one of its nodes (all
+ * but the dofs of the lower-order faces and edges that constrain a higher-order neighbour) and a
+ * positive approximation of it on those.  Uses the library-owned E-vector.  Asynchronous. */
+int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stream);
+
+/* Jacobi-PCG on the variable-order space with fe_vspace_diagonal as the Jacobi diagonal: the
+ * conventions of fe_pcg (x = 0 start, homogeneous essential conditions on the boundary mask,
+ * FP64 vectors, fixed-order reductions, stop at ||r|| <= rtol ||(1-m) b||; stats as fe_pcg's,
+ * with the true residual from the handle's variant).  Allocates 5 vectors on the first call (kept
+ * with the handle).  FE_ERR_NOT_CONVERGED / FE_ERR_BREAKDOWN / FE_ERR_NAN as fe_pcg.
+ * Synchronous. */
+int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
+                  int maxit, fe_pcg_stats* stats, void* stream);
+
 void fe_vspace_destroy(fe_vspace* vs);
 
 void fe_pa_destroy(fe_pa* pa);

@@ -269,12 +269,21 @@ class VarSpace:
             v[s:s + n] = K @ u[s:s + n]
         return E.T @ v
 
-    def assemble(self, vertices, kind, coeff=None):
-        """E^T blockdiag(A_e) E as a dense matrix (tiny meshes)."""
-        E = self.prolongation()
+    def jacobi_diagonal(self, vertices, kind, coeff=None, E=None):
+        """diag(E^T blockdiag(diag A_e) E) = sum_e sum_a E[a, i]^2 A_e[a, a]: the Jacobi diagonal
+        of the variable-order operator (exact wherever no element reaches a dof through two of its
+        nodes)."""
+        E = self.prolongation() if E is None else E
+        dloc = np.concatenate([np.diag(K) for K in self.element_matrices(vertices, kind, coeff)])
+        return E.multiply(E).T @ dloc
+
+    def assemble(self, vertices, kind, coeff=None, sparse=False, E=None):
+        """E^T blockdiag(A_e) E: dense (tiny meshes), or a scipy CSR matrix with sparse=True."""
+        E = self.prolongation() if E is None else E
         blocks = self.element_matrices(vertices, kind, coeff)
         A = sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")
-        return (E.T @ A @ E).toarray()
+        K = (E.T @ A @ E).tocsr()
+        return K if sparse else K.toarray()
 
 
 def _combine(weights, rows):

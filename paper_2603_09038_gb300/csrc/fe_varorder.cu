@@ -17,9 +17,16 @@
 #include <thread>
 #include <vector>
 
+#include <chrono>
+
+#include "fe_f2.h"
 #include "fe_internal.h"
 
 using namespace fe;
+
+namespace {
+#include "fe_solver_common.cuh"
+}  // namespace
 
 namespace {
 
@@ -272,6 +279,134 @@ __global__ void k_csr_gather(const int64_t* __restrict__ ptr, const int32_t* __r
   }
 }
 
+// y_i = sum_t val_t^2 x[col_t]: the diagonal of E^T diag(v) E from the E-vector v
+__global__ void k_csr_gather_sq(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, int64_t nrows,
+                                const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t t = ptr[r]; t < ptr[r + 1]; ++t) s = fma(val[t] * val[t], x[col[t]], s);
+    y[r] = s;
+  }
+}
+
+// ---- Jacobi-PCG on the variable-order space (same conventions as fe_pcg: x = 0 start,
+// homogeneous essential conditions on the boundary mask, FP64 vectors, fixed-order reductions)
+
+// dinv = 1/d on the free dofs, 0 on the boundary; flags[0] = 1 on a non-positive entry
+__global__ void k_vs_dinv(const double* __restrict__ d, const uint8_t* __restrict__ mask,
+                          double* __restrict__ dinv, int64_t n, int* flags) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (mask[i]) {
+      dinv[i] = 0.0;
+    } else {
+      const double v = d[i];
+      if (!(v > 0.0)) flags[0] = 1;
+      dinv[i] = v > 0.0 ? 1.0 / v : 0.0;
+    }
+  }
+}
+
+// x = 0, r = (1-m) b, z = dinv r, p = z; partials r.z and b.b (free dofs)
+__global__ void __launch_bounds__(kReduceThreads) k_vs_init(
+    const double* __restrict__ b, const uint8_t* __restrict__ mask,
+    const double* __restrict__ dinv, double* __restrict__ x, double* __restrict__ r,
+    double* __restrict__ z, double* __restrict__ p, int64_t n, double* part0, double* part1) {
+  double rz = 0.0, bb = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = mask[i] ? 0.0 : b[i];
+    const double zi = dinv[i] * bi;
+    x[i] = 0.0;
+    r[i] = bi;
+    z[i] = zi;
+    p[i] = zi;
+    rz = fma(bi, zi, rz);
+    bb = fma(bi, bi, bb);
+  }
+  block_sum2(rz, bb, part0, part1);
+}
+
+// partials of p.q over the free dofs (p is 0 on the boundary, so this is p.(1-m)Ap)
+__global__ void __launch_bounds__(kReduceThreads) k_vs_pq(const double* __restrict__ p,
+                                                          const double* __restrict__ q,
+                                                          const uint8_t* __restrict__ mask,
+                                                          int64_t n, double* part0) {
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!mask[i]) a = fma(p[i], q[i], a);
+  block_sum2(a, 0.0, part0, nullptr);
+}
+
+// x += alpha p, r -= alpha (1-m) q, z = dinv r; partials r.z and r.r
+__global__ void __launch_bounds__(kReduceThreads) k_vs_update(
+    double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+    const double* __restrict__ p, const double* __restrict__ q, const uint8_t* __restrict__ mask,
+    const double* __restrict__ dinv, int64_t n, const double* __restrict__ sc, double* part0,
+    double* part1) {
+  const double alpha = sc[S_ALPHA];
+  double rz = 0.0, rr = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = mask[i] ? r[i] : fma(-alpha, q[i], r[i]);
+    const double zi = dinv[i] * ri;
+    r[i] = ri;
+    z[i] = zi;
+    rz = fma(ri, zi, rz);
+    rr = fma(ri, ri, rr);
+  }
+  block_sum2(rz, rr, part0, part1);
+}
+
+__global__ void k_vs_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                       const double* __restrict__ sc) {
+  const double beta = sc[S_BETA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+// partials of ||(1-m)(b - q)||^2
+__global__ void __launch_bounds__(kReduceThreads) k_vs_resid(const double* __restrict__ b,
+                                                             const double* __restrict__ q,
+                                                             const uint8_t* __restrict__ mask,
+                                                             int64_t n, double* part0) {
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = mask[i] ? 0.0 : b[i] - q[i];
+    a = fma(ri, ri, a);
+  }
+  block_sum2(a, 0.0, part0, nullptr);
+}
+
+// mode 0: rz, bb; 1: pq, alpha = rz / pq; 2: beta = rz' / rz, rz = rz', rr; 3: true residual
+__global__ void __launch_bounds__(kFinishThreads) k_vs_finish(const double* part0,
+                                                              const double* part1, double* sc,
+                                                              int mode) {
+  const double a = ordered_sum(part0);
+  const double b = (mode == 0 || mode == 2) ? ordered_sum(part1) : 0.0;
+  if (threadIdx.x != 0) return;
+  if (mode == 0) {
+    sc[S_RZ] = a;
+    sc[S_BB] = b;
+    sc[S_RR] = b;
+  } else if (mode == 1) {
+    sc[S_PQ] = a;
+    sc[S_ALPHA] = sc[S_RZ] / a;
+  } else if (mode == 2) {
+    sc[S_BETA] = a / sc[S_RZ];
+    sc[S_RZ] = a;
+    sc[S_RR] = b;
+  } else {
+    sc[S_TRUE] = a;
+  }
+}
+
 __global__ void k_identity_map(int32_t* __restrict__ map, int64_t n) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)
@@ -298,6 +433,9 @@ struct fe_vspace {
   uint8_t* d_mask = nullptr;            // [ntrue]
   double* d_u = nullptr;                // E-vectors [nlocal]
   double* d_v = nullptr;
+  double* d_work = nullptr;             // PCG: x-free work vectors r, z, p, q, dinv [5][ntrue]
+  double* d_red = nullptr;              //      2 kReduceBlocks partials + kScalars
+  int* d_flags = nullptr;
   int ngroups = 0;
   int group_p[kMaxOrder];
   int64_t group_off[kMaxOrder];         // first E-vector row of the group
@@ -325,6 +463,9 @@ void vspace_free(fe_vspace* vs) {
   cudaFree(vs->d_mask);
   cudaFree(vs->d_u);
   cudaFree(vs->d_v);
+  cudaFree(vs->d_work);
+  cudaFree(vs->d_red);
+  cudaFree(vs->d_flags);
   delete vs;
 }
 
@@ -607,6 +748,127 @@ int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* de
   k_csr_gather<<<grid_of(vs->ntrue), 256, 0, s>>>(vs->d_tptr, vs->d_tcol, vs->d_tval, vs->ntrue,
                                                   vs->d_v, dev_y);
   return cuda_error(cudaGetLastError(), "fe_vspace_apply: scatter launch");
+}
+
+int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stream) {
+  clear_error();
+  if (!vs || !dev_diag) return set_error(FE_ERR_ARG, "fe_vspace_diagonal: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS)
+    return set_error(FE_ERR_ARG, "fe_vspace_diagonal: bad op");
+  if (!(vs->ops & op))
+    return set_error(FE_ERR_ARG, "fe_vspace_diagonal: operator not set up in fe_vspace_setup");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int g = 0; g < vs->ngroups; ++g) {
+    const int st = fe_assemble_diagonal(vs->group_pa[g], op, vs->d_u + vs->group_off[g], stream);
+    if (st != FE_OK) return st;
+  }
+  k_csr_gather_sq<<<grid_of(vs->ntrue), 256, 0, s>>>(vs->d_tptr, vs->d_tcol, vs->d_tval,
+                                                     vs->ntrue, vs->d_u, dev_diag);
+  return cuda_error(cudaGetLastError(), "fe_vspace_diagonal: launch");
+}
+
+int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
+                  int maxit, fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  if (!vs || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_vspace_pcg: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_pcg: bad op");
+  if (!(vs->ops & op)) return set_error(FE_ERR_ARG, "fe_vspace_pcg: operator not set up");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_vspace_pcg: bad rtol or maxit");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = vs->ntrue;
+  cudaError_t err = cudaSuccess;
+  if (!vs->d_work) {
+    if ((err = cudaMalloc(&vs->d_work, sizeof(double) * 5 * n)) != cudaSuccess ||
+        (err = cudaMalloc(&vs->d_red, sizeof(double) * (2 * kReduceBlocks + kScalars))) !=
+            cudaSuccess ||
+        (err = cudaMalloc(&vs->d_flags, sizeof(int) * 4)) != cudaSuccess) {
+      cudaFree(vs->d_work);
+      cudaFree(vs->d_red);
+      vs->d_work = nullptr;
+      vs->d_red = nullptr;
+      return cuda_error(err, "fe_vspace_pcg: workspace cudaMalloc");
+    }
+  }
+  double *r = vs->d_work, *z = r + n, *p = z + n, *q = p + n, *dinv = q + n;
+  double *part0 = vs->d_red, *part1 = part0 + kReduceBlocks, *sc = part1 + kReduceBlocks;
+  int launches = 0;
+  // Jacobi: the diagonal of E^T diag(A_E) E (q as scratch), inverted on the free dofs
+  int st = fe_vspace_diagonal(vs, op, q, stream);
+  if (st != FE_OK) return st;
+  cudaMemsetAsync(vs->d_flags, 0, sizeof(int) * 4, s);
+  k_vs_dinv<<<grid_of(n), 256, 0, s>>>(q, vs->d_mask, dinv, n, vs->d_flags);
+  k_vs_init<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, vs->d_mask, dinv, dev_x, r, z, p, n,
+                                                     part0, part1);
+  k_vs_finish<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, 0);
+  launches += 2 * vs->ngroups + 4;
+  double hsc[kScalars];
+  int hflag = 0;
+  auto read_sc = [&]() -> int {
+    cudaError_t e;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(hsc, sc, sizeof(hsc), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_error(e, "fe_vspace_pcg: iteration");
+    return FE_OK;
+  };
+  if ((st = read_sc()) != FE_OK) return st;
+  if ((err = cudaMemcpy(&hflag, vs->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_error(err, "fe_vspace_pcg: diagonal check");
+  if (hflag) return set_error(FE_ERR_BREAKDOWN, "fe_vspace_pcg: non-positive diagonal entry");
+  const double bb = hsc[S_BB];
+  int status = FE_ERR_NOT_CONVERGED, iters = 0;
+  double rel = bb > 0.0 ? 1.0 : 0.0;
+  if (!(bb > 0.0)) status = std::isfinite(bb) ? FE_OK : FE_ERR_NAN;
+  for (int it = 1; status == FE_ERR_NOT_CONVERGED && it <= maxit; ++it) {
+    if ((st = fe_vspace_apply(vs, op, p, q, stream)) != FE_OK) return st;
+    k_vs_pq<<<kReduceBlocks, kReduceThreads, 0, s>>>(p, q, vs->d_mask, n, part0);
+    k_vs_finish<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, 1);
+    k_vs_update<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, r, z, p, q, vs->d_mask, dinv, n, sc,
+                                                        part0, part1);
+    k_vs_finish<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, 2);
+    launches += vs->ngroups + 6;
+    if ((st = read_sc()) != FE_OK) return st;
+    iters = it;
+    rel = std::sqrt(hsc[S_RR] / bb);
+    if (!std::isfinite(rel) || !std::isfinite(hsc[S_PQ])) {
+      status = FE_ERR_NAN;
+    } else if (!(hsc[S_PQ] > 0.0)) {
+      status = FE_ERR_BREAKDOWN;
+    } else if (rel <= rtol) {
+      status = FE_OK;
+    } else {
+      k_vs_p<<<grid_of(n), 256, 0, s>>>(p, z, n, sc);
+      ++launches;
+    }
+  }
+  // true residual ||(1-m)(b - A x)|| / ||(1-m) b||
+  double true_rel = 0.0;
+  if ((st = fe_vspace_apply(vs, op, dev_x, q, stream)) != FE_OK) return st;
+  k_vs_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, vs->d_mask, n, part0);
+  k_vs_finish<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, 3);
+  launches += vs->ngroups + 4;
+  if ((st = read_sc()) != FE_OK) return st;
+  if (bb > 0.0) true_rel = std::sqrt(hsc[S_TRUE] / bb);
+  if (stats) {
+    stats->iters = iters;
+    stats->rel_resid = rel;
+    stats->true_rel_resid = true_rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = launches;
+    stats->outer_iters = 1;
+  }
+  switch (status) {
+    case FE_OK:
+      return FE_OK;
+    case FE_ERR_BREAKDOWN:
+      return set_error(FE_ERR_BREAKDOWN, "fe_vspace_pcg: p.Ap <= 0");
+    case FE_ERR_NAN:
+      return set_error(FE_ERR_NAN, "fe_vspace_pcg: NaN or Inf in the iteration");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, "fe_vspace_pcg: maxit reached before rtol");
+  }
 }
 
 void fe_vspace_destroy(fe_vspace* vs) {

@@ -114,6 +114,9 @@ _SIGS = {
     "fe_vspace_set_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "fe_vspace_prolong": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_vspace_apply": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "fe_vspace_diagonal": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
+    "fe_vspace_pcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_vspace_destroy": (None, [_VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
@@ -480,6 +483,20 @@ def fe_vspace_prolong(vs, dev_x, dev_e, stream=None):
 
 def fe_vspace_apply(vs, op, dev_x, dev_y, stream=None):
     _check(load().fe_vspace_apply(_VP(vs), int(op), _ptr(dev_x), _ptr(dev_y), _stream(stream)))
+
+
+def fe_vspace_diagonal(vs, op, dev_diag, stream=None):
+    _check(load().fe_vspace_diagonal(_VP(vs), int(op), _ptr(dev_diag), _stream(stream)))
+
+
+def fe_vspace_pcg(vs, op, dev_b, dev_x, rtol, maxit, stream=None):
+    """Jacobi-PCG on the variable-order space; returns (status, stats dict) like fe_pcg."""
+    st = fe_pcg_stats()
+    status = load().fe_vspace_pcg(_VP(vs), int(op), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                                  int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
 
 
 def fe_vspace_destroy(vs):

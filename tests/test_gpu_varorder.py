@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from oracle.element import DIFFUSION, MASS
+from oracle.solve import pcg as oracle_pcg
 from oracle.varorder import VarSpace
 from paper_2603_09038_gb300.inputs import (block_orders, lognormal_coefficient, perturbed_vertices,
                                            uniform_vector)
@@ -112,6 +113,60 @@ def test_apply_matches_oracle(name):
         fe.fe_vspace_destroy(vs)
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_diagonal_matches_oracle(name):
+    """fe_vspace_diagonal against diag(E^T blockdiag(diag A_e) E), from FP64 and float-pair data."""
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        d = torch.empty(S.ntrue, dtype=torch.float64, device="cuda")
+        for variant in ("f64", "f32x2"):
+            fe.fe_vspace_set_variant(vs, variant)
+            for kind, op in ((DIFFUSION, fe.FE_DIFFUSION), (MASS, fe.FE_MASS)):
+                fe.fe_vspace_diagonal(vs, op, d)
+                ref = S.jacobi_diagonal(V, kind, coeff=c, E=E)
+                assert rel_err(d.cpu().numpy(), ref) <= TOL, (kind, variant)
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+@pytest.mark.parametrize("name", ["blocks_2_4_6", "ragged_1to5_sigma1"])
+def test_pcg_matches_oracle(name):
+    """Jacobi-PCG on the variable-order space against the oracle's PCG on the same constrained
+    system (x = 0 start, homogeneous essential conditions, the same Jacobi diagonal): the same
+    iteration count (+-1), iterates that agree to the tolerance, and the true residual."""
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    K = S.assemble(V, DIFFUSION, coeff=c, sparse=True, E=E)
+    m = S.boundary_mask().astype(bool)
+    free = (~m).astype(np.float64)
+    d = S.jacobi_diagonal(V, DIFFUSION, coeff=c, E=E)
+    b = uniform_vector(S.ntrue, seed=31)
+    rtol = 1e-10
+    xo, it_o, _ = oracle_pcg(lambda v: free * (K @ (free * v)) + m * v, free * b,
+                             np.where(m, 1.0, d), rtol=rtol, maxit=5000)
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        for variant in ("f64", "f32x2"):
+            fe.fe_vspace_set_variant(vs, variant)
+            db = torch.from_numpy(b).cuda()
+            dx = torch.empty_like(db)
+            st, stats = fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, db, dx, rtol, 5000)
+            assert st == fe.FE_OK, fe.fe_last_error()
+            assert abs(stats["iters"] - it_o) <= 1, (stats["iters"], it_o)
+            assert stats["true_rel_resid"] <= 2 * rtol
+            x = dx.cpu().numpy()
+            assert np.abs(x - xo).max() <= 1e-7 * np.abs(xo).max()
+            assert np.all(x[m] == 0.0)
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
 def test_argument_errors():
     fe = lib()
     torch_cuda()
@@ -129,6 +184,11 @@ def test_argument_errors():
         with pytest.raises(fe.FEError) as ei:
             fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, torch.empty_like(x))
         assert ei.value.status == fe.FE_ERR_ARG
+        with pytest.raises(fe.FEError) as ei:
+            fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, x, torch.empty_like(x), 1e-8, 10)
+        assert ei.value.status == fe.FE_ERR_ARG
+        st, stats = fe.fe_vspace_pcg(vs, fe.FE_MASS, x, torch.empty_like(x), 1e-8, 10)
+        assert st == fe.FE_OK and stats["iters"] == 0        # b = 0: x = 0 at once
     finally:
         fe.fe_vspace_destroy(vs)
 

@@ -192,3 +192,35 @@ def test_block_orders_layout():
             for bx in range(2):
                 blk = o[bz * 8:(bz + 1) * 8, by * 8:(by + 1) * 8, bx * 8:(bx + 1) * 8]
                 assert np.unique(blk).size == 1
+
+
+def test_jacobi_diagonal_single_order_and_unconstrained_dofs():
+    """One order: the structured operator's diagonal (permuted).  Mixed orders: the exact
+    diagonal of the assembled E^T A E on every dof that each element reaches through at most one
+    of its nodes, positive everywhere."""
+    n, p = 2, 3
+    V = perturbed_vertices(n, n, n, seed=7)
+    S = VarSpace(n, n, n, [p] * n ** 3)
+    I = np.rint(S.true_lattice_coords() * p).astype(np.int64)
+    N = n * p + 1
+    perm = I[:, 0] + N * (I[:, 1] + N * I[:, 2])
+    prob = op.Problem(n, n, n, p, V)
+    for kind in (DIFFUSION, MASS):
+        np.testing.assert_allclose(S.jacobi_diagonal(V, kind), op.diagonal(prob, kind)[perm],
+                                   rtol=1e-13, atol=0)
+    nx, ny, nz = 3, 2, 2
+    S = VarSpace(nx, ny, nz, block_orders(nx, ny, nz, block=1, orders=(1, 2, 4), seed=8))
+    V = perturbed_vertices(nx, ny, nz, seed=3)
+    E = S.prolongation().tocsc()
+    single = np.ones(S.ntrue, dtype=bool)
+    for i in range(S.ntrue):
+        rows = E.indices[E.indptr[i]:E.indptr[i + 1]]
+        elems = np.searchsorted(S.local_first, rows, side="right") - 1
+        if np.unique(elems).size < elems.size:
+            single[i] = False
+    assert single.sum() > 0 and (~single).sum() > 0
+    for kind in (DIFFUSION, MASS):
+        d = S.jacobi_diagonal(V, kind)
+        A = S.assemble(V, kind)
+        assert np.all(d > 0)
+        np.testing.assert_allclose(d[single], np.diag(A)[single], rtol=1e-12, atol=0)
