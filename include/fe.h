@@ -369,16 +369,19 @@ void fe_lpc_destroy(fe_lpc* lpc);
  *    node's GLL_p position.
  * The E-vector holds the elements grouped by ascending order, elements ascending within a group,
  * D^3 nodes per element (a = i + D*(j + D*k)); fe_vspace_layout gives every element's offset.
- * The action is y = E^T blockdiag(A_e) E x: a CSR gather, the fused apply kernel of each order
- * (one launch per order present, each order's quadrature data at p+2 Gauss points), and a CSR
- * scatter.  Vectors are FP64 of length ntrue. */
+ * The action is y = E^T blockdiag(A_e) E x: rows of E that are a single weight 1 live in the
+ * element map of the fused apply kernel of each order (one launch per order present, each
+ * order's quadrature data at p+2 Gauss points); the other rows C (nodes constrained by a
+ * lower-order neighbour) are applied as [x; C x] before and folded back by C^T after.  Vectors
+ * are FP64 of length ntrue. */
 typedef struct fe_vspace fe_vspace;
 
 /* host_order: int32 [nx*ny*nz] orders 1..8; host_vertices as for fe_mesh_setup; host_coeff:
  * FP64 [ne] piecewise-constant coefficient or NULL for 1; ops: FE_DIFFUSION | FE_MASS.  Builds
- * the numbering and E on the host, uploads E and E^T (CSR: int64 row offsets, int32 columns,
- * FP64 weights), and the per-order partial assembly.  FE_ERR_ARG on a bad order, size or an
- * inverted element; FE_ERR_UNSUPPORTED past 2^31-1 true or local dofs.  Synchronous. */
+ * the numbering and E on the host, uploads the element map (int32 per E-vector row), C and C^T
+ * (CSR: int64 offsets, int32 columns, FP64 weights), two work vectors of ntrue + (rows of C)
+ * values, and the per-order partial assembly.  FE_ERR_ARG on a bad order, size or an inverted
+ * element; FE_ERR_UNSUPPORTED past 2^31-1 true, local or constrained values.  Synchronous. */
 int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
                     const double* host_vertices, const double* host_coeff, int ops, void* stream,
                     fe_vspace** out);
@@ -398,8 +401,8 @@ int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream);
 /* dev_e (FP64 [nlocal]) = E dev_x: the element values of a true-dof vector.  Asynchronous. */
 int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream);
 
-/* dev_y = E^T blockdiag(A_e) E dev_x for op (no boundary conditions); uses two library-owned
- * E-vectors, so calls on one handle must not overlap.  Asynchronous. */
+/* dev_y = E^T blockdiag(A_e) E dev_x for op (no boundary conditions); uses the handle's two
+ * work vectors, so calls on one handle must not overlap.  Asynchronous. */
 int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
                     void* stream);
 
@@ -407,7 +410,7 @@ int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* de
  * fe_assemble_diagonal of its order) summed with the squared weights of E.  It is the diagonal
  * of E^T A E on every true dof that no element reaches through more than one of its nodes (all
  * but the dofs of the lower-order faces and edges that constrain a higher-order neighbour) and a
- * positive approximation of it on those.  Uses the library-owned E-vector.  Asynchronous. */
+ * positive approximation of it on those.  Uses the handle's work vectors.  Asynchronous. */
 int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stream);
 
 /* Jacobi-PCG on the variable-order space with fe_vspace_diagonal as the Jacobi diagonal: the

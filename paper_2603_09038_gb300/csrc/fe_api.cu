@@ -713,8 +713,16 @@ int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_assemble_diagonal: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_assemble_diagonal: operator not set up");
   cudaStream_t s = (cudaStream_t)stream;
+  FE_CHECK_CUDA(cudaMemsetAsync(dev_diag, 0, sizeof(double) * pa->mesh->ndofs, s), "zero diag");
+  return fe::diagonal_accumulate(pa, op, dev_diag, s);
+}
+
+}  // extern "C"
+
+namespace fe {
+
+int diagonal_accumulate(const fe_pa* pa, int op, double* dev_diag, cudaStream_t s) {
   const fe_mesh* m = pa->mesh;
-  FE_CHECK_CUDA(cudaMemsetAsync(dev_diag, 0, sizeof(double) * m->ndofs, s), "zero diag");
   const double* qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
   k_diagonal<<<elem_grid(m->ne), kEltThreads, 0, s>>>(m->d_map, qd, m->ne, pa->D, pa->Q,
                                                       op == FE_DIFFUSION ? 1 : 0,
@@ -722,6 +730,10 @@ int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream
                                                       make_tables(pa->basis), dev_diag);
   return cuda_error(cudaGetLastError(), "diagonal kernel launch");
 }
+
+}  // namespace fe
+
+extern "C" {
 
 int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream) {
   clear_error();

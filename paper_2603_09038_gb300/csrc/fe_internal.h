@@ -101,6 +101,9 @@ int launch_apply_f32(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32_vec32(int op, const ApplyArgs& a, cudaStream_t s);
 int make_qd_f32(const double* src, float* dst, int64_t n, bool pairs, cudaStream_t s);
 
+// diag += the element diagonals of op scattered through the element map (no zeroing; atomic).
+int diagonal_accumulate(const fe_pa* pa, int op, double* diag, cudaStream_t s);
+
 // Re-encodes n FP64 values in place as float pairs (hi, lo) or back.
 int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);
 

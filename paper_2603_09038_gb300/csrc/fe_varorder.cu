@@ -3,12 +3,15 @@
 // Eq. (1) reads A = P^T G^T B^T D B G P; with one order P is the identity on one GPU, with
 // several it is the constraint operator (Fig. 1's caption).  The space and its numbering are
 // documented with fe_vspace_setup in fe.h.  Here E = G P is built on the host once, row by row,
-// by evaluating the entity functions at every element node, and kept on the device in CSR form
-// together with its transpose, so that an apply is
-//   u = E x (CSR gather, one thread per E-vector row),
-//   v_g = A_g u_g for every order g present (the fused PA kernel of that order; the group's
-//         element map is the identity into its slice of the E-vector),
-//   y = E^T v (CSR of the transpose, one thread per true dof, fixed order: deterministic).
+// by evaluating the entity functions at every element node.  Most rows are a single weight 1 (a
+// node that is itself a true dof); they become entries of an ordinary element map.  The other
+// rows ("constrained": nodes on faces and edges shared with a lower order) form a sparse matrix
+// C, and the map sends their nodes to ntrue + c.  An apply is then
+//   X = [x; C x] (a copy and a CSR pass over the constrained rows only),
+//   Y = sum_g A_g X for every order g present (the fused PA kernel of that order, gathering X and
+//       scatter-adding into Y through the group's map; Y zeroed once),
+//   y = Y[0, ntrue) + C^T Y[ntrue, ...) (a copy and the transpose over the true dofs C touches,
+//       one thread per such dof, fixed order).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -267,6 +270,114 @@ void parallel_for(int64_t n, F f) {
   for (auto& x : th) x.join();
 }
 
+// E in the split form the device uses: the element map (E-vector row -> true dof, or ntrue + c
+// for the c-th row that is not a single weight 1), the rows C of those, and C^T over the true
+// dofs it touches.  False if ntrue + nc passes 2^31 - 1.
+struct HostE {
+  int64_t nnz = 0, nc = 0;
+  std::vector<int32_t> map;
+  std::vector<int64_t> cptr;
+  std::vector<int32_t> ccol;
+  std::vector<double> cval;
+  std::vector<int32_t> trow;
+  std::vector<int64_t> tptr;
+  std::vector<int32_t> tcol;
+  std::vector<double> tval;
+};
+
+bool build_host_E(const Topo& T, const std::vector<int64_t>& order_elems,
+                  const std::vector<int64_t>& first, int64_t nlocal, HostE& H) {
+  // Rows of E: a single weight 1 goes into the element map; the others become rows of C.
+  std::vector<int64_t> map(nlocal);
+  std::vector<uint8_t> rown(nlocal);
+  auto classify = [&](int64_t b, int64_t e_end) {
+    Row r;
+    for (int64_t t = b; t < e_end; ++t) {
+      const int64_t e = order_elems[t];
+      const int D = T.ord[e] + 1;
+      for (int a = 0; a < D * D * D; ++a) {
+        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+        const int64_t row = first[e] + a;
+        rown[row] = (uint8_t)r.n;
+        map[row] = (r.n == 1 && r.w[0] == 1.0) ? r.col[0] : -1;
+      }
+    }
+  };
+  parallel_for((int64_t)order_elems.size(), classify);
+  int64_t nnz = 0, nc = 0;
+  std::vector<int64_t> cptr(1, 0);
+  for (int64_t row = 0; row < nlocal; ++row) {
+    nnz += rown[row];
+    if (map[row] < 0) {
+      map[row] = T.ntrue + nc++;
+      cptr.push_back(cptr.back() + rown[row]);
+    }
+  }
+  if (T.ntrue + nc > 2147483647LL) return false;
+  const int64_t cnnz = cptr.back();
+  std::vector<int32_t> ccol(cnnz);
+  std::vector<double> cval(cnnz);
+  auto fill = [&](int64_t b, int64_t e_end) {
+    Row r;
+    for (int64_t t = b; t < e_end; ++t) {
+      const int64_t e = order_elems[t];
+      const int D = T.ord[e] + 1;
+      for (int a = 0; a < D * D * D; ++a) {
+        const int64_t row = first[e] + a;
+        if (map[row] < T.ntrue) continue;
+        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+        // columns ascending within a row (a fixed summation order): insertion sort
+        for (int z = 1; z < r.n; ++z)
+          for (int y = z; y > 0 && r.col[y - 1] > r.col[y]; --y) {
+            std::swap(r.col[y - 1], r.col[y]);
+            std::swap(r.w[y - 1], r.w[y]);
+          }
+        const int64_t o = cptr[map[row] - T.ntrue];
+        for (int z = 0; z < r.n; ++z) {
+          ccol[o + z] = (int32_t)r.col[z];
+          cval[o + z] = r.w[z];
+        }
+      }
+    }
+  };
+  parallel_for((int64_t)order_elems.size(), fill);
+  std::vector<int32_t> map32(map.begin(), map.end());
+  std::vector<int64_t>().swap(map);
+
+  // C^T over the true dofs it touches (ascending), constrained rows ascending within each
+  std::vector<int32_t> tcount(T.ntrue, 0);
+  for (int64_t t = 0; t < cnnz; ++t) ++tcount[ccol[t]];
+  std::vector<int32_t> trow;
+  std::vector<int64_t> tptr(1, 0);
+  std::vector<int64_t> tpos(T.ntrue, -1);
+  for (int64_t i = 0; i < T.ntrue; ++i)
+    if (tcount[i] > 0) {
+      tpos[i] = tptr.back();
+      trow.push_back((int32_t)i);
+      tptr.push_back(tptr.back() + tcount[i]);
+    }
+  std::vector<int32_t> tcol(cnnz);
+  std::vector<double> tval(cnnz);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int64_t t = cptr[c]; t < cptr[c + 1]; ++t) {
+      const int64_t o = tpos[ccol[t]]++;
+      tcol[o] = (int32_t)c;
+      tval[o] = cval[t];
+    }
+
+  H.nnz = nnz;
+  H.nc = nc;
+  H.map.swap(map32);
+  H.cptr.swap(cptr);
+  H.ccol.swap(ccol);
+  H.cval.swap(cval);
+  H.trow.swap(trow);
+  H.tptr.swap(tptr);
+  H.tcol.swap(tcol);
+  H.tval.swap(tval);
+  return true;
+}
+
 __global__ void k_csr_gather(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                              const double* __restrict__ val, int64_t nrows,
                              const double* __restrict__ x, double* __restrict__ y) {
@@ -275,18 +386,6 @@ __global__ void k_csr_gather(const int64_t* __restrict__ ptr, const int32_t* __r
     const int64_t b = ptr[r], e = ptr[r + 1];
     double s = 0.0;
     for (int64_t t = b; t < e; ++t) s = fma(val[t], x[col[t]], s);
-    y[r] = s;
-  }
-}
-
-// y_i = sum_t val_t^2 x[col_t]: the diagonal of E^T diag(v) E from the E-vector v
-__global__ void k_csr_gather_sq(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, int64_t nrows,
-                                const double* __restrict__ x, double* __restrict__ y) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int64_t t = ptr[r]; t < ptr[r + 1]; ++t) s = fma(val[t] * val[t], x[col[t]], s);
     y[r] = s;
   }
 }
@@ -407,10 +506,29 @@ __global__ void __launch_bounds__(kFinishThreads) k_vs_finish(const double* part
   }
 }
 
-__global__ void k_identity_map(int32_t* __restrict__ map, int64_t n) {
+// e[t] = X[map[t]]: the E-vector from X = [x; C x] through the element map
+__global__ void k_map_gather(const int32_t* __restrict__ map, int64_t n,
+                             const double* __restrict__ X, double* __restrict__ e) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x)
-    map[t] = (int32_t)t;
+    e[t] = X[map[t]];
+}
+
+// y[rows[r]] += sum_t w_t Yc[col_t] (w_t = val_t, or val_t^2 with `square`): the transpose of the
+// constrained rows over the true dofs they touch (distinct rows: no atomics, fixed order)
+__global__ void k_ct_scatter(const int32_t* __restrict__ rows, const int64_t* __restrict__ ptr,
+                             const int32_t* __restrict__ col, const double* __restrict__ val,
+                             int64_t nrows, const double* __restrict__ Yc, double* __restrict__ y,
+                             int square) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t t = ptr[r]; t < ptr[r + 1]; ++t) {
+      const double w = square ? val[t] * val[t] : val[t];
+      s = fma(w, Yc[col[t]], s);
+    }
+    y[rows[r]] += s;
+  }
 }
 
 unsigned grid_of(int64_t n) {
@@ -419,20 +537,28 @@ unsigned grid_of(int64_t n) {
 
 }  // namespace
 
+// Most rows of E are a single weight 1 (a node that is itself a true dof): those stay in the
+// element map, which points into X = [x; C x] with C the other ("constrained") rows of E, so the
+// per-order kernels gather and scatter the true-dof vector directly; only C and its transpose
+// need a sparse pass.
 struct fe_vspace {
   int nx = 0, ny = 0, nz = 0, ops = 0;
   int64_t ne = 0, ntrue = 0, nlocal = 0, nnz = 0;
+  int64_t nc = 0, nct = 0;              // constrained rows of E; true dofs they touch
   std::vector<int64_t> elem_first;      // [ne] E-vector offset per element
   double* d_vertices = nullptr;
-  int64_t* d_eptr = nullptr;            // E: [nlocal + 1]
-  int32_t* d_ecol = nullptr;            // [nnz] true dof
-  double* d_eval = nullptr;
-  int64_t* d_tptr = nullptr;            // E^T: [ntrue + 1]
-  int32_t* d_tcol = nullptr;            // [nnz] E-vector row
+  int32_t* d_map = nullptr;             // [nlocal] E-vector row -> index into X = [x; C x]
+  int64_t* d_cptr = nullptr;            // C: [nc + 1]
+  int32_t* d_ccol = nullptr;            //    true dof
+  double* d_cval = nullptr;
+  int32_t* d_trow = nullptr;            // C^T: [nct] true dof of each row
+  int64_t* d_tptr = nullptr;            //      [nct + 1]
+  int32_t* d_tcol = nullptr;            //      constrained row
   double* d_tval = nullptr;
   uint8_t* d_mask = nullptr;            // [ntrue]
-  double* d_u = nullptr;                // E-vectors [nlocal]
-  double* d_v = nullptr;
+  double* d_X = nullptr;                // [ntrue + nc]: x then C x
+  double* d_Y = nullptr;                // [ntrue + nc]: the per-order kernels' scatter target
+  int* d_zero = nullptr;                // a device 0: "y is zeroed by the caller" for the applies
   double* d_work = nullptr;             // PCG: x-free work vectors r, z, p, q, dinv [5][ntrue]
   double* d_red = nullptr;              //      2 kReduceBlocks partials + kScalars
   int* d_flags = nullptr;
@@ -450,19 +576,23 @@ void vspace_free(fe_vspace* vs) {
     fe_pa_destroy(vs->group_pa[g]);
     if (vs->group_mesh[g]) {
       vs->group_mesh[g]->d_vertices = nullptr;  // shared, freed below
+      vs->group_mesh[g]->d_map = nullptr;       // a slice of vs->d_map
       fe_mesh_destroy(vs->group_mesh[g]);
     }
   }
   cudaFree(vs->d_vertices);
-  cudaFree(vs->d_eptr);
-  cudaFree(vs->d_ecol);
-  cudaFree(vs->d_eval);
+  cudaFree(vs->d_map);
+  cudaFree(vs->d_cptr);
+  cudaFree(vs->d_ccol);
+  cudaFree(vs->d_cval);
+  cudaFree(vs->d_trow);
   cudaFree(vs->d_tptr);
   cudaFree(vs->d_tcol);
   cudaFree(vs->d_tval);
   cudaFree(vs->d_mask);
-  cudaFree(vs->d_u);
-  cudaFree(vs->d_v);
+  cudaFree(vs->d_X);
+  cudaFree(vs->d_Y);
+  cudaFree(vs->d_zero);
   cudaFree(vs->d_work);
   cudaFree(vs->d_red);
   cudaFree(vs->d_flags);
@@ -474,6 +604,28 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
   cudaError_t err = cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size()));
   if (err != cudaSuccess) return err;
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+// X = [x; C x] on s
+int fill_X(const fe_vspace* vs, const double* x, cudaStream_t s) {
+  cudaError_t err = cudaMemcpyAsync(vs->d_X, x, sizeof(double) * vs->ntrue,
+                                    cudaMemcpyDeviceToDevice, s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace: copy x");
+  if (vs->nc > 0)
+    k_csr_gather<<<grid_of(vs->nc), 256, 0, s>>>(vs->d_cptr, vs->d_ccol, vs->d_cval, vs->nc, x,
+                                                 vs->d_X + vs->ntrue);
+  return cuda_error(cudaGetLastError(), "fe_vspace: constrained rows");
+}
+
+// y = Y[0, ntrue) + C^T Y[ntrue, ntrue + nc) (squared weights with `square`) on s
+int fold_Y(const fe_vspace* vs, double* y, int square, cudaStream_t s) {
+  cudaError_t err = cudaMemcpyAsync(y, vs->d_Y, sizeof(double) * vs->ntrue,
+                                    cudaMemcpyDeviceToDevice, s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace: copy y");
+  if (vs->nct > 0)
+    k_ct_scatter<<<grid_of(vs->nct), 256, 0, s>>>(vs->d_trow, vs->d_tptr, vs->d_tcol, vs->d_tval,
+                                                  vs->nct, vs->d_Y + vs->ntrue, y, square);
+  return cuda_error(cudaGetLastError(), "fe_vspace: constrained transpose");
 }
 
 }  // namespace
@@ -514,62 +666,10 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   if (T.ntrue > 2147483647LL || nlocal > 2147483647LL)
     return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_setup: more than 2^31-1 true or local dofs");
 
-  // E by rows: count, offsets, fill (two passes over the elements on the host's cores)
-  std::vector<int64_t> rowcnt(nlocal + 1, 0);
-  auto count = [&](int64_t b, int64_t e_end) {
-    Row r;
-    for (int64_t t = b; t < e_end; ++t) {
-      const int64_t e = order_elems[t];
-      const int D = T.ord[e] + 1;
-      for (int a = 0; a < D * D * D; ++a) {
-        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
-        rowcnt[first[e] + a + 1] = r.n;
-      }
-    }
-  };
-  parallel_for((int64_t)order_elems.size(), count);
-  for (int64_t r = 0; r < nlocal; ++r) rowcnt[r + 1] += rowcnt[r];
-  const int64_t nnz = rowcnt[nlocal];
-  std::vector<int32_t> ecol(nnz);
-  std::vector<double> evalv(nnz);
-  auto fill = [&](int64_t b, int64_t e_end) {
-    Row r;
-    for (int64_t t = b; t < e_end; ++t) {
-      const int64_t e = order_elems[t];
-      const int D = T.ord[e] + 1;
-      for (int a = 0; a < D * D * D; ++a) {
-        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
-        // columns ascending within a row (a fixed summation order): insertion sort
-        for (int z = 1; z < r.n; ++z)
-          for (int y = z; y > 0 && r.col[y - 1] > r.col[y]; --y) {
-            std::swap(r.col[y - 1], r.col[y]);
-            std::swap(r.w[y - 1], r.w[y]);
-          }
-        const int64_t o = rowcnt[first[e] + a];
-        for (int z = 0; z < r.n; ++z) {
-          ecol[o + z] = (int32_t)r.col[z];
-          evalv[o + z] = r.w[z];
-        }
-      }
-    }
-  };
-  parallel_for((int64_t)order_elems.size(), fill);
-
-  // E^T by counting sort on the column (rows ascending within each column)
-  std::vector<int64_t> tptr(T.ntrue + 1, 0);
-  for (int64_t t = 0; t < nnz; ++t) ++tptr[ecol[t] + 1];
-  for (int64_t c = 0; c < T.ntrue; ++c) tptr[c + 1] += tptr[c];
-  std::vector<int32_t> tcol(nnz);
-  std::vector<double> tval(nnz);
-  {
-    std::vector<int64_t> pos(tptr.begin(), tptr.end() - 1);
-    for (int64_t r = 0; r < nlocal; ++r)
-      for (int64_t t = rowcnt[r]; t < rowcnt[r + 1]; ++t) {
-        const int64_t o = pos[ecol[t]]++;
-        tcol[o] = (int32_t)r;
-        tval[o] = evalv[t];
-      }
-  }
+  HostE H;
+  if (!build_host_E(T, order_elems, first, nlocal, H))
+    return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_setup: more than 2^31-1 constrained values");
+  const int64_t nnz = H.nnz, nc = H.nc;
 
   // boundary mask of the true dofs
   std::vector<uint8_t> mask(T.ntrue, 0);
@@ -608,26 +708,33 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   vs->ntrue = T.ntrue;
   vs->nlocal = nlocal;
   vs->nnz = nnz;
+  vs->nc = nc;
+  vs->nct = (int64_t)H.trow.size();
   vs->elem_first = first;
-  const int64_t nv = T.nv;
+  const int64_t nv = T.nv, nX = T.ntrue + nc;
   cudaError_t err = cudaMalloc(&vs->d_vertices, sizeof(double) * 3 * nv);
   if (err == cudaSuccess)
     err = cudaMemcpy(vs->d_vertices, host_vertices, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = upload(&vs->d_eptr, rowcnt);
-  if (err == cudaSuccess) err = upload(&vs->d_ecol, ecol);
-  if (err == cudaSuccess) err = upload(&vs->d_eval, evalv);
-  if (err == cudaSuccess) err = upload(&vs->d_tptr, tptr);
-  if (err == cudaSuccess) err = upload(&vs->d_tcol, tcol);
-  if (err == cudaSuccess) err = upload(&vs->d_tval, tval);
+  if (err == cudaSuccess) err = upload(&vs->d_map, H.map);
+  if (err == cudaSuccess) err = upload(&vs->d_cptr, H.cptr);
+  if (err == cudaSuccess) err = upload(&vs->d_ccol, H.ccol);
+  if (err == cudaSuccess) err = upload(&vs->d_cval, H.cval);
+  if (err == cudaSuccess) err = upload(&vs->d_trow, H.trow);
+  if (err == cudaSuccess) err = upload(&vs->d_tptr, H.tptr);
+  if (err == cudaSuccess) err = upload(&vs->d_tcol, H.tcol);
+  if (err == cudaSuccess) err = upload(&vs->d_tval, H.tval);
   if (err == cudaSuccess) err = upload(&vs->d_mask, mask);
-  if (err == cudaSuccess) err = cudaMalloc(&vs->d_u, sizeof(double) * std::max<int64_t>(1, nlocal));
-  if (err == cudaSuccess) err = cudaMalloc(&vs->d_v, sizeof(double) * std::max<int64_t>(1, nlocal));
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_X, sizeof(double) * std::max<int64_t>(1, nX));
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_Y, sizeof(double) * std::max<int64_t>(1, nX));
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_zero, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(vs->d_zero, 0, sizeof(int));
   if (err != cudaSuccess) {
     vspace_free(vs);
     return cuda_error(err, "fe_vspace_setup: upload");
   }
 
-  // one partial assembly per order present, over that order's elements
+  // one partial assembly per order present, over that order's elements; each group's element
+  // map is its slice of d_map, into X / Y of length ntrue + nc
   int64_t t0 = 0;
   for (int p = 1; p <= kMaxOrder; ++p) {
     if (!present[p]) continue;
@@ -651,15 +758,11 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
     m->p = p;
     m->D = p + 1;
     m->ne = (int64_t)ids.size();
-    m->ndofs = m->ne * m->D * m->D * m->D;
+    m->ndofs = nX;
     cudaGetDevice(&m->device);
     m->d_vertices = vs->d_vertices;
+    m->d_map = vs->d_map + vs->group_off[g];
     err = upload(&m->d_elem_ids, ids);
-    if (err == cudaSuccess) err = cudaMalloc(&m->d_map, sizeof(int32_t) * m->ndofs);
-    if (err == cudaSuccess) {
-      k_identity_map<<<grid_of(m->ndofs), 256, 0, s>>>(m->d_map, m->ndofs);
-      err = cudaGetLastError();
-    }
     double* dc = nullptr;
     if (err == cudaSuccess && host_coeff) err = upload(&dc, coeff);
     if (err != cudaSuccess) {
@@ -722,8 +825,10 @@ int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream) {
 int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream) {
   clear_error();
   if (!vs || !dev_x || !dev_e) return set_error(FE_ERR_ARG, "fe_vspace_prolong: null argument");
-  k_csr_gather<<<grid_of(vs->nlocal), 256, 0, (cudaStream_t)stream>>>(
-      vs->d_eptr, vs->d_ecol, vs->d_eval, vs->nlocal, dev_x, dev_e);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int st = fill_X(vs, dev_x, s);
+  if (st != FE_OK) return st;
+  k_map_gather<<<grid_of(vs->nlocal), 256, 0, s>>>(vs->d_map, vs->nlocal, vs->d_X, dev_e);
   return cuda_error(cudaGetLastError(), "fe_vspace_prolong: launch");
 }
 
@@ -735,19 +840,17 @@ int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* de
   if (!(vs->ops & op))
     return set_error(FE_ERR_ARG, "fe_vspace_apply: operator not set up in fe_vspace_setup");
   cudaStream_t s = (cudaStream_t)stream;
-  k_csr_gather<<<grid_of(vs->nlocal), 256, 0, s>>>(vs->d_eptr, vs->d_ecol, vs->d_eval,
-                                                   vs->nlocal, dev_x, vs->d_u);
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: gather launch");
+  int st = fill_X(vs, dev_x, s);
+  if (st != FE_OK) return st;
+  cudaError_t err =
+      cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * (vs->ntrue + vs->nc), s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: zero Y");
   for (int g = 0; g < vs->ngroups; ++g) {
     const fe_pa* pa = vs->group_pa[g];
-    const int st = apply_dispatch(pa, op, pa->variant, vs->d_u + vs->group_off[g],
-                                  vs->d_v + vs->group_off[g], s);
-    if (st != FE_OK) return st;
+    if ((st = apply_dispatch(pa, op, pa->variant, vs->d_X, vs->d_Y, s, vs->d_zero)) != FE_OK)
+      return st;
   }
-  k_csr_gather<<<grid_of(vs->ntrue), 256, 0, s>>>(vs->d_tptr, vs->d_tcol, vs->d_tval, vs->ntrue,
-                                                  vs->d_v, dev_y);
-  return cuda_error(cudaGetLastError(), "fe_vspace_apply: scatter launch");
+  return fold_Y(vs, dev_y, 0, s);
 }
 
 int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stream) {
@@ -758,13 +861,13 @@ int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stre
   if (!(vs->ops & op))
     return set_error(FE_ERR_ARG, "fe_vspace_diagonal: operator not set up in fe_vspace_setup");
   cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t err = cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * (vs->ntrue + vs->nc), s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_diagonal: zero Y");
   for (int g = 0; g < vs->ngroups; ++g) {
-    const int st = fe_assemble_diagonal(vs->group_pa[g], op, vs->d_u + vs->group_off[g], stream);
+    const int st = diagonal_accumulate(vs->group_pa[g], op, vs->d_Y, s);
     if (st != FE_OK) return st;
   }
-  k_csr_gather_sq<<<grid_of(vs->ntrue), 256, 0, s>>>(vs->d_tptr, vs->d_tcol, vs->d_tval,
-                                                     vs->ntrue, vs->d_u, dev_diag);
-  return cuda_error(cudaGetLastError(), "fe_vspace_diagonal: launch");
+  return fold_Y(vs, dev_diag, 1, s);
 }
 
 int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
