@@ -769,11 +769,15 @@ def run_mixed_orders(args, local_rank):
     x = torch.rand(ntrue, dtype=torch.float64, device=dev) * 2 - 1
     y = torch.empty_like(x)
     e = torch.empty(nlocal, dtype=torch.float64, device=dev)
+    nc, cnnz, nct = fe.fe_vspace_constraint_sizes(vs)
     counts = {p: int((orders == p).sum()) for p in (2, 4, 6)}
     qd = sum(c * (p + 2) ** 3 * 6 * 8 for p, c in counts.items())
-    dmap = sum(c * 4 * (p + 1) ** 3 for p, c in counts.items())
-    csr = 2 * (8 * nnz + 4 * nnz) + 8 * (nlocal + ntrue + 2)
-    design = csr + 2 * 8 * ntrue + 4 * 8 * nlocal + qd + dmap
+    dmap = 4 * nlocal
+    # this design: x copied into X and y out of Y (16 B each way per dof), C x and C^T (offsets,
+    # columns, weights, the constrained values), Y zeroed, X read and Y written once by the
+    # kernels (the minimum their gather and scatter-add can move), maps and quadrature data once
+    constraint = 2 * 12 * cnnz + 8 * (nc + 1) + 12 * (nct + 1) + 2 * 8 * nc + 16 * nct
+    design = 2 * 16 * ntrue + constraint + 8 * (ntrue + nc) + 2 * 8 * (ntrue + nc) + qd + dmap
     minimum = 2 * 8 * ntrue + qd
     peaks, src = measured_peaks()
 
@@ -799,6 +803,7 @@ def run_mixed_orders(args, local_rank):
         print(json.dumps({
             "mixed_orders": True, "workload": "diffusion_%dcubed_blocks8_orders246" % n,
             "variant": variant, "ntrue": ntrue, "nlocal": nlocal, "nnz_E": nnz,
+            "constrained_rows": nc, "nnz_C": cnnz,
             "elements_per_order": counts, "setup_s": setup_s, "apply_ms": ms,
             "gdofs_true": ntrue / ms / 1e6, "gdofs_local": nlocal / ms / 1e6,
             "gather_ms": ms_gather, "design_bytes": design, "min_bytes": minimum,

@@ -389,6 +389,11 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
 /* Sizes: true dofs, E-vector length (sum of D_e^3), nonzeros of E; any pointer may be NULL. */
 int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_t* nnz);
 
+/* Size of the constraint part: rows of E that are not a single weight 1 (nodes constrained by a
+ * lower-order neighbour), their nonzeros, and the true dofs they touch; any pointer may be NULL. */
+int fe_vspace_constraint_sizes(const fe_vspace* vs, int64_t* nrows, int64_t* nnz,
+                               int64_t* ntouched);
+
 /* host_first: int64 [ne], the E-vector offset of every element (in element index order). */
 int fe_vspace_layout(const fe_vspace* vs, int64_t* host_first);
 

@@ -544,7 +544,7 @@ unsigned grid_of(int64_t n) {
 struct fe_vspace {
   int nx = 0, ny = 0, nz = 0, ops = 0;
   int64_t ne = 0, ntrue = 0, nlocal = 0, nnz = 0;
-  int64_t nc = 0, nct = 0;              // constrained rows of E; true dofs they touch
+  int64_t nc = 0, cnnz = 0, nct = 0;    // constrained rows of E, their nonzeros, true dofs touched
   std::vector<int64_t> elem_first;      // [ne] E-vector offset per element
   double* d_vertices = nullptr;
   int32_t* d_map = nullptr;             // [nlocal] E-vector row -> index into X = [x; C x]
@@ -710,6 +710,7 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   vs->nnz = nnz;
   vs->nc = nc;
   vs->nct = (int64_t)H.trow.size();
+  vs->cnnz = H.cptr.back();
   vs->elem_first = first;
   const int64_t nv = T.nv, nX = T.ntrue + nc;
   cudaError_t err = cudaMalloc(&vs->d_vertices, sizeof(double) * 3 * nv);
@@ -793,6 +794,16 @@ int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_
   if (ntrue) *ntrue = vs->ntrue;
   if (nlocal) *nlocal = vs->nlocal;
   if (nnz) *nnz = vs->nnz;
+  return FE_OK;
+}
+
+int fe_vspace_constraint_sizes(const fe_vspace* vs, int64_t* nrows, int64_t* nnz,
+                               int64_t* ntouched) {
+  clear_error();
+  if (!vs) return set_error(FE_ERR_ARG, "fe_vspace_constraint_sizes: handle is NULL");
+  if (nrows) *nrows = vs->nc;
+  if (nnz) *nnz = vs->cnnz;
+  if (ntouched) *ntouched = vs->nct;
   return FE_OK;
 }
 

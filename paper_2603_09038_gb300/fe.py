@@ -110,6 +110,9 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]),
     "fe_vspace_layout": (ctypes.c_int, [_VP, _VP]),
+    "fe_vspace_constraint_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.POINTER(ctypes.c_int64)]),
     "fe_vspace_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_vspace_set_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "fe_vspace_prolong": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -459,6 +462,14 @@ def fe_vspace_sizes(vs):
     """(ntrue, nlocal, nnz)."""
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(load().fe_vspace_sizes(_VP(vs), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def fe_vspace_constraint_sizes(vs):
+    """(constrained rows of E, their nonzeros, true dofs they touch)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fe_vspace_constraint_sizes(_VP(vs), ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(c)))
     return a.value, b.value, c.value
 
 

@@ -54,6 +54,13 @@ def test_sizes_layout_and_mask(name):
     try:
         ntrue, nlocal, nnz = fe.fe_vspace_sizes(vs)
         assert (ntrue, nlocal, nnz) == (S.ntrue, S.nlocal, E.nnz)
+        # constrained rows: every row of E other than a single weight 1
+        per_row = np.diff(E.indptr)
+        single = (per_row == 1) & (np.abs(E.data[np.minimum(E.indptr[:-1], E.nnz - 1)] - 1.0) == 0)
+        cons = ~single
+        touched = np.unique(E[np.nonzero(cons)[0]].indices).size
+        assert fe.fe_vspace_constraint_sizes(vs) == (int(cons.sum()), int(per_row[cons].sum()),
+                                                     touched)
         first = fe.fe_vspace_layout(vs, S.ne)
         # groups of ascending order, elements ascending within each
         key = sorted(range(S.ne), key=lambda e: (S.order[e], e))
