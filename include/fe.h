@@ -386,6 +386,16 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
                     const double* host_vertices, const double* host_coeff, int ops, void* stream,
                     fe_vspace** out);
 
+/* Host-only construction of E (no device, no CUDA call): the numbering, E-vector layout and
+ * boundary mask that fe_vspace_setup would build, for inspection and for tests on machines
+ * without a GPU.  ntrue, nlocal, nnz: required outputs.  Optional outputs (NULL to skip; call
+ * once with NULLs to get the sizes): rowptr int64 [nlocal + 1], cols int32 [nnz] and vals FP64
+ * [nnz] (E in CSR, rows in E-vector order; cols and vals together), elem_first int64 [ne],
+ * mask uint8 [ntrue].  FE_ERR_ARG on a bad size or order. */
+int fe_vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t* ntrue,
+                     int64_t* nlocal, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals,
+                     int64_t* elem_first, uint8_t* mask);
+
 /* Sizes: true dofs, E-vector length (sum of D_e^3), nonzeros of E; any pointer may be NULL. */
 int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_t* nnz);
 

@@ -378,6 +378,61 @@ bool build_host_E(const Topo& T, const std::vector<int64_t>& order_elems,
   return true;
 }
 
+// 1 for the true dofs on the boundary of the box (vertices, edges and faces on it).
+std::vector<uint8_t> boundary_mask(const Topo& T) {
+  const int nx = T.n[0], ny = T.n[1], nz = T.n[2];
+  std::vector<uint8_t> mask(T.ntrue, 0);
+  {
+    int64_t i[3];
+    for (i[2] = 0; i[2] <= nz; ++i[2])
+      for (i[1] = 0; i[1] <= ny; ++i[1])
+        for (i[0] = 0; i[0] <= nx; ++i[0])
+          mask[T.vertex(i)] = i[0] == 0 || i[1] == 0 || i[2] == 0 || i[0] == nx || i[1] == ny ||
+                              i[2] == nz;
+    for (int d = 0; d < 3; ++d) {
+      for (i[2] = 0; i[2] < T.ebox[d][2]; ++i[2])
+        for (i[1] = 0; i[1] < T.ebox[d][1]; ++i[1])
+          for (i[0] = 0; i[0] < T.ebox[d][0]; ++i[0]) {
+            const int64_t l = T.lin(T.ebox[d], i);
+            if (T.on_boundary_edge(d, i))
+              for (int m = 0; m < T.eq[d][l] - 1; ++m) mask[T.efirst[d][l] + m] = 1;
+          }
+      for (i[2] = 0; i[2] < T.fbox[d][2]; ++i[2])
+        for (i[1] = 0; i[1] < T.fbox[d][1]; ++i[1])
+          for (i[0] = 0; i[0] < T.fbox[d][0]; ++i[0]) {
+            const int64_t l = T.lin(T.fbox[d], i);
+            if (i[d] == 0 || i[d] == T.n[d])
+              for (int m = 0; m < (T.fq[d][l] - 1) * (T.fq[d][l] - 1); ++m)
+                mask[T.ffirst[d][l] + m] = 1;
+          }
+    }
+  }
+
+  return mask;
+}
+
+// E-vector layout: groups of ascending order, elements ascending within a group.  Returns the
+// total length; first[e] the offset of element e, order_elems the elements in E-vector order.
+int64_t evector_layout(const Topo& T, std::vector<int64_t>& first,
+                       std::vector<int64_t>& order_elems) {
+  first.assign(T.ne, 0);
+  order_elems.clear();
+  order_elems.reserve(T.ne);
+  int present[kMaxOrder + 1] = {0};
+  for (int p : T.ord) present[p] = 1;
+  int64_t nlocal = 0;
+  for (int p = 1; p <= kMaxOrder; ++p) {
+    if (!present[p]) continue;
+    for (int64_t e = 0; e < T.ne; ++e)
+      if (T.ord[e] == p) {
+        first[e] = nlocal;
+        nlocal += (int64_t)(p + 1) * (p + 1) * (p + 1);
+        order_elems.push_back(e);
+      }
+  }
+  return nlocal;
+}
+
 __global__ void k_csr_gather(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                              const double* __restrict__ val, int64_t nrows,
                              const double* __restrict__ x, double* __restrict__ y) {
@@ -647,22 +702,10 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
     return set_error(FE_ERR_ARG, "fe_vspace_setup: orders must be 1..8");
   cudaStream_t s = (cudaStream_t)stream;
 
-  // E-vector layout: groups of ascending order, elements ascending within a group
-  std::vector<int64_t> first(T.ne);
+  std::vector<int64_t> first, order_elems;
+  const int64_t nlocal = evector_layout(T, first, order_elems);
   int present[kMaxOrder + 1] = {0};
   for (int p : T.ord) present[p] = 1;
-  int64_t nlocal = 0;
-  std::vector<int64_t> order_elems;  // elements in E-vector order
-  order_elems.reserve(T.ne);
-  for (int p = 1; p <= kMaxOrder; ++p) {
-    if (!present[p]) continue;
-    for (int64_t e = 0; e < T.ne; ++e)
-      if (T.ord[e] == p) {
-        first[e] = nlocal;
-        nlocal += (int64_t)(p + 1) * (p + 1) * (p + 1);
-        order_elems.push_back(e);
-      }
-  }
   if (T.ntrue > 2147483647LL || nlocal > 2147483647LL)
     return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_setup: more than 2^31-1 true or local dofs");
 
@@ -671,33 +714,7 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
     return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_setup: more than 2^31-1 constrained values");
   const int64_t nnz = H.nnz, nc = H.nc;
 
-  // boundary mask of the true dofs
-  std::vector<uint8_t> mask(T.ntrue, 0);
-  {
-    int64_t i[3];
-    for (i[2] = 0; i[2] <= nz; ++i[2])
-      for (i[1] = 0; i[1] <= ny; ++i[1])
-        for (i[0] = 0; i[0] <= nx; ++i[0])
-          mask[T.vertex(i)] = i[0] == 0 || i[1] == 0 || i[2] == 0 || i[0] == nx || i[1] == ny ||
-                              i[2] == nz;
-    for (int d = 0; d < 3; ++d) {
-      for (i[2] = 0; i[2] < T.ebox[d][2]; ++i[2])
-        for (i[1] = 0; i[1] < T.ebox[d][1]; ++i[1])
-          for (i[0] = 0; i[0] < T.ebox[d][0]; ++i[0]) {
-            const int64_t l = T.lin(T.ebox[d], i);
-            if (T.on_boundary_edge(d, i))
-              for (int m = 0; m < T.eq[d][l] - 1; ++m) mask[T.efirst[d][l] + m] = 1;
-          }
-      for (i[2] = 0; i[2] < T.fbox[d][2]; ++i[2])
-        for (i[1] = 0; i[1] < T.fbox[d][1]; ++i[1])
-          for (i[0] = 0; i[0] < T.fbox[d][0]; ++i[0]) {
-            const int64_t l = T.lin(T.fbox[d], i);
-            if (i[d] == 0 || i[d] == T.n[d])
-              for (int m = 0; m < (T.fq[d][l] - 1) * (T.fq[d][l] - 1); ++m)
-                mask[T.ffirst[d][l] + m] = 1;
-          }
-    }
-  }
+  std::vector<uint8_t> mask = boundary_mask(T);
 
   fe_vspace* vs = new fe_vspace();
   vs->nx = nx;
@@ -785,6 +802,62 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
     return cuda_error(err, "fe_vspace_setup");
   }
   *out = vs;
+  return FE_OK;
+}
+
+int fe_vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t* ntrue,
+                     int64_t* nlocal, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals,
+                     int64_t* elem_first, uint8_t* mask) {
+  clear_error();
+  if (!host_order || !ntrue || !nlocal || !nnz)
+    return set_error(FE_ERR_ARG, "fe_vspace_host_E: null argument");
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(FE_ERR_ARG, "fe_vspace_host_E: mesh size < 1");
+  Topo T;
+  if (!build_topology(nx, ny, nz, host_order, T))
+    return set_error(FE_ERR_ARG, "fe_vspace_host_E: orders must be 1..8");
+  std::vector<int64_t> first, order_elems;
+  const int64_t nl = evector_layout(T, first, order_elems);
+  std::vector<int64_t> cnt(nl + 1, 0);
+  auto count = [&](int64_t b, int64_t e_end) {
+    Row r;
+    for (int64_t t = b; t < e_end; ++t) {
+      const int64_t e = order_elems[t];
+      const int D = T.ord[e] + 1;
+      for (int a = 0; a < D * D * D; ++a) {
+        T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+        cnt[first[e] + a + 1] = r.n;
+      }
+    }
+  };
+  parallel_for((int64_t)order_elems.size(), count);
+  for (int64_t r = 0; r < nl; ++r) cnt[r + 1] += cnt[r];
+  *ntrue = T.ntrue;
+  *nlocal = nl;
+  *nnz = cnt[nl];
+  if (rowptr) std::memcpy(rowptr, cnt.data(), sizeof(int64_t) * (nl + 1));
+  if (elem_first) std::memcpy(elem_first, first.data(), sizeof(int64_t) * T.ne);
+  if (mask) {
+    const std::vector<uint8_t> m = boundary_mask(T);
+    std::memcpy(mask, m.data(), (size_t)T.ntrue);
+  }
+  if (cols && vals) {
+    auto fill = [&](int64_t b, int64_t e_end) {
+      Row r;
+      for (int64_t t = b; t < e_end; ++t) {
+        const int64_t e = order_elems[t];
+        const int D = T.ord[e] + 1;
+        for (int a = 0; a < D * D * D; ++a) {
+          T.node_row(e, a % D, (a / D) % D, a / (D * D), r);
+          const int64_t o = cnt[first[e] + a];
+          for (int z = 0; z < r.n; ++z) {
+            cols[o + z] = (int32_t)r.col[z];
+            vals[o + z] = r.w[z];
+          }
+        }
+      }
+    };
+    parallel_for((int64_t)order_elems.size(), fill);
+  }
   return FE_OK;
 }
 

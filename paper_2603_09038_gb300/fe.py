@@ -106,6 +106,10 @@ _SIGS = {
     "fe_lpc_destroy": (None, [_VP]),
     "fe_vspace_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP,
                                        ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "fe_vspace_host_E": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP, _VP, _VP]),
     "fe_vspace_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]),
@@ -456,6 +460,26 @@ def fe_vspace_setup(nx, ny, nz, orders, vertices, coeff=None, ops=FE_DIFFUSION |
                                v.ctypes.data_as(_VP), None if c is None else c.ctypes.data_as(_VP),
                                int(ops), _stream(stream), ctypes.byref(out)))
     return out.value
+
+
+def fe_vspace_host_E(nx, ny, nz, orders):
+    """Host-only E of the variable-order space (no GPU needed): returns (ntrue, rowptr, cols,
+    vals, elem_first, mask) with E in CSR, rows in E-vector order."""
+    lib = load()
+    o = np.ascontiguousarray(orders, dtype=np.int32)
+    nt, nl, nz_ = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib.fe_vspace_host_E(int(nx), int(ny), int(nz), o.ctypes.data_as(_VP), ctypes.byref(nt),
+                                ctypes.byref(nl), ctypes.byref(nz_), None, None, None, None, None))
+    rowptr = np.zeros(nl.value + 1, dtype=np.int64)
+    cols = np.zeros(nz_.value, dtype=np.int32)
+    vals = np.zeros(nz_.value, dtype=np.float64)
+    first = np.zeros(o.size, dtype=np.int64)
+    mask = np.zeros(nt.value, dtype=np.uint8)
+    _check(lib.fe_vspace_host_E(int(nx), int(ny), int(nz), o.ctypes.data_as(_VP), ctypes.byref(nt),
+                                ctypes.byref(nl), ctypes.byref(nz_), rowptr.ctypes.data_as(_VP),
+                                cols.ctypes.data_as(_VP), vals.ctypes.data_as(_VP),
+                                first.ctypes.data_as(_VP), mask.ctypes.data_as(_VP)))
+    return nt.value, rowptr, cols, vals, first, mask
 
 
 def fe_vspace_sizes(vs):
