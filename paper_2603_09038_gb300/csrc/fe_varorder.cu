@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -687,10 +689,9 @@ int fold_Y(const fe_vspace* vs, double* y, int square, cudaStream_t s) {
 
 extern "C" {
 
-int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
-                    const double* host_vertices, const double* host_coeff, int ops, void* stream,
-                    fe_vspace** out) {
-  clear_error();
+static int vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
+                        const double* host_vertices, const double* host_coeff, int ops,
+                        void* stream, fe_vspace** out) {
   if (!out) return set_error(FE_ERR_ARG, "fe_vspace_setup: out is NULL");
   *out = nullptr;
   if (!host_order || !host_vertices) return set_error(FE_ERR_ARG, "fe_vspace_setup: null argument");
@@ -805,10 +806,9 @@ int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   return FE_OK;
 }
 
-int fe_vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t* ntrue,
-                     int64_t* nlocal, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals,
-                     int64_t* elem_first, uint8_t* mask) {
-  clear_error();
+static int vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t* ntrue,
+                         int64_t* nlocal, int64_t* nnz, int64_t* rowptr, int32_t* cols,
+                         double* vals, int64_t* elem_first, uint8_t* mask) {
   if (!host_order || !ntrue || !nlocal || !nnz)
     return set_error(FE_ERR_ARG, "fe_vspace_host_E: null argument");
   if (nx < 1 || ny < 1 || nz < 1) return set_error(FE_ERR_ARG, "fe_vspace_host_E: mesh size < 1");
@@ -859,6 +859,35 @@ int fe_vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t*
     parallel_for((int64_t)order_elems.size(), fill);
   }
   return FE_OK;
+}
+
+// The host construction allocates large vectors and starts threads: a failure there becomes a
+// status code instead of an exception crossing the C ABI.
+int fe_vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
+                    const double* host_vertices, const double* host_coeff, int ops, void* stream,
+                    fe_vspace** out) {
+  clear_error();
+  try {
+    return vspace_setup(nx, ny, nz, host_order, host_vertices, host_coeff, ops, stream, out);
+  } catch (const std::bad_alloc&) {
+    return set_error(FE_ERR_OOM, "fe_vspace_setup: host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(FE_ERR_CUDA, std::string("fe_vspace_setup: ") + e.what());
+  }
+}
+
+int fe_vspace_host_E(int nx, int ny, int nz, const int32_t* host_order, int64_t* ntrue,
+                     int64_t* nlocal, int64_t* nnz, int64_t* rowptr, int32_t* cols, double* vals,
+                     int64_t* elem_first, uint8_t* mask) {
+  clear_error();
+  try {
+    return vspace_host_E(nx, ny, nz, host_order, ntrue, nlocal, nnz, rowptr, cols, vals,
+                         elem_first, mask);
+  } catch (const std::bad_alloc&) {
+    return set_error(FE_ERR_OOM, "fe_vspace_host_E: host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(FE_ERR_ARG, std::string("fe_vspace_host_E: ") + e.what());
+  }
 }
 
 int fe_vspace_sizes(const fe_vspace* vs, int64_t* ntrue, int64_t* nlocal, int64_t* nnz) {
