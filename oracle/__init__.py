@@ -17,8 +17,15 @@ Galerkin forms (the paper is silent on them):
 ``operator.py`` applies them as ``y = sum_e G_e^T K_e G_e x`` -- the plain definition.  The
 sum-factorised apply in ``sumfact.py`` is a second, independent route used only to cross-check
 the first on tiny meshes (brute-force agreement) and as the timed CPU baseline.
+``solve.py`` holds CG / preconditioned CG and the Chebyshev polynomial preconditioner,
+``mlp.py`` the learned preconditioner's network (forward, loss, backpropagation), and
+``varorder.py`` the variable-order space: the constraint operator P of Eq. (1) under the
+minimum rule, its Jacobi diagonal and operator.
 
 Parity status of every function is pinned by the ``-m "not gpu"`` tests in ``tests/``:
 closed-form 1D rules, textbook element matrices, volume, null space, symmetry, exact polynomial
-integration, O(h^{p+1}) convergence, dense-solve agreement and brute-force cross-checks.
+integration, O(h^{p+1}) convergence, dense-solve agreement and brute-force cross-checks; for the
+network finite differences and the least-squares special case; for the variable-order space a
+hand-derived numbering, the dimension of the continuous space by brute force, polynomial
+reproduction, closed-form energies and the single-order case.
 """
