@@ -428,17 +428,23 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=None):
+def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=None, fit=False):
     """The learned element-patch preconditioner inside flexible CG to the same FP64 residual as
     Jacobi-PCG (time t_pcg, pcg_iters iterations): training (data generation from the operator's
-    own patch solves + Adam) timed once on the host clock, the solve timed with CUDA events like
-    the PCG, and the fused BF16 tensor-core preconditioner kernel alone (median of 20)."""
+    own patch solves + Adam, or with fit=True the least-squares fit of the linear map) timed once
+    on the host clock, the solve timed with CUDA events like the PCG, and the fused BF16
+    tensor-core preconditioner kernel alone (median of 20)."""
     import torch
     ndofs, ne, p = fe.fe_mesh_sizes(fe_mesh_of[pa])
     t0 = time.perf_counter()
     width = args.lpc_width if width is None else width
     lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 1)
-    loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
+    if args.lpc_fallback == "chebyshev":
+        fe.fe_lpc_set_fallback(lpc, fe.FE_PC_CHEBYSHEV)
+    if fit:
+        loss = fe.fe_lpc_fit_linear(lpc, 1e-6, 0, stream)
+    else:
+        loss = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3, 0, stream)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -506,8 +512,10 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
         "fallbacks_to_jacobi": s_fcg["outer_iters"] - 1,
         "true_rel_resid": s_fcg["true_rel_resid"],
         "jacobi_fcg_time_s": t_fj, "jacobi_fcg_iters": s_fj["iters"],
-        "train_s": t_train, "train_steps": args.lpc_steps, "train_batch": 1024,
+        "train_s": t_train, "train": "least-squares fit" if fit else "Adam",
+        "train_steps": 0 if fit else args.lpc_steps, "train_batch": 1024,
         "final_batch_loss": loss, "width": w, "patch": "element, %d dofs" % din,
+        "fallback": args.lpc_fallback,
         "network": ("relu(relu(x W1) W2) W3 + x W0" if w else "x W0 (linear patch map)") +
                    ", BF16 weights/activations, FP32 accumulate",
         "precond_apply_ms": ms_lpc, "precond_tflops": lpc_flops / (ms_lpc * 1e-3) / 1e12,
@@ -555,6 +563,9 @@ def run_learned(args, local_rank):
            "ndofs": ndofs, "variant": args.variant, "rtol": args.rtol}
     out.update(learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"]))
     out["linear"] = learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"], width=0)
+    if args.lpc_fit:
+        out["linear_fit"] = learned_fcg(fe, pa, b, x, args, stream, None, dev, t_pcg, s0["iters"],
+                                        width=0, fit=True)
     fe.fe_pa_destroy(pa)
     fe.fe_mesh_destroy(mesh)
     print(json.dumps(out))
@@ -862,6 +873,10 @@ def main():
     ap.add_argument("--lpc-width", type=int, default=128,
                     help="width of the learned preconditioner's MLP (0: skip that comparison)")
     ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
+    ap.add_argument("--lpc-fit", action="store_true",
+                    help="--learned: also the linear map fitted by least squares (fe_lpc_fit_linear)")
+    ap.add_argument("--lpc-fallback", choices=["jacobi", "chebyshev"], default="jacobi",
+                    help="what FCG continues with once it gives the network up")
     ap.add_argument("--learned", action="store_true",
                     help="only the learned-preconditioner comparison (with --n, --p, --sigma)")
     ap.add_argument("--batched-pcg", type=int, default=0,
