@@ -46,12 +46,16 @@ typedef enum {
   FE_ERR_UNSUPPORTED = -4,   /* order / quadrature / variant combination not built               */
   FE_ERR_NOT_CONVERGED = -5, /* fe_pcg hit maxit before reaching rtol                            */
   FE_ERR_BREAKDOWN = -6,     /* fe_pcg found p.Ap <= 0 (operator not SPD on the free dofs)        */
-  FE_ERR_NAN = -7            /* fe_pcg met a NaN or Inf                                          */
+  FE_ERR_NAN = -7,           /* fe_pcg met a NaN or Inf                                          */
+  FE_ERR_TIMEOUT = -8        /* reserved for a bounded device-side wait that ran out; no entry
+                                point returns it (no kernel of the library waits on another)    */
 } fe_status;
 
 typedef enum { FE_DIFFUSION = 1, FE_MASS = 2 } fe_op;
 
-typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1, FE_PC_CHEBYSHEV = 2 } fe_pc;
+/* FE_PC_LEARNED: flexible CG with the learned preconditioner attached by fe_pa_set_learned
+ * (fe_pcg only; it is fe_fcg with that preconditioner). */
+typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1, FE_PC_CHEBYSHEV = 2, FE_PC_LEARNED = 3 } fe_pc;
 
 /* Arithmetic of the apply kernels.  All variants take and return FP64 vectors.
  *  FE_VARIANT_F64     FP64 FMA on the FP64 pipe (IEEE double throughout).
@@ -88,6 +92,9 @@ int fe_mesh_setup(int nx, int ny, int nz, int order, const double* host_vertices
 
 /* Sizes of a mesh: global dofs (incl. boundary), elements, order. */
 int fe_mesh_sizes(const fe_mesh* mesh, int64_t* ndofs, int64_t* nelems, int* order);
+
+/* Global dofs of a mesh (incl. boundary); the first output of fe_mesh_sizes. */
+int fe_mesh_ndofs(const fe_mesh* mesh, int64_t* ndofs);
 
 /* Copies the boundary-dof mask (uint8 [ndofs], 1 on the cube's boundary lattice) to dev_mask. */
 int fe_mesh_boundary_mask(const fe_mesh* mesh, uint8_t* dev_mask, void* stream);
@@ -312,6 +319,11 @@ int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);
  * loss.  Does not update the weights.  Synchronous. */
 int fe_lpc_loss_grad(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
                      float* host_y, float* host_grad, double* loss);
+
+/* Attaches lpc (built for this pa; NULL detaches) as the preconditioner that fe_pcg uses for
+ * pc = FE_PC_LEARNED.  The handle is not owned; fe_lpc_destroy detaches it.  FE_ERR_ARG if lpc
+ * was built for another fe_pa. */
+int fe_pa_set_learned(fe_pa* pa, fe_lpc* lpc);
 
 /* What fe_fcg continues with once it gives up the network: FE_PC_JACOBI (the default: FCG
  * restarted with Jacobi from the current iterate) or FE_PC_CHEBYSHEV (Chebyshev-PCG on the

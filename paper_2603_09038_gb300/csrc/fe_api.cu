@@ -471,6 +471,13 @@ int fe_mesh_sizes(const fe_mesh* m, int64_t* ndofs, int64_t* nelems, int* order)
   return FE_OK;
 }
 
+int fe_mesh_ndofs(const fe_mesh* m, int64_t* ndofs) {
+  clear_error();
+  if (!m || !ndofs) return set_error(FE_ERR_ARG, "fe_mesh_ndofs: null argument");
+  *ndofs = m->ndofs;
+  return FE_OK;
+}
+
 int fe_mesh_boundary_mask(const fe_mesh* m, uint8_t* dev_mask, void* stream) {
   clear_error();
   if (!m || !dev_mask) return set_error(FE_ERR_ARG, "fe_mesh_boundary_mask: null argument");

@@ -72,6 +72,7 @@ struct fe_pa {
   int64_t dpart_cap = 0;
   double cheb_lmax[2] = {0.0, 0.0};  // cached lambda_max estimates of D^-1 A (diffusion, mass)
   bool pcg_graphs = true;          // fe_pcg replays its iteration batches as CUDA graphs
+  fe_lpc* lpc = nullptr;           // learned preconditioner for FE_PC_LEARNED (not owned)
 };
 
 namespace fe {

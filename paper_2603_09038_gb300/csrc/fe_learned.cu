@@ -1569,6 +1569,15 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
   }
 }
 
+int fe_pa_set_learned(fe_pa* pa, fe_lpc* lpc) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_pa_set_learned: pa is NULL");
+  if (lpc && lpc->pa != pa)
+    return set_error(FE_ERR_ARG, "fe_pa_set_learned: preconditioner built for another fe_pa");
+  pa->lpc = lpc;
+  return FE_OK;
+}
+
 int fe_lpc_set_fallback(fe_lpc* lpc, int pc) {
   clear_error();
   if (!lpc) return set_error(FE_ERR_ARG, "fe_lpc_set_fallback: lpc is NULL");
@@ -1580,6 +1589,7 @@ int fe_lpc_set_fallback(fe_lpc* lpc, int pc) {
 
 void fe_lpc_destroy(fe_lpc* L) {
   if (!L) return;
+  if (L->pa && L->pa->lpc == L) L->pa->lpc = nullptr;
   cudaFree(L->w32); cudaFree(L->wb); cudaFree(L->adam_m); cudaFree(L->adam_v); cudaFree(L->grad);
   cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->fsc32); cudaFree(L->wimg); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
   cudaFree(L->Xb); cudaFree(L->H1b); cudaFree(L->H2b); cudaFree(L->dYb); cudaFree(L->dA1b);

@@ -877,6 +877,12 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
   clear_error();
   if (pc == FE_PC_CHEBYSHEV)
     return fe_pcg_chebyshev(pa, op, 0, 0.0, 0.0, dev_b, dev_x, rtol, maxit, stats, stream);
+  if (pc == FE_PC_LEARNED) {
+    if (!pa) return set_error(FE_ERR_ARG, "fe_pcg: pa is NULL");
+    if (!pa->lpc)
+      return set_error(FE_ERR_ARG, "fe_pcg: FE_PC_LEARNED needs fe_pa_set_learned first");
+    return fe_fcg(pa, op, pa->lpc, dev_b, dev_x, rtol, maxit, stats, stream);
+  }
   const auto t0 = std::chrono::steady_clock::now();
   if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   int st = pcg_check_args(pa, op, pc, dev_b, dev_x, rtol, maxit, "fe_pcg");

@@ -22,12 +22,14 @@ FE_ERR_UNSUPPORTED = -4
 FE_ERR_NOT_CONVERGED = -5
 FE_ERR_BREAKDOWN = -6
 FE_ERR_NAN = -7
+FE_ERR_TIMEOUT = -8
 
 FE_DIFFUSION = 1
 FE_MASS = 2
 FE_PC_NONE = 0
 FE_PC_JACOBI = 1
 FE_PC_CHEBYSHEV = 2
+FE_PC_LEARNED = 3
 FE_VARIANT_F64 = 0
 FE_VARIANT_F32X2 = 1
 FE_VARIANT_F64_DMMA = 2
@@ -57,6 +59,7 @@ _SIGS = {
                                      ctypes.POINTER(_VP)]),
     "fe_mesh_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
+    "fe_mesh_ndofs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "fe_mesh_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_mesh_dof_map": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pa_setup": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -99,6 +102,7 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_lpc_set_fallback": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_pa_set_learned": (ctypes.c_int, [_VP, _VP]),
     "fe_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                               ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_fcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
@@ -187,6 +191,12 @@ def fe_mesh_sizes(mesh):
     nd, ne, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
     _check(lib.fe_mesh_sizes(_VP(mesh), ctypes.byref(nd), ctypes.byref(ne), ctypes.byref(p)))
     return nd.value, ne.value, p.value
+
+
+def fe_mesh_ndofs(mesh):
+    nd = ctypes.c_int64()
+    _check(load().fe_mesh_ndofs(_VP(mesh), ctypes.byref(nd)))
+    return nd.value
 
 
 def fe_mesh_boundary_mask(mesh, dev_mask, stream=None):
@@ -435,6 +445,11 @@ def fe_fcg_ir(pa, op, lpc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=Non
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_pa_set_learned(pa, lpc):
+    """Attach lpc (or None to detach) as fe_pcg's FE_PC_LEARNED preconditioner."""
+    _check(load().fe_pa_set_learned(_VP(pa), _VP(lpc) if lpc else None))
 
 
 def fe_lpc_set_fallback(lpc, pc):

@@ -211,6 +211,43 @@ def test_fcg_chebyshev_fallback_after_a_stall():
             fe.fe_lpc_destroy(lpc)
 
 
+def test_pcg_learned_is_fcg_with_the_attached_preconditioner():
+    """fe_pcg(pc = FE_PC_LEARNED) runs fe_fcg with the preconditioner attached by
+    fe_pa_set_learned; without one (or after detaching, or destroying it) it is an argument
+    error."""
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 2) as (fe, mesh, pa, V, c):
+        n = fe.fe_mesh_ndofs(mesh)
+        assert n == fe.fe_mesh_sizes(mesh)[0]
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x1 = torch.empty_like(b)
+        x2 = torch.empty_like(b)
+        with pytest.raises(fe.FEError) as e:
+            fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_LEARNED, b, x1, 1e-10, 2000)
+        assert e.value.status == fe.FE_ERR_ARG
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 16, 1)
+        try:
+            # a zero network: z = 0 exactly, so both solves take the same (Jacobi) path
+            fe.fe_lpc_weights(lpc, np.zeros(fe.fe_lpc_nparams(lpc), dtype=np.float32))
+            fe.fe_pa_set_learned(pa, lpc)
+            st1, s1 = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_LEARNED, b, x1, 1e-10, 2000)
+            st2, s2 = fe.fe_fcg(pa, fe.FE_DIFFUSION, lpc, b, x2, 1e-10, 2000)
+            assert st1 == st2 == fe.FE_OK, fe.fe_last_error()
+            assert abs(s1["iters"] - s2["iters"]) <= 1
+            assert s1["outer_iters"] == s2["outer_iters"] == 2
+            assert s1["true_rel_resid"] <= 1e-9
+            assert float((x1 - x2).abs().max()) <= 1e-7 * float(x2.abs().max())
+            fe.fe_pa_set_learned(pa, None)
+            with pytest.raises(fe.FEError):
+                fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_LEARNED, b, x1, 1e-10, 2000)
+            fe.fe_pa_set_learned(pa, lpc)
+        finally:
+            fe.fe_lpc_destroy(lpc)
+        with pytest.raises(fe.FEError):    # destroying the preconditioner detached it
+            fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_LEARNED, b, x1, 1e-10, 2000)
+
+
 def test_lpc_argument_errors():
     torch = torch_cuda()
     with gpu_problem(2, 2, 2, 5) as (fe, mesh, pa, V, c):
