@@ -15,14 +15,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <exception>
 #include <new>
 #include <thread>
 #include <vector>
-
-#include <chrono>
 
 #include "fe_f2.h"
 #include "fe_internal.h"
