@@ -86,10 +86,39 @@ def job_gdofs(world, ndofs, applies, seconds):
     return world * ndofs * applies / seconds / 1e9
 
 
-class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region (200 ms period)."""
+def parse_clock_samples(text, reasons_names=("hw_slowdown", "hw_thermal_slowdown",
+                                              "sw_thermal_slowdown", "sw_power_cap")):
+    """Summary of `nvidia-smi --query-gpu=clocks.sm,clocks.max.sm,power.draw,<5 reason columns>
+    --format=csv,noheader,nounits` lines: median SM clock under load, the maximum clock, the
+    throttle reasons seen Active, and the median board power (W) when it is reported."""
+    sm, mx, pw, reasons = [], [], [], set()
+    for line in text.splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 8:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        try:
+            pw.append(float(f[2]))
+        except ValueError:
+            pass
+        for name, val in zip(reasons_names, f[4:8]):
+            if val.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return None
+    out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+           "reasons": sorted(reasons)}
+    if pw:
+        out["power_w"] = statistics.median(pw)
+    return out
 
-    REASONS = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+class ClockSampler:
+    """nvidia-smi clock/throttle/power sampling during the timed region (200 ms period)."""
 
     def __init__(self, index):
         self.index = index
@@ -118,22 +147,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
-        for line in out.splitlines():
-            f = [s.strip() for s in line.split(",")]
-            if len(f) < 8:
-                continue
-            try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
-            except ValueError:
-                continue
-            for name, val in zip(self.REASONS[1:], f[4:8]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if sm:
-            self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                           "samples": len(sm), "reasons": sorted(reasons)}
+        self.result = parse_clock_samples(out)
         return False
 
 
@@ -418,6 +432,9 @@ def run_ours(args, rank, world, local_rank):
            "true_rel_resid": last_stats["true_rel_resid"] if args.steps else None}
     if clk.result:
         out["clocks"] = clk.result
+        if clk.result.get("power_w"):
+            # the paper's energy metric (Table VI): MDOF/s per watt of board power
+            out["mdof_per_w"] = 1000.0 * value / (world * clk.result["power_w"])
     fe.fe_pa_destroy(pa)
     fe.fe_mesh_destroy(mesh)
     if rank == 0:

@@ -40,3 +40,22 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_sample_parsing():
+    """The nvidia-smi sampling summary: median clock, max clock, throttle reasons seen Active,
+    median power (the MDOF/W denominator); malformed lines are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    text = "\n".join([
+        "2040, 2070, 900.5, Not Active, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1010.0, Active, Not Active, Not Active, Not Active, Active",
+        "1990, 2070, [N/A], Active, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "",
+    ])
+    r = bench.parse_clock_samples(text)
+    assert r["samples"] == 3 and r["sm_mhz"] == 2040 and r["sm_max_mhz"] == 2070
+    assert r["reasons"] == ["sw_power_cap"]
+    assert r["power_w"] == (900.5 + 1010.0) / 2
+    assert bench.parse_clock_samples("") is None
