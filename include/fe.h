@@ -320,6 +320,20 @@ int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);
 int fe_lpc_loss_grad(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
                      float* host_y, float* host_grad, double* loss);
 
+/* Checkpoint of a learned preconditioner, so that training resumes where it stopped.  File
+ * layout (little-endian): 8 bytes "FELPC001", int32 din (= D^3), int32 width, int64 nparam,
+ * int32 Adam step count, int32 0, then nparam FP32 weights (the fe_lpc_weights packing), the
+ * nparam FP32 Adam first moments and the nparam FP32 second moments.  fe_lpc_save writes it
+ * (FE_ERR_ARG if the file cannot be written); fe_lpc_load reads it into lpc (FE_ERR_ARG on a
+ * missing, foreign, truncated file or one of another network shape; the training set is not
+ * stored: the next fe_lpc_train regenerates it from the operator, with the same seed the same
+ * set).  fe_lpc_checkpoint_info reads only the header, on the host (no device needed); any
+ * output may be NULL.  Synchronous. */
+int fe_lpc_save(fe_lpc* lpc, const char* path);
+int fe_lpc_load(fe_lpc* lpc, const char* path);
+int fe_lpc_checkpoint_info(const char* path, int* din, int* width, int64_t* nparam,
+                           int* adam_steps);
+
 /* Attaches lpc (built for this pa; NULL detaches) as the preconditioner that fe_pcg uses for
  * pc = FE_PC_LEARNED.  The handle is not owned; fe_lpc_destroy detaches it.  FE_ERR_ARG if lpc
  * was built for another fe_pa. */

@@ -26,6 +26,8 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -1567,6 +1569,100 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
     default:
       return set_error(FE_ERR_NOT_CONVERGED, "fe_fcg: maxit reached before rtol");
   }
+}
+
+// ---- checkpoint: little-endian "FELPC001", int32 din, int32 width, int64 nparam, int32 Adam
+// step count, int32 0, then FP32 weights, Adam first and second moments (nparam each).
+static const char kLpcMagic[8] = {'F', 'E', 'L', 'P', 'C', '0', '0', '1'};
+
+struct LpcHeader {
+  char magic[8];
+  int32_t din, width;
+  int64_t nparam;
+  int32_t adam_t, pad;
+};
+static_assert(sizeof(LpcHeader) == 32, "checkpoint header layout");
+
+static int read_lpc_header(FILE* f, LpcHeader* h, const char* who) {
+  if (std::fread(h, sizeof(*h), 1, f) != 1 || std::memcmp(h->magic, kLpcMagic, 8) != 0)
+    return set_error(FE_ERR_ARG, std::string(who) + ": not a preconditioner checkpoint");
+  if (h->din < 1 || h->width < 0 || h->nparam < 1 || h->adam_t < 0)
+    return set_error(FE_ERR_ARG, std::string(who) + ": corrupt checkpoint header");
+  return FE_OK;
+}
+
+int fe_lpc_checkpoint_info(const char* path, int* din, int* width, int64_t* nparam,
+                           int* adam_steps) {
+  clear_error();
+  if (!path) return set_error(FE_ERR_ARG, "fe_lpc_checkpoint_info: path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(FE_ERR_ARG, std::string("fe_lpc_checkpoint_info: cannot open ") + path);
+  LpcHeader h;
+  const int st = read_lpc_header(f, &h, "fe_lpc_checkpoint_info");
+  std::fclose(f);
+  if (st != FE_OK) return st;
+  if (din) *din = h.din;
+  if (width) *width = h.width;
+  if (nparam) *nparam = h.nparam;
+  if (adam_steps) *adam_steps = h.adam_t;
+  return FE_OK;
+}
+
+int fe_lpc_save(fe_lpc* L, const char* path) {
+  clear_error();
+  if (!L || !path) return set_error(FE_ERR_ARG, "fe_lpc_save: null argument");
+  const int64_t n = L->nparam;
+  std::vector<float> w(n), m(n, 0.0f), v(n, 0.0f);
+  cudaError_t err = cudaMemcpy(w.data(), L->w32, 4 * n, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaMemcpy(m.data(), L->adam_m, 4 * n, cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess) err = cudaMemcpy(v.data(), L->adam_v, 4 * n, cudaMemcpyDeviceToHost);
+  if (err != cudaSuccess) return cuda_error(err, "fe_lpc_save: copy");
+  LpcHeader h;
+  std::memcpy(h.magic, kLpcMagic, 8);
+  h.din = L->din;
+  h.width = L->width;
+  h.nparam = n;
+  h.adam_t = L->adam_t;
+  h.pad = 0;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(FE_ERR_ARG, std::string("fe_lpc_save: cannot open ") + path);
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                  std::fwrite(w.data(), 4, n, f) == (size_t)n &&
+                  std::fwrite(m.data(), 4, n, f) == (size_t)n &&
+                  std::fwrite(v.data(), 4, n, f) == (size_t)n;
+  if (std::fclose(f) != 0 || !ok) return set_error(FE_ERR_ARG, "fe_lpc_save: write failed");
+  return FE_OK;
+}
+
+int fe_lpc_load(fe_lpc* L, const char* path) {
+  clear_error();
+  if (!L || !path) return set_error(FE_ERR_ARG, "fe_lpc_load: null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(FE_ERR_ARG, std::string("fe_lpc_load: cannot open ") + path);
+  LpcHeader h;
+  int st = read_lpc_header(f, &h, "fe_lpc_load");
+  if (st == FE_OK && (h.din != L->din || h.width != L->width || h.nparam != L->nparam))
+    st = set_error(FE_ERR_ARG, "fe_lpc_load: checkpoint of another network shape");
+  const int64_t n = L->nparam;
+  std::vector<float> w, m, v;
+  if (st == FE_OK) {
+    w.resize(n);
+    m.resize(n);
+    v.resize(n);
+    if (std::fread(w.data(), 4, n, f) != (size_t)n || std::fread(m.data(), 4, n, f) != (size_t)n ||
+        std::fread(v.data(), 4, n, f) != (size_t)n)
+      st = set_error(FE_ERR_ARG, "fe_lpc_load: truncated checkpoint");
+  }
+  std::fclose(f);
+  if (st != FE_OK) return st;
+  cudaError_t err = cudaMemcpy(L->w32, w.data(), 4 * n, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(L->adam_m, m.data(), 4 * n, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(L->adam_v, v.data(), 4 * n, cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return cuda_error(err, "fe_lpc_load: copy");
+  L->adam_t = h.adam_t;
+  k_to_bf16<<<grid1(n), kT>>>(L->w32, L->wb, n);
+  L->wimg_ok = false;
+  return cuda_error(cudaDeviceSynchronize(), "fe_lpc_load");
 }
 
 int fe_pa_set_learned(fe_pa* pa, fe_lpc* lpc) {

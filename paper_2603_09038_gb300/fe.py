@@ -103,6 +103,12 @@ _SIGS = {
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fe_lpc_set_fallback": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fe_pa_set_learned": (ctypes.c_int, [_VP, _VP]),
+    "fe_lpc_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "fe_lpc_load": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "fe_lpc_checkpoint_info": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int)]),
     "fe_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
                               ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_fcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int,
@@ -445,6 +451,24 @@ def fe_fcg_ir(pa, op, lpc, dev_b, dev_x, rtol, maxit, inner_rtol=0.0, stream=Non
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)
+
+
+def fe_lpc_save(lpc, path):
+    """Checkpoint of the weights and Adam state (format in include/fe.h)."""
+    _check(load().fe_lpc_save(_VP(lpc), os.fsencode(path)))
+
+
+def fe_lpc_load(lpc, path):
+    _check(load().fe_lpc_load(_VP(lpc), os.fsencode(path)))
+
+
+def fe_lpc_checkpoint_info(path):
+    """(din, width, nparam, adam_steps) from a checkpoint's header (host only)."""
+    din, w, ap = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    n = ctypes.c_int64()
+    _check(load().fe_lpc_checkpoint_info(os.fsencode(path), ctypes.byref(din), ctypes.byref(w),
+                                         ctypes.byref(n), ctypes.byref(ap)))
+    return din.value, w.value, n.value, ap.value
 
 
 def fe_pa_set_learned(pa, lpc):

@@ -248,6 +248,37 @@ def test_pcg_learned_is_fcg_with_the_attached_preconditioner():
             fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_LEARNED, b, x1, 1e-10, 2000)
 
 
+def test_checkpoint_roundtrip_and_resume(tmp_path):
+    """fe_lpc_save / fe_lpc_load: the weights come back exactly; training resumed from the
+    checkpoint follows the uninterrupted run (same batches: the batch draw depends on the seed and
+    the Adam step count); a checkpoint of another shape is refused."""
+    torch = torch_cuda()
+    with gpu_problem(4, 4, 4, 2) as (fe, mesh, pa, V, c):
+        path = str(tmp_path / "lpc.bin")
+        a = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 64, 5)
+        b = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 64, 5)
+        other = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 128, 5)
+        try:
+            n = fe.fe_lpc_nparams(a)
+            fe.fe_lpc_train(a, 30, 256, 1e-3)
+            fe.fe_lpc_save(a, path)
+            assert fe.fe_lpc_checkpoint_info(path) == (27, 64, n, 30)
+            wa = fe.fe_lpc_weights(a)            # one argument: read
+            fe.fe_lpc_load(b, path)
+            np.testing.assert_array_equal(wa, fe.fe_lpc_weights(b))
+            fe.fe_lpc_train(a, 30, 256, 1e-3)
+            fe.fe_lpc_train(b, 30, 256, 1e-3)
+            wa, wb = fe.fe_lpc_weights(a), fe.fe_lpc_weights(b)
+            assert np.abs(wa - wb).max() <= 1e-3 * np.abs(wa).max()
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_lpc_load(other, path)
+            assert e.value.status == fe.FE_ERR_ARG
+        finally:
+            fe.fe_lpc_destroy(a)
+            fe.fe_lpc_destroy(b)
+            fe.fe_lpc_destroy(other)
+
+
 def test_lpc_argument_errors():
     torch = torch_cuda()
     with gpu_problem(2, 2, 2, 5) as (fe, mesh, pa, V, c):
