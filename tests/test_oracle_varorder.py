@@ -99,6 +99,7 @@ def _jump_matrix(S):
     ((2, 2, 2), [1, 2, 3, 2, 2, 1, 3, 2]),
     ((3, 2, 1), [2, 4, 2, 3, 1, 4]),
     ((2, 2, 2), [3] * 8),
+    ((2, 1, 2), [8, 5, 7, 6]),
 ])
 def test_dimension_equals_continuous_space(dims, orders):
     """Brute force: the continuous piecewise-Q_{p_e} functions are the null space of the face
@@ -130,6 +131,18 @@ def test_polynomial_reproduction(dims, orders):
     E = S.prolongation()
     np.testing.assert_allclose(E @ u(S.true_lattice_coords()), u(_node_coords(S)),
                                rtol=0, atol=1e-12)
+
+
+def test_polynomial_reproduction_high_orders():
+    """Orders 5..8 reproduce a degree-5 polynomial in each variable exactly."""
+    S = VarSpace(2, 2, 1, [5, 8, 7, 6])
+
+    def u(X):
+        x, y, z = X[:, 0], X[:, 1], X[:, 2]
+        return (1 + x ** 5 - 0.3 * x ** 3) * (0.5 + y ** 4 - y ** 5 / 3) * (1 - z ** 5 + 2 * z)
+
+    np.testing.assert_allclose(S.prolongation() @ u(S.true_lattice_coords()), u(_node_coords(S)),
+                               rtol=0, atol=1e-11)
 
 
 def test_energy_closed_forms():
