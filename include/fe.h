@@ -90,6 +90,14 @@ typedef struct {
  * [(nx+1)(ny+1)(nz+1)][3], x fastest, copied.  order 1..8.  Synchronous. */
 int fe_mesh_setup(int nx, int ny, int nz, int order, const double* host_vertices, fe_mesh** out);
 
+/* The 1D tables of Eq. (2) that every apply uses (host only, no device needed): nodes[D] the
+ * order+1 Gauss-Lobatto-Legendre nodes on [0,1], pts[Q] / wts[Q] the q1d-point Gauss-Legendre
+ * rule on [0,1], B[Q][D] = l_d(x_q) and G[Q][D] = l_d'(x_q) (row-major, q slowest), computed in
+ * long double and rounded once.  Any output may be NULL.  FE_ERR_ARG unless order is 1..8 and
+ * q1d 1..10. */
+int fe_basis_1d(int order, int q1d, double* nodes, double* pts, double* wts, double* B,
+                double* G);
+
 /* Sizes of a mesh: global dofs (incl. boundary), elements, order. */
 int fe_mesh_sizes(const fe_mesh* mesh, int64_t* ndofs, int64_t* nelems, int* order);
 

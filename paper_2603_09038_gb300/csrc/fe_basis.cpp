@@ -120,3 +120,23 @@ bool make_basis_1d(int p, int q, Basis1D* out) {
 }
 
 }  // namespace fe
+
+extern "C" int fe_basis_1d(int order, int q1d, double* nodes, double* pts, double* wts,
+                           double* B, double* G) {
+  fe::clear_error();
+  fe::Basis1D b;
+  if (!fe::make_basis_1d(order, q1d, &b))
+    return fe::set_error(FE_ERR_ARG, "fe_basis_1d: order must be 1..8 and q1d 1..10");
+  const int D = b.D, Q = b.Q;
+  for (int d = 0; d < D; ++d)
+    if (nodes) nodes[d] = b.nodes[d];
+  for (int i = 0; i < Q; ++i) {
+    if (pts) pts[i] = b.pts[i];
+    if (wts) wts[i] = b.wts[i];
+    for (int d = 0; d < D; ++d) {
+      if (B) B[i * D + d] = b.B[i * D + d];
+      if (G) G[i * D + d] = b.G[i * D + d];
+    }
+  }
+  return FE_OK;
+}

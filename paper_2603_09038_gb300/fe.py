@@ -60,6 +60,7 @@ _SIGS = {
     "fe_mesh_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)]),
     "fe_mesh_ndofs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "fe_basis_1d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fe_mesh_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_mesh_dof_map": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pa_setup": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
@@ -197,6 +198,17 @@ def fe_mesh_sizes(mesh):
     nd, ne, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
     _check(lib.fe_mesh_sizes(_VP(mesh), ctypes.byref(nd), ctypes.byref(ne), ctypes.byref(p)))
     return nd.value, ne.value, p.value
+
+
+def fe_basis_1d(order, q1d):
+    """(nodes[D], pts[Q], wts[Q], B[Q, D], G[Q, D]) of the library's 1D tables (host only)."""
+    D, Q = int(order) + 1, int(q1d)
+    nodes, pts, wts = np.zeros(max(D, 1)), np.zeros(max(Q, 1)), np.zeros(max(Q, 1))
+    B, G = np.zeros((max(Q, 1), max(D, 1))), np.zeros((max(Q, 1), max(D, 1)))
+    _check(load().fe_basis_1d(int(order), int(q1d), nodes.ctypes.data_as(_VP),
+                              pts.ctypes.data_as(_VP), wts.ctypes.data_as(_VP),
+                              B.ctypes.data_as(_VP), G.ctypes.data_as(_VP)))
+    return nodes, pts, wts, B, G
 
 
 def fe_mesh_ndofs(mesh):
