@@ -20,7 +20,8 @@ the first on tiny meshes (brute-force agreement) and as the timed CPU baseline.
 ``solve.py`` holds CG / preconditioned CG and the Chebyshev polynomial preconditioner,
 ``mlp.py`` the learned preconditioner's network (forward, loss, backpropagation), and
 ``varorder.py`` the variable-order space: the constraint operator P of Eq. (1) under the
-minimum rule, its Jacobi diagonal and operator.
+minimum rule, its Jacobi diagonal and operator; ``mixed.py`` the paper's own mixed H1/L2
+gradient / divergence pair (Eq. (block-mult)'s off-diagonal blocks).
 
 Parity status of every function is pinned by the ``-m "not gpu"`` tests in ``tests/``:
 closed-form 1D rules, textbook element matrices, volume, null space, symmetry, exact polynomial
