@@ -98,16 +98,19 @@ int fe_mesh_setup(int nx, int ny, int nz, int order, const double* host_vertices
 int fe_basis_1d(int order, int q1d, double* nodes, double* pts, double* wts, double* B,
                 double* G);
 
-/* Sizes of a mesh: global dofs (incl. boundary), elements, order. */
+/* Sizes of a mesh: global dofs (incl. boundary; the L-vector length of Eq. (1)), elements,
+ * order. */
 int fe_mesh_sizes(const fe_mesh* mesh, int64_t* ndofs, int64_t* nelems, int* order);
 
 /* Global dofs of a mesh (incl. boundary); the first output of fe_mesh_sizes. */
 int fe_mesh_ndofs(const fe_mesh* mesh, int64_t* ndofs);
 
-/* Copies the boundary-dof mask (uint8 [ndofs], 1 on the cube's boundary lattice) to dev_mask. */
+/* Copies the boundary-dof mask (uint8 [ndofs], 1 on the cube's boundary lattice) to dev_mask:
+ * the essential-condition set of the solvers (the paper is silent; homogeneous Dirichlet). */
 int fe_mesh_boundary_mask(const fe_mesh* mesh, uint8_t* dev_mask, void* stream);
 
-/* Copies the element dof map (int32 [ne][D^3]) to dev_map. */
+/* Copies the element dof map (int32 [ne][D^3]) to dev_map: the index gather of G in Eq. (1),
+ * the indirect reads of Section III-G. */
 int fe_mesh_dof_map(const fe_mesh* mesh, int32_t* dev_map, void* stream);
 
 /* Partial assembly (Section II-B: the block-diagonal D at the quadrature points is evaluated once
@@ -121,7 +124,8 @@ int fe_mesh_dof_map(const fe_mesh* mesh, int32_t* dev_map, void* stream);
 int fe_pa_setup(const fe_mesh* mesh, int q1d, const double* dev_coeff, int ops, void* stream,
                 fe_pa** out);
 
-/* Selects the arithmetic of subsequent applies, diagonal-free; stream-ordered.  Switching to or
+/* Selects the arithmetic of subsequent applies (Sections III-B/F: FMA or DMMA; float-float and
+ * FP32 are extensions), diagonal-free; stream-ordered.  Switching to or
  * from FE_VARIANT_F32X2 re-encodes the stored quadrature data in place. */
 int fe_pa_set_variant(fe_pa* pa, int variant, void* stream);
 int fe_pa_get_variant(const fe_pa* pa, int* variant);
@@ -136,7 +140,9 @@ int fe_pa_get_variant(const fe_pa* pa, int* variant);
 int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, double* ms,
                    void* stream);
 
-/* y = A x on the full L-vector (no boundary conditions), with the handle's variant.
+/* y = A x = G^T B^T D B G x on the full L-vector (Eq. (1) with P the identity; B by sum
+ * factorisation, Eq. (2); one fused kernel, Section III-G), no boundary conditions, with the
+ * handle's variant.
  * Overwrites y (it is zeroed, then accumulated by atomic scatter-add).  Asynchronous. */
 int fe_apply_diffusion(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream);
 int fe_apply_mass(const fe_pa* pa, const double* dev_x, double* dev_y, void* stream);
@@ -152,17 +158,20 @@ int fe_apply(const fe_pa* pa, int op, int variant, const double* dev_x, double* 
 int fe_apply_batched(const fe_pa* pa, int op, int variant, int nrhs, const double* dev_x,
                      int64_t ldx, double* dev_y, int64_t ldy, void* stream);
 
-/* diag(A) (no boundary conditions) by a sum-factorised diagonal kernel in FP64 (with
+/* diag(A) of Eq. (1)'s operator (the Jacobi diagonal; the paper is silent on solvers), no
+ * boundary conditions, by a sum-factorised diagonal kernel in FP64 (with
  * FE_VARIANT_F32X2 data, each stored pair is widened to FP64 first).  Asynchronous. */
 int fe_assemble_diagonal(const fe_pa* pa, int op, double* dev_diag, void* stream);
 
-/* Load vector of the manufactured problem -div grad u = f, u = sin(pi x) sin(pi y) sin(pi z):
+/* Test problem (the paper is silent): load vector of -div grad u = f, u = sin(pi x) sin(pi y)
+ * sin(pi z):
  * b_a = sum_e sum_q w_q det J f(x_q) phi_a(x_q), f = 3 pi^2 u, with the operator's Gauss rule.
  * Asynchronous. */
 int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 
-/* Jacobi- (or un-, or Chebyshev-) preconditioned CG for A_bc x = b with homogeneous Dirichlet conditions on the
- * mesh boundary: A_bc = (1-m) A (1-m) + m (m = boundary mask).  b's boundary entries are
+/* The solver around Eq. (1)'s operator (the paper is silent; the time-to-solution metric):
+ * Jacobi- (or un-, or Chebyshev-, or learned-) preconditioned CG for A_bc x = b with homogeneous
+ * Dirichlet conditions on the mesh boundary: A_bc = (1-m) A (1-m) + m (m = boundary mask).  b's boundary entries are
  * ignored; x is overwritten (zero initial guess; x = 0 on the boundary).  Stops when the
  * recursive residual satisfies ||r||_2 <= rtol ||b||_2 or after maxit iterations.  FP64 vectors
  * and deterministic FP64 inner products; applies use the handle's variant.  Work vectors are
@@ -189,12 +198,14 @@ int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, double lmin_rat
                      const double* dev_b, double* dev_x, double rtol, int maxit,
                      fe_pcg_stats* stats, void* stream);
 
-/* Largest-eigenvalue estimate of D^-1 A_bc (D = diag(A), boundary rows and columns removed):
+/* Largest-eigenvalue estimate of D^-1 A_bc for the Chebyshev preconditioner (an extension;
+ * D = diag(A), boundary rows and columns removed):
  * `iters` power steps (0..1000) from a fixed pseudo-random start, then the generalised Rayleigh
  * quotient (v.Av)/(v.Dv) of the last iterate, a lower bound of lambda_max.  Synchronous. */
 int fe_estimate_lmax(fe_pa* pa, int op, int iters, double* lmax, void* stream);
 
-/* fe_pcg (Jacobi / none) enqueues its iterations in batches of 8 between two reads of the
+/* CUDA-graph replay of fe_pcg's iterations (an extension).  fe_pcg (Jacobi / none) enqueues its
+ * iterations in batches of 8 between two reads of the
  * device-resident stop flag.  By default the first batch is launched kernel by kernel and the
  * next ones are one captured CUDA graph of 8 iterations replayed with a single launch each
  * (captured on a private stream, so any caller stream works; if the capture fails, the kernels
