@@ -62,8 +62,13 @@ typedef enum { FE_PC_NONE = 0, FE_PC_JACOBI = 1, FE_PC_CHEBYSHEV = 2, FE_PC_LEAR
  *  FE_VARIANT_F32X2   FP64-accurate float-float ("double-FP32") arithmetic on the FP32 pipe:
  *                     each value is an unevaluated sum hi + lo of two floats (about 47 bits of
  *                     significand), products and sums by error-free transformations (Dekker's
- *                     product with FMA, Knuth's TwoSum).  Inputs must lie within the float
- *                     exponent range (|v| < 3e38; values below ~1e-22 lose relative accuracy).
+ *                     product with FMA, Knuth's TwoSum).  Power-of-two scales make it cover the
+ *                     whole FP64 range: each thread block's gathered inputs are scaled so that
+ *                     the largest lies in [1, 2), each element's quadrature data likewise (the
+ *                     scale is stored with the float-pair copy), and both scales are undone when
+ *                     the results are widened to FP64.  Inputs below 2^-126 times the largest
+ *                     input of their block, and FP64 subnormals, count as zero (relative effect
+ *                     below 1e-38 of the block's scale).
  *  FE_VARIANT_F64_DMMA FP64 with the 1D contractions on the FP64 tensor-core instruction
  *                     mma.sync.m8n8k4.f64 (the paper's DMMA, Section III-B).
  *  FE_VARIANT_F32     plain FP32 arithmetic on an FP32 copy of the quadrature data (made on
@@ -79,7 +84,8 @@ typedef enum {
 typedef struct {
   int iters;             /* iterations performed                                              */
   double rel_resid;      /* recursive ||r||_2 / ||b||_2 at exit                               */
-  double true_rel_resid; /* ||b - A x||_2 / ||b||_2 recomputed at exit (FP64 variant apply)  */
+  double true_rel_resid; /* ||b - A x||_2 / ||b||_2 recomputed at exit with FE_VARIANT_F64 (FP64
+                            quadrature data and FP64 arithmetic), whatever variant iterated */
   double seconds;        /* host wall time of the call, including the diagonal assembly       */
   int launches;          /* kernels of this library launched by the call (no-op ones included) */
   int outer_iters;       /* refinement steps (fe_pcg_ir); 1 for fe_pcg                        */
@@ -125,8 +131,11 @@ int fe_pa_setup(const fe_mesh* mesh, int q1d, const double* dev_coeff, int ops, 
                 fe_pa** out);
 
 /* Selects the arithmetic of subsequent applies (Sections III-B/F: FMA or DMMA; float-float and
- * FP32 are extensions), diagonal-free; stream-ordered.  Switching to or
- * from FE_VARIANT_F32X2 re-encodes the stored quadrature data in place. */
+ * FP32 are extensions).  The FP64 quadrature data are always kept (the FP64 residuals of the
+ * solvers and the diagonal read them); the first selection of FE_VARIANT_F32X2 adds a
+ * float-pair copy (same size, plus one int32 scale exponent per element), the first selection
+ * of FE_VARIANT_F32 an FP32 copy (half the size, shifted by a power of two into the float
+ * range); both are kept until fe_pa_destroy.  Synchronous when a copy is made. */
 int fe_pa_set_variant(fe_pa* pa, int variant, void* stream);
 int fe_pa_get_variant(const fe_pa* pa, int* variant);
 
@@ -174,10 +183,12 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
  * Dirichlet conditions on the mesh boundary: A_bc = (1-m) A (1-m) + m (m = boundary mask).  b's boundary entries are
  * ignored; x is overwritten (zero initial guess; x = 0 on the boundary).  Stops when the
  * recursive residual satisfies ||r||_2 <= rtol ||b||_2 or after maxit iterations.  FP64 vectors
- * and deterministic FP64 inner products; applies use the handle's variant.  Work vectors are
- * allocated on first use and cached in the handle.  Synchronous; fills *stats (may be NULL).
- * Returns FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN or FE_ERR_NAN (x holds the last
- * iterate in every case). */
+ * and deterministic FP64 inner products (p.Ap included, accumulated in FP64 inside the fused
+ * apply from the FP64 results it scatters); applies use the handle's variant, which must be
+ * FP64-accurate (FE_ERR_UNSUPPORTED for FE_VARIANT_F32); the exit true residual uses the FP64
+ * operator.  Work vectors are allocated on first use and cached in the handle.  Synchronous;
+ * fills *stats (may be NULL).  Returns FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN or
+ * FE_ERR_NAN (x holds the last iterate in every case). */
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
 
@@ -215,16 +226,19 @@ int fe_pcg_set_graphs(fe_pa* pa, int enable);
 
 /* Mixed-precision iterative refinement around an FP32 inner PCG (an extension; the paper
  * itself stays in FP64 throughout).  Outer loop, in FP64 vectors:
- *   r = (1-m)(b - A x)   with the handle's FP64-accurate operator (FE_VARIANT_F64, or
- *                        FE_VARIANT_F32X2 when the data is pair-encoded);
+ *   r = (1-m)(b - A x)   with the FP64 operator (FE_VARIANT_F64: FP64 data and arithmetic);
  *   solve A_bc d = r     by PCG (pc) with the FE_VARIANT_F32 operator to inner_rtol * ||r||
- *                        (0 => 1e-2, the fastest setting measured on the 64^3 p=3 problem);
+ *                        (0 => 1e-2, the fastest setting measured on the 64^3 p=3 problem), on
+ *                        FP32 vectors, with r scaled by a power of two to norm ~1 (so that the
+ *                        shrinking residual never leaves the float range) and the result
+ *                        scaled back exactly;
  *   x += d,
- * from x = 0 until ||r||_2 <= rtol ||b||_2 (checked with the FP64-accurate residual, so the
- * result meets the same residual criterion as fe_pcg).  maxit bounds the total inner iterations.
- * The FP32 copy of the quadrature data is made on first use.  stats: iters = inner iterations,
- * outer_iters = refinement steps, rel_resid = true_rel_resid = final FP64-accurate residual.
- * Returns FE_ERR_NOT_CONVERGED also when a refinement step fails to reduce the residual. */
+ * from x = 0 until ||r||_2 <= rtol ||b||_2 (checked on the FP64 residual, so the result meets
+ * the same residual criterion as fe_pcg).  maxit bounds the total inner iterations.  The
+ * handle's variant is not used.  The FP32 copy of the quadrature data is made on first use.
+ * stats: iters = inner iterations, outer_iters = refinement steps, rel_resid = true_rel_resid =
+ * final FP64 residual.  Returns FE_ERR_NOT_CONVERGED also when a refinement step fails to reduce
+ * the residual. */
 int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
               double inner_rtol, fe_pcg_stats* stats, void* stream);
 
@@ -254,9 +268,16 @@ int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double* dev_b, int
  * allocating routine (the fe_pa must already exist: fe_pa_setup does allocate).
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *    that device current and caches it; make that first call before any stream capture.
+ *    A cudaDeviceReset unloads the library's device image with the context, so the cached
+ *    address is stale afterwards: do not call this entry point again in that process after a
+ *    reset of that device.
  *  - All calls share the one array, which keeps the last call's contents (the call clears what
  *    must start at zero).  Calls whose GPU work overlaps -- on two streams, or from two host
  *    threads -- race on it and give wrong results: serialise them.
+ *  - Like fe_pcg it needs an FP64-accurate variant (FE_ERR_UNSUPPORTED for FE_VARIANT_F32); its
+ *    p.Ap comes from a separate FP64 dot-product pass instead of the apply's fused partials (those
+ *    would need one more allocated array per handle), and its exit residual uses the FP64
+ *    operator.
  * Synchronous, like fe_pcg. */
 #define FE_PCG_NOALLOC_MAX_DOFS 262144
 int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x,
@@ -382,11 +403,11 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
            int maxit, fe_pcg_stats* stats, void* stream);
 
 /* Mixed-precision iterative refinement with the learned preconditioner (the two extensions
- * combined): outer steps r = (1-m)(b - A x) with the handle's FP64-accurate operator
- * (FE_VARIANT_F32X2 or FE_VARIANT_F64 per the stored data) in FP64 vectors; inner flexible CG on
- * FP32 vectors with the FP32 apply (FP32 copy of the quadrature data, made on first use) and lpc
- * applied to FP32 vectors, to inner_rtol * ||r|| (0 => 1e-2); x += d; until ||r|| <= rtol ||b||,
- * checked on the FP64-accurate residual.  lpc must have width 0, 64 or 128 (FE_ERR_UNSUPPORTED
+ * combined): outer steps r = (1-m)(b - A x) with the FP64 operator (FE_VARIANT_F64) in FP64
+ * vectors; inner flexible CG on FP32 vectors with the FP32 apply (FP32 copy of the quadrature
+ * data, made on first use) and lpc applied to FP32 vectors, on r scaled by a power of two to
+ * norm ~1, to inner_rtol * ||r|| (0 => 1e-2); x += d (scaled back exactly); until
+ * ||r|| <= rtol ||b||, checked on the FP64 residual.  lpc must have width 0, 64 or 128 (FE_ERR_UNSUPPORTED
  * otherwise).  stats: iters = inner iterations, outer_iters = refinement steps, rel_resid =
  * true_rel_resid = the final FP64-accurate residual.  FE_ERR_NOT_CONVERGED also when a
  * refinement step fails to reduce the residual.  Allocates 2 FP64 and 7 FP32 vectors per call. */

@@ -192,7 +192,7 @@ struct EltSmem {
 __global__ void __launch_bounds__(kEltThreads) k_diagonal(const int32_t* __restrict__ map,
                                                           const double* __restrict__ qd,
                                                           int64_t ne, int D, int Q, int diff,
-                                                          int pairs, const Tables tab,
+                                                          const Tables tab,
                                                           double* __restrict__ diag) {
   __shared__ EltSmem sm;
   const int Q2 = Q * Q, Q3 = Q2 * Q, D3 = D * D * D, QD = Q * D;
@@ -207,14 +207,7 @@ __global__ void __launch_bounds__(kEltThreads) k_diagonal(const int32_t* __restr
         const int qx = t % Q, qy = (t / Q) % Q, qz = t / Q2;
         const int64_t idx = diff ? e * 6 * Q3 + (int64_t)qz * 6 * Q2 + m * Q2 + qy * Q + qx
                                  : e * Q3 + t;
-        double v;
-        if (pairs) {  // float-pair encoded data: widen hi + lo
-          const float2 hl = reinterpret_cast<const float2*>(qd)[idx];
-          v = (double)hl.x + (double)hl.y;
-        } else {
-          v = qd[idx];
-        }
-        sm.F[t] = scale * v;
+        sm.F[t] = scale * qd[idx];
       }
       for (int t = threadIdx.x; t < QD; t += blockDim.x) {
         double f[3];
@@ -323,11 +316,10 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
     if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr)
       return set_error(FE_ERR_ARG, "fe_apply: no FP32 quadrature data; call "
                                    "fe_pa_set_variant(FE_VARIANT_F32) first");
-  } else {
-    const bool pairs = (variant == FE_VARIANT_F32X2);
-    if (pairs != (pa->qd_format == FE_VARIANT_F32X2))
-      return set_error(FE_ERR_ARG, "fe_apply: variant does not match the stored quadrature data "
-                                   "encoding; call fe_pa_set_variant first");
+  } else if (variant == FE_VARIANT_F32X2) {
+    if ((op == FE_DIFFUSION ? pa->d_qd_diff2 : pa->d_qd_mass2) == nullptr)
+      return set_error(FE_ERR_ARG, "fe_apply: no float-pair quadrature data; call "
+                                   "fe_pa_set_variant(FE_VARIANT_F32X2) first");
   }
   if (nrhs < 1 || (nrhs > 1 && (ldx < m->ndofs || ldy < m->ndofs)))
     return set_error(FE_ERR_ARG, "fe_apply: nrhs >= 1 and ldx, ldy >= ndofs required");
@@ -346,10 +338,15 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
     return set_error(FE_ERR_UNSUPPORTED, "fe_apply: the DMMA kernel has no fused dot product");
   ApplyArgs a;
   a.map = m->d_map;
-  if (variant == FE_VARIANT_F32)
+  if (variant == FE_VARIANT_F32) {
     a.qd = reinterpret_cast<const double*>(op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32);
-  else
+    a.qshift = pa->qd32_shift[op == FE_DIFFUSION ? 0 : 1];
+  } else if (variant == FE_VARIANT_F32X2) {
+    a.qd = (op == FE_DIFFUSION) ? pa->d_qd_diff2 : pa->d_qd_mass2;
+    a.qscale = (op == FE_DIFFUSION) ? pa->d_qs_diff : pa->d_qs_mass;
+  } else {
     a.qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
+  }
   a.x = x;
   a.y = y;
   a.ne = m->ne;
@@ -580,45 +577,41 @@ int fe_pa_set_variant(fe_pa* pa, int variant, void* stream) {
       variant != FE_VARIANT_F32)
     return set_error(FE_ERR_ARG, "fe_pa_set_variant: unknown variant");
   cudaStream_t s = (cudaStream_t)stream;
+  const int64_t ne = pa->mesh->ne;
+  const int64_t nq = ne * (int64_t)pa->Q * pa->Q * pa->Q;
+  cudaError_t err = cudaSuccess;
   if (variant == FE_VARIANT_F32) {
-    // FP32 copy of the quadrature data next to the FP64 (or pair) data, made once
-    const int64_t nq = pa->mesh->ne * (int64_t)pa->Q * pa->Q * pa->Q;
-    const bool pairs = (pa->qd_format == FE_VARIANT_F32X2);
-    cudaError_t err = cudaSuccess;
+    // FP32 copy of the FP64 quadrature data (shifted into the float range), made once
     if (pa->d_qd_diff && !pa->d_qd_diff32) {
       err = cudaMalloc(&pa->d_qd_diff32, sizeof(float) * 6 * nq);
       if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
-      const int st = make_qd_f32(pa->d_qd_diff, pa->d_qd_diff32, 6 * nq, pairs, s);
+      const int st = make_qd_f32(pa->d_qd_diff, pa->d_qd_diff32, 6 * nq, &pa->qd32_shift[0], s);
       if (st != FE_OK) return st;
     }
     if (pa->d_qd_mass && !pa->d_qd_mass32) {
       err = cudaMalloc(&pa->d_qd_mass32, sizeof(float) * nq);
       if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
-      const int st = make_qd_f32(pa->d_qd_mass, pa->d_qd_mass32, nq, pairs, s);
+      const int st = make_qd_f32(pa->d_qd_mass, pa->d_qd_mass32, nq, &pa->qd32_shift[1], s);
       if (st != FE_OK) return st;
     }
-    pa->variant = variant;
-    return FE_OK;
-  }
-  const bool want_pairs = (variant == FE_VARIANT_F32X2);
-  const bool have_pairs = (pa->qd_format == FE_VARIANT_F32X2);
-  if (want_pairs && !have_pairs) {
-    const int64_t nq = pa->mesh->ne * (int64_t)pa->Q * pa->Q * pa->Q;
-    int st = encode_f32x2(pa->d_qd_diff, pa->d_qd_diff ? 6 * nq : 0, true, s);
-    if (st == FE_OK) st = encode_f32x2(pa->d_qd_mass, pa->d_qd_mass ? nq : 0, true, s);
-    if (st != FE_OK) return st;
-    pa->qd_format = FE_VARIANT_F32X2;
-  } else if (!want_pairs && have_pairs) {
-    // recompute the exact FP64 data rather than widen the pairs (which would lose bits)
-    int* d_bad = nullptr;
-    FE_CHECK_CUDA(cudaMalloc(&d_bad, sizeof(int)), "fe_pa_set_variant: cudaMalloc");
-    cudaMemsetAsync(d_bad, 0, sizeof(int), s);
-    int st = compute_qdata(pa, pa->d_coeff, s, d_bad);
-    cudaError_t err = cudaStreamSynchronize(s);
-    cudaFree(d_bad);
-    if (st != FE_OK) return st;
-    if (err != cudaSuccess) return cuda_error(err, "fe_pa_set_variant");
-    pa->qd_format = FE_VARIANT_F64;
+  } else if (variant == FE_VARIANT_F32X2) {
+    // float-pair copy with per-element scales next to the FP64 data, made once
+    if (pa->d_qd_diff && !pa->d_qd_diff2) {
+      if ((err = cudaMalloc(&pa->d_qd_diff2, sizeof(double) * 6 * nq)) != cudaSuccess ||
+          (err = cudaMalloc(&pa->d_qs_diff, sizeof(int32_t) * (ne > 0 ? ne : 1))) != cudaSuccess)
+        return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
+      const int st = encode_f32x2(pa->d_qd_diff, pa->d_qd_diff2, pa->d_qs_diff, ne,
+                                  6 * pa->Q * pa->Q * pa->Q, s);
+      if (st != FE_OK) return st;
+    }
+    if (pa->d_qd_mass && !pa->d_qd_mass2) {
+      if ((err = cudaMalloc(&pa->d_qd_mass2, sizeof(double) * nq)) != cudaSuccess ||
+          (err = cudaMalloc(&pa->d_qs_mass, sizeof(int32_t) * (ne > 0 ? ne : 1))) != cudaSuccess)
+        return cuda_error(err, "fe_pa_set_variant: cudaMalloc");
+      const int st = encode_f32x2(pa->d_qd_mass, pa->d_qd_mass2, pa->d_qs_mass, ne,
+                                  pa->Q * pa->Q * pa->Q, s);
+      if (st != FE_OK) return st;
+    }
   }
   pa->variant = variant;
   return FE_OK;
@@ -733,7 +726,6 @@ int diagonal_accumulate(const fe_pa* pa, int op, double* dev_diag, cudaStream_t 
   const double* qd = (op == FE_DIFFUSION) ? pa->d_qd_diff : pa->d_qd_mass;
   k_diagonal<<<elem_grid(m->ne), kEltThreads, 0, s>>>(m->d_map, qd, m->ne, pa->D, pa->Q,
                                                       op == FE_DIFFUSION ? 1 : 0,
-                                                      pa->qd_format == FE_VARIANT_F32X2 ? 1 : 0,
                                                       make_tables(pa->basis), dev_diag);
   return cuda_error(cudaGetLastError(), "diagonal kernel launch");
 }
@@ -759,6 +751,10 @@ void fe_pa_destroy(fe_pa* pa) {
   cudaFree(pa->d_qd_diff);
   cudaFree(pa->d_qd_mass);
   cudaFree(pa->d_coeff);
+  cudaFree(pa->d_qd_diff2);
+  cudaFree(pa->d_qd_mass2);
+  cudaFree(pa->d_qs_diff);
+  cudaFree(pa->d_qs_mass);
   cudaFree(pa->d_qd_diff32);
   cudaFree(pa->d_qd_mass32);
   cudaFree(pa->d_work);

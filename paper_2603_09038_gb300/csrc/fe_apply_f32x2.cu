@@ -17,27 +17,36 @@ int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s) {
   return dispatch_order<ArF32x2>(op, a, s);
 }
 
-// In-place re-encoding of FP64 quadrature data as (hi, lo) float pairs and back.  The pair is
-// produced on the host-independent path: hi = round-to-nearest float of v, lo = float of the
-// remainder v - hi (exact in FP64), so hi + lo carries ~48 significant bits.
-__global__ void k_encode_f32x2(double* __restrict__ data, int64_t n, int to_pairs) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    if (to_pairs) {
-      const double v = data[i];
-      const float h = __double2float_rn(v);
-      const float l = __double2float_rn(v - (double)h);
-      reinterpret_cast<float2*>(data)[i] = make_float2(h, l);
-    } else {
-      const float2 p = reinterpret_cast<const float2*>(data)[i];
-      data[i] = (double)p.x + (double)p.y;
+// Float-pair copy of the FP64 quadrature data, one warp per element: the element's largest
+// biased exponent e_max gives its scale s = e_max - 1023 (0 for an all-zero element), and each
+// entry v becomes the pair hi = rn(v 2^-s), lo = rn(v 2^-s - hi) (v 2^-s exact in FP64), so
+// the element's largest entry lies in [1, 2) and hi + lo carries ~48 significant bits whatever
+// the magnitude of the coefficient.
+__global__ void k_encode_f32x2(const double* __restrict__ src, double* __restrict__ dst,
+                               int32_t* __restrict__ scale, int64_t ne, int per_elem) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; e < ne;
+       e += warps) {
+    const double* v = src + e * per_elem;
+    int emax = 0;
+    for (int i = lane; i < per_elem; i += 32) emax = max(emax, f64_exponent(v[i]));
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    const int sc = emax > 0 ? emax - 1023 : 0;
+    if (lane == 0) scale[e] = sc;
+    float2* out = reinterpret_cast<float2*>(dst + e * per_elem);
+    for (int i = lane; i < per_elem; i += 32) {
+      const double w = ldexp(v[i], -sc);
+      const float h = __double2float_rn(w);
+      out[i] = make_float2(h, __double2float_rn(w - (double)h));
     }
   }
 }
 
-int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s) {
-  if (n == 0 || data == nullptr) return FE_OK;
-  k_encode_f32x2<<<4 * 152, 256, 0, s>>>(data, n, to_pairs ? 1 : 0);
+int encode_f32x2(const double* src, double* dst, int32_t* scale, int64_t ne, int per_elem,
+                 cudaStream_t s) {
+  if (ne == 0 || src == nullptr) return FE_OK;
+  k_encode_f32x2<<<8 * 152, 256, 0, s>>>(src, dst, scale, ne, per_elem);
   return cuda_error(cudaGetLastError(), "encode_f32x2 launch");
 }
 

@@ -21,6 +21,8 @@
 // contraction in registers, one (qx, qy) column per thread.
 #pragma once
 
+#include <type_traits>
+
 #include "fe_arith.cuh"
 #include "fe_smem_layout.h"
 
@@ -70,7 +72,8 @@ template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MI
           bool MULTI>
 __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
                                                  const typename Ar::QdT* __restrict__ qd,
-                                                 const VT* __restrict__ x0,
+                                                 const int32_t* __restrict__ qscale,
+                                                 int qshift, const VT* __restrict__ x0,
                                                  VT* __restrict__ y0, int64_t ne,
                                                  const int* __restrict__ skip,
                                                  double* __restrict__ dot_part, int nrhs,
@@ -95,6 +98,8 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   const int nel = (int)((ne - e0) < NE ? (ne - e0) : NE);
   const int tid = threadIdx.x;
   auto dacc = Ar::dot_zero();
+  // scaled policies: per-warp largest biased FP64 exponent of the gathered inputs
+  __shared__ int wexp[NT / 32];
 
   // Several right-hand sides (x0 + r ldx -> y0 + r ldy) are applied one after the other by the
   // same block: after the first, the block's dof map and quadrature data come from L2.
@@ -104,14 +109,36 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   VT* __restrict__ y = y0 + rhs * ldy;
   if (rhs > 0) __syncthreads();  // the previous scatter has read its last bufB value
 
-  // ---- gather (G): E0[i][j*D + k] = x[map[e][i + D j + D^2 k]]
-  for (int t = tid; t < nel * D3; t += NT) {
-    const int el = t / D3, a = t - el * D3;
-    const int i = a % D, j = (a / D) % D, k = a / D2;
-    const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-    bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_vec(__ldg(&x[g]));
+  // ---- gather (G): E0[i][j*D + k] = x[map[e][i + D j + D^2 k]].  Scaled policies keep the
+  //      FP64 value in the slot (same 8 bytes) and note its exponent; the x phase converts it
+  //      with the block's scale 2^(1023 - largest exponent).
+  if constexpr (Ar::kScaled) {
+    int emax = 0;
+    for (int t = tid; t < nel * D3; t += NT) {
+      const int el = t / D3, a = t - el * D3;
+      const int i = a % D, j = (a / D) % D, k = a / D2;
+      const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
+      const double v = __ldg(&x[g]);
+      reinterpret_cast<double*>(bufA)[el * SZ_A + i * S_DD + j * D + k] = v;
+      emax = max(emax, f64_exponent(v));
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((tid & 31) == 0) wexp[tid >> 5] = emax;
+  } else {
+    for (int t = tid; t < nel * D3; t += NT) {
+      const int el = t / D3, a = t - el * D3;
+      const int i = a % D, j = (a / D) % D, k = a / D2;
+      const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
+      bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_vec(__ldg(&x[g]));
+    }
   }
   __syncthreads();
+  int xexp = 1023;  // biased exponent that the scaled inputs map to 2^0
+  if constexpr (Ar::kScaled) {
+    xexp = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) xexp = max(xexp, wexp[w]);
+  }
 
   // ---- x phase: contract i -> qx.  line (j, k); out T1c[j][k*Q + qx], c = (B x, G x)
   for (int t = tid; t < nel * D2; t += NT) {
@@ -122,7 +149,10 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
     float m = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      v[i] = in[i * S_DD];
+      if constexpr (Ar::kScaled)
+        v[i] = Ar::from_raw(reinterpret_cast<const double*>(in)[i * S_DD], 1023 - xexp);
+      else
+        v[i] = in[i * S_DD];
       m = Ar::amax(m, v[i]);
     }
     const auto sb = Ar::sigB(tab, m, false);
@@ -420,13 +450,23 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   }
   __syncthreads();
 
-  // ---- scatter-add (G^T); optionally the block's share of x^T A x = sum_e x_e . (A_e x_e)
+  // ---- scatter-add (G^T); optionally the block's share of x^T A x = sum_e x_e . (A_e x_e),
+  //      accumulated from the FP64 inputs and the FP64 results that are scattered
   for (int t = tid; t < nel * D3; t += NT) {
     const int el = t / D3, a = t - el * D3;
     const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
     const T v = bufB[el * SZ_B + a];
-    Ar::scatter(&y[g], v);
-    if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), v);
+    if constexpr (std::is_same<VT, float>::value) {
+      Ar::scatter(&y[g], v);
+      if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), v);
+    } else {
+      // scaled policies: undo the input scale and the element's quadrature-data scale; FP32
+      // data: undo its global shift
+      const int off = Ar::kScaled ? (xexp - 1023) + __ldg(&qscale[e0 + el]) : qshift;
+      const double vd = Ar::widen(v, off);
+      atomicAdd(&y[g], vd);
+      if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), vd);
+    }
   }
   }  // right-hand sides
   if (dot_part != nullptr) {  // (single right-hand side only)  // deterministic block reduction (fixed shuffle tree, warp order)

@@ -154,8 +154,10 @@ int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   const int64_t nblk = (a.ne + NE - 1) / NE;
   if (a.blocks) *a.blocks = nblk;
   if (nblk == 0 || a.query_only) return FE_OK;
+  if (Ar::kScaled && a.qscale == nullptr)
+    return set_error(FE_ERR_ARG, "apply: float-pair quadrature data without its scales");
   kern<<<(unsigned int)nblk, NT, smem, s>>>(a.map, reinterpret_cast<const typename Ar::QdT*>(a.qd),
-                                            reinterpret_cast<const VT*>(a.x),
+                                            a.qscale, a.qshift, reinterpret_cast<const VT*>(a.x),
                                             reinterpret_cast<VT*>(a.y), a.ne, a.skip, a.dot_part,
                                             a.nrhs, a.ldx, a.ldy, tab);
   return cuda_error(cudaGetLastError(), "apply kernel launch");

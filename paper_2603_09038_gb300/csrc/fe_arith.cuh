@@ -58,6 +58,7 @@ struct TabF32 {
 // ---------------------------------------------------------------------------- policies
 struct ArF64 {
   static constexpr bool kAnchored = false;
+  static constexpr bool kScaled = false;  // inputs converted as they are gathered
   using QdT = double;
   using T = double;
   using Acc = double;
@@ -104,11 +105,12 @@ struct ArF64 {
   static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
     return fma(a2, x2, fma(a1, x1, a0 * x0));
   }
-  static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, v); }
+  // FP64 value of a result (no scaling in this policy)
+  static __device__ __forceinline__ double widen(T v, int) { return v; }
   // accumulation of the fused x . (A x): FP64
   using DotAcc = double;
   static __device__ __forceinline__ DotAcc dot_zero() { return 0.0; }
-  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) { a = fma(x, v, a); }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, double v) { a = fma(x, v, a); }
   static __device__ __forceinline__ double dot_value(DotAcc a) { return a; }
 };
 
@@ -117,6 +119,11 @@ struct ArF64 {
 template <bool ANCHORED, bool LAZY>
 struct ArF32x2T {
   static constexpr bool kAnchored = ANCHORED;
+  // Inputs are gathered as FP64 and converted with a power-of-two scale per thread block (its
+  // largest input in [1, 2)); the quadrature data carry a power-of-two scale per element (the
+  // element's largest entry in [1, 2)); results are widened with both scales undone.  So the
+  // arithmetic is FP64-accurate for inputs anywhere in the FP64 range, not only the float range.
+  static constexpr bool kScaled = true;
   using QdT = double;  // 8-byte (hi, lo) float pairs
   using T = f2;
   using Acc = Anch;
@@ -126,6 +133,10 @@ struct ArF32x2T {
 
   static __device__ __forceinline__ T zero() { return f2{0.0f, 0.0f}; }
   static __device__ __forceinline__ T from_vec(double v) { return f2_from_f64(v); }
+  // v * 2^off as a pair (off from the block's largest input exponent)
+  static __device__ __forceinline__ T from_raw(double v, int off) {
+    return f2_from_f64_scaled(v, off);
+  }
   // quadrature data is stored pre-split: the 8 bytes of each entry hold (h, l)
   static __device__ __forceinline__ T load_qd(const double* p) {
     const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
@@ -205,18 +216,16 @@ struct ArF32x2T {
     anch_mad(acc, a2.h, a2.l, x2);
     return end(acc, sg);
   }
-  static __device__ __forceinline__ void scatter(double* y, T v) {
-    atomicAdd(y, (double)v.h + (double)v.l);
+  // FP64 value of a result times 2^off: both words widened exactly by integer manipulation
+  // (no FP64-pipe conversion), then one exact FP64 add (h + l needs at most 49 bits)
+  static __device__ __forceinline__ double widen(T v, int off) {
+    return f64_from_f32_scaled(v.h, off) + f64_from_f32_scaled(v.l, off);
   }
-  // accumulation of the fused x . (A x): compensated float-float on the FP32 pipe (FP64-class
-  // accuracy without FP64 instructions per term), widened once per thread
-  using DotAcc = f2;
-  static __device__ __forceinline__ DotAcc dot_zero() { return f2{0.0f, 0.0f}; }
-  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) {
-    const f2 xf = f2_from_f64(x);
-    f2_mad(a, xf.h, xf.l, v);
-  }
-  static __device__ __forceinline__ double dot_value(DotAcc a) { return (double)a.h + (double)a.l; }
+  // accumulation of the fused x . (A x): FP64, on the FP64 inputs and the widened results
+  using DotAcc = double;
+  static __device__ __forceinline__ DotAcc dot_zero() { return 0.0; }
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, double v) { a = fma(x, v, a); }
+  static __device__ __forceinline__ double dot_value(DotAcc a) { return a; }
 };
 
 using ArF32x2 = ArF32x2T<true, false>;
@@ -225,6 +234,7 @@ using ArF32x2 = ArF32x2T<true, false>;
 // (half the bytes), FP32 FMAs; FP64 vectors in and out, converted by integer manipulation.
 struct ArF32 {
   static constexpr bool kAnchored = false;
+  static constexpr bool kScaled = false;
   using QdT = float;
   using T = float;
   using Acc = float;
@@ -269,13 +279,13 @@ struct ArF32 {
   static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
     return fmaf(a2, x2, fmaf(a1, x1, a0 * x0));
   }
-  static __device__ __forceinline__ void scatter(double* y, T v) { atomicAdd(y, f64_from_f32(v)); }
+  static __device__ __forceinline__ double widen(T v, int) { return f64_from_f32(v); }
   static __device__ __forceinline__ void scatter(float* y, T v) { atomicAdd(y, v); }
   // accumulation of the fused x . (A x): FP32 (the inner solves need no more)
   using DotAcc = float;
   static __device__ __forceinline__ DotAcc dot_zero() { return 0.0f; }
-  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, T v) {
-    a = fmaf(f2_from_f64(x).h, v, a);
+  static __device__ __forceinline__ void dot_acc(DotAcc& a, double x, double v) {
+    a = fmaf(f2_from_f64(x).h, f2_from_f64(v).h, a);
   }
   static __device__ __forceinline__ void dot_acc(DotAcc& a, float x, T v) { a = fmaf(x, v, a); }
   static __device__ __forceinline__ double dot_value(DotAcc a) { return f64_from_f32(a); }

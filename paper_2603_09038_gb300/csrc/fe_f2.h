@@ -147,6 +147,68 @@ FE_HD f2 f2_from_f64(double v) {
   return f2{h, f_from_bits(f_bits(l) | sign)};
 }
 
+// Biased FP64 exponent field of v (0 for zero and subnormals, 2047 for inf / NaN).
+FE_HD int f64_exponent(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  return (int)((b >> 52) & 0x7FFu);
+}
+
+// Split of v * 2^off into floats, by integer manipulation of the encodings like f2_from_f64.
+// The apply kernels call it with off = 1023 - (the largest biased exponent of a block's
+// inputs), so that the block's largest input lands in [1, 2) and the whole FP64 exponent range
+// maps into the float range.  Scaled values below 2^-126 (relative 2^-126 to the block's
+// largest) become zero, those below 2^-80 keep a high word only; FP64 zeros and subnormals
+// become zero; inf / NaN stay inf / NaN.
+FE_HD f2 f2_from_f64_scaled(double v, int off) {
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const uint32_t sign = hw & 0x80000000u;
+  const int ex = (int)((hw >> 20) & 0x7FFu);
+  if (ex == 0x7FF) {  // inf or NaN
+    const uint32_t nan = ((hw & 0xFFFFFu) | lw) ? 0x00400000u : 0u;
+    return f2{f_from_bits(sign | 0x7F800000u | nan), 0.0f};
+  }
+  const int es = ex + off;     // biased FP64 exponent of the scaled value
+  const int fexp = es - 896;   // its biased float exponent
+  if (ex == 0 || fexp <= 0) return f2{f_from_bits(sign), 0.0f};
+  if (fexp >= 255) return f2{f_from_bits(sign | 0x7F800000u), 0.0f};
+  const uint32_t mant = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  const float h = f_from_bits(sign | ((uint32_t)fexp << 23) | mant);
+  if (es < 943) return f2{h, 0.0f};
+  const uint32_t rem = (lw & 0x1FFFFFFFu) >> 6;
+  const float r = f_sub(f_from_bits(0x4B000000u | rem), 8388608.0f);
+  const float l = f_mul(r, f_from_bits((uint32_t)(es - 942) << 23));
+  return f2{h, f_from_bits(f_bits(l) | sign)};
+}
+
+// Exact widening of a float times 2^off to a double by integer manipulation (no FP64-pipe
+// conversion): zero and float subnormals map to a signed zero, inf / NaN to inf / NaN, results
+// below the FP64 normal range to zero and above it to inf.
+FE_HD double f64_from_f32_scaled(float a, int off) {
+  const uint32_t u = f_bits(a);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const int e = (int)((u >> 23) & 0xFFu);
+  uint64_t bits;
+  if (e == 0) {
+    bits = sign;
+  } else if (e == 0xFF) {
+    bits = sign | ((uint64_t)0x7FF << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+  } else {
+    const int ed = e + 896 + off;
+    if (ed <= 0)
+      bits = sign;
+    else if (ed >= 0x7FF)
+      bits = sign | ((uint64_t)0x7FF << 52);
+    else
+      bits = sign | ((uint64_t)ed << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+  }
+  double d;
+  std::memcpy(&d, &bits, 8);
+  return d;
+}
+
 // Exact widening of a float to a double by integer manipulation (no FP64-pipe conversion):
 // normal floats only; zero and subnormals map to a signed zero, inf/NaN to inf/NaN.
 FE_HD double f64_from_f32(float a) {

@@ -56,13 +56,22 @@ struct fe_pa {
   const fe_mesh* mesh = nullptr;   // not owned; must outlive the fe_pa
   int p = 0, D = 0, Q = 0, ops = 0;
   int variant = FE_VARIANT_F64;
-  int qd_format = FE_VARIANT_F64;  // encoding of the stored quadrature data
   fe::Basis1D basis;
+  // FP64 quadrature data, always kept (FE_VARIANT_F64, DMMA, the diagonal and every FP64
+  // residual of the solvers read it)
   double* d_qd_diff = nullptr;     // [ne][Q][6][Q][Q] (qz, component, qy, qx)
   double* d_qd_mass = nullptr;     // [ne][Q][Q][Q]
   double* d_coeff = nullptr;       // [ne] copy of the coefficient (nullptr => 1)
-  float* d_qd_diff32 = nullptr;    // FP32 copy for FE_VARIANT_F32 (made on first use)
-  float* d_qd_mass32 = nullptr;
+  // FE_VARIANT_F32X2 copy (made on first use): per element e, the entries times 2^-s_e as
+  // (hi, lo) float pairs in the same layout, s_e in d_qs_* (the element's largest entry times
+  // 2^-s_e lies in [1, 2))
+  double* d_qd_diff2 = nullptr;
+  double* d_qd_mass2 = nullptr;
+  int32_t* d_qs_diff = nullptr;    // [ne]
+  int32_t* d_qs_mass = nullptr;    // [ne]
+  float* d_qd_diff32 = nullptr;    // FP32 copy for FE_VARIANT_F32 (made on first use), times
+  float* d_qd_mass32 = nullptr;    // 2^-qd32_shift[op] (its largest entry in [1, 2))
+  int qd32_shift[2] = {0, 0};      // diffusion, mass
   // PCG workspace (allocated on first fe_pcg, freed by fe_pa_destroy)
   double* d_work = nullptr;        // 5 vectors of ndofs
   double* d_red = nullptr;         // reduction partials + scalars
@@ -81,6 +90,8 @@ namespace fe {
 struct ApplyArgs {
   const int32_t* map;
   const double* qd;      // FP64 or float-pair encoded, per variant
+  const int32_t* qscale = nullptr;  // per-element scale exponents of float-pair data
+  int qshift = 0;        // FP32 data: results on FP64 vectors are scaled by 2^qshift
   const double* x;
   double* y;
   int64_t ne;
@@ -100,13 +111,17 @@ int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_dmma(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32_vec32(int op, const ApplyArgs& a, cudaStream_t s);
-int make_qd_f32(const double* src, float* dst, int64_t n, bool pairs, cudaStream_t s);
+// FP32 copy of n FP64 quadrature values times 2^-*shift, *shift chosen so that the largest
+// lies in [1, 2) (the copy then spans the float range whatever the coefficient's magnitude).
+int make_qd_f32(const double* src, float* dst, int64_t n, int* shift, cudaStream_t s);
 
 // diag += the element diagonals of op scattered through the element map (no zeroing; atomic).
 int diagonal_accumulate(const fe_pa* pa, int op, double* diag, cudaStream_t s);
 
-// Re-encodes n FP64 values in place as float pairs (hi, lo) or back.
-int encode_f32x2(double* data, int64_t n, bool to_pairs, cudaStream_t s);
+// Float-pair copy of FP64 quadrature data: per element (per_elem values each) the scale
+// exponent s_e of its largest entry and the entries times 2^-s_e as (hi, lo) pairs.
+int encode_f32x2(const double* src, double* dst, int32_t* scale, int64_t ne, int per_elem,
+                 cudaStream_t s);
 
 // y = A x (y zeroed first unless skip is given; with skip the caller zeroes y).  skip:
 // optional device flag, nonzero => no-op.  dot_part: optional per-block partials of x^T A x

@@ -32,6 +32,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "fe_f2.h"
 #include "fe_internal.h"
 #include "fe_mlp.cuh"
 
@@ -801,8 +802,8 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
   }
   res->rel = rel;
   if constexpr (F64) {
-    if (st == FE_OK) {  // true residual with the handle's operator
-      if ((st = apply_dispatch(pa, op, pa->variant, x, q, s)) == FE_OK) {
+    if (st == FE_OK) {  // true residual with the FP64 operator (FP64 data and arithmetic)
+      if ((st = apply_dispatch(pa, op, FE_VARIANT_F64, x, q, s)) == FE_OK) {
         k_fcg_resid<<<kRB, kT, 0, s>>>(b, q, mask, n, part0, part1);
         k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
         res->launches += 3;
@@ -841,16 +842,20 @@ __global__ void k_add_f64(double* __restrict__ x, const double* __restrict__ d, 
     x[i] += d[i];
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+// b = a * 2^shift rounded to float (the power-of-two scale is exact in FP64)
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n,
+                         int shift) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+    b[i] = __double2float_rn(ldexp(a[i], shift));
 }
 
-__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n) {
+// x += d * 2^shift (exact widening and scaling by integer manipulation)
+__global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, int64_t n,
+                          int shift) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)d[i];
+    x[i] += fe::f64_from_f32_scaled(d[i], shift);
 }
 
 // Training data (first call of fe_lpc_train): probing, Cholesky, residual snapshots, samples.
@@ -885,7 +890,8 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
   if (el.empty())
     return set_error(FE_ERR_ARG, "fe_lpc_train: mesh too small (needs >= 3 elements per axis)");
   const int ns = (int)el.size();
-  const int hi = (L->pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  // probe applies with an FP64-accurate operator: the handle's float-float one when selected
+  const int hi = (L->pa->variant == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
   int32_t* d_el = nullptr;
   double *v = nullptr, *w = nullptr, *Aee = nullptr, *snapbuf = nullptr;
   int* d_fail = nullptr;
@@ -1145,7 +1151,11 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
     if ((st = fe_pa_set_variant(pa, FE_VARIANT_F32, stream)) != FE_OK) return st;
     pa->variant = saved;
   }
-  const int hi = (pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  // The outer residual is FP64 (FP64 data and arithmetic).  The inner solves run on
+  // A32 = 2^-s A (the FP32 data carry the shift s that puts them in the float range) with the
+  // right-hand side r 2^-e (e the exponent of ||r||, so that it stays in the float range as the
+  // refinement shrinks r); their solution d32 = A32^-1 r 2^-e gives d = 2^(e - s) d32.
+  const int qs = pa->qd32_shift[op == FE_DIFFUSION ? 0 : 1];
   const fe_mesh* m = pa->mesh;
   const int64_t n = m->ndofs;
   double *dv = nullptr, *red = nullptr;
@@ -1162,9 +1172,9 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
   float *r32 = fv, *x32 = fv + n, *d32 = fv + 2 * n, *work32 = fv + 3 * n;
   double *part0 = red, *part1 = red + kRB, *sc = red + 2 * kRB;
   int launches = 0, outer = 0, inner_total = 0, restarts = 0;
-  double rel = 1.0;
-  auto outer_residual = [&]() -> int {  // rr = (1-m)(b - A x) with the FP64-accurate operator
-    int st2 = apply_dispatch(pa, op, hi, dev_x, q, s);
+  double rel = 1.0, rnorm = 0.0;
+  auto outer_residual = [&]() -> int {  // rr = (1-m)(b - A x) with the FP64 operator
+    int st2 = apply_dispatch(pa, op, FE_VARIANT_F64, dev_x, q, s);
     if (st2 != FE_OK) return st2;
     k_ir_resid<<<kRB, kT, 0, s>>>(dev_b, q, m->d_mask, rr, n, part0, part1);
     k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
@@ -1176,12 +1186,13 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
       return cuda_error(e, "fe_fcg_ir: residual");
     rel = hsc[S_BB] > 0.0 ? sqrt(hsc[S_TRUE] / hsc[S_BB]) : 0.0;
+    rnorm = sqrt(hsc[S_TRUE]);
     return FE_OK;
   };
   int state = FE_ERR_NOT_CONVERGED;
   st = cuda_error(cudaMemsetAsync(dev_x, 0, sizeof(double) * n, s), "fe_fcg_ir: zero x");
   if (st == FE_OK) {
-    k_to_f32<<<grid1(n), kT, 0, s>>>(lpc->dinv, d32, n);
+    k_to_f32<<<grid1(n), kT, 0, s>>>(lpc->dinv, d32, n, qs);  // inverse diagonal of A32
     ++launches;
     st = outer_residual();
   }
@@ -1191,7 +1202,9 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
       state = FE_ERR_NAN;
       break;
     }
-    k_to_f32<<<grid1(n), kT, 0, s>>>(rr, r32, n);
+    int e = 0;
+    std::frexp(rnorm, &e);
+    k_to_f32<<<grid1(n), kT, 0, s>>>(rr, r32, n, -e);
     ++launches;
     FcgResult in;
     st = fcg_run<float>(pa, op, lpc, d32, r32, x32, inner_rtol, maxit - inner_total, nullptr, s,
@@ -1205,7 +1218,7 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
       state = in.status;
       break;
     }
-    k_add_f32<<<grid1(n), kT, 0, s>>>(dev_x, x32, n);
+    k_add_f32<<<grid1(n), kT, 0, s>>>(dev_x, x32, n, e - qs);
     ++launches;
     const double prev = rel;
     if ((st = outer_residual()) != FE_OK) break;
@@ -1285,7 +1298,7 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   if (st == FE_OK) {
     k_invert_diag<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, m->d_mask, m->ndofs);
     k_sqrt_vec<<<grid1(m->ndofs), kT, 0, s>>>(L->dinv, L->dis, L->wsq, L->fsc, m->ndofs);
-    k_to_f32<<<grid1(m->ndofs), kT, 0, s>>>(L->fsc, L->fsc32, m->ndofs);
+    k_to_f32<<<grid1(m->ndofs), kT, 0, s>>>(L->fsc, L->fsc32, m->ndofs, 0);
     err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) st = cuda_error(err, "fe_lpc_create");
@@ -1482,6 +1495,9 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
   if (lpc && (lpc->pa != pa || lpc->op != op))
     return set_error(FE_ERR_ARG, "fe_fcg: preconditioner built for another operator");
   if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_fcg: bad rtol or maxit");
+  if (pa->variant == FE_VARIANT_F32)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_fcg: the FP32 variant is not FP64-accurate; select "
+                                         "FE_VARIANT_F64, F32X2 or F64_DMMA (or use fe_fcg_ir)");
   cudaStream_t s = (cudaStream_t)stream;
   const fe_mesh* m = pa->mesh;
   double* dinv = lpc ? lpc->dinv : nullptr;
@@ -1515,7 +1531,7 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
     }
     double *q = buf, *r = buf + n, *d = buf + 2 * n;
     double hsc[S_N];
-    st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
+    st = apply_dispatch(pa, op, FE_VARIANT_F64, dev_x, q, s);  // FP64 residual
     if (st == FE_OK) {
       cudaMemsetAsync(red + 2 * kRB, 0, sizeof(double) * S_N, s);
       k_ir_resid<<<kRB, kT, 0, s>>>(dev_b, q, m->d_mask, r, n, red, red + kRB);

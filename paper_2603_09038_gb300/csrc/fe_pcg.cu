@@ -119,8 +119,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish_pq_var(const double* 
     sc[S_ALPHA] = sc[S_RZ] / pq;
 }
 
-// Per-dof inner-product terms accumulated in compensated float-float on the FP32 pipe (FP64-class
-// accuracy; GB300's FP64 pipe would make two DFMAs per dof the bottleneck of this pass).
+// x += alpha p, r -= alpha (1-m) q, z = D^-1 r; the r.z and r.r partials, accumulated in FP64.
 
 __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ x,
                                                            double* __restrict__ r,
@@ -134,7 +133,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
                                                            const int* flags) {
   if (flags[F_STATE] != ST_RUN) return;
   const double alpha = sc[S_ALPHA];
-  fe::f2 s_rz{0.0f, 0.0f}, s_rr{0.0f, 0.0f};
+  double s_rz = 0.0, s_rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool bnd = mask[i] != 0;
@@ -144,10 +143,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_update(double* __restrict__ 
     r[i] = ri;
     const double zi = d ? ri * d[i] : (bnd ? 0.0 : ri);
     z[i] = zi;
-    f2_acc_prod(s_rz, ri, zi);
-    f2_acc_prod(s_rr, ri, ri);
+    s_rz = fma(ri, zi, s_rz);
+    s_rr = fma(ri, ri, s_rr);
   }
-  block_sum2((double)s_rz.h + (double)s_rz.l, (double)s_rr.h + (double)s_rr.l, part0, part1);
+  block_sum2(s_rz, s_rr, part0, part1);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish_update(const double* part0,
@@ -241,16 +240,16 @@ __global__ void __launch_bounds__(kReduceThreads) k_cheb_first(const double* __r
                                                                double inv_theta, double* part0,
                                                                const int* flags, int with_dot) {
   if (flags[F_STATE] != ST_RUN) return;
-  fe::f2 acc{0.0f, 0.0f};
+  double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double ri = r[i];
     const double di = dinv[i] * ri * inv_theta;
     dv[i] = di;
     z[i] = di;
-    if (with_dot) f2_acc_prod(acc, ri, di);
+    if (with_dot) acc = fma(ri, di, acc);
   }
-  if (with_dot) block_sum2((double)acc.h + (double)acc.l, 0.0, part0, nullptr);
+  if (with_dot) block_sum2(acc, 0.0, part0, nullptr);
 }
 
 // step j: d = c1 d + c2 dinv (r - A z), z += d, and q2 (= A z, scatter target) zeroed for the
@@ -263,7 +262,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_cheb_step(const double* __re
                                                               double c1, double c2, double* part0,
                                                               const int* flags, int with_dot) {
   if (flags[F_STATE] != ST_RUN) return;
-  fe::f2 acc{0.0f, 0.0f};
+  double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double ri = r[i];
@@ -272,9 +271,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_cheb_step(const double* __re
     const double zi = z[i] + di;
     z[i] = zi;
     q2[i] = 0.0;
-    if (with_dot) f2_acc_prod(acc, ri, zi);
+    if (with_dot) acc = fma(ri, zi, acc);
   }
-  if (with_dot) block_sum2((double)acc.h + (double)acc.l, 0.0, part0, nullptr);
+  if (with_dot) block_sum2(acc, 0.0, part0, nullptr);
 }
 
 // x += alpha p, r -= alpha (1-m) q; the r.r partials (into part1)
@@ -287,16 +286,16 @@ __global__ void __launch_bounds__(kReduceThreads) k_update_xr(double* __restrict
                                                               double* part1, const int* flags) {
   if (flags[F_STATE] != ST_RUN) return;
   const double alpha = sc[S_ALPHA];
-  fe::f2 acc{0.0f, 0.0f};
+  double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double qi = mask[i] ? 0.0 : q[i];
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, qi, r[i]);
     r[i] = ri;
-    f2_acc_prod(acc, ri, ri);
+    acc = fma(ri, ri, acc);
   }
-  block_sum2((double)acc.h + (double)acc.l, 0.0, part1, nullptr);
+  block_sum2(acc, 0.0, part1, nullptr);
 }
 
 // initial r.z of the Chebyshev-preconditioned start; beta = 0 so that k_pupdate sets p = z
@@ -450,26 +449,27 @@ __global__ void __launch_bounds__(kReduceThreads) k_pupdate32(float* __restrict_
   }
 }
 
-// dst = (float) src (the outer residual as the inner right-hand side), and the FP32 inverse
-// diagonal when given.
+// dst = src * 2^sshift as float (the outer residual as the inner right-hand side), and the FP32
+// inverse diagonal d64 * 2^dshift when given (power-of-two scales: exact before the rounding).
 __global__ void __launch_bounds__(kReduceThreads) k_to32(const double* __restrict__ src,
-                                                         float* __restrict__ dst,
+                                                         float* __restrict__ dst, int sshift,
                                                          const double* __restrict__ d64,
-                                                         float* __restrict__ d32, int64_t n) {
+                                                         float* __restrict__ d32, int dshift,
+                                                         int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    dst[i] = fe::f2_from_f64(src[i]).h;
-    if (d32) d32[i] = (float)d64[i];
+    dst[i] = __double2float_rn(ldexp(src[i], sshift));
+    if (d32) d32[i] = __double2float_rn(ldexp(d64[i], dshift));
   }
 }
 
-// x += (double) dx
+// x += dx * 2^shift (exact widening and scaling by integer manipulation)
 __global__ void __launch_bounds__(kReduceThreads) k_axpy32(double* __restrict__ x,
                                                            const float* __restrict__ dx,
-                                                           int64_t n) {
+                                                           int64_t n, int shift) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += fe::f64_from_f32(dx[i]);
+    x[i] += fe::f64_from_f32_scaled(dx[i], shift);
 }
 
 }  // namespace
@@ -632,10 +632,10 @@ int pcg_run(fe_pa* pa, int op, int variant, const double* b, double* x, const do
 }
 
 // ||(1-m)(b - A x)|| / ||b|| with the given variant (q is overwritten); also stores the
-// residual in rout when given.
+// residual in rout when given, and its norm in *rnorm when given.
 int pcg_true_residual(const fe_pa* pa, int op, int variant, const double* b, const double* x,
                       double* rout, const PcgWork& w, cudaStream_t s, int* launches,
-                      double* rel) {
+                      double* rel, double* rnorm = nullptr) {
   const int64_t n = pa->mesh->ndofs;
   int st = apply_dispatch(pa, op, variant, x, w.q, s);
   if (st != FE_OK) return st;
@@ -651,6 +651,7 @@ int pcg_true_residual(const fe_pa* pa, int op, int variant, const double* b, con
       (err = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_error(err, "fe_pcg: residual");
   *rel = hsc[S_TRUE];
+  if (rnorm) *rnorm = hsc[S_TRUE] * std::sqrt(hsc[S_BB]);
   return FE_OK;
 }
 
@@ -869,6 +870,15 @@ int pcg_check_args(const fe_pa* pa, int op, int pc, const double* b, const doubl
   return FE_OK;
 }
 
+// Solvers that iterate with the handle's variant need an FP64-accurate one.
+int pcg_check_variant(const fe_pa* pa, const char* who) {
+  if (pa->variant == FE_VARIANT_F32)
+    return set_error(FE_ERR_UNSUPPORTED, std::string(who) + ": the FP32 variant is not "
+                                         "FP64-accurate; select FE_VARIANT_F64, F32X2 or "
+                                         "F64_DMMA (or use fe_pcg_ir)");
+  return FE_OK;
+}
+
 
 }  // namespace
 
@@ -886,6 +896,7 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
   const auto t0 = std::chrono::steady_clock::now();
   if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   int st = pcg_check_args(pa, op, pc, dev_b, dev_x, rtol, maxit, "fe_pcg");
+  if (st == FE_OK) st = pcg_check_variant(pa, "fe_pcg");
   if (st != FE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   PcgWork w;
@@ -895,8 +906,8 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
   st = pcg_run(pa, op, pa->variant, dev_b, dev_x, pc == FE_PC_JACOBI ? w.d : nullptr, rtol, maxit,
                w, s, &res);
   if (st != FE_OK) return st;
-  double true_rel = 0.0;
-  if ((st = pcg_true_residual(pa, op, pa->variant, dev_b, dev_x, nullptr, w, s, &res.launches,
+  double true_rel = 0.0;  // with the FP64 operator whatever the iteration's variant
+  if ((st = pcg_true_residual(pa, op, FE_VARIANT_F64, dev_b, dev_x, nullptr, w, s, &res.launches,
                               &true_rel)) != FE_OK)
     return st;
   if (stats) {
@@ -922,8 +933,11 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
   if (!(inner_rtol > 0.0 && inner_rtol < 1.0))
     return set_error(FE_ERR_ARG, "fe_pcg_ir: inner_rtol must lie in (0, 1)");
   cudaStream_t s = (cudaStream_t)stream;
-  // the accurate operator of the outer residual: the handle's FP64-accurate encoding
-  const int hi = (pa->qd_format == FE_VARIANT_F32X2) ? FE_VARIANT_F32X2 : FE_VARIANT_F64;
+  // The outer residual is FP64 (FP64 data and arithmetic).  The inner solves run on
+  // A32 = 2^-qs A (the FP32 data carry the shift qs that puts them in the float range) with
+  // the right-hand side r 2^-e (e the exponent of ||r||, so that it stays in the float range as
+  // the refinement shrinks r); their solution d32 = A32^-1 r 2^-e gives d = 2^(e - qs) d32.
+  const int hi = FE_VARIANT_F64;
   if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr) {
     const int saved = pa->variant;
     if ((st = fe_pa_set_variant(pa, FE_VARIANT_F32, stream)) != FE_OK) return st;
@@ -944,8 +958,10 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
   cudaError_t err;
   if ((err = cudaMemsetAsync(dev_x, 0, sizeof(double) * n, s)) != cudaSuccess)
     return cuda_error(err, "fe_pcg_ir: zero x");
-  double rel = 1.0;
-  if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel)) != FE_OK)
+  const int qs = pa->qd32_shift[op == FE_DIFFUSION ? 0 : 1];
+  double rel = 1.0, rnorm = 0.0;
+  if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel, &rnorm)) !=
+      FE_OK)
     return st;
   int outer = 0, inner_total = 0, state = (rel <= rtol) ? ST_CONV : ST_RUN;
   bool dinv_ready = false;
@@ -954,11 +970,11 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
       state = ST_NAN;
       break;
     }
-    // inner FP32 solve of A dx = r to inner_rtol relative to ||r||
-    k_to32<<<kReduceBlocks, kReduceThreads, 0, s>>>(rr, b32, w.d,
-                                                    (pc == FE_PC_JACOBI && !dinv_ready) ? v.dinv
-                                                                                        : nullptr,
-                                                    n);
+    // inner FP32 solve of A32 d32 = r 2^-e to inner_rtol relative to its right-hand side
+    int e = 0;
+    std::frexp(rnorm, &e);
+    k_to32<<<kReduceBlocks, kReduceThreads, 0, s>>>(
+        rr, b32, -e, w.d, (pc == FE_PC_JACOBI && !dinv_ready) ? v.dinv : nullptr, qs, n);
     dinv_ready = true;
     res.launches += 1;
     PcgResult in;
@@ -976,11 +992,12 @@ extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double*
       state = ST_BREAK;
       break;
     }
-    k_axpy32<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, v.x, n);
+    k_axpy32<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_x, v.x, n, e - qs);
     if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_ir: update launch");
     res.launches += 1;
     const double prev = rel;
-    if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel)) != FE_OK)
+    if ((st = pcg_true_residual(pa, op, hi, dev_b, dev_x, rr, w, s, &res.launches, &rel,
+                                &rnorm)) != FE_OK)
       return st;
     if (rel <= rtol)
       state = ST_CONV;
@@ -1051,6 +1068,8 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
   if (pc != FE_PC_NONE && pc != FE_PC_JACOBI)
     return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad preconditioner");
   if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_pcg_noalloc: bad rtol or maxit");
+  int st = pcg_check_variant(pa, "fe_pcg_noalloc");
+  if (st != FE_OK) return st;
   const fe_mesh* m = pa->mesh;
   const int64_t n = m->ndofs;
   if (n > kNoAllocMaxDofs)
@@ -1058,7 +1077,7 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
                                      " dofs, more than the fixed scratch holds (" +
                                      std::to_string(kNoAllocMaxDofs) + "); use fe_pcg");
   double* base = nullptr;
-  int st = noalloc_scratch(&base);
+  st = noalloc_scratch(&base);
   if (st != FE_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   double* r = base;
@@ -1126,7 +1145,7 @@ extern "C" int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev
       return cuda_error(err, "fe_pcg_noalloc: iteration");
     if (hflags[F_STATE] != ST_RUN || queued >= maxit) break;
   }
-  st = apply_dispatch(pa, op, pa->variant, dev_x, q, s);
+  st = apply_dispatch(pa, op, FE_VARIANT_F64, dev_x, q, s);  // FP64 true residual
   if (st != FE_OK) return st;
   k_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, mask, nullptr, n, part0, part1);
   k_finish_resid<<<1, kFinishThreads, 0, s>>>(part0, part1, sc);
@@ -1190,6 +1209,7 @@ extern "C" int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, doub
   const auto t0 = std::chrono::steady_clock::now();
   if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   int st = pcg_check_args(pa, op, FE_PC_JACOBI, dev_b, dev_x, rtol, maxit, "fe_pcg_chebyshev");
+  if (st == FE_OK) st = pcg_check_variant(pa, "fe_pcg_chebyshev");
   if (st != FE_OK) return st;
   if (degree == 0) degree = kChebDegree;
   if (lmin_ratio == 0.0) lmin_ratio = kChebRatio;
@@ -1216,8 +1236,8 @@ extern "C" int fe_pcg_chebyshev(fe_pa* pa, int op, int degree, double lmax, doub
   if ((st = pcg_run_cheb(pa, op, pa->variant, dev_b, dev_x, w.d, degree, hi / lmin_ratio, hi, rtol,
                          maxit, w, extra, extra + n, s, &res)) != FE_OK)
     return st;
-  double true_rel = 0.0;
-  if ((st = pcg_true_residual(pa, op, pa->variant, dev_b, dev_x, nullptr, w, s, &res.launches,
+  double true_rel = 0.0;  // with the FP64 operator whatever the iteration's variant
+  if ((st = pcg_true_residual(pa, op, FE_VARIANT_F64, dev_b, dev_x, nullptr, w, s, &res.launches,
                               &true_rel)) != FE_OK)
     return st;
   if (stats) {

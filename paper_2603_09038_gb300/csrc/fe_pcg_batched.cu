@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_binit(const double* __restri
   const double* b = B + j * ldb;
   double* x = X + j * ldx;
   double *r = R + j * n, *z = Z + j * n, *p = P + j * n, *q = Q + j * n;
-  fe::f2 s_rz{0.0f, 0.0f}, s_bb{0.0f, 0.0f};
+  double s_rz = 0.0, s_bb = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double bi = mask[i] ? 0.0 : b[i];
@@ -54,11 +54,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_binit(const double* __restri
     z[i] = zi;
     p[i] = zi;
     q[i] = 0.0;
-    f2_acc_prod(s_rz, bi, zi);
-    f2_acc_prod(s_bb, bi, bi);
+    s_rz = fma(bi, zi, s_rz);
+    s_bb = fma(bi, bi, s_bb);
   }
-  block_sum2((double)s_rz.h + (double)s_rz.l, (double)s_bb.h + (double)s_bb.l,
-             part0 + j * kReduceBlocks, part1 + j * kReduceBlocks);
+  block_sum2(s_rz, s_bb, part0 + j * kReduceBlocks, part1 + j * kReduceBlocks);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_bfinish_init(const double* part0,
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_bupdate(double* __restrict__
   double* x = X + j * ldx;
   double *r = R + j * n, *z = Z + j * n;
   const double *p = P + j * n, *q = Q + j * n;
-  fe::f2 s_rz{0.0f, 0.0f}, s_rr{0.0f, 0.0f};
+  double s_rz = 0.0, s_rr = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const bool bnd = mask[i] != 0;
@@ -146,11 +145,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_bupdate(double* __restrict__
     r[i] = ri;
     const double zi = dinv ? ri * dinv[i] : (bnd ? 0.0 : ri);
     z[i] = zi;
-    f2_acc_prod(s_rz, ri, zi);
-    f2_acc_prod(s_rr, ri, ri);
+    s_rz = fma(ri, zi, s_rz);
+    s_rr = fma(ri, ri, s_rr);
   }
-  block_sum2((double)s_rz.h + (double)s_rz.l, (double)s_rr.h + (double)s_rr.l,
-             part0 + j * kReduceBlocks, part1 + j * kReduceBlocks);
+  block_sum2(s_rz, s_rr, part0 + j * kReduceBlocks, part1 + j * kReduceBlocks);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_bfinish_update(const double* part0,
@@ -273,6 +271,8 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
   if (nrhs < 1 || nrhs > 1024 || ldb < n || ldx < n)
     return set_error(FE_ERR_ARG, "fe_pcg_batched: need 1 <= nrhs <= 1024 and ldb, ldx >= ndofs");
   if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_pcg_batched: bad rtol or maxit");
+  if (pa->variant == FE_VARIANT_F32)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_pcg_batched: the FP32 variant is not FP64-accurate");
   if (stats)
     for (int j = 0; j < nrhs; ++j) stats[j] = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
   cudaStream_t s = (cudaStream_t)stream;
@@ -360,18 +360,11 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
     }
     queued += count;
   }
-  // true residuals: Q = A X (batched), per-system norms
-  if (batched_apply) {
-    if ((st = apply_dispatch(pa, op, variant, dev_x, Q, s, nullptr, nullptr, nullptr, false, nrhs,
-                             ldx, n)) != FE_OK)
-      return st;
-    ++launches;
-  } else {
-    for (int j = 0; j < nrhs; ++j) {
-      if ((st = apply_dispatch(pa, op, variant, dev_x + j * ldx, Q + j * n, s)) != FE_OK) return st;
-      ++launches;
-    }
-  }
+  // true residuals with the FP64 operator: Q = A X (one batched launch), per-system norms
+  if ((st = apply_dispatch(pa, op, FE_VARIANT_F64, dev_x, Q, s, nullptr, nullptr, nullptr, false,
+                           nrhs, ldx, n)) != FE_OK)
+    return st;
+  ++launches;
   k_bresid<<<grid2, kReduceThreads, 0, s>>>(dev_b, ldb, Q, m->d_mask, n, part0, part1);
   k_bfinish_resid<<<nrhs, kFinishThreads, 0, s>>>(part0, part1, sc);
   launches += 2;

@@ -1,6 +1,6 @@
 // Shared pieces of the CG solvers (fe_pcg.cu, fe_pcg_batched.cu): deterministic block
-// reductions, the float-float accumulation of FP64 products, the device-state conventions and
-// the CUDA-graph capture of an iteration batch.  Included into an anonymous namespace of each
+// reductions of FP64 partials, the device-state conventions and the CUDA-graph capture of an
+// iteration batch.  Included into an anonymous namespace of each
 // solver translation unit.
 #pragma once
 
@@ -68,11 +68,6 @@ __device__ __forceinline__ double ordered_sum(const double* part) {
   return t;
 }
 
-
-__device__ __forceinline__ void f2_acc_prod(fe::f2& acc, double a, double b) {
-  const fe::f2 af = fe::f2_from_f64(a), bf = fe::f2_from_f64(b);
-  fe::f2_mad(acc, af.h, af.l, bf);
-}
 
 // One batch of PCG iterations captured as a CUDA graph (on a private stream: the caller's may be
 // the legacy stream, which cannot be captured) and replayed on the caller's stream with one

@@ -944,14 +944,12 @@ int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, v
   return cuda_error(cudaGetLastError(), "fe_vspace_prolong: launch");
 }
 
-int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
-                    void* stream) {
-  clear_error();
-  if (!vs || !dev_x || !dev_y) return set_error(FE_ERR_ARG, "fe_vspace_apply: null argument");
-  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_apply: bad op");
-  if (!(vs->ops & op))
-    return set_error(FE_ERR_ARG, "fe_vspace_apply: operator not set up in fe_vspace_setup");
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// y = E^T blockdiag(A_e) E x with the given variant (-1: each order's selected variant).
+int vspace_apply(const fe_vspace* vs, int op, int variant, const double* dev_x, double* dev_y,
+                 cudaStream_t s) {
   int st = fill_X(vs, dev_x, s);
   if (st != FE_OK) return st;
   cudaError_t err =
@@ -959,10 +957,24 @@ int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* de
   if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: zero Y");
   for (int g = 0; g < vs->ngroups; ++g) {
     const fe_pa* pa = vs->group_pa[g];
-    if ((st = apply_dispatch(pa, op, pa->variant, vs->d_X, vs->d_Y, s, vs->d_zero)) != FE_OK)
+    if ((st = apply_dispatch(pa, op, variant < 0 ? pa->variant : variant, vs->d_X, vs->d_Y, s,
+                             vs->d_zero)) != FE_OK)
       return st;
   }
   return fold_Y(vs, dev_y, 0, s);
+}
+}  // namespace
+
+extern "C" {
+
+int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
+                    void* stream) {
+  clear_error();
+  if (!vs || !dev_x || !dev_y) return set_error(FE_ERR_ARG, "fe_vspace_apply: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_apply: bad op");
+  if (!(vs->ops & op))
+    return set_error(FE_ERR_ARG, "fe_vspace_apply: operator not set up in fe_vspace_setup");
+  return vspace_apply(vs, op, -1, dev_x, dev_y, (cudaStream_t)stream);
 }
 
 int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stream) {
@@ -991,6 +1003,9 @@ int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, dou
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_pcg: bad op");
   if (!(vs->ops & op)) return set_error(FE_ERR_ARG, "fe_vspace_pcg: operator not set up");
   if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_vspace_pcg: bad rtol or maxit");
+  for (int g = 0; g < vs->ngroups; ++g)
+    if (vs->group_pa[g]->variant == FE_VARIANT_F32)
+      return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_pcg: the FP32 variant is not FP64-accurate");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = vs->ntrue;
   cudaError_t err = cudaSuccess;
@@ -1058,9 +1073,9 @@ int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, dou
       ++launches;
     }
   }
-  // true residual ||(1-m)(b - A x)|| / ||(1-m) b||
+  // true residual ||(1-m)(b - A x)|| / ||(1-m) b|| with the FP64 operator
   double true_rel = 0.0;
-  if ((st = fe_vspace_apply(vs, op, dev_x, q, stream)) != FE_OK) return st;
+  if ((st = vspace_apply(vs, op, FE_VARIANT_F64, dev_x, q, s)) != FE_OK) return st;
   k_vs_resid<<<kReduceBlocks, kReduceThreads, 0, s>>>(dev_b, q, vs->d_mask, n, part0);
   k_vs_finish<<<1, kFinishThreads, 0, s>>>(part0, part1, sc, 3);
   launches += vs->ngroups + 4;

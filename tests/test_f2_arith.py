@@ -75,7 +75,40 @@ int main() {
     double ec = absum > 0 ? (double)(std::fabs(val(c) - exact) / absum) : 0.0;
     if (ec > worst_comp) worst_comp = ec;
   }
-  std::printf("%.6e %.6e %.6e\n", worst_split, worst_anch, worst_comp);
+  // 4. scaled split of doubles anywhere in the FP64 range: v 2^off with off = 1023 - e_max
+  //    (e_max the biased exponent of a block maximum at or above |v|) reproduces v 2^off to
+  //    2^-46 relative down to 2^-80 below the block maximum, and to 2^-104 of the block scale
+  //    below that (the high word alone); widening back by -off is exact
+  double worst_scaled = 0;
+  int bad_widen = 0;
+  for (int i = 0; i < 200000; ++i) {
+    // block scale 2^eb, kept 2^120 above the FP64 subnormals (flushed to zero by design)
+    const int eb = (int)(rng() % 1800) - 900;
+    const double vmax = std::ldexp(1.0 + 0.5 * std::fabs(U(rng)), eb);
+    const double v = U(rng) * vmax * std::ldexp(1.0, -(int)(rng() % 70));
+    const int off = 1023 - f64_exponent(vmax);
+    f2 s = f2_from_f64_scaled(v, off);
+    const LD target = std::ldexp((LD)v, off);
+    if (v != 0.0) {  // relative to the value, or to 2^-58 of the block scale below that
+      const LD den = std::fmax(std::fabs(target), std::ldexp((LD)1, -58));
+      double rel = (double)(std::fabs(((LD)s.h + (LD)s.l) - target) / den);
+      if (rel > worst_scaled) worst_scaled = rel;
+    }
+    const double back = f64_from_f32_scaled(s.h, -off) + f64_from_f32_scaled(s.l, -off);
+    if ((LD)back != std::ldexp((LD)s.h + (LD)s.l, -off)) ++bad_widen;
+  }
+  // 5. special values: zero and FP64 subnormals give zero; inf and NaN survive; values far
+  //    below the block maximum flush to zero
+  int bad_special = 0;
+  if (f2_from_f64_scaled(0.0, 5).h != 0.0f) ++bad_special;
+  if (f2_from_f64_scaled(4.9e-324, 1000).h != 0.0f) ++bad_special;
+  if (!std::isinf(f2_from_f64_scaled(INFINITY, -1024).h)) ++bad_special;
+  if (!std::isnan(f2_from_f64_scaled(NAN, -1024).h)) ++bad_special;
+  if (f2_from_f64_scaled(std::ldexp(1.0, -200), 0).h != 0.0f) ++bad_special;
+  if (!std::isinf(f64_from_f32_scaled(1.0f, 2000))) ++bad_special;
+  if (f64_from_f32_scaled(1.0f, -2000) != 0.0) ++bad_special;
+  std::printf("%.6e %.6e %.6e %.6e %d %d\n", worst_split, worst_anch, worst_comp, worst_scaled,
+              bad_widen, bad_special);
   return 0;
 }
 '''
@@ -110,3 +143,12 @@ def test_anchored_dot_error_is_below_n_2_pow_minus_46_of_the_anchor(results):
 def test_compensated_dot_error_is_below_n_2_pow_minus_46_of_the_absolute_sum(results):
     # roundings of the low word relative to the largest partial sum, n <= 10 terms
     assert results[2] <= 10 * 2.0 ** -46
+
+
+def test_scaled_split_covers_the_fp64_range(results):
+    # block scales from 2^-900 to 2^900, values down to 2^-70 below the block maximum
+    assert results[3] <= 2.0 ** -46
+
+
+def test_scaled_widening_is_exact_and_special_values_hold(results):
+    assert results[4] == 0 and results[5] == 0
