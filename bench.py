@@ -12,7 +12,8 @@ Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the t
   ms_per_step  time of one PCG solve to 1e-8 (the metric's time-to-solution part);
   e2e          the same, through host buffers: pinned b -> device, fe_pcg, x -> pinned host;
   roofline     of the dominant kernel (the fused apply), timed alone with CUDA events;
-  cpu_baseline the CPU oracle (element-matrix apply) on a bounded sample of the same mesh;
+  cpu_baseline the CPU oracle (sum-factorised FP64 Jacobi-PCG in C/OpenMP) on a bounded sample
+               of PCG iterations of the same workload, on every host core;
   pcg_ir       mixed-precision iterative refinement (FP32 inner PCG) to the same residual;
   pcg_chebyshev  Chebyshev-polynomial preconditioned CG (degree 4) to the same residual;
   learned_fcg  the learned element-patch preconditioner (trained on the GPU from the operator's
@@ -69,6 +70,90 @@ def algorithmic(ndofs, ne, p, q, diffusion=True):
     else:
         f = 4 * (q * D ** 3 + q * q * D * D + q ** 3 * D) + q ** 3
     return nbytes, ne * f
+
+
+def mixed_algorithmic(n, ph=4, pl=3):
+    """Minimum bytes and FP64 flops of one fused application of the mixed pair (gradient and
+    divergence blocks) on n^3 hexes: the 9 quadrature values per point read once, p and u read
+    once, G p and G^T u written once, the H1 dof map once; flops of the sum-factorised
+    contractions (H1 reference gradient forward and transposed, the L2 basis forward and
+    transposed for three components) and the two 3x3 products per point."""
+    Dh, Dl, Q = ph + 1, pl + 1, ph + 1
+    ne = n ** 3
+    nh = (n * ph + 1) ** 3
+    nl = 3 * ne * Dl ** 3
+    nbytes = ne * (9 * Q ** 3 * 8 + 4 * Dh ** 3) + 16 * nh + 16 * nl
+    h1 = 2 * Q * Dh ** 3 + 3 * Q * Q * Dh * Dh + 3 * Q ** 3 * Dh
+    l2 = 3 * (Q * Dl ** 3 + Q * Q * Dl * Dl + Q ** 3 * Dl)
+    fma = 2 * (h1 + l2 + 9 * Q ** 3)
+    return nbytes, 2 * ne * fma, nh, nl
+
+
+def measure_mixed(fe, torch, n, stream, reps=10, ph=4, pl=3):
+    """The paper's own operator (mixed H1 order 4 / L2 order 3 gradient and divergence pair) on
+    n^3 perturbed hexes: the fused launch and each block alone (median of reps, CUDA events),
+    GDOF/s of (H1 + L2) values per fused application, against the FP64-pipe and HBM roofs."""
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    mx = fe.fe_mixed_setup(n, n, n, ph, pl, perturbed_vertices(n, n, n))
+    try:
+        nh, nl = fe.fe_mixed_sizes(mx)
+        g = torch.Generator(device="cuda").manual_seed(2)
+        p = torch.rand(nh, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+        u = torch.rand(nl, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+        gp = torch.empty(nl, dtype=torch.float64, device="cuda")
+        gtu = torch.empty(nh, dtype=torch.float64, device="cuda")
+
+        def timed(a, b, c, d):
+            for _ in range(3):
+                fe.fe_mixed_apply(mx, a, b, c, d, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            torch.cuda.synchronize()
+            for e0, e1 in ev:
+                e0.record(stream)
+                fe.fe_mixed_apply(mx, a, b, c, d, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            return statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
+
+        ms = timed(p, u, gp, gtu)
+        ms_g = timed(p, None, gp, None)
+        ms_d = timed(None, u, None, gtu)
+    finally:
+        fe.fe_mixed_destroy(mx)
+    nbytes, flops, _, _ = mixed_algorithmic(n, ph, pl)
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp64_peak = 152 * FP64_DFMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"workload": "mixed_h1p%d_l2p%d_%dcubed" % (ph, pl, n), "ndof_h1": nh, "ndof_l2": nl,
+            "dofs": nh + nl, "fused_ms": ms, "gradient_only_ms": ms_g, "divergence_only_ms": ms_d,
+            "gdofs_fused": (nh + nl) / (ms * 1e-3) / 1e9,
+            "fusion_speedup": (ms_g + ms_d) / ms, "dtype": "f64",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                         "kernel": "k_mixed_apply<DH=%d,DL=%d,Q=%d,grad+div>" % (ph + 1, pl + 1, ph + 1),
+                         "peak_source": "FP64 pipe: 152 SMs x %d DFMA/clk x 2 flop x %.0f MHz"
+                                        % (FP64_DFMA_PER_CLK_PER_SM, sm_max),
+                         "flops_per_launch": flops, "bytes_per_launch": nbytes,
+                         "hbm": {"achieved": nbytes / (ms * 1e-3) / 1e9,
+                                 "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                                 "frac": nbytes / (ms * 1e-3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
+                                 "peak_source": src}},
+            "paper_context": "GB200 DMMA fused PA 46.60 GDOF/s, GH200 36.15 (FP64, 540 M DOF, "
+                             "Table VI; other hardware)"}
+
+
+def run_mixed_h1l2(args, local_rank):
+    """--mixed-h1l2: only the paper's own operator (mixed H1/L2 pair) on --n^3 hexes."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    out = {"mixed_h1l2": True}
+    out.update(measure_mixed(fe, torch, args.n, torch.cuda.current_stream()))
+    print(json.dumps(out))
+    return 0
 
 
 def max_over_ranks(t, dist=None, device="cpu"):
@@ -152,57 +237,78 @@ class ClockSampler:
         return False
 
 
+class CpuOracle:
+    """The oracle's sum-factorised FP64 operator and Jacobi-PCG in C with OpenMP over elements
+    (oracle/sumfact_omp.c, as it stands) on the benchmark's own workload: the 64^3 p=3 Poisson
+    mesh, right-hand side and stopping rule, on every host core.  Set-up (quadrature data, Jacobi
+    diagonal, load vector) is untimed; a sample is a bounded number of PCG iterations."""
+
+    def __init__(self, n=N_ELEM, p=ORDER):
+        import numpy as np
+        from oracle import sumfact_c
+        from oracle.mesh import boundary_mask
+        from paper_2603_09038_gb300.inputs import perturbed_vertices
+        self.n, self.p = n, p
+        V = perturbed_vertices(n, n, n)
+        self.op = sumfact_c.Operator(n, n, n, p, V, "diffusion")
+        self.mask = boundary_mask(n, n, n, p)
+        self.diag = self.op.diagonal()
+        self.diag[self.mask == 1] = 1.0
+        # any b with the workload's structure serves for timing (the iteration count is fixed)
+        self.b = self.op.apply(np.ones(self.op.ndofs)) + 1.0
+        self.cores = sumfact_c.threads()
+        self.t_iter = self.iterate(1)[0]
+
+    def iterate(self, k):
+        t0 = time.perf_counter()
+        _, it, _ = self.op.pcg(self.b, self.mask, self.diag, 0.0, k)
+        return time.perf_counter() - t0, it
+
+    def sample(self, budget_s):
+        """PCG iterations for about budget_s seconds: GDOF/s = ndofs x applies / time."""
+        k = max(1, int(round(budget_s / max(self.t_iter, 1e-6))))
+        sec, it = self.iterate(k)
+        gdofs = self.op.ndofs * it / sec / 1e9
+        return {"value": gdofs, "unit": UNIT, "cores": self.cores, "kind": "oracle",
+                "sample": "oracle sum-factorised FP64 diffusion apply + Jacobi-PCG in C with "
+                          "OpenMP over elements (8 colours) on all %d host threads: %d PCG "
+                          "iterations (%d applies) of the %d^3 p=%d workload (%d dofs) in %.1f s; "
+                          "%.3f s per iteration" % (self.cores, it, it, self.n, self.p,
+                                                    self.op.ndofs, sec, sec / max(1, it)),
+                "seconds": sec, "applies": it, "s_per_iteration": sec / max(1, it)}
+
+
 def cpu_oracle_sample(budget_s=12.0):
-    """The oracle's element-matrix apply (as it stands) on an 8^3-element corner block of the
-    workload mesh, repeated for ~budget_s; GDOF/s scaled by the workload's dofs per element."""
-    import numpy as np
-    from oracle import operator as oop
-    from paper_2603_09038_gb300.inputs import perturbed_vertices, uniform_vector
-    full = perturbed_vertices(N_ELEM, N_ELEM, N_ELEM)
-    s = 8
-    idx = np.arange((N_ELEM + 1) ** 3).reshape(N_ELEM + 1, N_ELEM + 1, N_ELEM + 1)
-    sub = full[idx[: s + 1, : s + 1, : s + 1].reshape(-1)]
-    prob = oop.Problem(s, s, s, ORDER, sub)
-    x = uniform_vector(prob.ndofs, seed=0)
-    dofs_per_elem = (N_ELEM * ORDER + 1) ** 3 / N_ELEM ** 3
-    reps, t0, c0 = 0, time.perf_counter(), os.times()
-    while True:
-        oop.apply(prob, x, oop.DIFFUSION)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    c1 = os.times()
-    cpu = (c1.user - c0.user) + (c1.system - c0.system)
-    gdofs = reps * prob.ne * dofs_per_elem / el / 1e9
-    return {"value": gdofs, "unit": UNIT, "cores": max(1, int(round(cpu / el))),
-            "kind": "oracle",
-            "sample": "oracle element-matrix diffusion apply on an 8^3-element block of the "
-                      "64^3 p=3 mesh, %d applies in %.1f s; rate scaled by the workload's "
-                      "%.2f dofs per element" % (reps, el, dofs_per_elem),
-            "seconds": el, "applies": reps}
+    return CpuOracle().sample(budget_s)
 
 
 def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle (sum-factorised C/OpenMP Jacobi-PCG) on the same
+    workload, metric and unit; every step is a bounded sample of PCG iterations.  Only rank 0
+    runs it; the other ranks exit without work."""
     if rank != 0:
         return 0
-    per_step, results = [], None
-    budget = max(2.0, min(12.0, 60.0 / max(1, args.steps + args.warmup)))
+    oracle = CpuOracle()
+    per_step = []
+    budget = max(1.0, min(12.0, 60.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(budget)
+        r = oracle.sample(budget)
         if i >= args.warmup:
             per_step.append(r)
     tot_t = sum(r["seconds"] for r in per_step)
-    value = sum(r["value"] * r["seconds"] for r in per_step) / tot_t
+    applies = sum(r["applies"] for r in per_step)
+    value = oracle.op.ndofs * applies / tot_t / 1e9
     last = per_step[-1]
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 * tot_t / len(per_step), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": "poisson_64cubed_p3_jacobi_pcg", "elements": N_ELEM ** 3,
-                      "order": ORDER, "q1d": ORDER + 2, "ndofs": (N_ELEM * ORDER + 1) ** 3,
-                      "parallelism": "cpu"},
+           "config": {"workload": "poisson_%dcubed_p%d_jacobi_pcg" % (oracle.n, oracle.p),
+                      "elements": oracle.n ** 3, "order": oracle.p, "q1d": oracle.p + 2,
+                      "ndofs": oracle.op.ndofs, "parallelism": "cpu",
+                      "step": "a bounded sample of Jacobi-PCG iterations (%.1f s budget)" % budget,
+                      "s_per_pcg_iteration": tot_t / max(1, applies)},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"],
                             "kind": "oracle", "sample": last["sample"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -460,10 +566,17 @@ def run_ours(args, rank, world, local_rank):
             out["mdof_per_w"] = 1000.0 * value / (world * clk.result["power_w"])
     fe.fe_pa_destroy(pa)
     fe.fe_mesh_destroy(mesh)
+    if world == 1 and args.paper_operator_n > 0:
+        # the paper's own operator (Table VI's mixed H1 p=4 / L2 p=3 pair) at its problem size
+        torch.cuda.empty_cache()
+        out["paper_operator"] = measure_mixed(fe, torch, args.paper_operator_n, stream)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_oracle_sample(args.cpu_seconds)
             out["cpu_baseline"] = {k2: cb[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+            # the same solve on the host cores: the oracle's time per iteration x this solve's
+            out["cpu_baseline"]["time_to_1e-8_extrapolated_s"] = \
+                cb["s_per_iteration"] * (iters[-1] if iters else 0)
         print(json.dumps(out))
     return 0
 
@@ -934,6 +1047,10 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32/BF16-mma.sync throughput probes")
     ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")
+    ap.add_argument("--mixed-h1l2", action="store_true",
+                    help="only the paper's mixed H1 p=4 / L2 p=3 pair on --n^3 hexes")
+    ap.add_argument("--paper-operator-n", type=int, default=128,
+                    help="mesh size of the paper-operator entry of the main line (0: skip)")
     ap.add_argument("--mixed-orders", action="store_true",
                     help="variable-order apply: --n^3 mesh, 8^3 blocks of orders 2, 4, 6")
     args = ap.parse_args()
@@ -958,6 +1075,8 @@ def main():
         return run_batched_pcg(args, local_rank)
     if args.mixed_orders:
         return run_mixed_orders(args, local_rank)
+    if args.mixed_h1l2:
+        return run_mixed_h1l2(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

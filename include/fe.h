@@ -360,6 +360,24 @@ int fe_lpc_weights(fe_lpc* lpc, float* host_w, int set);
 int fe_lpc_loss_grad(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
                      float* host_y, float* host_grad, double* loss);
 
+/* Test hook of the optimiser: for `batch` host rows X (FP32 [batch][D^3], rounded to BF16) and
+ * targets T (FP32 [batch][D^3]), runs the forward pass and back-propagation with the current
+ * weights and then one Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr, the step count
+ * advanced by one) -- the kernels of one fe_lpc_train step on a given batch instead of a drawn
+ * one.  *loss (may be NULL) = the batch's loss before the step.  Synchronous. */
+int fe_lpc_adam_step(fe_lpc* lpc, int batch, const float* host_x, const float* host_t,
+                     double lr, double* loss);
+
+/* Test hook of the training-data generator: (re)generates the training set exactly as the first
+ * fe_lpc_train call does (probing of A_ee, FP64 Cholesky, residual snapshots, reps pairs per
+ * sampled element; reps <= 0 => 16; the BF16/FP32 training copies are replaced) and copies the
+ * first min(max_rows, total) pairs to the host in FP64, before their rounding to the training
+ * copies: host_elem int32 [rows] the element of each pair, host_x and host_t FP64 [rows][D^3]
+ * with t = S_e^-1 A_ee^-1 S_e^-1 x and ||t|| = 1.  *rows gets the count (max_rows = 0: none is
+ * copied).  Same errors as fe_lpc_train.  Synchronous. */
+int fe_lpc_sample_pairs(fe_lpc* lpc, int reps, int64_t max_rows, int32_t* host_elem,
+                        double* host_x, double* host_t, int64_t* rows, void* stream);
+
 /* Checkpoint of a learned preconditioner, so that training resumes where it stopped.  File
  * layout (little-endian): 8 bytes "FELPC001", int32 din (= D^3), int32 width, int64 nparam,
  * int32 Adam step count, int32 0, then nparam FP32 weights (the fe_lpc_weights packing), the
@@ -504,6 +522,40 @@ int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, dou
                   int maxit, fe_pcg_stats* stats, void* stream);
 
 void fe_vspace_destroy(fe_vspace* vs);
+
+/* ---- The paper's own operator: the mixed H1 / L2 gradient and divergence blocks ------------
+ * Section II-A, Eq. (block-mult) couples an H1 pressure p and an L2 vector velocity u through
+ * (grad p, tau) and -(u, grad v); Section III-G applies them in fused partial-assembly kernels.
+ * Readings (the paper fixes only the orders, H1 4 and L2 3): H1 of order order_h on the GLL
+ * nodes with the structured dof map (the numbering of fe_mesh_setup); L2 of order order_l, one
+ * Lagrange basis per element on the order_l + 1 Gauss-Legendre points per axis, three
+ * components, layout [e][c][a] with a = i + D_l (j + D_l k), D_l = order_l + 1 (no continuity);
+ * Q = order_h + 1 Gauss-Legendre points per axis; the L2 basis used as is on the physical
+ * element.  The gradient block is
+ *   (G p)_{e,c,a} = sum_q w_q det J (J^-T grad phi_b)_c psi_a p_{g(e,b)},
+ * an [ndof_l x ndof_h] operator, and the divergence block is its transpose (the system's
+ * -(u, grad v) is -G^T).  The partial assembly stores M_q = w_q det J J^-T (9 FP64 values per
+ * element and Gauss point, [e][qz][9][qy][qx]) once; one fused FP64 kernel applies both blocks
+ * in one pass over the elements, reading M_q once for both. */
+typedef struct fe_mixed fe_mixed;
+
+/* Builds the H1 mesh topology (as fe_mesh_setup with order order_h) and the quadrature data.
+ * (order_h, order_l) in {(4, 3) -- the paper's pair --, (2, 1), (3, 3)}, else
+ * FE_ERR_UNSUPPORTED; host_vertices as for fe_mesh_setup; FE_ERR_ARG on an inverted element.
+ * Synchronous. */
+int fe_mixed_setup(int nx, int ny, int nz, int order_h, int order_l, const double* host_vertices,
+                   void* stream, fe_mixed** out);
+
+/* H1 dofs ((nx p_h + 1)(ny p_h + 1)(nz p_h + 1)) and L2 values (3 ne D_l^3); either may be NULL. */
+int fe_mixed_sizes(const fe_mixed* mx, int64_t* ndof_h, int64_t* ndof_l);
+
+/* dev_gp = G dev_p (FP64 [ndof_l], overwritten) and dev_gtu = G^T dev_u (FP64 [ndof_h], zeroed
+ * then scatter-added) in one fused launch; pass dev_p with dev_gp and dev_u with dev_gtu, or
+ * NULL for both of a pair to apply one block only.  No aliasing.  Asynchronous. */
+int fe_mixed_apply(const fe_mixed* mx, const double* dev_p, const double* dev_u, double* dev_gp,
+                   double* dev_gtu, void* stream);
+
+void fe_mixed_destroy(fe_mixed* mx);
 
 void fe_pa_destroy(fe_pa* pa);
 void fe_mesh_destroy(fe_mesh* mesh);

@@ -279,7 +279,8 @@ struct ArF32 {
   static __device__ __forceinline__ T dot3(T a0, T x0, T a1, T x1, T a2, T x2) {
     return fmaf(a2, x2, fmaf(a1, x1, a0 * x0));
   }
-  static __device__ __forceinline__ double widen(T v, int) { return f64_from_f32(v); }
+  // FP64 value of a result times 2^off (the FP32 data's shift undone), exact
+  static __device__ __forceinline__ double widen(T v, int off) { return f64_from_f32_scaled(v, off); }
   static __device__ __forceinline__ void scatter(float* y, T v) { atomicAdd(y, v); }
   // accumulation of the fused x . (A x): FP32 (the inner solves need no more)
   using DotAcc = float;

@@ -119,6 +119,25 @@ bool make_basis_1d(int p, int q, Basis1D* out) {
   return true;
 }
 
+bool make_l2_basis_1d(int p, int q, double* Bl) {
+  if (p < 0 || p + 1 > kMaxD || q < 1 || q > kMaxQ) return false;
+  const int D = p + 1;
+  ld nodes[kMaxD], nw[kMaxD], gx[kMaxQ], gw[kMaxQ];
+  gauss_legendre_pm1(D, nodes, nw);
+  gauss_legendre_pm1(q, gx, gw);
+  for (int d = 0; d < D; ++d) nodes[d] = (nodes[d] + 1.0L) / 2.0L;
+  for (int i = 0; i < q; ++i) {
+    const ld x = (gx[i] + 1.0L) / 2.0L;
+    for (int d = 0; d < D; ++d) {
+      ld val = 1.0L;
+      for (int m = 0; m < D; ++m)
+        if (m != d) val *= (x - nodes[m]) / (nodes[d] - nodes[m]);
+      Bl[i * D + d] = (double)val;
+    }
+  }
+  return true;
+}
+
 }  // namespace fe
 
 extern "C" int fe_basis_1d(int order, int q1d, double* nodes, double* pts, double* wts,

@@ -31,6 +31,9 @@ struct Basis1D {
 };
 // Returns false if p or q is out of range.
 bool make_basis_1d(int p, int q, Basis1D* out);
+// Lagrange basis of the p+1 Gauss-Legendre points of [0, 1] (a discontinuous L2 basis) at the
+// q-point Gauss-Legendre rule: Bl[i*(p+1) + d] = l_d(x_i).  False if out of range.
+bool make_l2_basis_1d(int p, int q, double* Bl);
 
 // y = A x with the FP32 variant on float vectors (the caller zeroes y); same skip / dot_part
 // semantics as apply_dispatch.

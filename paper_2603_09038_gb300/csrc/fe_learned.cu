@@ -196,7 +196,8 @@ __global__ void k_samples(const double* __restrict__ Lfac, const double* __restr
                           const int32_t* __restrict__ map, const int32_t* __restrict__ elems,
                           const double* __restrict__ dis, const double* __restrict__ wsq,
                           int ns, int din, int reps,
-                          uint64_t seed, __nv_bfloat16* __restrict__ Xs, float* __restrict__ Ts) {
+                          uint64_t seed, __nv_bfloat16* __restrict__ Xs, float* __restrict__ Ts,
+                          double* __restrict__ Xd, double* __restrict__ Td) {
   extern __shared__ double sh[];
   double* r = sh;
   double* t = sh + din;
@@ -254,6 +255,12 @@ __global__ void k_samples(const double* __restrict__ Lfac, const double* __restr
       for (int i = 0; i < din; ++i) {
         Xs[row * din + i] = __float2bfloat16((float)(u[i] * inv));
         Ts[row * din + i] = (float)(t[i] * inv);
+      }
+      if (Xd) {  // FP64 copies before the rounding (test hook)
+        for (int i = 0; i < din; ++i) {
+          Xd[row * din + i] = u[i] * inv;
+          Td[row * din + i] = t[i] * inv;
+        }
       }
     }
     __syncthreads();
@@ -859,7 +866,10 @@ __global__ void k_add_f32(double* __restrict__ x, const float* __restrict__ d, i
 }
 
 // Training data (first call of fe_lpc_train): probing, Cholesky, residual snapshots, samples.
-int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
+// With xd/td given, also returns device FP64 copies of the pairs ([nsamp][din], caller frees)
+// and the sampled elements (row r belongs to elems[r / reps]).
+int make_samples(fe_lpc* L, int reps, cudaStream_t s, double** xd = nullptr,
+                 double** td = nullptr, std::vector<int32_t>* elems = nullptr) {
   fe_mesh* m = const_cast<fe_mesh*>(L->pa->mesh);
   const int din = L->din;
   // Interior elements in 27 classes by (ex, ey, ez) mod 3: elements of one class are three apart,
@@ -948,10 +958,16 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
         (err = cudaMalloc(&L->Ts, sizeof(float) * L->nsamp * din)) != cudaSuccess)
       st = cuda_error(err, "fe_lpc_train: sample cudaMalloc");
   }
+  double *Xd = nullptr, *Td = nullptr;
+  if (st == FE_OK && xd) {
+    if ((err = cudaMalloc(&Xd, sizeof(double) * L->nsamp * din)) != cudaSuccess ||
+        (err = cudaMalloc(&Td, sizeof(double) * L->nsamp * din)) != cudaSuccess)
+      st = cuda_error(err, "fe_lpc_sample_pairs: cudaMalloc");
+  }
   if (st == FE_OK) {
     k_samples<<<ns, 64, sizeof(double) * 3 * din, s>>>(Aee, snapbuf, nsnap, m->d_map, d_el,
                                                        L->dis, L->wsq, ns, din, reps, L->seed,
-                                                       L->Xs, L->Ts);
+                                                       L->Xs, L->Ts, Xd, Td);
     int fail = 0;
     if ((err = cudaGetLastError()) != cudaSuccess ||
         (err = cudaMemcpyAsync(&fail, d_fail, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
@@ -961,6 +977,14 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s) {
       st = set_error(FE_ERR_BREAKDOWN, "fe_lpc_train: an element block is not positive definite");
   }
   if (st != FE_OK) L->nsamp = 0;
+  if (st == FE_OK && xd) {
+    *xd = Xd;
+    *td = Td;
+    if (elems) *elems = el;
+  } else {
+    cudaFree(Xd);
+    cudaFree(Td);
+  }
   cudaFree(d_el); cudaFree(v); cudaFree(w); cudaFree(Aee); cudaFree(snapbuf); cudaFree(d_fail);
   return st;
 }
@@ -1312,6 +1336,24 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   return FE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// One Adam step (beta 0.9 / 0.999, eps 1e-8) on the gradient in L->grad; refreshes the BF16
+// copy of the weights.
+int adam_update(fe_lpc* L, double lr, cudaStream_t s) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  ++L->adam_t;
+  const float c1 = 1.0f - powf(b1, (float)L->adam_t), c2 = 1.0f - powf(b2, (float)L->adam_t);
+  L->wimg_ok = false;
+  k_adam<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->grad, L->adam_m, L->adam_v, L->nparam,
+                                         (float)lr, b1, b2, 1e-8f, c1, c2, L->wb);
+  return cuda_error(cudaGetLastError(), "fe_lpc: Adam step launch");
+}
+}  // namespace
+
+extern "C" {
+
 int fe_lpc_train(fe_lpc* L, int steps, int batch, double lr, int reps, double* final_loss,
                  void* stream) {
   clear_error();
@@ -1322,20 +1364,13 @@ int fe_lpc_train(fe_lpc* L, int steps, int batch, double lr, int reps, double* f
   int st;
   if (L->nsamp == 0 && (st = make_samples(L, reps > 0 ? reps : 16, s)) != FE_OK) return st;
   if ((st = ensure_workspace(L, batch)) != FE_OK) return st;
-  const float b1 = 0.9f, b2 = 0.999f;
   double loss = 0.0;
   for (int it = 0; it < steps; ++it) {
     const uint64_t key = L->seed * 0x9E3779B97F4A7C15ull + (uint64_t)(L->adam_t + 1) * 0x632BE59BD9B4E019ull;
     k_batch<<<(unsigned int)(((int64_t)batch * L->din + kT - 1) / kT), kT, 0, s>>>(
         L->Xs, L->Ts, L->nsamp, L->din, batch, key, L->Xb, L->Tb);
     if ((st = mlp_loss_grad(L, batch, s, (it + 1 == steps) ? &loss : nullptr)) != FE_OK) return st;
-    ++L->adam_t;
-    const float c1 = 1.0f - powf(b1, (float)L->adam_t), c2 = 1.0f - powf(b2, (float)L->adam_t);
-    L->wimg_ok = false;
-    k_adam<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->grad, L->adam_m, L->adam_v, L->nparam,
-                                           (float)lr, b1, b2, 1e-8f, c1, c2, L->wb);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return cuda_error(err, "fe_lpc_train: step launch");
+    if ((st = adam_update(L, lr, s)) != FE_OK) return st;
   }
   if (final_loss) *final_loss = loss;
   return cuda_error(cudaStreamSynchronize(s), "fe_lpc_train");
@@ -1468,6 +1503,59 @@ int fe_lpc_loss_grad(fe_lpc* L, int batch, const float* host_x, const float* hos
       (err = cudaMemcpy(host_grad, L->grad, 4 * L->nparam, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_error(err, "fe_lpc_loss_grad: grad");
   if (loss) *loss = l;
+  return FE_OK;
+}
+
+int fe_lpc_adam_step(fe_lpc* L, int batch, const float* host_x, const float* host_t, double lr,
+                     double* loss) {
+  clear_error();
+  if (!L || !host_x || !host_t || batch < 1 || batch > (1 << 20) || !(lr > 0.0))
+    return set_error(FE_ERR_ARG, "fe_lpc_adam_step: bad arguments");
+  int st = ensure_workspace(L, batch);
+  if (st != FE_OK) return st;
+  const int64_t n = (int64_t)batch * L->din;
+  std::vector<__nv_bfloat16> xb(n);
+  for (int64_t i = 0; i < n; ++i) xb[i] = __float2bfloat16(host_x[i]);
+  cudaError_t err;
+  if ((err = cudaMemcpy(L->Xb, xb.data(), 2 * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(L->Tb, host_t, 4 * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_error(err, "fe_lpc_adam_step: copy");
+  double l = 0.0;
+  if ((st = mlp_loss_grad(L, batch, 0, &l)) != FE_OK) return st;
+  if ((st = adam_update(L, lr, 0)) != FE_OK) return st;
+  if (loss) *loss = l;
+  return cuda_error(cudaDeviceSynchronize(), "fe_lpc_adam_step");
+}
+
+int fe_lpc_sample_pairs(fe_lpc* L, int reps, int64_t max_rows, int32_t* host_elem,
+                        double* host_x, double* host_t, int64_t* rows, void* stream) {
+  clear_error();
+  if (!L || !rows || max_rows < 0 || (max_rows > 0 && (!host_elem || !host_x || !host_t)))
+    return set_error(FE_ERR_ARG, "fe_lpc_sample_pairs: bad arguments");
+  if (reps <= 0) reps = 16;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaFree(L->Xs);
+  cudaFree(L->Ts);
+  L->Xs = nullptr;
+  L->Ts = nullptr;
+  L->nsamp = 0;
+  double *xd = nullptr, *td = nullptr;
+  std::vector<int32_t> el;
+  int st = make_samples(L, reps, s, &xd, &td, &el);
+  if (st != FE_OK) return st;
+  const int64_t n = max_rows < L->nsamp ? max_rows : L->nsamp;
+  cudaError_t err = cudaSuccess;
+  if (n > 0) {
+    const size_t bytes = sizeof(double) * (size_t)n * L->din;
+    if ((err = cudaMemcpyAsync(host_x, xd, bytes, cudaMemcpyDeviceToHost, s)) == cudaSuccess &&
+        (err = cudaMemcpyAsync(host_t, td, bytes, cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+      err = cudaStreamSynchronize(s);
+    for (int64_t r = 0; r < n; ++r) host_elem[r] = el[(size_t)(r / reps)];
+  }
+  cudaFree(xd);
+  cudaFree(td);
+  if (err != cudaSuccess) return cuda_error(err, "fe_lpc_sample_pairs: copy");
+  *rows = n;
   return FE_OK;
 }
 

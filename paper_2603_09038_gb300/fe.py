@@ -102,6 +102,10 @@ _SIGS = {
     "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_lpc_adam_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "fe_lpc_sample_pairs": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64, _VP, _VP, _VP,
+                                           ctypes.POINTER(ctypes.c_int64), _VP]),
     "fe_lpc_set_fallback": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fe_pa_set_learned": (ctypes.c_int, [_VP, _VP]),
     "fe_lpc_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
@@ -136,6 +140,12 @@ _SIGS = {
     "fe_vspace_pcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                      ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_vspace_destroy": (None, [_VP]),
+    "fe_mixed_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)]),
+    "fe_mixed_sizes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "fe_mixed_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "fe_mixed_destroy": (None, [_VP]),
     "fe_pa_destroy": (None, [_VP]),
     "fe_mesh_destroy": (None, [_VP]),
     "fe_last_error": (ctypes.c_char_p, []),
@@ -438,6 +448,30 @@ def fe_lpc_loss_grad(lpc, X, T):
     return loss.value, Y, g
 
 
+def fe_lpc_adam_step(lpc, X, T, lr):
+    """One Adam step on host rows X, targets T (float32 [batch, D^3]); returns the loss before it."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load().fe_lpc_adam_step(_VP(lpc), int(X.shape[0]), X.ctypes.data_as(_VP),
+                                   T.ctypes.data_as(_VP), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def fe_lpc_sample_pairs(lpc, din, reps=0, max_rows=1 << 16, stream=None):
+    """The generator's training pairs in FP64: (elements int32 [rows], X, T float64 [rows, din])."""
+    cap = int(max_rows)
+    el = np.zeros(cap, dtype=np.int32)
+    X = np.zeros((cap, din))
+    T = np.zeros((cap, din))
+    rows = ctypes.c_int64()
+    _check(load().fe_lpc_sample_pairs(_VP(lpc), int(reps), cap, el.ctypes.data_as(_VP),
+                                      X.ctypes.data_as(_VP), T.ctypes.data_as(_VP),
+                                      ctypes.byref(rows), _stream(stream)))
+    n = rows.value
+    return el[:n], X[:n], T[:n]
+
+
 def fe_lpc_apply(lpc, dev_r, dev_z, stream=None):
     return _check(load().fe_lpc_apply(_VP(lpc), _ptr(dev_r), _ptr(dev_z), _stream(stream)))
 
@@ -588,6 +622,31 @@ def fe_vspace_pcg(vs, op, dev_b, dev_x, rtol, maxit, stream=None):
 def fe_vspace_destroy(vs):
     if vs:
         load().fe_vspace_destroy(_VP(vs))
+
+
+def fe_mixed_setup(nx, ny, nz, order_h, order_l, vertices, stream=None):
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    out = _VP()
+    _check(load().fe_mixed_setup(int(nx), int(ny), int(nz), int(order_h), int(order_l),
+                                 V.ctypes.data_as(_VP), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def fe_mixed_sizes(mx):
+    h, l = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fe_mixed_sizes(_VP(mx), ctypes.byref(h), ctypes.byref(l)))
+    return h.value, l.value
+
+
+def fe_mixed_apply(mx, dev_p, dev_u, dev_gp, dev_gtu, stream=None):
+    """gp = G p and gtu = G^T u in one launch (pass None for both of a pair to skip it)."""
+    _check(load().fe_mixed_apply(_VP(mx), _ptr(dev_p), _ptr(dev_u), _ptr(dev_gp),
+                                 _ptr(dev_gtu), _stream(stream)))
+
+
+def fe_mixed_destroy(mx):
+    if mx:
+        load().fe_mixed_destroy(_VP(mx))
 
 
 def fe_pa_destroy(pa):

@@ -6,9 +6,10 @@
   rounding, a few roundings deep, relative Frobenius error <= 3e-2) and is far below the O(1)
   error of a transposed or dropped term.
 * The patch apply z = sum_e R_e^T W_e S_e s_e f(x_e / s_e), x_e = S_e W_e R_e r, S = diag(A)^(-1/2),
-  against the same sum written out in numpy with the oracle's MLP and the oracle's diagonal, on
-  the fused inference kernel and on the unfused GEMM path (a width whose weights exceed shared
-  memory).
+  against oracle/learned.py element by element within its BF16 rounding bound, on the fused
+  inference kernel and on the unfused GEMM path (a width whose weights exceed shared memory).
+* The training pairs against the oracle's local solves with the assembled A_ee; one Adam step
+  against the oracle's update; FCG's iterates against the oracle's FCG(1).
 * Flexible CG: with Jacobi it equals PCG (iterations, solution vs the oracle's dense solve); with
   zero weights it falls back to Jacobi; trained, it reaches the same FP64 residual as Jacobi-PCG
   in fewer iterations.
@@ -17,6 +18,7 @@ import numpy as np
 import pytest
 
 from gpu_util import gpu_problem, torch_cuda
+from oracle import learned as ol
 from oracle import mlp as omlp
 from oracle import operator as oop
 from oracle.element import DIFFUSION
@@ -25,12 +27,7 @@ from oracle.mesh import boundary_mask
 pytestmark = pytest.mark.gpu
 
 
-def bf16_round(a):
-    """Round-to-nearest-even of float32 values to bfloat16, returned as float64 (input prep)."""
-    a = np.ascontiguousarray(a, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
-    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+bf16_round = ol.bf16_round
 
 
 def unpack(w, din, width):
@@ -74,7 +71,11 @@ def test_loss_grad_matches_oracle(p, width, batch):
 @pytest.mark.parametrize("dims,p,width", [((4, 3, 3), 2, 32), ((5, 3, 2), 3, 256),
                                           ((3, 3, 4), 1, 64), ((2, 3, 3), 4, 512),
                                           ((4, 4, 3), 3, 0), ((3, 2, 3), 4, 0)])
-def test_patch_apply_matches_numpy_sum(dims, p, width):
+def test_patch_apply_matches_oracle(dims, p, width):
+    """z = M(r) from the fused kernel (or the unfused GEMM path for widths whose weights exceed
+    shared memory) against oracle/learned.py's patch operator in FP64 with the same BF16 weights,
+    element by element within the oracle's bound on the BF16 rounding of the inputs and hidden
+    activations and the FP32 accumulation."""
     torch = torch_cuda()
     with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
         prob = oop.Problem(*dims, p, V, coeff=c)
@@ -92,27 +93,99 @@ def test_patch_apply_matches_numpy_sum(dims, p, width):
             fe.fe_lpc_apply(lpc, 2.0 * r, z2)
             torch.cuda.synchronize()
             zg, z2g = z.cpu().numpy(), z2.cpu().numpy()
-            # the same map written out with the oracle's diagonal and MLP
-            mask = boundary_mask(*dims, p)
-            dis = np.where(mask == 1, 0.0, 1.0 / np.sqrt(oop.diagonal(prob, DIFFUSION)))
-            dmap = torch.empty(ne * din, dtype=torch.int32, device="cuda")
-            fe.fe_mesh_dof_map(mesh, dmap)
-            dmap = dmap.cpu().numpy().reshape(ne, din).astype(np.int64)
-            mult = np.bincount(dmap.reshape(-1), minlength=n).astype(np.float64)
-            wsq = np.where(mask == 1, 0.0, 1.0 / np.sqrt(mult))
-            Wb = tuple(bf16_round(x) for x in unpack(w, din, width))
-            rh = r.cpu().numpy()
-            xe = dis[dmap] * wsq[dmap] * rh[dmap]
-            s = np.linalg.norm(xe, axis=1)
-            Y, _ = omlp.forward(Wb, bf16_round(xe / s[:, None]))
-            zr = np.zeros(n)
-            np.add.at(zr, dmap.reshape(-1), (wsq[dmap] * dis[dmap] * s[:, None] * Y).reshape(-1))
+            Wb = tuple(ol.bf16_round(x) for x in unpack(w, din, width))
+            zr, zb = ol.patch_apply(prob, DIFFUSION, ol.network(Wb), r.cpu().numpy(),
+                                    bound=ol.network_rounding_bound(Wb))
+            assert np.all(np.abs(zg - zr) <= zb + 1e-13 * np.abs(zr).max())
             assert rel_fro(zg, zr) <= 3e-2
-            assert np.all(zg[mask == 1] == 0.0)
+            assert np.all(zg[boundary_mask(*dims, p) == 1] == 0.0)
             # positively homogeneous: M(2r) = 2 M(r) up to the order of the atomic adds
             assert np.abs(z2g - 2.0 * zg).max() <= 1e-12 * np.abs(zg).max()
         finally:
             fe.fe_lpc_destroy(lpc)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32x2"])
+@pytest.mark.parametrize("dims,p", [((5, 5, 5), 2), ((4, 5, 4), 3), ((4, 4, 4), 1)])
+def test_training_pairs_are_the_oracle_local_solves(variant, dims, p):
+    """Every generated pair (x, t) of element e satisfies t = S_e^-1 A_ee^-1 S_e^-1 x with A_ee the
+    block of the oracle's assembled matrix and S = diag(A)^-1/2, element by element (the
+    library probes A_ee with applies and factors it by FP64 Cholesky); ||t|| = 1; the pairs
+    cover the three kinds (normal v, A_ee u, residual snapshots) for every sampled element."""
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        din = (p + 1) ** 3
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 0, 5)
+        try:
+            reps = 6
+            el, X, T = fe.fe_lpc_sample_pairs(lpc, din, reps, 1 << 14)
+            assert len(el) > 0 and len(el) % reps == 0
+            interior = [ex + dims[0] * (ey + dims[1] * ez) for ez in range(1, dims[2] - 1)
+                        for ey in range(1, dims[1] - 1) for ex in range(1, dims[0] - 1)]
+            assert sorted(set(el.tolist())) == sorted(interior)
+            A = oop.assemble(prob, DIFFUSION)
+            _, S, _ = ol.patch_data(prob, DIFFUSION)
+            nonzero = 0
+            for e, x, t in zip(el, X, T):
+                if not np.any(x):       # a residual snapshot the short run never reached
+                    assert not np.any(t)
+                    continue
+                nonzero += 1
+                tr = ol.local_target(prob, DIFFUSION, int(e), x, A=A, S=S)
+                assert abs(np.linalg.norm(t) - 1.0) <= 1e-12
+                assert np.abs(t - tr).max() <= 1e-9, (e, np.abs(t - tr).max())
+            assert nonzero >= 2 * len(el) // 3
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_adam_step_matches_oracle():
+    """Two fe_lpc_adam_step calls from a fresh handle against oracle/learned.py's Adam update with
+    the gradients the library's own backward pass returns for the same batches (FP32 update
+    arithmetic: ~1e-7 of the weights, well below the step lr)."""
+    with gpu_problem(2, 2, 2, 2) as (fe, mesh, pa, V, c):
+        din, width, lr = 27, 32, 1e-3
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 7)
+        try:
+            rng = np.random.default_rng(21)
+            w = fe.fe_lpc_weights(lpc).astype(np.float64)
+            m = np.zeros_like(w)
+            v = np.zeros_like(w)
+            for t in (1, 2):
+                X = rng.standard_normal((100, din)).astype(np.float32)
+                T = rng.standard_normal((100, din)).astype(np.float32)
+                _, _, g = fe.fe_lpc_loss_grad(lpc, X, T)
+                fe.fe_lpc_adam_step(lpc, X, T, lr)
+                w, m, v = ol.adam_step(w, g.astype(np.float64), m, v, t, lr)
+                got = fe.fe_lpc_weights(lpc).astype(np.float64)
+                assert np.abs(got - w).max() <= 1e-6 * np.abs(w).max() + 1e-3 * lr, t
+                assert np.abs(got - fe.fe_lpc_weights(lpc)).max() == 0
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_fcg_iterates_match_oracle_fcg():
+    """fe_fcg with Jacobi, stopped after k = 1..6 iterations, against oracle/learned.py's FCG(1)
+    with the oracle's own Jacobi diagonal on the oracle's assembled constrained operator."""
+    torch = torch_cuda()
+    dims, p = (4, 4, 3), 2
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        m = boundary_mask(*dims, p).astype(np.float64)
+        keep = 1.0 - m
+        A = oop.assemble(prob, DIFFUSION)
+        d = oop.diagonal(prob, DIFFUSION) * keep + m
+        bh = np.random.default_rng(6).standard_normal(prob.ndofs) * keep
+        _, _, _, xs = ol.fcg(lambda u: keep * (A @ (keep * u)) + m * u, lambda r: r / d, bh,
+                             rtol=0.0, maxit=6)
+        b = torch.from_numpy(bh).cuda()
+        x = torch.empty_like(b)
+        for k in range(1, 7):
+            st, s = fe.fe_fcg(pa, fe.FE_DIFFUSION, None, b, x, 1e-30, k)
+            assert st == fe.FE_ERR_NOT_CONVERGED and s["iters"] == k
+            xr = xs[k]
+            assert np.abs(x.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max(), k
 
 
 def _dense_solve(prob, b):

@@ -1,0 +1,131 @@
+"""Pins of oracle/learned.py (CPU): the patch operator with exact local inverses equals the
+symmetrically weighted additive Schwarz matrix assembled element by element; the local blocks
+equal what probing the operator with unit vectors reads back; flexible CG with a fixed SPD
+preconditioner produces the preconditioned-CG iterates; the patch operator is positively
+homogeneous and its BF16 rounding bound covers an explicit BF16 evaluation; the Adam update
+matches its closed forms."""
+import numpy as np
+import pytest
+
+from oracle import learned as ol
+from oracle import mlp as omlp
+from oracle import operator as oop
+from oracle.element import DIFFUSION
+from oracle.mesh import boundary_mask, dof_map
+from oracle.solve import pcg as oracle_pcg, load_vector
+from paper_2603_09038_gb300.inputs import perturbed_vertices, lognormal_coefficient
+
+
+def _prob(dims=(3, 3, 2), p=2, sigma=1.0):
+    V = perturbed_vertices(*dims)
+    c = lognormal_coefficient(int(np.prod(dims)), sigma)
+    return oop.Problem(*dims, p, V, coeff=c)
+
+
+def test_exact_local_inverses_give_weighted_additive_schwarz():
+    prob = _prob()
+    A = oop.assemble(prob, DIFFUSION)
+    dmap, S, W = ol.patch_data(prob, DIFFUSION)
+    Sp = np.where(S > 0, 1.0 / np.where(S > 0, S, 1.0), 0.0)        # pseudo-inverse of S
+    inv = [np.linalg.inv(ol.local_block(prob, DIFFUSION, e, A)) for e in range(prob.ne)]
+
+    def f_exact(Xn, elems):   # x -> S_e^+ A_ee^-1 S_e^+ x, element by element
+        return np.stack([Sp[dmap[e]] * (inv[e] @ (Sp[dmap[e]] * x)) for x, e in zip(Xn, elems)])
+
+    Mx = ol.additive_schwarz(prob, DIFFUSION)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        r = rng.standard_normal(prob.ndofs)
+        z = ol.patch_apply(prob, DIFFUSION, f_exact, r)
+        assert np.abs(z - Mx @ r).max() <= 1e-12 * np.abs(Mx @ r).max()
+    mask = boundary_mask(prob.nx, prob.ny, prob.nz, prob.p) == 1
+    Mi = Mx[~mask][:, ~mask]
+    assert np.allclose(Mi, Mi.T, rtol=0, atol=1e-14 * np.abs(Mi).max())
+    assert np.linalg.eigvalsh(Mi).min() > 0                            # SPD on the free dofs
+    assert np.all(Mx[mask] == 0) and np.all(Mx[:, mask] == 0)
+
+
+def test_local_block_equals_probing_the_operator():
+    prob = _prob((4, 3, 3), 3)
+    e = 1 + 4 * (1 + 3 * 1)                                             # interior element
+    idx = dof_map(prob.nx, prob.ny, prob.nz, prob.p, [e])[0]
+    Aee = ol.local_block(prob, DIFFUSION, e)
+    probe = np.zeros_like(Aee)
+    for a, g in enumerate(idx):
+        u = np.zeros(prob.ndofs)
+        u[g] = 1.0
+        probe[:, a] = oop.apply(prob, u, DIFFUSION)[idx]
+    assert np.abs(probe - Aee).max() <= 1e-13 * np.abs(Aee).max()
+    # the target relation t = S^-1 A_ee^-1 S^-1 x, and t does not depend on the scale of x
+    _, S, _ = ol.patch_data(prob, DIFFUSION)
+    x = np.random.default_rng(1).standard_normal(len(idx))
+    t = ol.local_target(prob, DIFFUSION, e, x)
+    assert np.abs(S[idx] * (Aee @ (S[idx] * t)) - x).max() <= 1e-12 * np.abs(x).max()
+    assert np.allclose(ol.local_target(prob, DIFFUSION, e, 3.0 * x), 3.0 * t, rtol=1e-13, atol=0)
+    with pytest.raises(ValueError):
+        ol.local_target(prob, DIFFUSION, 0, x)                          # touches the boundary
+
+
+def test_fcg_with_fixed_spd_preconditioner_is_pcg():
+    prob = _prob((4, 3, 3), 2)
+    m = boundary_mask(prob.nx, prob.ny, prob.nz, prob.p).astype(np.float64)
+    keep = 1.0 - m
+    A = oop.assemble(prob, DIFFUSION)
+    Abc = lambda v: keep * (A @ (keep * v)) + m * v
+    d = oop.diagonal(prob, DIFFUSION) * keep + m
+    b = load_vector(prob) * keep
+    x_p, it_p, hist_p = oracle_pcg(Abc, b, d, rtol=1e-10)
+    x_f, it_f, hist_f, _ = ol.fcg(Abc, lambda r: r / d, b, rtol=1e-10)
+    assert it_f == it_p
+    assert np.allclose(hist_f, hist_p, rtol=1e-6, atol=1e-14)
+    assert np.abs(x_f - x_p).max() <= 1e-10 * np.abs(x_p).max()
+    # a nonlinear (positively homogeneous) preconditioner still converges to the solution
+    x_n, it_n, _, _ = ol.fcg(Abc, lambda r: r / d * (1.0 + 0.1 * np.tanh(r / (np.abs(r).max() + 1e-300))),
+                             b, rtol=1e-10, maxit=2000)
+    assert np.abs(x_n - x_p).max() <= 1e-7 * np.abs(x_p).max()
+
+
+@pytest.mark.parametrize("width", [0, 16])
+def test_patch_apply_homogeneous_and_bf16_bound(width):
+    prob = _prob((3, 2, 3), 2)
+    din = (prob.p + 1) ** 3
+    rng = np.random.default_rng(5 + width)
+    W = omlp.init_weights(din, width, 9)[:3] + (0.2 * rng.standard_normal((din, din)),)
+    Wb = tuple(ol.bf16_round(w) for w in W)
+    r = rng.standard_normal(prob.ndofs)
+    z, zb = ol.patch_apply(prob, DIFFUSION, ol.network(Wb), r, bound=ol.network_rounding_bound(Wb))
+    z2 = ol.patch_apply(prob, DIFFUSION, ol.network(Wb), 2.5 * r)
+    assert np.allclose(z2, 2.5 * z, rtol=1e-13, atol=1e-300)
+    # an explicit BF16 evaluation (rounded input and hidden activations) stays inside the bound
+    W1, W2, W3, W0 = omlp._weights(Wb)
+
+    def f_bf16(Xn, elems):
+        a = ol.bf16_round(Xn)
+        y = a @ W0
+        if width:
+            h = ol.bf16_round(omlp.relu(a @ W1))
+            h = ol.bf16_round(omlp.relu(h @ W2))
+            y = y + h @ W3
+        return y
+    zq = ol.patch_apply(prob, DIFFUSION, f_bf16, r)
+    assert np.all(np.abs(zq - z) <= zb)
+    assert np.abs(zq - z).max() > 0 and zb.max() <= 0.25 * np.abs(z).max()
+
+
+def test_adam_closed_forms():
+    rng = np.random.default_rng(2)
+    w0, g1, g2 = rng.standard_normal(50), rng.standard_normal(50), rng.standard_normal(50)
+    m0, v0 = np.zeros(50), np.zeros(50)
+    lr, eps = 1e-3, 1e-8
+    w1, m1, v1 = ol.adam_step(w0, g1, m0, v0, 1, lr)
+    # first step: bias-corrected moments are g and g^2, so the step is lr * g / (|g| + eps)
+    assert np.allclose(w1, w0 - lr * g1 / (np.abs(g1) + eps), rtol=1e-14, atol=0)
+    w2, m2, v2 = ol.adam_step(w1, g2, m1, v1, 2, lr)
+    mh = (0.9 * 0.1 * g1 + 0.1 * g2) / (1 - 0.81)
+    vh = (0.999 * 0.001 * g1 ** 2 + 0.001 * g2 ** 2) / (1 - 0.999 ** 2)
+    assert np.allclose(w2, w1 - lr * mh / (np.sqrt(vh) + eps), rtol=1e-13, atol=0)
+    # a constant gradient moves every weight by lr per step
+    w, m, v = w0.copy(), m0.copy(), v0.copy()
+    for t in range(1, 6):
+        w, m, v = ol.adam_step(w, np.full(50, 0.3), m, v, t, lr)
+    assert np.allclose(w, w0 - 5 * lr, rtol=0, atol=1e-9)
