@@ -47,7 +47,8 @@ EXTRA_STEPS = 5                        # timed repetitions of the secondary meas
 # 32^3 mesh of the same order, with that launch's algorithmic bytes: scaled to the benchmark's
 # launch by the algorithmic bytes (traffic grows with the elements).  Only for kernels
 # unchanged since the capture; (variant, order) -> (dram bytes, algorithmic bytes, case).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("f64", 3): (219.914496e6 + 4.658432e6, 219599376, "32^3 hexes, p = 3"),
+               ("f32x2", 3): (219.971840e6 + 4.723968e6, 219599376, "32^3 hexes, p = 3")}
 
 
 def measured_peaks():
@@ -142,6 +143,57 @@ def measure_mixed(fe, torch, n, stream, reps=10, ph=4, pl=3):
                                  "peak_source": src}},
             "paper_context": "GB200 DMMA fused PA 46.60 GDOF/s, GH200 36.15 (FP64, 540 M DOF, "
                              "Table VI; other hardware)"}
+
+
+def run_refinement(args, local_rank):
+    """--refinement: the mixed-precision configuration (default 96^3 hexes, p = 4, manufactured
+    sine load, Jacobi, rtol 1e-8): FP64 Jacobi-PCG, float-float Jacobi-PCG and the refinement
+    (FP32 inner PCG, FP64 outer residual), each timed with CUDA events; every answer's FP64 true
+    residual and its difference from the FP64 solve; one JSON line."""
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import perturbed_vertices
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    n, p = args.n, args.p
+    mesh = fe.fe_mesh_setup(n, n, n, p, perturbed_vertices(n, n, n))
+    pa = fe.fe_pa_setup(mesh, 0, None, fe.FE_DIFFUSION)
+    nd, ne, _ = fe.fe_mesh_sizes(mesh)
+    stream = torch.cuda.current_stream()
+    b = torch.empty(nd, dtype=torch.float64, device="cuda")
+    fe.fe_load_vector_sine(pa, b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"refinement": True, "workload": "poisson_%dcubed_p%d_jacobi" % (n, p), "ndofs": nd,
+           "rtol": args.rtol}
+    xs = {}
+    for name, variant in (("fp64_pcg", "f64"), ("ff_pcg", "f32x2"), ("ir_f32_inner", "f64")):
+        fe.fe_pa_set_variant(pa, variant)
+        x = torch.empty_like(b)
+
+        def run():
+            if name == "ir_f32_inner":
+                return fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT,
+                                    args.inner_rtol, stream)
+            return fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, args.rtol, MAXIT, stream)
+        run()                                           # warm-up (workspace, copies)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st, stats = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xs[name] = x
+        out[name] = {"status": st, "time_s": e0.elapsed_time(e1) / 1e3, "iters": stats["iters"],
+                     "outer_iters": stats["outer_iters"], "true_rel_resid": stats["true_rel_resid"],
+                     "variant": variant if name != "ir_f32_inner" else "f32 inner, f64 outer"}
+    ref = xs["fp64_pcg"]
+    for name in ("ff_pcg", "ir_f32_inner"):
+        out[name]["x_vs_fp64_pcg"] = float((xs[name] - ref).abs().max()) / float(ref.abs().max())
+        out[name]["speedup_vs_fp64_pcg"] = out["fp64_pcg"]["time_s"] / out[name]["time_s"]
+    out["ir_f32_inner"]["speedup_vs_ff_pcg"] = out["ff_pcg"]["time_s"] / out["ir_f32_inner"]["time_s"]
+    fe.fe_pa_destroy(pa)
+    fe.fe_mesh_destroy(mesh)
+    print(json.dumps(out))
+    return 0
 
 
 def run_mixed_h1l2(args, local_rank):
@@ -1047,6 +1099,9 @@ def main():
     ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32/BF16-mma.sync throughput probes")
     ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")
+    ap.add_argument("--refinement", action="store_true",
+                    help="FP64 / float-float Jacobi-PCG vs mixed-precision refinement on --n^3, "
+                         "order --p (the mixed-precision configuration is --n 96 --p 4)")
     ap.add_argument("--mixed-h1l2", action="store_true",
                     help="only the paper's mixed H1 p=4 / L2 p=3 pair on --n^3 hexes")
     ap.add_argument("--paper-operator-n", type=int, default=128,
@@ -1077,6 +1132,8 @@ def main():
         return run_mixed_orders(args, local_rank)
     if args.mixed_h1l2:
         return run_mixed_h1l2(args, local_rank)
+    if args.refinement:
+        return run_refinement(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

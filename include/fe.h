@@ -139,13 +139,26 @@ int fe_pa_setup(const fe_mesh* mesh, int q1d, const double* dev_coeff, int ops, 
 int fe_pa_set_variant(fe_pa* pa, int variant, void* stream);
 int fe_pa_get_variant(const fe_pa* pa, int* variant);
 
-/* Autotuner of the arithmetic (an extension): times one apply of op (nrhs right-hand sides in
- * one batched launch, 1..64) with each FP64-accurate variant -- FE_VARIANT_F32X2, FE_VARIANT_F64
- * and, for nrhs = 1, FE_VARIANT_F64_DMMA -- as the mean of `reps` launches after one
- * warm-up (CUDA events on `stream`), selects the fastest with fe_pa_set_variant, and returns it
- * in *best_variant; ms (NULL or double[4], indexed by fe_variant) gets the times, -1 where not
- * timed.  FE_VARIANT_F32 is not a candidate (not FP64-accurate).  Allocates 2 nrhs vectors of
- * scratch.  Synchronous. */
+/* Launch shape of the fused apply for (op, variant): every arithmetic has a few built shapes
+ * (threads per block, and a shared-memory budget that fixes the elements per block: shape 0 the
+ * default, others with smaller blocks and more of them per SM).  fe_pa_set_shape selects one
+ * (FE_ERR_ARG if the index is not built for the variant); fe_pa_get_shape returns the selected
+ * index, the number of built shapes, and the threads and elements per block of the selected
+ * shape for this handle's order (0 for FE_VARIANT_F64_DMMA, whose kernel has one fixed shape);
+ * any output may be NULL. */
+int fe_pa_set_shape(fe_pa* pa, int op, int variant, int shape);
+int fe_pa_get_shape(const fe_pa* pa, int op, int variant, int* shape, int* nshapes,
+                    int* threads_per_block, int* elems_per_block);
+
+/* Autotuner of the arithmetic and the launch shape (an extension): times one apply of op (nrhs
+ * right-hand sides in one batched launch, 1..64) with each FP64-accurate variant --
+ * FE_VARIANT_F32X2, FE_VARIANT_F64 and, for nrhs = 1, FE_VARIANT_F64_DMMA -- in each of its
+ * built launch shapes, as the mean of `reps` launches after one warm-up (CUDA events on
+ * `stream`); keeps the fastest shape of every variant (fe_pa_get_shape reports it), selects the
+ * fastest variant with fe_pa_set_variant and returns it in *best_variant; ms (NULL or double[4],
+ * indexed by fe_variant) gets each variant's time in its fastest shape, -1 where not timed.
+ * FE_VARIANT_F32 is not a candidate (not FP64-accurate).  Allocates 2 nrhs vectors of scratch.
+ * Synchronous. */
 int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, double* ms,
                    void* stream);
 
@@ -316,7 +329,9 @@ int fe_probe_throughput(int unit, double* tflops);
  * FP64 Cholesky; f is trained with Adam, to the relative squared error,
  * on pairs x = S_e v, t = S_e^{-1} A_ee^{-1} v scaled by 1/||t||, for v i.i.d. normal, A_ee u for
  * normal u, or W_e r for residuals r of a short Jacobi-FCG run.
- * Built for orders 1..4 (the FP64 Cholesky of A_ee runs in one block's shared memory).
+ * Built for orders 1..8: the FP64 Cholesky of A_ee runs in one block's shared memory up to
+ * order 4 and by 32-column panels in shared memory above; the fused inference kernel covers
+ * D^3 <= 128 (orders 1..4), higher orders apply the network by the unfused GEMM path.
  * Handles are library-owned, refer to (do not own) their fe_pa, and are not thread-safe. */
 typedef struct fe_lpc fe_lpc;
 
@@ -334,7 +349,7 @@ int fe_lpc_nparams(const fe_lpc* lpc, int64_t* nparams);
  * pairs drawn from the training set, which is generated on the first call with `reps` pairs per
  * sampled element (0 => 16).  *final_loss (may be NULL) = the relative squared error of the last
  * batch before its step.  Returns FE_ERR_ARG if the mesh has fewer than 3 elements per axis,
- * FE_ERR_UNSUPPORTED for orders above 4, FE_ERR_BREAKDOWN if a sampled block is not positive
+ * FE_ERR_BREAKDOWN if a sampled block is not positive
  * definite.  Synchronous. */
 int fe_lpc_train(fe_lpc* lpc, int steps, int batch, double lr, int reps, double* final_loss,
                  void* stream);

@@ -38,16 +38,10 @@ BIG = 1 << 20
 
 
 def _lagrange_at(nodes, x):
-    """Lagrange basis of ``nodes`` at the single point x; a point within 1e-13 of a node is that
-    node (GLL nodes of different orders coincide at 0, 1/2 and 1, and separately computed values
-    of one point may differ in the last bit)."""
-    t = np.asarray(nodes, dtype=np.float64)
-    hit = np.nonzero(np.abs(t - x) <= 1e-13)[0]
-    if hit.size:
-        out = np.zeros(len(t))
-        out[hit[0]] = 1.0
-        return out
-    return lagrange(t, [x])[0][0]
+    """Lagrange basis of ``nodes`` at the single point x (the product formula; where x coincides
+    with a node only up to the last bit -- GLL nodes of different orders meet at 0, 1/2 and 1 --
+    the values differ from 0 and 1 by rounding)."""
+    return lagrange(np.asarray(nodes, dtype=np.float64), [x])[0][0]
 
 
 class VarSpace:
@@ -196,8 +190,7 @@ class VarSpace:
                     row = _combine(w, frows)
                 r = int(self.local_first[e]) + a
                 for c, val in row.items():
-                    # cancelling contributions leave ~1e-17 where the exact weight is 0
-                    if abs(val) > 1e-13:
+                    if val != 0.0:
                         ri.append(r)
                         ci.append(c)
                         data.append(val)

@@ -305,9 +305,21 @@ int compute_qdata(fe_pa* pa, const double* coeff, cudaStream_t s, int* d_bad) {
 // ------------------------------------------------------------------------------- dispatch
 namespace fe {
 
+int apply_shape_count(int variant) {
+  switch (variant) {
+    case FE_VARIANT_F64:
+      return kShapesF64;
+    case FE_VARIANT_F32X2:
+      return kShapesF32x2;
+    default:
+      return 1;
+  }
+}
+
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
                    cudaStream_t s, const int* skip, double* dot_part, int64_t* blocks,
-                   bool query_only, int nrhs, int64_t ldx, int64_t ldy) {
+                   bool query_only, int nrhs, int64_t ldx, int64_t ldy, int* elems_per_block,
+                   int* threads_per_block) {
   if (!pa || ((!x || !y) && !query_only)) return set_error(FE_ERR_ARG, "fe_apply: null argument");
   if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_apply: bad op");
   if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_apply: operator not set up in fe_pa_setup");
@@ -360,6 +372,9 @@ int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double
   a.nrhs = nrhs;
   a.ldx = ldx;
   a.ldy = ldy;
+  if (variant >= 0 && variant < 4) a.shape = pa->shape[op == FE_DIFFUSION ? 0 : 1][variant];
+  a.elems_per_block = elems_per_block;
+  a.threads_per_block = threads_per_block;
   switch (variant) {
     case FE_VARIANT_F64:
       return launch_apply_f64(op, a, s);
@@ -624,6 +639,48 @@ int fe_pa_get_variant(const fe_pa* pa, int* variant) {
   return FE_OK;
 }
 
+int fe_pa_set_shape(fe_pa* pa, int op, int variant, int shape) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_pa_set_shape: pa is NULL");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pa_set_shape: bad op");
+  if (variant < 0 || variant > 3) return set_error(FE_ERR_ARG, "fe_pa_set_shape: bad variant");
+  if (shape < 0 || shape >= apply_shape_count(variant))
+    return set_error(FE_ERR_ARG, "fe_pa_set_shape: no such shape for this variant");
+  pa->shape[op == FE_DIFFUSION ? 0 : 1][variant] = shape;
+  return FE_OK;
+}
+
+int fe_pa_get_shape(const fe_pa* pa, int op, int variant, int* shape, int* nshapes,
+                    int* threads_per_block, int* elems_per_block) {
+  clear_error();
+  if (!pa) return set_error(FE_ERR_ARG, "fe_pa_get_shape: pa is NULL");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pa_get_shape: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pa_get_shape: operator not set up");
+  if (variant < 0 || variant > 3) return set_error(FE_ERR_ARG, "fe_pa_get_shape: bad variant");
+  if (shape) *shape = pa->shape[op == FE_DIFFUSION ? 0 : 1][variant];
+  if (nshapes) *nshapes = apply_shape_count(variant);
+  int ne = 0, nt = 0;
+  if (variant != FE_VARIANT_F64_DMMA) {
+    // the launch geometry without launching (no data needed for a query)
+    fe_pa tmp = *pa;
+    if (variant == FE_VARIANT_F32X2) {
+      tmp.d_qd_diff2 = tmp.d_qd_diff ? tmp.d_qd_diff : nullptr;
+      tmp.d_qd_mass2 = tmp.d_qd_mass ? tmp.d_qd_mass : nullptr;
+    }
+    if (variant == FE_VARIANT_F32) {
+      tmp.d_qd_diff32 = reinterpret_cast<float*>(tmp.d_qd_diff);
+      tmp.d_qd_mass32 = reinterpret_cast<float*>(tmp.d_qd_mass);
+    }
+    int64_t nblk = 0;
+    const int st = apply_dispatch(&tmp, op, variant, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  &nblk, true, 1, 0, 0, &ne, &nt);
+    if (st != FE_OK) return st;
+  }
+  if (threads_per_block) *threads_per_block = nt;
+  if (elems_per_block) *elems_per_block = ne;
+  return FE_OK;
+}
+
 int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, double* ms,
                    void* stream) {
   clear_error();
@@ -648,26 +705,36 @@ int fe_pa_autotune(fe_pa* pa, int op, int nrhs, int reps, int* best_variant, dou
   // any input gives the same work; a smooth, nonzero one keeps the arithmetic representative
   k_load_sine_like<<<256, 256, 0, s>>>(x, n * nrhs);
   const int cand[3] = {FE_VARIANT_F32X2, FE_VARIANT_F64, FE_VARIANT_F64_DMMA};
+  const int oi = (op == FE_DIFFUSION) ? 0 : 1;
   double t[4] = {-1.0, -1.0, -1.0, -1.0};
   int best = -1, st = FE_OK;
   for (int c = 0; c < 3 && st == FE_OK; ++c) {
     const int v = cand[c];
     if (v == FE_VARIANT_F64_DMMA && nrhs > 1) continue;  // no batched DMMA kernel
     if ((st = fe_pa_set_variant(pa, v, stream)) != FE_OK) break;
-    for (int r = 0; r <= reps && st == FE_OK; ++r) {  // the first launch is a warm-up
-      if (r == 1) cudaEventRecord(e0, s);
-      st = apply_dispatch(pa, op, v, x, y, s, nullptr, nullptr, nullptr, false, nrhs, n, n);
+    int best_shape = 0;
+    for (int k = 0; k < apply_shape_count(v) && st == FE_OK; ++k) {
+      pa->shape[oi][v] = k;
+      for (int r = 0; r <= reps && st == FE_OK; ++r) {  // the first launch is a warm-up
+        if (r == 1) cudaEventRecord(e0, s);
+        st = apply_dispatch(pa, op, v, x, y, s, nullptr, nullptr, nullptr, false, nrhs, n, n);
+      }
+      if (st != FE_OK) break;
+      cudaEventRecord(e1, s);
+      if ((err = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = cuda_error(err, "fe_pa_autotune: timing");
+        break;
+      }
+      float msf = 0.0f;
+      cudaEventElapsedTime(&msf, e0, e1);
+      const double tk = msf / reps;
+      if (t[v] < 0.0 || tk < t[v]) {
+        t[v] = tk;
+        best_shape = k;
+      }
     }
-    if (st != FE_OK) break;
-    cudaEventRecord(e1, s);
-    if ((err = cudaEventSynchronize(e1)) != cudaSuccess) {
-      st = cuda_error(err, "fe_pa_autotune: timing");
-      break;
-    }
-    float msf = 0.0f;
-    cudaEventElapsedTime(&msf, e0, e1);
-    t[v] = msf / reps;
-    if (best < 0 || t[v] < t[best]) best = v;
+    pa->shape[oi][v] = best_shape;
+    if (st == FE_OK && (best < 0 || t[v] < t[best])) best = v;
   }
   if (st == FE_OK) st = fe_pa_set_variant(pa, best, stream);
   if (st == FE_OK) {

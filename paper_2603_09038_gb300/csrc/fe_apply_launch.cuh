@@ -39,6 +39,20 @@ namespace fe {
 #define FE_F32X2_REREAD_D 2
 #endif
 
+// Launch shapes (threads per block, shared-memory budget -> elements per block, minimum blocks
+// per SM for the register allocation).  Each arithmetic has a few built shapes; shape 0 is the
+// default and fe_pa_autotune times the others.
+template <int NT_, int SMEM_, int MINB_>
+struct Shape {
+  static constexpr int NT = NT_, SMEM = SMEM_, MINB = MINB_;
+};
+template <class Ar, int I>
+struct ApplyShape;
+template <class Ar>
+struct ApplyShapeCount {
+  static constexpr int N = 1;
+};
+
 template <class Ar>
 struct ApplyTuning;
 // SPLIT: a separate single-right-hand-side instantiation (the batch loop cost the
@@ -70,7 +84,33 @@ struct ApplyTuning<ArF32x2T<A, L>> {
   static constexpr bool SPLIT = false;
 };
 
-// Elements per block: as many as fit in the variant's shared-memory budget, a power of two,
+template <>
+struct ApplyShape<ArF64, 0> : Shape<FE_F64_NT, FE_F64_SMEM, FE_F64_MINB> {};
+template <>
+struct ApplyShape<ArF64, 1> : Shape<128, 48 * 1024, 3> {};
+template <>
+struct ApplyShape<ArF64, 2> : Shape<256, 96 * 1024, 1> {};
+template <>
+struct ApplyShapeCount<ArF64> {
+  static constexpr int N = 3;
+};
+template <bool A, bool L>
+struct ApplyShape<ArF32x2T<A, L>, 0> : Shape<FE_F32X2_NT, FE_F32X2_SMEM, FE_F32X2_MINB> {};
+template <bool A, bool L>
+struct ApplyShape<ArF32x2T<A, L>, 1> : Shape<128, 48 * 1024, 4> {};
+template <bool A, bool L>
+struct ApplyShape<ArF32x2T<A, L>, 2> : Shape<256, 48 * 1024, 2> {};
+template <bool A, bool L>
+struct ApplyShapeCount<ArF32x2T<A, L>> {
+  static constexpr int N = 3;
+};
+template <>
+struct ApplyShape<ArF32, 0> : Shape<FE_F32_NT, FE_F32_SMEM, FE_F32_MINB> {};
+static_assert(ApplyShapeCount<ArF64>::N == kShapesF64 &&
+                  ApplyShapeCount<ArF32x2T<true, true>>::N == kShapesF32x2,
+              "shape counts of fe_internal.h out of date");
+
+// Elements per block: as many as fit in the shape's shared-memory budget, a power of two,
 // at most 64.
 template <int D, int Q, bool DIFF, class T, int SMEM, bool RR>
 constexpr int elems_per_block() {
@@ -134,15 +174,17 @@ inline void fill_tab(const Basis1D& b, TabF32x2<D, Q>* t) {
   t->cG = (float)(cG * up);
 }
 
-template <int D, int Q, bool DIFF, class Ar, class VT, bool MULTI>
+template <int D, int Q, bool DIFF, class Ar, class VT, bool MULTI, class SH>
 int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   using T = typename Ar::T;
   using Tune = ApplyTuning<Ar>;
-  constexpr int NT = Tune::NT;
+  constexpr int NT = SH::NT;
   constexpr bool RR = (D >= Tune::REREAD_D);
-  constexpr int NE = elems_per_block<D, Q, DIFF, T, Tune::SMEM, RR>();
+  constexpr int NE = elems_per_block<D, Q, DIFF, T, SH::SMEM, RR>();
+  if (a.elems_per_block) *a.elems_per_block = NE;
+  if (a.threads_per_block) *a.threads_per_block = NT;
   const size_t smem = (size_t)NE * ApplyLayout<D, Q, DIFF, (int)sizeof(T), RR>::PER_ELEM * sizeof(T);
-  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), Tune::MINB, VT, MULTI>;
+  auto kern = k_pa_apply<D, Q, NE, NT, DIFF, Ar, (D >= Tune::REREAD_D), SH::MINB, VT, MULTI>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -163,12 +205,23 @@ int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   return cuda_error(cudaGetLastError(), "apply kernel launch");
 }
 
+template <int D, int Q, bool DIFF, class Ar, class VT, class SH>
+int run_shape(const ApplyArgs& a, cudaStream_t s) {
+  if constexpr (ApplyTuning<Ar>::SPLIT) {
+    if (a.nrhs == 1) return launch_kernel<D, Q, DIFF, Ar, VT, false, SH>(a, s);
+  }
+  return launch_kernel<D, Q, DIFF, Ar, VT, true, SH>(a, s);
+}
+
 template <int D, int Q, bool DIFF, class Ar, class VT = double>
 int run_apply(const ApplyArgs& a, cudaStream_t s) {
-  if constexpr (ApplyTuning<Ar>::SPLIT) {
-    if (a.nrhs == 1) return launch_kernel<D, Q, DIFF, Ar, VT, false>(a, s);
-  }
-  return launch_kernel<D, Q, DIFF, Ar, VT, true>(a, s);
+  constexpr int N = ApplyShapeCount<Ar>::N;
+  if (a.shape < 0 || a.shape >= N) return set_error(FE_ERR_ARG, "apply: no such launch shape");
+  if constexpr (N > 2)
+    if (a.shape == 2) return run_shape<D, Q, DIFF, Ar, VT, ApplyShape<Ar, (N > 2 ? 2 : 0)>>(a, s);
+  if constexpr (N > 1)
+    if (a.shape == 1) return run_shape<D, Q, DIFF, Ar, VT, ApplyShape<Ar, (N > 1 ? 1 : 0)>>(a, s);
+  return run_shape<D, Q, DIFF, Ar, VT, ApplyShape<Ar, 0>>(a, s);
 }
 
 // Dispatch on the order for the default rule Q = p + 2 (Ar may depend on the order through

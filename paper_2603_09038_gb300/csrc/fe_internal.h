@@ -11,6 +11,8 @@
 namespace fe {
 
 constexpr int kMaxOrder = 8;
+// built launch shapes of the fused apply per arithmetic (fe_apply_launch.cuh lists them)
+constexpr int kShapesF64 = 3, kShapesF32x2 = 3;
 constexpr int kMaxD = kMaxOrder + 1;
 constexpr int kMaxQ = kMaxOrder + 2;
 
@@ -75,6 +77,7 @@ struct fe_pa {
   float* d_qd_diff32 = nullptr;    // FP32 copy for FE_VARIANT_F32 (made on first use), times
   float* d_qd_mass32 = nullptr;    // 2^-qd32_shift[op] (its largest entry in [1, 2))
   int qd32_shift[2] = {0, 0};      // diffusion, mass
+  int shape[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // launch shape per (operator, variant)
   // PCG workspace (allocated on first fe_pcg, freed by fe_pa_destroy)
   double* d_work = nullptr;        // 5 vectors of ndofs
   double* d_red = nullptr;         // reduction partials + scalars
@@ -106,6 +109,9 @@ struct ApplyArgs {
   bool query_only;       // only report the grid size
   int nrhs = 1;          // right-hand sides x + r ldx -> y + r ldy, r < nrhs
   int64_t ldx = 0, ldy = 0;
+  int shape = 0;         // launch shape index (fe_pa_set_shape)
+  int* elems_per_block = nullptr;    // optional outs: the launch shape's geometry
+  int* threads_per_block = nullptr;
 };
 
 // Launchers (one translation unit per variant); return FE_OK or an error status.
@@ -132,7 +138,10 @@ int encode_f32x2(const double* src, double* dst, int32_t* scale, int64_t ne, int
 int apply_dispatch(const fe_pa* pa, int op, int variant, const double* x, double* y,
                    cudaStream_t s, const int* skip = nullptr, double* dot_part = nullptr,
                    int64_t* blocks = nullptr, bool query_only = false, int nrhs = 1,
-                   int64_t ldx = 0, int64_t ldy = 0);
+                   int64_t ldx = 0, int64_t ldy = 0, int* elems_per_block = nullptr,
+                   int* threads_per_block = nullptr);
+// Number of built launch shapes of a variant (FE_VARIANT_F64_DMMA: 1).
+int apply_shape_count(int variant);
 
 // y = A x with the FP32 variant on float vectors (the caller zeroes y); same skip / dot_part
 // semantics as apply_dispatch.

@@ -76,7 +76,7 @@ struct fe_lpc {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kLpcMaxOrder = 4;          // FP64 Cholesky of A_ee in one block's shared memory
+constexpr int kLpcMaxOrder = 8;          // Cholesky of A_ee: whole block or panels in smem
 constexpr int64_t kProbeDoubles = 1 << 28;  // bound on the probed blocks (2 GB)
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // splitmix64 finaliser
@@ -186,6 +186,66 @@ __global__ void k_cholesky(double* __restrict__ Aee, int din, int* __restrict__ 
     __syncthreads();
   }
   for (int i = threadIdx.x; i < din * din; i += blockDim.x) A[i] = sm[i];
+}
+
+// Batched Cholesky for blocks too large for one block's shared memory (D^3 > 125): one thread
+// block per matrix, right-looking by panels of kPanel columns.  Each panel (its rows kb..n-1) is
+// loaded into shared memory, factored there column by column, written back, and then applied
+// to the trailing lower triangle (A[i][j] -= sum_c L[i][c] L[j][c]) with both factors read from
+// shared memory, so the trailing matrix in global memory is read and written once per panel.
+constexpr int kPanel = 32;
+
+__global__ void __launch_bounds__(256) k_cholesky_blocked(double* __restrict__ Aee, int din,
+                                                          int* __restrict__ fail) {
+  extern __shared__ double pn[];  // [din][kPanel]: rows kb.. of the current panel
+  double* A = Aee + (int64_t)blockIdx.x * din * din;
+  for (int kb = 0; kb < din; kb += kPanel) {
+    const int w = din - kb < kPanel ? din - kb : kPanel;
+    const int rows = din - kb;
+    for (int t = threadIdx.x; t < rows * w; t += blockDim.x) {
+      const int i = t / w, c = t - i * w;
+      pn[i * kPanel + c] = A[(int64_t)(kb + i) * din + kb + c];
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+      if (threadIdx.x == 0) {
+        const double d = pn[c * kPanel + c];
+        if (!(d > 0.0)) atomicExch(fail, 1);
+        pn[c * kPanel + c] = sqrt(d > 0.0 ? d : 1.0);
+      }
+      __syncthreads();
+      const double lcc = pn[c * kPanel + c];
+      for (int i = c + 1 + threadIdx.x; i < rows; i += blockDim.x) pn[i * kPanel + c] /= lcc;
+      __syncthreads();
+      // the rest of the panel: columns c' in (c, w), rows i >= c'
+      const int nc = w - c - 1;
+      for (int t = threadIdx.x; t < (rows - c - 1) * nc; t += blockDim.x) {
+        const int i = c + 1 + t / nc, cp = c + 1 + t % nc;
+        if (i >= cp) pn[i * kPanel + cp] -= pn[i * kPanel + c] * pn[cp * kPanel + c];
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < rows * w; t += blockDim.x) {
+      const int i = t / w, c = t - i * w;
+      if (i >= c) A[(int64_t)(kb + i) * din + kb + c] = pn[i * kPanel + c];
+    }
+    // trailing update of the lower triangle: rows and columns kb + w .. din - 1
+    const int m = rows - w;
+    const int64_t ntri = (int64_t)m * (m + 1) / 2;
+    for (int64_t t = threadIdx.x; t < ntri; t += blockDim.x) {
+      // (i, j) with 0 <= j <= i < m from the triangular index t = i (i + 1) / 2 + j
+      int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((int64_t)i * (i + 1) / 2 > t) --i;
+      while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+      const int j = (int)(t - (int64_t)i * (i + 1) / 2);
+      const double* li = pn + (w + i) * kPanel;
+      const double* lj = pn + (w + j) * kPanel;
+      double acc = 0.0;
+      for (int c = 0; c < w; ++c) acc = fma(li[c], lj[c], acc);
+      A[(int64_t)(kb + w + i) * din + kb + w + j] -= acc;
+    }
+    __syncthreads();
+  }
 }
 
 // Samples: per sample element s and replica q, v is (q mod 3) i.i.d. normal, A_ee u for normal u
@@ -951,8 +1011,15 @@ int make_samples(fe_lpc* L, int reps, cudaStream_t s, double** xd = nullptr,
   }
   if (st == FE_OK) {
     const size_t shm = sizeof(double) * din * din;
-    cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_cholesky<<<ns, 128, shm, s>>>(Aee, din, d_fail);
+    if (shm <= 200 * 1024) {  // the whole block in shared memory (orders 1..4)
+      cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_cholesky<<<ns, 128, shm, s>>>(Aee, din, d_fail);
+    } else {                  // panels in shared memory (orders 5..8)
+      const size_t pshm = sizeof(double) * din * kPanel;
+      cudaFuncSetAttribute(k_cholesky_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pshm);
+      k_cholesky_blocked<<<ns, 256, pshm, s>>>(Aee, din, d_fail);
+    }
     L->nsamp = (int64_t)ns * reps;
     if ((err = cudaMalloc(&L->Xs, sizeof(__nv_bfloat16) * L->nsamp * din)) != cudaSuccess ||
         (err = cudaMalloc(&L->Ts, sizeof(float) * L->nsamp * din)) != cudaSuccess)
@@ -1286,7 +1353,7 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
   if ((width != 0 && width < 8) || width > 4096)
     return set_error(FE_ERR_ARG, "fe_lpc_create: width must be 0 (linear) or 8..4096");
   if (pa->p > kLpcMaxOrder)
-    return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_create: orders above 4 are not built");
+    return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_create: orders above 8 are not built");
   fe_lpc* L = new fe_lpc();
   L->pa = pa;
   L->op = op;

@@ -84,6 +84,10 @@ _SIGS = {
                                         ctypes.c_double, _VP, _VP, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_set_graphs": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_pa_set_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "fe_pa_get_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fe_pa_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     "fe_pcg_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP,
@@ -333,6 +337,18 @@ def fe_pcg_batched(pa, op, pc, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stream
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, [_stats(x) for x in st]
+
+
+def fe_pa_set_shape(pa, op, variant, shape):
+    _check(load().fe_pa_set_shape(_VP(pa), int(op), VARIANTS.get(variant, variant), int(shape)))
+
+
+def fe_pa_get_shape(pa, op, variant):
+    """(selected shape, built shapes, threads per block, elements per block)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().fe_pa_get_shape(_VP(pa), int(op), VARIANTS.get(variant, variant),
+                                  *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def fe_pa_autotune(pa, op, nrhs=1, reps=5, stream=None):

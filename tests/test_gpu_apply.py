@@ -239,3 +239,29 @@ def test_autotune_selects_fastest_accurate_variant(nrhs):
         for bad in ((0, 3), (65, 3), (1, 0)):
             with pytest.raises(fe.FEError):
                 fe.fe_pa_autotune(pa, fe.FE_DIFFUSION, *bad)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32x2"])
+@pytest.mark.parametrize("p", [1, 3, 5, 8])
+def test_every_launch_shape_matches_oracle(variant, p):
+    """Each built launch shape (threads and elements per block, the autotuner's candidates) of
+    the FP64 and float-float kernels against the oracle, on meshes with a ragged last block."""
+    dims = (5, 4, 7) if p <= 3 else (3, 2, 5)
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, variant)
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        xh = uniform_vector(prob.ndofs, seed=p + 20)
+        _, nshapes, _, _ = fe.fe_pa_get_shape(pa, 1, variant)
+        assert nshapes >= 2
+        geoms = set()
+        for k in range(nshapes):
+            for op, kind in OPS:
+                fe.fe_pa_set_shape(pa, op, variant, k)
+                sel, _, nt, ne = fe.fe_pa_get_shape(pa, op, variant)
+                assert sel == k and nt >= 32 and ne >= 1
+                geoms.add((op, nt, ne))
+                err = rel_err(_apply(fe, pa, op, variant, xh), oop.apply(prob, xh, kind))
+                assert err <= TOL, (variant, p, k, kind, err)
+        assert len(geoms) > 2                                  # the shapes really differ
+        with pytest.raises(fe.FEError):
+            fe.fe_pa_set_shape(pa, 1, variant, nshapes)

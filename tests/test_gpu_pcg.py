@@ -323,3 +323,32 @@ def test_chebyshev_degree_one_is_scaled_jacobi():
         assert abs(sj["iters"] - sc["iters"]) <= 1
         d = (xc - xj).abs().max().item() / xj.abs().max().item()
         assert d <= 1e-9
+
+
+def test_refinement_on_the_mixed_precision_configuration():
+    """96^3 hexes, p = 4 (57 M dofs), sine load: the refinement (FP32 inner PCG, FP64 outer
+    residual) reaches the FP64 residual 1e-8; its residual on sampled rows, computed by the
+    oracle's own apply, is within the global bound |r_i| <= ||r||_2 <= 1e-8 ||b||_2; and it agrees
+    with the float-float Jacobi-PCG answer."""
+    torch = torch_cuda()
+    n, p = 96, 4
+    with gpu_problem(n, n, n, p, ops=1) as (fe, mesh, pa, V, c):
+        nd, _, _ = fe.fe_mesh_sizes(mesh)
+        b = torch.empty(nd, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        st, stats = fe.fe_pcg_ir(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, 1e-8, 20000)
+        assert st == fe.FE_OK and stats["true_rel_resid"] <= 1e-8, fe.fe_last_error()
+        mask = boundary_mask(n, n, n, p)
+        rng = np.random.default_rng(9)
+        rows = rng.choice(np.nonzero(mask == 0)[0], 40, replace=False)
+        prob = oop.Problem(n, n, n, p, V)
+        xh, bh = x.cpu().numpy(), b.cpu().numpy()
+        r_rows = bh[rows] - oop.apply_rows(prob, xh, DIFFUSION, rows)
+        bn = float(np.linalg.norm(bh * (1 - mask)))
+        assert np.abs(r_rows).max() <= 1e-8 * bn
+        fe.fe_pa_set_variant(pa, "f32x2")
+        xf = torch.empty_like(b)
+        st, sf = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, xf, 1e-8, 20000)
+        assert st == fe.FE_OK
+        assert float((x - xf).abs().max()) <= 1e-6 * float(xf.abs().max())

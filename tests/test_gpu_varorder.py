@@ -50,6 +50,11 @@ def test_sizes_layout_and_mask(name):
     fe = lib()
     dims, orders, V, c = _setup(name)
     S, E = _oracle(name)
+    # the library drops weights of magnitude <= 1e-13 (its documented rule); the oracle keeps
+    # every computed weight: compare structure with that rule applied to the oracle's values
+    E = E.tocsr(copy=True)
+    E.data[np.abs(E.data) <= 1e-13] = 0.0
+    E.eliminate_zeros()
     vs = fe.fe_vspace_setup(*dims, orders, V, c)
     try:
         ntrue, nlocal, nnz = fe.fe_vspace_sizes(vs)
