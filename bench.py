@@ -196,6 +196,72 @@ def run_refinement(args, local_rank):
     return 0
 
 
+def run_c5(args, local_rank):
+    """--c5: the batched configuration on the variable-order space: --n^3 hexes (64) in 8^3-element
+    blocks of orders 2, 4, 6 (seed 7), log-normal coefficient sigma = --sigma (2), 16 right-hand
+    sides U[-1, 1] (seeds 100..115), float-float arithmetic.  One single-system Jacobi-PCG solve
+    to --rtol gives the iteration count and time; the 16 systems in lockstep
+    (fe_vspace_pcg_batched: one persistent launch over all orders and right-hand sides per
+    iteration, iteration batches replayed as CUDA graphs) run a bounded number of iterations
+    (--c5-iters), timed with CUDA events; the time to the tolerance for all 16 is extrapolated
+    from that per-iteration time and the single solve's iteration count.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2603_09038_gb300 import fe
+    from paper_2603_09038_gb300.inputs import (block_orders, perturbed_vertices,
+                                               lognormal_coefficient, uniform_vector)
+    torch.cuda.set_device(local_rank)
+    fe.load()
+    n, nr = args.n, 16
+    sigma = args.sigma if args.sigma else 2.0
+    orders = block_orders(n, n, n, block=8, orders=(2, 4, 6), seed=7)
+    c = lognormal_coefficient(n ** 3, sigma)
+    vs = fe.fe_vspace_setup(n, n, n, orders, perturbed_vertices(n, n, n), c, ops=fe.FE_DIFFUSION)
+    fe.fe_vspace_set_variant(vs, "f32x2")
+    ntrue, _, _ = fe.fe_vspace_sizes(vs)
+    stream = torch.cuda.current_stream()
+    B = torch.from_numpy(np.stack([uniform_vector(ntrue, seed=100 + j) for j in range(nr)])).cuda()
+    X = torch.empty_like(B)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x1 = torch.empty(ntrue, dtype=torch.float64, device="cuda")
+    fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, B[0].contiguous(), x1, args.rtol, 20)    # warm-up
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st1, s1 = fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, B[0].contiguous(), x1, args.rtol, MAXIT, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1) / 1e3
+    kb = min(args.c5_iters, s1["iters"])
+    fe.fe_vspace_pcg_batched(vs, fe.FE_DIFFUSION, nr, B, ntrue, X, ntrue, args.rtol, 16, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stb, sb = fe.fe_vspace_pcg_batched(vs, fe.FE_DIFFUSION, nr, B, ntrue, X, ntrue, args.rtol, kb,
+                                       stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    per_iter_b = tb / kb
+    per_iter_1 = t1 / max(1, s1["iters"])
+    out = {"c5": True, "workload": "diffusion_%dcubed_blocks8_orders246_sigma%g_16rhs" % (n, sigma),
+           "ntrue": ntrue, "nrhs": nr, "variant": "f32x2", "rtol": args.rtol,
+           "single": {"status": st1, "iters": s1["iters"], "time_s": t1,
+                      "true_rel_resid": s1["true_rel_resid"], "ms_per_iter": 1e3 * per_iter_1},
+           "batched": {"iters_run": kb, "time_s": tb, "ms_per_iter_16rhs": 1e3 * per_iter_b,
+                       "ms_per_iter_per_rhs": 1e3 * per_iter_b / nr,
+                       "launches": sb[0]["launches"], "rel_resid_after": [x["rel_resid"] for x in sb],
+                       "apply": "one persistent launch over orders 2, 4, 6 and 16 right-hand "
+                                "sides per iteration; iteration batches replayed as CUDA graphs"},
+           "estimate_16_systems_to_rtol_s": {"batched": per_iter_b * s1["iters"],
+                                             "one_by_one": nr * t1},
+           "speedup_batched_vs_one_by_one": (nr * t1) / (per_iter_b * s1["iters"]),
+           "gdofs_per_rhs_iteration_batched": ntrue * nr / per_iter_b / 1e9,
+           "learned_preconditioner": "not built on variable-order spaces (per order on "
+                                     "single-order meshes only)"}
+    fe.fe_vspace_destroy(vs)
+    print(json.dumps(out))
+    return 0
+
+
 def run_mixed_h1l2(args, local_rank):
     """--mixed-h1l2: only the paper's own operator (mixed H1/L2 pair) on --n^3 hexes."""
     import torch
@@ -1015,6 +1081,9 @@ def run_mixed_orders(args, local_rank):
         if variant == "dmma":
             continue
         fe.fe_vspace_set_variant(vs, variant)
+        fe.fe_vspace_set_persistent(vs, 0)
+        ms_per_order = timed(lambda: fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, y, stream))
+        fe.fe_vspace_set_persistent(vs, 1)
         ms = timed(lambda: fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, x, y, stream))
         ms_gather = timed(lambda: fe.fe_vspace_prolong(vs, x, e, stream))
         print(json.dumps({
@@ -1022,6 +1091,8 @@ def run_mixed_orders(args, local_rank):
             "variant": variant, "ntrue": ntrue, "nlocal": nlocal, "nnz_E": nnz,
             "constrained_rows": nc, "nnz_C": cnnz,
             "elements_per_order": counts, "setup_s": setup_s, "apply_ms": ms,
+            "apply": "one persistent launch over all orders",
+            "apply_ms_one_launch_per_order": ms_per_order,
             "gdofs_true": ntrue / ms / 1e6, "gdofs_local": nlocal / ms / 1e6,
             "gather_ms": ms_gather, "design_bytes": design, "min_bytes": minimum,
             "design_gbs": design / ms / 1e6, "frac_of_hbm_design": design / ms / 1e6 / peaks["hbm_gbs"],
@@ -1102,6 +1173,10 @@ def main():
     ap.add_argument("--refinement", action="store_true",
                     help="FP64 / float-float Jacobi-PCG vs mixed-precision refinement on --n^3, "
                          "order --p (the mixed-precision configuration is --n 96 --p 4)")
+    ap.add_argument("--c5", action="store_true",
+                    help="16 right-hand sides on the 64^3 orders-2/4/6 space, sigma 2 (batched)")
+    ap.add_argument("--c5-iters", type=int, default=200,
+                    help="--c5: lockstep iterations timed for the 16 systems")
     ap.add_argument("--mixed-h1l2", action="store_true",
                     help="only the paper's mixed H1 p=4 / L2 p=3 pair on --n^3 hexes")
     ap.add_argument("--paper-operator-n", type=int, default=128,
@@ -1134,6 +1209,8 @@ def main():
         return run_mixed_h1l2(args, local_rank)
     if args.refinement:
         return run_refinement(args, local_rank)
+    if args.c5:
+        return run_c5(args, local_rank)
     if world > 1:
         import torch
         import torch.distributed as dist

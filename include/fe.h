@@ -469,8 +469,9 @@ void fe_lpc_destroy(fe_lpc* lpc);
  * The E-vector holds the elements grouped by ascending order, elements ascending within a group,
  * D^3 nodes per element (a = i + D*(j + D*k)); fe_vspace_layout gives every element's offset.
  * The action is y = E^T blockdiag(A_e) E x: rows of E that are a single weight 1 live in the
- * element map of the fused apply kernel of each order (one launch per order present, each
- * order's quadrature data at p+2 Gauss points); the other rows C (nodes constrained by a
+ * element map of the fused apply kernel of each order (one persistent launch over all orders,
+ * or one launch per order; each order's quadrature data at p+2 Gauss points); the other rows C
+ * (nodes constrained by a
  * lower-order neighbour) are applied as [x; C x] before and folded back by C^T after.  Vectors
  * are FP64 of length ntrue. */
 typedef struct fe_vspace fe_vspace;
@@ -515,6 +516,12 @@ int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream);
 /* dev_e (FP64 [nlocal]) = E dev_x: the element values of a true-dof vector.  Asynchronous. */
 int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream);
 
+/* How fe_vspace_apply runs the element applies: enable != 0 (the default) -- one persistent
+ * launch over all orders (thread blocks pull blocks of elements, highest order first, from a
+ * device counter), used when every order group has the same FE_VARIANT_F64 or FE_VARIANT_F32X2
+ * arithmetic; enable = 0 -- one fused launch per order.  Same results either way. */
+int fe_vspace_set_persistent(fe_vspace* vs, int enable);
+
 /* dev_y = E^T blockdiag(A_e) E dev_x for op (no boundary conditions); uses the handle's two
  * work vectors, so calls on one handle must not overlap.  Asynchronous. */
 int fe_vspace_apply(const fe_vspace* vs, int op, const double* dev_x, double* dev_y,
@@ -535,6 +542,27 @@ int fe_vspace_diagonal(const fe_vspace* vs, int op, double* dev_diag, void* stre
  * Synchronous. */
 int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
                   int maxit, fe_pcg_stats* stats, void* stream);
+
+/* Batched apply on the variable-order space: dev_y + r ldy = E^T blockdiag(A_e) E (dev_x + r ldx)
+ * for r < nrhs (1..1024, ld >= ntrue), all right-hand sides in one persistent launch over all
+ * orders (when fe_vspace_set_persistent is on and the arithmetic allows; else one launch per
+ * order), each thread block applying every right-hand side to its elements so that the dof map
+ * and quadrature data come from L2 after the first.  Uses work vectors of 2 nrhs (ntrue + rows
+ * of C) values kept with the handle (allocated on first use, grown when nrhs grows): calls on one
+ * handle must not overlap.  Asynchronous. */
+int fe_vspace_apply_batched(const fe_vspace* vs, int op, int nrhs, const double* dev_x,
+                            int64_t ldx, double* dev_y, int64_t ldy, void* stream);
+
+/* Jacobi-PCG for nrhs systems on the variable-order space in lockstep (the conventions of
+ * fe_pcg_batched: each system keeps its own scalars and stops on its own residual; every
+ * iteration applies the operator to all search directions with one fe_vspace_apply_batched;
+ * iteration batches are replayed as CUDA graphs; deterministic FP64 inner products; true
+ * residuals with the FP64 operator; diagonal as fe_vspace_diagonal).  stats: NULL or nrhs
+ * entries.  FE_ERR_UNSUPPORTED for the FP32 variant.  Allocates its work vectors per call.
+ * Synchronous. */
+int fe_vspace_pcg_batched(fe_vspace* vs, int op, int nrhs, const double* dev_b, int64_t ldb,
+                          double* dev_x, int64_t ldx, double rtol, int maxit,
+                          fe_pcg_stats* stats, void* stream);
 
 void fe_vspace_destroy(fe_vspace* vs);
 

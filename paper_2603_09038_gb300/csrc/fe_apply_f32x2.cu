@@ -17,6 +17,19 @@ int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s) {
   return dispatch_order<ArF32x2>(op, a, s);
 }
 
+int multi_elems_f32x2(int op, int order) {
+  using SH = ApplyShape<ArF32x2, 0>;
+  return op == FE_DIFFUSION ? multi_elems<ArF32x2, true, SH::SMEM>(order)
+                            : multi_elems<ArF32x2, false, SH::SMEM>(order);
+}
+
+int launch_apply_multi_f32x2(int op, const MultiGroups& g, const Basis1D* const* basis,
+                           const double* x, double* y, int* counter, int nrhs, int64_t ldx,
+                           int64_t ldy, cudaStream_t s) {
+  return op == FE_DIFFUSION ? launch_multi<ArF32x2, true>(g, basis, x, y, counter, nrhs, ldx, ldy, s)
+                            : launch_multi<ArF32x2, false>(g, basis, x, y, counter, nrhs, ldx, ldy, s);
+}
+
 // Float-pair copy of the FP64 quadrature data, one warp per element: the element's largest
 // biased exponent e_max gives its scale s = e_max - 1023 (0 for an all-zero element), and each
 // entry v becomes the pair hi = rn(v 2^-s), lo = rn(v 2^-s - hi) (v 2^-s exact in FP64), so

@@ -68,17 +68,19 @@ struct ApplyLayout {
 // DIFF: diffusion (qdata [e][qz][6][qy][qx]: xx, xy, xz, yy, yz, zz) or mass ([e][qz][qy][qx]).
 // VT: element type of the x and y vectors (double; float for the FP32 inner solves).
 // MULTI: several right-hand sides per launch (nrhs); when false the launch handles exactly one.
-template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB, class VT,
-          bool MULTI>
-__global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
-                                                 const typename Ar::QdT* __restrict__ qd,
-                                                 const int32_t* __restrict__ qscale,
-                                                 int qshift, const VT* __restrict__ x0,
-                                                 VT* __restrict__ y0, int64_t ne,
-                                                 const int* __restrict__ skip,
-                                                 double* __restrict__ dot_part, int nrhs,
-                                                 int64_t ldx, int64_t ldy,
-                                                 const typename Ar::template Tab<D, Q> tab) {
+//
+// One thread block's share of the fused apply: elements [blk NE, blk NE + NE) of the element list
+// (fewer at its end), for the right-hand sides.  Returns the thread's partial of x^T A x when
+// want_dot (single right-hand side).  smem_raw holds the NE elements' buffers, wexp NT / 32 ints
+// of shared memory.  Used by the per-order kernel (blk = blockIdx.x) and by the persistent
+// multi-order kernel (blk = the work item's block within its order group).
+template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, class VT, bool MULTI>
+__device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
+    const int32_t* __restrict__ map, const typename Ar::QdT* __restrict__ qd,
+    const int32_t* __restrict__ qscale, int qshift, const VT* __restrict__ x0,
+    VT* __restrict__ y0, int64_t ne, int64_t blk, bool want_dot, int nrhs, int64_t ldx,
+    int64_t ldy, const typename Ar::template Tab<D, Q>& tab, unsigned char* smem_raw,
+    int* wexp) {
   using T = typename Ar::T;
   using L = ApplyLayout<D, Q, DIFF, (int)sizeof(T), REREAD>;
   constexpr int D2 = L::D2, D3 = L::D3, Q2 = L::Q2, QD = L::QD;
@@ -86,20 +88,13 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
   constexpr int SZ_A = L::SZ_A, SZ_B = L::SZ_B;
   constexpr int NQD = DIFF ? 6 : 1;
 
-  // optional device flag: a nonzero value turns the launch into a no-op (used by the CG loop
-  // once it has converged, so that already-queued iterations cost nothing)
-  if (skip != nullptr && *skip != 0) return;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + NE * SZ_A;
 
-  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  const int64_t e0 = blk * NE;
   const int nel = (int)((ne - e0) < NE ? (ne - e0) : NE);
   const int tid = threadIdx.x;
   auto dacc = Ar::dot_zero();
-  // scaled policies: per-warp largest biased FP64 exponent of the gathered inputs
-  __shared__ int wexp[NT / 32];
 
   // Several right-hand sides (x0 + r ldx -> y0 + r ldy) are applied one after the other by the
   // same block: after the first, the block's dof map and quadrature data come from L2.
@@ -458,17 +453,41 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict
     const T v = bufB[el * SZ_B + a];
     if constexpr (std::is_same<VT, float>::value) {
       Ar::scatter(&y[g], v);
-      if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), v);
+      if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), v);
     } else {
       // scaled policies: undo the input scale and the element's quadrature-data scale; FP32
       // data: undo its global shift
       const int off = Ar::kScaled ? (xexp - 1023) + __ldg(&qscale[e0 + el]) : qshift;
       const double vd = Ar::widen(v, off);
       atomicAdd(&y[g], vd);
-      if (dot_part != nullptr) Ar::dot_acc(dacc, __ldg(&x[g]), vd);
+      if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), vd);
     }
   }
   }  // right-hand sides
+  return dacc;
+}
+
+// The per-order fused apply: block b applies elements [b NE, b NE + NE).
+template <int D, int Q, int NE, int NT, bool DIFF, class Ar, bool REREAD, int MINB, class VT,
+          bool MULTI>
+__global__ void __launch_bounds__(NT, MINB) k_pa_apply(const int32_t* __restrict__ map,
+                                                 const typename Ar::QdT* __restrict__ qd,
+                                                 const int32_t* __restrict__ qscale,
+                                                 int qshift, const VT* __restrict__ x0,
+                                                 VT* __restrict__ y0, int64_t ne,
+                                                 const int* __restrict__ skip,
+                                                 double* __restrict__ dot_part, int nrhs,
+                                                 int64_t ldx, int64_t ldy,
+                                                 const typename Ar::template Tab<D, Q> tab) {
+  // optional device flag: a nonzero value turns the launch into a no-op (used by the CG loop
+  // once it has converged, so that already-queued iterations cost nothing)
+  if (skip != nullptr && *skip != 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int wexp[NT / 32];  // scaled policies: per-warp largest input exponent
+  const int tid = threadIdx.x;
+  auto dacc = pa_apply_block<D, Q, NE, NT, DIFF, Ar, REREAD, VT, MULTI>(
+      map, qd, qscale, qshift, x0, y0, ne, blockIdx.x, dot_part != nullptr, nrhs, ldx, ldy, tab,
+      smem_raw, wexp);
   if (dot_part != nullptr) {  // (single right-hand side only)  // deterministic block reduction (fixed shuffle tree, warp order)
     double dsum = Ar::dot_value(dacc);
     __shared__ double wsum[NT / 32];

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <mutex>
 
@@ -252,6 +253,157 @@ int dispatch_order(int op, const ApplyArgs& a, cudaStream_t s) {
       return set_error(FE_ERR_UNSUPPORTED, "order out of range 1..8");
   }
 #undef FE_CASE
+}
+
+}  // namespace fe
+
+namespace fe {
+
+// ---- Persistent multi-order apply (a variable-order space): one launch applies every order
+// group.  Work items are blocks of elements of one order (the per-order kernel's element blocks);
+// the items of the highest order come first and each thread block pulls the next item from a
+// device counter until none is left, so the order groups share one grid and its tail.
+
+// 1D tables of every order (entries of absent orders are unused).
+template <class Base>
+struct MultiTabs {
+  typename ArForOrder<Base, 1>::type::template Tab<2, 3> t1;
+  typename ArForOrder<Base, 2>::type::template Tab<3, 4> t2;
+  typename ArForOrder<Base, 3>::type::template Tab<4, 5> t3;
+  typename ArForOrder<Base, 4>::type::template Tab<5, 6> t4;
+  typename ArForOrder<Base, 5>::type::template Tab<6, 7> t5;
+  typename ArForOrder<Base, 6>::type::template Tab<7, 8> t6;
+  typename ArForOrder<Base, 7>::type::template Tab<8, 9> t7;
+  typename ArForOrder<Base, 8>::type::template Tab<9, 10> t8;
+};
+
+template <class Base, bool DIFF, int SMEM, int P>
+struct MultiOrder {
+  using Ar = typename ArForOrder<Base, P>::type;
+  static constexpr bool RR = (P + 1 >= ApplyTuning<Ar>::REREAD_D);
+  static constexpr int NE = elems_per_block<P + 1, P + 2, DIFF, typename Ar::T, SMEM, RR>();
+  static constexpr size_t BYTES = (size_t)NE *
+      ApplyLayout<P + 1, P + 2, DIFF, (int)sizeof(typename Ar::T), RR>::PER_ELEM *
+      sizeof(typename Ar::T);
+};
+
+template <class Base, bool DIFF, int SMEM>
+constexpr size_t multi_smem() {
+  size_t m = 0;
+  const size_t b[8] = {MultiOrder<Base, DIFF, SMEM, 1>::BYTES, MultiOrder<Base, DIFF, SMEM, 2>::BYTES,
+                       MultiOrder<Base, DIFF, SMEM, 3>::BYTES, MultiOrder<Base, DIFF, SMEM, 4>::BYTES,
+                       MultiOrder<Base, DIFF, SMEM, 5>::BYTES, MultiOrder<Base, DIFF, SMEM, 6>::BYTES,
+                       MultiOrder<Base, DIFF, SMEM, 7>::BYTES, MultiOrder<Base, DIFF, SMEM, 8>::BYTES};
+  for (int i = 0; i < 8; ++i) m = b[i] > m ? b[i] : m;
+  return m;
+}
+
+template <class Base, bool DIFF, int SMEM>
+int multi_elems(int p) {
+  switch (p) {
+    case 1: return MultiOrder<Base, DIFF, SMEM, 1>::NE;
+    case 2: return MultiOrder<Base, DIFF, SMEM, 2>::NE;
+    case 3: return MultiOrder<Base, DIFF, SMEM, 3>::NE;
+    case 4: return MultiOrder<Base, DIFF, SMEM, 4>::NE;
+    case 5: return MultiOrder<Base, DIFF, SMEM, 5>::NE;
+    case 6: return MultiOrder<Base, DIFF, SMEM, 6>::NE;
+    case 7: return MultiOrder<Base, DIFF, SMEM, 7>::NE;
+    case 8: return MultiOrder<Base, DIFF, SMEM, 8>::NE;
+    default: return 0;
+  }
+}
+
+template <class Base, bool DIFF, int NT, int SMEM, int P>
+__device__ __forceinline__ void multi_body(const MultiGroups& g, int gi, int64_t blk,
+                                           const double* __restrict__ x, double* __restrict__ y,
+                                           int nrhs, int64_t ldx, int64_t ldy,
+                                           const typename MultiOrder<Base, DIFF, SMEM, P>::Ar::template Tab<P + 1, P + 2>& tab,
+                                           unsigned char* smem, int* wexp) {
+  using MO = MultiOrder<Base, DIFF, SMEM, P>;
+  using Ar = typename MO::Ar;
+  pa_apply_block<P + 1, P + 2, MO::NE, NT, DIFF, Ar, MO::RR, double, true>(
+      g.map[gi], reinterpret_cast<const typename Ar::QdT*>(g.qd[gi]), g.qscale[gi], 0, x, y,
+      g.ne[gi], blk, false, nrhs, ldx, ldy, tab, smem, wexp);
+}
+
+template <class Base, bool DIFF, int NT, int MINB, int SMEM>
+__global__ void __launch_bounds__(NT, MINB) k_pa_apply_multi(const MultiGroups g,
+                                                            const double* __restrict__ x,
+                                                            double* __restrict__ y,
+                                                            int* __restrict__ counter, int nrhs,
+                                                            int64_t ldx, int64_t ldy,
+                                                            const MultiTabs<Base> tabs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int wexp[NT / 32];
+  __shared__ int s_item;
+  const int total = (int)g.first_item[g.n];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();  // every thread has read the item before thread 0 fetches the next one
+    if (item >= total) break;
+    int gi = 0;
+    while (gi + 1 < g.n && item >= g.first_item[gi + 1]) ++gi;
+    const int64_t blk = item - g.first_item[gi];
+    switch (g.order[gi]) {
+      case 1: multi_body<Base, DIFF, NT, SMEM, 1>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t1, smem_raw, wexp); break;
+      case 2: multi_body<Base, DIFF, NT, SMEM, 2>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t2, smem_raw, wexp); break;
+      case 3: multi_body<Base, DIFF, NT, SMEM, 3>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t3, smem_raw, wexp); break;
+      case 4: multi_body<Base, DIFF, NT, SMEM, 4>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t4, smem_raw, wexp); break;
+      case 5: multi_body<Base, DIFF, NT, SMEM, 5>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t5, smem_raw, wexp); break;
+      case 6: multi_body<Base, DIFF, NT, SMEM, 6>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t6, smem_raw, wexp); break;
+      case 7: multi_body<Base, DIFF, NT, SMEM, 7>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t7, smem_raw, wexp); break;
+      default: multi_body<Base, DIFF, NT, SMEM, 8>(g, gi, blk, x, y, nrhs, ldx, ldy, tabs.t8, smem_raw, wexp); break;
+    }
+  }
+}
+
+template <class Base>
+void fill_multi_tabs(const Basis1D* const* basis, MultiTabs<Base>* t) {
+  std::memset(t, 0, sizeof(*t));
+  if (basis[0]) fill_tab<2, 3>(*basis[0], &t->t1);
+  if (basis[1]) fill_tab<3, 4>(*basis[1], &t->t2);
+  if (basis[2]) fill_tab<4, 5>(*basis[2], &t->t3);
+  if (basis[3]) fill_tab<5, 6>(*basis[3], &t->t4);
+  if (basis[4]) fill_tab<6, 7>(*basis[4], &t->t5);
+  if (basis[5]) fill_tab<7, 8>(*basis[5], &t->t6);
+  if (basis[6]) fill_tab<8, 9>(*basis[6], &t->t7);
+  if (basis[7]) fill_tab<9, 10>(*basis[7], &t->t8);
+}
+
+// One persistent launch over the groups of g for nrhs right-hand sides x + r ldx -> y + r ldy (y
+// zeroed by the caller; counter: one device int, zeroed here).  basis[p - 1]: the 1D tables of
+// order p (NULL where absent).
+template <class Base, bool DIFF>
+int launch_multi(const MultiGroups& g, const Basis1D* const* basis, const double* x, double* y,
+                 int* counter, int nrhs, int64_t ldx, int64_t ldy, cudaStream_t s) {
+  using SH = ApplyShape<typename ArForOrder<Base, 1>::type, 0>;
+  constexpr size_t smem = multi_smem<Base, DIFF, SH::SMEM>();
+  auto kern = k_pa_apply_multi<Base, DIFF, SH::NT, SH::MINB, SH::SMEM>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  static int grid_cap = 0;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0, dev = 0, sms = 0;
+    if (attr_err == cudaSuccess)
+      attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SH::NT, smem);
+    if (attr_err == cudaSuccess) attr_err = cudaGetDevice(&dev);
+    if (attr_err == cudaSuccess)
+      attr_err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid_cap = (occ > 0 ? occ : 1) * (sms > 0 ? sms : 1);
+  });
+  if (attr_err != cudaSuccess) return cuda_error(attr_err, "multi-order apply: setup");
+  const int64_t total = g.first_item[g.n];
+  if (total == 0) return FE_OK;
+  MultiTabs<Base> tabs;
+  fill_multi_tabs<Base>(basis, &tabs);
+  cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (err != cudaSuccess) return cuda_error(err, "multi-order apply: counter");
+  const int grid = (int)(total < grid_cap ? total : grid_cap);
+  kern<<<grid, SH::NT, smem, s>>>(g, x, y, counter, nrhs, ldx, ldy, tabs);
+  return cuda_error(cudaGetLastError(), "multi-order apply launch");
 }
 
 }  // namespace fe

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 
 #include "../../include/fe.h"
@@ -114,6 +115,44 @@ struct ApplyArgs {
   int* threads_per_block = nullptr;
 };
 
+// Order groups of a variable-order space for the persistent multi-order apply: group i has
+// elements of order order[i] (an element list with its own dof-map slice, quadrature data and,
+// for float pairs, scales); its work items are first_item[i] .. first_item[i + 1] - 1, each a
+// block of multi_elems(variant, op, order) consecutive elements of the list.
+struct MultiGroups {
+  int n = 0;
+  int order[kMaxOrder];
+  int64_t first_item[kMaxOrder + 1];
+  const int32_t* map[kMaxOrder];
+  const double* qd[kMaxOrder];
+  const int32_t* qscale[kMaxOrder];
+  int64_t ne[kMaxOrder];
+};
+// Elements per work item of the multi-order apply (FE_VARIANT_F64 or FE_VARIANT_F32X2), 0 if not
+// built; one persistent launch over the groups (y zeroed by the caller; counter: a device int).
+int multi_elems(int variant, int op, int order);
+int launch_apply_multi(int variant, int op, const MultiGroups& g, const Basis1D* const* basis,
+                       const double* x, double* y, int* counter, int nrhs, int64_t ldx,
+                       int64_t ldy, cudaStream_t s);
+
+// A linear operator for the batched CG (fe_pcg_batched, fe_vspace_pcg_batched): n unknowns,
+// the boundary mask (essential dofs), Q_j = A P_j for nr search directions stored with leading
+// dimension n (skip: a device flag the kernels may test to do nothing once every system has
+// stopped; Q is zeroed beforehand), the same with the FP64 operator for the true residuals
+// (X with leading dimension lx), and the Jacobi diagonal (empty: no preconditioner).  nk counts
+// the kernels launched.  graphs: replay iteration batches as CUDA graphs.
+struct BatchedOperator {
+  int64_t n = 0;
+  const uint8_t* mask = nullptr;
+  std::function<int(cudaStream_t, int, const double*, double*, const int*, int*)> apply;
+  std::function<int(cudaStream_t, int, const double*, int64_t, double*, int*)> apply_fp64;
+  std::function<int(cudaStream_t, double*)> diagonal;
+  bool graphs = true;
+};
+int pcg_batched_core(const BatchedOperator& A, int nrhs, const double* dev_b, int64_t ldb,
+                     double* dev_x, int64_t ldx, double rtol, int maxit, fe_pcg_stats* stats,
+                     cudaStream_t s, const char* who);
+
 // Launchers (one translation unit per variant); return FE_OK or an error status.
 int launch_apply_f64(int op, const ApplyArgs& a, cudaStream_t s);
 int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s);
@@ -123,6 +162,14 @@ int launch_apply_f32_vec32(int op, const ApplyArgs& a, cudaStream_t s);
 // FP32 copy of n FP64 quadrature values times 2^-*shift, *shift chosen so that the largest
 // lies in [1, 2) (the copy then spans the float range whatever the coefficient's magnitude).
 int make_qd_f32(const double* src, float* dst, int64_t n, int* shift, cudaStream_t s);
+int multi_elems_f64(int op, int order);
+int multi_elems_f32x2(int op, int order);
+int launch_apply_multi_f64(int op, const MultiGroups& g, const Basis1D* const* basis,
+                           const double* x, double* y, int* counter, int nrhs, int64_t ldx,
+                           int64_t ldy, cudaStream_t s);
+int launch_apply_multi_f32x2(int op, const MultiGroups& g, const Basis1D* const* basis,
+                             const double* x, double* y, int* counter, int nrhs, int64_t ldx,
+                             int64_t ldy, cudaStream_t s);
 
 // diag += the element diagonals of op scattered through the element map (no zeroing; atomic).
 int diagonal_accumulate(const fe_pa* pa, int op, double* diag, cudaStream_t s);

@@ -256,27 +256,21 @@ struct Buffers {
 
 }  // namespace
 
-extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double* dev_b,
-                              int64_t ldb, double* dev_x, int64_t ldx, double rtol, int maxit,
-                              fe_pcg_stats* stats, void* stream) {
-  clear_error();
+namespace fe {
+
+// The lockstep batched Jacobi- (or un-) preconditioned CG of fe_pcg_batched around any operator
+// (see BatchedOperator in fe_internal.h).
+int pcg_batched_core(const BatchedOperator& A, int nrhs, const double* dev_b, int64_t ldb,
+                     double* dev_x, int64_t ldx, double rtol, int maxit, fe_pcg_stats* stats,
+                     cudaStream_t s, const char* who) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_pcg_batched: null argument");
-  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pcg_batched: bad op");
-  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pcg_batched: operator not set up");
-  if (pc != FE_PC_NONE && pc != FE_PC_JACOBI)
-    return set_error(FE_ERR_ARG, "fe_pcg_batched: preconditioner must be none or Jacobi");
-  const fe_mesh* m = pa->mesh;
-  const int64_t n = m->ndofs;
+  const std::string w(who);
+  const int64_t n = A.n;
   if (nrhs < 1 || nrhs > 1024 || ldb < n || ldx < n)
-    return set_error(FE_ERR_ARG, "fe_pcg_batched: need 1 <= nrhs <= 1024 and ldb, ldx >= ndofs");
-  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_pcg_batched: bad rtol or maxit");
-  if (pa->variant == FE_VARIANT_F32)
-    return set_error(FE_ERR_UNSUPPORTED, "fe_pcg_batched: the FP32 variant is not FP64-accurate");
+    return set_error(FE_ERR_ARG, w + ": need 1 <= nrhs <= 1024 and ldb, ldx >= ndofs");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, w + ": bad rtol or maxit");
   if (stats)
     for (int j = 0; j < nrhs; ++j) stats[j] = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
-  cudaStream_t s = (cudaStream_t)stream;
-  const int variant = pa->variant;
   Buffers buf;
   cudaError_t err;
   const size_t nv = (size_t)nrhs * n;
@@ -284,7 +278,7 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
       (err = cudaMalloc(&buf.red, sizeof(double) * ((size_t)2 * nrhs * kReduceBlocks +
                                                     (size_t)nrhs * kScalars))) != cudaSuccess ||
       (err = cudaMalloc(&buf.flags, sizeof(int) * (4 * nrhs + 3))) != cudaSuccess)
-    return cuda_error(err, "fe_pcg_batched: cudaMalloc");
+    return cuda_error(err, (w + ": cudaMalloc").c_str());
   double *R = buf.vec, *Z = R + nv, *P = Z + nv, *Q = P + nv, *dinv = Q + nv;
   double *part0 = buf.red, *part1 = part0 + (size_t)nrhs * kReduceBlocks,
          *sc = part1 + (size_t)nrhs * kReduceBlocks;
@@ -293,44 +287,33 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
   int* bad = ctl + 2;
   int launches = 0;
   if ((err = cudaMemsetAsync(flags, 0, sizeof(int) * (4 * nrhs + 3), s)) != cudaSuccess)
-    return cuda_error(err, "fe_pcg_batched: flags");
+    return cuda_error(err, (w + ": flags").c_str());
   int st = FE_OK;
-  if (pc == FE_PC_JACOBI) {
-    if ((st = fe_assemble_diagonal(pa, op, dinv, s)) != FE_OK) return st;
-    k_invert_diag_b<<<kReduceBlocks, kReduceThreads, 0, s>>>(dinv, m->d_mask, n, bad);
+  if (A.diagonal) {
+    if ((st = A.diagonal(s, dinv)) != FE_OK) return st;
+    k_invert_diag_b<<<kReduceBlocks, kReduceThreads, 0, s>>>(dinv, A.mask, n, bad);
     launches += 2;
   }
-  const double* dj = pc == FE_PC_JACOBI ? dinv : nullptr;
+  const double* dj = A.diagonal ? dinv : nullptr;
   const dim3 grid2(kReduceBlocks, nrhs);
-  k_binit<<<grid2, kReduceThreads, 0, s>>>(dev_b, ldb, m->d_mask, dj, dev_x, ldx, R, Z, P, Q, n,
+  k_binit<<<grid2, kReduceThreads, 0, s>>>(dev_b, ldb, A.mask, dj, dev_x, ldx, R, Z, P, Q, n,
                                            part0, part1);
   k_bfinish_init<<<nrhs, kFinishThreads, 0, s>>>(part0, part1, sc, flags, ctl);
   k_bcheck<<<1, 32, 0, s>>>(ctl);
   launches += 3;
-  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "fe_pcg_batched: init");
-  const bool batched_apply = variant != FE_VARIANT_F64_DMMA;  // no batched DMMA kernel
+  if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, (w + ": init").c_str());
   auto enqueue = [&](cudaStream_t q, int count, int* nk) -> int {
     for (int it = 0; it < count; ++it) {
-      if (batched_apply) {
-        int st2 = apply_dispatch(pa, op, variant, P, Q, q, ctl + C_DONE, nullptr, nullptr, false,
-                                 nrhs, n, n);
-        if (st2 != FE_OK) return st2;
-        ++*nk;
-      } else {
-        for (int j = 0; j < nrhs; ++j) {
-          int st2 = apply_dispatch(pa, op, variant, P + j * n, Q + j * n, q, ctl + C_DONE);
-          if (st2 != FE_OK) return st2;
-          ++*nk;
-        }
-      }
+      int st2 = A.apply(q, nrhs, P, Q, ctl + C_DONE, nk);
+      if (st2 != FE_OK) return st2;
       k_bdot<<<grid2, kReduceThreads, 0, q>>>(P, Q, n, part0, flags);
       k_bfinish_pq<<<nrhs, kFinishThreads, 0, q>>>(part0, sc, flags, ctl);
-      k_bupdate<<<grid2, kReduceThreads, 0, q>>>(dev_x, ldx, R, Z, P, Q, dj, m->d_mask, n, sc,
+      k_bupdate<<<grid2, kReduceThreads, 0, q>>>(dev_x, ldx, R, Z, P, Q, dj, A.mask, n, sc,
                                                  part0, part1, flags);
       k_bfinish_update<<<nrhs, kFinishThreads, 0, q>>>(part0, part1, sc, flags, ctl, rtol, maxit);
       k_bpupdate<<<grid2, kReduceThreads, 0, q>>>(P, Z, Q, n, sc, flags, ctl);
       cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_error(e, "fe_pcg_batched: iteration launch");
+      if (e != cudaSuccess) return cuda_error(e, (w + ": iteration launch").c_str());
       *nk += 5;
     }
     return FE_OK;
@@ -342,30 +325,27 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
     if ((err = cudaMemcpyAsync(hctl, ctl, sizeof(int) * 3, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess ||
         (err = cudaStreamSynchronize(s)) != cudaSuccess)
-      return cuda_error(err, "fe_pcg_batched: iteration");
-    if (hctl[2]) return set_error(FE_ERR_BREAKDOWN, "fe_pcg_batched: non-positive diagonal entry");
+      return cuda_error(err, (w + ": iteration").c_str());
+    if (hctl[2]) return set_error(FE_ERR_BREAKDOWN, w + ": non-positive diagonal entry");
     if (hctl[C_DONE] || queued >= maxit) break;
     const int count = maxit - queued < kBatch ? maxit - queued : kBatch;
-    if (queued > 0 && count == kBatch && pa->pcg_graphs && !graph.failed && !graph.exec) {
+    if (queued > 0 && count == kBatch && A.graphs && !graph.failed && !graph.exec) {
       int nk = 0;
       graph.capture([&](cudaStream_t q) { return enqueue(q, kBatch, &nk); });
       graph.kernels = nk;
     }
     if (graph.exec && count == kBatch) {
       if ((err = cudaGraphLaunch(graph.exec, s)) != cudaSuccess)
-        return cuda_error(err, "fe_pcg_batched: graph launch");
+        return cuda_error(err, (w + ": graph launch").c_str());
       launches += graph.kernels;
     } else if ((st = enqueue(s, count, &launches)) != FE_OK) {
       return st;
     }
     queued += count;
   }
-  // true residuals with the FP64 operator: Q = A X (one batched launch), per-system norms
-  if ((st = apply_dispatch(pa, op, FE_VARIANT_F64, dev_x, Q, s, nullptr, nullptr, nullptr, false,
-                           nrhs, ldx, n)) != FE_OK)
-    return st;
-  ++launches;
-  k_bresid<<<grid2, kReduceThreads, 0, s>>>(dev_b, ldb, Q, m->d_mask, n, part0, part1);
+  // true residuals with the FP64 operator: Q = A X, per-system norms
+  if ((st = A.apply_fp64(s, nrhs, dev_x, ldx, Q, &launches)) != FE_OK) return st;
+  k_bresid<<<grid2, kReduceThreads, 0, s>>>(dev_b, ldb, Q, A.mask, n, part0, part1);
   k_bfinish_resid<<<nrhs, kFinishThreads, 0, s>>>(part0, part1, sc);
   launches += 2;
   std::vector<double> hsc((size_t)nrhs * kScalars);
@@ -376,7 +356,7 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
       (err = cudaMemcpyAsync(hf.data(), flags, sizeof(int) * hf.size(), cudaMemcpyDeviceToHost,
                              s)) != cudaSuccess ||
       (err = cudaStreamSynchronize(s)) != cudaSuccess)
-    return cuda_error(err, "fe_pcg_batched: stats");
+    return cuda_error(err, (w + ": stats").c_str());
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int worst = FE_OK;
   for (int j = 0; j < nrhs; ++j) {
@@ -395,7 +375,51 @@ extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double*
     else if (state != ST_CONV) code = FE_ERR_NOT_CONVERGED;
     if (worst == FE_OK && code != FE_OK) worst = code;
   }
-  if (worst != FE_OK)
-    return set_error(worst, "fe_pcg_batched: some right-hand side did not converge (see stats)");
+  if (worst != FE_OK) return set_error(worst, w + ": some right-hand side did not converge (see stats)");
   return FE_OK;
+}
+
+}  // namespace fe
+
+extern "C" int fe_pcg_batched(fe_pa* pa, int op, int pc, int nrhs, const double* dev_b,
+                              int64_t ldb, double* dev_x, int64_t ldx, double rtol, int maxit,
+                              fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  if (!pa || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_pcg_batched: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_pcg_batched: bad op");
+  if (!(pa->ops & op)) return set_error(FE_ERR_ARG, "fe_pcg_batched: operator not set up");
+  if (pc != FE_PC_NONE && pc != FE_PC_JACOBI)
+    return set_error(FE_ERR_ARG, "fe_pcg_batched: preconditioner must be none or Jacobi");
+  if (pa->variant == FE_VARIANT_F32)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_pcg_batched: the FP32 variant is not FP64-accurate");
+  const int variant = pa->variant;
+  const int64_t n = pa->mesh->ndofs;
+  BatchedOperator A;
+  A.n = n;
+  A.mask = pa->mesh->d_mask;
+  A.graphs = pa->pcg_graphs;
+  // one batched launch for all search directions (the DMMA kernel applies them one by one)
+  A.apply = [=](cudaStream_t q, int nr, const double* P, double* Q, const int* skip,
+                int* nk) -> int {
+    if (variant != FE_VARIANT_F64_DMMA) {
+      ++*nk;
+      return apply_dispatch(pa, op, variant, P, Q, q, skip, nullptr, nullptr, false, nr, n, n);
+    }
+    for (int j = 0; j < nr; ++j) {
+      const int st2 = apply_dispatch(pa, op, variant, P + j * n, Q + j * n, q, skip);
+      if (st2 != FE_OK) return st2;
+      ++*nk;
+    }
+    return FE_OK;
+  };
+  A.apply_fp64 = [=](cudaStream_t q, int nr, const double* X, int64_t lx, double* Q,
+                     int* nk) -> int {
+    ++*nk;
+    return apply_dispatch(pa, op, FE_VARIANT_F64, X, Q, q, nullptr, nullptr, nullptr, false, nr,
+                          lx, n);
+  };
+  if (pc == FE_PC_JACOBI)
+    A.diagonal = [=](cudaStream_t q, double* d) { return fe_assemble_diagonal(pa, op, d, q); };
+  return pcg_batched_core(A, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stats,
+                          (cudaStream_t)stream, "fe_pcg_batched");
 }

@@ -615,6 +615,11 @@ struct fe_vspace {
   double* d_X = nullptr;                // [ntrue + nc]: x then C x
   double* d_Y = nullptr;                // [ntrue + nc]: the per-order kernels' scatter target
   int* d_zero = nullptr;                // a device 0: "y is zeroed by the caller" for the applies
+  int* d_counter = nullptr;             // work counter of the persistent multi-order apply
+  bool persistent = true;               // one persistent launch over all orders (else one each)
+  double* d_Xb = nullptr;               // batched work vectors: [xb_cap][ntrue + nc] each
+  double* d_Yb = nullptr;
+  int xb_cap = 0;
   double* d_work = nullptr;             // PCG: x-free work vectors r, z, p, q, dinv [5][ntrue]
   double* d_red = nullptr;              //      2 kReduceBlocks partials + kScalars
   int* d_flags = nullptr;
@@ -649,6 +654,9 @@ void vspace_free(fe_vspace* vs) {
   cudaFree(vs->d_X);
   cudaFree(vs->d_Y);
   cudaFree(vs->d_zero);
+  cudaFree(vs->d_counter);
+  cudaFree(vs->d_Xb);
+  cudaFree(vs->d_Yb);
   cudaFree(vs->d_work);
   cudaFree(vs->d_red);
   cudaFree(vs->d_flags);
@@ -662,25 +670,27 @@ cudaError_t upload(T** dst, const std::vector<T>& src) {
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
 
-// X = [x; C x] on s
-int fill_X(const fe_vspace* vs, const double* x, cudaStream_t s) {
-  cudaError_t err = cudaMemcpyAsync(vs->d_X, x, sizeof(double) * vs->ntrue,
+// X = [x; C x] on s (X: a work vector of ntrue + nc values; default the handle's)
+int fill_X(const fe_vspace* vs, const double* x, cudaStream_t s, double* X = nullptr) {
+  if (!X) X = vs->d_X;
+  cudaError_t err = cudaMemcpyAsync(X, x, sizeof(double) * vs->ntrue,
                                     cudaMemcpyDeviceToDevice, s);
   if (err != cudaSuccess) return cuda_error(err, "fe_vspace: copy x");
   if (vs->nc > 0)
     k_csr_gather<<<grid_of(vs->nc), 256, 0, s>>>(vs->d_cptr, vs->d_ccol, vs->d_cval, vs->nc, x,
-                                                 vs->d_X + vs->ntrue);
+                                                 X + vs->ntrue);
   return cuda_error(cudaGetLastError(), "fe_vspace: constrained rows");
 }
 
 // y = Y[0, ntrue) + C^T Y[ntrue, ntrue + nc) (squared weights with `square`) on s
-int fold_Y(const fe_vspace* vs, double* y, int square, cudaStream_t s) {
-  cudaError_t err = cudaMemcpyAsync(y, vs->d_Y, sizeof(double) * vs->ntrue,
+int fold_Y(const fe_vspace* vs, double* y, int square, cudaStream_t s, const double* Y = nullptr) {
+  if (!Y) Y = vs->d_Y;
+  cudaError_t err = cudaMemcpyAsync(y, Y, sizeof(double) * vs->ntrue,
                                     cudaMemcpyDeviceToDevice, s);
   if (err != cudaSuccess) return cuda_error(err, "fe_vspace: copy y");
   if (vs->nct > 0)
     k_ct_scatter<<<grid_of(vs->nct), 256, 0, s>>>(vs->d_trow, vs->d_tptr, vs->d_tcol, vs->d_tval,
-                                                  vs->nct, vs->d_Y + vs->ntrue, y, square);
+                                                  vs->nct, Y + vs->ntrue, y, square);
   return cuda_error(cudaGetLastError(), "fe_vspace: constrained transpose");
 }
 
@@ -746,6 +756,7 @@ static int vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_Y, sizeof(double) * std::max<int64_t>(1, nX));
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_zero, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(vs->d_zero, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaMalloc(&vs->d_counter, sizeof(int));
   if (err != cudaSuccess) {
     vspace_free(vs);
     return cuda_error(err, "fe_vspace_setup: upload");
@@ -934,6 +945,13 @@ int fe_vspace_set_variant(fe_vspace* vs, int variant, void* stream) {
   return FE_OK;
 }
 
+int fe_vspace_set_persistent(fe_vspace* vs, int enable) {
+  clear_error();
+  if (!vs) return set_error(FE_ERR_ARG, "fe_vspace_set_persistent: handle is NULL");
+  vs->persistent = enable != 0;
+  return FE_OK;
+}
+
 int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, void* stream) {
   clear_error();
   if (!vs || !dev_x || !dev_e) return set_error(FE_ERR_ARG, "fe_vspace_prolong: null argument");
@@ -947,23 +965,102 @@ int fe_vspace_prolong(const fe_vspace* vs, const double* dev_x, double* dev_e, v
 }  // extern "C"
 
 namespace {
-// y = E^T blockdiag(A_e) E x with the given variant (-1: each order's selected variant).
+// The order groups of vs for the persistent multi-order apply with `variant`, highest order
+// first (its items are the largest); false if that apply is not built for the variant.
+bool multi_groups(const fe_vspace* vs, int op, int variant, MultiGroups* g,
+                  const Basis1D** basis) {
+  if (variant != FE_VARIANT_F64 && variant != FE_VARIANT_F32X2) return false;
+  for (int p = 0; p < kMaxOrder; ++p) basis[p] = nullptr;
+  g->n = 0;
+  g->first_item[0] = 0;
+  for (int k = vs->ngroups - 1; k >= 0; --k) {
+    const fe_pa* pa = vs->group_pa[k];
+    const int p = vs->group_p[k];
+    const int ne_item = multi_elems(variant, op, p);
+    if (ne_item <= 0) return false;
+    const int i = g->n++;
+    g->order[i] = p;
+    g->map[i] = pa->mesh->d_map;
+    g->ne[i] = pa->mesh->ne;
+    if (variant == FE_VARIANT_F32X2) {
+      g->qd[i] = op == FE_DIFFUSION ? pa->d_qd_diff2 : pa->d_qd_mass2;
+      g->qscale[i] = op == FE_DIFFUSION ? pa->d_qs_diff : pa->d_qs_mass;
+      if (!g->qd[i] || !g->qscale[i]) return false;
+    } else {
+      g->qd[i] = op == FE_DIFFUSION ? pa->d_qd_diff : pa->d_qd_mass;
+      g->qscale[i] = nullptr;
+    }
+    g->first_item[i + 1] = g->first_item[i] + (g->ne[i] + ne_item - 1) / ne_item;
+    basis[p - 1] = &pa->basis;
+  }
+  return true;
+}
+
+// y_r = E^T blockdiag(A_e) E x_r for r < nrhs (x_r = x + r ldx, y_r = y + r ldy) with the given
+// variant (-1: each order's selected variant), through the work vectors X, Y of nrhs (ntrue + nc)
+// values: one persistent launch over all orders and right-hand sides when every group uses the
+// same FP64-accurate arithmetic (and persistent launches are on), else one fused launch per
+// order.  nk (optional) counts the kernels.
+int vspace_apply_b(const fe_vspace* vs, int op, int variant, int nrhs, const double* dev_x,
+                   int64_t ldx, double* dev_y, int64_t ldy, double* X, double* Y,
+                   cudaStream_t s, int* nk = nullptr) {
+  const int64_t nX = vs->ntrue + vs->nc;
+  int st;
+  for (int r = 0; r < nrhs; ++r)
+    if ((st = fill_X(vs, dev_x + r * ldx, s, X + r * nX)) != FE_OK) return st;
+  cudaError_t err = cudaMemsetAsync(Y, 0, sizeof(double) * nX * nrhs, s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: zero Y");
+  if (nk) *nk += nrhs * (vs->nc > 0 ? 1 : 0);
+  int v0 = variant < 0 ? vs->group_pa[0]->variant : variant;
+  bool uniform = true;
+  for (int g = 0; g < vs->ngroups; ++g)
+    if ((variant < 0 ? vs->group_pa[g]->variant : variant) != v0) uniform = false;
+  MultiGroups mg;
+  const Basis1D* basis[kMaxOrder];
+  if (vs->persistent && uniform && multi_groups(vs, op, v0, &mg, basis)) {
+    if ((st = launch_apply_multi(v0, op, mg, basis, X, Y, vs->d_counter, nrhs, nX, nX, s)) !=
+        FE_OK)
+      return st;
+    if (nk) *nk += 1;
+  } else {
+    for (int g = 0; g < vs->ngroups; ++g) {
+      const fe_pa* pa = vs->group_pa[g];
+      if ((st = apply_dispatch(pa, op, variant < 0 ? pa->variant : variant, X, Y, s, vs->d_zero,
+                               nullptr, nullptr, false, nrhs, nX, nX)) != FE_OK)
+        return st;
+      if (nk) *nk += 1;
+    }
+  }
+  for (int r = 0; r < nrhs; ++r)
+    if ((st = fold_Y(vs, dev_y + r * ldy, 0, s, Y + r * nX)) != FE_OK) return st;
+  if (nk) *nk += nrhs * (vs->nct > 0 ? 1 : 0);
+  return FE_OK;
+}
+
+// the single right-hand side through the handle's work vectors
 int vspace_apply(const fe_vspace* vs, int op, int variant, const double* dev_x, double* dev_y,
                  cudaStream_t s) {
-  int st = fill_X(vs, dev_x, s);
-  if (st != FE_OK) return st;
-  cudaError_t err =
-      cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * (vs->ntrue + vs->nc), s);
-  if (err != cudaSuccess) return cuda_error(err, "fe_vspace_apply: zero Y");
-  for (int g = 0; g < vs->ngroups; ++g) {
-    const fe_pa* pa = vs->group_pa[g];
-    if ((st = apply_dispatch(pa, op, variant < 0 ? pa->variant : variant, vs->d_X, vs->d_Y, s,
-                             vs->d_zero)) != FE_OK)
-      return st;
-  }
-  return fold_Y(vs, dev_y, 0, s);
+  return vspace_apply_b(vs, op, variant, 1, dev_x, 0, dev_y, 0, vs->d_X, vs->d_Y, s);
 }
+
 }  // namespace
+
+namespace fe {
+int multi_elems(int variant, int op, int order) {
+  if (variant == FE_VARIANT_F64) return multi_elems_f64(op, order);
+  if (variant == FE_VARIANT_F32X2) return multi_elems_f32x2(op, order);
+  return 0;
+}
+int launch_apply_multi(int variant, int op, const MultiGroups& g, const Basis1D* const* basis,
+                       const double* x, double* y, int* counter, int nrhs, int64_t ldx,
+                       int64_t ldy, cudaStream_t s) {
+  if (variant == FE_VARIANT_F64)
+    return launch_apply_multi_f64(op, g, basis, x, y, counter, nrhs, ldx, ldy, s);
+  if (variant == FE_VARIANT_F32X2)
+    return launch_apply_multi_f32x2(op, g, basis, x, y, counter, nrhs, ldx, ldy, s);
+  return set_error(FE_ERR_UNSUPPORTED, "multi-order apply: variant not built");
+}
+}  // namespace fe
 
 extern "C" {
 
@@ -1099,6 +1196,72 @@ int fe_vspace_pcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, dou
     default:
       return set_error(FE_ERR_NOT_CONVERGED, "fe_vspace_pcg: maxit reached before rtol");
   }
+}
+
+}  // extern "C"
+
+namespace {
+// Batched work vectors for nrhs right-hand sides (kept with the handle, grown on demand).
+int batched_work(const fe_vspace* cvs, int nrhs) {
+  fe_vspace* vs = const_cast<fe_vspace*>(cvs);
+  if (nrhs <= vs->xb_cap) return FE_OK;
+  cudaFree(vs->d_Xb);
+  cudaFree(vs->d_Yb);
+  vs->d_Xb = vs->d_Yb = nullptr;
+  vs->xb_cap = 0;
+  const size_t bytes = sizeof(double) * (size_t)(vs->ntrue + vs->nc) * nrhs;
+  cudaError_t err;
+  if ((err = cudaMalloc(&vs->d_Xb, bytes)) != cudaSuccess ||
+      (err = cudaMalloc(&vs->d_Yb, bytes)) != cudaSuccess)
+    return cuda_error(err, "fe_vspace: batched work vectors");
+  vs->xb_cap = nrhs;
+  return FE_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int fe_vspace_apply_batched(const fe_vspace* vs, int op, int nrhs, const double* dev_x,
+                            int64_t ldx, double* dev_y, int64_t ldy, void* stream) {
+  clear_error();
+  if (!vs || !dev_x || !dev_y) return set_error(FE_ERR_ARG, "fe_vspace_apply_batched: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_apply_batched: bad op");
+  if (!(vs->ops & op)) return set_error(FE_ERR_ARG, "fe_vspace_apply_batched: operator not set up");
+  if (nrhs < 1 || nrhs > 1024 || ldx < vs->ntrue || ldy < vs->ntrue)
+    return set_error(FE_ERR_ARG, "fe_vspace_apply_batched: need 1 <= nrhs <= 1024, ld >= ntrue");
+  int st = batched_work(vs, nrhs);
+  if (st != FE_OK) return st;
+  return vspace_apply_b(vs, op, -1, nrhs, dev_x, ldx, dev_y, ldy, vs->d_Xb, vs->d_Yb,
+                        (cudaStream_t)stream);
+}
+
+int fe_vspace_pcg_batched(fe_vspace* vs, int op, int nrhs, const double* dev_b, int64_t ldb,
+                          double* dev_x, int64_t ldx, double rtol, int maxit,
+                          fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  if (!vs || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_vspace_pcg_batched: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_pcg_batched: bad op");
+  if (!(vs->ops & op)) return set_error(FE_ERR_ARG, "fe_vspace_pcg_batched: operator not set up");
+  for (int g = 0; g < vs->ngroups; ++g)
+    if (vs->group_pa[g]->variant == FE_VARIANT_F32)
+      return set_error(FE_ERR_UNSUPPORTED,
+                       "fe_vspace_pcg_batched: the FP32 variant is not FP64-accurate");
+  if (nrhs < 1 || nrhs > 1024) return set_error(FE_ERR_ARG, "fe_vspace_pcg_batched: bad nrhs");
+  int st = batched_work(vs, nrhs);
+  if (st != FE_OK) return st;
+  const int64_t n = vs->ntrue;
+  BatchedOperator A;
+  A.n = n;
+  A.mask = vs->d_mask;
+  A.apply = [=](cudaStream_t q, int nr, const double* P, double* Q, const int*, int* nk) {
+    return vspace_apply_b(vs, op, -1, nr, P, n, Q, n, vs->d_Xb, vs->d_Yb, q, nk);
+  };
+  A.apply_fp64 = [=](cudaStream_t q, int nr, const double* X, int64_t lx, double* Q, int* nk) {
+    return vspace_apply_b(vs, op, FE_VARIANT_F64, nr, X, lx, Q, n, vs->d_Xb, vs->d_Yb, q, nk);
+  };
+  A.diagonal = [=](cudaStream_t q, double* d) { return fe_vspace_diagonal(vs, op, d, q); };
+  return pcg_batched_core(A, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stats,
+                          (cudaStream_t)stream, "fe_vspace_pcg_batched");
 }
 
 void fe_vspace_destroy(fe_vspace* vs) {

@@ -139,6 +139,13 @@ _SIGS = {
     "fe_vspace_boundary_mask": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_vspace_set_variant": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "fe_vspace_prolong": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_vspace_set_persistent": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_vspace_apply_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP,
+                                               ctypes.c_int64, _VP, ctypes.c_int64, _VP]),
+    "fe_vspace_pcg_batched": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP,
+                                             ctypes.c_int64, _VP, ctypes.c_int64,
+                                             ctypes.c_double, ctypes.c_int,
+                                             ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_vspace_apply": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "fe_vspace_diagonal": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP]),
     "fe_vspace_pcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.c_int,
@@ -611,6 +618,26 @@ def fe_vspace_boundary_mask(vs, dev_mask, stream=None):
 def fe_vspace_set_variant(vs, variant, stream=None):
     v = VARIANTS.get(variant, variant)
     _check(load().fe_vspace_set_variant(_VP(vs), int(v), _stream(stream)))
+
+
+def fe_vspace_set_persistent(vs, enable):
+    _check(load().fe_vspace_set_persistent(_VP(vs), int(bool(enable))))
+
+
+def fe_vspace_apply_batched(vs, op, nrhs, dev_x, ldx, dev_y, ldy, stream=None):
+    _check(load().fe_vspace_apply_batched(_VP(vs), int(op), int(nrhs), _ptr(dev_x), int(ldx),
+                                          _ptr(dev_y), int(ldy), _stream(stream)))
+
+
+def fe_vspace_pcg_batched(vs, op, nrhs, dev_b, ldb, dev_x, ldx, rtol, maxit, stream=None):
+    """Returns (status, [stats dict per system]); non-convergence is a result, not raised."""
+    st = (fe_pcg_stats * int(nrhs))()
+    status = load().fe_vspace_pcg_batched(_VP(vs), int(op), int(nrhs), _ptr(dev_b), int(ldb),
+                                          _ptr(dev_x), int(ldx), float(rtol), int(maxit), st,
+                                          _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, [_stats(x) for x in st]
 
 
 def fe_vspace_prolong(vs, dev_x, dev_e, stream=None):

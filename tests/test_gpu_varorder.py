@@ -239,3 +239,70 @@ def test_benchmark_workload_properties():
             assert abs(a - b) <= 1e-12 * float(ax.abs().sum()), op
     finally:
         fe.fe_vspace_destroy(vs)
+
+
+@pytest.mark.parametrize("variant", ["f64", "f32x2"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_persistent_launch_equals_per_order_launches(name, variant):
+    """One persistent launch over all orders (the default) and one fused launch per order give
+    the same y = E^T blockdiag(A_e) E x (up to the order of the atomic adds), for both
+    operators; the 64^3 workload's block mix is covered by the first case's orders 2, 4, 6."""
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup(name)
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        fe.fe_vspace_set_variant(vs, variant)
+        ntrue, _, _ = fe.fe_vspace_sizes(vs)
+        x = torch.from_numpy(uniform_vector(ntrue, seed=17)).cuda()
+        for op in (fe.FE_DIFFUSION, fe.FE_MASS):
+            y1 = torch.empty_like(x)
+            y0 = torch.empty_like(x)
+            fe.fe_vspace_set_persistent(vs, 1)
+            fe.fe_vspace_apply(vs, op, x, y1)
+            fe.fe_vspace_set_persistent(vs, 0)
+            fe.fe_vspace_apply(vs, op, x, y0)
+            torch.cuda.synchronize()
+            err = float((y1 - y0).abs().max()) / float(y0.abs().max())
+            assert err <= 1e-13, (op, err)
+        fe.fe_vspace_set_persistent(vs, 1)
+    finally:
+        fe.fe_vspace_destroy(vs)
+
+
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_batched_apply_and_pcg_match_single(persistent):
+    """fe_vspace_apply_batched against one fe_vspace_apply per right-hand side; and
+    fe_vspace_pcg_batched (lockstep, graph-replayed iteration batches) against fe_vspace_pcg per
+    system: the same iteration counts (+-1) and iterates, true residuals within the tolerance."""
+    torch = torch_cuda()
+    fe = lib()
+    dims, orders, V, c = _setup("blocks_2_4_6")
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    try:
+        fe.fe_vspace_set_persistent(vs, persistent)
+        fe.fe_vspace_set_variant(vs, "f32x2")
+        n, _, _ = fe.fe_vspace_sizes(vs)
+        nr = 3
+        X = torch.from_numpy(np.stack([uniform_vector(n, seed=30 + j) for j in range(nr)])).cuda()
+        Y = torch.empty_like(X)
+        fe.fe_vspace_apply_batched(vs, fe.FE_DIFFUSION, nr, X, n, Y, n)
+        y1 = torch.empty(n, dtype=torch.float64, device="cuda")
+        for j in range(nr):
+            fe.fe_vspace_apply(vs, fe.FE_DIFFUSION, X[j].contiguous(), y1)
+            torch.cuda.synchronize()
+            assert float((Y[j] - y1).abs().max()) <= 1e-13 * float(y1.abs().max())
+        B = X.clone()
+        Xs = torch.empty_like(B)
+        rtol = 1e-9
+        st, stats = fe.fe_vspace_pcg_batched(vs, fe.FE_DIFFUSION, nr, B, n, Xs, n, rtol, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        for j in range(nr):
+            x1 = torch.empty(n, dtype=torch.float64, device="cuda")
+            st1, s1 = fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, B[j].contiguous(), x1, rtol, 5000)
+            assert st1 == fe.FE_OK
+            assert abs(stats[j]["iters"] - s1["iters"]) <= 1
+            assert stats[j]["true_rel_resid"] <= 10 * rtol
+            assert float((Xs[j] - x1).abs().max()) <= 1e-7 * float(x1.abs().max())
+    finally:
+        fe.fe_vspace_destroy(vs)
