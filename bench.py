@@ -10,7 +10,8 @@ Inputs (mesh, quadrature data, right-hand side) are resident in HBM before the t
   value        GDOF/s = ndofs * (PCG applies) / time, summed over ranks: the apply throughput
                the solver sustains end to end on the device (every PCG kernel inside the time);
   ms_per_step  time of one PCG solve to 1e-8 (the metric's time-to-solution part);
-  e2e          the same, through host buffers: pinned b -> device, fe_pcg, x -> pinned host;
+  e2e          the same, through host buffers: one fe_pcg_host call per step (pinned b ->
+               device, the solve, x -> pinned host, inside the library);
   roofline     of the dominant kernel (the fused apply), timed alone with CUDA events;
   cpu_baseline the CPU oracle (sum-factorised FP64 Jacobi-PCG in C/OpenMP) on a bounded sample
                of PCG iterations of the same workload, on every host core;
@@ -549,7 +550,8 @@ def run_ours(args, rank, world, local_rank):
     value = job_gdofs(world, ndofs, applies, t)
     x_head = x.clone()
 
-    # ---- end to end through host buffers: pinned b -> device, solve, x -> pinned host
+    # ---- end to end through host buffers, one C-ABI call per step (fe_pcg_host: pinned b ->
+    #      device, the solve, x -> pinned host, all inside the library)
     b_host = b.cpu().pin_memory()
     x_host = torch.empty(ndofs, dtype=torch.float64).pin_memory()
     e2e_applies = 0
@@ -557,17 +559,19 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(extra):
-        b.copy_(b_host, non_blocking=True)
-        s_ = solve()
-        x_host.copy_(x, non_blocking=True)
-        torch.cuda.synchronize()
+        st_, s_ = fe.fe_pcg_host(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b_host, x_host, args.rtol,
+                                 MAXIT, stream)
+        if st_ != fe.FE_OK:
+            raise RuntimeError("fe_pcg_host failed: %d %s" % (st_, fe.fe_last_error()))
         e2e_applies += s_["iters"] + 1
     te = time.perf_counter() - t0
+    e2e_dx = float((x_host.to(dev) - x_head).abs().max()) / float(x_head.abs().max())
     barrier()
     te = max_over_ranks(te, dist, dev)
     e2e = {"value": job_gdofs(world, ndofs, e2e_applies, te), "unit": UNIT,
            "h2d_bytes_per_step": 8 * ndofs, "d2h_bytes_per_step": 8 * ndofs,
-           "ms_per_step": 1000.0 * te / extra, "steps": extra}
+           "ms_per_step": 1000.0 * te / extra, "steps": extra, "call": "fe_pcg_host",
+           "x_vs_device_solve": e2e_dx}
 
     # ---- the same Jacobi-PCG with the float-float arithmetic (FP64-accurate, FP32 pipe): FP64
     #      vectors, inner products and exit residual; its answer against the FP64 one above
@@ -939,9 +943,10 @@ def run_batched_pcg(args, local_rank):
 
 
 def run_sweep(args, local_rank):
-    """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1): device time of one
-    apply (median of 10 after 3 warm-ups, CUDA events) per operator and variant, one JSON line
-    each.  Not the contract line: the per-order roofline table."""
+    """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1; or meshes sized by
+    --sweep-qd-gb): device time of one apply (median of --sweep-reps after --sweep-warm warm-ups,
+    CUDA events) per operator and variant, one JSON line each.  Not the contract line: the
+    per-order roofline table."""
     import torch
     from paper_2603_09038_gb300 import fe
     from paper_2603_09038_gb300.inputs import perturbed_vertices, lognormal_coefficient, ORDER_SWEEP_N
@@ -953,8 +958,15 @@ def run_sweep(args, local_rank):
     fp64_peak = 152 * FP64_DFMA_PER_CLK_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     stream = torch.cuda.current_stream()
     orders = [int(v) for v in args.orders.split(",")]
+    ops = [(fe.FE_DIFFUSION, "diffusion"), (fe.FE_MASS, "mass")]
+    ops = [o for o in ops if o[1] in args.sweep_ops.split(",")]
     for p in orders:
         n = ORDER_SWEEP_N[p]
+        if args.sweep_qd_gb > 0:
+            # a smaller mesh whose diffusion quadrature data take about --sweep-qd-gb GB (still
+            # larger than L2), for the per-order ncu captures
+            per_elem = 6 * (p + 2) ** 3 * 8
+            n = max(4, int(round((args.sweep_qd_gb * 1e9 / per_elem) ** (1.0 / 3.0))))
         V = perturbed_vertices(n, n, n)
         c = torch.from_numpy(lognormal_coefficient(n ** 3, 1.0)).to(dev)
         mesh = fe.fe_mesh_setup(n, n, n, p, V)
@@ -964,11 +976,11 @@ def run_sweep(args, local_rank):
         y = torch.empty_like(x)
         for variant in args.variants.split(","):
             fe.fe_pa_set_variant(pa, variant)
-            for op, name in ((fe.FE_DIFFUSION, "diffusion"), (fe.FE_MASS, "mass")):
-                for _ in range(3):
+            for op, name in ops:
+                for _ in range(args.sweep_warm):
                     fe.fe_apply(pa, op, variant, x, y, stream)
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(10)]
+                      for _ in range(args.sweep_reps)]
                 torch.cuda.synchronize()
                 for a, z in ev:
                     a.record(stream)
@@ -1167,6 +1179,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="order sweep p=1..8 at ~50 M dofs")
     ap.add_argument("--orders", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-ops", default="diffusion,mass", help="--sweep: operators")
+    ap.add_argument("--sweep-warm", type=int, default=3, help="--sweep: untimed applies")
+    ap.add_argument("--sweep-reps", type=int, default=10, help="--sweep: timed applies (median)")
+    ap.add_argument("--sweep-qd-gb", type=float, default=0.0,
+                    help="--sweep: size each order's mesh by this many GB of diffusion quadrature "
+                         "data instead of ~50 M dofs (for ncu captures)")
     ap.add_argument("--peaks", action="store_true", help="FP64/DMMA/FP32/BF16-mma.sync throughput probes")
     ap.add_argument("--batched", type=int, default=0, help="batched apply with this many RHS")
     ap.add_argument("--variants", default="f64,f32x2,dmma")

@@ -205,6 +205,18 @@ int fe_load_vector_sine(const fe_pa* pa, double* dev_b, void* stream);
 int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x, double rtol, int maxit,
            fe_pcg_stats* stats, void* stream);
 
+/* fe_pcg through host buffers: the call an application makes with its vectors in host memory.
+ * host_b [ndofs] is copied to the device on `stream`, the system is solved as by fe_pcg (same
+ * op, pc, rtol, maxit and statuses), and the solution is copied back into host_x [ndofs].  Both
+ * arrays are caller-owned host memory; page-locked (pinned) arrays make the two copies DMA
+ * transfers, pageable ones work too (the driver stages them).  The device copies of b and x are
+ * allocated on first use and cached in the handle (freed by fe_pa_destroy).  host_x receives
+ * the last iterate whenever the solve ran (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN,
+ * FE_ERR_NAN); on FE_ERR_ARG, FE_ERR_UNSUPPORTED, FE_ERR_OOM or a failed copy (FE_ERR_CUDA) it is
+ * left untouched.  Synchronous; stats->seconds includes both copies. */
+int fe_pcg_host(fe_pa* pa, int op, int pc, const double* host_b, double* host_x, double rtol,
+                int maxit, fe_pcg_stats* stats, void* stream);
+
 /* PCG with a Chebyshev polynomial preconditioner (an extension; the paper uses no solver here):
  * z = q(D^-1 A_bc) D^-1 r from `degree` steps of the Chebyshev semi-iteration for
  * D^-1 A_bc z = D^-1 r, started at z = 0, on the interval [hi / lmin_ratio, hi], so that

@@ -828,6 +828,7 @@ void fe_pa_destroy(fe_pa* pa) {
   cudaFree(pa->d_red);
   cudaFree(pa->d_flags);
   cudaFree(pa->d_dpart);
+  cudaFree(pa->d_hostio);
   delete pa;
 }
 

@@ -1,20 +1,32 @@
-// Float-float (FP64-accurate on the FP32 pipe) instantiations of the fused apply kernel.
+// Float-float (FP64-accurate on the FP32 pipe) fused apply: the order dispatch, the persistent
+// multi-order kernel and the float-pair encoding of the quadrature data.
 #include "fe_apply_launch.cuh"
 
 namespace fe {
 
-// Accumulation scheme per order, from the measured worst-case error against the FP64 apply
-// (whole ~25 M dof meshes, random x): anchored sums with lazy normalisation up to p = 3
-// (~1.3e-13), anchored with normalisation for p = 4, 5 (<= 2.1e-13), compensated sums for
-// p >= 6, where the anchored error reached 4.6e-13 (p = 6) to 5.7e-13 (p = 7) -- the
-// compensated sums stay near 3e-14, well inside the 1e-12 parity bar.
-template <int P>
-struct ArForOrder<ArF32x2, P> {
-  using type = ArF32x2T<(P <= 5), (P <= 3)>;
-};
+// The per-order kernels live in fe_apply_f32x2_p*.cu.
+extern template int apply_order<ArF32x2, 1>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 2>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 3>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 4>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 5>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 6>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 7>(int, const ApplyArgs&, cudaStream_t);
+extern template int apply_order<ArF32x2, 8>(int, const ApplyArgs&, cudaStream_t);
 
 int launch_apply_f32x2(int op, const ApplyArgs& a, cudaStream_t s) {
-  return dispatch_order<ArF32x2>(op, a, s);
+  if (a.Q != a.p + 2) return set_error(FE_ERR_UNSUPPORTED, "only q1d = order + 2 is built");
+  switch (a.p) {
+    case 1: return apply_order<ArF32x2, 1>(op, a, s);
+    case 2: return apply_order<ArF32x2, 2>(op, a, s);
+    case 3: return apply_order<ArF32x2, 3>(op, a, s);
+    case 4: return apply_order<ArF32x2, 4>(op, a, s);
+    case 5: return apply_order<ArF32x2, 5>(op, a, s);
+    case 6: return apply_order<ArF32x2, 6>(op, a, s);
+    case 7: return apply_order<ArF32x2, 7>(op, a, s);
+    case 8: return apply_order<ArF32x2, 8>(op, a, s);
+    default: return set_error(FE_ERR_UNSUPPORTED, "order out of range 1..8");
+  }
 }
 
 int multi_elems_f32x2(int op, int order) {

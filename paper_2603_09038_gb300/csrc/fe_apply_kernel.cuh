@@ -107,24 +107,47 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   // ---- gather (G): E0[i][j*D + k] = x[map[e][i + D j + D^2 k]].  Scaled policies keep the
   //      FP64 value in the slot (same 8 bytes) and note its exponent; the x phase converts it
   //      with the block's scale 2^(1023 - largest exponent).
-  if constexpr (Ar::kScaled) {
+  //      Two stages per chunk of GCH items, so that every thread has its independent loads in
+  //      flight at once: the block's dof-map entries (contiguous: item t = el D^3 + a), then the
+  //      values.  The chunk bounds the registers the staging takes.
+  constexpr int GPT = (NE * D3 + NT - 1) / NT;  // gather items per thread
+  constexpr int GCH = GPT < 8 ? GPT : 8;
+  const int ntot = nel * D3;
+  const int32_t* __restrict__ mb = map + e0 * D3;
+  {
     int emax = 0;
-    for (int t = tid; t < nel * D3; t += NT) {
-      const int el = t / D3, a = t - el * D3;
-      const int i = a % D, j = (a / D) % D, k = a / D2;
-      const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-      const double v = __ldg(&x[g]);
-      reinterpret_cast<double*>(bufA)[el * SZ_A + i * S_DD + j * D + k] = v;
-      emax = max(emax, f64_exponent(v));
+#pragma unroll 1
+    for (int u0 = 0; u0 < GPT; u0 += GCH) {
+      int32_t gi[GCH];
+#pragma unroll
+      for (int u = 0; u < GCH; ++u) {
+        const int t = tid + (u0 + u) * NT;
+        gi[u] = t < ntot ? __ldg(&mb[t]) : 0;
+      }
+      VT xv[GCH];
+#pragma unroll
+      for (int u = 0; u < GCH; ++u) {
+        const int t = tid + (u0 + u) * NT;
+        xv[u] = t < ntot ? __ldg(&x[gi[u]]) : VT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < GCH; ++u) {
+        const int t = tid + (u0 + u) * NT;
+        if (t < ntot) {
+          const int el = t / D3, a = t - el * D3;
+          const int i = a % D, j = (a / D) % D, k = a / D2;
+          if constexpr (Ar::kScaled) {
+            reinterpret_cast<double*>(bufA)[el * SZ_A + i * S_DD + j * D + k] = xv[u];
+            emax = max(emax, f64_exponent(xv[u]));
+          } else {
+            bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_vec(xv[u]);
+          }
+        }
+      }
     }
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if ((tid & 31) == 0) wexp[tid >> 5] = emax;
-  } else {
-    for (int t = tid; t < nel * D3; t += NT) {
-      const int el = t / D3, a = t - el * D3;
-      const int i = a % D, j = (a / D) % D, k = a / D2;
-      const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-      bufA[el * SZ_A + i * S_DD + j * D + k] = Ar::from_vec(__ldg(&x[g]));
+    if constexpr (Ar::kScaled) {
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if ((tid & 31) == 0) wexp[tid >> 5] = emax;
     }
   }
   __syncthreads();
@@ -447,20 +470,33 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
 
   // ---- scatter-add (G^T); optionally the block's share of x^T A x = sum_e x_e . (A_e x_e),
   //      accumulated from the FP64 inputs and the FP64 results that are scattered
-  for (int t = tid; t < nel * D3; t += NT) {
-    const int el = t / D3, a = t - el * D3;
-    const int32_t g = __ldg(&map[(e0 + el) * D3 + a]);
-    const T v = bufB[el * SZ_B + a];
-    if constexpr (std::is_same<VT, float>::value) {
-      Ar::scatter(&y[g], v);
-      if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), v);
-    } else {
-      // scaled policies: undo the input scale and the element's quadrature-data scale; FP32
-      // data: undo its global shift
-      const int off = Ar::kScaled ? (xexp - 1023) + __ldg(&qscale[e0 + el]) : qshift;
-      const double vd = Ar::widen(v, off);
-      atomicAdd(&y[g], vd);
-      if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), vd);
+  //      (the map entries of a chunk first, as in the gather)
+#pragma unroll 1
+  for (int u0 = 0; u0 < GPT; u0 += GCH) {
+    int32_t gs[GCH];
+#pragma unroll
+    for (int u = 0; u < GCH; ++u) {
+      const int t = tid + (u0 + u) * NT;
+      gs[u] = t < ntot ? __ldg(&mb[t]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < GCH; ++u) {
+      const int t = tid + (u0 + u) * NT;
+      if (t >= ntot) continue;
+      const int el = t / D3, a = t - el * D3;
+      const int32_t g = gs[u];
+      const T v = bufB[el * SZ_B + a];
+      if constexpr (std::is_same<VT, float>::value) {
+        Ar::scatter(&y[g], v);
+        if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), v);
+      } else {
+        // scaled policies: undo the input scale and the element's quadrature-data scale; FP32
+        // data: undo its global shift
+        const int off = Ar::kScaled ? (xexp - 1023) + __ldg(&qscale[e0 + el]) : qshift;
+        const double vd = Ar::widen(v, off);
+        atomicAdd(&y[g], vd);
+        if (want_dot) Ar::dot_acc(dacc, __ldg(&x[g]), vd);
+      }
     }
   }
   }  // right-hand sides

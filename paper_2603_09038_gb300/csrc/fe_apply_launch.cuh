@@ -232,6 +232,25 @@ struct ArForOrder {
   using type = Ar;
 };
 
+// Float-float accumulation scheme per order, from the measured worst-case error against the FP64
+// apply (whole ~25 M dof meshes, random x): anchored sums with lazy normalisation up to p = 3
+// (~1.3e-13), anchored with normalisation for p = 4, 5 (<= 2.1e-13), compensated sums for
+// p >= 6, where the anchored error reached 4.6e-13 (p = 6) to 5.7e-13 (p = 7) -- the
+// compensated sums stay near 3e-14, well inside the 1e-12 parity bar.
+template <int P>
+struct ArForOrder<ArF32x2, P> {
+  using type = ArF32x2T<(P <= 5), (P <= 3)>;
+};
+
+// One order's apply, both operators, FP64 vectors.  The float-float orders are instantiated in
+// several translation units (fe_apply_f32x2_p*.cu) so that they compile in parallel.
+template <class Ar, int P>
+int apply_order(int op, const ApplyArgs& a, cudaStream_t s) {
+  using A = typename ArForOrder<Ar, P>::type;
+  return op == FE_DIFFUSION ? run_apply<P + 1, P + 2, true, A, double>(a, s)
+                            : run_apply<P + 1, P + 2, false, A, double>(a, s);
+}
+
 template <class Ar, class VT = double>
 int dispatch_order(int op, const ApplyArgs& a, cudaStream_t s) {
   const bool diff = (op == FE_DIFFUSION);

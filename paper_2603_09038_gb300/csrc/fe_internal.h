@@ -85,6 +85,7 @@ struct fe_pa {
   int* d_flags = nullptr;
   int64_t work_ndofs = 0;
   double* d_dpart = nullptr;       // per-block partials of the apply-fused p.Ap
+  double* d_hostio = nullptr;      // device b and x of fe_pcg_host (2 vectors of ndofs)
   int64_t dpart_cap = 0;
   double cheb_lmax[2] = {0.0, 0.0};  // cached lambda_max estimates of D^-1 A (diffusion, mass)
   bool pcg_graphs = true;          // fe_pcg replays its iteration batches as CUDA graphs

@@ -921,6 +921,42 @@ extern "C" int fe_pcg(fe_pa* pa, int op, int pc, const double* dev_b, double* de
   return pcg_status(res.state, "fe_pcg");
 }
 
+extern "C" int fe_pcg_host(fe_pa* pa, int op, int pc, const double* host_b, double* host_x,
+                           double rtol, int maxit, fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  if (!pa || !pa->mesh) return set_error(FE_ERR_ARG, "fe_pcg_host: pa is NULL");
+  if (!host_b || !host_x) return set_error(FE_ERR_ARG, "fe_pcg_host: host_b or host_x is NULL");
+  const int64_t n = pa->mesh->ndofs;
+  cudaError_t err;
+  if (!pa->d_hostio) {
+    if ((err = cudaMalloc(&pa->d_hostio, sizeof(double) * 2 * n)) != cudaSuccess) {
+      pa->d_hostio = nullptr;
+      return cuda_error(err, "fe_pcg_host: device b and x");
+    }
+  }
+  double* db = pa->d_hostio;
+  double* dx = pa->d_hostio + n;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((err = cudaMemcpyAsync(db, host_b, sizeof(double) * n, cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return cuda_error(err, "fe_pcg_host: copy b to the device");
+  const int st = fe_pcg(pa, op, pc, db, dx, rtol, maxit, stats, stream);
+  if (st != FE_OK && st != FE_ERR_NOT_CONVERGED && st != FE_ERR_BREAKDOWN && st != FE_ERR_NAN) {
+    cudaStreamSynchronize(s);  // the copy of host_b has ended when the call returns
+    return st;
+  }
+  if ((err = cudaMemcpyAsync(host_x, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) !=
+      cudaSuccess)
+    return cuda_error(err, "fe_pcg_host: copy x to the host");
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_error(err, "fe_pcg_host: synchronize");
+  if (stats)
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
 extern "C" int fe_pcg_ir(fe_pa* pa, int op, int pc, const double* dev_b, double* dev_x,
                          double rtol, int maxit, double inner_rtol, fe_pcg_stats* stats,
                          void* stream) {

@@ -75,6 +75,8 @@ _SIGS = {
     "fe_load_vector_sine": (ctypes.c_int, [_VP, _VP, _VP]),
     "fe_pcg": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                               ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
+    "fe_pcg_host": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
+                                   ctypes.c_int, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_ir": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
                                  ctypes.c_int, ctypes.c_double, ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_pcg_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_double,
@@ -299,6 +301,31 @@ def fe_pcg(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
     st = fe_pcg_stats()
     status = lib.fe_pcg(_VP(pa), int(op), int(pc), _ptr(dev_b), _ptr(dev_x), float(rtol),
                         int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
+
+
+def _host_f64(a, writable=False):
+    """Address of a host FP64 vector: a C-contiguous numpy array or CPU torch tensor (not
+    copied, so that pinned memory stays pinned)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+            raise ValueError("host vector: need a C-contiguous%s float64 array"
+                             % (" writable" if writable else ""))
+        return _VP(a.ctypes.data)
+    if getattr(a, "is_cuda", True) or not a.is_contiguous() or str(a.dtype) != "torch.float64":
+        raise ValueError("host vector: need a contiguous float64 CPU tensor or numpy array")
+    return _VP(a.data_ptr())
+
+
+def fe_pcg_host(pa, op, pc, host_b, host_x, rtol, maxit, stream=None):
+    """fe_pcg on host vectors (copies inside the call); same return value as fe_pcg."""
+    lib = load()
+    st = fe_pcg_stats()
+    status = lib.fe_pcg_host(_VP(pa), int(op), int(pc), _host_f64(host_b),
+                             _host_f64(host_x, writable=True), float(rtol), int(maxit),
+                             ctypes.byref(st), _stream(stream))
     if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
         _check(status)
     return status, _stats(st)

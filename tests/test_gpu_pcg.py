@@ -42,6 +42,47 @@ def test_pcg_matches_oracle_cg(variant, dims, p):
         assert np.all(xg[boundary_mask(*dims, p) == 1] == 0.0)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pcg_host_buffers_match_device_solve(pinned):
+    """fe_pcg_host (host b in, host x out, copies inside the call) gives bit-for-bit the
+    device call's x and iteration count, with pinned torch tensors and with pageable numpy
+    arrays; the oracle's CG pins the answer as for fe_pcg."""
+    torch = torch_cuda()
+    dims, p = (5, 4, 4), 3
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        b = torch.empty(prob.ndofs, dtype=torch.float64, device="cuda")
+        fe.fe_load_vector_sine(pa, b)
+        x = torch.empty_like(b)
+        st, ref = fe.fe_pcg(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, x, 1e-10, 5000)
+        assert st == fe.FE_OK
+        if pinned:
+            hb = b.cpu().pin_memory()
+            hx = torch.full((prob.ndofs,), float("nan"), dtype=torch.float64).pin_memory()
+        else:
+            hb = b.cpu().numpy().copy()
+            hx = np.full(prob.ndofs, np.nan)
+        st, stats = fe.fe_pcg_host(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, hb, hx, 1e-10, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        got = hx.numpy() if pinned else hx
+        assert stats["iters"] == ref["iters"]
+        assert np.array_equal(got, x.cpu().numpy())
+        xr, it, _ = _oracle_solve(prob, load_vector(prob), 1e-10)
+        assert np.abs(got - xr).max() <= 1e-8 * np.abs(xr).max()
+        # not converged: the last iterate still comes back
+        hx2 = np.full(prob.ndofs, np.nan)
+        st, stats = fe.fe_pcg_host(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b.cpu().numpy(), hx2,
+                                   1e-12, 2)
+        assert st == fe.FE_ERR_NOT_CONVERGED and stats["iters"] == 2
+        assert np.all(np.isfinite(hx2))
+        with pytest.raises(ValueError):                 # a device tensor is not a host buffer
+            fe.fe_pcg_host(pa, fe.FE_DIFFUSION, fe.FE_PC_JACOBI, b, hx2, 1e-10, 10)
+        with pytest.raises(fe.FEError) as e:            # bad operator: host_x left untouched
+            hx3 = np.full(prob.ndofs, 7.0)
+            fe.fe_pcg_host(pa, 99, fe.FE_PC_JACOBI, b.cpu().numpy(), hx3, 1e-10, 10)
+        assert e.value.status == fe.FE_ERR_ARG and np.all(hx3 == 7.0)
+
+
 def test_pcg_failure_paths():
     torch = torch_cuda()
     with gpu_problem(3, 3, 3, 2) as (fe, mesh, pa, V, c):
