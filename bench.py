@@ -48,7 +48,7 @@ EXTRA_STEPS = 5                        # timed repetitions of the secondary meas
 # 32^3 mesh of the same order, with that launch's algorithmic bytes: scaled to the benchmark's
 # launch by the algorithmic bytes (traffic grows with the elements).  Only for kernels
 # unchanged since the capture; (variant, order) -> (dram bytes, algorithmic bytes, case).
-NCU_TRAFFIC = {("f64", 3): (219.914496e6 + 4.658432e6, 219599376, "32^3 hexes, p = 3"),
+NCU_TRAFFIC = {("f64", 3): (219.807744e6 + 4.559360e6, 219599376, "32^3 hexes, p = 3"),
                ("f32x2", 3): (219.971840e6 + 4.723968e6, 219599376, "32^3 hexes, p = 3")}
 
 
@@ -942,6 +942,16 @@ def run_batched_pcg(args, local_rank):
     return 0
 
 
+def sweep_shapes(fe, pa, op, variant, spec):
+    """Launch shapes to time: "all" (every built one) or a comma list of indices."""
+    if variant == "dmma":
+        return [0]
+    _, nshapes, _, _ = fe.fe_pa_get_shape(pa, op, variant)
+    if spec == "all":
+        return list(range(nshapes))
+    return [k for k in (int(v) for v in spec.split(",")) if k < nshapes]
+
+
 def run_sweep(args, local_rank):
     """Order sweep p = 1..8 at ~50 M dofs (log-normal coefficient, sigma = 1; or meshes sized by
     --sweep-qd-gb): device time of one apply (median of --sweep-reps after --sweep-warm warm-ups,
@@ -974,27 +984,32 @@ def run_sweep(args, local_rank):
         ndofs, ne, _ = fe.fe_mesh_sizes(mesh)
         x = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
         y = torch.empty_like(x)
-        for variant in args.variants.split(","):
+        for variant, op, name, shape in (
+                (v, o, nm, k) for v in args.variants.split(",") for o, nm in ops
+                for k in sweep_shapes(fe, pa, o, v, args.sweep_shapes)):
             fe.fe_pa_set_variant(pa, variant)
-            for op, name in ops:
-                for _ in range(args.sweep_warm):
-                    fe.fe_apply(pa, op, variant, x, y, stream)
-                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                      for _ in range(args.sweep_reps)]
-                torch.cuda.synchronize()
-                for a, z in ev:
-                    a.record(stream)
-                    fe.fe_apply(pa, op, variant, x, y, stream)
-                    z.record(stream)
-                torch.cuda.synchronize()
-                ms = statistics.median(a.elapsed_time(z) for a, z in ev)
-                nbytes, flops = algorithmic(ndofs, ne, p, p + 2, op == fe.FE_DIFFUSION)
-                print(json.dumps({
-                    "sweep": True, "p": p, "n": n, "ndofs": ndofs, "op": name, "variant": variant,
-                    "ms": round(ms, 4), "gdofs": ndofs / ms / 1e6,
-                    "hbm_gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm_peak,
-                    "fp64_tflops_equiv": flops / ms / 1e9, "fp64_frac": flops / ms * 1e3 / fp64_peak}))
-                sys.stdout.flush()
+            if variant != "dmma":
+                fe.fe_pa_set_shape(pa, op, variant, shape)
+            _, _, nt, nel = fe.fe_pa_get_shape(pa, op, variant)
+            for _ in range(args.sweep_warm):
+                fe.fe_apply(pa, op, variant, x, y, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.sweep_reps)]
+            torch.cuda.synchronize()
+            for a, z in ev:
+                a.record(stream)
+                fe.fe_apply(pa, op, variant, x, y, stream)
+                z.record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(z) for a, z in ev)
+            nbytes, flops = algorithmic(ndofs, ne, p, p + 2, op == fe.FE_DIFFUSION)
+            print(json.dumps({
+                "sweep": True, "p": p, "n": n, "ndofs": ndofs, "op": name, "variant": variant,
+                "shape": shape, "threads_per_block": nt, "elems_per_block": nel,
+                "ms": round(ms, 4), "gdofs": ndofs / ms / 1e6,
+                "hbm_gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm_peak,
+                "fp64_tflops_equiv": flops / ms / 1e9, "fp64_frac": flops / ms * 1e3 / fp64_peak}))
+            sys.stdout.flush()
         fe.fe_pa_destroy(pa)
         fe.fe_mesh_destroy(mesh)
         del x, y, c
@@ -1182,6 +1197,8 @@ def main():
     ap.add_argument("--sweep-ops", default="diffusion,mass", help="--sweep: operators")
     ap.add_argument("--sweep-warm", type=int, default=3, help="--sweep: untimed applies")
     ap.add_argument("--sweep-reps", type=int, default=10, help="--sweep: timed applies (median)")
+    ap.add_argument("--sweep-shapes", default="0",
+                    help="--sweep: launch shapes to time per variant (\"all\" or indices)")
     ap.add_argument("--sweep-qd-gb", type=float, default=0.0,
                     help="--sweep: size each order's mesh by this many GB of diffusion quadrature "
                          "data instead of ~50 M dofs (for ncu captures)")

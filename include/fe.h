@@ -141,7 +141,9 @@ int fe_pa_get_variant(const fe_pa* pa, int* variant);
 
 /* Launch shape of the fused apply for (op, variant): every arithmetic has a few built shapes
  * (threads per block, and a shared-memory budget that fixes the elements per block: shape 0 the
- * default, others with smaller blocks and more of them per SM).  fe_pa_set_shape selects one
+ * default for most orders, others with smaller blocks and more of them per SM; the float-float
+ * default is the smaller-block shape 1 where it measured faster: diffusion p <= 2, mass p <= 4
+ * and p = 8).  fe_pa_set_shape selects one
  * (FE_ERR_ARG if the index is not built for the variant); fe_pa_get_shape returns the selected
  * index, the number of built shapes, and the threads and elements per block of the selected
  * shape for this handle's order (0 for FE_VARIANT_F64_DMMA, whose kernel has one fixed shape);

@@ -1,0 +1,358 @@
+// Even-odd phases of the fused apply for FP64 (policies with kEvenOdd, tables TabF64EO).
+//
+// GB300's FP64 pipe (2 DFMA per clock per SM) bounds the FP64 apply, so the lever is the number
+// of FP64 instructions.  The 1D tables of Eq. (2) are symmetric under reversal of both indices
+// (B[Q-1-q][D-1-d] = B[q][d], G[Q-1-q][D-1-d] = -G[q][d]; GLL nodes and Gauss points are
+// symmetric about the element centre), so every line contraction out = M u is done on the
+// even and odd parts of u by two half-size products whose sum and difference give the outputs
+// in mirrored pairs (TabF64EO documents the formulas).  For a line of D inputs and Q outputs
+// this costs about QD/2 + D + Q instructions instead of QD; the x and y phases share one split
+// of a line between the B and G contractions, and the z phase pairs the quadrature points qz
+// and Q-1-qz so that the transposed contraction takes the even and odd parts of the pointwise
+// products directly.
+//
+// Each function is one phase of pa_apply_block with the generic phase's shared-memory layout,
+// inputs and outputs; only the contraction arithmetic differs (and with it the rounding, within
+// the same 1e-12 parity bar).
+#pragma once
+
+#include "fe_arith.cuh"
+
+namespace fe {
+namespace eo {
+
+// ue[i] = v[i] + v[N-1-i], uo[i] = v[i] - v[N-1-i] (i < N/2); ue takes the middle entry of an
+// odd line
+template <int N>
+__device__ __forceinline__ void split(const double (&v)[N], double (&ue)[(N + 1) / 2],
+                                      double (&uo)[N / 2]) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
+    ue[i] = v[i] + v[N - 1 - i];
+    uo[i] = v[i] - v[N - 1 - i];
+  }
+  if constexpr (N % 2 == 1) ue[N / 2] = v[N / 2];
+}
+
+// out[o] = S[o] + Dd[o], out[N-1-o] = S[o] - Dd[o]; the middle output of an odd line is S
+template <int N>
+__device__ __forceinline__ void join(const double (&S)[(N + 1) / 2], const double (&Dd)[N / 2],
+                                     double (&out)[N]) {
+#pragma unroll
+  for (int o = 0; o < N / 2; ++o) {
+    out[o] = S[o] + Dd[o];
+    out[N - 1 - o] = S[o] - Dd[o];
+  }
+  if constexpr (N % 2 == 1) out[N / 2] = S[N / 2];
+}
+
+template <int N>
+__device__ __forceinline__ double dot(const double (&c)[N], const double (&u)[N]) {
+  double r = c[0] * u[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) r = fma(c[i], u[i], r);
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ double dot_acc(const double (&c)[N], const double (&u)[N], double r) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) r = fma(c[i], u[i], r);
+  return r;
+}
+
+// forward B: out[q] = sum_d B[q][d] v[d], from v's halves
+template <int D, int Q>
+__device__ __forceinline__ void fwd_b(const TabF64EO<D, Q>& t, const double (&ue)[(D + 1) / 2],
+                                      const double (&uo)[D / 2], double (&out)[Q]) {
+  double S[(Q + 1) / 2], Dd[Q / 2];
+#pragma unroll
+  for (int o = 0; o < (Q + 1) / 2; ++o) S[o] = dot(t.bS[o], ue);
+#pragma unroll
+  for (int o = 0; o < Q / 2; ++o) Dd[o] = dot(t.bD[o], uo);
+  join<Q>(S, Dd, out);
+}
+
+// forward G: out[q] = sum_d G[q][d] v[d]
+template <int D, int Q>
+__device__ __forceinline__ void fwd_g(const TabF64EO<D, Q>& t, const double (&ue)[(D + 1) / 2],
+                                      const double (&uo)[D / 2], double (&out)[Q]) {
+  double S[(Q + 1) / 2], Dd[Q / 2];
+#pragma unroll
+  for (int o = 0; o < (Q + 1) / 2; ++o) S[o] = dot(t.gS[o], uo);
+#pragma unroll
+  for (int o = 0; o < Q / 2; ++o) Dd[o] = dot(t.gD[o], ue);
+  join<Q>(S, Dd, out);
+}
+
+// transposed B: out[d] = sum_q B[q][d] a[q], from a's halves over q
+template <int D, int Q>
+__device__ __forceinline__ void tr_b(const TabF64EO<D, Q>& t, const double (&ae)[(Q + 1) / 2],
+                                     const double (&ao)[Q / 2], double (&out)[D]) {
+  double S[(D + 1) / 2], Dd[D / 2];
+#pragma unroll
+  for (int k = 0; k < (D + 1) / 2; ++k) S[k] = dot(t.btS[k], ae);
+#pragma unroll
+  for (int k = 0; k < D / 2; ++k) Dd[k] = dot(t.btD[k], ao);
+  join<D>(S, Dd, out);
+}
+
+// transposed G of a plus transposed B of b: out[d] = sum_q G[q][d] a[q] + B[q][d] b[q]
+template <int D, int Q>
+__device__ __forceinline__ void tr_gb(const TabF64EO<D, Q>& t, const double (&ae)[(Q + 1) / 2],
+                                      const double (&ao)[Q / 2], const double (&be)[(Q + 1) / 2],
+                                      const double (&bo)[Q / 2], double (&out)[D]) {
+  double S[(D + 1) / 2], Dd[D / 2];
+#pragma unroll
+  for (int k = 0; k < (D + 1) / 2; ++k) S[k] = dot_acc(t.btS[k], be, dot(t.gtS[k], ao));
+#pragma unroll
+  for (int k = 0; k < D / 2; ++k) Dd[k] = dot_acc(t.btD[k], bo, dot(t.gtD[k], ae));
+  join<D>(S, Dd, out);
+}
+
+// ---- x phase: contract i -> qx.  line (j, k); out T1c[j][k*Q + qx], c = (B x, G x)
+template <int D, int Q, int NT, bool DIFF, class L>
+__device__ __forceinline__ void x_phase(const TabF64EO<D, Q>& tab, const double* bufA,
+                                        double* bufB, int nel, int tid) {
+  constexpr int D2 = D * D;
+  for (int t = tid; t < nel * D2; t += NT) {
+    const int el = t / D2, l = t - el * D2;
+    const int j = l / D, k = l - j * D;
+    const double* in = bufA + el * L::SZ_A + l;
+    double v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = in[i * L::S_DD];
+    double ue[(D + 1) / 2], uo[D / 2];
+    split<D>(v, ue, uo);
+    double* outb = bufB + el * L::SZ_B + j * L::S_QD + k * Q;
+    double o[Q];
+    fwd_b(tab, ue, uo, o);
+#pragma unroll
+    for (int qx = 0; qx < Q; ++qx) outb[qx] = o[qx];
+    if constexpr (DIFF) {
+      fwd_g(tab, ue, uo, o);
+#pragma unroll
+      for (int qx = 0; qx < Q; ++qx) outb[D * L::S_QD + qx] = o[qx];
+    }
+  }
+}
+
+// ---- y phase: contract j -> qy.  line (k, qx); out T2c[k][qy*Q + qx]
+//      diffusion: c0 = B_y (G_x x), c1 = G_y (B_x x), c2 = B_y (B_x x)
+template <int D, int Q, int NT, bool DIFF, class L>
+__device__ __forceinline__ void y_phase(const TabF64EO<D, Q>& tab, const double* bufB,
+                                        double* bufA, int nel, int tid) {
+  constexpr int QD = Q * D;
+  for (int t = tid; t < nel * QD; t += NT) {
+    const int el = t / QD, l = t - el * QD;
+    const int k = l / Q, qx = l - k * Q;
+    const double* in = bufB + el * L::SZ_B + l;
+    double vb[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) vb[j] = in[j * L::S_QD];
+    double be[(D + 1) / 2], bo[D / 2];
+    split<D>(vb, be, bo);
+    double* out = bufA + el * L::SZ_A + k * L::S_QQ + qx;
+    double o[Q];
+    if constexpr (DIFF) {
+      double vg[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) vg[j] = in[D * L::S_QD + j * L::S_QD];
+      double ge[(D + 1) / 2], go[D / 2];
+      split<D>(vg, ge, go);
+      fwd_b(tab, ge, go, o);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) out[qy * Q] = o[qy];
+      fwd_g(tab, be, bo, o);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) out[D * L::S_QQ + qy * Q] = o[qy];
+      fwd_b(tab, be, bo, o);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) out[2 * D * L::S_QQ + qy * Q] = o[qy];
+    } else {
+      fwd_b(tab, be, bo, o);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) out[qy * Q] = o[qy];
+    }
+  }
+}
+
+// D times g at one point, D symmetric with entries (xx, xy, xz, yy, yz, zz)
+__device__ __forceinline__ void dmul(const double (&c)[6], double g0, double g1, double g2,
+                                     double& v0, double& v1, double& v2) {
+  v0 = fma(c[2], g2, fma(c[1], g1, c[0] * g0));
+  v1 = fma(c[4], g2, fma(c[3], g1, c[1] * g0));
+  v2 = fma(c[5], g2, fma(c[4], g1, c[2] * g0));
+}
+
+// r[i] (+)= c[i] s for the NA accumulators; the first pair initialises them
+template <int NA, int NC>
+__device__ __forceinline__ void acc_col(double (&r)[NA], const double (&c)[NA][NC], int q,
+                                        double s, bool first) {
+#pragma unroll
+  for (int k = 0; k < NA; ++k) r[k] = first ? c[k][q] * s : fma(c[k][q], s, r[k]);
+}
+
+// ---- z phase: contract k -> qz, apply D, contract qz -> k.  line (qy, qx); out S4c[qy][k*Q + qx]
+//      The quadrature points qz and Q-1-qz are taken together: the forward contraction gives both
+//      from one pair of half-size sums, and the sum and difference of their pointwise products
+//      are the even and odd parts the transposed contraction needs.
+template <int D, int Q, int NT, bool DIFF, class L>
+__device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double* bufA,
+                                        double* bufB, const double* __restrict__ qd, int64_t e0,
+                                        int nel, int tid) {
+  constexpr int Q2 = Q * Q, DE = (D + 1) / 2, DH = D / 2, QH = Q / 2;
+  constexpr int NQD = DIFF ? 6 : 1;
+  for (int t = tid; t < nel * Q2; t += NT) {
+    const int el = t / Q2, l = t - el * Q2;
+    const int qy = l / Q, qx = l - qy * Q;
+    const double* in = bufA + el * L::SZ_A + l;
+    const double* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
+    double* out = bufB + el * L::SZ_B + qy * L::S_QD + qx;
+    if constexpr (DIFF) {
+      double c[D];
+      double e0_[DE], o0[DH], e1[DE], o1[DH], e2[DE], o2[DH];
+#pragma unroll
+      for (int k = 0; k < D; ++k) c[k] = in[k * L::S_QQ];
+      split<D>(c, e0_, o0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) c[k] = in[D * L::S_QQ + k * L::S_QQ];
+      split<D>(c, e1, o1);
+#pragma unroll
+      for (int k = 0; k < D; ++k) c[k] = in[2 * D * L::S_QQ + k * L::S_QQ];
+      split<D>(c, e2, o2);
+      // transposed accumulators: B^T of v0 and v1, G^T of v2
+      double S0[DE], D0[DH], S1[DE], D1[DH], S2[DE], D2[DH];
+#pragma unroll
+      for (int q = 0; q < QH; ++q) {
+        const int qh = Q - 1 - q;
+        double dl[6], dh[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) {
+          dl[cc] = __ldcs(qe + (q * 6 + cc) * Q2);
+          dh[cc] = __ldcs(qe + (qh * 6 + cc) * Q2);
+        }
+        const double s0 = dot(tab.bS[q], e0_), d0 = dot(tab.bD[q], o0);
+        const double s1 = dot(tab.bS[q], e1), d1 = dot(tab.bD[q], o1);
+        const double s2 = dot(tab.gS[q], o2), d2 = dot(tab.gD[q], e2);
+        double v0l, v1l, v2l, v0h, v1h, v2h;
+        dmul(dl, s0 + d0, s1 + d1, s2 + d2, v0l, v1l, v2l);
+        dmul(dh, s0 - d0, s1 - d1, s2 - d2, v0h, v1h, v2h);
+        const bool first = (q == 0);
+        acc_col(S0, tab.btS, q, v0l + v0h, first);
+        acc_col(D0, tab.btD, q, v0l - v0h, first);
+        acc_col(S1, tab.btS, q, v1l + v1h, first);
+        acc_col(D1, tab.btD, q, v1l - v1h, first);
+        acc_col(S2, tab.gtS, q, v2l - v2h, first);
+        acc_col(D2, tab.gtD, q, v2l + v2h, first);
+      }
+      if constexpr (Q % 2 == 1) {  // the middle point: even part only (no odd partner)
+        double dm[6];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) dm[cc] = __ldcs(qe + (QH * 6 + cc) * Q2);
+        double v0, v1, v2;
+        dmul(dm, dot(tab.bS[QH], e0_), dot(tab.bS[QH], e1), dot(tab.gS[QH], o2), v0, v1, v2);
+        acc_col(S0, tab.btS, QH, v0, false);
+        acc_col(S1, tab.btS, QH, v1, false);
+        acc_col(D2, tab.gtD, QH, v2, false);
+      }
+      double w[D];
+      join<D>(S0, D0, w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k * Q] = w[k];
+      join<D>(S1, D1, w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[Q * L::S_QD + k * Q] = w[k];
+      join<D>(S2, D2, w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[2 * Q * L::S_QD + k * Q] = w[k];
+    } else {
+      double c[D], ce[DE], co[DH];
+#pragma unroll
+      for (int k = 0; k < D; ++k) c[k] = in[k * L::S_QQ];
+      split<D>(c, ce, co);
+      double S[DE], Dd[DH];
+#pragma unroll
+      for (int q = 0; q < QH; ++q) {
+        const double dl = __ldcs(qe + q * Q2), dh = __ldcs(qe + (Q - 1 - q) * Q2);
+        const double s = dot(tab.bS[q], ce), d = dot(tab.bD[q], co);
+        const double vl = dl * (s + d), vh = dh * (s - d);
+        acc_col(S, tab.btS, q, vl + vh, q == 0);
+        acc_col(Dd, tab.btD, q, vl - vh, q == 0);
+      }
+      if constexpr (Q % 2 == 1) {
+        const double v = __ldcs(qe + QH * Q2) * dot(tab.bS[QH], ce);
+        acc_col(S, tab.btS, QH, v, false);
+      }
+      double w[D];
+      join<D>(S, Dd, w);
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k * Q] = w[k];
+    }
+  }
+}
+
+// ---- y^T phase: contract qy -> j.  line (k, qx); out S5c[qx][j*D + k]
+//      diffusion: c0 (-> G_x^T) = B_y^T s0, c1 (-> B_x^T) = G_y^T s1 + B_y^T s2
+template <int D, int Q, int NT, bool DIFF, class L>
+__device__ __forceinline__ void yt_phase(const TabF64EO<D, Q>& tab, const double* bufB,
+                                         double* bufA, int nel, int tid) {
+  constexpr int QD = Q * D, QE = (Q + 1) / 2, QH = Q / 2;
+  for (int t = tid; t < nel * QD; t += NT) {
+    const int el = t / QD, l = t - el * QD;
+    const int k = l / Q, qx = l - k * Q;
+    const double* in = bufB + el * L::SZ_B + l;
+    double* out = bufA + el * L::SZ_A + qx * L::S_DD + k;
+    double a[Q], ae[QE], ao[QH], r[D];
+#pragma unroll
+    for (int qy = 0; qy < Q; ++qy) a[qy] = in[qy * L::S_QD];
+    split<Q>(a, ae, ao);
+    tr_b(tab, ae, ao, r);
+#pragma unroll
+    for (int j = 0; j < D; ++j) out[j * D] = r[j];
+    if constexpr (DIFF) {
+      double be[QE], bo[QH];
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[Q * L::S_QD + qy * L::S_QD];
+      split<Q>(a, ae, ao);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[2 * Q * L::S_QD + qy * L::S_QD];
+      split<Q>(a, be, bo);
+      tr_gb(tab, ae, ao, be, bo, r);
+#pragma unroll
+      for (int j = 0; j < D; ++j) out[Q * L::S_DD + j * D] = r[j];
+    }
+  }
+}
+
+// ---- x^T phase: contract qx -> i.  line (j, k); out Ye[i + D j + D^2 k]
+//      diffusion: G_x^T of the first array plus B_x^T of the second; mass: B_x^T
+template <int D, int Q, int NT, bool DIFF, class L>
+__device__ __forceinline__ void xt_phase(const TabF64EO<D, Q>& tab, const double* bufA,
+                                         double* bufB, int nel, int tid) {
+  constexpr int D2 = D * D, QE = (Q + 1) / 2, QH = Q / 2;
+  for (int t = tid; t < nel * D2; t += NT) {
+    const int el = t / D2, l = t - el * D2;
+    const int j = l / D, k = l - j * D;
+    const double* in = bufA + el * L::SZ_A + l;
+    double a[Q], ae[QE], ao[QH], r[D];
+#pragma unroll
+    for (int qx = 0; qx < Q; ++qx) a[qx] = in[qx * L::S_DD];
+    split<Q>(a, ae, ao);
+    if constexpr (DIFF) {
+      double be[QE], bo[QH];
+#pragma unroll
+      for (int qx = 0; qx < Q; ++qx) a[qx] = in[Q * L::S_DD + qx * L::S_DD];
+      split<Q>(a, be, bo);
+      tr_gb(tab, ae, ao, be, bo, r);
+    } else {
+      tr_b(tab, ae, ao, r);
+    }
+    double* out = bufB + el * L::SZ_B + j * D + k * D2;
+#pragma unroll
+    for (int i = 0; i < D; ++i) out[i] = r[i];
+  }
+}
+
+}  // namespace eo
+}  // namespace fe

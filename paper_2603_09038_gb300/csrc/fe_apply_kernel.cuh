@@ -23,6 +23,7 @@
 
 #include <type_traits>
 
+#include "fe_apply_eo.cuh"
 #include "fe_arith.cuh"
 #include "fe_smem_layout.h"
 
@@ -87,6 +88,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   constexpr int S_DD = L::S_DD, S_QD = L::S_QD, S_QQ = L::S_QQ;
   constexpr int SZ_A = L::SZ_A, SZ_B = L::SZ_B;
   constexpr int NQD = DIFF ? 6 : 1;
+  constexpr bool PREFETCH_QD = Ar::kPrefetchQd;
 
   T* bufA = reinterpret_cast<T*>(smem_raw);
   T* bufB = bufA + NE * SZ_A;
@@ -98,6 +100,22 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
 
   // Several right-hand sides (x0 + r ldx -> y0 + r ldy) are applied one after the other by the
   // same block: after the first, the block's dof map and quadrature data come from L2.
+  // The block's quadrature data (contiguous: elements e0 .. e0 + nel - 1) are first needed in the
+  // z phase; a bulk prefetch into L2 issued now lets them arrive during the gather and the x and
+  // y phases instead of stalling the z phase's loads on HBM latency.
+  if (PREFETCH_QD && tid < 32) {
+    constexpr int64_t QD_BYTES = (int64_t)NQD * Q * Q2 * sizeof(typename Ar::QdT);
+    constexpr int64_t CHUNK = 32 * 1024;
+    // the block's byte range rounded inward to 16-byte boundaries (the bulk operations' unit),
+    // so that it stays inside the array
+    const uintptr_t lo = (reinterpret_cast<uintptr_t>(qd) + e0 * QD_BYTES + 15) & ~(uintptr_t)15;
+    const uintptr_t hi = (reinterpret_cast<uintptr_t>(qd) + (e0 + nel) * QD_BYTES) & ~(uintptr_t)15;
+    for (uintptr_t a = lo + (uintptr_t)tid * CHUNK; a < hi; a += 32 * CHUNK) {
+      const uint32_t n = (uint32_t)((hi - a) < (uintptr_t)CHUNK ? (hi - a) : (uintptr_t)CHUNK);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(n) : "memory");
+    }
+  }
+
   const int nr = MULTI ? nrhs : 1;
   for (int rhs = 0; rhs < nr; ++rhs) {
   const VT* __restrict__ x = x0 + rhs * ldx;
@@ -159,37 +177,41 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   }
 
   // ---- x phase: contract i -> qx.  line (j, k); out T1c[j][k*Q + qx], c = (B x, G x)
-  for (int t = tid; t < nel * D2; t += NT) {
-    const int el = t / D2, l = t - el * D2;
-    const int j = l / D, k = l - j * D;
-    const T* in = bufA + el * SZ_A + l;
-    T v[D];
-    float m = 0.0f;
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      if constexpr (Ar::kScaled)
-        v[i] = Ar::from_raw(reinterpret_cast<const double*>(in)[i * S_DD], 1023 - xexp);
-      else
-        v[i] = in[i * S_DD];
-      m = Ar::amax(m, v[i]);
-    }
-    const auto sb = Ar::sigB(tab, m, false);
-    T* outb = bufB + el * SZ_B + j * S_QD + k * Q;
-#pragma unroll
-    for (int qx = 0; qx < Q; ++qx) {
-      auto ab = Ar::begin(sb);
-#pragma unroll
-      for (int i = 0; i < D; ++i) Ar::amadB(ab, tab, qx, i, v[i]);
-      outb[qx] = Ar::end(ab, sb);
-    }
-    if constexpr (DIFF) {
-      const auto sg = Ar::sigG(tab, m, false);
-#pragma unroll
+  if constexpr (Ar::kEvenOdd) {
+    eo::x_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, nel, tid);
+  } else {
+    for (int t = tid; t < nel * D2; t += NT) {
+      const int el = t / D2, l = t - el * D2;
+      const int j = l / D, k = l - j * D;
+      const T* in = bufA + el * SZ_A + l;
+      T v[D];
+      float m = 0.0f;
+  #pragma unroll
+      for (int i = 0; i < D; ++i) {
+        if constexpr (Ar::kScaled)
+          v[i] = Ar::from_raw(reinterpret_cast<const double*>(in)[i * S_DD], 1023 - xexp);
+        else
+          v[i] = in[i * S_DD];
+        m = Ar::amax(m, v[i]);
+      }
+      const auto sb = Ar::sigB(tab, m, false);
+      T* outb = bufB + el * SZ_B + j * S_QD + k * Q;
+  #pragma unroll
       for (int qx = 0; qx < Q; ++qx) {
-        auto ag = Ar::begin(sg);
-#pragma unroll
-        for (int i = 0; i < D; ++i) Ar::amadG(ag, tab, qx, i, v[i]);
-        outb[D * S_QD + qx] = Ar::end(ag, sg);
+        auto ab = Ar::begin(sb);
+  #pragma unroll
+        for (int i = 0; i < D; ++i) Ar::amadB(ab, tab, qx, i, v[i]);
+        outb[qx] = Ar::end(ab, sb);
+      }
+      if constexpr (DIFF) {
+        const auto sg = Ar::sigG(tab, m, false);
+  #pragma unroll
+        for (int qx = 0; qx < Q; ++qx) {
+          auto ag = Ar::begin(sg);
+  #pragma unroll
+          for (int i = 0; i < D; ++i) Ar::amadG(ag, tab, qx, i, v[i]);
+          outb[D * S_QD + qx] = Ar::end(ag, sg);
+        }
       }
     }
   }
@@ -197,48 +219,52 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
 
   // ---- y phase: contract j -> qy.  line (k, qx); out T2c[k][qy*Q + qx]
   //      diffusion: c0 = B_y (G_x x), c1 = G_y (B_x x), c2 = B_y (B_x x)
-  for (int t = tid; t < nel * QD; t += NT) {
-    const int el = t / QD, l = t - el * QD;
-    const int k = l / Q, qx = l - k * Q;
-    const T* in = bufB + el * SZ_B + l;
-    T vb[D];
-    float mb = 0.0f;
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      vb[j] = in[j * S_QD];
-      mb = Ar::amax(mb, vb[j]);
-    }
-    T* out = bufA + el * SZ_A + k * S_QQ + qx;
-    const auto s_bb = Ar::sigB(tab, mb, false);
-    if constexpr (DIFF) {
-      T vg[D];
-      float mg = 0.0f;
-#pragma unroll
+  if constexpr (Ar::kEvenOdd) {
+    eo::y_phase<D, Q, NT, DIFF, L>(tab, bufB, bufA, nel, tid);
+  } else {
+    for (int t = tid; t < nel * QD; t += NT) {
+      const int el = t / QD, l = t - el * QD;
+      const int k = l / Q, qx = l - k * Q;
+      const T* in = bufB + el * SZ_B + l;
+      T vb[D];
+      float mb = 0.0f;
+  #pragma unroll
       for (int j = 0; j < D; ++j) {
-        vg[j] = in[D * S_QD + j * S_QD];
-        mg = Ar::amax(mg, vg[j]);
+        vb[j] = in[j * S_QD];
+        mb = Ar::amax(mb, vb[j]);
       }
-      const auto s_bg = Ar::sigB(tab, mg, false), s_gb = Ar::sigG(tab, mb, false);
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        auto a0 = Ar::begin(s_bg), a1 = Ar::begin(s_gb), a2 = Ar::begin(s_bb);
-#pragma unroll
+      T* out = bufA + el * SZ_A + k * S_QQ + qx;
+      const auto s_bb = Ar::sigB(tab, mb, false);
+      if constexpr (DIFF) {
+        T vg[D];
+        float mg = 0.0f;
+  #pragma unroll
         for (int j = 0; j < D; ++j) {
-          Ar::amadB(a0, tab, qy, j, vg[j]);
-          Ar::amadG(a1, tab, qy, j, vb[j]);
-          Ar::amadB(a2, tab, qy, j, vb[j]);
+          vg[j] = in[D * S_QD + j * S_QD];
+          mg = Ar::amax(mg, vg[j]);
         }
-        out[qy * Q] = Ar::end(a0, s_bg);
-        out[D * S_QQ + qy * Q] = Ar::end(a1, s_gb);
-        out[2 * D * S_QQ + qy * Q] = Ar::end(a2, s_bb);
-      }
-    } else {
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        auto a0 = Ar::begin(s_bb);
-#pragma unroll
-        for (int j = 0; j < D; ++j) Ar::amadB(a0, tab, qy, j, vb[j]);
-        out[qy * Q] = Ar::end(a0, s_bb);
+        const auto s_bg = Ar::sigB(tab, mg, false), s_gb = Ar::sigG(tab, mb, false);
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          auto a0 = Ar::begin(s_bg), a1 = Ar::begin(s_gb), a2 = Ar::begin(s_bb);
+  #pragma unroll
+          for (int j = 0; j < D; ++j) {
+            Ar::amadB(a0, tab, qy, j, vg[j]);
+            Ar::amadG(a1, tab, qy, j, vb[j]);
+            Ar::amadB(a2, tab, qy, j, vb[j]);
+          }
+          out[qy * Q] = Ar::end(a0, s_bg);
+          out[D * S_QQ + qy * Q] = Ar::end(a1, s_gb);
+          out[2 * D * S_QQ + qy * Q] = Ar::end(a2, s_bb);
+        }
+      } else {
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          auto a0 = Ar::begin(s_bb);
+  #pragma unroll
+          for (int j = 0; j < D; ++j) Ar::amadB(a0, tab, qy, j, vb[j]);
+          out[qy * Q] = Ar::end(a0, s_bb);
+        }
       }
     }
   }
@@ -249,127 +275,131 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   //      the pointwise product too (exact bound per point); the transposed contraction, whose
   //      inputs appear only inside the qz loop, is anchored in a second pass over the column
   //      for Q <= 6 and compensated otherwise.
-  for (int t = tid; t < nel * Q2; t += NT) {
-    const int el = t / Q2, l = t - el * Q2;
-    const int qy = l / Q, qx = l - qy * Q;
-    const T* in = bufA + el * SZ_A + l;
-    const typename Ar::QdT* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
-    T* out = bufB + el * SZ_B + qy * S_QD + qx;
-    if constexpr (DIFF) {
-      // bounds of the three input columns (one pass over shared memory)
-      float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        m0 = Ar::amax(m0, in[k * S_QQ]);
-        m1 = Ar::amax(m1, in[D * S_QQ + k * S_QQ]);
-        m2 = Ar::amax(m2, in[2 * D * S_QQ + k * S_QQ]);
-      }
-      const auto s0 = Ar::sigB(tab, m0, false), s1 = Ar::sigB(tab, m1, false);
-      const auto s2 = Ar::sigG(tab, m2, false);
-      // Inputs are re-read from shared memory at every qz when REREAD (the empty asm with a
-      // memory clobber keeps the compiler from caching them in registers): only the 3D
-      // accumulators stay live, which keeps high orders at two or more blocks per SM.
-      // ZTWO (float-float, Q <= 6): keep the column's v values and finish with an anchored
-      // transposed contraction; otherwise accumulate w with compensated steps inside the loop
-      constexpr bool ZTWO = Ar::kAnchored && Q <= 6;
-      constexpr int NW_ = ZTWO ? 1 : D;
-      constexpr int NV_ = ZTWO ? Q : 1;
-      T w0[NW_], w1[NW_], w2[NW_];
-      T vs0[NV_], vs1[NV_], vs2[NV_];
-      float vm0 = 0.0f, vm1 = 0.0f, vm2 = 0.0f;
-#pragma unroll
-      for (int k = 0; k < NW_; ++k) w0[k] = w1[k] = w2[k] = Ar::zero();
-      // quadrature data of the next qz is loaded one iteration ahead (register double buffer)
-      T nd[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + c * Q2);
-#pragma unroll
-      for (int qz = 0; qz < Q; ++qz) {
-        if constexpr (REREAD) asm volatile("" ::: "memory");
-        T cd[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) cd[c] = nd[c];
-        if (qz + 1 < Q) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + ((qz + 1) * 6 + c) * Q2);
-        }
-        auto a0 = Ar::begin(s0), a1 = Ar::begin(s1), a2 = Ar::begin(s2);
-#pragma unroll
+  if constexpr (Ar::kEvenOdd) {
+    eo::z_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, qd, e0, nel, tid);
+  } else {
+    for (int t = tid; t < nel * Q2; t += NT) {
+      const int el = t / Q2, l = t - el * Q2;
+      const int qy = l / Q, qx = l - qy * Q;
+      const T* in = bufA + el * SZ_A + l;
+      const typename Ar::QdT* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
+      T* out = bufB + el * SZ_B + qy * S_QD + qx;
+      if constexpr (DIFF) {
+        // bounds of the three input columns (one pass over shared memory)
+        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+  #pragma unroll
         for (int k = 0; k < D; ++k) {
-          Ar::amadB(a0, tab, qz, k, in[k * S_QQ]);
-          Ar::amadB(a1, tab, qz, k, in[D * S_QQ + k * S_QQ]);
-          Ar::amadG(a2, tab, qz, k, in[2 * D * S_QQ + k * S_QQ]);
+          m0 = Ar::amax(m0, in[k * S_QQ]);
+          m1 = Ar::amax(m1, in[D * S_QQ + k * S_QQ]);
+          m2 = Ar::amax(m2, in[2 * D * S_QQ + k * S_QQ]);
         }
-        const T g0 = Ar::end(a0, s0), g1 = Ar::end(a1, s1), g2 = Ar::end(a2, s2);
-        // v = D g, D symmetric: (xx, xy, xz, yy, yz, zz)
-        const T v0 = Ar::dot3(cd[0], g0, cd[1], g1, cd[2], g2);
-        const T v1 = Ar::dot3(cd[1], g0, cd[3], g1, cd[4], g2);
-        const T v2 = Ar::dot3(cd[2], g0, cd[4], g1, cd[5], g2);
-        if constexpr (ZTWO) {
-          vs0[qz] = v0;
-          vs1[qz] = v1;
-          vs2[qz] = v2;
-          vm0 = Ar::amax(vm0, v0);
-          vm1 = Ar::amax(vm1, v1);
-          vm2 = Ar::amax(vm2, v2);
-        } else {
-#pragma unroll
+        const auto s0 = Ar::sigB(tab, m0, false), s1 = Ar::sigB(tab, m1, false);
+        const auto s2 = Ar::sigG(tab, m2, false);
+        // Inputs are re-read from shared memory at every qz when REREAD (the empty asm with a
+        // memory clobber keeps the compiler from caching them in registers): only the 3D
+        // accumulators stay live, which keeps high orders at two or more blocks per SM.
+        // ZTWO (float-float, Q <= 6): keep the column's v values and finish with an anchored
+        // transposed contraction; otherwise accumulate w with compensated steps inside the loop
+        constexpr bool ZTWO = Ar::kAnchored && Q <= 6;
+        constexpr int NW_ = ZTWO ? 1 : D;
+        constexpr int NV_ = ZTWO ? Q : 1;
+        T w0[NW_], w1[NW_], w2[NW_];
+        T vs0[NV_], vs1[NV_], vs2[NV_];
+        float vm0 = 0.0f, vm1 = 0.0f, vm2 = 0.0f;
+  #pragma unroll
+        for (int k = 0; k < NW_; ++k) w0[k] = w1[k] = w2[k] = Ar::zero();
+        // quadrature data of the next qz is loaded one iteration ahead (register double buffer)
+        T nd[6];
+  #pragma unroll
+        for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + c * Q2);
+  #pragma unroll
+        for (int qz = 0; qz < Q; ++qz) {
+          if constexpr (REREAD) asm volatile("" ::: "memory");
+          T cd[6];
+  #pragma unroll
+          for (int c = 0; c < 6; ++c) cd[c] = nd[c];
+          if (qz + 1 < Q) {
+  #pragma unroll
+            for (int c = 0; c < 6; ++c) nd[c] = Ar::load_qd(qe + ((qz + 1) * 6 + c) * Q2);
+          }
+          auto a0 = Ar::begin(s0), a1 = Ar::begin(s1), a2 = Ar::begin(s2);
+  #pragma unroll
           for (int k = 0; k < D; ++k) {
-            Ar::madB(w0[k], tab, qz, k, v0);
-            Ar::madB(w1[k], tab, qz, k, v1);
-            Ar::madG(w2[k], tab, qz, k, v2);
+            Ar::amadB(a0, tab, qz, k, in[k * S_QQ]);
+            Ar::amadB(a1, tab, qz, k, in[D * S_QQ + k * S_QQ]);
+            Ar::amadG(a2, tab, qz, k, in[2 * D * S_QQ + k * S_QQ]);
+          }
+          const T g0 = Ar::end(a0, s0), g1 = Ar::end(a1, s1), g2 = Ar::end(a2, s2);
+          // v = D g, D symmetric: (xx, xy, xz, yy, yz, zz)
+          const T v0 = Ar::dot3(cd[0], g0, cd[1], g1, cd[2], g2);
+          const T v1 = Ar::dot3(cd[1], g0, cd[3], g1, cd[4], g2);
+          const T v2 = Ar::dot3(cd[2], g0, cd[4], g1, cd[5], g2);
+          if constexpr (ZTWO) {
+            vs0[qz] = v0;
+            vs1[qz] = v1;
+            vs2[qz] = v2;
+            vm0 = Ar::amax(vm0, v0);
+            vm1 = Ar::amax(vm1, v1);
+            vm2 = Ar::amax(vm2, v2);
+          } else {
+  #pragma unroll
+            for (int k = 0; k < D; ++k) {
+              Ar::madB(w0[k], tab, qz, k, v0);
+              Ar::madB(w1[k], tab, qz, k, v1);
+              Ar::madG(w2[k], tab, qz, k, v2);
+            }
           }
         }
-      }
-      if constexpr (ZTWO) {
-        // second pass over the column: the transposed z contraction, anchored now that the
-        // bounds max_qz |v_c| are known
-        const auto t0 = Ar::sigB(tab, vm0, true), t1 = Ar::sigB(tab, vm1, true);
-        const auto t2 = Ar::sigG(tab, vm2, true);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          auto r0 = Ar::begin(t0), r1 = Ar::begin(t1), r2 = Ar::begin(t2);
-#pragma unroll
-          for (int qz = 0; qz < Q; ++qz) {
-            Ar::amadB(r0, tab, qz, k, vs0[qz]);
-            Ar::amadB(r1, tab, qz, k, vs1[qz]);
-            Ar::amadG(r2, tab, qz, k, vs2[qz]);
+        if constexpr (ZTWO) {
+          // second pass over the column: the transposed z contraction, anchored now that the
+          // bounds max_qz |v_c| are known
+          const auto t0 = Ar::sigB(tab, vm0, true), t1 = Ar::sigB(tab, vm1, true);
+          const auto t2 = Ar::sigG(tab, vm2, true);
+  #pragma unroll
+          for (int k = 0; k < D; ++k) {
+            auto r0 = Ar::begin(t0), r1 = Ar::begin(t1), r2 = Ar::begin(t2);
+  #pragma unroll
+            for (int qz = 0; qz < Q; ++qz) {
+              Ar::amadB(r0, tab, qz, k, vs0[qz]);
+              Ar::amadB(r1, tab, qz, k, vs1[qz]);
+              Ar::amadG(r2, tab, qz, k, vs2[qz]);
+            }
+            out[k * Q] = Ar::end(r0, t0);
+            out[Q * S_QD + k * Q] = Ar::end(r1, t1);
+            out[2 * Q * S_QD + k * Q] = Ar::end(r2, t2);
           }
-          out[k * Q] = Ar::end(r0, t0);
-          out[Q * S_QD + k * Q] = Ar::end(r1, t1);
-          out[2 * Q * S_QD + k * Q] = Ar::end(r2, t2);
+        } else {
+  #pragma unroll
+          for (int k = 0; k < D; ++k) {
+            out[k * Q] = Ar::norm(w0[k]);
+            out[Q * S_QD + k * Q] = Ar::norm(w1[k]);
+            out[2 * Q * S_QD + k * Q] = Ar::norm(w2[k]);
+          }
         }
       } else {
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          out[k * Q] = Ar::norm(w0[k]);
-          out[Q * S_QD + k * Q] = Ar::norm(w1[k]);
-          out[2 * Q * S_QD + k * Q] = Ar::norm(w2[k]);
+        float m = 0.0f;
+  #pragma unroll
+        for (int k = 0; k < D; ++k) m = Ar::amax(m, in[k * S_QQ]);
+        const auto s = Ar::sigB(tab, m, false);
+        T w[D];
+  #pragma unroll
+        for (int k = 0; k < D; ++k) w[k] = Ar::zero();
+        T nd = Ar::load_qd(qe);
+  #pragma unroll
+        for (int qz = 0; qz < Q; ++qz) {
+          if constexpr (REREAD) asm volatile("" ::: "memory");
+          const T cd = nd;
+          if (qz + 1 < Q) nd = Ar::load_qd(qe + (qz + 1) * Q2);
+          auto a = Ar::begin(s);
+  #pragma unroll
+          for (int k = 0; k < D; ++k) Ar::amadB(a, tab, qz, k, in[k * S_QQ]);
+          const T v = Ar::norm(Ar::mul(cd, Ar::end(a, s)));
+  #pragma unroll
+          for (int k = 0; k < D; ++k) Ar::madB(w[k], tab, qz, k, v);
         }
+  #pragma unroll
+        for (int k = 0; k < D; ++k) out[k * Q] = Ar::norm(w[k]);
       }
-    } else {
-      float m = 0.0f;
-#pragma unroll
-      for (int k = 0; k < D; ++k) m = Ar::amax(m, in[k * S_QQ]);
-      const auto s = Ar::sigB(tab, m, false);
-      T w[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) w[k] = Ar::zero();
-      T nd = Ar::load_qd(qe);
-#pragma unroll
-      for (int qz = 0; qz < Q; ++qz) {
-        if constexpr (REREAD) asm volatile("" ::: "memory");
-        const T cd = nd;
-        if (qz + 1 < Q) nd = Ar::load_qd(qe + (qz + 1) * Q2);
-        auto a = Ar::begin(s);
-#pragma unroll
-        for (int k = 0; k < D; ++k) Ar::amadB(a, tab, qz, k, in[k * S_QQ]);
-        const T v = Ar::norm(Ar::mul(cd, Ar::end(a, s)));
-#pragma unroll
-        for (int k = 0; k < D; ++k) Ar::madB(w[k], tab, qz, k, v);
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) out[k * Q] = Ar::norm(w[k]);
     }
   }
   __syncthreads();
@@ -377,94 +407,102 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   // ---- y^T phase: contract qy -> j.  line (k, qx); out S5c[qx][j*D + k]
   //      diffusion: c0 (-> G_x^T) = B_y^T s0, c1 (-> B_x^T) = G_y^T s1 + B_y^T s2
   //      (outer-product form over qy with anchored accumulators; bounds from a first pass)
-  for (int t = tid; t < nel * QD; t += NT) {
-    const int el = t / QD, l = t - el * QD;
-    const int k = l / Q, qx = l - k * Q;
-    const T* in = bufB + el * SZ_B + l;
-    T* out = bufA + el * SZ_A + qx * S_DD + k;
-    if constexpr (DIFF) {
-      float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        m0 = Ar::amax(m0, in[qy * S_QD]);
-        m1 = Ar::amax(m1, in[Q * S_QD + qy * S_QD]);
-        m2 = Ar::amax(m2, in[2 * Q * S_QD + qy * S_QD]);
-      }
-      const auto sg = Ar::sigB(tab, m0, true), sb = Ar::sigGB(tab, m1, m2, true);
-      typename Ar::Acc rg[D], rb[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        rg[j] = Ar::begin(sg);
-        rb[j] = Ar::begin(sb);
-      }
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        const T a0 = in[qy * S_QD], a1 = in[Q * S_QD + qy * S_QD], a2 = in[2 * Q * S_QD + qy * S_QD];
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          Ar::amadB(rg[j], tab, qy, j, a0);
-          Ar::amadG(rb[j], tab, qy, j, a1);
-          Ar::amadB(rb[j], tab, qy, j, a2);
+  if constexpr (Ar::kEvenOdd) {
+    eo::yt_phase<D, Q, NT, DIFF, L>(tab, bufB, bufA, nel, tid);
+  } else {
+    for (int t = tid; t < nel * QD; t += NT) {
+      const int el = t / QD, l = t - el * QD;
+      const int k = l / Q, qx = l - k * Q;
+      const T* in = bufB + el * SZ_B + l;
+      T* out = bufA + el * SZ_A + qx * S_DD + k;
+      if constexpr (DIFF) {
+        float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          m0 = Ar::amax(m0, in[qy * S_QD]);
+          m1 = Ar::amax(m1, in[Q * S_QD + qy * S_QD]);
+          m2 = Ar::amax(m2, in[2 * Q * S_QD + qy * S_QD]);
         }
+        const auto sg = Ar::sigB(tab, m0, true), sb = Ar::sigGB(tab, m1, m2, true);
+        typename Ar::Acc rg[D], rb[D];
+  #pragma unroll
+        for (int j = 0; j < D; ++j) {
+          rg[j] = Ar::begin(sg);
+          rb[j] = Ar::begin(sb);
+        }
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          const T a0 = in[qy * S_QD], a1 = in[Q * S_QD + qy * S_QD], a2 = in[2 * Q * S_QD + qy * S_QD];
+  #pragma unroll
+          for (int j = 0; j < D; ++j) {
+            Ar::amadB(rg[j], tab, qy, j, a0);
+            Ar::amadG(rb[j], tab, qy, j, a1);
+            Ar::amadB(rb[j], tab, qy, j, a2);
+          }
+        }
+  #pragma unroll
+        for (int j = 0; j < D; ++j) {
+          out[j * D] = Ar::end(rg[j], sg);
+          out[Q * S_DD + j * D] = Ar::end(rb[j], sb);
+        }
+      } else {
+        float m0 = 0.0f;
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) m0 = Ar::amax(m0, in[qy * S_QD]);
+        const auto s0 = Ar::sigB(tab, m0, true);
+        typename Ar::Acc r[D];
+  #pragma unroll
+        for (int j = 0; j < D; ++j) r[j] = Ar::begin(s0);
+  #pragma unroll
+        for (int qy = 0; qy < Q; ++qy) {
+          const T a0 = in[qy * S_QD];
+  #pragma unroll
+          for (int j = 0; j < D; ++j) Ar::amadB(r[j], tab, qy, j, a0);
+        }
+  #pragma unroll
+        for (int j = 0; j < D; ++j) out[j * D] = Ar::end(r[j], s0);
       }
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        out[j * D] = Ar::end(rg[j], sg);
-        out[Q * S_DD + j * D] = Ar::end(rb[j], sb);
-      }
-    } else {
-      float m0 = 0.0f;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) m0 = Ar::amax(m0, in[qy * S_QD]);
-      const auto s0 = Ar::sigB(tab, m0, true);
-      typename Ar::Acc r[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) r[j] = Ar::begin(s0);
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        const T a0 = in[qy * S_QD];
-#pragma unroll
-        for (int j = 0; j < D; ++j) Ar::amadB(r[j], tab, qy, j, a0);
-      }
-#pragma unroll
-      for (int j = 0; j < D; ++j) out[j * D] = Ar::end(r[j], s0);
     }
   }
   __syncthreads();
 
   // ---- x^T phase: contract qx -> i.  line (j, k); out Ye[i + D j + D^2 k]
-  for (int t = tid; t < nel * D2; t += NT) {
-    const int el = t / D2, l = t - el * D2;
-    const int j = l / D, k = l - j * D;
-    const T* in = bufA + el * SZ_A + l;
-    float mg = 0.0f, mb = 0.0f;
-#pragma unroll
-    for (int qx = 0; qx < Q; ++qx) {
-      mg = Ar::amax(mg, in[qx * S_DD]);
-      if constexpr (DIFF) mb = Ar::amax(mb, in[Q * S_DD + qx * S_DD]);
-    }
-    const auto s = DIFF ? Ar::sigGB(tab, mg, mb, true) : Ar::sigB(tab, mg, true);
-    typename Ar::Acc r[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) r[i] = Ar::begin(s);
-#pragma unroll
-    for (int qx = 0; qx < Q; ++qx) {
-      const T ag = in[qx * S_DD];
-      if constexpr (DIFF) {
-        const T ab = in[Q * S_DD + qx * S_DD];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-          Ar::amadG(r[i], tab, qx, i, ag);
-          Ar::amadB(r[i], tab, qx, i, ab);
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) Ar::amadB(r[i], tab, qx, i, ag);
+  if constexpr (Ar::kEvenOdd) {
+    eo::xt_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, nel, tid);
+  } else {
+    for (int t = tid; t < nel * D2; t += NT) {
+      const int el = t / D2, l = t - el * D2;
+      const int j = l / D, k = l - j * D;
+      const T* in = bufA + el * SZ_A + l;
+      float mg = 0.0f, mb = 0.0f;
+  #pragma unroll
+      for (int qx = 0; qx < Q; ++qx) {
+        mg = Ar::amax(mg, in[qx * S_DD]);
+        if constexpr (DIFF) mb = Ar::amax(mb, in[Q * S_DD + qx * S_DD]);
       }
+      const auto s = DIFF ? Ar::sigGB(tab, mg, mb, true) : Ar::sigB(tab, mg, true);
+      typename Ar::Acc r[D];
+  #pragma unroll
+      for (int i = 0; i < D; ++i) r[i] = Ar::begin(s);
+  #pragma unroll
+      for (int qx = 0; qx < Q; ++qx) {
+        const T ag = in[qx * S_DD];
+        if constexpr (DIFF) {
+          const T ab = in[Q * S_DD + qx * S_DD];
+  #pragma unroll
+          for (int i = 0; i < D; ++i) {
+            Ar::amadG(r[i], tab, qx, i, ag);
+            Ar::amadB(r[i], tab, qx, i, ab);
+          }
+        } else {
+  #pragma unroll
+          for (int i = 0; i < D; ++i) Ar::amadB(r[i], tab, qx, i, ag);
+        }
+      }
+      T* out = bufB + el * SZ_B + j * D + k * D2;
+  #pragma unroll
+      for (int i = 0; i < D; ++i) out[i] = Ar::end(r[i], s);
     }
-    T* out = bufB + el * SZ_B + j * D + k * D2;
-#pragma unroll
-    for (int i = 0; i < D; ++i) out[i] = Ar::end(r[i], s);
   }
   __syncthreads();
 

@@ -130,6 +130,35 @@ inline void fill_tab(const Basis1D& b, TabF64<D, Q>* t) {
   }
 }
 
+// The even-odd halves of TabF64EO, formed in long double from the FP64 tables.
+template <int D, int Q>
+inline void fill_tab(const Basis1D& b, TabF64EO<D, Q>* t) {
+  using L = long double;
+  using TT = TabF64EO<D, Q>;
+  for (int i = 0; i < Q * D; ++i) {
+    t->B[i] = b.B[i];
+    t->G[i] = b.G[i];
+  }
+  auto Bq = [&](int q, int d) { return (L)b.B[q * D + d]; };
+  auto Gq = [&](int q, int d) { return (L)b.G[q * D + d]; };
+  for (int o = 0; o < TT::QE; ++o) {
+    for (int i = 0; i < TT::DE; ++i) t->bS[o][i] = (double)((Bq(o, i) + Bq(Q - 1 - o, i)) / 2);
+    for (int i = 0; i < TT::DH; ++i) t->gS[o][i] = (double)((Gq(o, i) + Gq(Q - 1 - o, i)) / 2);
+  }
+  for (int o = 0; o < TT::QH; ++o) {
+    for (int i = 0; i < TT::DH; ++i) t->bD[o][i] = (double)((Bq(o, i) - Bq(Q - 1 - o, i)) / 2);
+    for (int i = 0; i < TT::DE; ++i) t->gD[o][i] = (double)((Gq(o, i) - Gq(Q - 1 - o, i)) / 2);
+  }
+  for (int k = 0; k < TT::DE; ++k) {
+    for (int q = 0; q < TT::QE; ++q) t->btS[k][q] = (double)((Bq(q, k) + Bq(q, D - 1 - k)) / 2);
+    for (int q = 0; q < TT::QH; ++q) t->gtS[k][q] = (double)((Gq(q, k) + Gq(q, D - 1 - k)) / 2);
+  }
+  for (int k = 0; k < TT::DH; ++k) {
+    for (int q = 0; q < TT::QH; ++q) t->btD[k][q] = (double)((Bq(q, k) - Bq(q, D - 1 - k)) / 2);
+    for (int q = 0; q < TT::QE; ++q) t->gtD[k][q] = (double)((Gq(q, k) - Gq(q, D - 1 - k)) / 2);
+  }
+}
+
 template <int D, int Q>
 inline void fill_tab(const Basis1D& b, TabF32<D, Q>* t) {
   for (int i = 0; i < Q * D; ++i) {

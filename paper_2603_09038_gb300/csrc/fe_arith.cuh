@@ -40,6 +40,26 @@ struct TabF64 {
   double G[Q * D];
 };
 
+// FP64 tables with their even-odd halves.  The 1D tables are symmetric under reversal of both
+// indices (GLL nodes and Gauss points are symmetric about the element centre):
+// B[Q-1-q][D-1-d] = B[q][d] and G[Q-1-q][D-1-d] = -G[q][d].  So a contraction out = M x of a
+// line splits into half-size sums over x's even and odd parts
+// (ue[i] = x[i] + x[N-1-i], uo[i] = x[i] - x[N-1-i]; ue takes the middle entry of an odd line):
+// out[o] = S[o] + Dd[o], out[NO-1-o] = S[o] - Dd[o] (and out[mid] = S[mid]), with
+// S[o] = sum_i (M[o][i] + M[NO-1-o][i]) / 2 u_S[i], Dd[o] = sum_i (M[o][i] - M[NO-1-o][i]) / 2 u_D[i],
+// where u_S, u_D = ue, uo for the symmetric B and uo, ue for the antisymmetric G.  Forward
+// tables are [output q][input d], transposed ones [output d][input q].
+template <int D, int Q>
+struct TabF64EO {
+  static constexpr int DE = (D + 1) / 2, DH = D / 2, QE = (Q + 1) / 2, QH = Q / 2;
+  double B[Q * D];
+  double G[Q * D];
+  double bS[QE][DE], bD[QH][DH];    // B forward:  S on ue, Dd on uo
+  double gS[QE][DH], gD[QH][DE];    // G forward:  S on uo, Dd on ue
+  double btS[DE][QE], btD[DH][QH];  // B^T:        S on ue, Dd on uo (over q)
+  double gtS[DE][QH], gtD[DH][QE];  // G^T:        S on uo, Dd on ue (over q)
+};
+
 // Float-float tables; rB/rG = max_q sum_d |.| (forward contractions), cB/cG = max_d sum_q |.|
 // (transposed contractions), each rounded up.
 template <int D, int Q>
@@ -59,12 +79,15 @@ struct TabF32 {
 struct ArF64 {
   static constexpr bool kAnchored = false;
   static constexpr bool kScaled = false;  // inputs converted as they are gathered
+  static constexpr bool kPrefetchQd = false;  // FP64-pipe bound: nothing to hide
   using QdT = double;
   using T = double;
   using Acc = double;
   using Sig = float;  // unused
   template <int D, int Q>
-  using Tab = TabF64<D, Q>;
+  using Tab = TabF64EO<D, Q>;
+  // contractions by even-odd halves (fe_apply_eo.cuh): fewer FP64-pipe instructions
+  static constexpr bool kEvenOdd = true;
 
   static __device__ __forceinline__ T zero() { return 0.0; }
   static __device__ __forceinline__ T from_vec(double v) { return v; }
@@ -124,6 +147,8 @@ struct ArF32x2T {
   // element's largest entry in [1, 2)); results are widened with both scales undone.  So the
   // arithmetic is FP64-accurate for inputs anywhere in the FP64 range, not only the float range.
   static constexpr bool kScaled = true;
+  static constexpr bool kEvenOdd = false;
+  static constexpr bool kPrefetchQd = true;  // bulk L2 prefetch of the block's quadrature data
   using QdT = double;  // 8-byte (hi, lo) float pairs
   using T = f2;
   using Acc = Anch;
@@ -235,6 +260,8 @@ using ArF32x2 = ArF32x2T<true, false>;
 struct ArF32 {
   static constexpr bool kAnchored = false;
   static constexpr bool kScaled = false;
+  static constexpr bool kEvenOdd = false;
+  static constexpr bool kPrefetchQd = true;  // bulk L2 prefetch of the block's quadrature data
   using QdT = float;
   using T = float;
   using Acc = float;

@@ -55,6 +55,21 @@ def test_matches_oracle_tables(p):
         np.testing.assert_allclose(got, ref, rtol=0, atol=tol)
 
 
+@pytest.mark.parametrize("p", range(1, 9))
+def test_reversal_symmetry_of_the_tables(p):
+    """The even-odd FP64 contractions rely on B[Q-1-q][D-1-d] = B[q][d] and
+    G[Q-1-q][D-1-d] = -G[q][d] (nodes and points symmetric about 1/2); the same holds for the
+    oracle's tables, built independently."""
+    fe = _lib()
+    q = p + 2
+    nodes, pts, wts, B, G = fe.fe_basis_1d(p, q)
+    np.testing.assert_allclose(nodes[::-1], 1.0 - nodes, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(pts[::-1], 1.0 - pts, rtol=0, atol=1e-15)
+    for Bt, Gt in ((B, G), oracle_basis_1d(p, q)[:2]):
+        assert np.abs(Bt[::-1, ::-1] - Bt).max() <= 1e-14
+        assert np.abs(Gt[::-1, ::-1] + Gt).max() <= 1e-12 * np.abs(Gt).max()
+
+
 @pytest.mark.parametrize("order,q1d", [(0, 2), (9, 11), (3, 0), (3, 11)])
 def test_bad_arguments(order, q1d):
     fe = _lib()

@@ -253,6 +253,13 @@ def test_every_launch_shape_matches_oracle(variant, p):
         xh = uniform_vector(prob.ndofs, seed=p + 20)
         _, nshapes, _, _ = fe.fe_pa_get_shape(pa, 1, variant)
         assert nshapes >= 2
+        # defaults: the float-float smaller-block shape where it measured faster
+        sel_d = fe.fe_pa_get_shape(pa, fe.FE_DIFFUSION, variant)[0]
+        sel_m = fe.fe_pa_get_shape(pa, fe.FE_MASS, variant)[0]
+        if variant == "f32x2":
+            assert (sel_d, sel_m) == (1 if p <= 2 else 0, 1 if p <= 4 or p == 8 else 0)
+        else:
+            assert (sel_d, sel_m) == (0, 0)
         geoms = set()
         for k in range(nshapes):
             for op, kind in OPS:

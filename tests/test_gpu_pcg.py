@@ -44,9 +44,10 @@ def test_pcg_matches_oracle_cg(variant, dims, p):
 
 @pytest.mark.parametrize("pinned", [True, False])
 def test_pcg_host_buffers_match_device_solve(pinned):
-    """fe_pcg_host (host b in, host x out, copies inside the call) gives bit-for-bit the
-    device call's x and iteration count, with pinned torch tensors and with pageable numpy
-    arrays; the oracle's CG pins the answer as for fe_pcg."""
+    """fe_pcg_host (host b in, host x out, copies inside the call) gives the device call's
+    iteration count and x (to rounding: the scatter's FP64 atomics make the order of the sums,
+    and so the last bits, vary from solve to solve), with pinned torch tensors and with pageable
+    numpy arrays; the oracle's CG pins the answer as for fe_pcg."""
     torch = torch_cuda()
     dims, p = (5, 4, 4), 3
     with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
@@ -66,7 +67,8 @@ def test_pcg_host_buffers_match_device_solve(pinned):
         assert st == fe.FE_OK, fe.fe_last_error()
         got = hx.numpy() if pinned else hx
         assert stats["iters"] == ref["iters"]
-        assert np.array_equal(got, x.cpu().numpy())
+        xd = x.cpu().numpy()
+        assert np.abs(got - xd).max() <= 1e-9 * np.abs(xd).max()
         xr, it, _ = _oracle_solve(prob, load_vector(prob), 1e-10)
         assert np.abs(got - xr).max() <= 1e-8 * np.abs(xr).max()
         # not converged: the last iterate still comes back
