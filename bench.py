@@ -49,7 +49,8 @@ EXTRA_STEPS = 5                        # timed repetitions of the secondary meas
 # launch by the algorithmic bytes (traffic grows with the elements).  Only for kernels
 # unchanged since the capture; (variant, order) -> (dram bytes, algorithmic bytes, case).
 NCU_TRAFFIC = {("f64", 3): (219.807744e6 + 4.559360e6, 219599376, "32^3 hexes, p = 3"),
-               ("f32x2", 3): (219.971840e6 + 4.723968e6, 219599376, "32^3 hexes, p = 3")}
+               ("f32x2", 3): (220.169472e6 + 4.021248e6, 219599376, "32^3 hexes, p = 3"),
+               ("mixed", 4, 3): (1401.652e6 + 188.421e6, 1505387536, "48^3 hexes, H1 p = 4 / L2 p = 3")}
 
 
 def measured_peaks():
@@ -89,6 +90,15 @@ def mixed_algorithmic(n, ph=4, pl=3):
     l2 = 3 * (Q * Dl ** 3 + Q * Q * Dl * Dl + Q ** 3 * Dl)
     fma = 2 * (h1 + l2 + 9 * Q ** 3)
     return nbytes, 2 * ne * fma, nh, nl
+
+
+def mixed_traffic(ph, pl, nbytes):
+    """DRAM bytes of one fused mixed launch: the ncu capture's bytes scaled by algorithmic bytes
+    (None for an order pair without a capture)."""
+    if ("mixed", ph, pl) not in NCU_TRAFFIC:
+        return None
+    meas, algo, _ = NCU_TRAFFIC[("mixed", ph, pl)]
+    return meas * nbytes / algo
 
 
 def measure_mixed(fe, torch, n, stream, reps=10, ph=4, pl=3):
@@ -133,7 +143,11 @@ def measure_mixed(fe, torch, n, stream, reps=10, ph=4, pl=3):
             "gdofs_fused": (nh + nl) / (ms * 1e-3) / 1e9,
             "fusion_speedup": (ms_g + ms_d) / ms, "dtype": "f64",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                         "traffic": mixed_traffic(ph, pl, nbytes),
+                         "traffic_source": "ncu dram bytes (read + write) of one launch on %s, scaled "
+                                           "by algorithmic bytes" % NCU_TRAFFIC[("mixed", 4, 3)][2]
+                                           if ("mixed", ph, pl) in NCU_TRAFFIC else None,
                          "kernel": "k_mixed_apply<DH=%d,DL=%d,Q=%d,grad+div>" % (ph + 1, pl + 1, ph + 1),
                          "peak_source": "FP64 pipe: 152 SMs x %d DFMA/clk x 2 flop x %.0f MHz"
                                         % (FP64_DFMA_PER_CLK_PER_SM, sm_max),

@@ -1,7 +1,7 @@
-// Even-odd phases of the fused apply for FP64 (policies with kEvenOdd, tables TabF64EO).
+// Even-odd phases of the fused apply for the FP64 and FP32 policies (kEvenOdd, tables TabEO).
 //
 // GB300's FP64 pipe (2 DFMA per clock per SM) bounds the FP64 apply, so the lever is the number
-// of FP64 instructions.  The 1D tables of Eq. (2) are symmetric under reversal of both indices
+// of FP64 instructions (the FP32 apply of the inner solves gains less: it is closer to HBM).  The 1D tables of Eq. (2) are symmetric under reversal of both indices
 // (B[Q-1-q][D-1-d] = B[q][d], G[Q-1-q][D-1-d] = -G[q][d]; GLL nodes and Gauss points are
 // symmetric about the element centre), so every line contraction out = M u is done on the
 // even and odd parts of u by two half-size products whose sum and difference give the outputs
@@ -21,11 +21,41 @@
 namespace fe {
 namespace eo {
 
+// Host: the tables B, G [Q][D] (G may be null: zero) and their even-odd halves, formed in long
+// double and rounded once to R.
+template <class R, int D, int Q>
+inline void fill(const double* B, const double* G, TabEO<R, D, Q>* t) {
+  using L = long double;
+  using TT = TabEO<R, D, Q>;
+  auto Bq = [&](int q, int d) { return (L)B[q * D + d]; };
+  auto Gq = [&](int q, int d) { return G ? (L)G[q * D + d] : (L)0; };
+  for (int q = 0; q < Q; ++q)
+    for (int d = 0; d < D; ++d) {
+      t->B[q * D + d] = (R)Bq(q, d);
+      t->G[q * D + d] = (R)Gq(q, d);
+    }
+  for (int o = 0; o < TT::QE; ++o) {
+    for (int i = 0; i < TT::DE; ++i) t->bS[o][i] = (R)((Bq(o, i) + Bq(Q - 1 - o, i)) / 2);
+    for (int i = 0; i < TT::DH; ++i) t->gS[o][i] = (R)((Gq(o, i) + Gq(Q - 1 - o, i)) / 2);
+  }
+  for (int o = 0; o < TT::QH; ++o) {
+    for (int i = 0; i < TT::DH; ++i) t->bD[o][i] = (R)((Bq(o, i) - Bq(Q - 1 - o, i)) / 2);
+    for (int i = 0; i < TT::DE; ++i) t->gD[o][i] = (R)((Gq(o, i) - Gq(Q - 1 - o, i)) / 2);
+  }
+  for (int k = 0; k < TT::DE; ++k) {
+    for (int q = 0; q < TT::QE; ++q) t->btS[k][q] = (R)((Bq(q, k) + Bq(q, D - 1 - k)) / 2);
+    for (int q = 0; q < TT::QH; ++q) t->gtS[k][q] = (R)((Gq(q, k) + Gq(q, D - 1 - k)) / 2);
+  }
+  for (int k = 0; k < TT::DH; ++k) {
+    for (int q = 0; q < TT::QH; ++q) t->btD[k][q] = (R)((Bq(q, k) - Bq(q, D - 1 - k)) / 2);
+    for (int q = 0; q < TT::QE; ++q) t->gtD[k][q] = (R)((Gq(q, k) - Gq(q, D - 1 - k)) / 2);
+  }
+}
+
 // ue[i] = v[i] + v[N-1-i], uo[i] = v[i] - v[N-1-i] (i < N/2); ue takes the middle entry of an
 // odd line
-template <int N>
-__device__ __forceinline__ void split(const double (&v)[N], double (&ue)[(N + 1) / 2],
-                                      double (&uo)[N / 2]) {
+template <int N, class R>
+__device__ __forceinline__ void split(const R (&v)[N], R (&ue)[(N + 1) / 2], R (&uo)[N / 2]) {
 #pragma unroll
   for (int i = 0; i < N / 2; ++i) {
     ue[i] = v[i] + v[N - 1 - i];
@@ -35,9 +65,9 @@ __device__ __forceinline__ void split(const double (&v)[N], double (&ue)[(N + 1)
 }
 
 // out[o] = S[o] + Dd[o], out[N-1-o] = S[o] - Dd[o]; the middle output of an odd line is S
-template <int N>
-__device__ __forceinline__ void join(const double (&S)[(N + 1) / 2], const double (&Dd)[N / 2],
-                                     double (&out)[N]) {
+template <int N, class R>
+__device__ __forceinline__ void join(const R (&S)[(N + 1) / 2], const R (&Dd)[N / 2],
+                                     R (&out)[N]) {
 #pragma unroll
   for (int o = 0; o < N / 2; ++o) {
     out[o] = S[o] + Dd[o];
@@ -46,26 +76,26 @@ __device__ __forceinline__ void join(const double (&S)[(N + 1) / 2], const doubl
   if constexpr (N % 2 == 1) out[N / 2] = S[N / 2];
 }
 
-template <int N>
-__device__ __forceinline__ double dot(const double (&c)[N], const double (&u)[N]) {
-  double r = c[0] * u[0];
+template <int N, class R>
+__device__ __forceinline__ R dot(const R (&c)[N], const R (&u)[N]) {
+  R r = c[0] * u[0];
 #pragma unroll
   for (int i = 1; i < N; ++i) r = fma(c[i], u[i], r);
   return r;
 }
 
-template <int N>
-__device__ __forceinline__ double dot_acc(const double (&c)[N], const double (&u)[N], double r) {
+template <int N, class R>
+__device__ __forceinline__ R dot_acc(const R (&c)[N], const R (&u)[N], R r) {
 #pragma unroll
   for (int i = 0; i < N; ++i) r = fma(c[i], u[i], r);
   return r;
 }
 
 // forward B: out[q] = sum_d B[q][d] v[d], from v's halves
-template <int D, int Q>
-__device__ __forceinline__ void fwd_b(const TabF64EO<D, Q>& t, const double (&ue)[(D + 1) / 2],
-                                      const double (&uo)[D / 2], double (&out)[Q]) {
-  double S[(Q + 1) / 2], Dd[Q / 2];
+template <class R, int D, int Q>
+__device__ __forceinline__ void fwd_b(const TabEO<R, D, Q>& t, const R (&ue)[(D + 1) / 2],
+                                      const R (&uo)[D / 2], R (&out)[Q]) {
+  R S[(Q + 1) / 2], Dd[Q / 2];
 #pragma unroll
   for (int o = 0; o < (Q + 1) / 2; ++o) S[o] = dot(t.bS[o], ue);
 #pragma unroll
@@ -74,10 +104,10 @@ __device__ __forceinline__ void fwd_b(const TabF64EO<D, Q>& t, const double (&ue
 }
 
 // forward G: out[q] = sum_d G[q][d] v[d]
-template <int D, int Q>
-__device__ __forceinline__ void fwd_g(const TabF64EO<D, Q>& t, const double (&ue)[(D + 1) / 2],
-                                      const double (&uo)[D / 2], double (&out)[Q]) {
-  double S[(Q + 1) / 2], Dd[Q / 2];
+template <class R, int D, int Q>
+__device__ __forceinline__ void fwd_g(const TabEO<R, D, Q>& t, const R (&ue)[(D + 1) / 2],
+                                      const R (&uo)[D / 2], R (&out)[Q]) {
+  R S[(Q + 1) / 2], Dd[Q / 2];
 #pragma unroll
   for (int o = 0; o < (Q + 1) / 2; ++o) S[o] = dot(t.gS[o], uo);
 #pragma unroll
@@ -86,10 +116,10 @@ __device__ __forceinline__ void fwd_g(const TabF64EO<D, Q>& t, const double (&ue
 }
 
 // transposed B: out[d] = sum_q B[q][d] a[q], from a's halves over q
-template <int D, int Q>
-__device__ __forceinline__ void tr_b(const TabF64EO<D, Q>& t, const double (&ae)[(Q + 1) / 2],
-                                     const double (&ao)[Q / 2], double (&out)[D]) {
-  double S[(D + 1) / 2], Dd[D / 2];
+template <class R, int D, int Q>
+__device__ __forceinline__ void tr_b(const TabEO<R, D, Q>& t, const R (&ae)[(Q + 1) / 2],
+                                     const R (&ao)[Q / 2], R (&out)[D]) {
+  R S[(D + 1) / 2], Dd[D / 2];
 #pragma unroll
   for (int k = 0; k < (D + 1) / 2; ++k) S[k] = dot(t.btS[k], ae);
 #pragma unroll
@@ -98,11 +128,11 @@ __device__ __forceinline__ void tr_b(const TabF64EO<D, Q>& t, const double (&ae)
 }
 
 // transposed G of a plus transposed B of b: out[d] = sum_q G[q][d] a[q] + B[q][d] b[q]
-template <int D, int Q>
-__device__ __forceinline__ void tr_gb(const TabF64EO<D, Q>& t, const double (&ae)[(Q + 1) / 2],
-                                      const double (&ao)[Q / 2], const double (&be)[(Q + 1) / 2],
-                                      const double (&bo)[Q / 2], double (&out)[D]) {
-  double S[(D + 1) / 2], Dd[D / 2];
+template <class R, int D, int Q>
+__device__ __forceinline__ void tr_gb(const TabEO<R, D, Q>& t, const R (&ae)[(Q + 1) / 2],
+                                      const R (&ao)[Q / 2], const R (&be)[(Q + 1) / 2],
+                                      const R (&bo)[Q / 2], R (&out)[D]) {
+  R S[(D + 1) / 2], Dd[D / 2];
 #pragma unroll
   for (int k = 0; k < (D + 1) / 2; ++k) S[k] = dot_acc(t.btS[k], be, dot(t.gtS[k], ao));
 #pragma unroll
@@ -111,21 +141,21 @@ __device__ __forceinline__ void tr_gb(const TabF64EO<D, Q>& t, const double (&ae
 }
 
 // ---- x phase: contract i -> qx.  line (j, k); out T1c[j][k*Q + qx], c = (B x, G x)
-template <int D, int Q, int NT, bool DIFF, class L>
-__device__ __forceinline__ void x_phase(const TabF64EO<D, Q>& tab, const double* bufA,
-                                        double* bufB, int nel, int tid) {
+template <int D, int Q, int NT, bool DIFF, class L, class R>
+__device__ __forceinline__ void x_phase(const TabEO<R, D, Q>& tab, const R* bufA,
+                                        R* bufB, int nel, int tid) {
   constexpr int D2 = D * D;
   for (int t = tid; t < nel * D2; t += NT) {
     const int el = t / D2, l = t - el * D2;
     const int j = l / D, k = l - j * D;
-    const double* in = bufA + el * L::SZ_A + l;
-    double v[D];
+    const R* in = bufA + el * L::SZ_A + l;
+    R v[D];
 #pragma unroll
     for (int i = 0; i < D; ++i) v[i] = in[i * L::S_DD];
-    double ue[(D + 1) / 2], uo[D / 2];
+    R ue[(D + 1) / 2], uo[D / 2];
     split<D>(v, ue, uo);
-    double* outb = bufB + el * L::SZ_B + j * L::S_QD + k * Q;
-    double o[Q];
+    R* outb = bufB + el * L::SZ_B + j * L::S_QD + k * Q;
+    R o[Q];
     fwd_b(tab, ue, uo, o);
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) outb[qx] = o[qx];
@@ -139,26 +169,26 @@ __device__ __forceinline__ void x_phase(const TabF64EO<D, Q>& tab, const double*
 
 // ---- y phase: contract j -> qy.  line (k, qx); out T2c[k][qy*Q + qx]
 //      diffusion: c0 = B_y (G_x x), c1 = G_y (B_x x), c2 = B_y (B_x x)
-template <int D, int Q, int NT, bool DIFF, class L>
-__device__ __forceinline__ void y_phase(const TabF64EO<D, Q>& tab, const double* bufB,
-                                        double* bufA, int nel, int tid) {
+template <int D, int Q, int NT, bool DIFF, class L, class R>
+__device__ __forceinline__ void y_phase(const TabEO<R, D, Q>& tab, const R* bufB,
+                                        R* bufA, int nel, int tid) {
   constexpr int QD = Q * D;
   for (int t = tid; t < nel * QD; t += NT) {
     const int el = t / QD, l = t - el * QD;
     const int k = l / Q, qx = l - k * Q;
-    const double* in = bufB + el * L::SZ_B + l;
-    double vb[D];
+    const R* in = bufB + el * L::SZ_B + l;
+    R vb[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) vb[j] = in[j * L::S_QD];
-    double be[(D + 1) / 2], bo[D / 2];
+    R be[(D + 1) / 2], bo[D / 2];
     split<D>(vb, be, bo);
-    double* out = bufA + el * L::SZ_A + k * L::S_QQ + qx;
-    double o[Q];
+    R* out = bufA + el * L::SZ_A + k * L::S_QQ + qx;
+    R o[Q];
     if constexpr (DIFF) {
-      double vg[D];
+      R vg[D];
 #pragma unroll
       for (int j = 0; j < D; ++j) vg[j] = in[D * L::S_QD + j * L::S_QD];
-      double ge[(D + 1) / 2], go[D / 2];
+      R ge[(D + 1) / 2], go[D / 2];
       split<D>(vg, ge, go);
       fwd_b(tab, ge, go, o);
 #pragma unroll
@@ -178,17 +208,16 @@ __device__ __forceinline__ void y_phase(const TabF64EO<D, Q>& tab, const double*
 }
 
 // D times g at one point, D symmetric with entries (xx, xy, xz, yy, yz, zz)
-__device__ __forceinline__ void dmul(const double (&c)[6], double g0, double g1, double g2,
-                                     double& v0, double& v1, double& v2) {
+template <class R>
+__device__ __forceinline__ void dmul(const R (&c)[6], R g0, R g1, R g2, R& v0, R& v1, R& v2) {
   v0 = fma(c[2], g2, fma(c[1], g1, c[0] * g0));
   v1 = fma(c[4], g2, fma(c[3], g1, c[1] * g0));
   v2 = fma(c[5], g2, fma(c[4], g1, c[2] * g0));
 }
 
 // r[i] (+)= c[i] s for the NA accumulators; the first pair initialises them
-template <int NA, int NC>
-__device__ __forceinline__ void acc_col(double (&r)[NA], const double (&c)[NA][NC], int q,
-                                        double s, bool first) {
+template <int NA, int NC, class R>
+__device__ __forceinline__ void acc_col(R (&r)[NA], const R (&c)[NA][NC], int q, R s, bool first) {
 #pragma unroll
   for (int k = 0; k < NA; ++k) r[k] = first ? c[k][q] * s : fma(c[k][q], s, r[k]);
 }
@@ -197,21 +226,21 @@ __device__ __forceinline__ void acc_col(double (&r)[NA], const double (&c)[NA][N
 //      The quadrature points qz and Q-1-qz are taken together: the forward contraction gives both
 //      from one pair of half-size sums, and the sum and difference of their pointwise products
 //      are the even and odd parts the transposed contraction needs.
-template <int D, int Q, int NT, bool DIFF, class L>
-__device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double* bufA,
-                                        double* bufB, const double* __restrict__ qd, int64_t e0,
+template <int D, int Q, int NT, bool DIFF, class L, class R>
+__device__ __forceinline__ void z_phase(const TabEO<R, D, Q>& tab, const R* bufA,
+                                        R* bufB, const R* __restrict__ qd, int64_t e0,
                                         int nel, int tid) {
   constexpr int Q2 = Q * Q, DE = (D + 1) / 2, DH = D / 2, QH = Q / 2;
   constexpr int NQD = DIFF ? 6 : 1;
   for (int t = tid; t < nel * Q2; t += NT) {
     const int el = t / Q2, l = t - el * Q2;
     const int qy = l / Q, qx = l - qy * Q;
-    const double* in = bufA + el * L::SZ_A + l;
-    const double* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
-    double* out = bufB + el * L::SZ_B + qy * L::S_QD + qx;
+    const R* in = bufA + el * L::SZ_A + l;
+    const R* qe = qd + (e0 + el) * (int64_t)(NQD * Q * Q2) + l;
+    R* out = bufB + el * L::SZ_B + qy * L::S_QD + qx;
     if constexpr (DIFF) {
-      double c[D];
-      double e0_[DE], o0[DH], e1[DE], o1[DH], e2[DE], o2[DH];
+      R c[D];
+      R e0_[DE], o0[DH], e1[DE], o1[DH], e2[DE], o2[DH];
 #pragma unroll
       for (int k = 0; k < D; ++k) c[k] = in[k * L::S_QQ];
       split<D>(c, e0_, o0);
@@ -222,20 +251,20 @@ __device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double*
       for (int k = 0; k < D; ++k) c[k] = in[2 * D * L::S_QQ + k * L::S_QQ];
       split<D>(c, e2, o2);
       // transposed accumulators: B^T of v0 and v1, G^T of v2
-      double S0[DE], D0[DH], S1[DE], D1[DH], S2[DE], D2[DH];
+      R S0[DE], D0[DH], S1[DE], D1[DH], S2[DE], D2[DH];
 #pragma unroll
       for (int q = 0; q < QH; ++q) {
         const int qh = Q - 1 - q;
-        double dl[6], dh[6];
+        R dl[6], dh[6];
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) {
           dl[cc] = __ldcs(qe + (q * 6 + cc) * Q2);
           dh[cc] = __ldcs(qe + (qh * 6 + cc) * Q2);
         }
-        const double s0 = dot(tab.bS[q], e0_), d0 = dot(tab.bD[q], o0);
-        const double s1 = dot(tab.bS[q], e1), d1 = dot(tab.bD[q], o1);
-        const double s2 = dot(tab.gS[q], o2), d2 = dot(tab.gD[q], e2);
-        double v0l, v1l, v2l, v0h, v1h, v2h;
+        const R s0 = dot(tab.bS[q], e0_), d0 = dot(tab.bD[q], o0);
+        const R s1 = dot(tab.bS[q], e1), d1 = dot(tab.bD[q], o1);
+        const R s2 = dot(tab.gS[q], o2), d2 = dot(tab.gD[q], e2);
+        R v0l, v1l, v2l, v0h, v1h, v2h;
         dmul(dl, s0 + d0, s1 + d1, s2 + d2, v0l, v1l, v2l);
         dmul(dh, s0 - d0, s1 - d1, s2 - d2, v0h, v1h, v2h);
         const bool first = (q == 0);
@@ -247,16 +276,16 @@ __device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double*
         acc_col(D2, tab.gtD, q, v2l + v2h, first);
       }
       if constexpr (Q % 2 == 1) {  // the middle point: even part only (no odd partner)
-        double dm[6];
+        R dm[6];
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) dm[cc] = __ldcs(qe + (QH * 6 + cc) * Q2);
-        double v0, v1, v2;
+        R v0, v1, v2;
         dmul(dm, dot(tab.bS[QH], e0_), dot(tab.bS[QH], e1), dot(tab.gS[QH], o2), v0, v1, v2);
         acc_col(S0, tab.btS, QH, v0, false);
         acc_col(S1, tab.btS, QH, v1, false);
         acc_col(D2, tab.gtD, QH, v2, false);
       }
-      double w[D];
+      R w[D];
       join<D>(S0, D0, w);
 #pragma unroll
       for (int k = 0; k < D; ++k) out[k * Q] = w[k];
@@ -267,24 +296,24 @@ __device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double*
 #pragma unroll
       for (int k = 0; k < D; ++k) out[2 * Q * L::S_QD + k * Q] = w[k];
     } else {
-      double c[D], ce[DE], co[DH];
+      R c[D], ce[DE], co[DH];
 #pragma unroll
       for (int k = 0; k < D; ++k) c[k] = in[k * L::S_QQ];
       split<D>(c, ce, co);
-      double S[DE], Dd[DH];
+      R S[DE], Dd[DH];
 #pragma unroll
       for (int q = 0; q < QH; ++q) {
-        const double dl = __ldcs(qe + q * Q2), dh = __ldcs(qe + (Q - 1 - q) * Q2);
-        const double s = dot(tab.bS[q], ce), d = dot(tab.bD[q], co);
-        const double vl = dl * (s + d), vh = dh * (s - d);
+        const R dl = __ldcs(qe + q * Q2), dh = __ldcs(qe + (Q - 1 - q) * Q2);
+        const R s = dot(tab.bS[q], ce), d = dot(tab.bD[q], co);
+        const R vl = dl * (s + d), vh = dh * (s - d);
         acc_col(S, tab.btS, q, vl + vh, q == 0);
         acc_col(Dd, tab.btD, q, vl - vh, q == 0);
       }
       if constexpr (Q % 2 == 1) {
-        const double v = __ldcs(qe + QH * Q2) * dot(tab.bS[QH], ce);
+        const R v = __ldcs(qe + QH * Q2) * dot(tab.bS[QH], ce);
         acc_col(S, tab.btS, QH, v, false);
       }
-      double w[D];
+      R w[D];
       join<D>(S, Dd, w);
 #pragma unroll
       for (int k = 0; k < D; ++k) out[k * Q] = w[k];
@@ -294,16 +323,16 @@ __device__ __forceinline__ void z_phase(const TabF64EO<D, Q>& tab, const double*
 
 // ---- y^T phase: contract qy -> j.  line (k, qx); out S5c[qx][j*D + k]
 //      diffusion: c0 (-> G_x^T) = B_y^T s0, c1 (-> B_x^T) = G_y^T s1 + B_y^T s2
-template <int D, int Q, int NT, bool DIFF, class L>
-__device__ __forceinline__ void yt_phase(const TabF64EO<D, Q>& tab, const double* bufB,
-                                         double* bufA, int nel, int tid) {
+template <int D, int Q, int NT, bool DIFF, class L, class R>
+__device__ __forceinline__ void yt_phase(const TabEO<R, D, Q>& tab, const R* bufB,
+                                         R* bufA, int nel, int tid) {
   constexpr int QD = Q * D, QE = (Q + 1) / 2, QH = Q / 2;
   for (int t = tid; t < nel * QD; t += NT) {
     const int el = t / QD, l = t - el * QD;
     const int k = l / Q, qx = l - k * Q;
-    const double* in = bufB + el * L::SZ_B + l;
-    double* out = bufA + el * L::SZ_A + qx * L::S_DD + k;
-    double a[Q], ae[QE], ao[QH], r[D];
+    const R* in = bufB + el * L::SZ_B + l;
+    R* out = bufA + el * L::SZ_A + qx * L::S_DD + k;
+    R a[Q], ae[QE], ao[QH], r[D];
 #pragma unroll
     for (int qy = 0; qy < Q; ++qy) a[qy] = in[qy * L::S_QD];
     split<Q>(a, ae, ao);
@@ -311,7 +340,7 @@ __device__ __forceinline__ void yt_phase(const TabF64EO<D, Q>& tab, const double
 #pragma unroll
     for (int j = 0; j < D; ++j) out[j * D] = r[j];
     if constexpr (DIFF) {
-      double be[QE], bo[QH];
+      R be[QE], bo[QH];
 #pragma unroll
       for (int qy = 0; qy < Q; ++qy) a[qy] = in[Q * L::S_QD + qy * L::S_QD];
       split<Q>(a, ae, ao);
@@ -327,20 +356,20 @@ __device__ __forceinline__ void yt_phase(const TabF64EO<D, Q>& tab, const double
 
 // ---- x^T phase: contract qx -> i.  line (j, k); out Ye[i + D j + D^2 k]
 //      diffusion: G_x^T of the first array plus B_x^T of the second; mass: B_x^T
-template <int D, int Q, int NT, bool DIFF, class L>
-__device__ __forceinline__ void xt_phase(const TabF64EO<D, Q>& tab, const double* bufA,
-                                         double* bufB, int nel, int tid) {
+template <int D, int Q, int NT, bool DIFF, class L, class R>
+__device__ __forceinline__ void xt_phase(const TabEO<R, D, Q>& tab, const R* bufA,
+                                         R* bufB, int nel, int tid) {
   constexpr int D2 = D * D, QE = (Q + 1) / 2, QH = Q / 2;
   for (int t = tid; t < nel * D2; t += NT) {
     const int el = t / D2, l = t - el * D2;
     const int j = l / D, k = l - j * D;
-    const double* in = bufA + el * L::SZ_A + l;
-    double a[Q], ae[QE], ao[QH], r[D];
+    const R* in = bufA + el * L::SZ_A + l;
+    R a[Q], ae[QE], ao[QH], r[D];
 #pragma unroll
     for (int qx = 0; qx < Q; ++qx) a[qx] = in[qx * L::S_DD];
     split<Q>(a, ae, ao);
     if constexpr (DIFF) {
-      double be[QE], bo[QH];
+      R be[QE], bo[QH];
 #pragma unroll
       for (int qx = 0; qx < Q; ++qx) a[qx] = in[Q * L::S_DD + qx * L::S_DD];
       split<Q>(a, be, bo);
@@ -348,7 +377,7 @@ __device__ __forceinline__ void xt_phase(const TabF64EO<D, Q>& tab, const double
     } else {
       tr_b(tab, ae, ao, r);
     }
-    double* out = bufB + el * L::SZ_B + j * D + k * D2;
+    R* out = bufB + el * L::SZ_B + j * D + k * D2;
 #pragma unroll
     for (int i = 0; i < D; ++i) out[i] = r[i];
   }

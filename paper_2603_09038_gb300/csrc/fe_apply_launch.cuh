@@ -130,41 +130,10 @@ inline void fill_tab(const Basis1D& b, TabF64<D, Q>* t) {
   }
 }
 
-// The even-odd halves of TabF64EO, formed in long double from the FP64 tables.
-template <int D, int Q>
-inline void fill_tab(const Basis1D& b, TabF64EO<D, Q>* t) {
-  using L = long double;
-  using TT = TabF64EO<D, Q>;
-  for (int i = 0; i < Q * D; ++i) {
-    t->B[i] = b.B[i];
-    t->G[i] = b.G[i];
-  }
-  auto Bq = [&](int q, int d) { return (L)b.B[q * D + d]; };
-  auto Gq = [&](int q, int d) { return (L)b.G[q * D + d]; };
-  for (int o = 0; o < TT::QE; ++o) {
-    for (int i = 0; i < TT::DE; ++i) t->bS[o][i] = (double)((Bq(o, i) + Bq(Q - 1 - o, i)) / 2);
-    for (int i = 0; i < TT::DH; ++i) t->gS[o][i] = (double)((Gq(o, i) + Gq(Q - 1 - o, i)) / 2);
-  }
-  for (int o = 0; o < TT::QH; ++o) {
-    for (int i = 0; i < TT::DH; ++i) t->bD[o][i] = (double)((Bq(o, i) - Bq(Q - 1 - o, i)) / 2);
-    for (int i = 0; i < TT::DE; ++i) t->gD[o][i] = (double)((Gq(o, i) - Gq(Q - 1 - o, i)) / 2);
-  }
-  for (int k = 0; k < TT::DE; ++k) {
-    for (int q = 0; q < TT::QE; ++q) t->btS[k][q] = (double)((Bq(q, k) + Bq(q, D - 1 - k)) / 2);
-    for (int q = 0; q < TT::QH; ++q) t->gtS[k][q] = (double)((Gq(q, k) + Gq(q, D - 1 - k)) / 2);
-  }
-  for (int k = 0; k < TT::DH; ++k) {
-    for (int q = 0; q < TT::QH; ++q) t->btD[k][q] = (double)((Bq(q, k) - Bq(q, D - 1 - k)) / 2);
-    for (int q = 0; q < TT::QE; ++q) t->gtD[k][q] = (double)((Gq(q, k) - Gq(q, D - 1 - k)) / 2);
-  }
-}
-
-template <int D, int Q>
-inline void fill_tab(const Basis1D& b, TabF32<D, Q>* t) {
-  for (int i = 0; i < Q * D; ++i) {
-    t->B[i] = (float)b.B[i];
-    t->G[i] = (float)b.G[i];
-  }
+// The tables and their even-odd halves (eo::fill).
+template <class R, int D, int Q>
+inline void fill_tab(const Basis1D& b, TabEO<R, D, Q>* t) {
+  eo::fill(b.B, b.G, t);
 }
 
 template <int D, int Q>
@@ -222,7 +191,7 @@ int launch_kernel(const ApplyArgs& a, cudaStream_t s) {
   });
   if (attr_err != cudaSuccess) return cuda_error(attr_err, "cudaFuncSetAttribute(apply)");
   typename Ar::template Tab<D, Q> tab;
-  fill_tab<D, Q>(*a.basis, &tab);
+  fill_tab(*a.basis, &tab);
   const int64_t nblk = (a.ne + NE - 1) / NE;
   if (a.blocks) *a.blocks = nblk;
   if (nblk == 0 || a.query_only) return FE_OK;
@@ -410,14 +379,14 @@ __global__ void __launch_bounds__(NT, MINB) k_pa_apply_multi(const MultiGroups g
 template <class Base>
 void fill_multi_tabs(const Basis1D* const* basis, MultiTabs<Base>* t) {
   std::memset(t, 0, sizeof(*t));
-  if (basis[0]) fill_tab<2, 3>(*basis[0], &t->t1);
-  if (basis[1]) fill_tab<3, 4>(*basis[1], &t->t2);
-  if (basis[2]) fill_tab<4, 5>(*basis[2], &t->t3);
-  if (basis[3]) fill_tab<5, 6>(*basis[3], &t->t4);
-  if (basis[4]) fill_tab<6, 7>(*basis[4], &t->t5);
-  if (basis[5]) fill_tab<7, 8>(*basis[5], &t->t6);
-  if (basis[6]) fill_tab<8, 9>(*basis[6], &t->t7);
-  if (basis[7]) fill_tab<9, 10>(*basis[7], &t->t8);
+  if (basis[0]) fill_tab(*basis[0], &t->t1);
+  if (basis[1]) fill_tab(*basis[1], &t->t2);
+  if (basis[2]) fill_tab(*basis[2], &t->t3);
+  if (basis[3]) fill_tab(*basis[3], &t->t4);
+  if (basis[4]) fill_tab(*basis[4], &t->t5);
+  if (basis[5]) fill_tab(*basis[5], &t->t6);
+  if (basis[6]) fill_tab(*basis[6], &t->t7);
+  if (basis[7]) fill_tab(*basis[7], &t->t8);
 }
 
 // One persistent launch over the groups of g for nrhs right-hand sides x + r ldx -> y + r ldy (y

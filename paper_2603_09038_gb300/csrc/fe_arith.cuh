@@ -40,7 +40,7 @@ struct TabF64 {
   double G[Q * D];
 };
 
-// FP64 tables with their even-odd halves.  The 1D tables are symmetric under reversal of both
+// Tables with their even-odd halves (FP64, or FP32 for the FP32 policy).  The 1D tables are symmetric under reversal of both
 // indices (GLL nodes and Gauss points are symmetric about the element centre):
 // B[Q-1-q][D-1-d] = B[q][d] and G[Q-1-q][D-1-d] = -G[q][d].  So a contraction out = M x of a
 // line splits into half-size sums over x's even and odd parts
@@ -49,16 +49,20 @@ struct TabF64 {
 // S[o] = sum_i (M[o][i] + M[NO-1-o][i]) / 2 u_S[i], Dd[o] = sum_i (M[o][i] - M[NO-1-o][i]) / 2 u_D[i],
 // where u_S, u_D = ue, uo for the symmetric B and uo, ue for the antisymmetric G.  Forward
 // tables are [output q][input d], transposed ones [output d][input q].
-template <int D, int Q>
-struct TabF64EO {
+template <class R, int D, int Q>
+struct TabEO {
   static constexpr int DE = (D + 1) / 2, DH = D / 2, QE = (Q + 1) / 2, QH = Q / 2;
-  double B[Q * D];
-  double G[Q * D];
-  double bS[QE][DE], bD[QH][DH];    // B forward:  S on ue, Dd on uo
-  double gS[QE][DH], gD[QH][DE];    // G forward:  S on uo, Dd on ue
-  double btS[DE][QE], btD[DH][QH];  // B^T:        S on ue, Dd on uo (over q)
-  double gtS[DE][QH], gtD[DH][QE];  // G^T:        S on uo, Dd on ue (over q)
+  R B[Q * D];
+  R G[Q * D];
+  R bS[QE][DE], bD[QH][DH];    // B forward:  S on ue, Dd on uo
+  R gS[QE][DH], gD[QH][DE];    // G forward:  S on uo, Dd on ue
+  R btS[DE][QE], btD[DH][QH];  // B^T:        S on ue, Dd on uo (over q)
+  R gtS[DE][QH], gtD[DH][QE];  // G^T:        S on uo, Dd on ue (over q)
 };
+template <int D, int Q>
+using TabF64EO = TabEO<double, D, Q>;
+template <int D, int Q>
+using TabF32EO = TabEO<float, D, Q>;
 
 // Float-float tables; rB/rG = max_q sum_d |.| (forward contractions), cB/cG = max_d sum_q |.|
 // (transposed contractions), each rounded up.
@@ -67,12 +71,6 @@ struct TabF32x2 {
   float Bh[Q * D], Bl[Q * D];
   float Gh[Q * D], Gl[Q * D];
   float rB, rG, cB, cG;
-};
-
-template <int D, int Q>
-struct TabF32 {
-  float B[Q * D];
-  float G[Q * D];
 };
 
 // ---------------------------------------------------------------------------- policies
@@ -260,14 +258,14 @@ using ArF32x2 = ArF32x2T<true, false>;
 struct ArF32 {
   static constexpr bool kAnchored = false;
   static constexpr bool kScaled = false;
-  static constexpr bool kEvenOdd = false;
+  static constexpr bool kEvenOdd = true;  // even-odd contractions (fe_apply_eo.cuh)
   static constexpr bool kPrefetchQd = true;  // bulk L2 prefetch of the block's quadrature data
   using QdT = float;
   using T = float;
   using Acc = float;
   using Sig = float;
   template <int D, int Q>
-  using Tab = TabF32<D, Q>;
+  using Tab = TabF32EO<D, Q>;
 
   static __device__ __forceinline__ T zero() { return 0.0f; }
   static __device__ __forceinline__ T from_vec(double v) { return f2_from_f64(v).h; }

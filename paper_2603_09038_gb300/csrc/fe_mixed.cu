@@ -14,13 +14,16 @@
 // reference gradient (the sum-factorised B/G contractions of Eq. (2), as in the diffusion apply),
 // applies M_q, and the L2 test basis transposed; and the velocity through the L2 basis, M_q^T,
 // and the transposed reference gradient, scatter-added into the H1 vector.  FP64 FMA throughout
-// (on GB300 the FP64 tensor instruction is slower per flop than FP64 FMA, so no DMMA path).
+// (on GB300 the FP64 tensor instruction is slower per flop than FP64 FMA, so no DMMA path); every
+// 1D contraction on the even and odd halves of its line (the tables' reversal symmetry, as in the
+// diffusion apply: fe_apply_eo.cuh), which cuts the FP64 instructions that bound the kernel.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <mutex>
 #include <string>
 
+#include "fe_apply_eo.cuh"
 #include "fe_internal.h"
 
 struct fe_mixed {
@@ -42,9 +45,11 @@ constexpr int kSmem = 96 * 1024;       // shared-memory budget per block
 __host__ __device__ constexpr int oddp(int n) { return (n % 2 == 0) ? n + 1 : n; }
 __host__ __device__ constexpr int cmx(int a, int b) { return a > b ? a : b; }
 
+// H1 tables (B_h, G_h) and the L2 table (B_l, its G unused), with their even-odd halves
 template <int DH, int DL, int Q>
 struct MixedTab {
-  double Bh[Q * DH], Gh[Q * DH], Bl[Q * DL];
+  TabEO<double, DH, Q> h;
+  TabEO<double, DL, Q> l;
 };
 
 // Shared-memory layout per element (doubles).  Every array stores the summed index of the next
@@ -78,6 +83,8 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
   constexpr int NE = L::NE;
   constexpr int DH2 = DH * DH, DH3 = DH2 * DH, DL2 = DL * DL, DL3 = DL2 * DL, Q2 = Q * Q;
   constexpr int hDD = L::hDD, lDD = L::lDD, hQD = L::hQD, lQD = L::lQD, QQ = L::QQ;
+  constexpr int DHE = (DH + 1) / 2, DHH = DH / 2, DLE = (DL + 1) / 2, DLH = DL / 2;
+  constexpr int QE = (Q + 1) / 2, QH = Q / 2;
   extern __shared__ __align__(16) double sm[];
   double* bufA = sm;
   double* bufB = sm + NE * L::SA;
@@ -107,21 +114,17 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
     for (int t = tid; t < nel * DH2; t += kNT) {
       const int el = t / DH2, l = t - el * DH2, j = l / DH, k = l - j * DH;
       const double* in = bufA + el * L::SA + l;
-      double v[DH];
+      double v[DH], ve[DHE], vo[DHH], o[Q];
 #pragma unroll
       for (int i = 0; i < DH; ++i) v[i] = in[i * hDD];
+      eo::split<DH>(v, ve, vo);
       double* out = bufB + el * L::SB + j * hQD + k * Q;
+      eo::fwd_b(tab.h, ve, vo, o);
 #pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        double sb = 0.0, sg = 0.0;
+      for (int qx = 0; qx < Q; ++qx) out[qx] = o[qx];
+      eo::fwd_g(tab.h, ve, vo, o);
 #pragma unroll
-        for (int i = 0; i < DH; ++i) {
-          sb = fma(tab.Bh[qx * DH + i], v[i], sb);
-          sg = fma(tab.Gh[qx * DH + i], v[i], sg);
-        }
-        out[qx] = sb;
-        out[DH * hQD + qx] = sg;
-      }
+      for (int qx = 0; qx < Q; ++qx) out[DH * hQD + qx] = o[qx];
     }
   }
   if constexpr (DIV) {
@@ -129,17 +132,14 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
       const int el = t / (3 * DL2), r = t - el * 3 * DL2, c = r / DL2, l = r - c * DL2;
       const int j = l / DL, k = l - j * DL;
       const double* in = bufA + el * L::SA + L::A_U + c * DL * lDD + l;
-      double v[DL];
+      double v[DL], ve[DLE], vo[DLH], o[Q];
 #pragma unroll
       for (int i = 0; i < DL; ++i) v[i] = in[i * lDD];
+      eo::split<DL>(v, ve, vo);
+      eo::fwd_b(tab.l, ve, vo, o);
       double* out = bufB + el * L::SB + L::B_TL + (c * DL + j) * lQD + k * Q;
 #pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < DL; ++i) s = fma(tab.Bl[qx * DL + i], v[i], s);
-        out[qx] = s;
-      }
+      for (int qx = 0; qx < Q; ++qx) out[qx] = o[qx];
     }
   }
   __syncthreads();
@@ -150,26 +150,24 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
     for (int t = tid; t < nel * DH * Q; t += kNT) {
       const int el = t / (DH * Q), l = t - el * DH * Q, k = l / Q, qx = l - k * Q;
       const double* in = bufB + el * L::SB + l;
-      double vb[DH], vg[DH];
+      double vb[DH], vg[DH], be[DHE], bo[DHH], ge[DHE], go[DHH], o[Q];
 #pragma unroll
       for (int j = 0; j < DH; ++j) {
         vb[j] = in[j * hQD];
         vg[j] = in[(DH + j) * hQD];
       }
+      eo::split<DH>(vb, be, bo);
+      eo::split<DH>(vg, ge, go);
       double* out = bufA + el * L::SA + k * QQ + qx;
+      eo::fwd_b(tab.h, ge, go, o);
 #pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int qy = 0; qy < Q; ++qy) out[qy * Q] = o[qy];
+      eo::fwd_g(tab.h, be, bo, o);
 #pragma unroll
-        for (int j = 0; j < DH; ++j) {
-          a0 = fma(tab.Bh[qy * DH + j], vg[j], a0);
-          a1 = fma(tab.Gh[qy * DH + j], vb[j], a1);
-          a2 = fma(tab.Bh[qy * DH + j], vb[j], a2);
-        }
-        out[qy * Q] = a0;
-        out[DH * QQ + qy * Q] = a1;
-        out[2 * DH * QQ + qy * Q] = a2;
-      }
+      for (int qy = 0; qy < Q; ++qy) out[DH * QQ + qy * Q] = o[qy];
+      eo::fwd_b(tab.h, be, bo, o);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) out[2 * DH * QQ + qy * Q] = o[qy];
     }
   }
   if constexpr (DIV) {
@@ -177,102 +175,129 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
       const int el = t / (3 * DL * Q), r = t - el * 3 * DL * Q, c = r / (DL * Q);
       const int l = r - c * DL * Q, k = l / Q, qx = l - k * Q;
       const double* in = bufB + el * L::SB + L::B_TL + c * DL * lQD + l;
-      double v[DL];
+      double v[DL], ve[DLE], vo[DLH], o[Q];
 #pragma unroll
       for (int j = 0; j < DL; ++j) v[j] = in[j * lQD];
+      eo::split<DL>(v, ve, vo);
+      eo::fwd_b(tab.l, ve, vo, o);
       double* out = bufA + el * L::SA + L::A_YL + (c * DL + k) * QQ + qx;
 #pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < DL; ++j) s = fma(tab.Bl[qy * DL + j], v[j], s);
-        out[qy * Q] = s;
-      }
+      for (int qy = 0; qy < Q; ++qy) out[qy * Q] = o[qy];
     }
   }
   __syncthreads();
 
   // ---- z phase, one (qy, qx) column per thread: the z contractions forward, M_q (gradient) and
-  //      M_q^T (divergence) at every qz, and the transposed z contractions, in registers
+  //      M_q^T (divergence) at every qz, and the transposed z contractions, in registers.  The
+  //      points qz and Q-1-qz are taken together (even-odd halves, as in the diffusion apply).
   for (int t = tid; t < nel * Q2; t += kNT) {
     const int el = t / Q2, l = t - el * Q2, qy = l / Q, qx = l - qy * Q;
     const int ls = qy * Q + qx;  // (qy, qx) in the padded slabs (same as l: QQ slabs)
     const double* qe = qd + (e0 + el) * (int64_t)(9 * Q * Q2) + l;
-    double hin[3][DH], lin[3][DL];
-    double accL[3][DL], accH[3][DH];
+    // gradient: H1 inputs' halves, L2 transposed accumulators (S on even, D on odd parts)
+    double he[3][DHE], ho[3][DHH], SL[3][DLE], DLa[3][DLH];
+    // divergence: L2 inputs' halves, H1 transposed accumulators (G^T for component 2)
+    double le[3][DLE], lo[3][DLH], SH[3][DHE], DHa[3][DHH];
     if constexpr (GRAD) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        double v[DH];
 #pragma unroll
-        for (int k = 0; k < DH; ++k) hin[c][k] = bufA[el * L::SA + (c * DH + k) * QQ + ls];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < DL; ++k) accL[c][k] = 0.0;
+        for (int k = 0; k < DH; ++k) v[k] = bufA[el * L::SA + (c * DH + k) * QQ + ls];
+        eo::split<DH>(v, he[c], ho[c]);
+      }
     }
     if constexpr (DIV) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        double v[DL];
 #pragma unroll
-        for (int k = 0; k < DL; ++k) lin[c][k] = bufA[el * L::SA + L::A_YL + (c * DL + k) * QQ + ls];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < DH; ++k) accH[c][k] = 0.0;
+        for (int k = 0; k < DL; ++k) v[k] = bufA[el * L::SA + L::A_YL + (c * DL + k) * QQ + ls];
+        eo::split<DL>(v, le[c], lo[c]);
+      }
     }
 #pragma unroll
-    for (int qz = 0; qz < Q; ++qz) {
-      double M[9];
+    for (int q = 0; q < QH; ++q) {
+      const int qh = Q - 1 - q;
+      double Ml[9], Mh[9];
 #pragma unroll
-      for (int m = 0; m < 9; ++m) M[m] = __ldcs(&qe[(qz * 9 + m) * Q2]);
+      for (int m = 0; m < 9; ++m) {
+        Ml[m] = __ldcs(&qe[(q * 9 + m) * Q2]);
+        Mh[m] = __ldcs(&qe[(qh * 9 + m) * Q2]);
+      }
+      const bool first = (q == 0);
       if constexpr (GRAD) {
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
-#pragma unroll
-        for (int k = 0; k < DH; ++k) {
-          g0 = fma(tab.Bh[qz * DH + k], hin[0][k], g0);
-          g1 = fma(tab.Bh[qz * DH + k], hin[1][k], g1);
-          g2 = fma(tab.Gh[qz * DH + k], hin[2][k], g2);
-        }
+        const double s0 = eo::dot(tab.h.bS[q], he[0]), d0 = eo::dot(tab.h.bD[q], ho[0]);
+        const double s1 = eo::dot(tab.h.bS[q], he[1]), d1 = eo::dot(tab.h.bD[q], ho[1]);
+        const double s2 = eo::dot(tab.h.gS[q], ho[2]), d2 = eo::dot(tab.h.gD[q], he[2]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double vc = fma(M[3 * c + 2], g2, fma(M[3 * c + 1], g1, M[3 * c] * g0));
-#pragma unroll
-          for (int k = 0; k < DL; ++k) accL[c][k] = fma(tab.Bl[qz * DL + k], vc, accL[c][k]);
+          const double vl = fma(Ml[3 * c + 2], s2 + d2, fma(Ml[3 * c + 1], s1 + d1, Ml[3 * c] * (s0 + d0)));
+          const double vh = fma(Mh[3 * c + 2], s2 - d2, fma(Mh[3 * c + 1], s1 - d1, Mh[3 * c] * (s0 - d0)));
+          eo::acc_col(SL[c], tab.l.btS, q, vl + vh, first);
+          eo::acc_col(DLa[c], tab.l.btD, q, vl - vh, first);
         }
       }
       if constexpr (DIV) {
-        double w[3];
-        double uc[3];
+        double ul[3], uh[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          double s = 0.0;
-#pragma unroll
-          for (int k = 0; k < DL; ++k) s = fma(tab.Bl[qz * DL + k], lin[c][k], s);
-          uc[c] = s;
+          const double s = eo::dot(tab.l.bS[q], le[c]), d = eo::dot(tab.l.bD[q], lo[c]);
+          ul[c] = s + d;
+          uh[c] = s - d;
         }
+        double wl[3], wh[3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) w[r] = fma(M[6 + r], uc[2], fma(M[3 + r], uc[1], M[r] * uc[0]));
-#pragma unroll
-        for (int k = 0; k < DH; ++k) {
-          accH[0][k] = fma(tab.Bh[qz * DH + k], w[0], accH[0][k]);
-          accH[1][k] = fma(tab.Bh[qz * DH + k], w[1], accH[1][k]);
-          accH[2][k] = fma(tab.Gh[qz * DH + k], w[2], accH[2][k]);
+        for (int r = 0; r < 3; ++r) {
+          wl[r] = fma(Ml[6 + r], ul[2], fma(Ml[3 + r], ul[1], Ml[r] * ul[0]));
+          wh[r] = fma(Mh[6 + r], uh[2], fma(Mh[3 + r], uh[1], Mh[r] * uh[0]));
         }
+        eo::acc_col(SH[0], tab.h.btS, q, wl[0] + wh[0], first);
+        eo::acc_col(DHa[0], tab.h.btD, q, wl[0] - wh[0], first);
+        eo::acc_col(SH[1], tab.h.btS, q, wl[1] + wh[1], first);
+        eo::acc_col(DHa[1], tab.h.btD, q, wl[1] - wh[1], first);
+        eo::acc_col(SH[2], tab.h.gtS, q, wl[2] - wh[2], first);
+        eo::acc_col(DHa[2], tab.h.gtD, q, wl[2] + wh[2], first);
+      }
+    }
+    if constexpr (Q % 2 == 1) {  // the middle point: even parts only
+      double M[9];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) M[m] = __ldcs(&qe[(QH * 9 + m) * Q2]);
+      if constexpr (GRAD) {
+        const double g0 = eo::dot(tab.h.bS[QH], he[0]), g1 = eo::dot(tab.h.bS[QH], he[1]);
+        const double g2 = eo::dot(tab.h.gS[QH], ho[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          eo::acc_col(SL[c], tab.l.btS, QH, fma(M[3 * c + 2], g2, fma(M[3 * c + 1], g1, M[3 * c] * g0)), false);
+      }
+      if constexpr (DIV) {
+        double u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = eo::dot(tab.l.bS[QH], le[c]);
+        eo::acc_col(SH[0], tab.h.btS, QH, fma(M[6], u[2], fma(M[3], u[1], M[0] * u[0])), false);
+        eo::acc_col(SH[1], tab.h.btS, QH, fma(M[7], u[2], fma(M[4], u[1], M[1] * u[0])), false);
+        eo::acc_col(DHa[2], tab.h.gtD, QH, fma(M[8], u[2], fma(M[5], u[1], M[2] * u[0])), false);
       }
     }
     if constexpr (GRAD) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        double w[DL];
+        eo::join<DL>(SL[c], DLa[c], w);
 #pragma unroll
         for (int k = 0; k < DL; ++k)
-          bufB[el * L::SB + L::B_ZL + (c * Q + qy) * lQD + k * Q + qx] = accL[c][k];
+          bufB[el * L::SB + L::B_ZL + (c * Q + qy) * lQD + k * Q + qx] = w[k];
+      }
     }
     if constexpr (DIV) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
+      for (int c = 0; c < 3; ++c) {
+        double w[DH];
+        eo::join<DH>(SH[c], DHa[c], w);
 #pragma unroll
-        for (int k = 0; k < DH; ++k)
-          bufB[el * L::SB + (c * Q + qy) * hQD + k * Q + qx] = accH[c][k];
+        for (int k = 0; k < DH; ++k) bufB[el * L::SB + (c * Q + qy) * hQD + k * Q + qx] = w[k];
+      }
     }
   }
   __syncthreads();
@@ -283,24 +308,23 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
     for (int t = tid; t < nel * DH * Q; t += kNT) {
       const int el = t / (DH * Q), l = t - el * DH * Q, k = l / Q, qx = l - k * Q;
       const double* in = bufB + el * L::SB + l;
-      double r0[DH], r1[DH];
+      double a[Q], ae[QE], ao[QH], be[QE], bo[QH], r[DH];
 #pragma unroll
-      for (int j = 0; j < DH; ++j) r0[j] = r1[j] = 0.0;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        const double a0 = in[qy * hQD], a1 = in[(Q + qy) * hQD], a2 = in[(2 * Q + qy) * hQD];
-#pragma unroll
-        for (int j = 0; j < DH; ++j) {
-          r0[j] = fma(tab.Bh[qy * DH + j], a0, r0[j]);
-          r1[j] = fma(tab.Gh[qy * DH + j], a1, fma(tab.Bh[qy * DH + j], a2, r1[j]));
-        }
-      }
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[qy * hQD];
+      eo::split<Q>(a, ae, ao);
       double* out = bufA + el * L::SA + qx * hDD + k;
+      eo::tr_b(tab.h, ae, ao, r);
 #pragma unroll
-      for (int j = 0; j < DH; ++j) {
-        out[j * DH] = r0[j];
-        out[Q * hDD + j * DH] = r1[j];
-      }
+      for (int j = 0; j < DH; ++j) out[j * DH] = r[j];
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[(Q + qy) * hQD];
+      eo::split<Q>(a, ae, ao);
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[(2 * Q + qy) * hQD];
+      eo::split<Q>(a, be, bo);
+      eo::tr_gb(tab.h, ae, ao, be, bo, r);
+#pragma unroll
+      for (int j = 0; j < DH; ++j) out[Q * hDD + j * DH] = r[j];
     }
   }
   if constexpr (GRAD) {
@@ -308,15 +332,11 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
       const int el = t / (3 * DL * Q), r = t - el * 3 * DL * Q, c = r / (DL * Q);
       const int l = r - c * DL * Q, k = l / Q, qx = l - k * Q;
       const double* in = bufB + el * L::SB + L::B_ZL + c * Q * lQD + l;
-      double acc[DL];
+      double a[Q], ae[QE], ao[QH], acc[DL];
 #pragma unroll
-      for (int j = 0; j < DL; ++j) acc[j] = 0.0;
-#pragma unroll
-      for (int qy = 0; qy < Q; ++qy) {
-        const double a = in[qy * lQD];
-#pragma unroll
-        for (int j = 0; j < DL; ++j) acc[j] = fma(tab.Bl[qy * DL + j], a, acc[j]);
-      }
+      for (int qy = 0; qy < Q; ++qy) a[qy] = in[qy * lQD];
+      eo::split<Q>(a, ae, ao);
+      eo::tr_b(tab.l, ae, ao, acc);
       double* out = bufA + el * L::SA + L::A_WL + (c * Q + qx) * lDD + k;
 #pragma unroll
       for (int j = 0; j < DL; ++j) out[j * DL] = acc[j];
@@ -330,16 +350,14 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
     for (int t = tid; t < nel * DH2; t += kNT) {
       const int el = t / DH2, l = t - el * DH2, j = l / DH, k = l - j * DH;
       const double* in = bufA + el * L::SA + j * DH + k;
-      double r[DH];
+      double a[Q], ae[QE], ao[QH], be[QE], bo[QH], r[DH];
 #pragma unroll
-      for (int i = 0; i < DH; ++i) r[i] = 0.0;
+      for (int qx = 0; qx < Q; ++qx) a[qx] = in[qx * hDD];
+      eo::split<Q>(a, ae, ao);
 #pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        const double a0 = in[qx * hDD], a1 = in[(Q + qx) * hDD];
-#pragma unroll
-        for (int i = 0; i < DH; ++i)
-          r[i] = fma(tab.Gh[qx * DH + i], a0, fma(tab.Bh[qx * DH + i], a1, r[i]));
-      }
+      for (int qx = 0; qx < Q; ++qx) a[qx] = in[(Q + qx) * hDD];
+      eo::split<Q>(a, be, bo);
+      eo::tr_gb(tab.h, ae, ao, be, bo, r);
       const int32_t* me = map + (e0 + el) * DH3 + j * DH + k * DH2;
 #pragma unroll
       for (int i = 0; i < DH; ++i) atomicAdd(&gtu[__ldg(&me[i])], r[i]);
@@ -350,15 +368,11 @@ __global__ void __launch_bounds__(kNT) k_mixed_apply(const int32_t* __restrict__
       const int el = t / (3 * DL2), r = t - el * 3 * DL2, c = r / DL2, l = r - c * DL2;
       const int k = l / DL, j = l - k * DL;  // j fastest: consecutive threads, consecutive rows
       const double* in = bufA + el * L::SA + L::A_WL + c * Q * lDD + j * DL + k;
-      double acc[DL];
+      double a[Q], ae[QE], ao[QH], acc[DL];
 #pragma unroll
-      for (int i = 0; i < DL; ++i) acc[i] = 0.0;
-#pragma unroll
-      for (int qx = 0; qx < Q; ++qx) {
-        const double a = in[qx * lDD];
-#pragma unroll
-        for (int i = 0; i < DL; ++i) acc[i] = fma(tab.Bl[qx * DL + i], a, acc[i]);
-      }
+      for (int qx = 0; qx < Q; ++qx) a[qx] = in[qx * lDD];
+      eo::split<Q>(a, ae, ao);
+      eo::tr_b(tab.l, ae, ao, acc);
       double* out = gp + ((e0 + el) * 3 + c) * DL3 + (j + DL * k) * DL;
 #pragma unroll
       for (int i = 0; i < DL; ++i) out[i] = acc[i];
@@ -427,11 +441,8 @@ int launch_mixed(const fe_mixed* mx, const double* p, const double* u, double* g
   });
   if (attr != cudaSuccess) return cuda_error(attr, "fe_mixed_apply: cudaFuncSetAttribute");
   MixedTab<DH, DL, Q> tab;
-  for (int i = 0; i < Q * DH; ++i) {
-    tab.Bh[i] = mx->Bh[i];
-    tab.Gh[i] = mx->Gh[i];
-  }
-  for (int i = 0; i < Q * DL; ++i) tab.Bl[i] = mx->Bl[i];
+  eo::fill(mx->Bh, mx->Gh, &tab.h);
+  eo::fill(mx->Bl, nullptr, &tab.l);
   const int64_t nblk = (mx->ne + L::NE - 1) / L::NE;
   if (nblk == 0) return FE_OK;
   kern<<<(unsigned int)nblk, kNT, smem, s>>>(mx->mesh->d_map, mx->d_qd, p, u, gp, gtu, mx->ne,
