@@ -178,7 +178,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
 
   // ---- x phase: contract i -> qx.  line (j, k); out T1c[j][k*Q + qx], c = (B x, G x)
   if constexpr (Ar::kEvenOdd) {
-    eo::x_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, nel, tid);
+    eo::x_phase<D, Q, NT, DIFF, L, Ar>(tab, bufA, bufB, nel, tid, xexp);
   } else {
     for (int t = tid; t < nel * D2; t += NT) {
       const int el = t / D2, l = t - el * D2;
@@ -220,7 +220,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   // ---- y phase: contract j -> qy.  line (k, qx); out T2c[k][qy*Q + qx]
   //      diffusion: c0 = B_y (G_x x), c1 = G_y (B_x x), c2 = B_y (B_x x)
   if constexpr (Ar::kEvenOdd) {
-    eo::y_phase<D, Q, NT, DIFF, L>(tab, bufB, bufA, nel, tid);
+    eo::y_phase<D, Q, NT, DIFF, L, Ar>(tab, bufB, bufA, nel, tid);
   } else {
     for (int t = tid; t < nel * QD; t += NT) {
       const int el = t / QD, l = t - el * QD;
@@ -276,7 +276,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   //      inputs appear only inside the qz loop, is anchored in a second pass over the column
   //      for Q <= 6 and compensated otherwise.
   if constexpr (Ar::kEvenOdd) {
-    eo::z_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, qd, e0, nel, tid);
+    eo::z_phase<D, Q, NT, DIFF, L, Ar>(tab, bufA, bufB, qd, e0, nel, tid);
   } else {
     for (int t = tid; t < nel * Q2; t += NT) {
       const int el = t / Q2, l = t - el * Q2;
@@ -408,7 +408,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
   //      diffusion: c0 (-> G_x^T) = B_y^T s0, c1 (-> B_x^T) = G_y^T s1 + B_y^T s2
   //      (outer-product form over qy with anchored accumulators; bounds from a first pass)
   if constexpr (Ar::kEvenOdd) {
-    eo::yt_phase<D, Q, NT, DIFF, L>(tab, bufB, bufA, nel, tid);
+    eo::yt_phase<D, Q, NT, DIFF, L, Ar>(tab, bufB, bufA, nel, tid);
   } else {
     for (int t = tid; t < nel * QD; t += NT) {
       const int el = t / QD, l = t - el * QD;
@@ -468,7 +468,7 @@ __device__ __forceinline__ typename Ar::DotAcc pa_apply_block(
 
   // ---- x^T phase: contract qx -> i.  line (j, k); out Ye[i + D j + D^2 k]
   if constexpr (Ar::kEvenOdd) {
-    eo::xt_phase<D, Q, NT, DIFF, L>(tab, bufA, bufB, nel, tid);
+    eo::xt_phase<D, Q, NT, DIFF, L, Ar>(tab, bufA, bufB, nel, tid);
   } else {
     for (int t = tid; t < nel * D2; t += NT) {
       const int el = t / D2, l = t - el * D2;

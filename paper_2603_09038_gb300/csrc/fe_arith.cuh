@@ -24,6 +24,8 @@
 //  error-free steps also run in the CPU unit test of that header.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -145,14 +147,16 @@ struct ArF32x2T {
   // element's largest entry in [1, 2)); results are widened with both scales undone.  So the
   // arithmetic is FP64-accurate for inputs anywhere in the FP64 range, not only the float range.
   static constexpr bool kScaled = true;
-  static constexpr bool kEvenOdd = false;
+  // compensated orders: even-odd contractions with TwoSum splits and joins (fe_apply_eo.cuh);
+  // anchored orders keep the direct contractions, whose anchors need a-priori bounds
+  static constexpr bool kEvenOdd = !ANCHORED;
   static constexpr bool kPrefetchQd = true;  // bulk L2 prefetch of the block's quadrature data
   using QdT = double;  // 8-byte (hi, lo) float pairs
   using T = f2;
   using Acc = Anch;
   using Sig = float;
   template <int D, int Q>
-  using Tab = TabF32x2<D, Q>;
+  using Tab = typename std::conditional<ANCHORED, TabF32x2<D, Q>, TabEO<f2, D, Q>>::type;
 
   static __device__ __forceinline__ T zero() { return f2{0.0f, 0.0f}; }
   static __device__ __forceinline__ T from_vec(double v) { return f2_from_f64(v); }
@@ -166,11 +170,11 @@ struct ArF32x2T {
     return f2{v.x, v.y};
   }
   template <int D, int Q>
-  static __device__ __forceinline__ void madB(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
+  static __device__ __forceinline__ void madB(T& acc, const TabF32x2<D, Q>& t, int q, int d, T x) {
     f2_mad(acc, t.Bh[q * D + d], t.Bl[q * D + d], x);
   }
   template <int D, int Q>
-  static __device__ __forceinline__ void madG(T& acc, const Tab<D, Q>& t, int q, int d, T x) {
+  static __device__ __forceinline__ void madG(T& acc, const TabF32x2<D, Q>& t, int q, int d, T x) {
     f2_mad(acc, t.Gh[q * D + d], t.Gl[q * D + d], x);
   }
   static __device__ __forceinline__ void mad(T& acc, T a, T x) { f2_mad(acc, a.h, a.l, x); }
@@ -183,16 +187,16 @@ struct ArF32x2T {
   static __device__ __forceinline__ float amax(float m, T x) { return fmaxf(m, fabsf(x.h)); }
   // anchors: forward (row sums) or transposed (column sums) use of the table
   template <int D, int Q>
-  static __device__ __forceinline__ Sig sigB(const Tab<D, Q>& t, float m, bool transposed) {
+  static __device__ __forceinline__ Sig sigB(const TabF32x2<D, Q>& t, float m, bool transposed) {
     return anchor_of(f_mul(transposed ? t.cB : t.rB, m));
   }
   template <int D, int Q>
-  static __device__ __forceinline__ Sig sigG(const Tab<D, Q>& t, float m, bool transposed) {
+  static __device__ __forceinline__ Sig sigG(const TabF32x2<D, Q>& t, float m, bool transposed) {
     return anchor_of(f_mul(transposed ? t.cG : t.rG, m));
   }
   // bound of G.a + B.b with max |a| = mg, max |b| = mb
   template <int D, int Q>
-  static __device__ __forceinline__ Sig sigGB(const Tab<D, Q>& t, float mg, float mb,
+  static __device__ __forceinline__ Sig sigGB(const TabF32x2<D, Q>& t, float mg, float mb,
                                              bool transposed) {
     return anchor_of(f_fma(transposed ? t.cG : t.rG, mg, f_mul(transposed ? t.cB : t.rB, mb)));
   }
@@ -200,11 +204,11 @@ struct ArF32x2T {
     return ANCHORED ? anch_begin(s) : Anch{0.0f, 0.0f};
   }
   template <int D, int Q>
-  static __device__ __forceinline__ void amadB(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+  static __device__ __forceinline__ void amadB(Acc& acc, const TabF32x2<D, Q>& t, int q, int d, T x) {
     amad(acc, t.Bh[q * D + d], t.Bl[q * D + d], x);
   }
   template <int D, int Q>
-  static __device__ __forceinline__ void amadG(Acc& acc, const Tab<D, Q>& t, int q, int d, T x) {
+  static __device__ __forceinline__ void amadG(Acc& acc, const TabF32x2<D, Q>& t, int q, int d, T x) {
     amad(acc, t.Gh[q * D + d], t.Gl[q * D + d], x);
   }
   static __device__ __forceinline__ void amad(Acc& acc, float ah, float al, T x) {
