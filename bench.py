@@ -758,19 +758,40 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
     t_fj, s_fj = timed(lambda: solve_fcg(None), max(1, min(args.steps, EXTRA_STEPS)))
     r_ = torch.rand(ndofs, dtype=torch.float64, device=dev) * 2 - 1
     z_ = torch.empty_like(r_)
-    for _ in range(3):
-        fe.fe_lpc_apply(lpc, r_, z_, stream)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(20)]
-    torch.cuda.synchronize()
-    for a_, z2 in ev:
-        a_.record(stream)
-        fe.fe_lpc_apply(lpc, r_, z_, stream)
-        z2.record(stream)
-    torch.cuda.synchronize()
-    ms_lpc = statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
+
+    def time_apply():
+        for _ in range(3):
+            fe.fe_lpc_apply(lpc, r_, z_, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(20)]
+        torch.cuda.synchronize()
+        for a_, z2 in ev:
+            a_.record(stream)
+            fe.fe_lpc_apply(lpc, r_, z_, stream)
+            z2.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a_.elapsed_time(z2) for a_, z2 in ev)
+
+    # the preconditioner apply alone with every built inference kernel; the solves above used
+    # the default one
+    kernel_used = fe.fe_lpc_get_kernel(lpc)[0]
+    kernel_names = {fe.FE_LPC_KERNEL_TCGEN05: "tcgen05", fe.FE_LPC_KERNEL_MMA_SYNC: "mma_sync",
+                    fe.FE_LPC_KERNEL_GEMM: "gemm"}
+    ms_by_kernel = {}
+    for k_, name_ in kernel_names.items():
+        try:
+            fe.fe_lpc_set_kernel(lpc, k_)
+        except fe.FEError:
+            continue
+        ms_by_kernel[name_] = time_apply()
+    fe.fe_lpc_set_kernel(lpc, fe.FE_LPC_KERNEL_AUTO)
+    ms_lpc = ms_by_kernel[kernel_names[kernel_used]]
+    tc_faults = fe.fe_lpc_get_kernel(lpc)[1]
     din, w = (p + 1) ** 3, width
     lpc_flops = 2.0 * ne * (2 * din * w + w * w + din * din)
+    # algorithmic bytes: the dof map (int32) once, r and z (FP64) and the FP32 scaling once
+    # per dof (the kernels read the map a second time in the scatter)
+    lpc_bytes = ne * din * 4 + ndofs * (8 + 8 + 4)
     mma_peak = fe.fe_probe_throughput("bf16_mma")
     bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
     ir = None
@@ -813,7 +834,12 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
         "mma_sync_bf16_probe_tflops": mma_peak,
         "frac_of_mma_sync_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / mma_peak,
         "frac_of_bf16_peak": lpc_flops / (ms_lpc * 1e-3) / 1e12 / bf16_peak,
-        "kernel": "k_lpc_fused<DP=%d,W=%d>" % ((din + 15) // 16 * 16, w)}
+        "precond_apply_ms_by_kernel": ms_by_kernel, "tcgen05_faults": tc_faults,
+        "precond_bytes_per_launch": lpc_bytes,
+        "precond_hbm_frac": lpc_bytes / (ms_lpc * 1e-3) / 1e9 /
+                            float(measured_peaks()[0].get("hbm_gbs", 6800.0)),
+        "kernel": {"tcgen05": "k_lpc_tc", "mma_sync": "k_lpc_fused", "gemm": "unfused GEMMs"}[
+            kernel_names[kernel_used]] + "<DP=%d,W=%d>" % ((din + 15) // 16 * 16, w)}
 
 
 fe_mesh_of = {}   # fe_pa handle -> its fe_mesh handle (for sizes)

@@ -436,6 +436,30 @@ int fe_lpc_set_fallback(fe_lpc* lpc, int pc);
  * Asynchronous. */
 int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
 
+/* Inference kernel of the learned preconditioner (fe_lpc_apply, fe_fcg, fe_fcg_ir):
+ *   FE_LPC_KERNEL_AUTO      the fastest built kernel as measured on GB300: the mma.sync fused
+ *                           kernel where it is built, else the tcgen05 one, else the unfused
+ *                           GEMM path (the default);
+ *   FE_LPC_KERNEL_TCGEN05   fused, one CTA per 128 elements, every layer on the 5th-generation
+ *                           tensor cores (tcgen05.mma, FP32 accumulators in tensor memory,
+ *                           weights staged by bulk copies); built for D^3 <= 128 (padded to a
+ *                           multiple of 16) and width 0, 64 or 128;
+ *   FE_LPC_KERNEL_MMA_SYNC  fused, one warp per 16 elements, warp-level mma.sync;
+ *   FE_LPC_KERNEL_GEMM      gather kernel, the training path's four BF16 GEMMs, scatter kernel.
+ * FE_ERR_UNSUPPORTED if the fused kernel asked for is not built for this order and width.
+ * fe_lpc_get_kernel returns the kernel a call uses now (never AUTO) and, when tc_faults is not
+ * NULL, whether a tcgen05 launch has given up a bounded wait on the tensor core since the
+ * handle was created (synchronous; such a launch leaves z incomplete, and fe_fcg / fe_fcg_ir
+ * return FE_ERR_CUDA when it happens during their solve). */
+typedef enum {
+  FE_LPC_KERNEL_AUTO = 0,
+  FE_LPC_KERNEL_TCGEN05 = 1,
+  FE_LPC_KERNEL_MMA_SYNC = 2,
+  FE_LPC_KERNEL_GEMM = 3
+} fe_lpc_kernel;
+int fe_lpc_set_kernel(fe_lpc* lpc, int kernel);
+int fe_lpc_get_kernel(const fe_lpc* lpc, int* kernel, int* tc_faults);
+
 /* Flexible CG (FCG with one stored direction: beta = -(z.q)/(p.q), alpha = (p.r)/(p.q)) for the
  * same system, arguments and stopping rule as fe_pcg, preconditioned by lpc, or by Jacobi when
  * lpc is NULL.  If the learned preconditioner produces a non-descent direction (z.r <= 0) or the

@@ -35,6 +35,7 @@
 #include "fe_f2.h"
 #include "fe_internal.h"
 #include "fe_mlp.cuh"
+#include "fe_mlp_tc.cuh"
 
 using namespace fe;
 
@@ -60,6 +61,12 @@ struct fe_lpc {
   __nv_bfloat16* wimg = nullptr;  // shared-memory weight image of the fused apply
   bool wimg_ok = false;
   int fused_grid = 0;           // persistent grid of the fused apply (0: unfused GEMM path)
+  __nv_bfloat16* tcimg = nullptr;  // canonical K-major weight images of the tcgen05 apply
+  bool tcimg_ok = false;
+  int tc_grid = 0;              // persistent grid of the tcgen05 apply (0: not built / no fit)
+  int tc_grid32 = 0;            // the same for FP32 vectors
+  int* d_tcfail = nullptr;      // raised by the tcgen05 apply when it gives up a wait
+  int kernel = FE_LPC_KERNEL_AUTO;  // which inference kernel fe_lpc_apply and the solvers use
   // training samples
   int64_t nsamp = 0;
   __nv_bfloat16* Xs = nullptr;  // [nsamp][din]
@@ -1161,6 +1168,143 @@ void fused_setup(fe_lpc* L) {
   L->fused_grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
 }
 
+// ---- the tcgen05 fused apply (fe_mlp_tc.cuh)
+constexpr int kSmemPerSm = 233472;  // 228 KB of shared memory per SM
+
+// Dynamic shared memory per CTA: the layout's, raised where needed so that no more CTAs fit on
+// one SM than its 512 TMEM columns serve (a CTA whose allocation cannot be met would otherwise
+// wait inside tcgen05.alloc for another CTA to finish).
+template <int DP, int W>
+constexpr int tc_smem() {
+  using Lay = mlptc::TcLayout<DP, W>;
+  constexpr int cap = 512 / Lay::NCOLS;
+  constexpr int floor_ = kSmemPerSm / (cap + 1) + 1;
+  return Lay::SMEM > floor_ ? Lay::SMEM : floor_;
+}
+
+// Resident CTAs per SM of the tcgen05 apply for (DP, W), 0 if it does not fit.
+template <int DP, int W, class VT>
+int tc_occupancy() {
+  constexpr int smem = tc_smem<DP, W>();
+  if constexpr (smem <= (int)kMaxSmem) {
+    auto kern = mlptc::k_lpc_tc<DP, W, VT>;
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, mlptc::kThreads, smem) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    const int cap = 512 / mlptc::TcLayout<DP, W>::NCOLS;
+    return occ < cap ? occ : cap;
+  }
+  return 0;
+}
+
+template <int DP, int W, class VT>
+cudaError_t tc_launch(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStream_t s) {
+  constexpr int smem = tc_smem<DP, W>();
+  if constexpr (smem <= (int)kMaxSmem) {
+    const fe_mesh* m = L->pa->mesh;
+    mlptc::k_lpc_tc<DP, W, VT><<<grid, mlptc::kThreads, smem, s>>>(
+        L->tcimg, r, m->d_map, L->fsc32, m->ne, L->din, z, L->d_tcfail);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+// The built (DP, W) pairs of the tcgen05 apply.
+#define FE_TC_CASES(X) \
+  X(16, 0) X(16, 64) X(16, 128) X(32, 0) X(32, 64) X(32, 128) X(64, 0) X(64, 64) X(64, 128) \
+  X(128, 0) X(128, 64) X(128, 128)
+
+template <class VT>
+int tc_occ(int DP, int W) {
+#define FE_TC_OCC(dp, w) \
+  if (DP == dp && W == w) return tc_occupancy<dp, w, VT>();
+  FE_TC_CASES(FE_TC_OCC)
+#undef FE_TC_OCC
+  return 0;
+}
+
+template <class VT>
+cudaError_t tc_run(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStream_t s) {
+  const int DP = mlp::fused_dp(L->din), W = L->width;
+#define FE_TC_RUN(dp, w) \
+  if (DP == dp && W == w) return tc_launch<dp, w, VT>(L, r, z, grid, s);
+  FE_TC_CASES(FE_TC_RUN)
+#undef FE_TC_RUN
+  return cudaErrorInvalidConfiguration;
+}
+
+// Persistent grids of the tcgen05 apply for FP64 and FP32 vectors (0 where it is not built or
+// the device has no tcgen05), its weight images and its fault flag.
+void tc_setup(fe_lpc* L) {
+  L->tc_grid = L->tc_grid32 = 0;
+  int dev = 0, sms = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (major != 10) return;  // tcgen05: the sm_100 family
+  const int DP = mlp::fused_dp(L->din);
+  const int occ = tc_occ<double>(DP, L->width), occ32 = tc_occ<float>(DP, L->width);
+  if (occ <= 0 && occ32 <= 0) return;
+  int64_t off[5];
+  mlptc::tc_offsets(DP, L->width, off);
+  if (cudaMalloc(&L->tcimg, sizeof(__nv_bfloat16) * off[4]) != cudaSuccess ||
+      cudaMalloc(&L->d_tcfail, sizeof(int)) != cudaSuccess ||
+      cudaMemset(L->d_tcfail, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(L->tcimg);
+    cudaFree(L->d_tcfail);
+    L->tcimg = nullptr;
+    L->d_tcfail = nullptr;
+    return;
+  }
+  const int64_t tiles = (L->pa->mesh->ne + mlptc::kRows - 1) / mlptc::kRows;
+  auto grid = [&](int o) -> int {
+    if (o <= 0) return 0;
+    const int64_t cap = (int64_t)sms * o;
+    return (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
+  };
+  L->tc_grid = grid(occ);
+  L->tc_grid32 = grid(occ32);
+}
+
+// The inference kernel a call uses (AUTO resolved); fp32: the FP32-vector solves, which have
+// no unfused path.  AUTO takes the measured-fastest built kernel: the mma.sync fused kernel
+// (its warps each gather, transform and scatter 16 elements with no block-wide barrier, which
+// hides the dof-map gather's latency better than the tcgen05 kernel's 128-element tile
+// pipeline: 0.22 against 0.27 ms at 64^3, p = 3, width 128), then tcgen05, then the GEMMs.
+int lpc_kernel(const fe_lpc* L, bool fp32) {
+  if (L->kernel != FE_LPC_KERNEL_AUTO) return L->kernel;
+  if (L->fused_grid > 0) return FE_LPC_KERNEL_MMA_SYNC;
+  if ((fp32 ? L->tc_grid32 : L->tc_grid) > 0) return FE_LPC_KERNEL_TCGEN05;
+  return FE_LPC_KERNEL_GEMM;
+}
+
+// The tcgen05 weight images, packed on first use after every weight update.
+void tc_pack(fe_lpc* L, cudaStream_t s) {
+  if (L->tcimg_ok) return;
+  int64_t off[5];
+  const int DP = mlp::fused_dp(L->din);
+  mlptc::tc_offsets(DP, L->width, off);
+  mlptc::k_pack_tc<<<grid1(off[4]), kT, 0, s>>>(L->w32, L->din, L->width, DP, L->tcimg);
+  L->tcimg_ok = true;
+}
+
+// 1 if a tcgen05 launch has given up a wait (synchronous read of the device flag).
+int tc_faulted(const fe_lpc* L) {
+  if (!L || !L->d_tcfail) return 0;
+  int f = 0;
+  if (cudaMemcpy(&f, L->d_tcfail, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+  return f;
+}
+
 }  // namespace
 
 namespace {
@@ -1169,6 +1313,10 @@ int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s) {
   cudaError_t err;
   if ((err = cudaMemsetAsync(z, 0, sizeof(float) * L->pa->mesh->ndofs, s)) != cudaSuccess)
     return cuda_error(err, "fe_fcg_ir: zero z");
+  if (lpc_kernel(L, true) == FE_LPC_KERNEL_TCGEN05) {
+    tc_pack(L, s);
+    return cuda_error(tc_run<float>(L, r, z, L->tc_grid32, s), "fe_fcg_ir: tcgen05 launch");
+  }
   if (!L->wimg_ok) {
     int64_t off[5];
     const int DP = mlp::fused_dp(L->din);
@@ -1185,7 +1333,15 @@ namespace fe {
 int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
   const fe_mesh* m = L->pa->mesh;
   const int din = L->din;
-  if (L->fused_grid > 0) {
+  const int kernel = lpc_kernel(L, false);
+  if (kernel == FE_LPC_KERNEL_TCGEN05) {
+    cudaError_t err;
+    if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+      return cuda_error(err, "fe_lpc_apply: zero z");
+    tc_pack(L, s);
+    return cuda_error(tc_run<double>(L, r, z, L->tc_grid, s), "fe_lpc_apply: tcgen05 launch");
+  }
+  if (kernel == FE_LPC_KERNEL_MMA_SYNC) {
     cudaError_t err;
     if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
       return cuda_error(err, "fe_lpc_apply: zero z");
@@ -1232,9 +1388,14 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
   if (inner_rtol == 0.0) inner_rtol = 1e-2;
   if (!(inner_rtol > 0.0 && inner_rtol < 1.0))
     return set_error(FE_ERR_ARG, "fe_fcg_ir: inner_rtol must lie in (0, 1)");
-  if (lpc->fused_grid <= 0 || !fused_f32_built(lpc))
-    return set_error(FE_ERR_UNSUPPORTED,
-                     "fe_fcg_ir: no FP32 fused kernel for this order and width (0, 64 or 128)");
+  {
+    const int k = lpc_kernel(lpc, true);
+    const bool ok = (k == FE_LPC_KERNEL_TCGEN05 && lpc->tc_grid32 > 0) ||
+                    (k == FE_LPC_KERNEL_MMA_SYNC && lpc->fused_grid > 0 && fused_f32_built(lpc));
+    if (!ok)
+      return set_error(FE_ERR_UNSUPPORTED,
+                       "fe_fcg_ir: no FP32 fused kernel for this order, width and kernel choice");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   int st;
   if ((op == FE_DIFFUSION ? pa->d_qd_diff32 : pa->d_qd_mass32) == nullptr) {
@@ -1331,6 +1492,9 @@ int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x
     stats->launches = launches;
     stats->outer_iters = outer;
   }
+  if (tc_faulted(lpc))
+    return set_error(FE_ERR_CUDA, "fe_fcg_ir: the tcgen05 preconditioner gave up a wait on the "
+                                  "tensor core");
   switch (state) {
     case FE_OK:
       return FE_OK;
@@ -1399,6 +1563,7 @@ int fe_lpc_create(fe_pa* pa, int op, int width, uint64_t seed, fe_lpc** out) {
     return st;
   }
   fused_setup(L);
+  tc_setup(L);
   *out = L;
   return FE_OK;
 }
@@ -1413,6 +1578,7 @@ int adam_update(fe_lpc* L, double lr, cudaStream_t s) {
   ++L->adam_t;
   const float c1 = 1.0f - powf(b1, (float)L->adam_t), c2 = 1.0f - powf(b2, (float)L->adam_t);
   L->wimg_ok = false;
+  L->tcimg_ok = false;
   k_adam<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->grad, L->adam_m, L->adam_v, L->nparam,
                                          (float)lr, b1, b2, 1e-8f, c1, c2, L->wb);
   return cuda_error(cudaGetLastError(), "fe_lpc: Adam step launch");
@@ -1530,6 +1696,7 @@ int fe_lpc_fit_linear(fe_lpc* L, double ridge, int reps, double* fit_loss, void*
     return cuda_error(err, "fe_lpc_fit_linear: weights");
   k_to_bf16<<<grid1(L->nparam), kT, 0, s>>>(L->w32, L->wb, L->nparam);
   L->wimg_ok = false;
+  L->tcimg_ok = false;
   return cuda_error(cudaStreamSynchronize(s), "fe_lpc_fit_linear");
 }
 
@@ -1542,6 +1709,7 @@ int fe_lpc_weights(fe_lpc* L, float* host_w, int set) {
       return cuda_error(err, "fe_lpc_weights");
     k_to_bf16<<<grid1(L->nparam), kT>>>(L->w32, L->wb, L->nparam);
     L->wimg_ok = false;
+    L->tcimg_ok = false;
     return cuda_error(cudaDeviceSynchronize(), "fe_lpc_weights");
   }
   return cuda_error(cudaMemcpy(host_w, L->w32, 4 * L->nparam, cudaMemcpyDeviceToHost),
@@ -1630,6 +1798,29 @@ int fe_lpc_apply(fe_lpc* L, const double* dev_r, double* dev_z, void* stream) {
   clear_error();
   if (!L || !dev_r || !dev_z) return set_error(FE_ERR_ARG, "fe_lpc_apply: null argument");
   return lpc_apply(L, dev_r, dev_z, (cudaStream_t)stream);
+}
+
+int fe_lpc_set_kernel(fe_lpc* L, int kernel) {
+  clear_error();
+  if (!L) return set_error(FE_ERR_ARG, "fe_lpc_set_kernel: lpc is NULL");
+  if (kernel < FE_LPC_KERNEL_AUTO || kernel > FE_LPC_KERNEL_GEMM)
+    return set_error(FE_ERR_ARG, "fe_lpc_set_kernel: unknown kernel");
+  if (kernel == FE_LPC_KERNEL_TCGEN05 && L->tc_grid <= 0 && L->tc_grid32 <= 0)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_set_kernel: no tcgen05 kernel for this order "
+                                         "and width (D^3 <= 128, width 0, 64 or 128)");
+  if (kernel == FE_LPC_KERNEL_MMA_SYNC && L->fused_grid <= 0)
+    return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_set_kernel: no mma.sync fused kernel for this "
+                                         "order and width");
+  L->kernel = kernel;
+  return FE_OK;
+}
+
+int fe_lpc_get_kernel(const fe_lpc* L, int* kernel, int* tc_faults) {
+  clear_error();
+  if (!L || !kernel) return set_error(FE_ERR_ARG, "fe_lpc_get_kernel: null argument");
+  *kernel = lpc_kernel(L, false);
+  if (tc_faults) *tc_faults = tc_faulted(L);
+  return FE_OK;
 }
 
 int fe_lpc_nparams(const fe_lpc* L, int64_t* n) {
@@ -1730,6 +1921,9 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
     stats->launches = res.launches;
     stats->outer_iters = 1 + res.restarts;
   }
+  if (tc_faulted(lpc))
+    return set_error(FE_ERR_CUDA, "fe_fcg: the tcgen05 preconditioner gave up a wait on the "
+                                  "tensor core");
   switch (res.status) {
     case FE_OK:
       return FE_OK;
@@ -1833,6 +2027,7 @@ int fe_lpc_load(fe_lpc* L, const char* path) {
   L->adam_t = h.adam_t;
   k_to_bf16<<<grid1(n), kT>>>(L->w32, L->wb, n);
   L->wimg_ok = false;
+  L->tcimg_ok = false;
   return cuda_error(cudaDeviceSynchronize(), "fe_lpc_load");
 }
 
@@ -1858,7 +2053,7 @@ void fe_lpc_destroy(fe_lpc* L) {
   if (!L) return;
   if (L->pa && L->pa->lpc == L) L->pa->lpc = nullptr;
   cudaFree(L->w32); cudaFree(L->wb); cudaFree(L->adam_m); cudaFree(L->adam_v); cudaFree(L->grad);
-  cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->fsc32); cudaFree(L->wimg); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
+  cudaFree(L->wsq); cudaFree(L->dinv); cudaFree(L->dis); cudaFree(L->fsc); cudaFree(L->fsc32); cudaFree(L->wimg); cudaFree(L->tcimg); cudaFree(L->d_tcfail); cudaFree(L->red); cudaFree(L->Xs); cudaFree(L->Ts);
   cudaFree(L->Xb); cudaFree(L->H1b); cudaFree(L->H2b); cudaFree(L->dYb); cudaFree(L->dA1b);
   cudaFree(L->dA2b); cudaFree(L->Z1); cudaFree(L->Z2); cudaFree(L->Y); cudaFree(L->Tb);
   cudaFree(L->scale);

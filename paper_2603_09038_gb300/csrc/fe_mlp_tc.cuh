@@ -1,0 +1,447 @@
+// Fused inference of the learned patch preconditioner on the 5th-generation tensor cores
+// (tcgen05.mma with TMEM accumulators; sm_100-family, built here for sm_103a).
+//
+// z += sum_e R_e^T F_e s_e f(x_e / s_e), x_e = F_e R_e r, s_e = ||x_e||_2, with
+// f(x) = relu(relu(x W1) W2) W3 + x W0 (W = 0: the linear patch map f(x) = x W0) -- the same
+// operator as mlp::k_lpc_fused, re-tiled for tcgen05:
+//   * one CTA (8 warps) takes 128 elements at a time: the 128 rows of every layer's M = 128 MMA;
+//   * the weights live in shared memory for the whole persistent kernel, copied once by
+//     cp.async.bulk behind an mbarrier, as BF16 images in the tensor core's canonical K-major
+//     layout without swizzle (8-row x 16-byte core matrices, element (n, k) of an N x K image at
+//     ((n/8)(K/8) + k/8) 128 + (n%8) 16 + (k%8) 2 bytes: K-adjacent core matrices 128 bytes
+//     apart (the descriptor's leading offset), 8-row groups K/8 x 128 bytes apart (its stride
+//     offset));
+//   * the gather writes the normalised BF16 rows (the A operand of layer 1 and of the skip term)
+//     into the same layout; one thread issues each layer's chain of K = 16 MMAs into a FP32
+//     accumulator of 128 TMEM lanes x N columns and commits it to an mbarrier; the epilogue
+//     warps read their lane quadrant back with tcgen05.ld, apply ReLU and write the BF16 A
+//     operand of the next layer; layer 3 and the skip term accumulate into the same columns;
+//   * the result goes through a shared staging tile so that the scatter's dof-map reads and
+//     atomic adds are warp-coalesced along each element's dofs.
+// Every wait on an mbarrier has an iteration limit: on expiry the kernel raises a device flag,
+// all threads leave the tile loop together, and the TMEM is freed before the kernel returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fe {
+namespace mlptc {
+
+constexpr int kRows = 128;     // rows (elements) per tile: the MMA's M
+constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quadrant
+constexpr long long kWaitLimit = 1ll << 22;  // mbarrier polls before a wait is given up
+
+__host__ __device__ constexpr int pow2_cols(int n) {
+  int c = 32;
+  while (c < n) c *= 2;
+  return c;
+}
+
+// Byte sizes of the shared-memory regions for (DP, W).
+template <int DP, int W>
+struct TcLayout {
+  static constexpr int W1 = 0;                           // [W][DP]
+  static constexpr int W2 = W1 + W * DP * 2;             // [W][W]
+  static constexpr int W3 = W2 + W * W * 2;              // [DP][W]
+  static constexpr int W0 = W3 + DP * W * 2;             // [DP][DP]
+  static constexpr int WBYTES = W0 + DP * DP * 2;        // weight images
+  static constexpr int X = WBYTES;                       // [128][DP] BF16
+  static constexpr int H = X + kRows * DP * 2;           // [128][W] BF16
+  static constexpr int YS = DP + 4;                      // staging row stride (floats)
+  static constexpr int ACT = (kRows * (DP + W) * 2 > kRows * YS * 4) ? kRows * (DP + W) * 2
+                                                                     : kRows * YS * 4;
+  static constexpr int SCALE = X + ACT;                  // float[128]
+  static constexpr int BAR = SCALE + kRows * 4;          // two mbarriers (weights, MMA)
+  static constexpr int SLOT = BAR + 16;                  // TMEM base address
+  static constexpr int SMEM = SLOT + 16;
+  static constexpr int NCOLS = pow2_cols(W > DP ? W : DP);  // TMEM columns
+  static_assert(DP % 16 == 0 && W % 16 == 0 && DP >= 16 && DP <= 256 && W <= 256,
+                "tcgen05 tile sizes: N and K multiples of 16, N <= 256");
+  static_assert(WBYTES % 16 == 0 && X % 16 == 0 && H % 16 == 0, "16-byte aligned regions");
+};
+
+// Host: offsets (BF16 elements) of the four images in the packed weight buffer.
+__host__ __device__ inline void tc_offsets(int DP, int W, int64_t off[5]) {
+  off[0] = 0;
+  off[1] = off[0] + (int64_t)W * DP;
+  off[2] = off[1] + (int64_t)W * W;
+  off[3] = off[2] + (int64_t)DP * W;
+  off[4] = off[3] + (int64_t)DP * DP;
+}
+
+// Element (n, k) of an N x K BF16 image in the canonical K-major layout (BF16 elements).
+__host__ __device__ inline int64_t canon(int n, int k, int K) {
+  return ((int64_t)(n >> 3) * (K >> 3) + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+}
+
+// One image element per thread: layer L (0..3 = W1, W2, W3, W0) from the FP32 master weights
+// (row-major [k][n] with the true sizes; zero padding beyond them), as for k_pack_wimg.
+__global__ void k_pack_tc(const float* __restrict__ w32, int din, int width, int DP,
+                          __nv_bfloat16* __restrict__ img) {
+  int64_t off[5];
+  tc_offsets(DP, width, off);
+  const int64_t src2 = (int64_t)din * width, src3 = src2 + (int64_t)width * width,
+                src0 = src3 + (int64_t)width * din;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < off[4];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int L = 0;
+    while (i >= off[L + 1]) ++L;
+    const int64_t j = i - off[L];
+    int K, nv, kv;
+    int64_t src;
+    if (L == 0) { K = DP; nv = width; kv = din; src = 0; }
+    else if (L == 1) { K = width; nv = width; kv = width; src = src2; }
+    else if (L == 2) { K = width; nv = din; kv = width; src = src3; }
+    else { K = DP; nv = din; kv = din; src = src0; }
+    const int n = (int)(j / K), k = (int)(j % K);
+    const float v = (n < nv && k < kv) ? w32[src + (int64_t)k * nv + n] : 0.0f;
+    img[off[L] + canon(n, k, K)] = __float2bfloat16(v);
+  }
+}
+
+// ---- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction) and stride (8-row
+// direction) byte offsets, the fixed version bits 46-48 = 0b001, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9
+// and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy writes to shared memory made visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Bounded wait for the phase with parity `parity` of the mbarrier: 1 if it completed.
+__device__ __forceinline__ int bar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return 1;
+  }
+  return 0;
+}
+
+// The calling thread's share of an expected transaction byte count, and its arrival.
+__device__ __forceinline__ void bar_arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
+// `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"(slot), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 8 consecutive FP32 columns of the calling thread's TMEM lane (32x32b shape: warp w reads lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, thread t lane 32 (w % 4) + t).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(hi)) << 16);
+}
+
+// One elected thread issues the K / 16 MMAs of D[128 x N] (+)= A[128 x K] B[N x K]^T, both
+// operands canonical K-major images in shared memory (K-adjacent core matrices 128 bytes apart,
+// 8-row groups K / 8 x 128 bytes apart; a K = 16 step advances the start by two core matrices).
+__device__ __forceinline__ void issue_chain(uint32_t tmem, uint32_t a, uint32_t b, int K, int N,
+                                            bool accumulate) {
+  const uint32_t id = idesc_bf16(kRows, N), sbo = (uint32_t)(K / 8) * 128u;
+  for (int kk = 0; kk < K / 16; ++kk)
+    mma_bf16(tmem, sdesc(a + kk * 256u, 128u, sbo), sdesc(b + kk * 256u, 128u, sbo), id,
+             (accumulate || kk > 0) ? 1u : 0u);
+}
+
+// Epilogue of a hidden layer: the warp's lane quadrant, its half of the N columns, ReLU, BF16,
+// into the canonical [128][N] image at dst.
+template <int N>
+__device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int half,
+                                              unsigned char* dst) {
+#pragma unroll
+  for (int c = half * (N / 2); c < (half + 1) * (N / 2); c += 8) {
+    float v[8];
+    tmem_ld8(t_lane + (uint32_t)c, v);
+    uint4 pk;
+    pk.x = pack_bf16(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
+    pk.y = pack_bf16(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
+    pk.z = pack_bf16(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
+    pk.w = pack_bf16(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
+    *reinterpret_cast<uint4*>(dst + canon(row, c, N) * 2) = pk;
+  }
+}
+
+// VT: element type of r and z (double; float inside the mixed-precision solver).  fail: device
+// flag raised when a wait on the tensor core or on the weight copy is given up.
+template <int DP, int W, class VT>
+__global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
+    const __nv_bfloat16* __restrict__ wimg, const VT* __restrict__ r,
+    const int32_t* __restrict__ map, const float* __restrict__ fsc, int64_t ne, int din,
+    VT* __restrict__ z, int* __restrict__ fail) {
+  using Lay = TcLayout<DP, W>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sb = smem_u32(smem);
+  const uint32_t bar_w = sb + Lay::BAR, bar_m = sb + Lay::BAR + 8;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(smem + Lay::SLOT);
+  float* sscale = reinterpret_cast<float*>(smem + Lay::SCALE);
+  unsigned char* sX = smem + Lay::X;
+  unsigned char* sH = smem + Lay::H;
+  const float* sY = reinterpret_cast<const float*>(smem + Lay::X);  // after the last MMA
+
+  // ---- barriers, TMEM, the weight images (one bulk copy stream behind an mbarrier)
+  if (tid == 0) {
+    bar_init(bar_w, 1);
+    bar_init(bar_m, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(smem_u32(slot), Lay::NCOLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *slot;
+  if (tid == 0) {
+    bar_arrive_expect(bar_w, (uint32_t)Lay::WBYTES);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(wimg);
+    for (int off = 0; off < Lay::WBYTES; off += 16384) {
+      const int n = (Lay::WBYTES - off) < 16384 ? (Lay::WBYTES - off) : 16384;
+      bulk_g2s(sb + (uint32_t)off, src + off, (uint32_t)n, bar_w);
+    }
+  }
+  int bad = __syncthreads_or(!bar_wait(bar_w, 0));
+
+  const int q = warp & 3, half = warp >> 2;
+  const int erow = 32 * q + lane;  // this thread's TMEM lane = tile row in the epilogues
+  const uint32_t t_lane = tmem + ((uint32_t)(32 * q) << 16);
+  uint32_t phase = 0;
+  const int64_t ntiles = (ne + kRows - 1) / kRows;
+  constexpr int NPAIR = DP / 2, PPL = (NPAIR + 31) / 32;  // BF16 pairs per row, per lane
+  constexpr int RG = PPL > 1 ? 4 : 8;                     // rows per gather / scatter group
+  for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
+    // ---- gather: x = F r on each element, normalised by its norm, BF16 into the X image;
+    //      warp w takes rows 16 w .. 16 w + 15, RG at a time: every dof-map entry of the group
+    //      is loaded first, then the values, so that all of them are in flight together
+#pragma unroll 1
+    for (int r0 = 16 * warp; r0 < 16 * warp + 16; r0 += RG) {
+      int32_t gi[RG][PPL][2];
+#pragma unroll
+      for (int i = 0; i < RG; ++i) {
+        const int64_t e = tile * kRows + r0 + i;
+#pragma unroll
+        for (int w = 0; w < PPL; ++w)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = 2 * (lane + 32 * w) + h;
+            gi[i][w][h] = (k < din && e < ne) ? __ldg(&map[e * din + k]) : -1;
+          }
+      }
+      float xv[RG][PPL][2];
+#pragma unroll
+      for (int i = 0; i < RG; ++i)
+#pragma unroll
+        for (int w = 0; w < PPL; ++w)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int32_t idx = gi[i][w][h];
+            xv[i][w][h] = idx >= 0 ? __ldg(&fsc[idx]) * (float)__ldg(&r[idx]) : 0.0f;
+          }
+#pragma unroll
+      for (int i = 0; i < RG; ++i) {
+        float mx = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PPL; ++w) mx = fmaxf(mx, fmaxf(fabsf(xv[i][w][0]), fabsf(xv[i][w][1])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float im = mx > 0.0f ? 1.0f / mx : 0.0f;
+        float ss = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PPL; ++w) {
+          const float a0 = xv[i][w][0] * im, a1 = xv[i][w][1] * im;
+          ss = fmaf(a0, a0, fmaf(a1, a1, ss));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float sn = sqrtf(ss);  // ||x|| / max |x|
+        const float inv = mx > 0.0f ? im / sn : 0.0f;
+        const int row = r0 + i;
+#pragma unroll
+        for (int w = 0; w < PPL; ++w) {
+          const int kp = lane + 32 * w;
+          if (kp < NPAIR)
+            *reinterpret_cast<uint32_t*>(sX + canon(row, 2 * kp, DP) * 2) =
+                pack_bf16(xv[i][w][0] * inv, xv[i][w][1] * inv);
+        }
+        if (lane == 0) sscale[row] = mx * sn;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    // ---- the layers: one thread issues, everybody waits on the commit, the epilogue warps
+    //      read their lane quadrant back
+    if constexpr (W > 0) {
+#pragma unroll 1
+      for (int layer = 0; layer < 2 && !bad; ++layer) {
+        if (tid == 0) {
+          fence_after();
+          if (layer == 0)
+            issue_chain(tmem, sb + Lay::X, sb + Lay::W1, DP, W, false);
+          else
+            issue_chain(tmem, sb + Lay::H, sb + Lay::W2, W, W, false);
+          mma_commit(bar_m);
+        }
+        bad = __syncthreads_or(!bar_wait(bar_m, phase));
+        phase ^= 1u;
+        if (bad) break;
+        fence_after();
+        relu_to_image<W>(t_lane, erow, half, sH);
+        fence_before();
+        fence_proxy_async();
+        __syncthreads();
+      }
+      if (bad) break;
+    }
+    if (tid == 0) {
+      fence_after();
+      issue_chain(tmem, sb + Lay::X, sb + Lay::W0, DP, DP, false);  // skip term x W0
+      if constexpr (W > 0) issue_chain(tmem, sb + Lay::H, sb + Lay::W3, W, DP, true);
+      mma_commit(bar_m);
+    }
+    bad = __syncthreads_or(!bar_wait(bar_m, phase));
+    phase ^= 1u;
+    if (bad) break;
+    fence_after();
+    {
+      float* yrow = reinterpret_cast<float*>(smem + Lay::X) + erow * Lay::YS;
+#pragma unroll
+      for (int c = half * (DP / 2); c < (half + 1) * (DP / 2); c += 8) {
+        float v[8];
+        tmem_ld8(t_lane + (uint32_t)c, v);
+        *reinterpret_cast<float4*>(yrow + c) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(yrow + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
+    fence_before();
+    __syncthreads();
+
+    // ---- scatter: z += F s y, warp w rows 16 w .. 16 w + 15, lanes along the element's dofs,
+    //      RG rows at a time with their dof-map and scaling loads issued before the adds
+#pragma unroll 1
+    for (int r0 = 16 * warp; r0 < 16 * warp + 16; r0 += RG) {
+      int32_t gi[RG][PPL][2];
+#pragma unroll
+      for (int i = 0; i < RG; ++i) {
+        const int64_t e = tile * kRows + r0 + i;
+#pragma unroll
+        for (int w = 0; w < PPL; ++w)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = 2 * (lane + 32 * w) + h;
+            gi[i][w][h] = (k < din && e < ne) ? __ldg(&map[e * din + k]) : -1;
+          }
+      }
+      float fv[RG][PPL][2];
+#pragma unroll
+      for (int i = 0; i < RG; ++i)
+#pragma unroll
+        for (int w = 0; w < PPL; ++w)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            fv[i][w][h] = gi[i][w][h] >= 0 ? __ldg(&fsc[gi[i][w][h]]) : 0.0f;
+#pragma unroll
+      for (int i = 0; i < RG; ++i) {
+        const int row = r0 + i;
+        const float s = sscale[row];
+#pragma unroll
+        for (int w = 0; w < PPL; ++w)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = 2 * (lane + 32 * w) + h;
+            if (fv[i][w][h] != 0.0f)
+              atomicAdd(&z[gi[i][w][h]], (VT)(fv[i][w][h] * s * sY[row * Lay::YS + k]));
+          }
+      }
+    }
+    __syncthreads();  // the next tile's gather rewrites X (and the staging that aliases it)
+  }
+
+  // ---- teardown: a given-up wait is reported, in-flight MMAs get one more bounded wait, and
+  //      the TMEM is always freed
+  if (bad) {
+    if (tid == 0) atomicExch(fail, 1);
+    bar_wait(bar_m, phase);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, Lay::NCOLS);
+  }
+}
+
+}  // namespace mlptc
+}  // namespace fe

@@ -108,6 +108,9 @@ _SIGS = {
     "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_lpc_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "fe_lpc_get_kernel": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int)]),
     "fe_lpc_adam_step": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_sample_pairs": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64, _VP, _VP, _VP,
@@ -524,6 +527,20 @@ def fe_lpc_sample_pairs(lpc, din, reps=0, max_rows=1 << 16, stream=None):
 
 def fe_lpc_apply(lpc, dev_r, dev_z, stream=None):
     return _check(load().fe_lpc_apply(_VP(lpc), _ptr(dev_r), _ptr(dev_z), _stream(stream)))
+
+
+FE_LPC_KERNEL_AUTO, FE_LPC_KERNEL_TCGEN05, FE_LPC_KERNEL_MMA_SYNC, FE_LPC_KERNEL_GEMM = 0, 1, 2, 3
+
+
+def fe_lpc_set_kernel(lpc, kernel):
+    return _check(load().fe_lpc_set_kernel(_VP(lpc), int(kernel)))
+
+
+def fe_lpc_get_kernel(lpc):
+    """(the inference kernel in use, 1 if a tcgen05 launch has given up a wait else 0)."""
+    k, f = ctypes.c_int(), ctypes.c_int()
+    _check(load().fe_lpc_get_kernel(_VP(lpc), ctypes.byref(k), ctypes.byref(f)))
+    return k.value, f.value
 
 
 def fe_fcg(pa, op, lpc, dev_b, dev_x, rtol, maxit, stream=None):

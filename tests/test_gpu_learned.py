@@ -105,6 +105,93 @@ def test_patch_apply_matches_oracle(dims, p, width):
             fe.fe_lpc_destroy(lpc)
 
 
+@pytest.mark.parametrize("dims,p,width", [((9, 8, 7), 1, 64), ((5, 4, 3), 2, 128),
+                                          ((6, 5, 4), 3, 128), ((5, 5, 6), 3, 0),
+                                          ((3, 4, 3), 4, 64), ((4, 3, 3), 4, 128),
+                                          ((50, 50, 50), 1, 128)])
+def test_inference_kernels_match_oracle(dims, p, width):
+    """Every inference kernel built for (order, width) -- tcgen05 (one CTA per 128 elements, FP32
+    accumulators in tensor memory), the mma.sync fused kernel, the unfused GEMM path -- against
+    oracle/learned.py's patch operator element by element within its BF16 rounding bound. The
+    meshes leave a ragged last 128-element tile; at 50^3 the persistent tcgen05 grid takes
+    several tiles per CTA. No tcgen05 launch may give up a wait."""
+    torch = torch_cuda()
+    with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
+        prob = oop.Problem(*dims, p, V, coeff=c)
+        n, ne, _ = fe.fe_mesh_sizes(mesh)
+        din = (p + 1) ** 3
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 3)
+        try:
+            w = fe.fe_lpc_weights(lpc)
+            w[-din * din:] = 0.1 * np.random.default_rng(8).standard_normal(din * din)
+            fe.fe_lpc_weights(lpc, w)
+            default = fe.fe_lpc_get_kernel(lpc)[0]       # the fastest built one
+            assert default in (fe.FE_LPC_KERNEL_MMA_SYNC, fe.FE_LPC_KERNEL_TCGEN05)
+            r = torch.from_numpy(np.random.default_rng(4).standard_normal(n)).cuda()
+            Wb = tuple(ol.bf16_round(x) for x in unpack(w, din, width))
+            zr, zb = ol.patch_apply(prob, DIFFUSION, ol.network(Wb), r.cpu().numpy(),
+                                    bound=ol.network_rounding_bound(Wb))
+            tested = []
+            for k in (fe.FE_LPC_KERNEL_TCGEN05, fe.FE_LPC_KERNEL_MMA_SYNC, fe.FE_LPC_KERNEL_GEMM):
+                try:
+                    fe.fe_lpc_set_kernel(lpc, k)
+                except fe.FEError as e:
+                    assert e.status == fe.FE_ERR_UNSUPPORTED and k == fe.FE_LPC_KERNEL_MMA_SYNC
+                    continue
+                z = torch.full_like(r, float("nan"))
+                fe.fe_lpc_apply(lpc, r, z)
+                torch.cuda.synchronize()
+                zg = z.cpu().numpy()
+                assert np.all(np.abs(zg - zr) <= zb + 1e-13 * np.abs(zr).max()), k
+                assert rel_fro(zg, zr) <= 3e-2
+                assert np.all(zg[boundary_mask(*dims, p) == 1] == 0.0)
+                tested.append(k)
+            assert fe.FE_LPC_KERNEL_TCGEN05 in tested and fe.FE_LPC_KERNEL_GEMM in tested
+            assert fe.fe_lpc_get_kernel(lpc)[1] == 0
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
+def test_tcgen05_kernel_selection_errors_and_fp32_solve():
+    """Kernel choice errors (unknown id; tcgen05 asked for a width it is not built for); the
+    FP32-vector tcgen05 kernel inside fe_fcg_ir reaches the FP64 residual like the mma.sync one."""
+    torch = torch_cuda()
+    with gpu_problem(6, 6, 5, 2, sigma=1.0) as (fe, mesh, pa, V, c):
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 48, 1)       # width 48: no tcgen05 kernel
+        try:
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_lpc_set_kernel(lpc, fe.FE_LPC_KERNEL_TCGEN05)
+            assert e.value.status == fe.FE_ERR_UNSUPPORTED
+            with pytest.raises(fe.FEError) as e:
+                fe.fe_lpc_set_kernel(lpc, 7)
+            assert e.value.status == fe.FE_ERR_ARG
+            assert fe.fe_lpc_get_kernel(lpc)[0] != fe.FE_LPC_KERNEL_TCGEN05
+        finally:
+            fe.fe_lpc_destroy(lpc)
+    with gpu_problem(16, 16, 16, 3, ops=1) as (fe, mesh, pa, V, c):
+        fe.fe_pa_set_variant(pa, "f32x2")
+        n, _, _ = fe.fe_mesh_sizes(mesh)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 0, 4)
+        try:
+            fe.fe_lpc_fit_linear(lpc)
+            b = torch.empty(n, dtype=torch.float64, device="cuda")
+            fe.fe_load_vector_sine(pa, b)
+            res = {}
+            for k in (fe.FE_LPC_KERNEL_MMA_SYNC, fe.FE_LPC_KERNEL_TCGEN05):
+                fe.fe_lpc_set_kernel(lpc, k)
+                x = torch.empty_like(b)
+                st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, 1e-8, 20000)
+                assert st == fe.FE_OK, (k, fe.fe_last_error())
+                assert stats["true_rel_resid"] <= 1e-8
+                res[k] = x.cpu().numpy()
+            xt, xm = res[fe.FE_LPC_KERNEL_TCGEN05], res[fe.FE_LPC_KERNEL_MMA_SYNC]
+            assert np.abs(xt - xm).max() <= 1e-6 * np.abs(xm).max()
+            assert fe.fe_lpc_get_kernel(lpc)[1] == 0
+        finally:
+            fe.fe_lpc_destroy(lpc)
+
+
 @pytest.mark.parametrize("variant", ["f64", "f32x2"])
 @pytest.mark.parametrize("dims,p", [((5, 5, 5), 2), ((4, 5, 4), 3), ((4, 4, 4), 1),
                                     ((3, 3, 4), 5)])
