@@ -602,6 +602,32 @@ int fe_vspace_pcg_batched(fe_vspace* vs, int op, int nrhs, const double* dev_b, 
                           double* dev_x, int64_t ldx, double rtol, int maxit,
                           fe_pcg_stats* stats, void* stream);
 
+/* The learned patch preconditioner on a variable-order space (an extension; the paper has no
+ * learned part): one network per order, M(r) = E^T F_X sum_e R_e^T s_e f_p(e)(x_e / s_e) with
+ * x_e = R_e F_X E r, s_e = ||x_e||_2, R_e element e's rows of the local vector E r (true dofs
+ * and the constrained rows C r), and F_X = (mult_X diag_X)^(-1/2) on those rows: mult_X the
+ * number of element rows of every order that read the row, diag_X the sum of their element
+ * diagonals (0 on boundary rows; a constrained row is a boundary row when every true dof it
+ * interpolates is one); r is taken zero on the boundary.  With one order everywhere M is
+ * fe_lpc_apply's operator.
+ * fe_vspace_set_learned attaches to the order group `order` a copy of the weights of `trained`
+ * (an fe_lpc of that order, trained or fitted on a single-order mesh; the copy is owned by vs
+ * and recomputes F_X), or detaches it (trained = NULL); networks of another operator are
+ * dropped.  FE_ERR_ARG for an order the space does not contain or a network of another order.
+ * Synchronous. */
+int fe_vspace_set_learned(fe_vspace* vs, int op, int order, const fe_lpc* trained, void* stream);
+
+/* z = M(r) (FP64 device vectors of length ntrue, z overwritten, 0 on the boundary);
+ * FE_ERR_UNSUPPORTED unless every order has a network.  Asynchronous. */
+int fe_vspace_lpc_apply(fe_vspace* vs, const double* dev_r, double* dev_z, void* stream);
+
+/* Flexible CG (as fe_fcg) on the variable-order space with M, falling back to Jacobi (the diagonal
+ * of fe_vspace_diagonal) when it stalls; FP64 inner products and exit true residual with the
+ * FP64 operator.  FE_ERR_UNSUPPORTED unless every order has a network for op, or for the FP32
+ * variant.  Same statuses as fe_pcg.  Synchronous. */
+int fe_vspace_fcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
+                  int maxit, fe_pcg_stats* stats, void* stream);
+
 void fe_vspace_destroy(fe_vspace* vs);
 
 /* ---- The paper's own operator: the mixed H1 / L2 gradient and divergence blocks ------------

@@ -75,6 +75,77 @@ def patch_apply(prob, kind, f, r, bound=None):
     return z, zb
 
 
+def vspace_patch_apply(space, vertices, kind, nets, r, coeff=None, E=None, bounds=None,
+                       mats=None):
+    """M(r) on a variable-order space (oracle/varorder.VarSpace) with one network per order:
+
+        M(r) = E^T F sum_e R_e^T s_e f_p(e)(x_e / s_e),   x_e = R_e F E r,   s_e = ||x_e||_2,
+
+    in the local numbering X: a row of E with a single stored weight (a node that is a true
+    dof's node) is that true dof's row, shared by every element that reaches it; every other row
+    (a constrained node of one element) is its own row.  R_e picks element e's rows; F = (mult
+    diag)^-1/2 per X row, mult = the number of element rows mapped to it and diag = the sum of
+    their element-matrix diagonal entries, F = 0 on boundary rows (a boundary true dof, or a
+    constrained row whose stored weights all sit on boundary true dofs).  r is taken zero and the
+    result is zeroed on the boundary true dofs, so that M = (1-m) M (1-m); elements with s_e = 0
+    add nothing.  With one order everywhere this is
+    patch_apply's operator.  nets: {order: f(Xn, elems) -> Y}; E: the prolongation with the
+    sparsity to use (default: the space's own); bounds: optional {order: bound map} (as in
+    patch_apply), the second return value then bounds |M_computed - M| element-wise; mats: the
+    element matrices (space.element_matrices), when already computed."""
+    E = (space.prolongation() if E is None else E).tocsr()
+    nloc, ntrue = E.shape
+    mask = space.boundary_mask() == 1
+    nnz_row = np.diff(E.indptr)
+    xrow = np.empty(nloc, dtype=np.int64)
+    unit = nnz_row == 1
+    xrow[unit] = E.indices[E.indptr[:-1][unit]]
+    own = np.nonzero(~unit)[0]
+    xrow[own] = ntrue + np.arange(own.size)
+    nX = ntrue + own.size
+    maskX = np.zeros(nX, dtype=bool)
+    maskX[:ntrue] = mask
+    for t, i in enumerate(own):
+        cols = E.indices[E.indptr[i]:E.indptr[i + 1]]
+        maskX[ntrue + t] = bool(np.all(mask[cols]))
+    if mats is None:
+        mats = space.element_matrices(vertices, kind, coeff)
+    dloc = np.concatenate([np.diag(K) for K in mats])
+    mult = np.bincount(xrow, minlength=nX).astype(np.float64)
+    diag = np.bincount(xrow, weights=dloc, minlength=nX)
+    live_rows = (~maskX) & (mult > 0) & (diag > 0)
+    F = np.zeros(nX)
+    F[live_rows] = 1.0 / np.sqrt(mult[live_rows] * diag[live_rows])
+    Fl = F[xrow]                                   # the scaling of every element row
+    r_free = np.where(mask, 0.0, np.asarray(r, dtype=np.float64))
+    x_loc = Fl * (E @ r_free)
+    y_loc = np.zeros(nloc)
+    yb_loc = np.zeros(nloc)
+    first = space.local_first
+    for p in np.unique(space.order):
+        el = np.nonzero(space.order == p)[0]
+        D3 = (int(p) + 1) ** 3
+        rows = (first[el][:, None] + np.arange(D3)[None, :])          # [ne_p, D^3]
+        X = x_loc[rows]
+        s = np.linalg.norm(X, axis=1)
+        live = s > 0
+        if not np.any(live):
+            continue
+        Xn = X[live] / s[live, None]
+        Y = nets[int(p)](Xn, el[live])
+        y_loc[rows[live].reshape(-1)] = (Fl[rows[live]] * s[live, None] * Y).reshape(-1)
+        if bounds is not None:
+            yb_loc[rows[live].reshape(-1)] = (np.abs(Fl[rows[live]]) * s[live, None] *
+                                              bounds[int(p)](Xn, el[live])).reshape(-1)
+    z = E.T @ y_loc
+    z[mask] = 0.0
+    if bounds is None:
+        return z
+    zb = abs(E).T @ yb_loc
+    zb[mask] = 0.0
+    return z, zb
+
+
 def network(W):
     """The network f of the patch operator: oracle/mlp.py's forward pass in FP64 with the given
     (BF16) weights, the same for every element."""

@@ -43,6 +43,26 @@ bool make_l2_basis_1d(int p, int q, double* Bl);
 int apply_f32_vectors(const fe_pa* pa, int op, const float* x, float* y, cudaStream_t s,
                       const int* skip, double* dot_part);
 
+// Learned patch preconditioner hooks of the variable-order space (fe_learned.cu): z (+)= M(r) on
+// the handle's mesh numbering; shape; weight copy; external input/output scaling.
+int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s, bool accumulate);
+void lpc_shape(const fe_lpc* L, int* order, int* din, int* width);
+int lpc_copy_weights(fe_lpc* dst, const fe_lpc* src, cudaStream_t s);
+int lpc_set_scaling(fe_lpc* L, const double* F, cudaStream_t s);
+
+// Flexible CG (fe_learned.cu) on an arbitrary FP64 operator of n dofs with boundary mask `mask`:
+// apply (out = A in), prec (z = M(r), the learned preconditioner; FCG falls back to Jacobi with
+// dinv when it stalls), true_apply (the FP64 operator for the exit true residual).  Fills
+// *stats; returns the solver status (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_NAN)
+// or an error.  Synchronous.
+struct FcgOperator {
+  int64_t n = 0;
+  const uint8_t* mask = nullptr;
+  std::function<int(const double*, double*)> apply, prec, true_apply;
+};
+int fcg_solve(const FcgOperator& op, const double* dinv, const double* b, double* x, double rtol,
+              int maxit, cudaStream_t s, fe_pcg_stats* stats, const char* who);
+
 }  // namespace fe
 
 struct fe_mesh {

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,7 +41,7 @@
 using namespace fe;
 
 namespace fe {
-int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s);
+int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s, bool accumulate = false);
 }
 
 struct fe_lpc {
@@ -730,18 +731,20 @@ struct FcgResult {
 
 int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s);
 
-// FCG from x = 0; lpc == nullptr => Jacobi throughout.  Synchronous.  VT = double: the handle's
-// variant applies the operator and the true residual is computed at the end; VT = float: the
-// FP32 apply on float vectors (the inner solve of fe_fcg_ir), no true residual.  work: NULL, or
-// 4 n VT values plus reduction space of 2 kRB + S_N doubles (red) supplied by the caller.
+// FCG from x = 0 on an n-vector system with boundary mask `mask`.  apply: out = A in (out
+// overwritten); prec_learned: z = M(r) with the learned preconditioner, or empty for Jacobi
+// throughout (z = dinv r); true_apply: the FP64 operator for the exit true residual (VT = double
+// only).  snap_map: the element map the residual snapshots of the training data read through.
+// Synchronous.  work: NULL, or 4 n VT values plus reduction space of 2 kRB + S_N doubles (red)
+// supplied by the caller.
 template <class VT>
-int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, double rtol,
-            int maxit, Snapshots* snap, cudaStream_t s, FcgResult* res, VT* work = nullptr,
-            double* red_in = nullptr) {
+int fcg_core(int64_t n, const uint8_t* mask, const int32_t* snap_map,
+             const std::function<int(const VT*, VT*)>& apply,
+             const std::function<int(const VT*, VT*)>& prec_learned,
+             const std::function<int(const double*, double*)>& true_apply, const VT* dinv,
+             const VT* b, VT* x, double rtol, int maxit, Snapshots* snap, cudaStream_t s,
+             FcgResult* res, VT* work = nullptr, double* red_in = nullptr) {
   constexpr bool F64 = std::is_same<VT, double>::value;
-  const fe_mesh* m = pa->mesh;
-  const int64_t n = m->ndofs;
-  const uint8_t* mask = m->d_mask;
   VT* vec = work;
   double* red = red_in;
   cudaError_t err;
@@ -754,32 +757,20 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
   VT *r = vec, *z = vec + n, *p = vec + 2 * n, *q = vec + 3 * n;
   double *part0 = red, *part1 = red + kRB, *sc = red + 2 * kRB;
   int st = FE_OK;
-  bool learned = lpc != nullptr;
+  bool learned = static_cast<bool>(prec_learned);
   size_t next_snap = 0;
   auto precond = [&]() -> int {
     res->launches += learned ? 2 : 1;
-    if (learned) {
-      if constexpr (F64)
-        return fe::lpc_apply(lpc, r, z, s);
-      else
-        return lpc_apply32(lpc, r, z, s);
-    }
+    if (learned) return prec_learned(r, z);
     k_fcg_jacobi<VT><<<kRB, kT, 0, s>>>(dinv, r, z, n);
     return FE_OK;
-  };
-  auto apply = [&](const VT* in, VT* out) -> int {  // out = A in (out overwritten)
-    if constexpr (F64) {
-      return apply_dispatch(pa, op, pa->variant, in, out, s);
-    } else {
-      return apply_f32_vectors(pa, op, in, out, s, nullptr, nullptr);  // out zeroed by k_fcg_p
-    }
   };
   auto take_snap = [&](int it) {
     if constexpr (F64) {
       if (!snap) return;
       while (next_snap < snap->at.size() && snap->at[next_snap] == it) {
         k_snap<<<(unsigned int)(((int64_t)snap->ns * snap->din + kT - 1) / kT), kT, 0, s>>>(
-            r, m->d_map, snap->elems, snap->ns, snap->din,
+            r, snap_map, snap->elems, snap->ns, snap->din,
             snap->out + (int64_t)next_snap * snap->ns * snap->din);
         ++next_snap;
       }
@@ -877,7 +868,7 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
   res->rel = rel;
   if constexpr (F64) {
     if (st == FE_OK) {  // true residual with the FP64 operator (FP64 data and arithmetic)
-      if ((st = apply_dispatch(pa, op, FE_VARIANT_F64, x, q, s)) == FE_OK) {
+      if ((st = true_apply(x, q)) == FE_OK) {
         k_fcg_resid<<<kRB, kT, 0, s>>>(b, q, mask, n, part0, part1);
         k_fcg_finish<<<1, kRB, 0, s>>>(part0, part1, sc, 4);
         res->launches += 3;
@@ -889,6 +880,36 @@ int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, 
   if (!work) cudaFree(vec);
   if (!red_in) cudaFree(red);
   return st;
+}
+
+// FCG on a single-order handle: its operator (the handle's variant; FP32 data on float vectors),
+// lpc's preconditioner or Jacobi (lpc == nullptr), the FP64 operator for the true residual.
+template <class VT>
+int fcg_run(fe_pa* pa, int op, fe_lpc* lpc, const VT* dinv, const VT* b, VT* x, double rtol,
+            int maxit, Snapshots* snap, cudaStream_t s, FcgResult* res, VT* work = nullptr,
+            double* red_in = nullptr) {
+  constexpr bool F64 = std::is_same<VT, double>::value;
+  const fe_mesh* m = pa->mesh;
+  std::function<int(const VT*, VT*)> apply = [&](const VT* in, VT* out) -> int {
+    if constexpr (F64)
+      return apply_dispatch(pa, op, pa->variant, in, out, s);
+    else
+      return apply_f32_vectors(pa, op, in, out, s, nullptr, nullptr);  // out zeroed by k_fcg_p
+  };
+  std::function<int(const VT*, VT*)> prec;
+  if (lpc) {
+    prec = [&](const VT* r, VT* z) -> int {
+      if constexpr (F64)
+        return fe::lpc_apply(lpc, r, z, s);
+      else
+        return lpc_apply32(lpc, r, z, s);
+    };
+  }
+  std::function<int(const double*, double*)> true_apply = [&](const double* in, double* out) {
+    return apply_dispatch(pa, op, FE_VARIANT_F64, in, out, s);
+  };
+  return fcg_core<VT>(m->ndofs, m->d_mask, m->d_map, apply, prec, true_apply, dinv, b, x, rtol,
+                      maxit, snap, s, res, work, red_in);
 }
 
 // r = (1-m)(b - q) into rout; partials ||r||^2 and ||(1-m) b||^2 (the outer residual of fe_fcg_ir)
@@ -1329,21 +1350,22 @@ int lpc_apply32(fe_lpc* L, const float* r, float* z, cudaStream_t s) {
 }  // namespace
 
 namespace fe {
-// z = M(r): the learned additive patch preconditioner (z overwritten).
-int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
+// z = M(r): the learned additive patch preconditioner (z overwritten, or z += M(r) when
+// accumulating).
+int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s, bool accumulate) {
   const fe_mesh* m = L->pa->mesh;
   const int din = L->din;
   const int kernel = lpc_kernel(L, false);
   if (kernel == FE_LPC_KERNEL_TCGEN05) {
     cudaError_t err;
-    if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+    if (!accumulate && (err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
       return cuda_error(err, "fe_lpc_apply: zero z");
     tc_pack(L, s);
     return cuda_error(tc_run<double>(L, r, z, L->tc_grid, s), "fe_lpc_apply: tcgen05 launch");
   }
   if (kernel == FE_LPC_KERNEL_MMA_SYNC) {
     cudaError_t err;
-    if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+    if (!accumulate && (err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
       return cuda_error(err, "fe_lpc_apply: zero z");
     const int DP = mlp::fused_dp(din);
     if (!L->wimg_ok) {
@@ -1358,7 +1380,7 @@ int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
   int st = ensure_workspace(L, chunk);
   if (st != FE_OK) return st;
   cudaError_t err;
-  if ((err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
+  if (!accumulate && (err = cudaMemsetAsync(z, 0, sizeof(double) * m->ndofs, s)) != cudaSuccess)
     return cuda_error(err, "fe_lpc_apply: zero z");
   for (int64_t e0 = 0; e0 < m->ne; e0 += chunk) {
     const int64_t rows = (m->ne - e0) < chunk ? (m->ne - e0) : chunk;
@@ -1369,6 +1391,63 @@ int lpc_apply(fe_lpc* L, const double* r, double* z, cudaStream_t s) {
                                                                            L->fsc, e0, rows, din, z);
   }
   return cuda_error(cudaGetLastError(), "fe_lpc_apply launch");
+}
+
+int fcg_solve(const FcgOperator& op, const double* dinv, const double* b, double* x, double rtol,
+              int maxit, cudaStream_t s, fe_pcg_stats* stats, const char* who) {
+  const auto t0 = std::chrono::steady_clock::now();
+  FcgResult res;
+  const int st = fcg_core<double>(op.n, op.mask, nullptr, op.apply, op.prec, op.true_apply, dinv,
+                                  b, x, rtol, maxit, nullptr, s, &res);
+  if (st != FE_OK) return st;
+  if (stats) {
+    stats->iters = res.iters;
+    stats->rel_resid = res.rel;
+    stats->true_rel_resid = res.true_rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->launches = res.launches;
+    stats->outer_iters = 1 + res.restarts;
+  }
+  switch (res.status) {
+    case FE_OK:
+      return FE_OK;
+    case FE_ERR_BREAKDOWN:
+      return set_error(FE_ERR_BREAKDOWN, std::string(who) + ": p.Ap <= 0");
+    case FE_ERR_NAN:
+      return set_error(FE_ERR_NAN, std::string(who) + ": NaN or Inf in the iteration");
+    default:
+      return set_error(FE_ERR_NOT_CONVERGED, std::string(who) + ": maxit reached before rtol");
+  }
+}
+
+// Order, patch size D^3 and width of a handle.
+void lpc_shape(const fe_lpc* L, int* order, int* din, int* width) {
+  if (order) *order = L->pa->p;
+  if (din) *din = L->din;
+  if (width) *width = L->width;
+}
+
+// dst's weights := src's (same patch size and width); the inference images are rebuilt on use.
+int lpc_copy_weights(fe_lpc* dst, const fe_lpc* src, cudaStream_t s) {
+  if (dst->din != src->din || dst->width != src->width)
+    return set_error(FE_ERR_ARG, "learned preconditioner: patch size or width differ");
+  cudaError_t err = cudaMemcpyAsync(dst->w32, src->w32, 4 * (size_t)src->nparam,
+                                    cudaMemcpyDeviceToDevice, s);
+  if (err != cudaSuccess) return cuda_error(err, "learned preconditioner: weight copy");
+  k_to_bf16<<<grid1(dst->nparam), kT, 0, s>>>(dst->w32, dst->wb, dst->nparam);
+  dst->wimg_ok = false;
+  dst->tcimg_ok = false;
+  return cuda_error(cudaGetLastError(), "learned preconditioner: weight copy");
+}
+
+// The input/output scaling F of the patch operator (FP64 [ndofs], 0 on masked dofs) replaced by
+// a caller's (the shared scaling of a variable-order space).
+int lpc_set_scaling(fe_lpc* L, const double* F, cudaStream_t s) {
+  const int64_t n = L->pa->mesh->ndofs;
+  cudaError_t err = cudaMemcpyAsync(L->fsc, F, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (err != cudaSuccess) return cuda_error(err, "learned preconditioner: scaling");
+  k_to_f32<<<grid1(n), kT, 0, s>>>(L->fsc, L->fsc32, n, 0);
+  return cuda_error(cudaGetLastError(), "learned preconditioner: scaling");
 }
 }  // namespace fe
 

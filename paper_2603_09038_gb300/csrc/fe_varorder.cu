@@ -628,16 +628,26 @@ struct fe_vspace {
   int64_t group_off[kMaxOrder];         // first E-vector row of the group
   fe_mesh* group_mesh[kMaxOrder];
   fe_pa* group_pa[kMaxOrder];
+  // learned patch preconditioner: one network per order group (copies of networks trained on
+  // single-order meshes), applied in the X numbering with one shared input/output scaling
+  uint8_t* d_maskX = nullptr;           // [ntrue + nc]: boundary rows of X (a constrained row when
+                                        // every true dof it interpolates is a boundary dof)
+  fe_lpc* group_lpc[kMaxOrder] = {};    // owned
+  int lpc_op = 0;
+  double* d_FX = nullptr;               // [ntrue + nc]: the shared scaling (mult_X diag_X)^(-1/2)
+  double* d_rm = nullptr;               // [ntrue]: the preconditioner's masked input
 };
 
 namespace {
 
 void vspace_free(fe_vspace* vs) {
   for (int g = 0; g < vs->ngroups; ++g) {
+    fe_lpc_destroy(vs->group_lpc[g]);
     fe_pa_destroy(vs->group_pa[g]);
     if (vs->group_mesh[g]) {
       vs->group_mesh[g]->d_vertices = nullptr;  // shared, freed below
       vs->group_mesh[g]->d_map = nullptr;       // a slice of vs->d_map
+      vs->group_mesh[g]->d_mask = nullptr;      // vs->d_maskX, freed below
       fe_mesh_destroy(vs->group_mesh[g]);
     }
   }
@@ -651,6 +661,9 @@ void vspace_free(fe_vspace* vs) {
   cudaFree(vs->d_tcol);
   cudaFree(vs->d_tval);
   cudaFree(vs->d_mask);
+  cudaFree(vs->d_maskX);
+  cudaFree(vs->d_FX);
+  cudaFree(vs->d_rm);
   cudaFree(vs->d_X);
   cudaFree(vs->d_Y);
   cudaFree(vs->d_zero);
@@ -752,6 +765,18 @@ static int vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   if (err == cudaSuccess) err = upload(&vs->d_tcol, H.tcol);
   if (err == cudaSuccess) err = upload(&vs->d_tval, H.tval);
   if (err == cudaSuccess) err = upload(&vs->d_mask, mask);
+  if (err == cudaSuccess) {
+    // X rows on the boundary: true dofs by the mask, constrained rows when all of theirs are
+    std::vector<uint8_t> maskX(mask.begin(), mask.end());
+    maskX.resize((size_t)nX, 1);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int64_t k = H.cptr[c]; k < H.cptr[c + 1]; ++k)
+        if (!mask[H.ccol[k]]) {
+          maskX[T.ntrue + c] = 0;
+          break;
+        }
+    err = upload(&vs->d_maskX, maskX);
+  }
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_X, sizeof(double) * std::max<int64_t>(1, nX));
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_Y, sizeof(double) * std::max<int64_t>(1, nX));
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_zero, sizeof(int));
@@ -791,6 +816,7 @@ static int vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
     cudaGetDevice(&m->device);
     m->d_vertices = vs->d_vertices;
     m->d_map = vs->d_map + vs->group_off[g];
+    m->d_mask = vs->d_maskX;
     err = upload(&m->d_elem_ids, ids);
     double* dc = nullptr;
     if (err == cudaSuccess && host_coeff) err = upload(&dc, coeff);
@@ -1266,6 +1292,201 @@ int fe_vspace_pcg_batched(fe_vspace* vs, int op, int nrhs, const double* dev_b, 
 
 void fe_vspace_destroy(fe_vspace* vs) {
   if (vs) vspace_free(vs);
+}
+
+}  // extern "C"
+
+// ---- the learned patch preconditioner on a variable-order space: M(r) = E^T F_X
+//      sum_e R_e^T s_e f_p(e)(x_e / s_e), x_e = R_e F_X E r, one network f_p per order (the
+//      order group's copy of a network trained on a single-order mesh), R_e the element's rows
+//      of X = [r; C r], F_X the shared scaling (mult_X diag_X)^(-1/2) of the X rows: mult_X counts
+//      the element rows of every order mapped to an X row, diag_X sums their element diagonals
+//      (0 on boundary X rows).  With one order everywhere this is the single-order operator.
+namespace {
+
+__global__ void k_count_rows(const int32_t* __restrict__ map, int64_t n, double* __restrict__ c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&c[map[i]], 1.0);
+}
+
+__global__ void k_fx(const double* __restrict__ mult, const double* __restrict__ diag,
+                     const uint8_t* __restrict__ mask, double* __restrict__ F, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double m = mult[i], d = diag[i];
+    F[i] = (mask[i] || !(m > 0.0) || !(d > 0.0)) ? 0.0 : 1.0 / sqrt(m * d);
+  }
+}
+
+__global__ void k_mask_copy(const double* __restrict__ r, const uint8_t* __restrict__ mask,
+                            double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = mask[i] ? 0.0 : r[i];
+}
+
+__global__ void k_mask_zero(double* __restrict__ z, const uint8_t* __restrict__ mask, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (mask[i]) z[i] = 0.0;
+}
+
+// F_X for operator op, handed to every attached group network.
+int vspace_lpc_scaling(fe_vspace* vs, int op, cudaStream_t s) {
+  const int64_t nX = vs->ntrue + vs->nc;
+  cudaError_t err = cudaSuccess;
+  if (!vs->d_FX && (err = cudaMalloc(&vs->d_FX, sizeof(double) * nX)) != cudaSuccess) {
+    vs->d_FX = nullptr;
+    return cuda_error(err, "fe_vspace_set_learned: scaling cudaMalloc");
+  }
+  double* mult = nullptr;
+  if ((err = cudaMalloc(&mult, sizeof(double) * nX)) != cudaSuccess)
+    return cuda_error(err, "fe_vspace_set_learned: scaling cudaMalloc");
+  int st = FE_OK;
+  cudaMemsetAsync(mult, 0, sizeof(double) * nX, s);
+  k_count_rows<<<grid_of(vs->nlocal), 256, 0, s>>>(vs->d_map, vs->nlocal, mult);
+  cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * nX, s);
+  for (int g = 0; g < vs->ngroups && st == FE_OK; ++g)
+    st = diagonal_accumulate(vs->group_pa[g], op, vs->d_Y, s);
+  if (st == FE_OK) {
+    k_fx<<<grid_of(nX), 256, 0, s>>>(mult, vs->d_Y, vs->d_maskX, vs->d_FX, nX);
+    for (int g = 0; g < vs->ngroups && st == FE_OK; ++g)
+      if (vs->group_lpc[g]) st = lpc_set_scaling(vs->group_lpc[g], vs->d_FX, s);
+  }
+  if (st == FE_OK) st = cuda_error(cudaStreamSynchronize(s), "fe_vspace_set_learned: scaling");
+  cudaFree(mult);
+  return st;
+}
+
+bool vspace_lpc_complete(const fe_vspace* vs, int op) {
+  if (vs->lpc_op != op) return false;
+  for (int g = 0; g < vs->ngroups; ++g)
+    if (!vs->group_lpc[g]) return false;
+  return true;
+}
+
+// z = M(r) on true dofs: r taken zero and z zeroed on the boundary (M = (1-m) M (1-m)).
+int vspace_lpc_apply(fe_vspace* vs, const double* r, double* z, cudaStream_t s) {
+  cudaError_t err0;
+  if (!vs->d_rm && (err0 = cudaMalloc(&vs->d_rm, sizeof(double) * vs->ntrue)) != cudaSuccess) {
+    vs->d_rm = nullptr;
+    return cuda_error(err0, "fe_vspace: learned preconditioner workspace");
+  }
+  k_mask_copy<<<grid_of(vs->ntrue), 256, 0, s>>>(r, vs->d_mask, vs->d_rm, vs->ntrue);
+  int st = fill_X(vs, vs->d_rm, s);
+  if (st != FE_OK) return st;
+  cudaError_t err = cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * (vs->ntrue + vs->nc), s);
+  if (err != cudaSuccess) return cuda_error(err, "fe_vspace: zero Y");
+  for (int g = 0; g < vs->ngroups; ++g)
+    if ((st = lpc_apply(vs->group_lpc[g], vs->d_X, vs->d_Y, s, true)) != FE_OK) return st;
+  if ((st = fold_Y(vs, z, 0, s)) != FE_OK) return st;
+  k_mask_zero<<<grid_of(vs->ntrue), 256, 0, s>>>(z, vs->d_mask, vs->ntrue);
+  return cuda_error(cudaGetLastError(), "fe_vspace: learned preconditioner");
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_vspace_set_learned(fe_vspace* vs, int op, int order, const fe_lpc* trained, void* stream) {
+  clear_error();
+  if (!vs) return set_error(FE_ERR_ARG, "fe_vspace_set_learned: vs is NULL");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_set_learned: bad op");
+  if (!(vs->ops & op))
+    return set_error(FE_ERR_ARG, "fe_vspace_set_learned: operator not set up in fe_vspace_setup");
+  int g = -1;
+  for (int k = 0; k < vs->ngroups; ++k)
+    if (vs->group_p[k] == order) g = k;
+  if (g < 0) return set_error(FE_ERR_ARG, "fe_vspace_set_learned: no element of this order");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (vs->lpc_op != op) {  // networks of another operator are dropped
+    for (int k = 0; k < vs->ngroups; ++k) {
+      fe_lpc_destroy(vs->group_lpc[k]);
+      vs->group_lpc[k] = nullptr;
+    }
+    vs->lpc_op = op;
+  }
+  if (!trained) {
+    fe_lpc_destroy(vs->group_lpc[g]);
+    vs->group_lpc[g] = nullptr;
+    return FE_OK;
+  }
+  int to = 0, tdin = 0, tw = 0;
+  lpc_shape(trained, &to, &tdin, &tw);
+  if (to != order) return set_error(FE_ERR_ARG, "fe_vspace_set_learned: network of another order");
+  int cw = -1;
+  if (vs->group_lpc[g]) lpc_shape(vs->group_lpc[g], nullptr, nullptr, &cw);
+  if (cw != tw) {
+    fe_lpc_destroy(vs->group_lpc[g]);
+    vs->group_lpc[g] = nullptr;
+    int st = fe_lpc_create(vs->group_pa[g], op, tw, 1, &vs->group_lpc[g]);
+    if (st != FE_OK) {
+      vs->group_lpc[g] = nullptr;
+      return st;
+    }
+  }
+  int st = lpc_copy_weights(vs->group_lpc[g], trained, s);
+  if (st == FE_OK) st = vspace_lpc_scaling(vs, op, s);
+  return st;
+}
+
+int fe_vspace_lpc_apply(fe_vspace* vs, const double* dev_r, double* dev_z, void* stream) {
+  clear_error();
+  if (!vs || !dev_r || !dev_z) return set_error(FE_ERR_ARG, "fe_vspace_lpc_apply: null argument");
+  if (!vspace_lpc_complete(vs, vs->lpc_op))
+    return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_lpc_apply: a network is missing for an order");
+  return vspace_lpc_apply(vs, dev_r, dev_z, (cudaStream_t)stream);
+}
+
+int fe_vspace_fcg(fe_vspace* vs, int op, const double* dev_b, double* dev_x, double rtol,
+                  int maxit, fe_pcg_stats* stats, void* stream) {
+  clear_error();
+  if (stats) *stats = fe_pcg_stats{0, 0.0, 0.0, 0.0, 0, 0};
+  if (!vs || !dev_b || !dev_x) return set_error(FE_ERR_ARG, "fe_vspace_fcg: null argument");
+  if (op != FE_DIFFUSION && op != FE_MASS) return set_error(FE_ERR_ARG, "fe_vspace_fcg: bad op");
+  if (!(vs->ops & op)) return set_error(FE_ERR_ARG, "fe_vspace_fcg: operator not set up");
+  if (maxit < 1 || !(rtol >= 0.0)) return set_error(FE_ERR_ARG, "fe_vspace_fcg: bad rtol or maxit");
+  if (!vspace_lpc_complete(vs, op))
+    return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_fcg: attach a network to every order first "
+                                         "(fe_vspace_set_learned)");
+  for (int g = 0; g < vs->ngroups; ++g)
+    if (vs->group_pa[g]->variant == FE_VARIANT_F32)
+      return set_error(FE_ERR_UNSUPPORTED, "fe_vspace_fcg: the FP32 variant is not FP64-accurate");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = vs->ntrue;
+  double *dinv = nullptr, *diag = nullptr;
+  int* flag = nullptr;
+  cudaError_t err;
+  if ((err = cudaMalloc(&dinv, sizeof(double) * n)) != cudaSuccess ||
+      (err = cudaMalloc(&diag, sizeof(double) * n)) != cudaSuccess ||
+      (err = cudaMalloc(&flag, sizeof(int))) != cudaSuccess) {
+    cudaFree(dinv);
+    cudaFree(diag);
+    return cuda_error(err, "fe_vspace_fcg: cudaMalloc");
+  }
+  // the Jacobi fallback's inverse diagonal of E^T diag(A_E) E (0 on the boundary)
+  int st = fe_vspace_diagonal(vs, op, diag, stream);
+  if (st == FE_OK) {
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    k_vs_dinv<<<grid_of(n), 256, 0, s>>>(diag, vs->d_mask, dinv, n, flag);
+    st = cuda_error(cudaGetLastError(), "fe_vspace_fcg: diagonal");
+  }
+  if (st == FE_OK) {
+    FcgOperator A;
+    A.n = n;
+    A.mask = vs->d_mask;
+    A.apply = [&](const double* in, double* out) { return vspace_apply(vs, op, -1, in, out, s); };
+    A.prec = [&](const double* r, double* z) { return vspace_lpc_apply(vs, r, z, s); };
+    A.true_apply = [&](const double* in, double* out) {
+      return vspace_apply(vs, op, FE_VARIANT_F64, in, out, s);
+    };
+    st = fcg_solve(A, dinv, dev_b, dev_x, rtol, maxit, s, stats, "fe_vspace_fcg");
+  }
+  cudaFree(dinv);
+  cudaFree(diag);
+  cudaFree(flag);
+  return st;
 }
 
 }  // extern "C"

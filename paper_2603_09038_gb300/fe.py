@@ -108,6 +108,10 @@ _SIGS = {
     "fe_lpc_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_double)]),
     "fe_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_vspace_set_learned": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    "fe_vspace_lpc_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fe_vspace_fcg": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(fe_pcg_stats), _VP]),
     "fe_lpc_set_kernel": (ctypes.c_int, [_VP, ctypes.c_int]),
     "fe_lpc_get_kernel": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -530,6 +534,26 @@ def fe_lpc_apply(lpc, dev_r, dev_z, stream=None):
 
 
 FE_LPC_KERNEL_AUTO, FE_LPC_KERNEL_TCGEN05, FE_LPC_KERNEL_MMA_SYNC, FE_LPC_KERNEL_GEMM = 0, 1, 2, 3
+
+
+def fe_vspace_set_learned(vs, op, order, trained, stream=None):
+    """Attach a copy of a trained single-order network to the order group (None detaches)."""
+    return _check(load().fe_vspace_set_learned(_VP(vs), int(op), int(order),
+                                               _VP(trained) if trained else None, _stream(stream)))
+
+
+def fe_vspace_lpc_apply(vs, dev_r, dev_z, stream=None):
+    return _check(load().fe_vspace_lpc_apply(_VP(vs), _ptr(dev_r), _ptr(dev_z), _stream(stream)))
+
+
+def fe_vspace_fcg(vs, op, dev_b, dev_x, rtol, maxit, stream=None):
+    """Flexible CG with the attached networks; same return value as fe_pcg."""
+    st = fe_pcg_stats()
+    status = load().fe_vspace_fcg(_VP(vs), int(op), _ptr(dev_b), _ptr(dev_x), float(rtol),
+                                  int(maxit), ctypes.byref(st), _stream(stream))
+    if status in (FE_ERR_ARG, FE_ERR_CUDA, FE_ERR_OOM, FE_ERR_UNSUPPORTED):
+        _check(status)
+    return status, _stats(st)
 
 
 def fe_lpc_set_kernel(lpc, kernel):

@@ -306,3 +306,77 @@ def test_batched_apply_and_pcg_match_single(persistent):
             assert float((Xs[j] - x1).abs().max()) <= 1e-7 * float(x1.abs().max())
     finally:
         fe.fe_vspace_destroy(vs)
+
+
+def _unpack(w, din, width):
+    n1, n2 = din * width, width * width
+    n3 = n1 + n2 + width * din
+    return (w[:n1].reshape(din, width), w[n1:n1 + n2].reshape(width, width),
+            w[n1 + n2:n3].reshape(width, din), w[n3:].reshape(din, din))
+
+
+def test_learned_preconditioner_on_the_variable_order_space():
+    """One network per order (orders 2, 4, 6: widths 64, 64 and the linear map for order 6, which
+    runs the unfused GEMM path), copied from single-order handles: fe_vspace_lpc_apply against
+    the oracle's variable-order patch operator element by element within its BF16 rounding
+    bound; flexible CG with it reaches the FP64 residual and the Jacobi-PCG solution; the error
+    paths (an order missing, a network of another order, an order the space lacks)."""
+    from oracle import learned as ol
+    from tests.gpu_util import gpu_problem
+    torch = torch_cuda()
+    fe = lib()
+    name = "blocks_2_4_6"
+    dims, orders, V, c = _setup(name)
+    S, E = _oracle(name)
+    E = E.tocsr(copy=True)
+    E.data[np.abs(E.data) <= 1e-13] = 0.0   # the library's documented sparsity rule
+    E.eliminate_zeros()
+    vs = fe.fe_vspace_setup(*dims, orders, V, c)
+    rng = np.random.default_rng(21)
+    nets, bounds = {}, {}
+    try:
+        ntrue, _, _ = fe.fe_vspace_sizes(vs)
+        b = torch.from_numpy(uniform_vector(ntrue, seed=8)).cuda()
+        x = torch.empty_like(b)
+        for p, width in ((2, 64), (4, 64), (6, 0)):
+            if p == 6:   # not every order attached yet
+                with pytest.raises(fe.FEError) as e:
+                    fe.fe_vspace_fcg(vs, fe.FE_DIFFUSION, b, x, 1e-8, 10)
+                assert e.value.status == fe.FE_ERR_UNSUPPORTED
+            with gpu_problem(3, 3, 3, p) as (_, mesh, pa, _V, _c):
+                lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 10 + p)
+                try:
+                    din = (p + 1) ** 3
+                    w = fe.fe_lpc_weights(lpc)
+                    w[-din * din:] = 0.1 * rng.standard_normal(din * din)
+                    fe.fe_lpc_weights(lpc, w)
+                    with pytest.raises(fe.FEError) as e:      # a network of another order
+                        fe.fe_vspace_set_learned(vs, fe.FE_DIFFUSION, 2 if p != 2 else 4, lpc)
+                    assert e.value.status == fe.FE_ERR_ARG
+                    fe.fe_vspace_set_learned(vs, fe.FE_DIFFUSION, p, lpc)
+                    Wb = tuple(ol.bf16_round(a) for a in _unpack(w, din, width))
+                    nets[p] = ol.network(Wb)
+                    bounds[p] = ol.network_rounding_bound(Wb)
+                finally:
+                    fe.fe_lpc_destroy(lpc)
+        with pytest.raises(fe.FEError) as e:                  # no element of order 3 here
+            fe.fe_vspace_set_learned(vs, fe.FE_DIFFUSION, 3, None)
+        assert e.value.status == fe.FE_ERR_ARG
+        r = torch.from_numpy(np.random.default_rng(4).standard_normal(ntrue)).cuda()
+        z = torch.full_like(r, float("nan"))
+        fe.fe_vspace_lpc_apply(vs, r, z)
+        torch.cuda.synchronize()
+        zg = z.cpu().numpy()
+        zr, zb = ol.vspace_patch_apply(S, V, DIFFUSION, nets, r.cpu().numpy(), coeff=c, E=E,
+                                       bounds=bounds)
+        assert np.abs(zr).max() > 0
+        assert np.all(np.abs(zg - zr) <= zb + 1e-13 * np.abs(zr).max())
+        st, sf = fe.fe_vspace_fcg(vs, fe.FE_DIFFUSION, b, x, 1e-8, 5000)
+        assert st == fe.FE_OK, fe.fe_last_error()
+        assert sf["true_rel_resid"] <= 1e-8
+        xj = torch.empty_like(b)
+        st, sj = fe.fe_vspace_pcg(vs, fe.FE_DIFFUSION, b, xj, 1e-8, 5000)
+        assert st == fe.FE_OK
+        assert (x - xj).abs().max().item() <= 1e-6 * xj.abs().max().item()
+    finally:
+        fe.fe_vspace_destroy(vs)

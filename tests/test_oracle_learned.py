@@ -129,3 +129,66 @@ def test_adam_closed_forms():
     for t in range(1, 6):
         w, m, v = ol.adam_step(w, np.full(50, 0.3), m, v, t, lr)
     assert np.allclose(w, w0 - 5 * lr, rtol=0, atol=1e-9)
+
+
+def _lattice_perm(S, nx, ny, nz, p):
+    """perm[i] = the variable-order space's true dof at the single-order mesh's dof i (matched by
+    lattice coordinates)."""
+    from oracle.quadrature import gauss_lobatto
+    t = gauss_lobatto(p + 1)
+
+    def coord(I, n):
+        e = np.minimum(I // p, n - 1)
+        return e + t[I - e * p]
+    N = [nx * p + 1, ny * p + 1, nz * p + 1]
+    K, J, I = np.meshgrid(np.arange(N[2]), np.arange(N[1]), np.arange(N[0]), indexing="ij")
+    mc = np.stack([coord(I.reshape(-1), nx), coord(J.reshape(-1), ny), coord(K.reshape(-1), nz)], 1)
+    key = {tuple(np.round(c, 9)): k for k, c in enumerate(S.true_lattice_coords())}
+    return np.array([key[tuple(np.round(c, 9))] for c in mc])
+
+
+def test_vspace_patch_operator_reduces_to_the_single_order_one():
+    """With one order on every element the variable-order patch operator (the X numbering, the
+    shared scaling (mult diag)^-1/2, the constrained-row mask) is patch_apply's, dof by dof."""
+    from oracle.varorder import VarSpace
+    dims, p = (3, 2, 3), 2
+    prob = _prob(dims, p, sigma=1.0)
+    S = VarSpace(*dims, np.full(int(np.prod(dims)), p, dtype=np.int32))
+    perm = _lattice_perm(S, *dims, p)
+    din = (p + 1) ** 3
+    rng = np.random.default_rng(3)
+    W = omlp.init_weights(din, 16, 3)
+    W = (W[0], W[1], W[2], W[3] + 0.1 * rng.standard_normal(W[3].shape))
+    r = rng.standard_normal(prob.ndofs)
+    zs = ol.patch_apply(prob, DIFFUSION, ol.network(W), r)
+    rv = np.zeros(S.ntrue)
+    rv[perm] = r
+    zv = ol.vspace_patch_apply(S, prob.vertices, DIFFUSION, {p: ol.network(W)}, rv,
+                               coeff=prob.coeff)
+    assert np.abs(zv[perm] - zs).max() <= 1e-12 * np.abs(zs).max()
+
+
+def test_vspace_patch_operator_symmetric_for_a_symmetric_linear_map():
+    """f(x) = x W0 with W0 symmetric per order: M = E^T F (sum_e R_e^T W0 R_e) F E is symmetric on
+    a mixed-order space with constrained nodes (built column by column)."""
+    from oracle.varorder import VarSpace
+    from paper_2603_09038_gb300.inputs import block_orders
+    dims = (2, 2, 2)
+    orders = block_orders(*dims, block=1, orders=(1, 2, 3), seed=4)
+    S = VarSpace(*dims, orders)
+    V = perturbed_vertices(*dims, seed=5)
+    rng = np.random.default_rng(6)
+    nets = {}
+    for p in np.unique(orders):
+        d = (int(p) + 1) ** 3
+        A = rng.standard_normal((d, d))
+        W0 = A + A.T
+        nets[int(p)] = (lambda W0_: (lambda Xn, el: Xn @ W0_))(W0)
+    n = S.ntrue
+    E, mats = S.prolongation(), S.element_matrices(V, DIFFUSION)
+    M = np.stack([ol.vspace_patch_apply(S, V, DIFFUSION, nets, np.eye(n)[j], E=E, mats=mats)
+                  for j in range(n)], 1)
+    assert np.abs(M).max() > 0
+    assert np.abs(M - M.T).max() <= 1e-11 * np.abs(M).max()
+    interior = S.boundary_mask() == 0
+    assert np.all(M[~interior] == 0.0) and np.all(M[:, ~interior] == 0.0)
