@@ -1235,7 +1235,7 @@ def run_peaks(local_rank):
     torch.cuda.set_device(local_rank)
     fe.load()
     out = {"peaks": True}
-    for unit in ("fp64_fma", "fp64_dmma", "fp32_fma", "f32x2_mac", "bf16_mma"):
+    for unit in ("fp64_fma", "fp64_dmma", "fp64_dfma_dmma", "fp32_fma", "f32x2_mac", "bf16_mma"):
         out[unit + "_tflops"] = fe.fe_probe_throughput(unit)
     props = torch.cuda.get_device_properties(local_rank)
     out["sms"] = props.multi_processor_count

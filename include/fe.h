@@ -316,13 +316,16 @@ int fe_pcg_noalloc(const fe_pa* pa, int op, int pc, const double* dev_b, double*
  * flops).  Units: FE_PROBE_FP64_FMA, FE_PROBE_FP64_DMMA, FE_PROBE_FP32_FMA, FE_PROBE_F32X2_MAC
  * (the anchored float-float step of the apply, counted as one FP64-equivalent multiply-add),
  * FE_PROBE_BF16_MMA (mma.sync m16n8k16 BF16 with FP32 accumulation, the instruction of the
- * learned preconditioner's kernels).  Synchronous; allocates 64 bytes of scratch. */
+ * learned preconditioner's kernels), FE_PROBE_FP64_DFMA_DMMA (DFMA chains in half the warps and
+ * DMMA chains in the other half at once, both counted: above the DFMA rate only if the two do
+ * not share a datapath).  Synchronous; allocates 64 bytes of scratch. */
 enum {
   FE_PROBE_FP64_FMA = 0,
   FE_PROBE_FP64_DMMA = 1,
   FE_PROBE_FP32_FMA = 2,
   FE_PROBE_F32X2_MAC = 3,
-  FE_PROBE_BF16_MMA = 4
+  FE_PROBE_BF16_MMA = 4,
+  FE_PROBE_FP64_DFMA_DMMA = 5
 };
 int fe_probe_throughput(int unit, double* tflops);
 

@@ -1197,7 +1197,7 @@ constexpr int kSmemPerSm = 233472;  // 228 KB of shared memory per SM
 // wait inside tcgen05.alloc for another CTA to finish).
 template <int DP, int W>
 constexpr int tc_smem() {
-  using Lay = mlptc::TcLayout<DP, W>;
+  using Lay = mlptc::TcLayout<DP, W, mlptc::tc_groups<DP, W>()>;
   constexpr int cap = 512 / Lay::NCOLS;
   constexpr int floor_ = kSmemPerSm / (cap + 1) + 1;
   return Lay::SMEM > floor_ ? Lay::SMEM : floor_;
@@ -1207,17 +1207,18 @@ constexpr int tc_smem() {
 template <int DP, int W, class VT>
 int tc_occupancy() {
   constexpr int smem = tc_smem<DP, W>();
+  constexpr int G = mlptc::tc_groups<DP, W>();
   if constexpr (smem <= (int)kMaxSmem) {
-    auto kern = mlptc::k_lpc_tc<DP, W, VT>;
+    auto kern = mlptc::k_lpc_tc<DP, W, VT, G>;
     int occ = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, mlptc::kThreads, smem) !=
-            cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G * mlptc::kGroupThreads,
+                                                      smem) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    const int cap = 512 / mlptc::TcLayout<DP, W>::NCOLS;
+    const int cap = 512 / mlptc::TcLayout<DP, W, G>::NCOLS;
     return occ < cap ? occ : cap;
   }
   return 0;
@@ -1226,19 +1227,31 @@ int tc_occupancy() {
 template <int DP, int W, class VT>
 cudaError_t tc_launch(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStream_t s) {
   constexpr int smem = tc_smem<DP, W>();
+  constexpr int G = mlptc::tc_groups<DP, W>();
   if constexpr (smem <= (int)kMaxSmem) {
     const fe_mesh* m = L->pa->mesh;
-    mlptc::k_lpc_tc<DP, W, VT><<<grid, mlptc::kThreads, smem, s>>>(
+    mlptc::k_lpc_tc<DP, W, VT, G><<<grid, G * mlptc::kGroupThreads, smem, s>>>(
         L->tcimg, r, m->d_map, L->fsc32, m->ne, L->din, z, L->d_tcfail);
     return cudaGetLastError();
   }
   return cudaErrorInvalidConfiguration;
 }
 
+// Tile pipelines per CTA of the built (DP, W) (the grid counts pairs of tiles where it is 2).
+int tc_groups_of(int DP, int W);
+
 // The built (DP, W) pairs of the tcgen05 apply.
 #define FE_TC_CASES(X) \
   X(16, 0) X(16, 64) X(16, 128) X(32, 0) X(32, 64) X(32, 128) X(64, 0) X(64, 64) X(64, 128) \
   X(128, 0) X(128, 64) X(128, 128)
+
+int tc_groups_of(int DP, int W) {
+#define FE_TC_G(dp, w) \
+  if (DP == dp && W == w) return mlptc::tc_groups<dp, w>();
+  FE_TC_CASES(FE_TC_G)
+#undef FE_TC_G
+  return 1;
+}
 
 template <class VT>
 int tc_occ(int DP, int W) {
@@ -1286,11 +1299,14 @@ void tc_setup(fe_lpc* L) {
     L->d_tcfail = nullptr;
     return;
   }
+  // one CTA runs G pipelines on interleaved 128-element tiles
   const int64_t tiles = (L->pa->mesh->ne + mlptc::kRows - 1) / mlptc::kRows;
+  const int G = tc_groups_of(DP, L->width);
+  const int64_t units = (tiles + G - 1) / G;
   auto grid = [&](int o) -> int {
     if (o <= 0) return 0;
     const int64_t cap = (int64_t)sms * o;
-    return (int)(tiles < cap ? (tiles < 1 ? 1 : tiles) : cap);
+    return (int)(units < cap ? (units < 1 ? 1 : units) : cap);
   };
   L->tc_grid = grid(occ);
   L->tc_grid32 = grid(occ32);

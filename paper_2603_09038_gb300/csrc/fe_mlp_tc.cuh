@@ -4,7 +4,10 @@
 // z += sum_e R_e^T F_e s_e f(x_e / s_e), x_e = F_e R_e r, s_e = ||x_e||_2, with
 // f(x) = relu(relu(x W1) W2) W3 + x W0 (W = 0: the linear patch map f(x) = x W0) -- the same
 // operator as mlp::k_lpc_fused, re-tiled for tcgen05:
-//   * one CTA (8 warps) takes 128 elements at a time: the 128 rows of every layer's M = 128 MMA;
+//   * a tile of 128 elements (the 128 rows of every layer's M = 128 MMA) is taken by a pipeline
+//     of 8 warps; a CTA runs two pipelines on interleaved tiles where their shared memory fits (their own operand tiles, TMEM
+//     columns, mbarriers and named barriers), so that one gathers or scatters while the other
+//     waits, and they share one copy of the weights;
 //   * the weights live in shared memory for the whole persistent kernel, copied once by
 //     cp.async.bulk behind an mbarrier, as BF16 images in the tensor core's canonical K-major
 //     layout without swizzle (8-row x 16-byte core matrices, element (n, k) of an N x K image at
@@ -30,7 +33,8 @@ namespace fe {
 namespace mlptc {
 
 constexpr int kRows = 128;     // rows (elements) per tile: the MMA's M
-constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quadrant
+constexpr int kGroupThreads = 256;   // one tile pipeline: 8 warps, two per TMEM lane quadrant
+constexpr int kMaxSmemCta = 232448;  // 227 KB of dynamic shared memory per CTA
 constexpr long long kWaitLimit = 1ll << 22;  // mbarrier polls before a wait is given up
 
 __host__ __device__ constexpr int pow2_cols(int n) {
@@ -39,28 +43,41 @@ __host__ __device__ constexpr int pow2_cols(int n) {
   return c;
 }
 
-// Byte sizes of the shared-memory regions for (DP, W).
-template <int DP, int W>
+// Byte offsets of the shared-memory regions for (DP, W) and G tile pipelines per CTA: the weight
+// images once, then per pipeline g its operand tiles (X, H; the staging tile aliases them after
+// the last MMA), its row scales and its mbarrier.
+template <int DP, int W, int G>
 struct TcLayout {
   static constexpr int W1 = 0;                           // [W][DP]
   static constexpr int W2 = W1 + W * DP * 2;             // [W][W]
   static constexpr int W3 = W2 + W * W * 2;              // [DP][W]
   static constexpr int W0 = W3 + DP * W * 2;             // [DP][DP]
   static constexpr int WBYTES = W0 + DP * DP * 2;        // weight images
-  static constexpr int X = WBYTES;                       // [128][DP] BF16
-  static constexpr int H = X + kRows * DP * 2;           // [128][W] BF16
   static constexpr int YS = DP + 4;                      // staging row stride (floats)
   static constexpr int ACT = (kRows * (DP + W) * 2 > kRows * YS * 4) ? kRows * (DP + W) * 2
                                                                      : kRows * YS * 4;
-  static constexpr int SCALE = X + ACT;                  // float[128]
-  static constexpr int BAR = SCALE + kRows * 4;          // two mbarriers (weights, MMA)
-  static constexpr int SLOT = BAR + 16;                  // TMEM base address
+  static constexpr int GROUP = ACT + kRows * 4;          // one pipeline's region
+  static constexpr int X = WBYTES;                       // + g GROUP: [128][DP] BF16
+  static constexpr int H = X + kRows * DP * 2;           // + g GROUP: [128][W] BF16
+  static constexpr int SCALE = X + ACT;                  // + g GROUP: float[128]
+  static constexpr int BAR = WBYTES + G * GROUP;         // weight mbarrier, one per pipeline
+  static constexpr int SLOT = BAR + 8 * (1 + G);         // TMEM base address
   static constexpr int SMEM = SLOT + 16;
-  static constexpr int NCOLS = pow2_cols(W > DP ? W : DP);  // TMEM columns
+  static constexpr int NC = pow2_cols(W > DP ? W : DP);  // TMEM columns of one pipeline
+  static constexpr int NCOLS = G * NC;                   // allocated per CTA
   static_assert(DP % 16 == 0 && W % 16 == 0 && DP >= 16 && DP <= 256 && W <= 256,
                 "tcgen05 tile sizes: N and K multiples of 16, N <= 256");
-  static_assert(WBYTES % 16 == 0 && X % 16 == 0 && H % 16 == 0, "16-byte aligned regions");
+  static_assert(WBYTES % 16 == 0 && GROUP % 16 == 0 && (kRows * DP * 2) % 16 == 0,
+                "16-byte aligned regions");
+  static_assert(NCOLS <= 512, "tensor memory columns");
 };
+
+// Pipelines per CTA for (DP, W): two (one gathers or scatters while the other waits on its
+// tensor-core chain, sharing the weights) where their shared memory fits, else one.
+template <int DP, int W>
+constexpr int tc_groups() {
+  return TcLayout<DP, W, 2>::SMEM <= kMaxSmemCta ? 2 : 1;
+}
 
 // Host: offsets (BF16 elements) of the four images in the packed weight buffer.
 __host__ __device__ inline void tc_offsets(int DP, int W, int64_t off[5]) {
@@ -201,6 +218,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Barrier of one pipeline's 8 warps (named barrier 1 + g; barrier 0 is __syncthreads), and the
+// same with an OR-vote of v over them.
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+__device__ __forceinline__ int group_or(int g, int v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+      : "=r"(r) : "r"(v), "r"(1 + g), "r"(kGroupThreads) : "memory");
+  return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16(lo)) |
          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(hi)) << 16);
@@ -237,33 +268,36 @@ __device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int half
 
 // VT: element type of r and z (double; float inside the mixed-precision solver).  fail: device
 // flag raised when a wait on the tensor core or on the weight copy is given up.
-template <int DP, int W, class VT>
-__global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
+template <int DP, int W, class VT, int G>
+__global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
     const __nv_bfloat16* __restrict__ wimg, const VT* __restrict__ r,
     const int32_t* __restrict__ map, const float* __restrict__ fsc, int64_t ne, int din,
     VT* __restrict__ z, int* __restrict__ fail) {
-  using Lay = TcLayout<DP, W>;
+  using Lay = TcLayout<DP, W, G>;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // pipeline g: warps 8 g .. 8 g + 7, its own operand tiles, scales, mbarrier, TMEM columns
+  const int g = warp >> 3, gtid = tid & (kGroupThreads - 1), gwarp = warp & 7;
   const uint32_t sb = smem_u32(smem);
-  const uint32_t bar_w = sb + Lay::BAR, bar_m = sb + Lay::BAR + 8;
+  const int gb = g * Lay::GROUP;
+  const uint32_t bar_w = sb + Lay::BAR, bar_m = sb + Lay::BAR + 8 * (1 + g);
   uint32_t* slot = reinterpret_cast<uint32_t*>(smem + Lay::SLOT);
-  float* sscale = reinterpret_cast<float*>(smem + Lay::SCALE);
-  unsigned char* sX = smem + Lay::X;
-  unsigned char* sH = smem + Lay::H;
-  const float* sY = reinterpret_cast<const float*>(smem + Lay::X);  // after the last MMA
+  float* sscale = reinterpret_cast<float*>(smem + Lay::SCALE + gb);
+  unsigned char* sX = smem + Lay::X + gb;
+  unsigned char* sH = smem + Lay::H + gb;
+  const float* sY = reinterpret_cast<const float*>(sX);  // after the last MMA of a tile
 
   // ---- barriers, TMEM, the weight images (one bulk copy stream behind an mbarrier)
   if (tid == 0) {
     bar_init(bar_w, 1);
-    bar_init(bar_m, 1);
+    for (int k = 0; k < G; ++k) bar_init(sb + Lay::BAR + 8 * (1 + k), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(slot), Lay::NCOLS);
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *slot;
+  const uint32_t tmem = *slot, tmem_g = tmem + (uint32_t)(g * Lay::NC);
   if (tid == 0) {
     bar_arrive_expect(bar_w, (uint32_t)Lay::WBYTES);
     const unsigned char* src = reinterpret_cast<const unsigned char*>(wimg);
@@ -274,19 +308,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
   }
   int bad = __syncthreads_or(!bar_wait(bar_w, 0));
 
-  const int q = warp & 3, half = warp >> 2;
+  const int q = warp & 3, half = gwarp >> 2;
   const int erow = 32 * q + lane;  // this thread's TMEM lane = tile row in the epilogues
-  const uint32_t t_lane = tmem + ((uint32_t)(32 * q) << 16);
+  const uint32_t t_lane = tmem_g + ((uint32_t)(32 * q) << 16);
   uint32_t phase = 0;
   const int64_t ntiles = (ne + kRows - 1) / kRows;
   constexpr int NPAIR = DP / 2, PPL = (NPAIR + 31) / 32;  // BF16 pairs per row, per lane
   constexpr int RG = PPL > 1 ? 4 : 8;                     // rows per gather / scatter group
-  for (int64_t tile = blockIdx.x; tile < ntiles && !bad; tile += gridDim.x) {
+  for (int64_t tile = (int64_t)blockIdx.x * G + g; tile < ntiles && !bad;
+       tile += (int64_t)gridDim.x * G) {
     // ---- gather: x = F r on each element, normalised by its norm, BF16 into the X image;
     //      warp w takes rows 16 w .. 16 w + 15, RG at a time: every dof-map entry of the group
     //      is loaded first, then the values, so that all of them are in flight together
 #pragma unroll 1
-    for (int r0 = 16 * warp; r0 < 16 * warp + 16; r0 += RG) {
+    for (int r0 = 16 * gwarp; r0 < 16 * gwarp + 16; r0 += RG) {
       int32_t gi[RG][PPL][2];
 #pragma unroll
       for (int i = 0; i < RG; ++i) {
@@ -339,44 +374,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
       }
     }
     fence_proxy_async();
-    __syncthreads();
+    group_sync(g);
 
     // ---- the layers: one thread issues, everybody waits on the commit, the epilogue warps
     //      read their lane quadrant back
     if constexpr (W > 0) {
 #pragma unroll 1
       for (int layer = 0; layer < 2 && !bad; ++layer) {
-        if (tid == 0) {
+        if (gtid == 0) {
           fence_after();
           if (layer == 0)
-            issue_chain(tmem, sb + Lay::X, sb + Lay::W1, DP, W, false);
+            issue_chain(tmem_g, sb + Lay::X + gb, sb + Lay::W1, DP, W, false);
           else
-            issue_chain(tmem, sb + Lay::H, sb + Lay::W2, W, W, false);
+            issue_chain(tmem_g, sb + Lay::H + gb, sb + Lay::W2, W, W, false);
           mma_commit(bar_m);
         }
-        bad = __syncthreads_or(!bar_wait(bar_m, phase));
+        bad = group_or(g, !bar_wait(bar_m, phase));
         phase ^= 1u;
         if (bad) break;
         fence_after();
         relu_to_image<W>(t_lane, erow, half, sH);
         fence_before();
         fence_proxy_async();
-        __syncthreads();
+        group_sync(g);
       }
       if (bad) break;
     }
-    if (tid == 0) {
+    if (gtid == 0) {
       fence_after();
-      issue_chain(tmem, sb + Lay::X, sb + Lay::W0, DP, DP, false);  // skip term x W0
-      if constexpr (W > 0) issue_chain(tmem, sb + Lay::H, sb + Lay::W3, W, DP, true);
+      issue_chain(tmem_g, sb + Lay::X + gb, sb + Lay::W0, DP, DP, false);  // skip term x W0
+      if constexpr (W > 0) issue_chain(tmem_g, sb + Lay::H + gb, sb + Lay::W3, W, DP, true);
       mma_commit(bar_m);
     }
-    bad = __syncthreads_or(!bar_wait(bar_m, phase));
+    bad = group_or(g, !bar_wait(bar_m, phase));
     phase ^= 1u;
     if (bad) break;
     fence_after();
     {
-      float* yrow = reinterpret_cast<float*>(smem + Lay::X) + erow * Lay::YS;
+      float* yrow = reinterpret_cast<float*>(sX) + erow * Lay::YS;
 #pragma unroll
       for (int c = half * (DP / 2); c < (half + 1) * (DP / 2); c += 8) {
         float v[8];
@@ -386,12 +421,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
       }
     }
     fence_before();
-    __syncthreads();
+    group_sync(g);
 
     // ---- scatter: z += F s y, warp w rows 16 w .. 16 w + 15, lanes along the element's dofs,
     //      RG rows at a time with their dof-map and scaling loads issued before the adds
 #pragma unroll 1
-    for (int r0 = 16 * warp; r0 < 16 * warp + 16; r0 += RG) {
+    for (int r0 = 16 * gwarp; r0 < 16 * gwarp + 16; r0 += RG) {
       int32_t gi[RG][PPL][2];
 #pragma unroll
       for (int i = 0; i < RG; ++i) {
@@ -426,13 +461,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_lpc_tc(
           }
       }
     }
-    __syncthreads();  // the next tile's gather rewrites X (and the staging that aliases it)
+    group_sync(g);  // the next tile's gather rewrites X (and the staging that aliases it)
   }
 
   // ---- teardown: a given-up wait is reported, in-flight MMAs get one more bounded wait, and
   //      the TMEM is always freed
   if (bad) {
-    if (tid == 0) atomicExch(fail, 1);
+    if (gtid == 0) atomicExch(fail, 1);
     bar_wait(bar_m, phase);
   }
   fence_before();

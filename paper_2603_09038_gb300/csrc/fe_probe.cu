@@ -57,6 +57,40 @@ __global__ void k_probe_dmma(double* out, int iters) {
   if (s == 12345.678) out[0] = s;
 }
 
+// DFMA chains in the even warps and DMMA chains in the odd ones, at the same time: whether the two
+// FP64 instruction kinds share one datapath (the combined rate stays at the DFMA rate) or not
+// (the rates add).  The chain lengths make each half run about equally long on its own unit.
+__global__ void k_probe_dfma_dmma(double* out, int iters_f, int iters_m) {
+  const int warp = threadIdx.x >> 5;
+  double s = 0;
+  if ((warp & 1) == 0) {
+    double a[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = threadIdx.x * 1e-3 + i;
+    for (int it = 0; it < iters_f; ++it) {
+#pragma unroll
+      for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], 0.9999, 1e-3);
+    }
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += a[i];
+  } else {
+    double a = threadIdx.x * 1e-3, b = 0.999;
+    double c[kChains][2];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) c[i][0] = c[i][1] = i;
+    for (int it = 0; it < iters_m; ++it) {
+#pragma unroll
+      for (int i = 0; i < kChains; ++i)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(c[i][0]), "+d"(c[i][1])
+                     : "d"(a), "d"(b));
+    }
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s += c[i][0] + c[i][1];
+  }
+  if (s == 12345.678) out[0] = s;
+}
+
 // BF16 m16n8k16 tensor-core MMA chains with FP32 accumulation (the instruction of the learned
 // preconditioner's kernels), 4096 flops each per warp
 __global__ void k_probe_hmma(float* out, int iters, uint32_t av, uint32_t bv) {
@@ -137,6 +171,15 @@ extern "C" int fe_probe_throughput(int unit, double* tflops) {
         flops_per_iter = 4096.0 * kChains * (nthreads / 32);
         k_probe_hmma<<<blocks, threads>>>((float*)buf, iters, 0x3F803F80u, 0x3F7F3F7Fu);
         break;
+      case FE_PROBE_FP64_DFMA_DMMA: {
+        // half the warps each: 2 flops x 8 chains x 32 lanes per DFMA iteration, 512 x 8 per
+        // DMMA iteration; 1/8 the DMMA iterations gives each half the same flop count
+        iters = 4096;
+        const int iters_m = iters / 8;
+        flops_per_iter = (2.0 * kChains * 32 + 512.0 * kChains / 8) * (nthreads / 64);
+        k_probe_dfma_dmma<<<blocks, threads>>>((double*)buf, iters, iters_m);
+        break;
+      }
       default:
         iters = 8192;
         flops_per_iter = 2.0 * kChains * nthreads;
@@ -145,7 +188,7 @@ extern "C" int fe_probe_throughput(int unit, double* tflops) {
     }
   };
   int st = FE_OK;
-  if (unit < FE_PROBE_FP64_FMA || unit > FE_PROBE_BF16_MMA) {
+  if (unit < FE_PROBE_FP64_FMA || unit > FE_PROBE_FP64_DFMA_DMMA) {
     st = fe::set_error(FE_ERR_ARG, "fe_probe_throughput: unknown unit");
   } else {
     launch();  // warm-up

@@ -428,7 +428,8 @@ def fe_pcg_noalloc(pa, op, pc, dev_b, dev_x, rtol, maxit, stream=None):
     return status, _stats(st)
 
 
-PROBE_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "f32x2_mac": 3, "bf16_mma": 4}
+PROBE_UNITS = {"fp64_fma": 0, "fp64_dmma": 1, "fp32_fma": 2, "f32x2_mac": 3, "bf16_mma": 4,
+               "fp64_dfma_dmma": 5}
 
 
 def fe_probe_throughput(unit):
