@@ -836,25 +836,22 @@ def learned_fcg(fe, pa, b, x, args, stream, dist, dev, t_pcg, pcg_iters, width=N
     lpc_bytes = ne * din * 4 + ndofs * (8 + 8 + 4)
     mma_peak = fe.fe_probe_throughput("bf16_mma")
     bf16_peak = float(measured_peaks()[0].get("bf16_tflops", 1900.0))
-    ir = None
-    if width in (0, 64, 128):   # the same preconditioner inside mixed-precision refinement
-        def solve_ir():
-            st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, args.rtol, MAXIT,
-                                     args.inner_rtol, stream)
-            if st != fe.FE_OK:
-                raise RuntimeError("fe_fcg_ir failed: %d %s" % (st, fe.fe_last_error()))
-            return stats
-        try:
-            t_ir, s_ir = timed(solve_ir, max(1, min(args.steps, EXTRA_STEPS)))
-        except (fe.FEError, RuntimeError) as exc:  # no FP32 kernel, or the solve failed
-            t_ir, s_ir = None, str(exc)
-            ir = {"failed": str(exc).splitlines()[-1]}
-    if ir is None and width in (0, 64, 128) and t_ir is not None:
+    # the same preconditioner inside mixed-precision refinement, where an FP32 kernel is built
+    def solve_ir():
+        st, stats = fe.fe_fcg_ir(pa, fe.FE_DIFFUSION, lpc, b, x, args.rtol, MAXIT,
+                                 args.inner_rtol, stream)
+        if st != fe.FE_OK:
+            raise RuntimeError("fe_fcg_ir failed: %d %s" % (st, fe.fe_last_error()))
+        return stats
+    try:
+        t_ir, s_ir = timed(solve_ir, max(1, min(args.steps, EXTRA_STEPS)))
         ir = {"time_to_1e-8_s": t_ir, "speedup_vs_jacobi_pcg": t_pcg / t_ir if t_pcg else None,
               "inner_iters": s_ir["iters"], "outer_iters": s_ir["outer_iters"],
               "true_rel_resid": s_ir["true_rel_resid"], "inner": "FP32 FCG + this network",
               "inner_rtol": args.inner_rtol or 1e-2,
               "outer_operator": "f64"}
+    except (fe.FEError, RuntimeError) as exc:  # no FP32 kernel, or the solve failed
+        ir = {"failed": str(exc).splitlines()[-1]}
     fe.fe_lpc_destroy(lpc)
     return {
         "mixed_precision_ir": ir,
@@ -1257,8 +1254,9 @@ def main():
     ap.add_argument("--p", type=int, default=ORDER)
     ap.add_argument("--rtol", type=float, default=RTOL)
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="fe_pcg_ir inner tolerance")
-    ap.add_argument("--lpc-width", type=int, default=128,
-                    help="width of the learned preconditioner's MLP (0: skip that comparison)")
+    ap.add_argument("--lpc-width", type=int, default=256,
+                    help="width of the learned preconditioner's MLP (3 layers and a linear skip "
+                         "term; 0: skip that comparison)")
     ap.add_argument("--lpc-steps", type=int, default=3000, help="Adam steps of its training")
     ap.add_argument("--lpc-fit", action="store_true",
                     help="--learned: also the linear map fitted by least squares (fe_lpc_fit_linear)")

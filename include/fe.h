@@ -440,13 +440,15 @@ int fe_lpc_set_fallback(fe_lpc* lpc, int pc);
 int fe_lpc_apply(fe_lpc* lpc, const double* dev_r, double* dev_z, void* stream);
 
 /* Inference kernel of the learned preconditioner (fe_lpc_apply, fe_fcg, fe_fcg_ir):
- *   FE_LPC_KERNEL_AUTO      the fastest built kernel as measured on GB300: the mma.sync fused
- *                           kernel where it is built, else the tcgen05 one, else the unfused
- *                           GEMM path (the default);
- *   FE_LPC_KERNEL_TCGEN05   fused, one CTA per 128 elements, every layer on the 5th-generation
- *                           tensor cores (tcgen05.mma, FP32 accumulators in tensor memory,
- *                           weights staged by bulk copies); built for D^3 <= 128 (padded to a
- *                           multiple of 16) and width 0, 64 or 128;
+ *   FE_LPC_KERNEL_AUTO      the fastest built kernel as measured on GB300: tcgen05 at width
+ *                           256, else the mma.sync fused kernel where it is built, else the
+ *                           tcgen05 one, else the unfused GEMM path (the default);
+ *   FE_LPC_KERNEL_TCGEN05   fused, 128-element tiles, every layer on the 5th-generation tensor
+ *                           cores (tcgen05.mma, FP32 accumulators in tensor memory, weights
+ *                           staged by bulk copies; at width 256 the hidden activations stay in
+ *                           tensor memory as the next layer's operand); built for width 0, 64
+ *                           or 128 with D^3 <= 128 (padded to a multiple of 16), and width 256
+ *                           with D^3 <= 64;
  *   FE_LPC_KERNEL_MMA_SYNC  fused, one warp per 16 elements, warp-level mma.sync;
  *   FE_LPC_KERNEL_GEMM      gather kernel, the training path's four BF16 GEMMs, scatter kernel.
  * FE_ERR_UNSUPPORTED if the fused kernel asked for is not built for this order and width.
@@ -481,8 +483,8 @@ int fe_fcg(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, d
  * vectors; inner flexible CG on FP32 vectors with the FP32 apply (FP32 copy of the quadrature
  * data, made on first use) and lpc applied to FP32 vectors, on r scaled by a power of two to
  * norm ~1, to inner_rtol * ||r|| (0 => 1e-2); x += d (scaled back exactly); until
- * ||r|| <= rtol ||b||, checked on the FP64 residual.  lpc must have width 0, 64 or 128 (FE_ERR_UNSUPPORTED
- * otherwise).  stats: iters = inner iterations, outer_iters = refinement steps, rel_resid =
+ * ||r|| <= rtol ||b||, checked on the FP64 residual.  lpc needs an FP32 fused kernel (the
+ * mma.sync one at width 0, 64 or 128, or tcgen05; FE_ERR_UNSUPPORTED otherwise).  stats: iters = inner iterations, outer_iters = refinement steps, rel_resid =
  * true_rel_resid = the final FP64-accurate residual.  FE_ERR_NOT_CONVERGED also when a
  * refinement step fails to reduce the residual.  Allocates 2 FP64 and 7 FP32 vectors per call. */
 int fe_fcg_ir(fe_pa* pa, int op, fe_lpc* lpc, const double* dev_b, double* dev_x, double rtol,

@@ -1197,28 +1197,34 @@ constexpr int kSmemPerSm = 233472;  // 228 KB of shared memory per SM
 // wait inside tcgen05.alloc for another CTA to finish).
 template <int DP, int W>
 constexpr int tc_smem() {
-  using Lay = mlptc::TcLayout<DP, W, mlptc::tc_groups<DP, W>()>;
+  using Lay = typename mlptc::TcConfig<DP, W>::Lay;
   constexpr int cap = 512 / Lay::NCOLS;
   constexpr int floor_ = kSmemPerSm / (cap + 1) + 1;
   return Lay::SMEM > floor_ ? Lay::SMEM : floor_;
 }
 
+template <int DP, int W, class VT>
+constexpr auto tc_kernel() {
+  using C = mlptc::TcConfig<DP, W>;
+  return mlptc::k_lpc_tc<DP, W, VT, C::G, C::AT, C::WPG>;
+}
+
 // Resident CTAs per SM of the tcgen05 apply for (DP, W), 0 if it does not fit.
 template <int DP, int W, class VT>
 int tc_occupancy() {
+  using C = mlptc::TcConfig<DP, W>;
   constexpr int smem = tc_smem<DP, W>();
-  constexpr int G = mlptc::tc_groups<DP, W>();
-  if constexpr (smem <= (int)kMaxSmem) {
-    auto kern = mlptc::k_lpc_tc<DP, W, VT, G>;
+  if constexpr (C::FITS && smem <= (int)kMaxSmem) {
+    auto kern = tc_kernel<DP, W, VT>();
     int occ = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, G * mlptc::kGroupThreads,
-                                                      smem) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::THREADS, smem) !=
+            cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    const int cap = 512 / mlptc::TcLayout<DP, W, G>::NCOLS;
+    const int cap = 512 / C::Lay::NCOLS;
     return occ < cap ? occ : cap;
   }
   return 0;
@@ -1226,12 +1232,12 @@ int tc_occupancy() {
 
 template <int DP, int W, class VT>
 cudaError_t tc_launch(const fe_lpc* L, const VT* r, VT* z, int grid, cudaStream_t s) {
+  using C = mlptc::TcConfig<DP, W>;
   constexpr int smem = tc_smem<DP, W>();
-  constexpr int G = mlptc::tc_groups<DP, W>();
-  if constexpr (smem <= (int)kMaxSmem) {
+  if constexpr (C::FITS && smem <= (int)kMaxSmem) {
     const fe_mesh* m = L->pa->mesh;
-    mlptc::k_lpc_tc<DP, W, VT, G><<<grid, G * mlptc::kGroupThreads, smem, s>>>(
-        L->tcimg, r, m->d_map, L->fsc32, m->ne, L->din, z, L->d_tcfail);
+    tc_kernel<DP, W, VT>()<<<grid, C::THREADS, smem, s>>>(L->tcimg, r, m->d_map, L->fsc32, m->ne,
+                                                         L->din, z, L->d_tcfail);
     return cudaGetLastError();
   }
   return cudaErrorInvalidConfiguration;
@@ -1242,12 +1248,12 @@ int tc_groups_of(int DP, int W);
 
 // The built (DP, W) pairs of the tcgen05 apply.
 #define FE_TC_CASES(X) \
-  X(16, 0) X(16, 64) X(16, 128) X(32, 0) X(32, 64) X(32, 128) X(64, 0) X(64, 64) X(64, 128) \
-  X(128, 0) X(128, 64) X(128, 128)
+  X(16, 0) X(16, 64) X(16, 128) X(16, 256) X(32, 0) X(32, 64) X(32, 128) X(32, 256) X(64, 0) \
+  X(64, 64) X(64, 128) X(64, 256) X(128, 0) X(128, 64) X(128, 128)
 
 int tc_groups_of(int DP, int W) {
 #define FE_TC_G(dp, w) \
-  if (DP == dp && W == w) return mlptc::tc_groups<dp, w>();
+  if (DP == dp && W == w) return mlptc::TcConfig<dp, w>::G;
   FE_TC_CASES(FE_TC_G)
 #undef FE_TC_G
   return 1;
@@ -1313,14 +1319,17 @@ void tc_setup(fe_lpc* L) {
 }
 
 // The inference kernel a call uses (AUTO resolved); fp32: the FP32-vector solves, which have
-// no unfused path.  AUTO takes the measured-fastest built kernel: the mma.sync fused kernel
-// (its warps each gather, transform and scatter 16 elements with no block-wide barrier, which
-// hides the dof-map gather's latency better than the tcgen05 kernel's 128-element tile
-// pipeline: 0.22 against 0.27 ms at 64^3, p = 3, width 128), then tcgen05, then the GEMMs.
+// no unfused path.  AUTO takes the measured-fastest built kernel: tcgen05 at width 256, where
+// the layers are dense enough for the tensor cores to matter; below that the mma.sync fused
+// kernel (its independent 16-element warps hide the dof-map gather's latency as well as the
+// tcgen05 tile pipelines do at width 128, and better for the linear map); else whichever fused
+// kernel is built; else the GEMMs.
 int lpc_kernel(const fe_lpc* L, bool fp32) {
   if (L->kernel != FE_LPC_KERNEL_AUTO) return L->kernel;
-  if (L->fused_grid > 0) return FE_LPC_KERNEL_MMA_SYNC;
-  if ((fp32 ? L->tc_grid32 : L->tc_grid) > 0) return FE_LPC_KERNEL_TCGEN05;
+  const bool tc = (fp32 ? L->tc_grid32 : L->tc_grid) > 0;
+  const bool ms = L->fused_grid > 0 && (!fp32 || fused_f32_built(L));
+  if (tc && (L->width >= 256 || !ms)) return FE_LPC_KERNEL_TCGEN05;
+  if (ms) return FE_LPC_KERNEL_MMA_SYNC;
   return FE_LPC_KERNEL_GEMM;
 }
 
@@ -1902,7 +1911,8 @@ int fe_lpc_set_kernel(fe_lpc* L, int kernel) {
     return set_error(FE_ERR_ARG, "fe_lpc_set_kernel: unknown kernel");
   if (kernel == FE_LPC_KERNEL_TCGEN05 && L->tc_grid <= 0 && L->tc_grid32 <= 0)
     return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_set_kernel: no tcgen05 kernel for this order "
-                                         "and width (D^3 <= 128, width 0, 64 or 128)");
+                                         "and width (width 0, 64 or 128 with D^3 <= 128; "
+                                         "width 256 with D^3 <= 64)");
   if (kernel == FE_LPC_KERNEL_MMA_SYNC && L->fused_grid <= 0)
     return set_error(FE_ERR_UNSUPPORTED, "fe_lpc_set_kernel: no mma.sync fused kernel for this "
                                          "order and width");

@@ -33,7 +33,6 @@ namespace fe {
 namespace mlptc {
 
 constexpr int kRows = 128;     // rows (elements) per tile: the MMA's M
-constexpr int kGroupThreads = 256;   // one tile pipeline: 8 warps, two per TMEM lane quadrant
 constexpr int kMaxSmemCta = 232448;  // 227 KB of dynamic shared memory per CTA
 constexpr long long kWaitLimit = 1ll << 22;  // mbarrier polls before a wait is given up
 
@@ -43,10 +42,11 @@ __host__ __device__ constexpr int pow2_cols(int n) {
   return c;
 }
 
-// Byte offsets of the shared-memory regions for (DP, W) and G tile pipelines per CTA: the weight
-// images once, then per pipeline g its operand tiles (X, H; the staging tile aliases them after
-// the last MMA), its row scales and its mbarrier.
-template <int DP, int W, int G>
+// Byte offsets of the shared-memory regions for (DP, W), G tile pipelines per CTA and the place
+// of the hidden activations (AT: in tensor memory, as the A operand of the next layer; else in
+// shared memory): the weight images once, then per pipeline g its operand tiles (X, and H unless
+// AT; the staging tile aliases them after the last MMA), its row scales and its mbarrier.
+template <int DP, int W, int G, bool AT>
 struct TcLayout {
   static constexpr int W1 = 0;                           // [W][DP]
   static constexpr int W2 = W1 + W * DP * 2;             // [W][W]
@@ -54,30 +54,45 @@ struct TcLayout {
   static constexpr int W0 = W3 + DP * W * 2;             // [DP][DP]
   static constexpr int WBYTES = W0 + DP * DP * 2;        // weight images
   static constexpr int YS = DP + 4;                      // staging row stride (floats)
-  static constexpr int ACT = (kRows * (DP + W) * 2 > kRows * YS * 4) ? kRows * (DP + W) * 2
-                                                                     : kRows * YS * 4;
+  static constexpr int YROWS = AT ? kRows / 2 : kRows;   // rows staged per scatter pass
+  static constexpr int OPND = kRows * (DP + (AT ? 0 : W)) * 2;
+  static constexpr int ACT = OPND > YROWS * YS * 4 ? OPND : YROWS * YS * 4;
   static constexpr int GROUP = ACT + kRows * 4;          // one pipeline's region
   static constexpr int X = WBYTES;                       // + g GROUP: [128][DP] BF16
-  static constexpr int H = X + kRows * DP * 2;           // + g GROUP: [128][W] BF16
+  static constexpr int H = X + kRows * DP * 2;           // + g GROUP: [128][W] BF16 (not AT)
   static constexpr int SCALE = X + ACT;                  // + g GROUP: float[128]
   static constexpr int BAR = WBYTES + G * GROUP;         // weight mbarrier, one per pipeline
   static constexpr int SLOT = BAR + 8 * (1 + G);         // TMEM base address
   static constexpr int SMEM = SLOT + 16;
-  static constexpr int NC = pow2_cols(W > DP ? W : DP);  // TMEM columns of one pipeline
+  // TMEM columns of one pipeline: the FP32 accumulator (max(W, DP) columns), and with AT the
+  // BF16 activations after it (two per 32-bit column)
+  static constexpr int ACC = pow2_cols(W > DP ? W : DP);
+  static constexpr int ACOL = AT ? ACC : 0;              // first activation column
+  static constexpr int NC = pow2_cols(ACC + (AT ? W / 2 : 0));
   static constexpr int NCOLS = G * NC;                   // allocated per CTA
   static_assert(DP % 16 == 0 && W % 16 == 0 && DP >= 16 && DP <= 256 && W <= 256,
                 "tcgen05 tile sizes: N and K multiples of 16, N <= 256");
   static_assert(WBYTES % 16 == 0 && GROUP % 16 == 0 && (kRows * DP * 2) % 16 == 0,
                 "16-byte aligned regions");
   static_assert(NCOLS <= 512, "tensor memory columns");
+  static_assert(!AT || G == 1, "activations in tensor memory take all of it: one pipeline");
 };
 
-// Pipelines per CTA for (DP, W): two (one gathers or scatters while the other waits on its
-// tensor-core chain, sharing the weights) where their shared memory fits, else one.
+// How (DP, W) is built: two pipelines of 8 warps with the activations in shared memory where
+// they fit (one gathers or scatters while the other waits on its tensor-core chain, sharing the
+// weights); else one such pipeline; else (the widest layers, whose weights alone nearly fill
+// shared memory) one pipeline of 16 warps keeping the activations in tensor memory.
 template <int DP, int W>
-constexpr int tc_groups() {
-  return TcLayout<DP, W, 2>::SMEM <= kMaxSmemCta ? 2 : 1;
-}
+struct TcConfig {
+  static constexpr bool TWO = TcLayout<DP, W, 2, false>::SMEM <= kMaxSmemCta;
+  static constexpr bool ONE = TcLayout<DP, W, 1, false>::SMEM <= kMaxSmemCta;
+  static constexpr int G = TWO ? 2 : 1;
+  static constexpr bool AT = !TWO && !ONE;
+  static constexpr int WPG = AT ? 16 : 8;                // warps per pipeline
+  using Lay = TcLayout<DP, W, G, AT>;
+  static constexpr bool FITS = Lay::SMEM <= kMaxSmemCta;
+  static constexpr int THREADS = G * WPG * 32;
+};
 
 // Host: offsets (BF16 elements) of the four images in the packed weight buffer.
 __host__ __device__ inline void tc_offsets(int DP, int W, int64_t off[5]) {
@@ -218,18 +233,39 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Barrier of one pipeline's 8 warps (named barrier 1 + g; barrier 0 is __syncthreads), and the
-// same with an OR-vote of v over them.
-__device__ __forceinline__ void group_sync(int g) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+// Barrier of one pipeline's nt threads (named barrier 1 + g; barrier 0 is __syncthreads), and
+// the same with an OR-vote of v over them.
+__device__ __forceinline__ void group_sync(int g, int nt) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nt) : "memory");
 }
-__device__ __forceinline__ int group_or(int g, int v) {
+__device__ __forceinline__ int group_or(int g, int nt, int v) {
   int r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
       "bar.red.or.pred p, %2, %3, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
-      : "=r"(r) : "r"(v), "r"(1 + g), "r"(kGroupThreads) : "memory");
+      : "=r"(r) : "r"(v), "r"(1 + g), "r"(nt) : "memory");
   return r;
+}
+
+// 8 consecutive 32-bit columns of the calling thread's TMEM lane, stored (the 32x32b shape of
+// tmem_ld8), and complete before return.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&w)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+      ::"r"(taddr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+        "r"(w[7])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D (+)= A B^T with A[128 x 16] in tensor memory (row i in lane i, two BF16 per 32-bit column,
+// the lower half first) and B in shared memory.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -248,13 +284,23 @@ __device__ __forceinline__ void issue_chain(uint32_t tmem, uint32_t a, uint32_t 
              (accumulate || kk > 0) ? 1u : 0u);
 }
 
-// Epilogue of a hidden layer: the warp's lane quadrant, its half of the N columns, ReLU, BF16,
-// into the canonical [128][N] image at dst.
-template <int N>
-__device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int half,
+// The same with A in tensor memory from column a (a K = 16 step advances it by 8 columns).
+__device__ __forceinline__ void issue_chain_ts(uint32_t tmem, uint32_t a, uint32_t b, int K,
+                                               int N, bool accumulate) {
+  const uint32_t id = idesc_bf16(kRows, N), sbo = (uint32_t)(K / 8) * 128u;
+  for (int kk = 0; kk < K / 16; ++kk)
+    mma_bf16_ts(tmem, a + 8u * kk, sdesc(b + kk * 256u, 128u, sbo), id,
+                (accumulate || kk > 0) ? 1u : 0u);
+}
+
+// Epilogues of a hidden layer: the thread's TMEM lane (its tile row), ReLU, BF16, as the next
+// layer's A operand; the NQ warps of a lane quadrant take interleaved column chunks (part =
+// this warp's rank among them).  Into the canonical [128][N] image at dst in shared memory:
+template <int N, int NQ>
+__device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int part,
                                               unsigned char* dst) {
 #pragma unroll
-  for (int c = half * (N / 2); c < (half + 1) * (N / 2); c += 8) {
+  for (int c = 8 * part; c < N; c += 8 * NQ) {
     float v[8];
     tmem_ld8(t_lane + (uint32_t)c, v);
     uint4 pk;
@@ -265,19 +311,39 @@ __device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int half
     *reinterpret_cast<uint4*>(dst + canon(row, c, N) * 2) = pk;
   }
 }
+// or into tensor memory from column acol of the same lane (16 values per 8 columns).
+template <int N, int NQ>
+__device__ __forceinline__ void relu_to_tmem(uint32_t t_lane, int part, uint32_t acol) {
+#pragma unroll
+  for (int c = 16 * part; c < N; c += 16 * NQ) {
+    float v[16];
+    tmem_ld8(t_lane + (uint32_t)c, *reinterpret_cast<float(*)[8]>(v));
+    tmem_ld8(t_lane + (uint32_t)c + 8u, *reinterpret_cast<float(*)[8]>(v + 8));
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = pack_bf16(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+    tmem_st8(t_lane + acol + (uint32_t)(c / 2), w);
+  }
+}
 
 // VT: element type of r and z (double; float inside the mixed-precision solver).  fail: device
-// flag raised when a wait on the tensor core or on the weight copy is given up.
-template <int DP, int W, class VT, int G>
-__global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
+// flag raised when a wait on the tensor core or on the weight copy is given up.  G pipelines of
+// WPG warps per CTA; AT: hidden activations in tensor memory (TcConfig).
+template <int DP, int W, class VT, int G, bool AT, int WPG>
+__global__ void __launch_bounds__(G * WPG * 32, 1) k_lpc_tc(
     const __nv_bfloat16* __restrict__ wimg, const VT* __restrict__ r,
     const int32_t* __restrict__ map, const float* __restrict__ fsc, int64_t ne, int din,
     VT* __restrict__ z, int* __restrict__ fail) {
-  using Lay = TcLayout<DP, W, G>;
+  using Lay = TcLayout<DP, W, G, AT>;
+  constexpr int GT = WPG * 32;             // threads of one pipeline
+  constexpr int NQ = WPG / 4;              // its warps per TMEM lane quadrant
+  constexpr int RPW = kRows / WPG;         // tile rows per warp in the gather
+  constexpr int SPW = Lay::YROWS / WPG;    // staged rows per warp in one scatter pass
+  static_assert(WPG % 4 == 0 && RPW >= 4 && SPW >= 4, "pipeline shape");
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // pipeline g: warps 8 g .. 8 g + 7, its own operand tiles, scales, mbarrier, TMEM columns
-  const int g = warp >> 3, gtid = tid & (kGroupThreads - 1), gwarp = warp & 7;
+  // pipeline g: warps WPG g .. WPG g + WPG - 1, its own operand tiles, scales, mbarrier, TMEM
+  const int g = warp / WPG, gtid = tid - g * GT, gwarp = warp - g * WPG;
   const uint32_t sb = smem_u32(smem);
   const int gb = g * Lay::GROUP;
   const uint32_t bar_w = sb + Lay::BAR, bar_m = sb + Lay::BAR + 8 * (1 + g);
@@ -285,7 +351,7 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
   float* sscale = reinterpret_cast<float*>(smem + Lay::SCALE + gb);
   unsigned char* sX = smem + Lay::X + gb;
   unsigned char* sH = smem + Lay::H + gb;
-  const float* sY = reinterpret_cast<const float*>(sX);  // after the last MMA of a tile
+  float* sY = reinterpret_cast<float*>(sX);  // after the last MMA of a tile
 
   // ---- barriers, TMEM, the weight images (one bulk copy stream behind an mbarrier)
   if (tid == 0) {
@@ -308,20 +374,22 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
   }
   int bad = __syncthreads_or(!bar_wait(bar_w, 0));
 
-  const int q = warp & 3, half = gwarp >> 2;
+  const int q = warp & 3, part = gwarp >> 2;
   const int erow = 32 * q + lane;  // this thread's TMEM lane = tile row in the epilogues
   const uint32_t t_lane = tmem_g + ((uint32_t)(32 * q) << 16);
   uint32_t phase = 0;
   const int64_t ntiles = (ne + kRows - 1) / kRows;
   constexpr int NPAIR = DP / 2, PPL = (NPAIR + 31) / 32;  // BF16 pairs per row, per lane
-  constexpr int RG = PPL > 1 ? 4 : 8;                     // rows per gather / scatter group
+  constexpr int RG0 = PPL > 1 ? 4 : 8;
+  constexpr int RG = RG0 < RPW ? RG0 : RPW;               // rows per gather group
+  constexpr int RS = RG0 < SPW ? RG0 : SPW;               // rows per scatter group
   for (int64_t tile = (int64_t)blockIdx.x * G + g; tile < ntiles && !bad;
        tile += (int64_t)gridDim.x * G) {
     // ---- gather: x = F r on each element, normalised by its norm, BF16 into the X image;
-    //      warp w takes rows 16 w .. 16 w + 15, RG at a time: every dof-map entry of the group
-    //      is loaded first, then the values, so that all of them are in flight together
+    //      warp w takes rows RPW w .. RPW w + RPW - 1, RG at a time: every dof-map entry of the
+    //      group is loaded first, then the values, so that all of them are in flight together
 #pragma unroll 1
-    for (int r0 = 16 * gwarp; r0 < 16 * gwarp + 16; r0 += RG) {
+    for (int r0 = RPW * gwarp; r0 < RPW * gwarp + RPW; r0 += RG) {
       int32_t gi[RG][PPL][2];
 #pragma unroll
       for (int i = 0; i < RG; ++i) {
@@ -374,7 +442,7 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
       }
     }
     fence_proxy_async();
-    group_sync(g);
+    group_sync(g, GT);
 
     // ---- the layers: one thread issues, everybody waits on the commit, the epilogue warps
     //      read their lane quadrant back
@@ -385,83 +453,98 @@ __global__ void __launch_bounds__(G * kGroupThreads, 1) k_lpc_tc(
           fence_after();
           if (layer == 0)
             issue_chain(tmem_g, sb + Lay::X + gb, sb + Lay::W1, DP, W, false);
+          else if constexpr (AT)
+            issue_chain_ts(tmem_g, tmem_g + Lay::ACOL, sb + Lay::W2, W, W, false);
           else
             issue_chain(tmem_g, sb + Lay::H + gb, sb + Lay::W2, W, W, false);
           mma_commit(bar_m);
         }
-        bad = group_or(g, !bar_wait(bar_m, phase));
+        bad = group_or(g, GT, !bar_wait(bar_m, phase));
         phase ^= 1u;
         if (bad) break;
         fence_after();
-        relu_to_image<W>(t_lane, erow, half, sH);
-        fence_before();
-        fence_proxy_async();
-        group_sync(g);
+        if constexpr (AT) {
+          relu_to_tmem<W, NQ>(t_lane, part, (uint32_t)Lay::ACOL);
+          fence_before();
+        } else {
+          relu_to_image<W, NQ>(t_lane, erow, part, sH);
+          fence_before();
+          fence_proxy_async();
+        }
+        group_sync(g, GT);
       }
       if (bad) break;
     }
     if (gtid == 0) {
       fence_after();
       issue_chain(tmem_g, sb + Lay::X + gb, sb + Lay::W0, DP, DP, false);  // skip term x W0
-      if constexpr (W > 0) issue_chain(tmem_g, sb + Lay::H + gb, sb + Lay::W3, W, DP, true);
+      if constexpr (W > 0) {
+        if constexpr (AT)
+          issue_chain_ts(tmem_g, tmem_g + Lay::ACOL, sb + Lay::W3, W, DP, true);
+        else
+          issue_chain(tmem_g, sb + Lay::H + gb, sb + Lay::W3, W, DP, true);
+      }
       mma_commit(bar_m);
     }
-    bad = group_or(g, !bar_wait(bar_m, phase));
+    bad = group_or(g, GT, !bar_wait(bar_m, phase));
     phase ^= 1u;
     if (bad) break;
     fence_after();
-    {
-      float* yrow = reinterpret_cast<float*>(sX) + erow * Lay::YS;
-#pragma unroll
-      for (int c = half * (DP / 2); c < (half + 1) * (DP / 2); c += 8) {
-        float v[8];
-        tmem_ld8(t_lane + (uint32_t)c, v);
-        *reinterpret_cast<float4*>(yrow + c) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4*>(yrow + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
-      }
-    }
-    fence_before();
-    group_sync(g);
 
-    // ---- scatter: z += F s y, warp w rows 16 w .. 16 w + 15, lanes along the element's dofs,
-    //      RG rows at a time with their dof-map and scaling loads issued before the adds
+    // ---- staging and scatter, Lay::YROWS rows per pass: z += F s y, warp w staged rows
+    //      SPW w .. SPW w + SPW - 1, lanes along the element's dofs, RS rows at a time with their
+    //      dof-map and scaling loads issued before the adds
 #pragma unroll 1
-    for (int r0 = 16 * gwarp; r0 < 16 * gwarp + 16; r0 += RG) {
-      int32_t gi[RG][PPL][2];
+    for (int ph = 0; ph < kRows / Lay::YROWS; ++ph) {
+      if (erow / Lay::YROWS == ph) {  // warp-uniform: the quadrant's rows are in this pass
+        float* yrow = sY + (erow - ph * Lay::YROWS) * Lay::YS;
 #pragma unroll
-      for (int i = 0; i < RG; ++i) {
-        const int64_t e = tile * kRows + r0 + i;
-#pragma unroll
-        for (int w = 0; w < PPL; ++w)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = 2 * (lane + 32 * w) + h;
-            gi[i][w][h] = (k < din && e < ne) ? __ldg(&map[e * din + k]) : -1;
-          }
+        for (int c = 8 * part; c < DP; c += 8 * NQ) {
+          float v[8];
+          tmem_ld8(t_lane + (uint32_t)c, v);
+          *reinterpret_cast<float4*>(yrow + c) = make_float4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(yrow + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
       }
-      float fv[RG][PPL][2];
+      fence_before();
+      group_sync(g, GT);
+#pragma unroll 1
+      for (int s0 = SPW * gwarp; s0 < SPW * gwarp + SPW; s0 += RS) {
+        int32_t gi[RS][PPL][2];
 #pragma unroll
-      for (int i = 0; i < RG; ++i)
+        for (int i = 0; i < RS; ++i) {
+          const int64_t e = tile * kRows + ph * Lay::YROWS + s0 + i;
 #pragma unroll
-        for (int w = 0; w < PPL; ++w)
+          for (int w = 0; w < PPL; ++w)
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
-            fv[i][w][h] = gi[i][w][h] >= 0 ? __ldg(&fsc[gi[i][w][h]]) : 0.0f;
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * (lane + 32 * w) + h;
+              gi[i][w][h] = (k < din && e < ne) ? __ldg(&map[e * din + k]) : -1;
+            }
+        }
+        float fv[RS][PPL][2];
 #pragma unroll
-      for (int i = 0; i < RG; ++i) {
-        const int row = r0 + i;
-        const float s = sscale[row];
+        for (int i = 0; i < RS; ++i)
 #pragma unroll
-        for (int w = 0; w < PPL; ++w)
+          for (int w = 0; w < PPL; ++w)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int k = 2 * (lane + 32 * w) + h;
-            if (fv[i][w][h] != 0.0f)
-              atomicAdd(&z[gi[i][w][h]], (VT)(fv[i][w][h] * s * sY[row * Lay::YS + k]));
-          }
+            for (int h = 0; h < 2; ++h)
+              fv[i][w][h] = gi[i][w][h] >= 0 ? __ldg(&fsc[gi[i][w][h]]) : 0.0f;
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+          const float sc = sscale[ph * Lay::YROWS + s0 + i];
+#pragma unroll
+          for (int w = 0; w < PPL; ++w)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * (lane + 32 * w) + h;
+              if (fv[i][w][h] != 0.0f)
+                atomicAdd(&z[gi[i][w][h]], (VT)(fv[i][w][h] * sc * sY[(s0 + i) * Lay::YS + k]));
+            }
+        }
       }
+      group_sync(g, GT);  // the next pass (or tile's gather) rewrites the staging (and X)
     }
-    group_sync(g);  // the next tile's gather rewrites X (and the staging that aliases it)
   }
 
   // ---- teardown: a given-up wait is reported, in-flight MMAs get one more bounded wait, and

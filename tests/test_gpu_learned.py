@@ -108,13 +108,15 @@ def test_patch_apply_matches_oracle(dims, p, width):
 @pytest.mark.parametrize("dims,p,width", [((9, 8, 7), 1, 64), ((5, 4, 3), 2, 128),
                                           ((6, 5, 4), 3, 128), ((5, 5, 6), 3, 0),
                                           ((3, 4, 3), 4, 64), ((4, 3, 3), 4, 128),
-                                          ((50, 50, 50), 1, 128)])
+                                          ((50, 50, 50), 1, 128), ((9, 8, 7), 1, 256),
+                                          ((6, 5, 4), 3, 256), ((30, 30, 30), 2, 256)])
 def test_inference_kernels_match_oracle(dims, p, width):
-    """Every inference kernel built for (order, width) -- tcgen05 (one CTA per 128 elements, FP32
-    accumulators in tensor memory), the mma.sync fused kernel, the unfused GEMM path -- against
-    oracle/learned.py's patch operator element by element within its BF16 rounding bound. The
-    meshes leave a ragged last 128-element tile; at 50^3 the persistent tcgen05 grid takes
-    several tiles per CTA. No tcgen05 launch may give up a wait."""
+    """Every inference kernel built for (order, width) -- tcgen05 (128-element tiles, FP32
+    accumulators in tensor memory; at width 256 and D^3 >= 27 the hidden activations in tensor
+    memory too), the mma.sync fused kernel, the unfused GEMM path -- against oracle/learned.py's
+    patch operator element by element within its BF16 rounding bound. The meshes leave a ragged
+    last 128-element tile; at 50^3 (p = 1) and 30^3 (p = 2, width 256) the persistent tcgen05
+    grid takes several tiles per CTA. No tcgen05 launch may give up a wait."""
     torch = torch_cuda()
     with gpu_problem(*dims, p, sigma=1.0) as (fe, mesh, pa, V, c):
         prob = oop.Problem(*dims, p, V, coeff=c)
@@ -514,7 +516,7 @@ def test_trained_fcg_beats_jacobi_iterations(n, p, sigma, width):
             fe.fe_lpc_destroy(lpc)
 
 
-@pytest.mark.parametrize("width,sigma", [(0, None), (128, None), (0, 1.0)])
+@pytest.mark.parametrize("width,sigma", [(0, None), (128, None), (0, 1.0), (256, None)])
 def test_fcg_ir_learned_mixed_precision(width, sigma):
     """Mixed-precision refinement around the FP32 learned-FCG inner solve reaches the
     FP64-accurate 1e-8 residual and the Jacobi-PCG solution."""
@@ -542,8 +544,10 @@ def test_fcg_ir_learned_mixed_precision(width, sigma):
 
 
 def test_fcg_ir_rejects_unsupported_width():
+    """Order 4 (D^3 = 125) at width 256 has no FP32 fused kernel: its weights do not fit in
+    shared memory beside a tcgen05 tile, and the mma.sync kernel is not built for it."""
     torch = torch_cuda()
-    with gpu_problem(4, 4, 4, 3, ops=1) as (fe, mesh, pa, V, c):
+    with gpu_problem(3, 3, 3, 4, ops=1) as (fe, mesh, pa, V, c):
         nd, _, _ = fe.fe_mesh_sizes(mesh)
         b = torch.ones(nd, dtype=torch.float64, device="cuda")
         x = torch.empty_like(b)
