@@ -212,12 +212,14 @@ def run_refinement(args, local_rank):
     return 0
 
 
-def c5_learned(fe, torch, vs, b, args, sigma, s_pcg, t_pcg, stream, n_train=16):
-    """C5's learned leg: for each order of the space a linear patch map (width 0; fe_lpc_fit_linear,
-    least squares on operator-generated local-solve pairs) fitted on an n_train^3 single-order
-    mesh with the same log-normal coefficient distribution, attached to the space's order group
-    (fe_vspace_set_learned), then flexible CG on the first right-hand side to --rtol against the
-    single-system Jacobi-PCG above (iterations, time with CUDA events, FP64 true residual)."""
+def c5_learned(fe, torch, vs, b, args, sigma, s_pcg, t_pcg, stream, width=0, n_train=16):
+    """C5's learned leg: for each order of the space a patch network -- width 0: the linear map
+    fitted by least squares (fe_lpc_fit_linear); else the MLP of that width trained by --lpc-steps
+    Adam steps (fe_lpc_train) -- on operator-generated local-solve pairs of an n_train^3
+    single-order mesh with the same log-normal coefficient distribution, attached to the space's
+    order group (fe_vspace_set_learned), then flexible CG on the first right-hand side to --rtol
+    against the single-system Jacobi-PCG above (iterations, time with CUDA events, FP64 true
+    residual)."""
     from paper_2603_09038_gb300.inputs import perturbed_vertices, lognormal_coefficient
     t0 = time.perf_counter()
     fits = {}
@@ -226,9 +228,12 @@ def c5_learned(fe, torch, vs, b, args, sigma, s_pcg, t_pcg, stream, n_train=16):
         cm = torch.from_numpy(lognormal_coefficient(n_train ** 3, sigma)).cuda()
         mesh = fe.fe_mesh_setup(n_train, n_train, n_train, p, V)
         pa = fe.fe_pa_setup(mesh, 0, cm, fe.FE_DIFFUSION)
-        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 0, 5)
+        lpc = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, width, 5)
         try:
-            fits[p] = fe.fe_lpc_fit_linear(lpc)
+            if width == 0:
+                fits[p] = fe.fe_lpc_fit_linear(lpc)
+            else:
+                fits[p] = fe.fe_lpc_train(lpc, args.lpc_steps, 1024, 1e-3)
             fe.fe_vspace_set_learned(vs, fe.FE_DIFFUSION, p, lpc)
         finally:
             fe.fe_lpc_destroy(lpc)
@@ -245,9 +250,13 @@ def c5_learned(fe, torch, vs, b, args, sigma, s_pcg, t_pcg, stream, n_train=16):
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3
-    return {"preconditioner": "linear patch map per order (width 0), fitted by least squares on "
-                              "%d^3 single-order meshes, log-normal sigma %g" % (n_train, sigma),
-            "fit_relative_loss": fits, "setup_s": t_setup, "status": st, "fcg_iters": sf["iters"],
+    kind = ("linear patch map per order (width 0), fitted by least squares" if width == 0 else
+            "MLP per order (3 layers and a linear skip term, width %d, BF16), %d Adam steps"
+            % (width, args.lpc_steps))
+    return {"preconditioner": kind + " on %d^3 single-order meshes, log-normal sigma %g"
+                                     % (n_train, sigma),
+            "width": width, "fit_relative_loss": fits, "setup_s": t_setup, "status": st,
+            "fcg_iters": sf["iters"],
             "time_s": t, "ms_per_iter": 1e3 * t / max(1, sf["iters"]),
             "true_rel_resid": sf["true_rel_resid"], "fallbacks_to_jacobi": sf["outer_iters"] - 1,
             "jacobi_pcg_iters": s_pcg["iters"], "jacobi_pcg_time_s": t_pcg,
@@ -314,6 +323,9 @@ def run_c5(args, local_rank):
            "speedup_batched_vs_one_by_one": (nr * t1) / (per_iter_b * s1["iters"]),
            "gdofs_per_rhs_iteration_batched": ntrue * nr / per_iter_b / 1e9,
            "learned": c5_learned(fe, torch, vs, B[0].contiguous(), args, sigma, s1, t1, stream)}
+    if args.lpc_width > 0:   # the configured network (C5 names 3 layers of width 256)
+        out["learned_mlp"] = c5_learned(fe, torch, vs, B[0].contiguous(), args, sigma, s1, t1,
+                                        stream, width=args.lpc_width)
     fe.fe_vspace_destroy(vs)
     print(json.dumps(out))
     return 0

@@ -219,18 +219,51 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
                : "memory");
 }
 
-// 8 consecutive FP32 columns of the calling thread's TMEM lane (32x32b shape: warp w reads lanes
-// 32 (w % 4) .. 32 (w % 4) + 31, thread t lane 32 (w % 4) + t).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// NCOL (8, 16 or 32) consecutive FP32 columns of the calling thread's TMEM lane (32x32b shape:
+// warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31, thread t lane 32 (w % 4) + t).  The load and
+// its wait are one asm statement, so no use of the registers can be scheduled before the wait.
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  uint32_t r[NCOL];
+  if constexpr (NCOL == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr) : "memory");
+  } else if constexpr (NCOL == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr) : "memory");
+  } else {
+    static_assert(NCOL == 32, "8, 16 or 32 columns");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr) : "memory");
+  }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < NCOL; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Columns per TMEM load when the NQ warps of a lane quadrant share N columns in interleaved
+// chunks: as wide as the share allows, at most 32.
+__host__ __device__ constexpr int ld_cols(int N, int NQ) {
+  return N / NQ >= 32 ? 32 : (N / NQ >= 16 ? 16 : 8);
 }
 
 // Barrier of one pipeline's nt threads (named barrier 1 + g; barrier 0 is __syncthreads), and
@@ -248,7 +281,7 @@ __device__ __forceinline__ int group_or(int g, int nt, int v) {
 }
 
 // 8 consecutive 32-bit columns of the calling thread's TMEM lane, stored (the 32x32b shape of
-// tmem_ld8), and complete before return.
+// tmem_ld), and complete before return.
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&w)[8]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
@@ -294,35 +327,45 @@ __device__ __forceinline__ void issue_chain_ts(uint32_t tmem, uint32_t a, uint32
 }
 
 // Epilogues of a hidden layer: the thread's TMEM lane (its tile row), ReLU, BF16, as the next
-// layer's A operand; the NQ warps of a lane quadrant take interleaved column chunks (part =
-// this warp's rank among them).  Into the canonical [128][N] image at dst in shared memory:
+// layer's A operand; the NQ warps of a lane quadrant take interleaved chunks of CW columns (part
+// = this warp's rank among them), one TMEM load each.  Into the canonical [128][N] image at dst
+// in shared memory:
 template <int N, int NQ>
 __device__ __forceinline__ void relu_to_image(uint32_t t_lane, int row, int part,
                                               unsigned char* dst) {
+  constexpr int CW = ld_cols(N, NQ);
 #pragma unroll
-  for (int c = 8 * part; c < N; c += 8 * NQ) {
-    float v[8];
-    tmem_ld8(t_lane + (uint32_t)c, v);
-    uint4 pk;
-    pk.x = pack_bf16(fmaxf(v[0], 0.f), fmaxf(v[1], 0.f));
-    pk.y = pack_bf16(fmaxf(v[2], 0.f), fmaxf(v[3], 0.f));
-    pk.z = pack_bf16(fmaxf(v[4], 0.f), fmaxf(v[5], 0.f));
-    pk.w = pack_bf16(fmaxf(v[6], 0.f), fmaxf(v[7], 0.f));
-    *reinterpret_cast<uint4*>(dst + canon(row, c, N) * 2) = pk;
+  for (int c = CW * part; c < N; c += CW * NQ) {
+    float v[CW];
+    tmem_ld<CW>(t_lane + (uint32_t)c, v);
+#pragma unroll
+    for (int j = 0; j < CW; j += 8) {
+      uint4 pk;
+      pk.x = pack_bf16(fmaxf(v[j + 0], 0.f), fmaxf(v[j + 1], 0.f));
+      pk.y = pack_bf16(fmaxf(v[j + 2], 0.f), fmaxf(v[j + 3], 0.f));
+      pk.z = pack_bf16(fmaxf(v[j + 4], 0.f), fmaxf(v[j + 5], 0.f));
+      pk.w = pack_bf16(fmaxf(v[j + 6], 0.f), fmaxf(v[j + 7], 0.f));
+      *reinterpret_cast<uint4*>(dst + canon(row, c + j, N) * 2) = pk;
+    }
   }
 }
 // or into tensor memory from column acol of the same lane (16 values per 8 columns).
 template <int N, int NQ>
 __device__ __forceinline__ void relu_to_tmem(uint32_t t_lane, int part, uint32_t acol) {
+  constexpr int CW = ld_cols(N, NQ) < 16 ? 16 : ld_cols(N, NQ);
+  static_assert(N % (CW * NQ) == 0, "whole chunks");
 #pragma unroll
-  for (int c = 16 * part; c < N; c += 16 * NQ) {
-    float v[16];
-    tmem_ld8(t_lane + (uint32_t)c, *reinterpret_cast<float(*)[8]>(v));
-    tmem_ld8(t_lane + (uint32_t)c + 8u, *reinterpret_cast<float(*)[8]>(v + 8));
-    uint32_t w[8];
+  for (int c = CW * part; c < N; c += CW * NQ) {
+    float v[CW];
+    tmem_ld<CW>(t_lane + (uint32_t)c, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) w[i] = pack_bf16(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
-    tmem_st8(t_lane + acol + (uint32_t)(c / 2), w);
+    for (int j = 0; j < CW; j += 16) {
+      uint32_t w[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        w[i] = pack_bf16(fmaxf(v[j + 2 * i], 0.f), fmaxf(v[j + 2 * i + 1], 0.f));
+      tmem_st8(t_lane + acol + (uint32_t)((c + j) / 2), w);
+    }
   }
 }
 
@@ -498,12 +541,15 @@ __global__ void __launch_bounds__(G * WPG * 32, 1) k_lpc_tc(
     for (int ph = 0; ph < kRows / Lay::YROWS; ++ph) {
       if (erow / Lay::YROWS == ph) {  // warp-uniform: the quadrant's rows are in this pass
         float* yrow = sY + (erow - ph * Lay::YROWS) * Lay::YS;
+        constexpr int CW = ld_cols(DP, NQ);
 #pragma unroll
-        for (int c = 8 * part; c < DP; c += 8 * NQ) {
-          float v[8];
-          tmem_ld8(t_lane + (uint32_t)c, v);
-          *reinterpret_cast<float4*>(yrow + c) = make_float4(v[0], v[1], v[2], v[3]);
-          *reinterpret_cast<float4*>(yrow + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        for (int c = CW * part; c < DP; c += CW * NQ) {
+          float v[CW];
+          tmem_ld<CW>(t_lane + (uint32_t)c, v);
+#pragma unroll
+          for (int j = 0; j < CW; j += 4)
+            *reinterpret_cast<float4*>(yrow + c + j) = make_float4(v[j], v[j + 1], v[j + 2],
+                                                                   v[j + 3]);
         }
       }
       fence_before();
