@@ -5,9 +5,12 @@
 // f(x) = relu(relu(x W1) W2) W3 + x W0 (W = 0: the linear patch map f(x) = x W0) -- the same
 // operator as mlp::k_lpc_fused, re-tiled for tcgen05:
 //   * a tile of 128 elements (the 128 rows of every layer's M = 128 MMA) is taken by a pipeline
-//     of 8 warps; a CTA runs two pipelines on interleaved tiles where their shared memory fits (their own operand tiles, TMEM
-//     columns, mbarriers and named barriers), so that one gathers or scatters while the other
-//     waits, and they share one copy of the weights;
+//     of 8 warps; a CTA runs two pipelines on interleaved tiles where their shared memory fits
+//     (their own operand tiles, TMEM columns, mbarriers and named barriers), so that one gathers
+//     or scatters while the other waits, and they share one copy of the weights;
+//   * at width 256 the weights alone nearly fill shared memory: one pipeline of 16 warps keeps
+//     the hidden activations in tensor memory instead (ReLU's BF16 output stored by tcgen05.st
+//     beside the accumulator, read back by the next layer's MMA as its A operand);
 //   * the weights live in shared memory for the whole persistent kernel, copied once by
 //     cp.async.bulk behind an mbarrier, as BF16 images in the tensor core's canonical K-major
 //     layout without swizzle (8-row x 16-byte core matrices, element (n, k) of an N x K image at
@@ -19,8 +22,9 @@
 //     accumulator of 128 TMEM lanes x N columns and commits it to an mbarrier; the epilogue
 //     warps read their lane quadrant back with tcgen05.ld, apply ReLU and write the BF16 A
 //     operand of the next layer; layer 3 and the skip term accumulate into the same columns;
-//   * the result goes through a shared staging tile so that the scatter's dof-map reads and
-//     atomic adds are warp-coalesced along each element's dofs.
+//   * the result goes through a shared staging tile (in two 64-row passes at width 256, where
+//     only X's space is free for it) so that the scatter's dof-map reads and atomic adds are
+//     warp-coalesced along each element's dofs.
 // Every wait on an mbarrier has an iteration limit: on expiry the kernel raises a device flag,
 // all threads leave the tile loop together, and the TMEM is freed before the kernel returns.
 #pragma once
