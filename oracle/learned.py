@@ -85,8 +85,10 @@ def vspace_patch_apply(space, vertices, kind, nets, r, coeff=None, E=None, bound
     dof's node) is that true dof's row, shared by every element that reaches it; every other row
     (a constrained node of one element) is its own row.  R_e picks element e's rows; F = (mult
     diag)^-1/2 per X row, mult = the number of element rows mapped to it and diag = the sum of
-    their element-matrix diagonal entries, F = 0 on boundary rows (a boundary true dof, or a
-    constrained row whose stored weights all sit on boundary true dofs).  r is taken zero and the
+    their element-matrix diagonal entries, F = 0 on the rows that carry no patch unknown: the
+    boundary true dofs and every constrained row (the true dofs it interpolates are unknowns of
+    the elements that own them; gathering E r there too would count their residual twice).
+    r is taken zero and the
     result is zeroed on the boundary true dofs, so that M = (1-m) M (1-m); elements with s_e = 0
     add nothing.  With one order everywhere this is
     patch_apply's operator.  nets: {order: f(Xn, elems) -> Y}; E: the prolongation with the
@@ -103,11 +105,8 @@ def vspace_patch_apply(space, vertices, kind, nets, r, coeff=None, E=None, bound
     own = np.nonzero(~unit)[0]
     xrow[own] = ntrue + np.arange(own.size)
     nX = ntrue + own.size
-    maskX = np.zeros(nX, dtype=bool)
+    maskX = np.ones(nX, dtype=bool)
     maskX[:ntrue] = mask
-    for t, i in enumerate(own):
-        cols = E.indices[E.indptr[i]:E.indptr[i + 1]]
-        maskX[ntrue + t] = bool(np.all(mask[cols]))
     if mats is None:
         mats = space.element_matrices(vertices, kind, coeff)
     dloc = np.concatenate([np.diag(K) for K in mats])

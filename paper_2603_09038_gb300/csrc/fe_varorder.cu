@@ -630,8 +630,8 @@ struct fe_vspace {
   fe_pa* group_pa[kMaxOrder];
   // learned patch preconditioner: one network per order group (copies of networks trained on
   // single-order meshes), applied in the X numbering with one shared input/output scaling
-  uint8_t* d_maskX = nullptr;           // [ntrue + nc]: boundary rows of X (a constrained row when
-                                        // every true dof it interpolates is a boundary dof)
+  uint8_t* d_maskX = nullptr;           // [ntrue + nc]: rows of X without patch unknowns (the
+                                        // boundary true dofs and every constrained row)
   fe_lpc* group_lpc[kMaxOrder] = {};    // owned
   int lpc_op = 0;
   double* d_FX = nullptr;               // [ntrue + nc]: the shared scaling (mult_X diag_X)^(-1/2)
@@ -766,15 +766,11 @@ static int vspace_setup(int nx, int ny, int nz, const int32_t* host_order,
   if (err == cudaSuccess) err = upload(&vs->d_tval, H.tval);
   if (err == cudaSuccess) err = upload(&vs->d_mask, mask);
   if (err == cudaSuccess) {
-    // X rows on the boundary: true dofs by the mask, constrained rows when all of theirs are
+    // X rows without patch unknowns: the boundary true dofs, and every constrained row (its
+    // value interpolates true dofs that are patch unknowns of the elements owning them, so
+    // gathering the residual there as well would count it twice)
     std::vector<uint8_t> maskX(mask.begin(), mask.end());
     maskX.resize((size_t)nX, 1);
-    for (int64_t c = 0; c < nc; ++c)
-      for (int64_t k = H.cptr[c]; k < H.cptr[c + 1]; ++k)
-        if (!mask[H.ccol[k]]) {
-          maskX[T.ntrue + c] = 0;
-          break;
-        }
     err = upload(&vs->d_maskX, maskX);
   }
   if (err == cudaSuccess) err = cudaMalloc(&vs->d_X, sizeof(double) * std::max<int64_t>(1, nX));
