@@ -84,10 +84,12 @@ def vspace_patch_apply(space, vertices, kind, nets, r, coeff=None, E=None, bound
     in the local numbering X: a row of E with a single stored weight (a node that is a true
     dof's node) is that true dof's row, shared by every element that reaches it; every other row
     (a constrained node of one element) is its own row.  R_e picks element e's rows; F = (mult
-    diag)^-1/2 per X row, mult = the number of element rows mapped to it and diag = the sum of
-    their element-matrix diagonal entries, F = 0 on the rows that carry no patch unknown: the
-    boundary true dofs and every constrained row (the true dofs it interpolates are unknowns of
-    the elements that own them; gathering E r there too would count their residual twice).
+    diag)^-1/2 per X row, mult = the number of element rows mapped to it and diag = the space's
+    Jacobi diagonal diag(E^T blockdiag(diag A_e) E) at its true dof (space.jacobi_diagonal: the
+    higher-order neighbours that read the dof through constrained nodes count too), F = 0 on the
+    rows that carry no patch unknown: the boundary true dofs and every constrained row (the true
+    dofs it interpolates are unknowns of the elements that own them; gathering E r there too
+    would count their residual twice).
     r is taken zero and the
     result is zeroed on the boundary true dofs, so that M = (1-m) M (1-m); elements with s_e = 0
     add nothing.  With one order everywhere this is
@@ -109,9 +111,10 @@ def vspace_patch_apply(space, vertices, kind, nets, r, coeff=None, E=None, bound
     maskX[:ntrue] = mask
     if mats is None:
         mats = space.element_matrices(vertices, kind, coeff)
-    dloc = np.concatenate([np.diag(K) for K in mats])
+    dloc = np.concatenate([np.diag(K) for K in mats])    # element diagonals, local row order
     mult = np.bincount(xrow, minlength=nX).astype(np.float64)
-    diag = np.bincount(xrow, weights=dloc, minlength=nX)
+    diag = np.zeros(nX)
+    diag[:ntrue] = E.multiply(E).T @ dloc               # sum_i E_ij^2 (A_e)_ii
     live_rows = (~maskX) & (mult > 0) & (diag > 0)
     F = np.zeros(nX)
     F[live_rows] = 1.0 / np.sqrt(mult[live_rows] * diag[live_rows])

@@ -1296,8 +1296,11 @@ void fe_vspace_destroy(fe_vspace* vs) {
 //      sum_e R_e^T s_e f_p(e)(x_e / s_e), x_e = R_e F_X E r, one network f_p per order (the
 //      order group's copy of a network trained on a single-order mesh), R_e the element's rows
 //      of X = [r; C r], F_X the shared scaling (mult_X diag_X)^(-1/2) of the X rows: mult_X counts
-//      the element rows of every order mapped to an X row, diag_X sums their element diagonals
-//      (0 on boundary X rows).  With one order everywhere this is the single-order operator.
+//      the element rows of every order mapped to an X row, diag_X is the space's Jacobi diagonal
+//      diag(E^T blockdiag(diag A_e) E) of its true dof (the higher-order neighbours reading it
+//      through constrained nodes included), and F_X is 0 on the rows without patch unknowns (the
+//      boundary true dofs and every constrained row).  With one order everywhere this is the
+//      single-order operator.
 namespace {
 
 __global__ void k_count_rows(const int32_t* __restrict__ map, int64_t n, double* __restrict__ c) {
@@ -1337,14 +1340,21 @@ int vspace_lpc_scaling(fe_vspace* vs, int op, cudaStream_t s) {
     return cuda_error(err, "fe_vspace_set_learned: scaling cudaMalloc");
   }
   double* mult = nullptr;
-  if ((err = cudaMalloc(&mult, sizeof(double) * nX)) != cudaSuccess)
+  if ((err = cudaMalloc(&mult, sizeof(double) * (nX + vs->ntrue))) != cudaSuccess)
     return cuda_error(err, "fe_vspace_set_learned: scaling cudaMalloc");
+  double* dtrue = mult + nX;
   int st = FE_OK;
   cudaMemsetAsync(mult, 0, sizeof(double) * nX, s);
   k_count_rows<<<grid_of(vs->nlocal), 256, 0, s>>>(vs->d_map, vs->nlocal, mult);
   cudaMemsetAsync(vs->d_Y, 0, sizeof(double) * nX, s);
   for (int g = 0; g < vs->ngroups && st == FE_OK; ++g)
     st = diagonal_accumulate(vs->group_pa[g], op, vs->d_Y, s);
+  // the true-dof rows take the space's Jacobi diagonal (constrained rows folded in)
+  if (st == FE_OK) st = fold_Y(vs, dtrue, 1, s);
+  if (st == FE_OK)
+    st = cuda_error(cudaMemcpyAsync(vs->d_Y, dtrue, sizeof(double) * vs->ntrue,
+                                    cudaMemcpyDeviceToDevice, s),
+                    "fe_vspace_set_learned: scaling copy");
   if (st == FE_OK) {
     k_fx<<<grid_of(nX), 256, 0, s>>>(mult, vs->d_Y, vs->d_maskX, vs->d_FX, nX);
     for (int g = 0; g < vs->ngroups && st == FE_OK; ++g)

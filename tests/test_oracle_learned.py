@@ -194,10 +194,12 @@ def test_vspace_patch_operator_symmetric_for_a_symmetric_linear_map():
     assert np.all(M[~interior] == 0.0) and np.all(M[:, ~interior] == 0.0)
 
 
-def _mean_scaled_inverse(p, n=4):
-    """Mean over the interior elements of a unit-coefficient n^3 order-p mesh of the scaled local
-    inverse S_e^-1 A_ee^-1 S_e^-1 (the map an exact patch network would realise)."""
-    prob = oop.Problem(n, n, n, p, perturbed_vertices(n, n, n))
+def _mean_scaled_inverse(p, sigma, n=4):
+    """Mean over the interior elements of an n^3 order-p mesh (log-normal coefficient sigma, its
+    own seed) of the scaled local inverse S_e^-1 A_ee^-1 S_e^-1 (the map an exact patch network
+    would realise)."""
+    c = None if sigma == 0 else np.exp(sigma * np.random.default_rng(11).standard_normal(n ** 3))
+    prob = oop.Problem(n, n, n, p, perturbed_vertices(n, n, n), coeff=c)
     A = oop.assemble(prob, DIFFUSION)
     _, S, _ = ol.patch_data(prob, DIFFUSION)
     d = (p + 1) ** 3
@@ -212,11 +214,14 @@ def _mean_scaled_inverse(p, n=4):
     return acc / cnt
 
 
-def test_vspace_patch_operator_beats_jacobi_with_exact_patch_maps():
+@pytest.mark.parametrize("sigma", [0.0, 2.0])
+def test_vspace_patch_operator_beats_jacobi_with_exact_patch_maps(sigma):
     """Per-order maps set to the mean exact scaled local inverse of a single-order mesh: flexible
     CG with the variable-order patch operator needs fewer iterations than Jacobi on a mixed-order
-    space. This fails when the constrained rows also gather E r (that counts the residual of the
-    true dofs they interpolate twice, and made FCG slower than Jacobi)."""
+    space, with a unit and a log-normal (sigma = 2) coefficient. This fails when the constrained
+    rows also gather E r (that counts the residual of the true dofs they interpolate twice), and
+    at sigma = 2 when a true dof's scaling leaves out the higher-order neighbours that read it
+    through constrained nodes."""
     from oracle.varorder import VarSpace
     from paper_2603_09038_gb300.inputs import block_orders
     import scipy.sparse as sp
@@ -225,17 +230,19 @@ def test_vspace_patch_operator_beats_jacobi_with_exact_patch_maps():
     assert len(set(orders.tolist())) == 2
     S = VarSpace(n, n, n, orders)
     V = perturbed_vertices(n, n, n)
-    E, mats = S.prolongation(), S.element_matrices(V, DIFFUSION)
-    A = S.assemble(V, DIFFUSION, sparse=True).tocsr()
+    c = None if sigma == 0 else np.exp(sigma * np.random.default_rng(2).standard_normal(n ** 3))
+    E, mats = S.prolongation(), S.element_matrices(V, DIFFUSION, c)
+    A = S.assemble(V, DIFFUSION, coeff=c, sparse=True).tocsr()
     inner = (S.boundary_mask() == 0).astype(np.float64)
     Abc = (sp.diags(inner) @ A @ sp.diags(inner) + sp.diags(1.0 - inner)).tocsr()
     nets = {}
     for p in (2, 3):
-        T = _mean_scaled_inverse(p)
+        T = _mean_scaled_inverse(p, sigma)
         nets[p] = (lambda T_: (lambda Xn, el: Xn @ T_.T))(T)
     b = np.random.default_rng(5).uniform(-1, 1, S.ntrue) * inner
     diag = Abc.diagonal()
     _, it_j, _, _ = ol.fcg(Abc, lambda r: r / diag, b, rtol=1e-8)
-    _, it_l, _, _ = ol.fcg(Abc, lambda r: ol.vspace_patch_apply(S, V, DIFFUSION, nets, r, E=E,
-                                                                mats=mats), b, rtol=1e-8)
+    _, it_l, _, _ = ol.fcg(Abc, lambda r: ol.vspace_patch_apply(S, V, DIFFUSION, nets, r,
+                                                                coeff=c, E=E, mats=mats),
+                           b, rtol=1e-8)
     assert it_l < 0.85 * it_j, (it_l, it_j)
