@@ -371,13 +371,15 @@ int fe_lpc_nparams(const fe_lpc* lpc, int64_t* nparams);
 int fe_lpc_train(fe_lpc* lpc, int steps, int batch, double lr, int reps, double* final_loss,
                  void* stream);
 
-/* Least-squares fit of the linear term: W0 = argmin sum ||x W0 - t||^2 + ridge mean(diag X^T X)
- * ||W0||^2 over the whole training set (generated first if needed, `reps` pairs per sampled
+/* Least-squares fit of the linear term: W = argmin sum ||x W - t||^2 + ridge mean(diag X^T X)
+ * ||W||^2 over the whole training set (generated first if needed, `reps` pairs per sampled
  * element, 0 => 16), by the normal equations -- X^T X and X^T T with the BF16 tensor-core GEMM
- * (FP32 accumulation), FP64 Cholesky on the host -- in milliseconds instead of Adam steps.  The
- * other weights are untouched: for width 0 this is the whole preconditioner; for an MLP it is a
- * starting point for fe_lpc_train.  *fit_loss (may be NULL): the relative squared error of the
- * fit on the training set.  Synchronous. */
+ * (FP32 accumulation), FP64 Cholesky on the host -- in milliseconds instead of Adam steps; W0 =
+ * (W + W^T) / 2, its symmetric part (the scaled local inverse it approximates is symmetric; an
+ * antisymmetric remainder from sampling makes flexible CG stall at high coefficient contrast).
+ * The other weights are untouched: for width 0 this is the whole preconditioner; for an MLP it
+ * is a starting point for fe_lpc_train.  *fit_loss (may be NULL): the relative squared error of
+ * W0 on the training set.  Synchronous. */
 int fe_lpc_fit_linear(fe_lpc* lpc, double ridge, int reps, double* fit_loss, void* stream);
 
 /* Copies the FP32 master weights (fe_lpc_nparams floats) to host_w (set = 0) or from host_w

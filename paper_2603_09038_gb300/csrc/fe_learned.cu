@@ -1750,7 +1750,7 @@ int fe_lpc_fit_linear(fe_lpc* L, double ridge, int reps, double* fit_loss, void*
   cudaFree(tb);
   cudaFree(gh);
   if (err != cudaSuccess) return cuda_error(err, "fe_lpc_fit_linear: copy");
-  // (G + ridge mean(diag G) I) W0 = H by FP64 Cholesky on the host (d <= 125)
+  // (G + ridge mean(diag G) I) W0 = H by FP64 Cholesky on the host
   std::vector<double> G(d * d), W(d * d);
   double tr = 0.0;
   for (int i = 0; i < d; ++i) tr += hgh[i * d + i];
@@ -1781,6 +1781,15 @@ int fe_lpc_fit_linear(fe_lpc* L, double ridge, int reps, double* fit_loss, void*
       W[i * d + c] = v / G[i * d + i];
     }
   }
+  // the map kept is the symmetric part of the fit: the local inverse it approximates is
+  // symmetric, and an antisymmetric remainder (sampling noise, a few per cent) makes flexible CG
+  // with one stored direction stall and fall back at high coefficient contrast
+  for (int i = 0; i < d; ++i)
+    for (int c = i + 1; c < d; ++c) {
+      const double v = 0.5 * (W[i * d + c] + W[c * d + i]);
+      W[i * d + c] = v;
+      W[c * d + i] = v;
+    }
   // loss = (||T||^2 - 2 tr(W^T H) + tr(W^T G W)) / ||T||^2 with the unregularised G
   double cross = 0.0, quad = 0.0;
   for (int i = 0; i < d; ++i)

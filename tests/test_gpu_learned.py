@@ -563,8 +563,9 @@ def test_fcg_ir_rejects_unsupported_width():
 
 
 def test_fit_linear_matches_adam_and_beats_jacobi():
-    """The least-squares fit of the linear patch map reaches at most the relative loss of 2000
-    Adam steps on the same training set, and FCG with it beats Jacobi-PCG in iterations."""
+    """The least-squares fit of the linear patch map (its symmetric part, exactly symmetric in
+    FP32) reaches at most the relative loss of 2000 Adam steps on the same training set, and FCG
+    with it beats Jacobi-PCG in iterations."""
     torch = torch_cuda()
     n, p = 16, 3
     with gpu_problem(n, n, n, p, ops=1) as (fe, mesh, pa, V, c):
@@ -578,6 +579,8 @@ def test_fit_linear_matches_adam_and_beats_jacobi():
         adam = fe.fe_lpc_create(pa, fe.FE_DIFFUSION, 0, 4)
         try:
             lf = fe.fe_lpc_fit_linear(fit, 1e-6)
+            w0 = fe.fe_lpc_weights(fit).reshape(64, 64)
+            assert np.array_equal(w0, w0.T)
             la = fe.fe_lpc_train(adam, 2000, 1024, 1e-3)
             assert 0.0 <= lf <= la * 1.05 + 1e-3, (lf, la)
             st, sf = fe.fe_fcg(pa, fe.FE_DIFFUSION, fit, b, x, 1e-8, 20000)
