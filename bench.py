@@ -255,7 +255,8 @@ def c5_learned(fe, torch, vs, b, args, sigma, s_pcg, t_pcg, stream, width=0, n_t
             % (width, args.lpc_steps))
     return {"preconditioner": kind + " on %d^3 single-order meshes, log-normal sigma %g"
                                      % (n_train, sigma),
-            "width": width, "fit_relative_loss": fits, "setup_s": t_setup, "status": st,
+            "width": width, ("fit_relative_loss" if width == 0 else "final_batch_loss"): fits,
+            "setup_s": t_setup, "status": st,
             "fcg_iters": sf["iters"],
             "time_s": t, "ms_per_iter": 1e3 * t / max(1, sf["iters"]),
             "true_rel_resid": sf["true_rel_resid"], "fallbacks_to_jacobi": sf["outer_iters"] - 1,

@@ -612,11 +612,11 @@ int fe_vspace_pcg_batched(fe_vspace* vs, int op, int nrhs, const double* dev_b, 
 /* The learned patch preconditioner on a variable-order space (an extension; the paper has no
  * learned part): one network per order, M(r) = E^T F_X sum_e R_e^T s_e f_p(e)(x_e / s_e) with
  * x_e = R_e F_X E r, s_e = ||x_e||_2, R_e element e's rows of the local vector E r (true dofs
- * and the constrained rows C r), and F_X = (mult_X diag_X)^(-1/2) on those rows: mult_X the
- * number of element rows of every order that read the row, diag_X the sum of their element
- * diagonals (0 on boundary rows; a constrained row is a boundary row when every true dof it
- * interpolates is one); r is taken zero on the boundary.  With one order everywhere M is
- * fe_lpc_apply's operator.
+ * and the constrained rows C r), and F_X = (mult_X diag_X)^(-1/2) on the true-dof rows: mult_X
+ * the number of element rows of every order that read the row, diag_X the true dof's entry of
+ * fe_vspace_diagonal; F_X = 0 on the boundary rows and on every constrained row (the true dofs
+ * it interpolates are patch unknowns of the elements that own them); r is taken zero on the
+ * boundary.  With one order everywhere M is fe_lpc_apply's operator.
  * fe_vspace_set_learned attaches to the order group `order` a copy of the weights of `trained`
  * (an fe_lpc of that order, trained or fitted on a single-order mesh; the copy is owned by vs
  * and recomputes F_X), or detaches it (trained = NULL); networks of another operator are
